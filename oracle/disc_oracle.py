@@ -1,0 +1,501 @@
+"""Plain FP64 CPU oracle for the DISC hot path (Zhen et al., arXiv 1204.6295).
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the CPU
+baseline leg of the benchmark may import this module.  The CUDA library never
+calls it and shares no code with it.
+
+Every function follows one passage of the paper, in the paper's notation, with
+numpy float64 arrays and no blocking, fusion or reordering beyond what the
+definition states.  Where the paper is silent or garbled the reading used is
+stated in the docstring (readings R1..R16, listed with their reasons in the
+design notes of the repository).
+
+Layout: images are ``[nz][ny][nx]`` (x fastest); fields are ``[3][nz][ny][nx]``
+with components (x, y, z), in voxel units of the level they live on.
+
+Roles (Sec. 2.2): the moving image ``I_m`` is the planning CT, the static image
+``I_s`` is the CBCT; the field ``r`` relates them by ``I_m(x + r(x)) = I_s(x)``
+(Sec. 2.1).
+
+Pins: every function here is checked in ``tests/test_oracle_pins.py`` against
+brute force, closed forms, library special cases or invariants.  The one
+function without an independent pin is noted as "parity unpinned" below
+(none at present).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import List
+
+import numpy as np
+
+AXES = ("x", "y", "z")          # field component order
+ARRAY_AXIS = {0: 2, 1: 1, 2: 0}  # field component -> numpy axis of [nz][ny][nx]
+
+FORCE_THIRION = 0
+FORCE_DOUBLE = 1
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2.3, first paragraph; Algorithm A1, first line: global intensity shift
+# ---------------------------------------------------------------------------
+
+def global_shift(I_m, I_s):
+    """Shift the CBCT by the constant dHU that equalises the two image means.
+
+    Sec. 2.3: a constant shift of the CBCT intensity so that the mean
+    intensities of CT and CBCT agree.  Returns (shifted I_s, dHU).
+    """
+    I_m = np.asarray(I_m, np.float64)
+    I_s = np.asarray(I_s, np.float64)
+    dHU = I_m.mean() - I_s.mean()
+    return I_s + dHU, dHU
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2.3, multi-scale strategy; Algorithm A1 "down-sample" / "up-sample"
+# Reading R13: 2x2x2 mean down-sampling, cell-centred trilinear up-sampling.
+# ---------------------------------------------------------------------------
+
+def level_dims(dims, levels):
+    """Grid sizes (nx, ny, nz) of each pyramid level, finest first.
+
+    Each coarser level has ceil(n/2) voxels per axis (reading R13).
+    """
+    out = [tuple(int(d) for d in dims)]
+    for _ in range(1, levels):
+        out.append(tuple((d + 1) // 2 for d in out[-1]))
+    return out
+
+
+def downsample2(img):
+    """Mean over each 2x2x2 cell; a partial last cell averages its in-bounds voxels."""
+    img = np.asarray(img, np.float64)
+    nz, ny, nx = img.shape
+    cz, cy, cx = (nz + 1) // 2, (ny + 1) // 2, (nx + 1) // 2
+    acc = np.zeros((cz, cy, cx))
+    cnt = np.zeros((cz, cy, cx))
+    for dz in (0, 1):
+        for dy in (0, 1):
+            for dx in (0, 1):
+                sub = img[dz::2, dy::2, dx::2]
+                acc[:sub.shape[0], :sub.shape[1], :sub.shape[2]] += sub
+                cnt[:sub.shape[0], :sub.shape[1], :sub.shape[2]] += 1.0
+    return acc / cnt
+
+
+def _clamped_linear_coords(n_fine, n_coarse):
+    """Index pairs and weights mapping fine voxel i to coarse position (i - 0.5)/2."""
+    pos = (np.arange(n_fine, dtype=np.float64) - 0.5) / 2.0
+    pos = np.clip(pos, 0.0, n_coarse - 1)
+    i0 = np.floor(pos).astype(np.int64)
+    t = pos - i0
+    i1 = np.minimum(i0 + 1, n_coarse - 1)
+    return i0, i1, t
+
+
+def upsample_field2(r_coarse, fine_shape):
+    """Coarse field -> fine field: trilinear at (x - 0.5)/2, values doubled.
+
+    The field is in voxel units, and a coarse voxel spans two fine voxels, so
+    the displacement magnitude doubles (reading R13).
+    """
+    r_coarse = np.asarray(r_coarse, np.float64)
+    nzf, nyf, nxf = fine_shape
+    _, nzc, nyc, nxc = r_coarse.shape
+    zi0, zi1, tz = _clamped_linear_coords(nzf, nzc)
+    yi0, yi1, ty = _clamped_linear_coords(nyf, nyc)
+    xi0, xi1, tx = _clamped_linear_coords(nxf, nxc)
+    out = np.zeros((3, nzf, nyf, nxf))
+    for c in range(3):
+        v = r_coarse[c]
+        acc = np.zeros((nzf, nyf, nxf))
+        for zi, wz in ((zi0, 1 - tz), (zi1, tz)):
+            for yi, wy in ((yi0, 1 - ty), (yi1, ty)):
+                for xi, wx in ((xi0, 1 - tx), (xi1, tx)):
+                    w = wz[:, None, None] * wy[None, :, None] * wx[None, None, :]
+                    acc += w * v[np.ix_(zi, yi, xi)]
+        out[c] = 2.0 * acc
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2.1, I_m(x + v(x)); Sec. 2.3 kernel 5 (interpolation kernel)
+# Reading R6: trilinear, sample position clamped to [0, n-1] per axis.
+# ---------------------------------------------------------------------------
+
+def warp(I_m, r):
+    """Deformed moving image I_m^(k)(x) = I_m(x + r(x)), trilinear interpolation."""
+    I_m = np.asarray(I_m, np.float64)
+    r = np.asarray(r, np.float64)
+    nz, ny, nx = I_m.shape
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    px = np.clip(x + r[0], 0.0, nx - 1)
+    py = np.clip(y + r[1], 0.0, ny - 1)
+    pz = np.clip(z + r[2], 0.0, nz - 1)
+    x0 = np.floor(px).astype(np.int64)
+    y0 = np.floor(py).astype(np.int64)
+    z0 = np.floor(pz).astype(np.int64)
+    tx, ty, tz = px - x0, py - y0, pz - z0
+    x1 = np.minimum(x0 + 1, nx - 1)
+    y1 = np.minimum(y0 + 1, ny - 1)
+    z1 = np.minimum(z0 + 1, nz - 1)
+    out = np.zeros(I_m.shape)
+    for zi, wz in ((z0, 1 - tz), (z1, tz)):
+        for yi, wy in ((y0, 1 - ty), (y1, ty)):
+            for xi, wx in ((x0, 1 - tx), (x1, tx)):
+                out += wz * wy * wx * I_m[zi, yi, xi]
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Eq. (3): raw moments of a patch; reading R7: truncated box at the borders
+# ---------------------------------------------------------------------------
+
+def box_sum(X, half):
+    """Sum of X over the box |dx|<=hx, |dy|<=hy, |dz|<=hz clipped to the volume.
+
+    ``half`` = (hx, hy, hz).  Out-of-volume positions contribute nothing.
+    """
+    X = np.asarray(X, np.float64)
+    out = X
+    for comp, h in enumerate(half):
+        ax = ARRAY_AXIS[comp]
+        n = out.shape[ax]
+        acc = np.zeros(out.shape)
+        for d in range(-h, h + 1):
+            # acc[i] += out[i + d] where 0 <= i + d < n
+            lo, hi = max(0, -d), min(n, n - d)
+            if lo >= hi:
+                continue
+            dst = [slice(None)] * 3
+            src = [slice(None)] * 3
+            dst[ax] = slice(lo, hi)
+            src[ax] = slice(lo + d, hi + d)
+            acc[tuple(dst)] += out[tuple(src)]
+        out = acc
+    return out
+
+
+def box_count(shape, half):
+    """Number of in-volume voxels n(x) of the truncated box around each voxel."""
+    return box_sum(np.ones(shape), half)
+
+
+def patch_moments(X, half):
+    """First and second raw moments E(X), E(X^2) of the patch around each voxel (Eq. 3)."""
+    n = box_count(X.shape, half)
+    E1 = box_sum(X, half) / n
+    E2 = box_sum(np.asarray(X, np.float64) ** 2, half) / n
+    return E1, E2
+
+
+def patch_std(E1, E2):
+    """STD = sqrt(E(X^2) - E(X)^2) (Appendix, Eq. A.4), clipped at 0 for rounding."""
+    return np.sqrt(np.maximum(E2 - E1 * E1, 0.0))
+
+
+# ---------------------------------------------------------------------------
+# Eqs. (2)-(6) and Appendix A.1-A.7: moment matching; Sec. 2.2: I'_s = a I_s + b
+# Reading R9: a = 0 where the CBCT patch variance is <= var_floor.
+# ---------------------------------------------------------------------------
+
+def intensity_coefficients(m, I_s, half, var_floor=1e-6):
+    """Per-voxel a(x), b(x) of Eqs. (5), (6) from patches of I_m^(k) and I_s.
+
+    a = STD(M) / STD(S),  b = E(M) - a E(S).  Where Var(S) <= var_floor the
+    ratio is undefined; a = 0 there (so I'_s = E(M)).
+    """
+    EM, EM2 = patch_moments(m, half)
+    ES, ES2 = patch_moments(I_s, half)
+    var_m = np.maximum(EM2 - EM * EM, 0.0)
+    var_s = np.maximum(ES2 - ES * ES, 0.0)
+    std_m = np.where(var_m > var_floor, np.sqrt(var_m), 0.0)
+    ok = var_s > var_floor
+    std_s = np.sqrt(np.where(ok, var_s, 1.0))
+    a = np.where(ok, std_m / std_s, 0.0)
+    b = EM - a * ES
+    return a, b
+
+
+def correct(m, I_s, half, var_floor=1e-6):
+    """Intensity-corrected static image I'_s = a I_s + b (Sec. 2.2, last paragraph)."""
+    a, b = intensity_coefficients(m, I_s, half, var_floor)
+    return a * np.asarray(I_s, np.float64) + b
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2.3 kernel 3 (gradient kernel); reading R10: central differences in
+# the interior, one-sided first-order differences at the faces, voxel units.
+# ---------------------------------------------------------------------------
+
+def gradient(f):
+    """Gradient of an image, returned as [3][nz][ny][nx] with components (x, y, z)."""
+    f = np.asarray(f, np.float64)
+    g = np.zeros((3,) + f.shape)
+    for comp in range(3):
+        ax = ARRAY_AXIS[comp]
+        n = f.shape[ax]
+        if n < 2:
+            continue
+        fm = np.moveaxis(f, ax, 0)
+        gm = np.moveaxis(g[comp], ax, 0)
+        gm[1:n - 1] = (fm[2:] - fm[:n - 2]) / 2.0
+        gm[0] = fm[1] - fm[0]
+        gm[n - 1] = fm[n - 1] - fm[n - 2]
+    return g
+
+
+# ---------------------------------------------------------------------------
+# Eq. (1): demons force.  Reading R1: the image difference is taken as
+# (I'_s - I_m^(k)) so that adding dr moves I_m(x + r) toward I_s under the
+# Sec. 2.1 convention.  Reading R11: a term is 0 where its denominator is
+# <= 1e-9.  Reading R2: THIRION = first (passive) term; DOUBLE = both terms.
+# ---------------------------------------------------------------------------
+
+def force(m, f, mode=FORCE_THIRION, den_floor=1e-9):
+    """Displacement increment dr at every voxel ([3][nz][ny][nx])."""
+    m = np.asarray(m, np.float64)
+    f = np.asarray(f, np.float64)
+    diff = f - m
+    gf = gradient(f)
+    den = (gf ** 2).sum(axis=0) + diff ** 2
+    safe = np.where(den > den_floor, den, 1.0)
+    dr = np.where(den > den_floor, diff / safe, 0.0) * gf
+    if mode == FORCE_DOUBLE:
+        gm = gradient(m)
+        den2 = (gm ** 2).sum(axis=0) + diff ** 2
+        safe2 = np.where(den2 > den_floor, den2, 1.0)
+        dr = dr + np.where(den2 > den_floor, diff / safe2, 0.0) * gm
+    return dr
+
+
+# ---------------------------------------------------------------------------
+# Algorithm A1 step 6 and Sec. 2.3 kernel 2: Gaussian regularisation of r.
+# Reading R12: sampled exp(-i^2 / 2 sigma^2), |i| <= R, separable, weights
+# renormalised over the in-volume taps of each axis.
+# ---------------------------------------------------------------------------
+
+def gaussian_taps(sigma, radius=0):
+    """Unnormalised taps w_i = exp(-i^2 / (2 sigma^2)), i = -R..R (R = ceil(3 sigma))."""
+    if radius <= 0:
+        radius = int(math.ceil(3.0 * sigma))
+    i = np.arange(-radius, radius + 1, dtype=np.float64)
+    return np.exp(-(i * i) / (2.0 * sigma * sigma))
+
+
+def gaussian_smooth(v, sigma, radius=0):
+    """Separable Gaussian of a scalar volume, renormalised over in-volume taps."""
+    w = gaussian_taps(sigma, radius)
+    R = (len(w) - 1) // 2
+    out = np.asarray(v, np.float64)
+    for ax in (2, 1, 0):            # x, then y, then z
+        n = out.shape[ax]
+        num = np.zeros(out.shape)
+        den = np.zeros(n)
+        for k in range(-R, R + 1):
+            lo, hi = max(0, -k), min(n, n - k)
+            if lo >= hi:
+                continue
+            dst = [slice(None)] * 3
+            src = [slice(None)] * 3
+            dst[ax] = slice(lo, hi)
+            src[ax] = slice(lo + k, hi + k)
+            num[tuple(dst)] += w[k + R] * out[tuple(src)]
+            den[lo:hi] += w[k + R]
+        shape = [1, 1, 1]
+        shape[ax] = n
+        out = num / den.reshape(shape)
+    return out
+
+
+def gaussian_smooth_field(r, sigma, radius=0):
+    """Apply the Gaussian to each of the three field components independently."""
+    return np.stack([gaussian_smooth(r[c], sigma, radius) for c in range(3)])
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2.3 stopping criterion.  Reading R5: |.| is the per-voxel Euclidean
+# norm; l = +inf while sum |r| = 0; stop once k >= window and
+# l^(k-window) - l^(k) <= eps.
+# ---------------------------------------------------------------------------
+
+def relative_norm(dr, r):
+    """l^(k) = sum |dr^(k+1)| / sum |r^(k)|."""
+    num = np.sqrt((np.asarray(dr, np.float64) ** 2).sum(axis=0)).sum()
+    den = np.sqrt((np.asarray(r, np.float64) ** 2).sum(axis=0)).sum()
+    return math.inf if den == 0.0 else num / den
+
+
+def should_stop(history, eps, window=10):
+    k = len(history) - 1
+    if eps <= 0 or k < window:
+        return False
+    a, b = history[k - window], history[k]
+    if math.isinf(a) or math.isinf(b):
+        return False
+    return a - b <= eps
+
+
+# ---------------------------------------------------------------------------
+# Algorithm A1: one iteration at one level, and the whole driver
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Params:
+    patch: tuple = (3, 3, 3)       # odd sizes (px, py, pz); Sec. 3.3 uses 3x3x3
+    sigma: float = 1.0             # Gaussian sigma in voxels (not given by the paper)
+    radius: int = 0                # 0 -> ceil(3 sigma)
+    levels: int = 2                # Sec. 2.3 uses two levels
+    iters: List[int] = field(default_factory=lambda: [50, 50])  # coarsest first
+    stop_eps: float = 0.0          # 1e-4 in Sec. 2.3; 0 = fixed iteration counts
+    stop_window: int = 10
+    force_mode: int = FORCE_THIRION
+    global_shift: bool = True
+    var_floor: float = 1e-6
+    den_floor: float = 1e-9
+
+    @property
+    def half(self):
+        return tuple((p - 1) // 2 for p in self.patch)
+
+
+def iteration(I_m, I_s, r, p: Params):
+    """One pass of Algorithm A1 steps 1-6 at one level.
+
+    Returns (r_new, dr, l, extras) where extras holds m = I_m^(k) and f = I'_s.
+    Step 2 (interpolation of a, b where xi = 1, Eqs. 7-10) is not part of this
+    path: the mask is taken as all-zero.
+    """
+    m = warp(I_m, r)                                   # update the moving image
+    f = correct(m, I_s, p.half, p.var_floor)           # steps 1 and 3
+    dr = force(m, f, p.force_mode, p.den_floor)        # step 4
+    u = r + dr                                         # step 5
+    r_new = gaussian_smooth_field(u, p.sigma, p.radius)  # step 6
+    l = relative_norm(dr, r)
+    return r_new, dr, l, {"m": m, "f": f}
+
+
+def build_pyramid(img, levels):
+    pyr = [np.asarray(img, np.float64)]
+    for _ in range(1, levels):
+        pyr.append(downsample2(pyr[-1]))
+    return pyr
+
+
+def register(I_m, I_s, p: Params, return_history=False):
+    """Algorithm A1: global shift, pyramid, coarse-to-fine demons with correction.
+
+    Returns the finest-level field r ([3][nz][ny][nx], voxel units) and, with
+    ``return_history``, the per-level list of l^(k) values and the corrected
+    static image at the last iteration.
+    """
+    I_m = np.asarray(I_m, np.float64)
+    I_s = np.asarray(I_s, np.float64)
+    if p.global_shift:
+        I_s, _ = global_shift(I_m, I_s)
+    pm = build_pyramid(I_m, p.levels)
+    ps = build_pyramid(I_s, p.levels)
+    r = np.zeros((3,) + pm[-1].shape)
+    history = []
+    f = None
+    for lev in range(p.levels - 1, -1, -1):
+        n_it = p.iters[p.levels - 1 - lev]
+        hist = []
+        for _k in range(n_it):
+            r, _dr, l, ex = iteration(pm[lev], ps[lev], r, p)
+            f = ex["f"]
+            hist.append(l)
+            if should_stop(hist, p.stop_eps, p.stop_window):
+                break
+        history.append(hist)
+        if lev > 0:
+            r = upsample_field2(r, pm[lev - 1].shape)
+    if return_history:
+        return r, history, f
+    return r
+
+
+# ---------------------------------------------------------------------------
+# Differentiable form (not in the paper): SSD between the warped CT and the
+# corrected CBCT, and its adjoint with respect to the field.
+# Reading R15: L = sum_x (m(x) - I'_s(x))^2 with m = I_m(x + r(x)) and I'_s
+# from Eqs. (5)-(6); the CBCT patch statistics do not depend on r.
+# ---------------------------------------------------------------------------
+
+def ssd_loss(I_m, I_s, r, half, var_floor=1e-6):
+    m = warp(I_m, r)
+    f = correct(m, I_s, half, var_floor)
+    return float(((m - f) ** 2).sum())
+
+
+def warp_coord_gradient(I_m, r):
+    """d I_m(p) / d p at p = x + r(x) for trilinear interpolation, [3][...].
+
+    Zero along an axis where the sample position is clamped to the volume.
+    """
+    I_m = np.asarray(I_m, np.float64)
+    r = np.asarray(r, np.float64)
+    nz, ny, nx = I_m.shape
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    raw = [x + r[0], y + r[1], z + r[2]]
+    n = [nx, ny, nz]
+    lo, t, hi, inside = [], [], [], []
+    for a in range(3):
+        pa = np.clip(raw[a], 0.0, n[a] - 1)
+        i0 = np.floor(pa).astype(np.int64)
+        lo.append(i0)
+        t.append(pa - i0)
+        hi.append(np.minimum(i0 + 1, n[a] - 1))
+        inside.append((raw[a] > 0.0) & (raw[a] < n[a] - 1))
+    g = np.zeros((3,) + I_m.shape)
+    for a in range(3):
+        acc = np.zeros(I_m.shape)
+        for cz in (0, 1):
+            for cy in (0, 1):
+                for cx in (0, 1):
+                    c = (cx, cy, cz)
+                    w = np.ones(I_m.shape)
+                    for b in range(3):
+                        if b == a:
+                            w = w * (1.0 if c[b] else -1.0)
+                        else:
+                            w = w * (t[b] if c[b] else 1.0 - t[b])
+                    idx = [hi[b] if c[b] else lo[b] for b in range(3)]
+                    acc += w * I_m[idx[2], idx[1], idx[0]]
+        g[a] = np.where(inside[a], acc, 0.0)
+    return g
+
+
+def ssd_grad(I_m, I_s, r, half, var_floor=1e-6):
+    """dL/dr by the adjoint of warp -> patch moments -> correction -> SSD.
+
+    f(x) = z_s(x) sigma_m(x) + mu_m(x) with z_s = (I_s - E(S)) / STD(S)
+    (algebraically a I_s + b of Eqs. 5-6).  Back-propagation:
+      g_f = -2 (m - f);  g_mu = g_f;  g_sigma = g_f z_s
+      g_m(y) = 2 (m - f)(y) + sum_{x: y in box(x)} [g_mu(x)/n(x)
+               + g_sigma(x) (m(y) - mu(x)) / (n(x) sigma(x))]
+      dL/dr(y) = g_m(y) * dI_m/dp at p = y + r(y).
+    The sigma term is 0 where Var(M) <= var_floor (sigma_m is held at 0 there).
+    """
+    m = warp(I_m, r)
+    I_s = np.asarray(I_s, np.float64)
+    EM, EM2 = patch_moments(m, half)
+    ES, ES2 = patch_moments(I_s, half)
+    n = box_count(m.shape, half)
+    var_m = np.maximum(EM2 - EM * EM, 0.0)
+    var_s = np.maximum(ES2 - ES * ES, 0.0)
+    ok_m = var_m > var_floor
+    ok_s = var_s > var_floor
+    sig_m = np.where(ok_m, np.sqrt(np.where(ok_m, var_m, 1.0)), 0.0)
+    z_s = np.where(ok_s, (I_s - ES) / np.sqrt(np.where(ok_s, var_s, 1.0)), 0.0)
+    f = z_s * sig_m + EM
+    g_f = -2.0 * (m - f)
+    g_mu = g_f
+    g_sig = g_f * z_s
+    A = g_mu / n
+    B = np.where(ok_m, g_sig / (n * np.where(ok_m, sig_m, 1.0)), 0.0)
+    C = B * EM
+    g_m = 2.0 * (m - f) + box_sum(A, half) + m * box_sum(B, half) - box_sum(C, half)
+    return g_m[None] * warp_coord_gradient(I_m, r)
