@@ -1,0 +1,401 @@
+#!/usr/bin/env python
+"""DISC hot-path benchmark: voxel-iterations per second on one B300.
+
+A step is one full DISC registration schedule (Algorithm A1) of a synthetic
+CT/CBCT pair already resident in HBM: the field is reset at the coarsest level
+and every iteration of every level runs (warp, patch moments, correction,
+force, update, Gaussian, convergence norm; field up-sampling between levels).
+The metric is the total number of voxel-iterations of the schedule divided by
+the step time (CUDA events on the library's stream, after warm-up).
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # the head-and-neck-sized pair: 256x256x128, patch 11^3, sigma 1.5, 3 levels x 100 iterations
+    "headneck-256x256x128": dict(dims=(256, 256, 128), patch=(11, 11, 11), sigma=1.5, levels=3,
+                                 iters=(100, 100, 100), gen="head_neck"),
+    # the small ellipsoid pair: 64x64x32, patch 7^3, sigma 1, 1 level x 50 iterations
+    "ellipsoid-64x64x32": dict(dims=(64, 64, 32), patch=(7, 7, 7), sigma=1.0, levels=1, iters=(50,),
+                               gen="ellipsoid"),
+    # the large pair: 512x512x256, patch 15^3, sigma 2, 4 levels x 200 iterations
+    "large-512x512x256": dict(dims=(512, 512, 256), patch=(15, 15, 15), sigma=2.0, levels=4,
+                              iters=(200, 200, 200, 200), gen="head_neck"),
+}
+DEFAULT_WORKLOAD = "headneck-256x256x128"
+METRIC = "Gvoxel-iterations/s and % of HBM roofline, plain vs batched/adjoint form, 1 B300"
+UNIT = "Gvoxel-it/s"
+PASS_A_BYTES_PER_VOXEL = 32   # read r (12) + I_m (4) + zs (4), write u (12)
+PASS_B_BYTES_PER_VOXEL = 24   # read u (12), write r (12)
+
+
+def level_dims(dims, levels):
+    out = [tuple(dims)]
+    for _ in range(1, levels):
+        out.append(tuple((d + 1) // 2 for d in out[-1]))
+    return out
+
+
+def schedule_units(w):
+    """Voxel-iterations of one full schedule (coarsest level first in iters)."""
+    dims = level_dims(w["dims"], w["levels"])
+    tot = 0
+    for lev in range(w["levels"]):
+        nx, ny, nz = dims[lev]
+        tot += nx * ny * nz * w["iters"][w["levels"] - 1 - lev]
+    return tot
+
+
+def make_pair(w):
+    from paper_1204_6295_b300 import phantom
+    nx, ny, nz = w["dims"]
+    if w["gen"] == "ellipsoid":
+        return phantom.ellipsoid_pair(nx, ny, nz)
+    return phantom.head_neck_pair(nx, ny, nz)
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def source_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1204_6295_b300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode())
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload):
+    """DRAM bytes per launch of the pass-A kernel from a committed ncu summary, if current."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d[workload]
+        if e.get("source_digest") != source_digest():
+            return None
+        return float(e["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(w, pair, budget_s=15.0):
+    """The FP64 oracle timed on this host: iterations on a z-slab of the finest level."""
+    import numpy as np
+    from oracle import disc_oracle as O
+    nx, ny, nz = w["dims"]
+    planes = max(1, min(nz, (2 << 20) // (nx * ny)))
+    P = O.Params(patch=w["patch"], sigma=w["sigma"], levels=1, iters=[1])
+    Is, _ = O.global_shift(pair.ct, pair.cbct)
+    ct = pair.ct[:planes].astype(np.float64)
+    Is = Is[:planes]
+    r = np.zeros((3,) + ct.shape)
+    n_vox = ct.size
+    t0 = time.perf_counter()
+    its = 0
+    while True:
+        r, _, _, _ = O.iteration(ct, Is, r, P)
+        its += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or its >= 50:
+            break
+    return {"value": its * n_vox / el / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{its} oracle iterations on the first {planes} z-planes ({nx}x{ny}x{planes}) "
+                      f"of the finest level, numpy float64, single thread, {el:.1f} s"}
+
+
+def run_reference(args, w, rank, world):
+    if rank != 0:
+        return 0
+    import numpy as np
+    from oracle import disc_oracle as O
+    pair = make_pair(w)
+    nx, ny, nz = w["dims"]
+    planes = max(1, min(nz, (1 << 20) // (nx * ny)))
+    P = O.Params(patch=w["patch"], sigma=w["sigma"], levels=1, iters=[1])
+    Is, _ = O.global_shift(pair.ct, pair.cbct)
+    ct = pair.ct[:planes].astype(np.float64)
+    Is = Is[:planes]
+    r = np.zeros((3,) + ct.shape)
+    for _ in range(args.warmup):
+        r, _, _, _ = O.iteration(ct, Is, r, P)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r, _, _, _ = O.iteration(ct, Is, r, P)
+    el = time.perf_counter() - t0
+    value = args.steps * ct.size / el / 1e9
+    sample = (f"each step = one oracle iteration (warp, moments, correction, force, Gaussian) on the first "
+              f"{planes} z-planes ({nx}x{ny}x{planes}) of the finest level, numpy float64, single thread")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": args.workload, "dims": list(w["dims"]), "patch": list(w["patch"]),
+                       "sigma": w["sigma"], "levels": w["levels"], "iters": list(w["iters"]),
+                       "sample_planes": planes},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def time_kernels(disc, torch, w, pair_dev, field_dev, reps=20):
+    """CUDA-event timing of the two per-iteration kernels at the finest level.
+
+    Same launch configuration as inside the schedule (the plan depends only on
+    sizes and patch), launched on the current torch stream.
+    """
+    nx, ny, nz = w["dims"]
+    N = nx * ny * nz
+    ct, cbct = pair_dev
+    patch = w["patch"]
+    qs_s = disc.qscale(float(cbct.abs().max()), patch)
+    qs_m = disc.qscale(float(ct.abs().max()), patch)
+    zs = torch.empty_like(ct)
+    disc.k_static_norm(cbct, zs, patch, qs_s)
+    u = torch.empty_like(field_dev)
+    r2 = torch.empty_like(field_dev)
+    s = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for _ in range(3):
+        disc.k_pass_a(ct, zs, field_dev, u, patch, qs_m)
+        disc.k_gauss(u, r2, w["sigma"])
+    torch.cuda.synchronize()
+    ev[0].record(s)
+    for _ in range(reps):
+        disc.k_pass_a(ct, zs, field_dev, u, patch, qs_m)
+    ev[1].record(s)
+    ev[2].record(s)
+    for _ in range(reps):
+        disc.k_gauss(u, r2, w["sigma"])
+    ev[3].record(s)
+    torch.cuda.synchronize()
+    ta = ev[0].elapsed_time(ev[1]) / reps / 1e3
+    tb = ev[2].elapsed_time(ev[3]) / reps / 1e3
+    return {"pass_a_s": ta, "pass_b_s": tb, "N": N}
+
+
+def run_ours(args, w, rank, world, local_rank):
+    import numpy as np
+    import torch
+    from paper_1204_6295_b300 import disc
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    pair = make_pair(w)
+    nx, ny, nz = w["dims"]
+    dims = level_dims(w["dims"], w["levels"])
+    cnx, cny, cnz = dims[-1]
+    ct = torch.from_numpy(pair.ct).cuda()
+    cbct = torch.from_numpy(pair.cbct).cuda()
+    zeros_coarse = torch.zeros((3, cnz, cny, cnx), dtype=torch.float32, device="cuda")
+    reg = disc.Registration(patch=w["patch"], sigma=w["sigma"], levels=w["levels"], iters=w["iters"])
+    reg.set_images(ct, cbct)
+    units = schedule_units(w)
+    L = w["levels"]
+
+    def step():
+        reg.set_field(L - 1, zeros_coarse)
+        reg.iterate(-1, sync=False)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * units / (ms / 1e3) / 1e9
+
+    # kernel timing for the roofline at the finest level, on the final field
+    field = torch.empty((3, nz, ny, nx), dtype=torch.float32, device="cuda")
+    reg.get_field(field)
+    kt = time_kernels(disc, torch, w, (ct, cbct), field)
+    peak, peak_kind = load_peaks()
+    a_gbs = PASS_A_BYTES_PER_VOXEL * kt["N"] / kt["pass_a_s"] / 1e9
+    b_gbs = PASS_B_BYTES_PER_VOXEL * kt["N"] / kt["pass_b_s"] / 1e9
+    traffic = recorded_traffic(args.workload)
+
+    # end to end through the public API with host buffers (pinned)
+    ct_h = torch.from_numpy(pair.ct).pin_memory()
+    cbct_h = torch.from_numpy(pair.cbct).pin_memory()
+    out_h = torch.empty((3, nz, ny, nx), dtype=torch.float32).pin_memory()
+    ct_np, cbct_np, out_np = ct_h.numpy(), cbct_h.numpy(), out_h.numpy()
+    e2e_steps = max(1, min(args.steps, 3))
+    reg.set_images(ct_np, cbct_np)
+    reg.iterate(-1, sync=False)
+    reg.get_field(out_np)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        reg.set_images(ct_np, cbct_np)
+        reg.iterate(-1, sync=False)
+        reg.get_field(out_np)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * units / e2e_s / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": int(2 * nx * ny * nz * 4), "d2h_bytes_per_step": int(3 * nx * ny * nz * 4),
+           "ms_per_step": e2e_s * 1e3,
+           "what": "disc_set_images(host CT, CBCT) + disc_iterate(full schedule) + disc_get_field(host)"}
+    reg.close()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    launches = sum(w["iters"]) * 3 + (L - 1)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "dims": list(w["dims"]), "patch": list(w["patch"]),
+                   "sigma": w["sigma"], "levels": w["levels"], "iters_coarse_to_fine": list(w["iters"]),
+                   "voxel_iterations_per_step": units, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2: finest-level working set "
+                         f"{(9 * nx * ny * nz * 4) / 1e6:.0f} MB > 126 MB"},
+        "roofline": {"bound": "hbm", "kernel": "k_box_pass<kModeIterate> (warp+moments+correction+force)",
+                     "achieved": a_gbs, "peak": peak, "unit": "GB/s", "frac": a_gbs / peak,
+                     "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                     "traffic": traffic, "algorithmic_bytes_per_voxel": PASS_A_BYTES_PER_VOXEL,
+                     "launch_ms": kt["pass_a_s"] * 1e3},
+        "kernels": {"pass_b_gauss": {"achieved_gbs": b_gbs, "frac": b_gbs / peak,
+                                      "launch_ms": kt["pass_b_s"] * 1e3,
+                                      "algorithmic_bytes_per_voxel": PASS_B_BYTES_PER_VOXEL}},
+        "e2e": e2e,
+        "gpu_launches": launches * args.steps,
+        "clocks": clk.summary(),
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, pair)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus > 0 else 1)))
+    if "WORLD_SIZE" not in os.environ:
+        world = 1
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w, rank, world)
+    return run_ours(args, w, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,215 @@
+/*
+ * disc.h -- C ABI of the B300 (sm_103a) DISC library, libdisc.so.
+ *
+ * DISC ("Deformation with Intensity Simultaneously Corrected", Zhen et al.,
+ * arXiv 1204.6295) registers a planning CT (the moving image I_m) to a CBCT
+ * (the static image I_s) with demons, correcting the CBCT intensity at every
+ * iteration by matching the first two moments of a patch around each voxel
+ * to the same patch of the deformed CT.
+ *
+ * Problem statement (Sec. 2.1, Sec. 2.2): given I_m and I_s on one grid,
+ * find a displacement field r with I_m(x + r(x)) = I_s(x), together with the
+ * corrected CBCT I'_s = a I_s + b (Eqs. 2-6).  Algorithm A1 gives the
+ * procedure this library runs: a global intensity shift, a multi-resolution
+ * pyramid, then per level and per iteration: warp, moment matching,
+ * correction, demons force (Eq. 1), field update and Gaussian regularisation.
+ *
+ * Conventions shared by every call
+ *  - Layout: images are float32 [nz][ny][nx] (x fastest, C order).  Fields
+ *    are float32 structure-of-arrays [3][nz][ny][nx], components (x, y, z),
+ *    in voxel units of the grid they are defined on.
+ *  - Memory kinds: DISC_MEM_HOST pointers are ordinary host memory (pinned
+ *    or pageable); DISC_MEM_DEVICE pointers are device memory on the
+ *    context's device.  The library never keeps a caller pointer after a
+ *    call returns, and the caller owns every buffer it passes.
+ *  - Streams: all device work is enqueued on the stream given at creation
+ *    (NULL makes the library create its own non-blocking stream).  Calls that
+ *    write host memory synchronise that stream before returning.
+ *  - Errors: every call returns a disc_status by value; no C++ exception
+ *    crosses this boundary.  The first CUDA error seen by a context is
+ *    sticky: later calls on it return DISC_ERR_STATE until disc_destroy.
+ *  - Threads: a context is not thread-safe; distinct contexts are independent.
+ *  - Kernel-level calls (disc_k_*) take device pointers only, enqueue on the
+ *    given stream and return without synchronising.
+ */
+#ifndef DISC_H
+#define DISC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct disc_ctx disc_ctx;       /* opaque, owned by the library */
+
+typedef enum {
+  DISC_OK = 0,
+  DISC_ERR_ARG = 1,      /* NULL pointer, bad enum or parameter value      */
+  DISC_ERR_SHAPE = 2,    /* sizes inconsistent or outside supported range  */
+  DISC_ERR_STATE = 3,    /* call out of order, or context already failed   */
+  DISC_ERR_OOM = 4,      /* device allocation failed                        */
+  DISC_ERR_CUDA = 5,     /* a CUDA runtime call failed                      */
+  DISC_ERR_TIMEOUT = 6   /* a bounded device-side wait gave up              */
+} disc_status;
+
+enum { DISC_MEM_HOST = 0, DISC_MEM_DEVICE = 1 };
+
+/* Demons force, Eq. (1).  THIRION is the first (passive) term alone; DOUBLE
+ * is the double-force form Eq. (1) prints.  The image difference is taken
+ * as (I'_s - I_m^(k)) so that adding dr moves I_m(x + r) toward I_s under
+ * the Sec. 2.1 convention I_m(x + v(x)) = I_s(x). */
+enum { DISC_FORCE_THIRION = 0, DISC_FORCE_DOUBLE = 1 };
+
+#define DISC_MAX_LEVELS 8
+#define DISC_MAX_HALF_PATCH 15   /* patch sizes up to 31 voxels per axis   */
+#define DISC_MAX_GAUSS_RADIUS 16
+
+typedef struct {
+  int32_t patch[3];      /* odd patch sizes (px, py, pz); Sec. 3.3 uses 3x3x3 */
+  float gauss_sigma;     /* Gaussian sigma of the field regularisation, voxels */
+  int32_t gauss_radius;  /* taps |i| <= radius; 0 = ceil(3 sigma)              */
+  int32_t levels;        /* pyramid levels, >= 1 (Sec. 2.3 uses 2)             */
+  int32_t iters[DISC_MAX_LEVELS];  /* iterations per level, coarsest first     */
+  float stop_eps;        /* Sec. 2.3 stop rule threshold (1e-4); <= 0 = fixed counts */
+  int32_t stop_window;   /* Sec. 2.3 compares l^(k-10) with l^(k): 10          */
+  int32_t force_mode;    /* DISC_FORCE_THIRION or DISC_FORCE_DOUBLE            */
+  int32_t global_shift;  /* 1 = shift I_s by mean(I_m) - mean(I_s) (Sec. 2.3)  */
+  float var_floor;       /* patch variance (HU^2) at or below which STD = 0    */
+} disc_params;
+
+/* Fill *p with defaults: patch 3x3x3, sigma 1, radius 0, 2 levels of 50
+ * iterations, stop_eps 0 (fixed counts), window 10, THIRION, global shift on,
+ * var_floor 1e-6.  Returns DISC_ERR_ARG for NULL. */
+disc_status disc_params_default(disc_params* p);
+
+/* Human-readable name of a status code (static storage, never NULL). */
+const char* disc_status_str(disc_status s);
+
+/* Create a context on CUDA device `device`, enqueueing on `cuda_stream`
+ * (a cudaStream_t, or NULL for a library-owned stream).  Validates *p:
+ * odd patch sizes in [1, 31], sigma > 0, levels in [1, 8], iters >= 0.
+ * On success *out owns device resources until disc_destroy. */
+disc_status disc_create(const disc_params* p, int device, void* cuda_stream,
+                        disc_ctx** out);
+
+/* Load the CT (moving, I_m) and CBCT (static, I_s) images, both
+ * [nz][ny][nx] float32, from host or device memory (mem_kind).  Applies the
+ * global shift (Sec. 2.3, Algorithm A1 first line), builds the pyramid by
+ * 2x2x2 averaging (ceil(n/2) voxels per axis per level), precomputes each
+ * level's CBCT patch statistics, and sets r = 0 at the coarsest level
+ * (Algorithm A1).  Sizes: every axis >= 1.  Replaces any previous images. */
+disc_status disc_set_images(disc_ctx* ctx, const float* ct_moving,
+                            const float* cbct_static, int32_t nx, int32_t ny,
+                            int32_t nz, int mem_kind);
+
+/* Advance the schedule of Algorithm A1 by at most `max_iters` iterations
+ * (-1 = run to the end of the schedule), coarsest level first, up-sampling
+ * r to the next level at each level's end.  One iteration = warp, patch
+ * moments of I_m^(k) and I_s, correction I'_s = a I_s + b (Eqs. 5-6),
+ * Thirion or double force (Eq. 1), r += dr, r <- G_sigma * r.  With
+ * stop_eps > 0 a level ends early once l^(k-window) - l^(k) <= stop_eps,
+ * l^(k) = sum|dr^(k+1)| / sum|r^(k)| (Sec. 2.3).
+ * If iters_done or last_l is non-NULL the call synchronises the stream and
+ * returns the iterations executed by this call and the last l^(k) (+inf
+ * while sum|r| = 0); otherwise it returns without synchronising. */
+disc_status disc_iterate(disc_ctx* ctx, int32_t max_iters, int32_t* iters_done,
+                         float* last_l);
+
+/* Copy the displacement field on the finest grid, [3][nz][ny][nx] float32,
+ * in finest-grid voxel units, to `out` (host or device).  Before the
+ * schedule reaches the finest level, the current field is up-sampled
+ * through the remaining levels first. */
+disc_status disc_get_field(disc_ctx* ctx, float* out, int mem_kind);
+
+/* Copy the corrected CBCT I'_s (Sec. 2.2, last paragraph), computed from
+ * the current field at the current level, [nz][ny][nx] of that level. */
+disc_status disc_get_corrected(disc_ctx* ctx, float* out, int mem_kind);
+
+/* Replace the field of pyramid level `level` (0 = finest) with `r`
+ * ([3][nz][ny][nx] of that level) and make it the current level with its
+ * iteration count reset: resuming from a saved field. */
+disc_status disc_set_field(disc_ctx* ctx, int32_t level, const float* r,
+                           int mem_kind);
+
+/* Position in the schedule: current level (0 = finest) and iterations
+ * already run at it.  *dims receives that level's (nx, ny, nz) if non-NULL. */
+disc_status disc_get_progress(disc_ctx* ctx, int32_t* level, int32_t* iter,
+                              int32_t dims[3]);
+
+/* Copy the l^(k) history of `level` (up to `cap` values, one per iteration
+ * run there) into host memory; *count receives the number written. */
+disc_status disc_get_norm_history(disc_ctx* ctx, int32_t level, float* out,
+                                  int32_t cap, int32_t* count);
+
+/* Release every resource of the context.  NULL is accepted. */
+disc_status disc_destroy(disc_ctx* ctx);
+
+/* ---------------------------------------------------------------------
+ * Kernel-level calls: one hot-path step on caller-owned device buffers.
+ * All pointers are device pointers on the current device; work goes on
+ * `stream` (cudaStream_t, NULL = legacy default stream).  `patch` is the
+ * odd patch size per axis; `qscale` is the fixed-point scale (a power of
+ * two, see disc_qscale).  Buffers may not overlap unless stated.
+ * ------------------------------------------------------------------- */
+
+/* Fixed-point scale 2^e used for exact integer patch sums of an image
+ * whose largest magnitude is `max_abs`, for patches of `patch` voxels:
+ * the largest e with |q| = |v| 2^e small enough that every patch sum of q^2
+ * fits in 63 bits.  Returns 0 for invalid arguments. */
+float disc_qscale(float max_abs, const int32_t patch[3]);
+
+/* Largest |v| over n floats, written to *out (device float). */
+disc_status disc_k_max_abs(const float* v, int64_t n, float* out, void* stream);
+
+/* Global intensity shift (Sec. 2.3): Is_out = Is + (mean(Im) - mean(Is)),
+ * means over n voxels; *delta_out (device float, may be NULL) gets the
+ * shift.  Is_out may equal Is. */
+disc_status disc_k_global_shift(const float* Im, const float* Is, float* Is_out,
+                                int64_t n, float* delta_out, void* stream);
+
+/* 2x2x2 mean down-sampling (pyramid build, Sec. 2.3): in [nz][ny][nx] ->
+ * out [ceil(nz/2)][ceil(ny/2)][ceil(nx/2)]; a partial cell averages the
+ * voxels it has. */
+disc_status disc_k_downsample2(const float* in, float* out, int32_t nx, int32_t ny,
+                               int32_t nz, void* stream);
+
+/* Field up-sampling to the next finer level (Algorithm A1): fine voxel i
+ * samples the coarse field at (i - 0.5)/2 per axis (clamped), trilinear,
+ * times 2.  rc [3][cz][cy][cx] -> rf [3][nz][ny][nx], where cz = ceil(nz/2)
+ * and likewise for y and x. */
+disc_status disc_k_upsample_field2(const float* rc, float* rf, int32_t nx,
+                                   int32_t ny, int32_t nz, void* stream);
+
+/* CBCT patch normalisation for Eqs. (5)-(6): zs = (I_s - E(S)) / STD(S)
+ * over the truncated patch around each voxel (0 where Var(S) <= var_floor).
+ * Then I'_s = zs * STD(M) + E(M) equals a I_s + b. */
+disc_status disc_k_static_norm(const float* Is, float* zs, int32_t nx, int32_t ny,
+                               int32_t nz, const int32_t patch[3], float qscale,
+                               float var_floor, void* stream);
+
+/* One fused iteration front (Algorithm A1 steps 1, 3, 4, 5):
+ * m = I_m(x + r(x)) (trilinear, clamped); E(M), STD(M) over the patch;
+ * f = zs STD(M) + E(M); dr from Eq. (1) with f as I_s; u = r + dr.
+ * Optional taps m_out, f_out (NULL to skip) receive m and f.
+ * norms_out (device double[2], may be NULL) receives sum|dr| and sum|r|.
+ * u must not alias r. */
+disc_status disc_k_pass_a(const float* Im, const float* zs, const float* r, float* u,
+                          float* m_out, float* f_out, double* norms_out,
+                          int32_t nx, int32_t ny, int32_t nz, const int32_t patch[3],
+                          float qscale, float var_floor, int32_t force_mode,
+                          void* stream);
+
+/* Gaussian regularisation (Algorithm A1 step 6, Sec. 2.3 kernel 2): each
+ * component of u [3][nz][ny][nx] smoothed separably with taps
+ * exp(-i^2 / 2 sigma^2), |i| <= radius (0 = ceil(3 sigma)), weights
+ * renormalised over in-volume taps per axis; result in r.  r must not
+ * alias u. */
+disc_status disc_k_gauss(const float* u, float* r, int32_t nx, int32_t ny, int32_t nz,
+                         float sigma, int32_t radius, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DISC_H */

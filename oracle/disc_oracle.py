@@ -149,6 +149,34 @@ def warp(I_m, r):
     return out
 
 
+def warp_region(I_m, r_region, origin):
+    """I_m(x + r(x)) for the voxels x of a sub-box of the grid.
+
+    ``r_region`` is the field on the sub-box ([3][dz][dy][dx]) whose first
+    voxel is ``origin`` = (x0, y0, z0) of the full grid of ``I_m``; used to
+    evaluate the warp at sampled voxels of large volumes.  Same definition as
+    ``warp``: trilinear, sample position clamped to the full grid.
+    """
+    I_m = np.asarray(I_m, np.float64)
+    r = np.asarray(r_region, np.float64)
+    nz, ny, nx = I_m.shape
+    _, dz, dy, dx = r.shape
+    x0, y0, z0 = origin
+    z, y, x = np.meshgrid(np.arange(z0, z0 + dz), np.arange(y0, y0 + dy), np.arange(x0, x0 + dx),
+                          indexing="ij")
+    p = [np.clip(x + r[0], 0.0, nx - 1), np.clip(y + r[1], 0.0, ny - 1), np.clip(z + r[2], 0.0, nz - 1)]
+    lo = [np.floor(q).astype(np.int64) for q in p]
+    t = [q - i for q, i in zip(p, lo)]
+    hi = [np.minimum(i + 1, n - 1) for i, n in zip(lo, (nx, ny, nz))]
+    out = np.zeros(r.shape[1:])
+    for cz in (0, 1):
+        for cy in (0, 1):
+            for cx in (0, 1):
+                w = (t[0] if cx else 1 - t[0]) * (t[1] if cy else 1 - t[1]) * (t[2] if cz else 1 - t[2])
+                out += w * I_m[(hi if cz else lo)[2], (hi if cy else lo)[1], (hi if cx else lo)[0]]
+    return out
+
+
 # ---------------------------------------------------------------------------
 # Eq. (3): raw moments of a patch; reading R7: truncated box at the borders
 # ---------------------------------------------------------------------------

@@ -1,0 +1,117 @@
+// Internal declarations shared by the translation units of libdisc.so.
+// Nothing here is part of the public ABI (include/disc.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "disc.h"
+
+namespace disc {
+
+constexpr int kThreads = 256;          // threads per CTA of every z-marching kernel
+constexpr int kNumSMs = 148;           // B300: 2 dies x 74 SMs (queried at run time too)
+
+// ----------------------------------------------------------------------------
+// Index helpers
+// ----------------------------------------------------------------------------
+__host__ __device__ __forceinline__ size_t vix(int x, int y, int z, int nx, int ny) {
+  return ((size_t)z * (size_t)ny + (size_t)y) * (size_t)nx + (size_t)x;
+}
+
+// Number of in-volume positions of the window [c-h, c+h] on an axis of n voxels
+// (the truncated patch of the moment statistics, Eq. 3).
+__host__ __device__ __forceinline__ int box_count(int c, int n, int h) {
+  int lo = c - h < 0 ? 0 : c - h;
+  int hi = c + h > n - 1 ? n - 1 : c + h;
+  return hi - lo + 1;
+}
+
+// ----------------------------------------------------------------------------
+// Box-pass (warp + moment statistics) kernels, box_pass.cu
+// ----------------------------------------------------------------------------
+enum BoxMode : int {
+  kModeStatic = 0,     // zs = (I_s - E(S)) / STD(S)
+  kModeIterate = 1,    // warp, moments, correction, force, u = r + dr, norms
+  kModeCorrected = 2,  // warp, moments, f = I'_s written out
+  kModeSsdLoss = 3,    // warp, moments, per-CTA partial sum of (m - f)^2
+  kModeSsdAdjoint = 4  // warp, moments, per-voxel adjoint coefficients (A, B, C, D)
+};
+
+struct BoxArgs {
+  const float* src;     // kModeStatic: I_s; otherwise I_m (gathered by the warp)
+  const float* zs;      // CBCT normalised patch value (all modes but kModeStatic)
+  const float* r;       // field [3][N]
+  float* out;           // kModeStatic: zs; kModeIterate: u [3][N]; kModeCorrected: f;
+                        // kModeSsdAdjoint: [4][N] (A, B, C, D)
+  float* m_tap;         // optional (kModeIterate): m = I_m(x + r)
+  float* f_tap;         // optional (kModeIterate): f = I'_s
+  float* partials;      // per-CTA float[2] (kModeIterate: sum|dr|, sum|r|; kModeSsdLoss: loss)
+  const int* stop;      // device flag: when non-zero the kernel returns at once
+  int nx, ny, nz;
+  int hx, hy, hz;       // patch half sizes
+  float qscale, inv_qscale, var_floor;
+  int force_mode;
+  int zlen;             // output planes per CTA (z chunk)
+};
+
+struct BoxPlan {
+  dim3 grid;
+  size_t smem;
+  int zlen;
+  int tx, ty;
+};
+
+// Plan a launch (grid, z chunk, dynamic shared memory) for a volume and patch.
+BoxPlan box_plan(int mode, int nx, int ny, int nz, int hx, int hy, int hz, int num_sms);
+cudaError_t box_launch(int mode, const BoxArgs& a, const BoxPlan& plan, cudaStream_t s);
+
+// ----------------------------------------------------------------------------
+// Gaussian pass, gauss.cu
+// ----------------------------------------------------------------------------
+struct GaussArgs {
+  const float* u;       // [3][N]
+  float* r;             // [3][N]
+  const int* stop;
+  int nx, ny, nz;
+  int R;
+  int zlen;
+  float w[2 * DISC_MAX_GAUSS_RADIUS + 1];   // normalised taps (sum 1)
+};
+struct GaussPlan {
+  dim3 grid;
+  size_t smem;
+  int zlen;
+};
+int gauss_radius(float sigma, int radius);
+void gauss_taps(float sigma, int R, float* w);
+GaussPlan gauss_plan(int nx, int ny, int nz, int R, int num_sms);
+cudaError_t gauss_launch(const GaussArgs& a, const GaussPlan& plan, cudaStream_t s);
+
+// ----------------------------------------------------------------------------
+// Small kernels, misc.cu
+// ----------------------------------------------------------------------------
+cudaError_t launch_max_abs(const float* v, int64_t n, float* out, cudaStream_t s);
+// Sums of two arrays into per-CTA double partials, then the shift Is_out = Is + delta.
+cudaError_t launch_global_shift(const float* Im, const float* Is, float* Is_out, int64_t n,
+                                double* scratch /* >= 2*kShiftBlocks+1 doubles */,
+                                float* delta_out, cudaStream_t s);
+constexpr int kShiftBlocks = 592;
+cudaError_t launch_down2(const float* in, float* out, int nx, int ny, int nz, cudaStream_t s);
+cudaError_t launch_up2(const float* rc, float* rf, int nx, int ny, int nz, cudaStream_t s);
+// Reduce per-CTA partial norms to l^(k), append to the level history, update the stop flag.
+struct NormState {
+  float* hist;          // [cap] l values of the current level
+  int* iter;            // iterations run at the current level
+  int* stop;            // stop flag
+  int cap;
+  int window;
+  float eps;
+};
+cudaError_t launch_norm_finalize(const float* partials, int nparts, NormState st, cudaStream_t s);
+// Deterministic fixed-order sum of per-CTA float partials (stride 2, component c) into *out.
+cudaError_t launch_partials_sum(const float* partials, int nparts, int comp, double* out,
+                                cudaStream_t s);
+
+}  // namespace disc

@@ -1,0 +1,300 @@
+"""Python binding of libdisc.so (the C ABI in include/disc.h).
+
+Argument marshalling only: every step of the registration runs in the CUDA
+library.  Device buffers are torch CUDA tensors (float32, contiguous); host
+buffers are numpy arrays.  Importing this module loads the library and fails
+loudly if it has not been built (``python -m paper_1204_6295_b300.build``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdisc.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "disc.h")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libdisc.so not found at {LIB_PATH}; build it with "
+                      "`python -m paper_1204_6295_b300.build` (nvcc, sm_103a)")
+_lib = ctypes.CDLL(LIB_PATH)
+
+MEM_HOST, MEM_DEVICE = 0, 1
+FORCE_THIRION, FORCE_DOUBLE = 0, 1
+MAX_LEVELS = 8
+
+STATUS = {0: "DISC_OK", 1: "DISC_ERR_ARG", 2: "DISC_ERR_SHAPE", 3: "DISC_ERR_STATE",
+          4: "DISC_ERR_OOM", 5: "DISC_ERR_CUDA", 6: "DISC_ERR_TIMEOUT"}
+
+
+class DiscError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = _lib.disc_status_str(status).decode()
+        super().__init__(f"{where}: {msg}")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("patch", ctypes.c_int32 * 3),
+        ("gauss_sigma", ctypes.c_float),
+        ("gauss_radius", ctypes.c_int32),
+        ("levels", ctypes.c_int32),
+        ("iters", ctypes.c_int32 * MAX_LEVELS),
+        ("stop_eps", ctypes.c_float),
+        ("stop_window", ctypes.c_int32),
+        ("force_mode", ctypes.c_int32),
+        ("global_shift", ctypes.c_int32),
+        ("var_floor", ctypes.c_float),
+    ]
+
+
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+_f32 = ctypes.c_float
+_st = ctypes.c_int
+
+_SIGS = {
+    "disc_params_default": (_st, [ctypes.POINTER(Params)]),
+    "disc_status_str": (ctypes.c_char_p, [_st]),
+    "disc_create": (_st, [ctypes.POINTER(Params), ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
+    "disc_set_images": (_st, [_vp, _vp, _vp, _i32, _i32, _i32, ctypes.c_int]),
+    "disc_iterate": (_st, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_f32)]),
+    "disc_get_field": (_st, [_vp, _vp, ctypes.c_int]),
+    "disc_get_corrected": (_st, [_vp, _vp, ctypes.c_int]),
+    "disc_set_field": (_st, [_vp, _i32, _vp, ctypes.c_int]),
+    "disc_get_progress": (_st, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
+    "disc_get_norm_history": (_st, [_vp, _i32, _vp, _i32, ctypes.POINTER(_i32)]),
+    "disc_destroy": (_st, [_vp]),
+    "disc_qscale": (_f32, [_f32, ctypes.POINTER(_i32)]),
+    "disc_k_max_abs": (_st, [_vp, _i64, _vp, _vp]),
+    "disc_k_global_shift": (_st, [_vp, _vp, _vp, _i64, _vp, _vp]),
+    "disc_k_downsample2": (_st, [_vp, _vp, _i32, _i32, _i32, _vp]),
+    "disc_k_upsample_field2": (_st, [_vp, _vp, _i32, _i32, _i32, _vp]),
+    "disc_k_static_norm": (_st, [_vp, _vp, _i32, _i32, _i32, ctypes.POINTER(_i32), _f32, _f32, _vp]),
+    "disc_k_pass_a": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _i32, _i32,
+                            ctypes.POINTER(_i32), _f32, _f32, _i32, _vp]),
+    "disc_k_gauss": (_st, [_vp, _vp, _i32, _i32, _i32, _f32, _i32, _vp]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _fn = getattr(_lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+
+def header_functions(path=HEADER):
+    """Names of the functions include/disc.h declares."""
+    src = open(path).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:disc_status|float|const char\*)\s+(disc_\w+)\s*\(", src, re.M)))
+
+
+def _check(status, where):
+    if status != 0:
+        raise DiscError(status, where)
+
+
+def _ptr(t):
+    """Raw pointer of a torch tensor (device) or numpy array (host)."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        if not t.flags["C_CONTIGUOUS"]:
+            raise ValueError("numpy buffer must be C-contiguous")
+        return t.ctypes.data
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _mem_kind(t):
+    if isinstance(t, np.ndarray):
+        return MEM_HOST
+    return MEM_DEVICE if t.is_cuda else MEM_HOST
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _f32_check(t, shape, name):
+    if isinstance(t, np.ndarray):
+        if t.dtype != np.float32:
+            raise TypeError(f"{name} must be float32")
+    else:
+        import torch
+        if t.dtype != torch.float32:
+            raise TypeError(f"{name} must be float32")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+
+
+def make_params(patch=(3, 3, 3), sigma=1.0, radius=0, levels=2, iters=(50, 50), stop_eps=0.0,
+                stop_window=10, force_mode=FORCE_THIRION, global_shift=True, var_floor=1e-6):
+    p = Params()
+    _check(_lib.disc_params_default(ctypes.byref(p)), "disc_params_default")
+    for a in range(3):
+        p.patch[a] = int(patch[a])
+    p.gauss_sigma = float(sigma)
+    p.gauss_radius = int(radius)
+    p.levels = int(levels)
+    iters = list(iters)
+    if len(iters) != levels:
+        raise ValueError("one iteration count per level (coarsest first)")
+    for i in range(MAX_LEVELS):
+        p.iters[i] = int(iters[i]) if i < len(iters) else 0
+    p.stop_eps = float(stop_eps)
+    p.stop_window = int(stop_window)
+    p.force_mode = int(force_mode)
+    p.global_shift = 1 if global_shift else 0
+    p.var_floor = float(var_floor)
+    return p
+
+
+class Registration:
+    """One DISC registration context (disc_create .. disc_destroy).
+
+    ``stream``: a torch.cuda.Stream, a raw cudaStream_t int, or None for the
+    current torch stream.
+    """
+
+    def __init__(self, params: Params | None = None, device=0, stream=None, **kw):
+        if params is None:
+            params = make_params(**kw)
+        self.params = params
+        self.device = device
+        self._stream = _stream(stream)
+        h = _vp()
+        _check(_lib.disc_create(ctypes.byref(params), device, self._stream, ctypes.byref(h)), "disc_create")
+        self._h = h
+        self.dims = None
+
+    # -- lifetime ------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.disc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- calls ---------------------------------------------------------------
+    def set_images(self, ct, cbct):
+        nz, ny, nx = ct.shape
+        _f32_check(ct, (nz, ny, nx), "ct")
+        _f32_check(cbct, (nz, ny, nx), "cbct")
+        kind = _mem_kind(ct)
+        if _mem_kind(cbct) != kind:
+            raise ValueError("ct and cbct must both be host or both be device buffers")
+        _check(_lib.disc_set_images(self._h, _ptr(ct), _ptr(cbct), nx, ny, nz, kind), "disc_set_images")
+        self.dims = (nx, ny, nz)
+
+    def iterate(self, max_iters=-1, sync=True):
+        if sync:
+            done, last = _i32(0), _f32(0)
+            _check(_lib.disc_iterate(self._h, int(max_iters), ctypes.byref(done), ctypes.byref(last)),
+                   "disc_iterate")
+            return int(done.value), float(last.value)
+        _check(_lib.disc_iterate(self._h, int(max_iters), None, None), "disc_iterate")
+        return None
+
+    def get_field(self, out=None):
+        nx, ny, nz = self.dims
+        if out is None:
+            out = np.empty((3, nz, ny, nx), np.float32)
+        _f32_check(out, (3, nz, ny, nx), "out")
+        _check(_lib.disc_get_field(self._h, _ptr(out), _mem_kind(out)), "disc_get_field")
+        return out
+
+    def progress(self):
+        lev, it = _i32(0), _i32(0)
+        dims = (_i32 * 3)()
+        _check(_lib.disc_get_progress(self._h, ctypes.byref(lev), ctypes.byref(it), dims), "disc_get_progress")
+        return int(lev.value), int(it.value), (dims[0], dims[1], dims[2])
+
+    def get_corrected(self, out=None):
+        _, _, (nx, ny, nz) = self.progress()
+        if out is None:
+            out = np.empty((nz, ny, nx), np.float32)
+        _f32_check(out, (nz, ny, nx), "out")
+        _check(_lib.disc_get_corrected(self._h, _ptr(out), _mem_kind(out)), "disc_get_corrected")
+        return out
+
+    def set_field(self, level, r):
+        _check(_lib.disc_set_field(self._h, int(level), _ptr(r), _mem_kind(r)), "disc_set_field")
+
+    def norm_history(self, level, cap=100000):
+        out = np.empty(cap, np.float32)
+        n = _i32(0)
+        _check(_lib.disc_get_norm_history(self._h, int(level), out.ctypes.data, cap, ctypes.byref(n)),
+               "disc_get_norm_history")
+        return out[:n.value].copy()
+
+
+# ---------------------------------------------------------------------------
+# Kernel-level calls (device tensors, caller's stream)
+# ---------------------------------------------------------------------------
+
+def qscale(max_abs, patch):
+    p = (_i32 * 3)(*patch)
+    return float(_lib.disc_qscale(float(max_abs), p))
+
+
+def k_max_abs(v, out, stream=None):
+    _check(_lib.disc_k_max_abs(_ptr(v), v.numel(), _ptr(out), _stream(stream)), "disc_k_max_abs")
+
+
+def k_global_shift(Im, Is, Is_out, delta_out=None, stream=None):
+    _check(_lib.disc_k_global_shift(_ptr(Im), _ptr(Is), _ptr(Is_out), Im.numel(), _ptr(delta_out),
+                                    _stream(stream)), "disc_k_global_shift")
+
+
+def k_downsample2(inp, out, stream=None):
+    nz, ny, nx = inp.shape
+    _check(_lib.disc_k_downsample2(_ptr(inp), _ptr(out), nx, ny, nz, _stream(stream)), "disc_k_downsample2")
+
+
+def k_upsample_field2(rc, rf, stream=None):
+    _, nz, ny, nx = rf.shape
+    _check(_lib.disc_k_upsample_field2(_ptr(rc), _ptr(rf), nx, ny, nz, _stream(stream)),
+           "disc_k_upsample_field2")
+
+
+def k_static_norm(Is, zs, patch, qs, var_floor=1e-6, stream=None):
+    nz, ny, nx = Is.shape
+    p = (_i32 * 3)(*patch)
+    _check(_lib.disc_k_static_norm(_ptr(Is), _ptr(zs), nx, ny, nz, p, float(qs), float(var_floor),
+                                   _stream(stream)), "disc_k_static_norm")
+
+
+def k_pass_a(Im, zs, r, u, patch, qs, m_out=None, f_out=None, norms_out=None, var_floor=1e-6,
+             force_mode=FORCE_THIRION, stream=None):
+    nz, ny, nx = Im.shape
+    p = (_i32 * 3)(*patch)
+    _check(_lib.disc_k_pass_a(_ptr(Im), _ptr(zs), _ptr(r), _ptr(u), _ptr(m_out), _ptr(f_out),
+                              _ptr(norms_out), nx, ny, nz, p, float(qs), float(var_floor),
+                              int(force_mode), _stream(stream)), "disc_k_pass_a")
+
+
+def k_gauss(u, r, sigma, radius=0, stream=None):
+    _, nz, ny, nx = u.shape
+    _check(_lib.disc_k_gauss(_ptr(u), _ptr(r), nx, ny, nz, float(sigma), int(radius), _stream(stream)),
+           "disc_k_gauss")

@@ -82,6 +82,14 @@ def test_warp_matches_scalar_bruteforce():
                 assert abs(out[z, y, x] - ref) <= 1e-10 * (1 + abs(ref))
 
 
+def test_warp_region_equals_warp_on_the_full_grid():
+    img = phantom.random_volume((7, 8, 9), 27).astype(np.float64)
+    r = phantom.random_field((7, 8, 9), 28, amp=4.0).astype(np.float64)
+    full = O.warp(img, r)
+    sub = O.warp_region(img, r[:, 2:6, 1:7, 3:9], (3, 1, 2))
+    np.testing.assert_array_equal(sub, full[2:6, 1:7, 3:9])
+
+
 # ------------------------------------------------------------ moments (Eq. 3)
 
 def _patch(X, z, y, x, half):
