@@ -22,9 +22,12 @@
  *    or pageable); DISC_MEM_DEVICE pointers are device memory on the
  *    context's device.  The library never keeps a caller pointer after a
  *    call returns, and the caller owns every buffer it passes.
- *  - Streams: all device work is enqueued on the stream given at creation
- *    (NULL makes the library create its own non-blocking stream).  Calls that
- *    write host memory synchronise that stream before returning.
+ *  - Streams: every call is ordered on the caller's stream given at
+ *    creation (a cudaStream_t; NULL = the legacy default stream): the work
+ *    runs on a library stream that waits for the caller's stream on entry and
+ *    that the caller's stream waits for on exit (CUDA events), so that the
+ *    library can replay CUDA graphs.  Calls that write host memory
+ *    synchronise before returning.
  *  - Errors: every call returns a disc_status by value; no C++ exception
  *    crosses this boundary.  The first CUDA error seen by a context is
  *    sticky: later calls on it return DISC_ERR_STATE until disc_destroy.
@@ -87,8 +90,8 @@ disc_status disc_params_default(disc_params* p);
 /* Human-readable name of a status code (static storage, never NULL). */
 const char* disc_status_str(disc_status s);
 
-/* Create a context on CUDA device `device`, enqueueing on `cuda_stream`
- * (a cudaStream_t, or NULL for a library-owned stream).  Validates *p:
+/* Create a context on CUDA device `device`, ordered on `cuda_stream`
+ * (a cudaStream_t, or NULL for the legacy default stream).  Validates *p:
  * odd patch sizes in [1, 31], sigma > 0, levels in [1, 8], iters >= 0.
  * On success *out owns device resources until disc_destroy. */
 disc_status disc_create(const disc_params* p, int device, void* cuda_stream,
@@ -189,14 +192,23 @@ disc_status disc_k_static_norm(const float* Is, float* zs, int32_t nx, int32_t n
                                int32_t nz, const int32_t patch[3], float qscale,
                                float var_floor, void* stream);
 
-/* One fused iteration front (Algorithm A1 steps 1, 3, 4, 5):
- * m = I_m(x + r(x)) (trilinear, clamped); E(M), STD(M) over the patch;
- * f = zs STD(M) + E(M); dr from Eq. (1) with f as I_s; u = r + dr.
- * Optional taps m_out, f_out (NULL to skip) receive m and f.
- * norms_out (device double[2], may be NULL) receives sum|dr| and sum|r|.
- * u must not alias r. */
+/* Trilinear warp (Sec. 2.1; Sec. 2.3 kernel 5): m(x) = I_m(x + r(x)), the
+ * sample position clamped to the volume per axis.  Im, m [nz][ny][nx];
+ * r [3][nz][ny][nx].  ny, nz <= 65535.  m must not alias Im or r. */
+disc_status disc_k_warp(const float* Im, const float* r, float* m, int32_t nx,
+                        int32_t ny, int32_t nz, void* stream);
+
+/* One iteration front (Algorithm A1 steps 1, 3, 4, 5):
+ * m = I_m(x + r(x)); E(M), STD(M) over the truncated patch (Eq. 3);
+ * I'_s = zs STD(M) + E(M) (= a I_s + b of Eqs. 5-6); dr from Eq. (1) with
+ * I'_s in place of I_s; u = r + dr.
+ * Optional outputs (NULL to skip): m_out receives m; d_out receives
+ * I'_s - m (the corrected CBCT relative to the warped CT, the quantity the
+ * force is computed from).  norms_out (device double[2], may be NULL)
+ * receives sum|dr| and sum|r|.  u must not alias r.  Temporary device
+ * memory is taken from the stream-ordered allocator. */
 disc_status disc_k_pass_a(const float* Im, const float* zs, const float* r, float* u,
-                          float* m_out, float* f_out, double* norms_out,
+                          float* m_out, float* d_out, double* norms_out,
                           int32_t nx, int32_t ny, int32_t nz, const int32_t patch[3],
                           float qscale, float var_floor, int32_t force_mode,
                           void* stream);

@@ -33,6 +33,7 @@ struct Level {
   float* Im = nullptr;   // moving image (CT) at this level
   float* Is = nullptr;   // static image (CBCT, shifted) at this level
   float* zs = nullptr;   // (I_s - E(S)) / STD(S) over the patch
+  float* m = nullptr;    // warped CT I_m(x + r(x))
   float* r = nullptr;    // field [3][N]
   float* u = nullptr;    // r + dr [3][N]
   float* hist = nullptr; // l^(k) history
@@ -112,6 +113,7 @@ void free_levels(disc_ctx* c) {
     cudaFree(v.Im);
     cudaFree(v.Is);
     cudaFree(v.zs);
+    cudaFree(v.m);
     cudaFree(v.r);
     cudaFree(v.u);
     cudaFree(v.hist);
@@ -125,14 +127,12 @@ void free_levels(disc_ctx* c) {
 
 // Make the library stream wait for work already queued on the caller's stream.
 cudaError_t enter(disc_ctx* c) {
-  if (c->user == c->s) return cudaSuccess;
   cudaError_t e = cudaEventRecord(c->ev_in, c->user);
   if (e != cudaSuccess) return e;
   return cudaStreamWaitEvent(c->s, c->ev_in, 0);
 }
 // Make the caller's stream wait for the work this call queued.
 cudaError_t leave(disc_ctx* c) {
-  if (c->user == c->s) return cudaSuccess;
   cudaError_t e = cudaEventRecord(c->ev_out, c->s);
   if (e != cudaSuccess) return e;
   return cudaStreamWaitEvent(c->user, c->ev_out, 0);
@@ -165,7 +165,7 @@ BoxArgs box_args(const disc_ctx* c, const Level& v) {
 cudaError_t queue_iterations(disc_ctx* c, int l, int n) {
   Level& v = c->lev[l];
   BoxArgs a = box_args(c, v);
-  a.src = v.Im;
+  a.src = v.m;
   a.zs = v.zs;
   a.r = v.r;
   a.out = v.u;
@@ -185,7 +185,9 @@ cudaError_t queue_iterations(disc_ctx* c, int l, int n) {
   NormState st{v.hist, c->d_iter + l, c->d_stop + l, v.hist_cap, c->p.stop_window, c->p.stop_eps};
   const int nparts = (int)(v.pa.grid.x * v.pa.grid.y * v.pa.grid.z);
   for (int k = 0; k < n; ++k) {
-    cudaError_t e = box_launch(kModeIterate, a, v.pa, c->s);
+    cudaError_t e = launch_warp(v.Im, v.r, v.m, v.nx, v.ny, v.nz, c->d_stop + l, c->s);
+    if (e != cudaSuccess) return e;
+    e = box_launch(kModeIterate, a, v.pa, c->s);
     if (e != cudaSuccess) return e;
     e = gauss_launch(g, v.pb, c->s);
     if (e != cudaSuccess) return e;
@@ -295,7 +297,7 @@ disc_status disc_create(const disc_params* p, int device, void* cuda_stream, dis
   cudaError_t e = cudaStreamCreateWithFlags(&ctx->s, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming);
-  ctx->user = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : ctx->s;
+  ctx->user = static_cast<cudaStream_t>(cuda_stream);   // NULL: the legacy default stream
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_iter, sizeof(int) * DISC_MAX_LEVELS);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_stop, sizeof(int) * DISC_MAX_LEVELS);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_scratch, sizeof(double) * (2 * kShiftBlocks + 2));
@@ -368,6 +370,7 @@ disc_status disc_set_images(disc_ctx* ctx, const float* ct, const float* cbct, i
       cudaError_t e = cudaMalloc(&v.Im, v.N * sizeof(float));
       if (e == cudaSuccess) e = cudaMalloc(&v.Is, v.N * sizeof(float));
       if (e == cudaSuccess) e = cudaMalloc(&v.zs, v.N * sizeof(float));
+      if (e == cudaSuccess) e = cudaMalloc(&v.m, v.N * sizeof(float));
       if (e == cudaSuccess) e = cudaMalloc(&v.r, 3 * v.N * sizeof(float));
       if (e == cudaSuccess) e = cudaMalloc(&v.u, 3 * v.N * sizeof(float));
       if (e == cudaSuccess) e = cudaMalloc(&v.hist, v.hist_cap * sizeof(float));
@@ -528,8 +531,9 @@ disc_status disc_get_corrected(disc_ctx* ctx, float* out, int mem_kind) {
   DeviceGuard guard(ctx->device);
   CK(enter(ctx));
   Level& v = ctx->lev[ctx->cur_level];
+  CK(launch_warp(v.Im, v.r, v.m, v.nx, v.ny, v.nz, nullptr, ctx->s));
   BoxArgs a = box_args(ctx, v);
-  a.src = v.Im;
+  a.src = v.m;
   a.zs = v.zs;
   a.r = v.r;
   a.out = v.u;
@@ -691,8 +695,17 @@ disc_status disc_k_static_norm(const float* Is, float* zs, int32_t nx, int32_t n
   return DISC_OK;
 }
 
+disc_status disc_k_warp(const float* Im, const float* r, float* m, int32_t nx, int32_t ny, int32_t nz,
+                       void* stream) {
+  if (!Im || !r || !m) return DISC_ERR_ARG;
+  if (nx < 1 || ny < 1 || nz < 1 || ny > 65535 || nz > 65535) return DISC_ERR_SHAPE;
+  disc_ctx* ctx = nullptr;
+  CK(launch_warp(Im, r, m, nx, ny, nz, nullptr, (cudaStream_t)stream));
+  return DISC_OK;
+}
+
 disc_status disc_k_pass_a(const float* Im, const float* zs, const float* r, float* u, float* m_out,
-                          float* f_out, double* norms_out, int32_t nx, int32_t ny, int32_t nz,
+                          float* d_out, double* norms_out, int32_t nx, int32_t ny, int32_t nz,
                           const int32_t patch[3], float qscale, float var_floor, int32_t force_mode,
                           void* stream) {
   int h[3];
@@ -701,7 +714,7 @@ disc_status disc_k_pass_a(const float* Im, const float* zs, const float* r, floa
   if (force_mode != DISC_FORCE_THIRION && force_mode != DISC_FORCE_DOUBLE) return DISC_ERR_ARG;
   disc_status st = check_patch(patch, h);
   if (st != DISC_OK) return st;
-  if (nx < 1 || ny < 1 || nz < 1) return DISC_ERR_SHAPE;
+  if (nx < 1 || ny < 1 || nz < 1 || ny > 65535 || nz > 65535) return DISC_ERR_SHAPE;
   int dev = 0, sms = kNumSMs;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -710,15 +723,19 @@ disc_status disc_k_pass_a(const float* Im, const float* zs, const float* r, floa
   cudaStream_t s = (cudaStream_t)stream;
   disc_ctx* ctx = nullptr;
   const int nparts = (int)(p.grid.x * p.grid.y * p.grid.z);
+  const size_t N = (size_t)nx * ny * nz;
   float* parts = nullptr;
+  float* m = m_out;
   CK(cudaMallocAsync(&parts, sizeof(float) * 2 * nparts, s));
+  cudaError_t e = cudaSuccess;
+  if (!m) e = cudaMallocAsync(&m, sizeof(float) * N, s);
+  if (e == cudaSuccess) e = launch_warp(Im, r, m, nx, ny, nz, nullptr, s);
   BoxArgs a{};
-  a.src = Im;
+  a.src = m;
   a.zs = zs;
   a.r = r;
   a.out = u;
-  a.m_tap = m_out;
-  a.f_tap = f_out;
+  a.f_tap = d_out;
   a.partials = parts;
   a.nx = nx;
   a.ny = ny;
@@ -730,12 +747,16 @@ disc_status disc_k_pass_a(const float* Im, const float* zs, const float* r, floa
   a.inv_qscale = 1.0f / qscale;
   a.var_floor = var_floor;
   a.force_mode = force_mode;
-  cudaError_t e = box_launch(kModeIterate, a, p, s);
+  if (e == cudaSuccess) e = box_launch(kModeIterate, a, p, s);
   if (e == cudaSuccess && norms_out) {
     e = launch_partials_sum(parts, nparts, 0, norms_out, s);
     if (e == cudaSuccess) e = launch_partials_sum(parts, nparts, 1, norms_out + 1, s);
   }
   cudaError_t e2 = cudaFreeAsync(parts, s);
+  if (!m_out && m) {
+    cudaError_t e3 = cudaFreeAsync(m, s);
+    if (e2 == cudaSuccess) e2 = e3;
+  }
   CK(e);
   CK(e2);
   return DISC_OK;

@@ -1,0 +1,436 @@
+// Patch-moment kernels specialised for cubic patches of half size H (patch
+// 2H+1 per axis, H = 1..7) on a 32 x 16 column tile (sm_103a).
+//
+// Same computation as the generic box pass (box_pass.cu): exact integer
+// sliding sums of q = rint(v 2^e) and q^2 over the truncated patch (Eq. 3),
+// the patch moments E(X), STD(X) (Appendix A.4), the moment-matched CBCT kept
+// as d = I'_s - I_m^(k) = zs STD(M) + (E(M) - m) (Eqs. 5-6), and in iteration
+// mode the demons force of Eq. (1) with grad I'_s = grad d + grad m and the
+// update u = r + dr (Algorithm A1 steps 3-5).  With every size known at
+// compile time the index arithmetic uses constant divisors, the per-column z
+// sums live in registers, the leaving plane is re-read from L2 instead of
+// being kept in shared memory, and the x and y window sums slide.
+
+#include <cuda_runtime.h>
+
+#include "internal.cuh"
+
+namespace disc {
+
+namespace {
+
+template <int MODE, int H>
+struct FastLayout {
+  static constexpr int EXT = (MODE == kModeIterate) ? 1 : 0;
+  static constexpr int TX = 32, TY = 16;
+  static constexpr int FX = TX + 2 * EXT, FY = TY + 2 * EXT;
+  static constexpr int WX = FX + 2 * H, WY = FY + 2 * H;
+  static constexpr int WXP = WX | 1;                     // odd row stride of the z-sum plane
+  static constexpr int WN = WX * WY;
+  static constexpr int K1 = (WN + kThreads - 1) / kThreads;   // W columns per thread
+  static constexpr int FN = FX * FY;
+  static constexpr int NSX0 = (kThreads / WY) < 1 ? 1 : (kThreads / WY);
+  static constexpr int SX = (FX + NSX0 - 1) / NSX0;     // x outputs per sliding task
+  static constexpr int NSX = (FX + SX - 1) / SX;
+  static constexpr int NSY0 = (kThreads / FX) < 1 ? 1 : (kThreads / FX);
+  static constexpr int SY = (FY + NSY0 - 1) / NSY0;     // y outputs per sliding task
+  static constexpr int NSY = (FY + SY - 1) / SY;
+  static constexpr int NP = (2 * H + 1) * (2 * H + 1) * (2 * H + 1);
+  static constexpr size_t o_s2z = 0;
+  static constexpr size_t o_xb1 = o_s2z + 8 * (size_t)WY * WXP;
+  static constexpr size_t o_xb2 = o_xb1 + 8 * (size_t)WY * FX;
+  static constexpr size_t o_s1z = o_xb2 + 8 * (size_t)WY * FX;
+  static constexpr size_t o_dring = o_s1z + 4 * (size_t)WY * WXP;
+  static constexpr size_t o_mring = o_dring + (EXT ? 4 * 3 * (size_t)FN : 0);
+  static constexpr size_t bytes = ((o_mring + (EXT ? 4 * 3 * (size_t)FN : 0)) + 15) & ~(size_t)15;
+};
+
+// Patch moments from exact integer sums (see box_pass.cu for the derivation):
+// dc = E(X) - v_c; sigma = STD(X), 0 when Var(X) <= var_floor.
+// T = sum (q - k)^2 = S2 - k (S1 + e) with k = round(S1/n), e = S1 - n k.
+__device__ __forceinline__ void moments_fast(long long S1, long long S2, int n, float inv_n, int qc,
+                                             float inv_qs, float var_floor, float& dc, float& sigma) {
+  const long long ec = S1 - (long long)n * qc;
+  dc = (float)ec * (inv_n * inv_qs);
+  const int k = __float2int_rn((float)S1 * inv_n);
+  const long long e = S1 - (long long)n * k;
+  const unsigned long long T = (unsigned long long)S2 - (unsigned long long)k * (unsigned long long)(S1 + e);
+  const float ef = (float)e * inv_n;
+  const float varq = fmaf((float)(long long)T, inv_n, -ef * ef);
+  const float var = varq * (inv_qs * inv_qs);
+  sigma = var > var_floor ? sqrtf(var) : 0.0f;
+}
+
+__device__ __forceinline__ float diff1(float vm, float v0, float vp, int c, int n) {
+  if (n < 2) return 0.0f;
+  if (c == 0) return vp - v0;
+  if (c == n - 1) return v0 - vm;
+  return 0.5f * (vp - vm);
+}
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+template <int MODE, int H>
+__global__ void __launch_bounds__(kThreads) k_box_h(BoxArgs a) {
+  using B = FastLayout<MODE, H>;
+  if (a.stop != nullptr && *(volatile const int*)a.stop != 0) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  long long* s2z = reinterpret_cast<long long*>(smem + B::o_s2z);
+  long long* xb1 = reinterpret_cast<long long*>(smem + B::o_xb1);
+  long long* xb2 = reinterpret_cast<long long*>(smem + B::o_xb2);
+  int* s1z = reinterpret_cast<int*>(smem + B::o_s1z);
+  float* dring = reinterpret_cast<float*>(smem + B::o_dring);
+  float* mring = reinterpret_cast<float*>(smem + B::o_mring);
+
+  const int tid = threadIdx.x;
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const int plane = nx * ny;                 // N < 2^31 is checked on the host
+  const int N = plane * nz;
+  const int x0 = blockIdx.x * B::TX, y0 = blockIdx.y * B::TY;
+  const int z0 = blockIdx.z * a.zlen;
+  const int z1 = min(nz, z0 + a.zlen);
+  const float* __restrict__ src = a.src;
+  const float qs = a.qscale, inv_qs = a.inv_qscale, vfl = a.var_floor;
+
+  // ---- this thread's W columns: plane offset (or -1 outside) and z sums ------
+  int goff[B::K1], sidx[B::K1], s1r[B::K1];
+  long long s2r[B::K1];
+#pragma unroll
+  for (int k = 0; k < B::K1; ++k) {
+    const int e = tid + k * kThreads;
+    goff[k] = -1;
+    sidx[k] = -1;
+    s1r[k] = 0;
+    s2r[k] = 0;
+    if (e < B::WN) {
+      const int wy = e / B::WX, wx = e - wy * B::WX;
+      const int gx = x0 - B::EXT - H + wx, gy = y0 - B::EXT - H + wy;
+      sidx[k] = wy * B::WXP + wx;
+      if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) goff[k] = gy * nx + gx;
+    }
+  }
+
+  const int zc_lo = max(0, z0 - B::EXT);
+  const int zc_hi = min(nz - 1, z1 - 1 + B::EXT);
+  const int zi0 = max(0, zc_lo - H);
+  const int zi1 = zc_hi + H;
+  float acc0 = 0.0f, acc1 = 0.0f;
+
+  for (int zi = zi0; zi <= zi1; ++zi) {
+    // ---- stage 1: z sliding sums (registers), published for the x pass -------
+    const int zold = zi - (2 * H + 1);
+    const bool has_new = zi < nz, has_old = zold >= zi0;
+    const float* pn = src + (size_t)zi * plane;
+    const float* po = src + (size_t)(has_old ? zold : 0) * plane;
+    float vn[B::K1], vo[B::K1];
+#pragma unroll
+    for (int k = 0; k < B::K1; ++k) {
+      vn[k] = (has_new && goff[k] >= 0) ? __ldg(pn + goff[k]) : 0.0f;
+      vo[k] = (has_old && goff[k] >= 0) ? __ldg(po + goff[k]) : 0.0f;
+    }
+#pragma unroll
+    for (int k = 0; k < B::K1; ++k) {
+      if (sidx[k] < 0) continue;
+      const int qn = __float2int_rn(vn[k] * qs), qo = __float2int_rn(vo[k] * qs);
+      s1r[k] += qn - qo;
+      s2r[k] += (long long)qn * qn - (long long)qo * qo;
+      s1z[sidx[k]] = s1r[k];
+      s2z[sidx[k]] = s2r[k];
+    }
+    __syncthreads();
+
+    const int zc = zi - H;
+    if (zc < zc_lo || zc > zc_hi) continue;   // uniform
+
+    // ---- stage 2a: x window sums, sliding, one task per (segment, row) ---------
+    for (int t = tid; t < B::NSX * B::WY; t += kThreads) {
+      const int sg = t / B::WY, wy = t - sg * B::WY;
+      const int fx0 = sg * B::SX;
+      const int* r1 = s1z + wy * B::WXP + fx0;
+      const long long* r2 = s2z + wy * B::WXP + fx0;
+      long long b1 = 0, b2 = 0;
+#pragma unroll
+      for (int k = 0; k <= 2 * H; ++k) {
+        b1 += r1[k];
+        b2 += r2[k];
+      }
+      long long* o1 = xb1 + wy * B::FX + fx0;
+      long long* o2 = xb2 + wy * B::FX + fx0;
+      o1[0] = b1;
+      o2[0] = b2;
+#pragma unroll
+      for (int j = 1; j < B::SX; ++j) {
+        if (fx0 + j < B::FX) {
+          b1 += r1[j + 2 * H] - r1[j - 1];
+          b2 += r2[j + 2 * H] - r2[j - 1];
+          o1[j] = b1;
+          o2[j] = b2;
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---- stage 2b: y window sums, sliding; moments and correction --------------
+    const int zslot = zc % 3;
+    const bool zin = zc >= H && zc < nz - H;
+    const int nzc = box_count(zc, nz, H);
+    const bool out_plane = zc >= z0 && zc < z1;
+    const float* zplane = src + (size_t)zc * plane;
+    for (int t = tid; t < B::NSY * B::FX; t += kThreads) {
+      const int sy = t / B::FX, fx = t - sy * B::FX;
+      const int gx = x0 - B::EXT + fx;
+      if (gx < 0 || gx >= nx) continue;
+      const int fy0 = sy * B::SY;
+      const bool xin = gx >= H && gx < nx - H;
+      const int nxc = box_count(gx, nx, H);
+      long long b1 = 0, b2 = 0;
+#pragma unroll
+      for (int k = 0; k <= 2 * H; ++k) {
+        b1 += xb1[(fy0 + k) * B::FX + fx];
+        b2 += xb2[(fy0 + k) * B::FX + fx];
+      }
+#pragma unroll
+      for (int j = 0; j < B::SY; ++j) {
+        const int fy = fy0 + j;
+        if (fy >= B::FY) break;
+        if (j > 0) {
+          b1 += xb1[(fy + 2 * H) * B::FX + fx] - xb1[(fy - 1) * B::FX + fx];
+          b2 += xb2[(fy + 2 * H) * B::FX + fx] - xb2[(fy - 1) * B::FX + fx];
+        }
+        const int gy = y0 - B::EXT + fy;
+        if (gy < 0 || gy >= ny) continue;
+        int n;
+        float inv_n;
+        if (xin && zin && gy >= H && gy < ny - H) {
+          n = B::NP;
+          inv_n = 1.0f / (float)B::NP;
+        } else {
+          n = nxc * box_count(gy, ny, H) * nzc;
+          inv_n = 1.0f / (float)n;
+        }
+        const int g = gy * nx + gx;
+        const float vc = __ldg(zplane + g);
+        float dc, sg_;
+        moments_fast(b1, b2, n, inv_n, __float2int_rn(vc * qs), inv_qs, vfl, dc, sg_);
+        const size_t gz = (size_t)zc * plane + g;
+        if (MODE == kModeStatic) {
+          a.out[gz] = sg_ > 0.0f ? -dc / sg_ : 0.0f;   // (I_s - E(S)) / STD(S)
+          continue;
+        }
+        const float zsv = __ldg(a.zs + gz);
+        const float d = fmaf(zsv, sg_, dc);               // I'_s - I_m^(k)
+        if (MODE == kModeIterate) {
+          const int fi = zslot * B::FN + fy * B::FX + fx;
+          dring[fi] = d;
+          mring[fi] = vc;
+          if (a.f_tap && out_plane && fx >= 1 && fx <= B::TX && fy >= 1 && fy <= B::TY) a.f_tap[gz] = d;
+        } else if (MODE == kModeCorrected) {
+          a.out[gz] = vc + d;
+        } else if (MODE == kModeSsdLoss) {
+          acc0 = fmaf(d, d, acc0);
+        } else if (MODE == kModeSsdAdjoint) {
+          const float D = -2.0f * d;
+          const float A = -D * inv_n;
+          const float Bc = sg_ > 0.0f ? -D * zsv * inv_n / sg_ : 0.0f;
+          a.out[gz] = A;
+          a.out[(size_t)N + gz] = Bc;
+          a.out[2 * (size_t)N + gz] = Bc * (vc + dc);
+          a.out[3 * (size_t)N + gz] = D;
+        }
+      }
+    }
+    if (MODE != kModeIterate) continue;
+    __syncthreads();
+
+    // ---- stage 3: demons force (Eq. 1) and update ------------------------------
+#pragma unroll
+    for (int back = 1; back >= 0; --back) {
+      const int zo = zc - back;
+      if (zo < z0 || zo >= z1) continue;
+      if (back == 0 && zc != nz - 1) continue;
+      const int so = zo % 3, sm = (zo + 2) % 3, sp = (zo + 1) % 3;
+      const float* dp = dring + so * B::FN;
+      const float* mp = mring + so * B::FN;
+      const bool zlo = zo > 0, zhi = zo < nz - 1;
+#pragma unroll
+      for (int i = 0; i < (B::TX * B::TY) / kThreads; ++i) {
+        const int o = tid + i * kThreads;
+        const int oy = o / B::TX, ox = o - oy * B::TX;
+        const int gx = x0 + ox, gy = y0 + oy;
+        if (gx >= nx || gy >= ny) continue;
+        const int fi = (oy + 1) * B::FX + (ox + 1);
+        const float d0 = dp[fi], m0 = mp[fi];
+        const float gdx = diff1(dp[fi - 1], d0, dp[fi + 1], gx, nx);
+        const float gmx = diff1(mp[fi - 1], m0, mp[fi + 1], gx, nx);
+        const float gdy = diff1(dp[fi - B::FX], d0, dp[fi + B::FX], gy, ny);
+        const float gmy = diff1(mp[fi - B::FX], m0, mp[fi + B::FX], gy, ny);
+        const float dzm = zlo ? dring[sm * B::FN + fi] : d0, dzp = zhi ? dring[sp * B::FN + fi] : d0;
+        const float mzm = zlo ? mring[sm * B::FN + fi] : m0, mzp = zhi ? mring[sp * B::FN + fi] : m0;
+        const float gdz = diff1(dzm, d0, dzp, zo, nz);
+        const float gmz = diff1(mzm, m0, mzp, zo, nz);
+        const float gfx = gdx + gmx, gfy = gdy + gmy, gfz = gdz + gmz;
+        const float diff = d0;
+        const float d2 = diff * diff;
+        const float den = fmaf(gfx, gfx, fmaf(gfy, gfy, fmaf(gfz, gfz, d2)));
+        const float s = den > 1e-9f ? __fdividef(diff, den) : 0.0f;
+        float drx = s * gfx, dry = s * gfy, drz = s * gfz;
+        if (a.force_mode == DISC_FORCE_DOUBLE) {
+          const float den2 = fmaf(gmx, gmx, fmaf(gmy, gmy, fmaf(gmz, gmz, d2)));
+          const float s2 = den2 > 1e-9f ? __fdividef(diff, den2) : 0.0f;
+          drx = fmaf(s2, gmx, drx);
+          dry = fmaf(s2, gmy, dry);
+          drz = fmaf(s2, gmz, drz);
+        }
+        const size_t g = (size_t)zo * plane + (size_t)gy * nx + gx;
+        const float rx = __ldg(a.r + g), ry = __ldg(a.r + (size_t)N + g), rz = __ldg(a.r + 2 * (size_t)N + g);
+        a.out[g] = rx + drx;
+        a.out[(size_t)N + g] = ry + dry;
+        a.out[2 * (size_t)N + g] = rz + drz;
+        acc0 += sqrt_approx(fmaf(drx, drx, fmaf(dry, dry, drz * drz)));
+        acc1 += sqrt_approx(fmaf(rx, rx, fmaf(ry, ry, rz * rz)));
+      }
+    }
+    // stage 2b of the next plane rewrites a ring slot read here only after two
+    // more barriers (after its stage 1 and stage 2a)
+  }
+
+  if (MODE == kModeIterate || MODE == kModeSsdLoss) {
+    __shared__ float red[2][kThreads / 32];
+    for (int off = 16; off > 0; off >>= 1) {
+      acc0 += __shfl_down_sync(0xffffffffu, acc0, off);
+      acc1 += __shfl_down_sync(0xffffffffu, acc1, off);
+    }
+    const int lane = tid & 31, wid = tid >> 5;
+    if (lane == 0) {
+      red[0][wid] = acc0;
+      red[1][wid] = acc1;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      float t0 = 0.0f, t1 = 0.0f;
+      for (int w = 0; w < kThreads / 32; ++w) {
+        t0 += red[0][w];
+        t1 += red[1][w];
+      }
+      const size_t b = (size_t)blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
+      a.partials[2 * b] = t0;
+      a.partials[2 * b + 1] = t1;
+    }
+  }
+}
+
+constexpr int kMaxDevices = 64;
+
+template <int MODE, int H>
+cudaError_t launch_fast(const BoxArgs& a, const BoxPlan& p, cudaStream_t s) {
+  static int set[kMaxDevices] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  if (!set[dev]) {
+    e = cudaFuncSetAttribute(k_box_h<MODE, H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)FastLayout<MODE, H>::bytes);
+    if (e != cudaSuccess) return e;
+    set[dev] = 1;
+  }
+  k_box_h<MODE, H><<<p.grid, kThreads, p.smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t launch_fast_h(const BoxArgs& a, const BoxPlan& p, cudaStream_t s) {
+  switch (a.hx) {
+    case 1: return launch_fast<MODE, 1>(a, p, s);
+    case 2: return launch_fast<MODE, 2>(a, p, s);
+    case 3: return launch_fast<MODE, 3>(a, p, s);
+    case 4: return launch_fast<MODE, 4>(a, p, s);
+    case 5: return launch_fast<MODE, 5>(a, p, s);
+    case 6: return launch_fast<MODE, 6>(a, p, s);
+    case 7: return launch_fast<MODE, 7>(a, p, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int MODE, int H>
+int occ_one(size_t smem) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_box_h<MODE, H>, kThreads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return n < 1 ? 1 : n;
+}
+
+template <int MODE>
+int fast_occ(int h, size_t smem) {
+  switch (h) {
+    case 1: return occ_one<MODE, 1>(smem);
+    case 2: return occ_one<MODE, 2>(smem);
+    case 3: return occ_one<MODE, 3>(smem);
+    case 4: return occ_one<MODE, 4>(smem);
+    case 5: return occ_one<MODE, 5>(smem);
+    case 6: return occ_one<MODE, 6>(smem);
+    case 7: return occ_one<MODE, 7>(smem);
+    default: return 1;
+  }
+}
+
+template <int MODE>
+size_t fast_bytes(int h) {
+  switch (h) {
+    case 1: return FastLayout<MODE, 1>::bytes;
+    case 2: return FastLayout<MODE, 2>::bytes;
+    case 3: return FastLayout<MODE, 3>::bytes;
+    case 4: return FastLayout<MODE, 4>::bytes;
+    case 5: return FastLayout<MODE, 5>::bytes;
+    case 6: return FastLayout<MODE, 6>::bytes;
+    case 7: return FastLayout<MODE, 7>::bytes;
+    default: return 0;
+  }
+}
+
+}  // namespace
+
+bool box_fast_ok(int nx, int ny, int nz, int hx, int hy, int hz) {
+  return hx == hy && hy == hz && hx >= 1 && hx <= 7 && (double)nx * ny * nz * 3.0 < 2147483647.0;
+}
+
+size_t box_fast_smem(int mode, int h) {
+  switch (mode) {
+    case kModeStatic: return fast_bytes<kModeStatic>(h);
+    case kModeIterate: return fast_bytes<kModeIterate>(h);
+    case kModeCorrected: return fast_bytes<kModeCorrected>(h);
+    case kModeSsdLoss: return fast_bytes<kModeSsdLoss>(h);
+    case kModeSsdAdjoint: return fast_bytes<kModeSsdAdjoint>(h);
+    default: return 0;
+  }
+}
+
+int box_fast_occupancy(int mode, int h, size_t smem) {
+  switch (mode) {
+    case kModeStatic: return fast_occ<kModeStatic>(h, smem);
+    case kModeIterate: return fast_occ<kModeIterate>(h, smem);
+    case kModeCorrected: return fast_occ<kModeCorrected>(h, smem);
+    case kModeSsdLoss: return fast_occ<kModeSsdLoss>(h, smem);
+    case kModeSsdAdjoint: return fast_occ<kModeSsdAdjoint>(h, smem);
+    default: return 1;
+  }
+}
+
+cudaError_t box_fast_launch(int mode, const BoxArgs& a, const BoxPlan& p, cudaStream_t s) {
+  switch (mode) {
+    case kModeStatic: return launch_fast_h<kModeStatic>(a, p, s);
+    case kModeIterate: return launch_fast_h<kModeIterate>(a, p, s);
+    case kModeCorrected: return launch_fast_h<kModeCorrected>(a, p, s);
+    case kModeSsdLoss: return launch_fast_h<kModeSsdLoss>(a, p, s);
+    case kModeSsdAdjoint: return launch_fast_h<kModeSsdAdjoint>(a, p, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace disc

@@ -29,24 +29,23 @@ __host__ __device__ __forceinline__ int box_count(int c, int n, int h) {
 }
 
 // ----------------------------------------------------------------------------
-// Box-pass (warp + moment statistics) kernels, box_pass.cu
+// Patch-moment (box) kernels, box_pass.cu
 // ----------------------------------------------------------------------------
 enum BoxMode : int {
   kModeStatic = 0,     // zs = (I_s - E(S)) / STD(S)
-  kModeIterate = 1,    // warp, moments, correction, force, u = r + dr, norms
-  kModeCorrected = 2,  // warp, moments, f = I'_s written out
-  kModeSsdLoss = 3,    // warp, moments, per-CTA partial sum of (m - f)^2
-  kModeSsdAdjoint = 4  // warp, moments, per-voxel adjoint coefficients (A, B, C, D)
+  kModeIterate = 1,    // moments of m, correction, force, u = r + dr, norms
+  kModeCorrected = 2,  // moments of m, I'_s written out
+  kModeSsdLoss = 3,    // moments of m, per-CTA partial sum of (m - I'_s)^2
+  kModeSsdAdjoint = 4  // moments of m, per-voxel adjoint coefficients (A, B, C, D)
 };
 
 struct BoxArgs {
-  const float* src;     // kModeStatic: I_s; otherwise I_m (gathered by the warp)
+  const float* src;     // kModeStatic: I_s; otherwise the warped CT m = I_m(x + r)
   const float* zs;      // CBCT normalised patch value (all modes but kModeStatic)
-  const float* r;       // field [3][N]
-  float* out;           // kModeStatic: zs; kModeIterate: u [3][N]; kModeCorrected: f;
+  const float* r;       // field [3][N] (kModeIterate)
+  float* out;           // kModeStatic: zs; kModeIterate: u [3][N]; kModeCorrected: I'_s;
                         // kModeSsdAdjoint: [4][N] (A, B, C, D)
-  float* m_tap;         // optional (kModeIterate): m = I_m(x + r)
-  float* f_tap;         // optional (kModeIterate): f = I'_s
+  float* f_tap;         // optional (kModeIterate): I'_s - m
   float* partials;      // per-CTA float[2] (kModeIterate: sum|dr|, sum|r|; kModeSsdLoss: loss)
   const int* stop;      // device flag: when non-zero the kernel returns at once
   int nx, ny, nz;
@@ -61,11 +60,22 @@ struct BoxPlan {
   size_t smem;
   int zlen;
   int tx, ty;
+  bool fast;            // cubic-patch kernel specialised on the half size (box_fast.cu)
 };
+
+// Specialised cubic-patch path (box_fast.cu)
+bool box_fast_ok(int nx, int ny, int nz, int hx, int hy, int hz);
+size_t box_fast_smem(int mode, int h);
+int box_fast_occupancy(int mode, int h, size_t smem);
+cudaError_t box_fast_launch(int mode, const BoxArgs& a, const BoxPlan& p, cudaStream_t s);
 
 // Plan a launch (grid, z chunk, dynamic shared memory) for a volume and patch.
 BoxPlan box_plan(int mode, int nx, int ny, int nz, int hx, int hy, int hz, int num_sms);
 cudaError_t box_launch(int mode, const BoxArgs& a, const BoxPlan& plan, cudaStream_t s);
+
+// Trilinear warp m = I_m(x + r(x)), warp.cu
+cudaError_t launch_warp(const float* Im, const float* r, float* m, int nx, int ny, int nz, const int* stop,
+                        cudaStream_t s);
 
 // ----------------------------------------------------------------------------
 // Gaussian pass, gauss.cu
@@ -83,6 +93,7 @@ struct GaussPlan {
   dim3 grid;
   size_t smem;
   int zlen;
+  bool queue;           // register-queue kernel (radius 1..8) or the generic one
 };
 int gauss_radius(float sigma, int radius);
 void gauss_taps(float sigma, int R, float* w);

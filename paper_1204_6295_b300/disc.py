@@ -76,6 +76,7 @@ _SIGS = {
     "disc_k_downsample2": (_st, [_vp, _vp, _i32, _i32, _i32, _vp]),
     "disc_k_upsample_field2": (_st, [_vp, _vp, _i32, _i32, _i32, _vp]),
     "disc_k_static_norm": (_st, [_vp, _vp, _i32, _i32, _i32, ctypes.POINTER(_i32), _f32, _f32, _vp]),
+    "disc_k_warp": (_st, [_vp, _vp, _vp, _i32, _i32, _i32, _vp]),
     "disc_k_pass_a": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _i32, _i32,
                             ctypes.POINTER(_i32), _f32, _f32, _i32, _vp]),
     "disc_k_gauss": (_st, [_vp, _vp, _i32, _i32, _i32, _f32, _i32, _vp]),
@@ -285,11 +286,17 @@ def k_static_norm(Is, zs, patch, qs, var_floor=1e-6, stream=None):
                                    _stream(stream)), "disc_k_static_norm")
 
 
-def k_pass_a(Im, zs, r, u, patch, qs, m_out=None, f_out=None, norms_out=None, var_floor=1e-6,
+def k_warp(Im, r, m, stream=None):
+    nz, ny, nx = Im.shape
+    _check(_lib.disc_k_warp(_ptr(Im), _ptr(r), _ptr(m), nx, ny, nz, _stream(stream)), "disc_k_warp")
+
+
+def k_pass_a(Im, zs, r, u, patch, qs, m_out=None, d_out=None, norms_out=None, var_floor=1e-6,
              force_mode=FORCE_THIRION, stream=None):
+    """Warp, patch moments, correction, force and update; d_out gets I'_s - m."""
     nz, ny, nx = Im.shape
     p = (_i32 * 3)(*patch)
-    _check(_lib.disc_k_pass_a(_ptr(Im), _ptr(zs), _ptr(r), _ptr(u), _ptr(m_out), _ptr(f_out),
+    _check(_lib.disc_k_pass_a(_ptr(Im), _ptr(zs), _ptr(r), _ptr(u), _ptr(m_out), _ptr(d_out),
                               _ptr(norms_out), nx, ny, nz, p, float(qs), float(var_floor),
                               int(force_mode), _stream(stream)), "disc_k_pass_a")
 

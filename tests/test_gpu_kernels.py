@@ -76,17 +76,18 @@ def test_pass_a_matches_oracle(disc, shape, patch, mode):
     zs = empty(*shape)
     disc.k_static_norm(dev(Is), zs, patch, qs_s)
     import torch
-    u, m, f = empty(3, *shape), empty(*shape), empty(*shape)
+    u, m, d = empty(3, *shape), empty(*shape), empty(*shape)
     norms = torch.zeros(2, dtype=torch.float64, device="cuda")
     r_d = dev(r)
-    disc.k_pass_a(dev(Im), zs, r_d, u, patch, qs_m, m_out=m, f_out=f, norms_out=norms, force_mode=mode)
-    m_g, f_g, u_g = host(m), host(f), host(u)
+    disc.k_pass_a(dev(Im), zs, r_d, u, patch, qs_m, m_out=m, d_out=d, norms_out=norms, force_mode=mode)
+    m_g, d_g, u_g = host(m), host(d), host(u)
+    f_g = m_g + d_g          # I'_s, formed in float64 from the GPU's m and I'_s - m
     # warp (Sec. 2.1, kernel 5)
     assert rel_err(m_g, O.warp(Im, r)) <= TOL
     # moments and correction (Eqs. 3-6) from the GPU's own warped image
     f_ref = O.correct(m_g, Is, half)
     assert rel_err(f_g, f_ref) <= TOL
-    # force and update (Eq. 1, A1 steps 4-5) from the GPU's own m and f
+    # force and update (Eq. 1, A1 steps 4-5) from the GPU's own m and I'_s
     dr_ref = O.force(m_g, f_g, mode)
     dr_g = u_g - r.astype(np.float64)
     scale = max(np.abs(dr_ref).max(), 1e-3)
@@ -105,10 +106,10 @@ def test_pass_a_affine_recovery_at_identity(disc):
     qs_m = disc.qscale(float(np.abs(Im).max()), patch)
     zs = empty(*shape)
     disc.k_static_norm(dev(Is), zs, patch, qs_s)
-    u, m, f = empty(3, *shape), empty(*shape), empty(*shape)
-    disc.k_pass_a(dev(Im), zs, dev(np.zeros((3,) + shape, np.float32)), u, patch, qs_m, m_out=m, f_out=f)
+    u, m, d = empty(3, *shape), empty(*shape), empty(*shape)
+    disc.k_pass_a(dev(Im), zs, dev(np.zeros((3,) + shape, np.float32)), u, patch, qs_m, m_out=m, d_out=d)
     assert np.array_equal(host(m), Im.astype(np.float64))       # identity warp is exact
-    assert rel_err(host(f), Im) <= TOL
+    assert rel_err(host(m) + host(d), Im) <= TOL
 
 
 def test_pass_a_constant_patches_give_zero_force(disc):
@@ -122,12 +123,20 @@ def test_pass_a_constant_patches_give_zero_force(disc):
     interior = np.ones(shape, bool)
     interior[:, :, 16:21] = False
     assert np.all(host(zs)[interior] == 0.0)   # constant CBCT patches away from the step
-    u, f = empty(3, *shape), empty(*shape)
+    u, d = empty(3, *shape), empty(*shape)
     r0 = np.zeros((3,) + shape, np.float32)
-    disc.k_pass_a(dev(Im), zs, dev(r0), u, patch, qs, f_out=f)
-    fg = host(f)
-    assert np.array_equal(fg[interior], Im[interior].astype(np.float64))
+    disc.k_pass_a(dev(Im), zs, dev(r0), u, patch, qs, d_out=d)
+    assert np.all(host(d)[interior] == 0.0)       # I'_s == I_m exactly in constant patches
     assert np.all(host(u)[:, interior] == 0.0)
+
+
+@pytest.mark.parametrize("shape", [(13, 37, 70), (1, 1, 1), (4, 3, 129), (6, 1, 1)])
+def test_warp_matches_oracle(disc, shape):
+    Im = ct_like(shape, 12)
+    r = phantom.random_field(shape, 13, amp=4.0)        # samples leave the volume too
+    m = empty(*shape)
+    disc.k_warp(dev(Im), dev(r), m)
+    assert rel_err(host(m), O.warp(Im, r)) <= TOL
 
 
 @pytest.mark.parametrize("shape", [(13, 37, 70), (1, 1, 1), (1, 5, 40), (40, 1, 1), (7, 16, 32), (30, 3, 65)])
