@@ -36,6 +36,7 @@ struct Level {
   float* m = nullptr;    // warped CT I_m(x + r(x))
   float* r = nullptr;    // field [3][N]
   float* u = nullptr;    // r + dr [3][N]
+  float* t = nullptr;    // xy-filtered field [3][N] (Gaussian scratch)
   float* hist = nullptr; // l^(k) history
   int hist_cap = 0;
   BoxPlan pa{};
@@ -116,6 +117,7 @@ void free_levels(disc_ctx* c) {
     cudaFree(v.m);
     cudaFree(v.r);
     cudaFree(v.u);
+    cudaFree(v.t);
     cudaFree(v.hist);
     v = Level{};
   }
@@ -176,6 +178,9 @@ cudaError_t queue_iterations(disc_ctx* c, int l, int n) {
   GaussArgs g{};
   g.u = v.u;
   g.r = v.r;
+  g.t = v.t;
+  g.Im = v.Im;
+  g.m = v.m;                // the z pass also warps I_m for the next iteration
   g.stop = c->d_stop + l;
   g.nx = v.nx;
   g.ny = v.ny;
@@ -184,10 +189,12 @@ cudaError_t queue_iterations(disc_ctx* c, int l, int n) {
   std::memcpy(g.w, c->w, sizeof(c->w));
   NormState st{v.hist, c->d_iter + l, c->d_stop + l, v.hist_cap, c->p.stop_window, c->p.stop_eps};
   const int nparts = (int)(v.pa.grid.x * v.pa.grid.y * v.pa.grid.z);
+  // m for the field the first iteration starts from; later iterations get it
+  // from the fused warp of the Gaussian z pass
+  cudaError_t e0 = launch_warp(v.Im, v.r, v.m, v.nx, v.ny, v.nz, c->d_stop + l, c->s);
+  if (e0 != cudaSuccess) return e0;
   for (int k = 0; k < n; ++k) {
-    cudaError_t e = launch_warp(v.Im, v.r, v.m, v.nx, v.ny, v.nz, c->d_stop + l, c->s);
-    if (e != cudaSuccess) return e;
-    e = box_launch(kModeIterate, a, v.pa, c->s);
+    cudaError_t e = box_launch(kModeIterate, a, v.pa, c->s);
     if (e != cudaSuccess) return e;
     e = gauss_launch(g, v.pb, c->s);
     if (e != cudaSuccess) return e;
@@ -373,6 +380,7 @@ disc_status disc_set_images(disc_ctx* ctx, const float* ct, const float* cbct, i
       if (e == cudaSuccess) e = cudaMalloc(&v.m, v.N * sizeof(float));
       if (e == cudaSuccess) e = cudaMalloc(&v.r, 3 * v.N * sizeof(float));
       if (e == cudaSuccess) e = cudaMalloc(&v.u, 3 * v.N * sizeof(float));
+      if (e == cudaSuccess) e = cudaMalloc(&v.t, 3 * v.N * sizeof(float));
       if (e == cudaSuccess) e = cudaMalloc(&v.hist, v.hist_cap * sizeof(float));
       if (e != cudaSuccess) {
         free_levels(ctx);
@@ -782,7 +790,14 @@ disc_status disc_k_gauss(const float* u, float* r, int32_t nx, int32_t ny, int32
   g.R = R;
   gauss_taps(sigma, R, g.w);
   disc_ctx* ctx = nullptr;
-  CK(gauss_launch(g, p, (cudaStream_t)stream));
+  cudaStream_t s = (cudaStream_t)stream;
+  float* t = nullptr;
+  if (p.queue) CK(cudaMallocAsync(&t, sizeof(float) * 3 * (size_t)nx * ny * nz, s));
+  g.t = t;
+  cudaError_t e = gauss_launch(g, p, s);
+  cudaError_t e2 = t ? cudaFreeAsync(t, s) : cudaSuccess;
+  CK(e);
+  CK(e2);
   return DISC_OK;
 }
 

@@ -29,12 +29,16 @@ struct FastLayout {
   static constexpr int WN = WX * WY;
   static constexpr int K1 = (WN + kThreads - 1) / kThreads;   // W columns per thread
   static constexpr int FN = FX * FY;
+  // sliding tasks: about one per thread (short tasks keep every warp busy)
   static constexpr int NSX0 = (kThreads / WY) < 1 ? 1 : (kThreads / WY);
   static constexpr int SX = (FX + NSX0 - 1) / NSX0;     // x outputs per sliding task
   static constexpr int NSX = (FX + SX - 1) / SX;
   static constexpr int NSY0 = (kThreads / FX) < 1 ? 1 : (kThreads / FX);
   static constexpr int SY = (FY + NSY0 - 1) / NSY0;     // y outputs per sliding task
   static constexpr int NSY = (FY + SY - 1) / SY;
+  static constexpr int KF = (FN + kThreads - 1) / kThreads;      // F elements per thread
+  static constexpr int TN = TX * TY;
+  static constexpr int KO = (TN + kThreads - 1) / kThreads;      // tile elements per thread
   static constexpr int NP = (2 * H + 1) * (2 * H + 1) * (2 * H + 1);
   static constexpr size_t o_s2z = 0;
   static constexpr size_t o_xb1 = o_s2z + 8 * (size_t)WY * WXP;
@@ -42,7 +46,9 @@ struct FastLayout {
   static constexpr size_t o_s1z = o_xb2 + 8 * (size_t)WY * FX;
   static constexpr size_t o_dring = o_s1z + 4 * (size_t)WY * WXP;
   static constexpr size_t o_mring = o_dring + (EXT ? 4 * 3 * (size_t)FN : 0);
-  static constexpr size_t bytes = ((o_mring + (EXT ? 4 * 3 * (size_t)FN : 0)) + 15) & ~(size_t)15;
+  static constexpr size_t o_zsf = o_mring + 4 * (EXT ? 3 : 1) * (size_t)FN;   // zs of the centre plane
+  static constexpr size_t o_ro = o_zsf + (MODE == kModeStatic ? 0 : 4 * (size_t)FN);
+  static constexpr size_t bytes = ((o_ro + (EXT ? 4 * 3 * (size_t)TN : 0)) + 15) & ~(size_t)15;
 };
 
 // Patch moments from exact integer sums (see box_pass.cu for the derivation):
@@ -50,15 +56,17 @@ struct FastLayout {
 // T = sum (q - k)^2 = S2 - k (S1 + e) with k = round(S1/n), e = S1 - n k.
 __device__ __forceinline__ void moments_fast(long long S1, long long S2, int n, float inv_n, int qc,
                                              float inv_qs, float var_floor, float& dc, float& sigma) {
-  const long long ec = S1 - (long long)n * qc;
-  dc = (float)ec * (inv_n * inv_qs);
-  const int k = __float2int_rn((float)S1 * inv_n);
-  const long long e = S1 - (long long)n * k;
-  const unsigned long long T = (unsigned long long)S2 - (unsigned long long)k * (unsigned long long)(S1 + e);
+  const int k = __float2int_rn((float)S1 * inv_n);       // ~ mean of q (within a few units)
+  const int e = (int)(S1 - (long long)n * k);            // |e| < 2^31: a few times n
   const float ef = (float)e * inv_n;
+  dc = ((float)(k - qc) + ef) * inv_qs;                   // E(X) - v_c
+  const unsigned long long T = (unsigned long long)S2 - (unsigned long long)(long long)k *
+                                                            (unsigned long long)(S1 + e);
   const float varq = fmaf((float)(long long)T, inv_n, -ef * ef);
   const float var = varq * (inv_qs * inv_qs);
-  sigma = var > var_floor ? sqrtf(var) : 0.0f;
+  float sq;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(sq) : "f"(var));
+  sigma = var > var_floor ? sq : 0.0f;
 }
 
 __device__ __forceinline__ float diff1(float vm, float v0, float vp, int c, int n) {
@@ -75,7 +83,7 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 }
 
 template <int MODE, int H>
-__global__ void __launch_bounds__(kThreads) k_box_h(BoxArgs a) {
+__global__ void __launch_bounds__(kThreads, 3) k_box_h(BoxArgs a) {
   using B = FastLayout<MODE, H>;
   if (a.stop != nullptr && *(volatile const int*)a.stop != 0) return;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -84,11 +92,14 @@ __global__ void __launch_bounds__(kThreads) k_box_h(BoxArgs a) {
   long long* xb2 = reinterpret_cast<long long*>(smem + B::o_xb2);
   int* s1z = reinterpret_cast<int*>(smem + B::o_s1z);
   float* dring = reinterpret_cast<float*>(smem + B::o_dring);
-  float* mring = reinterpret_cast<float*>(smem + B::o_mring);
+  float* mring = reinterpret_cast<float*>(smem + B::o_mring);   // v on the F region (3 planes if EXT)
+  float* zsf = reinterpret_cast<float*>(smem + B::o_zsf);       // zs on the F region, centre plane
+  float* ro = reinterpret_cast<float*>(smem + B::o_ro);         // r on the tile, force plane
+  constexpr int NMR = B::EXT ? 3 : 1;
 
   const int tid = threadIdx.x;
   const int nx = a.nx, ny = a.ny, nz = a.nz;
-  const int plane = nx * ny;                 // N < 2^31 is checked on the host
+  const int plane = nx * ny;                 // 3 N < 2^31 is checked on the host
   const int N = plane * nz;
   const int x0 = blockIdx.x * B::TX, y0 = blockIdx.y * B::TY;
   const int z0 = blockIdx.z * a.zlen;
@@ -96,7 +107,8 @@ __global__ void __launch_bounds__(kThreads) k_box_h(BoxArgs a) {
   const float* __restrict__ src = a.src;
   const float qs = a.qscale, inv_qs = a.inv_qscale, vfl = a.var_floor;
 
-  // ---- this thread's W columns: plane offset (or -1 outside) and z sums ------
+  // ---- per-thread element maps (fixed for the whole march) -------------------
+  // W columns: plane offset (or -1 outside) and smem index; running z sums
   int goff[B::K1], sidx[B::K1], s1r[B::K1];
   long long s2r[B::K1];
 #pragma unroll
@@ -113,6 +125,26 @@ __global__ void __launch_bounds__(kThreads) k_box_h(BoxArgs a) {
       if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) goff[k] = gy * nx + gx;
     }
   }
+  // F elements: plane offset (or -1)
+  int foff[B::KF];
+#pragma unroll
+  for (int k = 0; k < B::KF; ++k) {
+    const int e = tid + k * kThreads;
+    foff[k] = -1;
+    if (e < B::FN) {
+      const int fy = e / B::FX, fx = e - fy * B::FX;
+      const int gx = x0 - B::EXT + fx, gy = y0 - B::EXT + fy;
+      if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) foff[k] = gy * nx + gx;
+    }
+  }
+  // tile elements: plane offset (or -1)
+  int ooff[B::KO];
+#pragma unroll
+  for (int k = 0; k < B::KO; ++k) {
+    const int e = tid + k * kThreads;
+    const int oy = e / B::TX, ox = e - oy * B::TX;
+    ooff[k] = (e < B::TN && x0 + ox < nx && y0 + oy < ny) ? (y0 + oy) * nx + x0 + ox : -1;
+  }
 
   const int zc_lo = max(0, z0 - B::EXT);
   const int zc_hi = min(nz - 1, z1 - 1 + B::EXT);
@@ -121,7 +153,11 @@ __global__ void __launch_bounds__(kThreads) k_box_h(BoxArgs a) {
   float acc0 = 0.0f, acc1 = 0.0f;
 
   for (int zi = zi0; zi <= zi1; ++zi) {
-    // ---- stage 1: z sliding sums (registers), published for the x pass -------
+    const int zc = zi - H;                   // centre plane of the patch window
+    const bool do2 = zc >= zc_lo && zc <= zc_hi;
+    const int zf = zc - 1;                   // plane whose force is computed this step
+    const bool do3 = (MODE == kModeIterate) && do2 && zf >= z0 && zf < z1;
+    // ---- stage 1: every global load of this step, issued together ------------
     const int zold = zi - (2 * H + 1);
     const bool has_new = zi < nz, has_old = zold >= zi0;
     const float* pn = src + (size_t)zi * plane;
@@ -132,6 +168,25 @@ __global__ void __launch_bounds__(kThreads) k_box_h(BoxArgs a) {
       vn[k] = (has_new && goff[k] >= 0) ? __ldg(pn + goff[k]) : 0.0f;
       vo[k] = (has_old && goff[k] >= 0) ? __ldg(po + goff[k]) : 0.0f;
     }
+    float fm[B::KF], fz[B::KF];
+    if (do2) {
+      const float* pc = src + (size_t)zc * plane;
+      const float* pz = a.zs + (size_t)zc * plane;
+#pragma unroll
+      for (int k = 0; k < B::KF; ++k) {
+        fm[k] = foff[k] >= 0 ? __ldg(pc + foff[k]) : 0.0f;
+        fz[k] = (MODE != kModeStatic && foff[k] >= 0) ? __ldg(pz + foff[k]) : 0.0f;
+      }
+    }
+    float rv[3][B::KO];
+    if (do3) {
+      const float* pr = a.r + (size_t)zf * plane;
+#pragma unroll
+      for (int k = 0; k < B::KO; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) rv[c][k] = ooff[k] >= 0 ? __ldg(pr + (size_t)c * N + ooff[k]) : 0.0f;
+    }
+    // z sliding sums
 #pragma unroll
     for (int k = 0; k < B::K1; ++k) {
       if (sidx[k] < 0) continue;
@@ -141,10 +196,25 @@ __global__ void __launch_bounds__(kThreads) k_box_h(BoxArgs a) {
       s1z[sidx[k]] = s1r[k];
       s2z[sidx[k]] = s2r[k];
     }
+    if (do2) {
+      float* mr = mring + (zc % NMR) * B::FN;
+#pragma unroll
+      for (int k = 0; k < B::KF; ++k) {
+        const int e = tid + k * kThreads;
+        if (e < B::FN) {
+          mr[e] = fm[k];
+          if (MODE != kModeStatic) zsf[e] = fz[k];
+        }
+      }
+    }
+    if (do3) {
+#pragma unroll
+      for (int k = 0; k < B::KO; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) ro[c * B::TN + tid + k * kThreads] = rv[c][k];
+    }
     __syncthreads();
-
-    const int zc = zi - H;
-    if (zc < zc_lo || zc > zc_hi) continue;   // uniform
+    if (!do2) continue;                      // uniform
 
     // ---- stage 2a: x window sums, sliding, one task per (segment, row) ---------
     for (int t = tid; t < B::NSX * B::WY; t += kThreads) {
@@ -175,11 +245,10 @@ __global__ void __launch_bounds__(kThreads) k_box_h(BoxArgs a) {
     __syncthreads();
 
     // ---- stage 2b: y window sums, sliding; moments and correction --------------
-    const int zslot = zc % 3;
     const bool zin = zc >= H && zc < nz - H;
     const int nzc = box_count(zc, nz, H);
     const bool out_plane = zc >= z0 && zc < z1;
-    const float* zplane = src + (size_t)zc * plane;
+    const float* mr = mring + (zc % NMR) * B::FN;
     for (int t = tid; t < B::NSY * B::FX; t += kThreads) {
       const int sy = t / B::FX, fx = t - sy * B::FX;
       const int gx = x0 - B::EXT + fx;
@@ -212,21 +281,19 @@ __global__ void __launch_bounds__(kThreads) k_box_h(BoxArgs a) {
           n = nxc * box_count(gy, ny, H) * nzc;
           inv_n = 1.0f / (float)n;
         }
-        const int g = gy * nx + gx;
-        const float vc = __ldg(zplane + g);
+        const int fi = fy * B::FX + fx;
+        const float vc = mr[fi];
         float dc, sg_;
         moments_fast(b1, b2, n, inv_n, __float2int_rn(vc * qs), inv_qs, vfl, dc, sg_);
-        const size_t gz = (size_t)zc * plane + g;
+        const size_t gz = (size_t)zc * plane + (size_t)gy * nx + gx;
         if (MODE == kModeStatic) {
           a.out[gz] = sg_ > 0.0f ? -dc / sg_ : 0.0f;   // (I_s - E(S)) / STD(S)
           continue;
         }
-        const float zsv = __ldg(a.zs + gz);
+        const float zsv = zsf[fi];
         const float d = fmaf(zsv, sg_, dc);               // I'_s - I_m^(k)
         if (MODE == kModeIterate) {
-          const int fi = zslot * B::FN + fy * B::FX + fx;
-          dring[fi] = d;
-          mring[fi] = vc;
+          dring[(zc % 3) * B::FN + fi] = d;
           if (a.f_tap && out_plane && fx >= 1 && fx <= B::TX && fy >= 1 && fy <= B::TY) a.f_tap[gz] = d;
         } else if (MODE == kModeCorrected) {
           a.out[gz] = vc + d;
@@ -243,7 +310,7 @@ __global__ void __launch_bounds__(kThreads) k_box_h(BoxArgs a) {
         }
       }
     }
-    if (MODE != kModeIterate) continue;
+    if (MODE == kModeIterate) {
     __syncthreads();
 
     // ---- stage 3: demons force (Eq. 1) and update ------------------------------
@@ -257,11 +324,11 @@ __global__ void __launch_bounds__(kThreads) k_box_h(BoxArgs a) {
       const float* mp = mring + so * B::FN;
       const bool zlo = zo > 0, zhi = zo < nz - 1;
 #pragma unroll
-      for (int i = 0; i < (B::TX * B::TY) / kThreads; ++i) {
+      for (int i = 0; i < B::KO; ++i) {
         const int o = tid + i * kThreads;
+        if (ooff[i] < 0) continue;
         const int oy = o / B::TX, ox = o - oy * B::TX;
         const int gx = x0 + ox, gy = y0 + oy;
-        if (gx >= nx || gy >= ny) continue;
         const int fi = (oy + 1) * B::FX + (ox + 1);
         const float d0 = dp[fi], m0 = mp[fi];
         const float gdx = diff1(dp[fi - 1], d0, dp[fi + 1], gx, nx);
@@ -285,8 +352,17 @@ __global__ void __launch_bounds__(kThreads) k_box_h(BoxArgs a) {
           dry = fmaf(s2, gmy, dry);
           drz = fmaf(s2, gmz, drz);
         }
-        const size_t g = (size_t)zo * plane + (size_t)gy * nx + gx;
-        const float rx = __ldg(a.r + g), ry = __ldg(a.r + (size_t)N + g), rz = __ldg(a.r + 2 * (size_t)N + g);
+        const size_t g = (size_t)zo * plane + ooff[i];
+        float rx, ry, rz;
+        if (back == 1) {                       // staged in stage 1
+          rx = ro[o];
+          ry = ro[B::TN + o];
+          rz = ro[2 * B::TN + o];
+        } else {                               // last plane of the volume only
+          rx = __ldg(a.r + g);
+          ry = __ldg(a.r + (size_t)N + g);
+          rz = __ldg(a.r + 2 * (size_t)N + g);
+        }
         a.out[g] = rx + drx;
         a.out[(size_t)N + g] = ry + dry;
         a.out[2 * (size_t)N + g] = rz + drz;
@@ -294,8 +370,10 @@ __global__ void __launch_bounds__(kThreads) k_box_h(BoxArgs a) {
         acc1 += sqrt_approx(fmaf(rx, rx, fmaf(ry, ry, rz * rz)));
       }
     }
-    // stage 2b of the next plane rewrites a ring slot read here only after two
-    // more barriers (after its stage 1 and stage 2a)
+    }
+    // the next step's stage 1 rewrites the staged planes (mring, zsf, ro) and the
+    // next stage 2b the d ring: everything read above must be consumed first
+    __syncthreads();
   }
 
   if (MODE == kModeIterate || MODE == kModeSsdLoss) {
@@ -335,6 +413,10 @@ cudaError_t launch_fast(const BoxArgs& a, const BoxPlan& p, cudaStream_t s) {
   if (!set[dev]) {
     e = cudaFuncSetAttribute(k_box_h<MODE, H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)FastLayout<MODE, H>::bytes);
+    if (e != cudaSuccess) return e;
+    // prefer the largest shared-memory carveout so that several CTAs fit per SM
+    e = cudaFuncSetAttribute(k_box_h<MODE, H>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     set[dev] = 1;
   }

@@ -13,6 +13,7 @@
 #include <cmath>
 
 #include "internal.cuh"
+#include "warp_dev.cuh"
 
 namespace disc {
 
@@ -132,187 +133,276 @@ __global__ void __launch_bounds__(kThreads) k_gauss(GaussArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Register-queue form for radius R (compile time).  A CTA owns a 32 x 16
-// tile; each thread owns two x-adjacent voxels of one row and all three field
-// components.  Per plane: stage the plane (tile + R halo) in shared memory,
-// filter along x into shared memory, then each thread filters its own column
-// along y and adds the result, times each z tap, into a queue of 2R+1 pending
-// output planes held in registers (float2, packed FFMA2).  The queue slot of
-// output plane z is z mod (2R+1), made static by unrolling the plane loop by
-// 2R+1.  The next plane's loads are issued before the y/z work of the
-// current one, so their latency overlaps the arithmetic.
+// Split form for radius R = 1..8 (compile time), two streaming kernels:
+//  k_gauss_xy: one CTA per 32 x 16 tile of one plane filters u along x and
+//    then y in shared memory and writes the plane of t = G_y * G_x * u;
+//  k_gauss_z: one thread per (x, y) column and z chunk filters t along z with
+//    a queue of 2R+1 pending output planes in registers (slots made static by
+//    unrolling the plane loop by 2R+1), writes r, and optionally evaluates the
+//    warped moving image m = I_m(x + r(x)) for the next iteration while r is
+//    still in registers (Algorithm A1: "update the moving image").
+// The x and y field components are processed as float2 pairs (packed FFMA2),
+// the z component as a scalar.
 // ---------------------------------------------------------------------------
-constexpr int kQX = 32;
-constexpr int kQY = 16;
+constexpr int kSX = 32;        // xy tile
+constexpr int kSY = 32;
+constexpr int kZThreads = 128; // z kernel: threads along x
+constexpr int kBX = 4;         // x outputs per x-filter task
+constexpr int kBY = 4;         // y outputs per thread in the y filter
 
 template <int R>
-struct QLayout {
-  static constexpr int IX = kQX + 2 * R;
-  static constexpr int IY = kQY + 2 * R;
-  static constexpr int KZ = 2 * R + 1;
-  static constexpr int INP = IX * IY;          // floats per component plane
-  static constexpr int XCP = (kQX / 2) * IY;   // float2 per component plane
-  static constexpr int NLOAD = (3 * INP + kThreads - 1) / kThreads;
-  static constexpr size_t o_ring = 0;
-  static constexpr size_t o_xc = o_ring + 8 * (size_t)KZ * 3 * kThreads;
-  static constexpr size_t o_in = o_xc + 8 * 3 * (size_t)XCP;
-  static constexpr size_t bytes = o_in + 4 * 3 * (size_t)INP;
+struct XYLayout {
+  static constexpr int IX = kSX + 2 * R;
+  static constexpr int IY = kSY + 2 * R;
+  static constexpr int IXP = IX + 1;                   // row stride (odd)
+  static constexpr int NXT = IY * (kSX / kBX);         // x-filter tasks (row, x quad)
+  static constexpr size_t o_in2 = 0;                   // float2 [IY][IXP]  (ux, uy)
+  static constexpr size_t o_inz = o_in2 + 8 * (size_t)IY * IXP;   // float [IY][IXP]
+  static constexpr size_t o_x2 = o_inz + 4 * (size_t)IY * IXP;    // float2 [IY][kSX]
+  static constexpr size_t o_xz = o_x2 + 8 * (size_t)IY * kSX;     // float [IY][kSX]
+  static constexpr size_t bytes = o_xz + 4 * (size_t)IY * kSX;
 };
 
 template <int R>
-__global__ void __launch_bounds__(kThreads) k_gauss_q(GaussArgs a) {
-  using Q = QLayout<R>;
+__global__ void __launch_bounds__(kThreads) k_gauss_xy(GaussArgs a) {
+  using X = XYLayout<R>;
   if (a.stop != nullptr && *(volatile const int*)a.stop != 0) return;
   extern __shared__ __align__(16) unsigned char smem[];
-  float* in = reinterpret_cast<float*>(smem + Q::o_in);
-  float2* xc = reinterpret_cast<float2*>(smem + Q::o_xc);
-  float2* ring = reinterpret_cast<float2*>(smem + Q::o_ring);   // [KZ][3][threads], thread-private
-  __shared__ float w[2 * R + 1];
-  __shared__ float nrm_x[kQX], nrm_y[kQY];
+  float2* in2 = reinterpret_cast<float2*>(smem + X::o_in2);
+  float* inz = reinterpret_cast<float*>(smem + X::o_inz);
+  float2* x2 = reinterpret_cast<float2*>(smem + X::o_x2);
+  float* xz = reinterpret_cast<float*>(smem + X::o_xz);
+  __shared__ float nrm_x[kSX], nrm_y[kSY];
   const int tid = threadIdx.x;
-  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const int nx = a.nx, ny = a.ny;
   const size_t plane = (size_t)nx * ny;
-  const size_t N = plane * nz;
-  const int x0 = blockIdx.x * kQX, y0 = blockIdx.y * kQY;
-  const int z0 = blockIdx.z * a.zlen;
-  const int z1 = min(nz, z0 + a.zlen);
-  if (tid < 2 * R + 1) w[tid] = a.w[tid];
+  const size_t N = plane * a.nz;
+  const int x0 = blockIdx.x * kSX, y0 = blockIdx.y * kSY, z = blockIdx.z;
+  float w[2 * R + 1];
 #pragma unroll
-  for (int j = 0; j < Q::KZ * 3; ++j) ring[j * kThreads + tid] = make_float2(0.0f, 0.0f);
+  for (int k = 0; k <= 2 * R; ++k) w[k] = a.w[k];
+  const bool border = x0 - R < 0 || x0 + kSX + R > nx || y0 - R < 0 || y0 + kSY + R > ny;
+  if (border) {
+    if (tid < kSX) nrm_x[tid] = tap_norm(a.w, R, x0 + tid, nx);
+    if (tid >= 64 && tid < 64 + kSY) nrm_y[tid - 64] = tap_norm(a.w, R, y0 + tid - 64, ny);
+  }
+  // stage the plane with its halo (zeros outside the volume)
+  const float* ux = a.u + (size_t)z * plane;
+  for (int e = tid; e < X::IY * X::IX; e += kThreads) {
+    const int iy = e / X::IX, ix = e - iy * X::IX;
+    const int gx = x0 - R + ix, gy = y0 - R + iy;
+    float vx = 0.0f, vy = 0.0f, vz = 0.0f;
+    if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
+      const size_t g = (size_t)gy * nx + gx;
+      vx = __ldg(ux + g);
+      vy = __ldg(ux + N + g);
+      vz = __ldg(ux + 2 * N + g);
+    }
+    in2[iy * X::IXP + ix] = make_float2(vx, vy);
+    inz[iy * X::IXP + ix] = vz;
+  }
   __syncthreads();
-  if (tid < kQX) nrm_x[tid] = tap_norm(w, R, x0 + tid, nx);
-  if (tid >= 64 && tid < 64 + kQY) nrm_y[tid - 64] = tap_norm(w, R, y0 + tid - 64, ny);
-
-  // this thread's output pair
-  const int px = tid & 15, oy = tid >> 4;
-  const int gx = x0 + 2 * px, gy = y0 + oy;
-  const bool own0 = gx < nx && gy < ny, own1 = gx + 1 < nx && gy < ny;
-
-  // staged-plane element e -> global offset c N + Y nx + X (or -1 outside)
-  int goff[Q::NLOAD];
+  // x filter: each task computes kBX adjacent outputs of one row from a window
+  // of kBX + 2R inputs held in registers
+  for (int t = tid; t < X::NXT; t += kThreads) {
+    const int iy = t / (kSX / kBX), j = t - iy * (kSX / kBX);
+    const float2* r2 = in2 + iy * X::IXP + kBX * j;
+    const float* rz = inz + iy * X::IXP + kBX * j;
+    float2 acc[kBX];
+    float accz[kBX];
 #pragma unroll
-  for (int k = 0; k < Q::NLOAD; ++k) {
-    const int e = tid + k * kThreads;
-    goff[k] = -1;
-    if (e < 3 * Q::INP) {
-      const int c = e / Q::INP, rem = e - c * Q::INP;
-      const int iy = rem / Q::IX, ix = rem - iy * Q::IX;
-      const int X = x0 - R + ix, Y = y0 - R + iy;
-      if (X >= 0 && X < nx && Y >= 0 && Y < ny) goff[k] = (int)((size_t)c * N + (size_t)Y * nx + X);
+    for (int b = 0; b < kBX; ++b) {
+      acc[b] = make_float2(0.0f, 0.0f);
+      accz[b] = 0.0f;
+    }
+#pragma unroll
+    for (int i = 0; i < kBX + 2 * R; ++i) {
+      const float2 v = r2[i];
+      const float vzz = rz[i];
+#pragma unroll
+      for (int b = 0; b < kBX; ++b) {
+        const int k = i - b;                  // tap index of input i for output b
+        if (k >= 0 && k <= 2 * R) {
+          acc[b] = __ffma2_rn(make_float2(w[k], w[k]), v, acc[b]);
+          accz[b] = fmaf(w[k], vzz, accz[b]);
+        }
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < kBX; ++b) {
+      if (border) {
+        const float n = nrm_x[kBX * j + b];
+        if (n != 1.0f) {
+          acc[b].x = acc[b].x / n;
+          acc[b].y = acc[b].y / n;
+          accz[b] = accz[b] / n;
+        }
+      }
+      x2[iy * kSX + kBX * j + b] = acc[b];
+      xz[iy * kSX + kBX * j + b] = accz[b];
     }
   }
-  float pre[Q::NLOAD];
-  const int zs = max(0, z0 - R);
-  const int ze = z1 - 1 + R;                 // last plane that still feeds an output
-  auto prefetch = [&](int z) {
-#pragma unroll
-    for (int k = 0; k < Q::NLOAD; ++k)
-      pre[k] = (z < nz && goff[k] >= 0) ? __ldg(a.u + (size_t)goff[k] + (size_t)z * plane) : 0.0f;
-  };
-
-  prefetch(zs);
   __syncthreads();
-  const float nyv = nrm_y[oy];
-  for (int zi = zs; zi <= ze; ++zi) {
-    const bool live = zi < nz;               // uniform
-    float2* slot = ring + (zi % Q::KZ) * 3 * kThreads + tid;
-    if (live) {
-      __syncthreads();                       // the previous plane's y filter is done with xc
+  // y filter: each thread computes kBY adjacent rows of one column
+  {
+    const int ox = tid & (kSX - 1), jy = tid >> 5;      // 32 columns x 8 row groups
+    const int gx = x0 + ox;
+    const float2* c2 = x2 + kBY * jy * kSX + ox;
+    const float* cz = xz + kBY * jy * kSX + ox;
+    float2 acc[kBY];
+    float accz[kBY];
 #pragma unroll
-      for (int k = 0; k < Q::NLOAD; ++k) {
-        const int e = tid + k * kThreads;
-        if (e < 3 * Q::INP) in[e] = pre[k];
-      }
-      __syncthreads();
-      // x filter: (component, row, pair) tasks
-      for (int t = tid; t < 3 * Q::XCP; t += kThreads) {
-        const int c = t / Q::XCP, rem = t - c * Q::XCP;
-        const int iy = rem / (kQX / 2), jx = rem - iy * (kQX / 2);
-        const float* row = in + c * Q::INP + iy * Q::IX + 2 * jx;
-        float2 sacc = make_float2(0.0f, 0.0f);
-#pragma unroll
-        for (int k = 0; k <= 2 * R; ++k)
-          sacc = __ffma2_rn(make_float2(w[k], w[k]), make_float2(row[k], row[k + 1]), sacc);
-        const float n0 = nrm_x[2 * jx], n1 = nrm_x[2 * jx + 1];
-        if (n0 != 1.0f) sacc.x = sacc.x / n0;
-        if (n1 != 1.0f) sacc.y = sacc.y / n1;
-        xc[t] = sacc;
-      }
-      __syncthreads();
-      if (zi + 1 <= ze) prefetch(zi + 1);    // overlaps the y/z work below
-      // y filter of this thread's pair into its private ring slot
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const float2* col = xc + c * Q::XCP + oy * (kQX / 2) + px;
-        float2 t2 = make_float2(0.0f, 0.0f);
-#pragma unroll
-        for (int k = 0; k <= 2 * R; ++k) t2 = __ffma2_rn(make_float2(w[k], w[k]), col[k * (kQX / 2)], t2);
-        if (nyv != 1.0f) {
-          t2.x = t2.x / nyv;
-          t2.y = t2.y / nyv;
-        }
-        slot[c * kThreads] = t2;
-      }
-    } else {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) slot[c * kThreads] = make_float2(0.0f, 0.0f);
-      if (zi + 1 <= ze) prefetch(zi + 1);
+    for (int b = 0; b < kBY; ++b) {
+      acc[b] = make_float2(0.0f, 0.0f);
+      accz[b] = 0.0f;
     }
-    // z filter for output plane zo = zi - R (planes outside the volume hold 0)
-    const int zo = zi - R;
-    if (zo >= z0 && zo < z1) {
-      float2 o[3] = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
 #pragma unroll
-      for (int k = -R; k <= R; ++k) {
-        const float2* sk = ring + ((zo + k + Q::KZ) % Q::KZ) * 3 * kThreads + tid;
-        const float2 wk = make_float2(w[k + R], w[k + R]);
+    for (int i = 0; i < kBY + 2 * R; ++i) {
+      const float2 v = c2[i * kSX];
+      const float vzz = cz[i * kSX];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) o[c] = __ffma2_rn(wk, sk[c * kThreads], o[c]);
-      }
-      const float nz_ = tap_norm(w, R, zo, nz);
-      const size_t g = (size_t)zo * plane + (size_t)gy * nx + gx;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        float2 oc = o[c];
-        if (nz_ != 1.0f) {
-          oc.x = oc.x / nz_;
-          oc.y = oc.y / nz_;
+      for (int b = 0; b < kBY; ++b) {
+        const int k = i - b;
+        if (k >= 0 && k <= 2 * R) {
+          acc[b] = __ffma2_rn(make_float2(w[k], w[k]), v, acc[b]);
+          accz[b] = fmaf(w[k], vzz, accz[b]);
         }
-        if (own0) a.r[c * N + g] = oc.x;
-        if (own1) a.r[c * N + g + 1] = oc.y;
+      }
+    }
+    if (gx < nx) {
+      float* t = a.r + (size_t)z * plane;
+#pragma unroll
+      for (int b = 0; b < kBY; ++b) {
+        const int gy = y0 + kBY * jy + b;
+        if (gy >= ny) break;
+        if (border) {
+          const float n = nrm_y[kBY * jy + b];
+          if (n != 1.0f) {
+            acc[b].x = acc[b].x / n;
+            acc[b].y = acc[b].y / n;
+            accz[b] = accz[b] / n;
+          }
+        }
+        const size_t g = (size_t)gy * nx + gx;
+        t[g] = acc[b].x;
+        t[N + g] = acc[b].y;
+        t[2 * N + g] = accz[b];
       }
     }
   }
 }
 
+// z pass with a register queue; WARP also evaluates m = I_m(x + r(x)).
+template <int R, bool WARP>
+__global__ void __launch_bounds__(kZThreads) k_gauss_z(GaussArgs a) {
+  constexpr int KZ = 2 * R + 1;
+  if (a.stop != nullptr && *(volatile const int*)a.stop != 0) return;
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const int x = blockIdx.x * kZThreads + threadIdx.x, y = blockIdx.y;
+  if (x >= nx) return;
+  const size_t plane = (size_t)nx * ny;
+  const size_t N = plane * nz;
+  const int z0 = blockIdx.z * a.zlen;
+  const int z1 = min(nz, z0 + a.zlen);
+  float w[KZ];
+#pragma unroll
+  for (int k = 0; k < KZ; ++k) w[k] = a.w[k];
+  const size_t col = (size_t)y * nx + x;
+  const float* t = a.u + col;       // t = G_y G_x u, [3][N]
+  float2 q2[KZ];                    // pending outputs, (x, y) components
+  float qz[KZ];
+#pragma unroll
+  for (int k = 0; k < KZ; ++k) {
+    q2[k] = make_float2(0.0f, 0.0f);
+    qz[k] = 0.0f;
+  }
+  const int zs = max(0, z0 - R);
+  const int ze = z1 - 1 + R;
+  const int zb0 = zs - (zs % KZ);
+  for (int zb = zb0; zb <= ze; zb += KZ) {
+    // issue the loads of the whole block of 2R+1 planes first (memory-level parallelism)
+    float2 v2[KZ];
+    float vz[KZ];
+#pragma unroll
+    for (int j = 0; j < KZ; ++j) {
+      const int zi = zb + j;
+      const bool ok = zi >= zs && zi <= ze && zi < nz;
+      const size_t g = (size_t)(ok ? zi : 0) * plane;
+      v2[j] = ok ? make_float2(__ldg(t + g), __ldg(t + N + g)) : make_float2(0.0f, 0.0f);
+      vz[j] = ok ? __ldg(t + 2 * N + g) : 0.0f;
+    }
+#pragma unroll
+    for (int j = 0; j < KZ; ++j) {
+      const int zi = zb + j;                  // zi mod KZ == j
+      if (zi < zs || zi > ze) continue;
+      // plane zi feeds output plane zi - k with tap w[R + k] (zero planes add nothing)
+#pragma unroll
+      for (int k = -R; k <= R; ++k) {
+        const int slot = ((j - k) % KZ + KZ) % KZ;
+        q2[slot] = __ffma2_rn(make_float2(w[R + k], w[R + k]), v2[j], q2[slot]);
+        qz[slot] = fmaf(w[R + k], vz[j], qz[slot]);
+      }
+      const int zo = zi - R;
+      const int so = ((j - R) % KZ + KZ) % KZ;
+      if (zo >= z0 && zo < z1) {
+        float2 o2 = q2[so];
+        float oz = qz[so];
+        const float nrm = tap_norm(a.w, R, zo, nz);
+        if (nrm != 1.0f) {
+          o2.x = o2.x / nrm;
+          o2.y = o2.y / nrm;
+          oz = oz / nrm;
+        }
+        const size_t g = (size_t)zo * plane + col;
+        a.r[g] = o2.x;
+        a.r[N + g] = o2.y;
+        a.r[2 * N + g] = oz;
+        if (WARP) a.m[g] = warp_at(a.Im, x, y, zo, o2.x, o2.y, oz, nx, ny, nz);
+      }
+      q2[so] = make_float2(0.0f, 0.0f);
+      qz[so] = 0.0f;
+    }
+  }
+}
+
 template <int R>
-cudaError_t launch_q(const GaussArgs& a, const GaussPlan& p, cudaStream_t s) {
+cudaError_t launch_split(const GaussArgs& a, const GaussPlan& p, cudaStream_t s) {
   static int set[64] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (!set[dev]) {
-    e = cudaFuncSetAttribute(k_gauss_q<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+    e = cudaFuncSetAttribute(k_gauss_xy<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)XYLayout<R>::bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_gauss_xy<R>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     set[dev] = 1;
   }
-  k_gauss_q<R><<<p.grid, kThreads, p.smem, s>>>(a);
+  // xy: u -> t
+  GaussArgs xy = a;
+  xy.r = a.t;
+  dim3 gxy((a.nx + kSX - 1) / kSX, (a.ny + kSY - 1) / kSY, a.nz);
+  k_gauss_xy<R><<<gxy, kThreads, XYLayout<R>::bytes, s>>>(xy);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // z: t -> r (and m)
+  GaussArgs zz = a;
+  zz.u = a.t;
+  zz.zlen = p.zlen;
+  dim3 gz((a.nx + kZThreads - 1) / kZThreads, a.ny, (a.nz + p.zlen - 1) / p.zlen);
+  if (a.m != nullptr)
+    k_gauss_z<R, true><<<gz, kZThreads, 0, s>>>(zz);
+  else
+    k_gauss_z<R, false><<<gz, kZThreads, 0, s>>>(zz);
   return cudaGetLastError();
 }
 
-size_t q_smem(int R) {
-  switch (R) {
-#define QCASE(RR) case RR: return QLayout<RR>::bytes;
-    QCASE(1) QCASE(2) QCASE(3) QCASE(4) QCASE(5) QCASE(6) QCASE(7) QCASE(8)
-#undef QCASE
-    default: return 0;
-  }
-}
-
-cudaError_t launch_q_any(const GaussArgs& a, const GaussPlan& p, cudaStream_t s) {
+cudaError_t launch_split_any(const GaussArgs& a, const GaussPlan& p, cudaStream_t s) {
   switch (a.R) {
-#define QCASE(RR) case RR: return launch_q<RR>(a, p, s);
+#define QCASE(RR) case RR: return launch_split<RR>(a, p, s);
     QCASE(1) QCASE(2) QCASE(3) QCASE(4) QCASE(5) QCASE(6) QCASE(7) QCASE(8)
 #undef QCASE
     default: return cudaErrorInvalidValue;
@@ -337,21 +427,18 @@ void gauss_taps(float sigma, int R, float* w) {
 
 GaussPlan gauss_plan(int nx, int ny, int nz, int R, int num_sms) {
   GaussPlan p;
-  p.queue = R >= 1 && R <= 8 && 3.0 * nx * ny * nz < 2147483647.0;
+  p.queue = R >= 1 && R <= 8 && ny <= 65535 && nz <= 65535;
   if (p.queue) {
-    p.smem = q_smem(R);
-    const int gx = (nx + kQX - 1) / kQX, gy = (ny + kQY - 1) / kQY;
-    int per_sm = (int)((228 * 1024) / (p.smem + 1024));
-    if (per_sm < 1) per_sm = 1;
-    if (per_sm > 3) per_sm = 3;
-    const long long slots = (long long)num_sms * per_sm;
-    long long chunks = (slots + (long long)gx * gy - 1) / ((long long)gx * gy);
+    p.smem = 0;
+    // z kernel: chunks long enough to amortise the 2R halo planes, enough CTAs
+    const long long cols = (long long)((nx + kZThreads - 1) / kZThreads) * ny;
+    long long chunks = (8LL * num_sms + cols - 1) / cols;
     if (chunks < 1) chunks = 1;
-    long long max_chunks = (nz + 3) / 4;
+    long long max_chunks = (nz + 15) / 16;   // at least 16 planes per chunk
     if (max_chunks < 1) max_chunks = 1;
     if (chunks > max_chunks) chunks = max_chunks;
     p.zlen = (int)((nz + chunks - 1) / chunks);
-    p.grid = dim3(gx, gy, (nz + p.zlen - 1) / p.zlen);
+    p.grid = dim3(1, 1, 1);
     return p;
   }
   const GaussLayout L = gauss_layout(R);
@@ -380,7 +467,7 @@ cudaError_t gauss_launch(const GaussArgs& a, const GaussPlan& p, cudaStream_t s)
   if (p.grid.x == 0) return cudaErrorInvalidConfiguration;
   GaussArgs b = a;
   b.zlen = p.zlen;
-  if (p.queue) return launch_q_any(b, p, s);
+  if (p.queue) return launch_split_any(b, p, s);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;

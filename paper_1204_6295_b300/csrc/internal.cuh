@@ -81,8 +81,11 @@ cudaError_t launch_warp(const float* Im, const float* r, float* m, int nx, int n
 // Gaussian pass, gauss.cu
 // ----------------------------------------------------------------------------
 struct GaussArgs {
-  const float* u;       // [3][N]
-  float* r;             // [3][N]
+  const float* u;       // [3][N] input field
+  float* r;             // [3][N] smoothed field
+  float* t;             // [3][N] scratch: the xy-filtered field (split kernels)
+  const float* Im;      // moving image, for the fused warp (may be NULL)
+  float* m;             // if non-NULL: m = I_m(x + r(x)) is written too
   const int* stop;
   int nx, ny, nz;
   int R;
