@@ -440,6 +440,14 @@ cudaError_t launch_fast_h(const BoxArgs& a, const BoxPlan& p, cudaStream_t s) {
 
 template <int MODE, int H>
 int occ_one(size_t smem) {
+  // the opt-in shared memory size and carveout change the answer: set them first
+  if (cudaFuncSetAttribute(k_box_h<MODE, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_box_h<MODE, H>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_box_h<MODE, H>, kThreads, smem) != cudaSuccess) {
     cudaGetLastError();

@@ -383,9 +383,10 @@ BoxPlan box_plan(int mode, int nx, int ny, int nz, int hx, int hy, int hz, int n
   const int gx = (nx + kTX - 1) / kTX, gy = (ny + kTY - 1) / kTY;
   if (per_sm < 1) per_sm = 1;
   if (per_sm > 8) per_sm = 8;                 // 8 CTAs of 256 threads fill an SM
-  // one wave of resident CTAs: fewer, longer z chunks amortise the z halo
+  // at most one wave of resident CTAs: fewer, longer z chunks amortise the z
+  // halo, and a partial second wave would double the time of the first
   const long long slots = (long long)num_sms * per_sm;
-  long long chunks = (slots + (long long)gx * gy - 1) / ((long long)gx * gy);
+  long long chunks = slots / ((long long)gx * gy);
   if (chunks < 1) chunks = 1;
   long long max_chunks = (nz + 3) / 4;       // at least 4 output planes per chunk
   if (max_chunks < 1) max_chunks = 1;

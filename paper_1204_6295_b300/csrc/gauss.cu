@@ -186,20 +186,29 @@ __global__ void __launch_bounds__(kThreads) k_gauss_xy(GaussArgs a) {
     if (tid < kSX) nrm_x[tid] = tap_norm(a.w, R, x0 + tid, nx);
     if (tid >= 64 && tid < 64 + kSY) nrm_y[tid - 64] = tap_norm(a.w, R, y0 + tid - 64, ny);
   }
-  // stage the plane with its halo (zeros outside the volume)
+  // stage the plane with its halo (zeros outside the volume): all loads first
+  constexpr int NL = (X::IY * X::IX + kThreads - 1) / kThreads;
   const float* ux = a.u + (size_t)z * plane;
-  for (int e = tid; e < X::IY * X::IX; e += kThreads) {
+  float vx[NL], vy[NL], vz[NL];
+#pragma unroll
+  for (int k = 0; k < NL; ++k) {
+    const int e = tid + k * kThreads;
     const int iy = e / X::IX, ix = e - iy * X::IX;
     const int gx = x0 - R + ix, gy = y0 - R + iy;
-    float vx = 0.0f, vy = 0.0f, vz = 0.0f;
-    if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
-      const size_t g = (size_t)gy * nx + gx;
-      vx = __ldg(ux + g);
-      vy = __ldg(ux + N + g);
-      vz = __ldg(ux + 2 * N + g);
+    const bool ok = e < X::IY * X::IX && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+    const size_t g = ok ? (size_t)gy * nx + gx : 0;
+    vx[k] = ok ? __ldg(ux + g) : 0.0f;
+    vy[k] = ok ? __ldg(ux + N + g) : 0.0f;
+    vz[k] = ok ? __ldg(ux + 2 * N + g) : 0.0f;
+  }
+#pragma unroll
+  for (int k = 0; k < NL; ++k) {
+    const int e = tid + k * kThreads;
+    if (e < X::IY * X::IX) {
+      const int iy = e / X::IX, ix = e - iy * X::IX;
+      in2[iy * X::IXP + ix] = make_float2(vx[k], vy[k]);
+      inz[iy * X::IXP + ix] = vz[k];
     }
-    in2[iy * X::IXP + ix] = make_float2(vx, vy);
-    inz[iy * X::IXP + ix] = vz;
   }
   __syncthreads();
   // x filter: each task computes kBX adjacent outputs of one row from a window
@@ -319,7 +328,10 @@ __global__ void __launch_bounds__(kZThreads) k_gauss_z(GaussArgs a) {
   const int zs = max(0, z0 - R);
   const int ze = z1 - 1 + R;
   const int zb0 = zs - (zs % KZ);
-  for (int zb = zb0; zb <= ze; zb += KZ) {
+  const float* tb = t + (size_t)zb0 * plane;  // plane zb of the block, advanced by KZ planes
+  float* rb = a.r + col + (size_t)(zb0 - R) * plane;   // output plane zb - R
+  const size_t step = (size_t)KZ * plane;
+  for (int zb = zb0; zb <= ze; zb += KZ, tb += step, rb += step) {
     // issue the loads of the whole block of 2R+1 planes first (memory-level parallelism)
     float2 v2[KZ];
     float vz[KZ];
@@ -327,9 +339,9 @@ __global__ void __launch_bounds__(kZThreads) k_gauss_z(GaussArgs a) {
     for (int j = 0; j < KZ; ++j) {
       const int zi = zb + j;
       const bool ok = zi >= zs && zi <= ze && zi < nz;
-      const size_t g = (size_t)(ok ? zi : 0) * plane;
-      v2[j] = ok ? make_float2(__ldg(t + g), __ldg(t + N + g)) : make_float2(0.0f, 0.0f);
-      vz[j] = ok ? __ldg(t + 2 * N + g) : 0.0f;
+      const float* tp = tb + (size_t)j * plane;
+      v2[j] = ok ? make_float2(__ldg(tp), __ldg(tp + N)) : make_float2(0.0f, 0.0f);
+      vz[j] = ok ? __ldg(tp + 2 * N) : 0.0f;
     }
 #pragma unroll
     for (int j = 0; j < KZ; ++j) {
@@ -353,11 +365,11 @@ __global__ void __launch_bounds__(kZThreads) k_gauss_z(GaussArgs a) {
           o2.y = o2.y / nrm;
           oz = oz / nrm;
         }
-        const size_t g = (size_t)zo * plane + col;
-        a.r[g] = o2.x;
-        a.r[N + g] = o2.y;
-        a.r[2 * N + g] = oz;
-        if (WARP) a.m[g] = warp_at(a.Im, x, y, zo, o2.x, o2.y, oz, nx, ny, nz);
+        float* rp = rb + (size_t)j * plane;
+        rp[0] = o2.x;
+        rp[N] = o2.y;
+        rp[2 * N] = oz;
+        if (WARP) a.m[(size_t)zo * plane + col] = warp_at(a.Im, x, y, zo, o2.x, o2.y, oz, nx, ny, nz);
       }
       q2[so] = make_float2(0.0f, 0.0f);
       qz[so] = 0.0f;
