@@ -213,6 +213,26 @@ disc_status disc_k_pass_a(const float* Im, const float* zs, const float* r, floa
                           float qscale, float var_floor, int32_t force_mode,
                           void* stream);
 
+/* Allocation-free form of disc_k_pass_a (the paper has no counterpart: this
+ * exists for callers that cannot let a library allocate device memory, such
+ * as applications that own all device memory through their own pool or run
+ * under a fixed memory budget, and hosts that forbid plug-ins from calling
+ * cudaMalloc or the stream-ordered allocator).  Same computation and outputs
+ * as disc_k_pass_a, except that m_out is required (it receives m and is the
+ * working buffer the moment pass reads).  The only scratch, the per-CTA norm
+ * partial sums, lives in a fixed 64 KiB __device__ array inside the library,
+ * present on every device that loads it until the process exits; launches
+ * that would need more than 8192 CTAs (roughly, planes larger than about
+ * 2048 x 2048 voxels) are rejected with DISC_ERR_SHAPE before any work is
+ * queued.  The first call on each device looks up the array's device address
+ * (call it once before any stream capture).  All calls share the array:
+ * calls whose work overlaps on the GPU race on it. */
+disc_status disc_k_pass_a_static(const float* Im, const float* zs, const float* r,
+                                 float* u, float* m_out, float* d_out,
+                                 double* norms_out, int32_t nx, int32_t ny, int32_t nz,
+                                 const int32_t patch[3], float qscale, float var_floor,
+                                 int32_t force_mode, void* stream);
+
 /* Gaussian regularisation (Algorithm A1 step 6, Sec. 2.3 kernel 2): each
  * component of u [3][nz][ny][nx] smoothed separably with taps
  * exp(-i^2 / 2 sigma^2), |i| <= radius (0 = ceil(3 sigma)), weights

@@ -79,6 +79,8 @@ _SIGS = {
     "disc_k_warp": (_st, [_vp, _vp, _vp, _i32, _i32, _i32, _vp]),
     "disc_k_pass_a": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _i32, _i32,
                             ctypes.POINTER(_i32), _f32, _f32, _i32, _vp]),
+    "disc_k_pass_a_static": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _i32, _i32,
+                                   ctypes.POINTER(_i32), _f32, _f32, _i32, _vp]),
     "disc_k_gauss": (_st, [_vp, _vp, _i32, _i32, _i32, _f32, _i32, _vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -299,6 +301,16 @@ def k_pass_a(Im, zs, r, u, patch, qs, m_out=None, d_out=None, norms_out=None, va
     _check(_lib.disc_k_pass_a(_ptr(Im), _ptr(zs), _ptr(r), _ptr(u), _ptr(m_out), _ptr(d_out),
                               _ptr(norms_out), nx, ny, nz, p, float(qs), float(var_floor),
                               int(force_mode), _stream(stream)), "disc_k_pass_a")
+
+
+def k_pass_a_static(Im, zs, r, u, m_out, patch, qs, d_out=None, norms_out=None, var_floor=1e-6,
+                    force_mode=FORCE_THIRION, stream=None):
+    """disc_k_pass_a without device allocation (fixed in-library scratch; m_out required)."""
+    nz, ny, nx = Im.shape
+    p = (_i32 * 3)(*patch)
+    _check(_lib.disc_k_pass_a_static(_ptr(Im), _ptr(zs), _ptr(r), _ptr(u), _ptr(m_out), _ptr(d_out),
+                                     _ptr(norms_out), nx, ny, nz, p, float(qs), float(var_floor),
+                                     int(force_mode), _stream(stream)), "disc_k_pass_a_static")
 
 
 def k_gauss(u, r, sigma, radius=0, stream=None):
