@@ -377,6 +377,32 @@ def run_ours(args, w, rank, world, local_rank):
     return 0
 
 
+def run_profile_once(w):
+    """One launch of each per-iteration kernel at the finest level (for ncu captures).
+
+    Launch order: static patch normalisation, warp, box pass (iteration mode),
+    Gaussian xy pass, Gaussian z pass.
+    """
+    import torch
+    from paper_1204_6295_b300 import disc
+    pair = make_pair(w)
+    nx, ny, nz = w["dims"]
+    ct = torch.from_numpy(pair.ct).cuda()
+    cbct = torch.from_numpy(pair.cbct).cuda()
+    r = torch.from_numpy(pair.u_true).cuda()        # a realistic smooth field
+    patch = w["patch"]
+    qs_s = disc.qscale(float(cbct.abs().max()), patch)
+    qs_m = disc.qscale(float(ct.abs().max()), patch)
+    zs, m = torch.empty_like(ct), torch.empty_like(ct)
+    u, r2 = torch.empty_like(r), torch.empty_like(r)
+    disc.k_static_norm(cbct, zs, patch, qs_s)
+    disc.k_pass_a(ct, zs, r, u, patch, qs_m, m_out=m)
+    disc.k_gauss(u, r2, w["sigma"])
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_once": True, "workload": [nx, ny, nz], "patch": list(patch)}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -385,6 +411,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-once", action="store_true",
+                    help="launch each per-iteration kernel once at the finest level and exit")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus > 0 else 1)))
@@ -392,6 +420,8 @@ def main():
         world = 1
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     w = WORKLOADS[args.workload]
+    if args.profile_once:
+        return run_profile_once(w)
     if args.impl == "reference":
         return run_reference(args, w, rank, world)
     return run_ours(args, w, rank, world, local_rank)
