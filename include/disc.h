@@ -213,6 +213,37 @@ disc_status disc_k_pass_a(const float* Im, const float* zs, const float* r, floa
                           float qscale, float var_floor, int32_t force_mode,
                           void* stream);
 
+/* The moment, correction, force and update pass of disc_k_pass_a on a warped
+ * image m (= I_m(x + r(x)), e.g. from disc_k_warp) given by the caller
+ * (Eqs. 3-6, Eq. 1, Algorithm A1 steps 1, 3, 4, 5).  Same outputs as
+ * disc_k_pass_a except m. */
+disc_status disc_k_force_update(const float* m, const float* zs, const float* r, float* u,
+                                float* d_out, double* norms_out, int32_t nx, int32_t ny,
+                                int32_t nz, const int32_t patch[3], float qscale,
+                                float var_floor, int32_t force_mode, void* stream);
+
+/* Differentiable form (not in the paper): the SSD between the warped CT and
+ * the moment-matched CBCT, L(r) = sum_x (I_m(x + r(x)) - I'_s(x))^2 with
+ * I'_s = zs STD(M) + E(M) over the truncated patch (Eqs. 3-6; the CBCT side zs
+ * is fixed).  *loss_out (device double) receives L.  Temporary device memory
+ * comes from the stream-ordered allocator. */
+disc_status disc_k_ssd_loss(const float* Im, const float* zs, const float* r,
+                            double* loss_out, int32_t nx, int32_t ny, int32_t nz,
+                            const int32_t patch[3], float qscale, float var_floor,
+                            void* stream);
+
+/* Gradient dL/dr of the loss above, [3][nz][ny][nx], by adjoint kernels:
+ * the patch statistics are recomputed (not stored), the adjoint of the
+ * moment matching is a truncated box sum of three per-voxel coefficients,
+ * and the warp's adjoint is the analytic trilinear derivative (zero along an
+ * axis whose sample position is clamped).  Cubic patches only (half size 1..8;
+ * other patches return DISC_ERR_SHAPE).  loss_out (may be NULL) also receives
+ * L.  grad must not alias r. */
+disc_status disc_k_ssd_grad(const float* Im, const float* zs, const float* r, float* grad,
+                            double* loss_out, int32_t nx, int32_t ny, int32_t nz,
+                            const int32_t patch[3], float qscale, float var_floor,
+                            void* stream);
+
 /* Allocation-free form of disc_k_pass_a (the paper has no counterpart: this
  * exists for callers that cannot let a library allocate device memory, such
  * as applications that own all device memory through their own pool or run

@@ -770,6 +770,54 @@ disc_status disc_k_pass_a(const float* Im, const float* zs, const float* r, floa
   return DISC_OK;
 }
 
+disc_status disc_k_force_update(const float* m, const float* zs, const float* r, float* u, float* d_out,
+                                double* norms_out, int32_t nx, int32_t ny, int32_t nz, const int32_t patch[3],
+                                float qscale, float var_floor, int32_t force_mode, void* stream) {
+  int h[3];
+  if (!m || !zs || !r || !u || !(qscale > 0.0f) || !(var_floor >= 0.0f)) return DISC_ERR_ARG;
+  if (u == r) return DISC_ERR_ARG;
+  if (force_mode != DISC_FORCE_THIRION && force_mode != DISC_FORCE_DOUBLE) return DISC_ERR_ARG;
+  disc_status st = check_patch(patch, h);
+  if (st != DISC_OK) return st;
+  if (nx < 1 || ny < 1 || nz < 1) return DISC_ERR_SHAPE;
+  int dev = 0, sms = kNumSMs;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  BoxPlan p = box_plan(kModeIterate, nx, ny, nz, h[0], h[1], h[2], sms);
+  if (p.grid.x == 0) return DISC_ERR_SHAPE;
+  cudaStream_t s = (cudaStream_t)stream;
+  disc_ctx* ctx = nullptr;
+  const int nparts = (int)(p.grid.x * p.grid.y * p.grid.z);
+  float* parts = nullptr;
+  CK(cudaMallocAsync(&parts, sizeof(float) * 2 * nparts, s));
+  BoxArgs a{};
+  a.src = m;
+  a.zs = zs;
+  a.r = r;
+  a.out = u;
+  a.f_tap = d_out;
+  a.partials = parts;
+  a.nx = nx;
+  a.ny = ny;
+  a.nz = nz;
+  a.hx = h[0];
+  a.hy = h[1];
+  a.hz = h[2];
+  a.qscale = qscale;
+  a.inv_qscale = 1.0f / qscale;
+  a.var_floor = var_floor;
+  a.force_mode = force_mode;
+  cudaError_t e = box_launch(kModeIterate, a, p, s);
+  if (e == cudaSuccess && norms_out) {
+    e = launch_partials_sum(parts, nparts, 0, norms_out, s);
+    if (e == cudaSuccess) e = launch_partials_sum(parts, nparts, 1, norms_out + 1, s);
+  }
+  cudaError_t e2 = cudaFreeAsync(parts, s);
+  CK(e);
+  CK(e2);
+  return DISC_OK;
+}
+
 disc_status disc_k_gauss(const float* u, float* r, int32_t nx, int32_t ny, int32_t nz, float sigma,
                          int32_t radius, void* stream) {
   if (!u || !r || u == r || !(sigma > 0.0f) || radius < 0) return DISC_ERR_ARG;

@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(kThreads) k_gauss(GaussArgs a) {
         const float* row = in + c * INP + iy * IX + ox;
         float acc = 0.0f;
         for (int k = 0; k <= 2 * R; ++k) acc = fmaf(w[k], row[k], acc);
-        const float nrm = tap_norm(w, R, gx, nx);
+        const float nrm = a.box_sum ? 1.0f : tap_norm(w, R, gx, nx);
         xc[e] = nrm == 1.0f ? acc : acc / nrm;
       }
       __syncthreads();
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(kThreads) k_gauss(GaussArgs a) {
         const float* col = xc + c * XCP + oy * kGX + ox;
         float acc = 0.0f;
         for (int k = 0; k <= 2 * R; ++k) acc = fmaf(w[k], col[k * kGX], acc);
-        const float nrm = tap_norm(w, R, gy, ny);
+        const float nrm = a.box_sum ? 1.0f : tap_norm(w, R, gy, ny);
         slot[e] = nrm == 1.0f ? acc : acc / nrm;
       }
       __syncthreads();
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kThreads) k_gauss(GaussArgs a) {
     // z filter for the plane R behind
     const int zo = zi - R;
     if (zo >= z0 && zo < z1) {
-      const float nrm = tap_norm(w, R, zo, nz);
+      const float nrm = a.box_sum ? 1.0f : tap_norm(w, R, zo, nz);
       const int klo = max(-R, -zo), khi = min(R, nz - 1 - zo);
       for (int e = tid; e < 3 * OP; e += kThreads) {
         const int c = e / OP, rem = e - c * OP;
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kThreads) k_gauss_xy(GaussArgs a) {
   float w[2 * R + 1];
 #pragma unroll
   for (int k = 0; k <= 2 * R; ++k) w[k] = a.w[k];
-  const bool border = x0 - R < 0 || x0 + kSX + R > nx || y0 - R < 0 || y0 + kSY + R > ny;
+  const bool border = !a.box_sum && (x0 - R < 0 || x0 + kSX + R > nx || y0 - R < 0 || y0 + kSY + R > ny);
   if (border) {
     if (tid < kSX) nrm_x[tid] = tap_norm(a.w, R, x0 + tid, nx);
     if (tid >= 64 && tid < 64 + kSY) nrm_y[tid - 64] = tap_norm(a.w, R, y0 + tid - 64, ny);
@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(kZThreads) k_gauss_z(GaussArgs a) {
       if (zo >= z0 && zo < z1) {
         float2 o2 = q2[so];
         float oz = qz[so];
-        const float nrm = tap_norm(a.w, R, zo, nz);
+        const float nrm = a.box_sum ? 1.0f : tap_norm(a.w, R, zo, nz);
         if (nrm != 1.0f) {
           o2.x = o2.x / nrm;
           o2.y = o2.y / nrm;

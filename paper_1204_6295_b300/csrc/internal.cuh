@@ -90,7 +90,8 @@ struct GaussArgs {
   int nx, ny, nz;
   int R;
   int zlen;
-  float w[2 * DISC_MAX_GAUSS_RADIUS + 1];   // normalised taps (sum 1)
+  int box_sum;          // 1: plain truncated sums (no renormalisation at the borders)
+  float w[2 * DISC_MAX_GAUSS_RADIUS + 1];   // normalised taps (sum 1), or all 1 for box sums
 };
 struct GaussPlan {
   dim3 grid;
@@ -102,6 +103,14 @@ int gauss_radius(float sigma, int radius);
 void gauss_taps(float sigma, int R, float* w);
 GaussPlan gauss_plan(int nx, int ny, int nz, int R, int num_sms);
 cudaError_t gauss_launch(const GaussArgs& a, const GaussPlan& plan, cudaStream_t s);
+
+// ----------------------------------------------------------------------------
+// Differentiable form, ssd.cu
+// ----------------------------------------------------------------------------
+// grad = (D + S_A + m S_B - S_C) * dI_m/dp at p = x + r(x): the last step of the
+// adjoint of the SSD loss (D, and the patch sums S of the coefficients A, B, C).
+cudaError_t launch_ssd_final(const float* Im, const float* r, const float* m, const float* D,
+                             const float* S, float* grad, int nx, int ny, int nz, cudaStream_t s);
 
 // ----------------------------------------------------------------------------
 // Small kernels, misc.cu

@@ -46,4 +46,42 @@ static __device__ __forceinline__ float warp_at(const float* __restrict__ Im, in
   return lerpf(lerpf(c00, c01, ty), lerpf(c10, c11, ty), tz);
 }
 
+
+// d I_m(p) / d p at p = (x, y, z) + r for the trilinear interpolant, with the
+// cell chosen as in warp_at ([floor(p), floor(p) + 1]); zero along an axis whose
+// sample position is clamped (p <= 0 or p >= n - 1 before clamping).
+static __device__ __forceinline__ void warp_grad_at(const float* __restrict__ Im, int x, int y, int z,
+                                                    float rx, float ry, float rz, int nx, int ny, int nz,
+                                                    float& gx, float& gy, float& gz) {
+  int i0[3], i1[3];
+  float t[3];
+  bool inside[3];
+  const int c[3] = {x, y, z};
+  const float rv[3] = {rx, ry, rz};
+  const int n[3] = {nx, ny, nz};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float fl = floorf(rv[a]);
+    fl = fminf(fmaxf(fl, -1073741824.0f), 1073741824.0f);
+    const int i = c[a] + (int)fl;
+    const float tt = rv[a] - fl;
+    inside[a] = (i > 0 || (i == 0 && tt > 0.0f)) && i <= n[a] - 2;
+    axis_setup(c[a], rv[a], n[a], i0[a], i1[a], t[a]);
+  }
+  const size_t sx = 1, sy = (size_t)nx, sz = (size_t)nx * ny;
+  auto at = [&](int a, int b, int cc) { return __ldg(Im + (size_t)cc * sz + (size_t)b * sy + (size_t)a * sx); };
+  const float c000 = at(i0[0], i0[1], i0[2]), c100 = at(i1[0], i0[1], i0[2]);
+  const float c010 = at(i0[0], i1[1], i0[2]), c110 = at(i1[0], i1[1], i0[2]);
+  const float c001 = at(i0[0], i0[1], i1[2]), c101 = at(i1[0], i0[1], i1[2]);
+  const float c011 = at(i0[0], i1[1], i1[2]), c111 = at(i1[0], i1[1], i1[2]);
+  const float tx = t[0], ty = t[1], tz = t[2];
+  // d/dx: differences along x, interpolated in y and z
+  const float dx00 = c100 - c000, dx10 = c110 - c010, dx01 = c101 - c001, dx11 = c111 - c011;
+  const float dy00 = c010 - c000, dy10 = c110 - c100, dy01 = c011 - c001, dy11 = c111 - c101;
+  const float dz00 = c001 - c000, dz10 = c101 - c100, dz01 = c011 - c010, dz11 = c111 - c110;
+  gx = inside[0] ? lerpf(lerpf(dx00, dx10, ty), lerpf(dx01, dx11, ty), tz) : 0.0f;
+  gy = inside[1] ? lerpf(lerpf(dy00, dy10, tx), lerpf(dy01, dy11, tx), tz) : 0.0f;
+  gz = inside[2] ? lerpf(lerpf(dz00, dz10, tx), lerpf(dz01, dz11, tx), ty) : 0.0f;
+}
+
 }  // namespace disc

@@ -82,6 +82,11 @@ _SIGS = {
     "disc_k_pass_a_static": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _i32, _i32,
                                    ctypes.POINTER(_i32), _f32, _f32, _i32, _vp]),
     "disc_k_gauss": (_st, [_vp, _vp, _i32, _i32, _i32, _f32, _i32, _vp]),
+    "disc_k_force_update": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _i32, _i32, _i32,
+                                  ctypes.POINTER(_i32), _f32, _f32, _i32, _vp]),
+    "disc_k_ssd_loss": (_st, [_vp, _vp, _vp, _vp, _i32, _i32, _i32, ctypes.POINTER(_i32), _f32, _f32, _vp]),
+    "disc_k_ssd_grad": (_st, [_vp, _vp, _vp, _vp, _vp, _i32, _i32, _i32, ctypes.POINTER(_i32), _f32, _f32,
+                              _vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -317,3 +322,27 @@ def k_gauss(u, r, sigma, radius=0, stream=None):
     _, nz, ny, nx = u.shape
     _check(_lib.disc_k_gauss(_ptr(u), _ptr(r), nx, ny, nz, float(sigma), int(radius), _stream(stream)),
            "disc_k_gauss")
+
+
+def k_force_update(m, zs, r, u, patch, qs, d_out=None, norms_out=None, var_floor=1e-6,
+                   force_mode=FORCE_THIRION, stream=None):
+    """Moment, correction, force and update pass on a given warped image m."""
+    nz, ny, nx = m.shape
+    p = (_i32 * 3)(*patch)
+    _check(_lib.disc_k_force_update(_ptr(m), _ptr(zs), _ptr(r), _ptr(u), _ptr(d_out), _ptr(norms_out),
+                                    nx, ny, nz, p, float(qs), float(var_floor), int(force_mode),
+                                    _stream(stream)), "disc_k_force_update")
+
+
+def k_ssd_loss(Im, zs, r, loss_out, patch, qs, var_floor=1e-6, stream=None):
+    nz, ny, nx = Im.shape
+    p = (_i32 * 3)(*patch)
+    _check(_lib.disc_k_ssd_loss(_ptr(Im), _ptr(zs), _ptr(r), _ptr(loss_out), nx, ny, nz, p, float(qs),
+                                float(var_floor), _stream(stream)), "disc_k_ssd_loss")
+
+
+def k_ssd_grad(Im, zs, r, grad, patch, qs, loss_out=None, var_floor=1e-6, stream=None):
+    nz, ny, nx = Im.shape
+    p = (_i32 * 3)(*patch)
+    _check(_lib.disc_k_ssd_grad(_ptr(Im), _ptr(zs), _ptr(r), _ptr(grad), _ptr(loss_out), nx, ny, nz, p,
+                                float(qs), float(var_floor), _stream(stream)), "disc_k_ssd_grad")
