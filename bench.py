@@ -42,8 +42,9 @@ WORKLOADS = {
 DEFAULT_WORKLOAD = "headneck-256x256x128"
 METRIC = "Gvoxel-iterations/s and % of HBM roofline, plain vs batched/adjoint form, 1 B300"
 UNIT = "Gvoxel-it/s"
-PASS_A_BYTES_PER_VOXEL = 32   # read r (12) + I_m (4) + zs (4), write u (12)
-PASS_B_BYTES_PER_VOXEL = 24   # read u (12), write r (12)
+BOX_BYTES_PER_VOXEL = 32     # moments/force pass: read m (4) + zs (4) + r (12), write u (12)
+GAUSS_BYTES_PER_VOXEL = 24   # Gaussian (field in and out, 12 + 12)
+WARP_BYTES_PER_VOXEL = 20    # warp: read r (12) + I_m (4, taps amortised), write m (4)
 
 
 def level_dims(dims, levels):
@@ -81,14 +82,17 @@ def load_peaks():
         return 6400.0, "fallback"
 
 
+ROOFLINE_SOURCES = ("box_fast.cu", "box_pass.cu")   # the box kernel and its planner
+
+
 def source_digest():
+    """Digest of the sources that define the roofline kernel (its counters go stale with them)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1204_6295_b300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode())
-                h.update(f.read())
+    for name in ROOFLINE_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
@@ -221,10 +225,11 @@ def run_reference(args, w, rank, world):
 
 
 def time_kernels(disc, torch, w, pair_dev, field_dev, reps=20):
-    """CUDA-event timing of the two per-iteration kernels at the finest level.
+    """CUDA-event timing of the per-iteration kernels at the finest level.
 
-    Same launch configuration as inside the schedule (the plan depends only on
-    sizes and patch), launched on the current torch stream.
+    Each is launched through its kernel-level entry point on the current torch
+    stream, with the launch configuration the schedule uses (the plan depends
+    only on sizes and patch).  Returns seconds per launch.
     """
     nx, ny, nz = w["dims"]
     N = nx * ny * nz
@@ -232,28 +237,59 @@ def time_kernels(disc, torch, w, pair_dev, field_dev, reps=20):
     patch = w["patch"]
     qs_s = disc.qscale(float(cbct.abs().max()), patch)
     qs_m = disc.qscale(float(ct.abs().max()), patch)
-    zs = torch.empty_like(ct)
+    zs, m = torch.empty_like(ct), torch.empty_like(ct)
     disc.k_static_norm(cbct, zs, patch, qs_s)
+    disc.k_warp(ct, field_dev, m)
     u = torch.empty_like(field_dev)
     r2 = torch.empty_like(field_dev)
     s = torch.cuda.current_stream()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    for _ in range(3):
-        disc.k_pass_a(ct, zs, field_dev, u, patch, qs_m)
-        disc.k_gauss(u, r2, w["sigma"])
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(reps):
+            fn()
+        e1.record(s)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps / 1e3
+
+    return {"box_s": timed(lambda: disc.k_force_update(m, zs, field_dev, u, patch, qs_m)),
+            "gauss_s": timed(lambda: disc.k_gauss(u, r2, w["sigma"])),
+            "warp_s": timed(lambda: disc.k_warp(ct, field_dev, m)),
+            "N": N, "zs": zs, "qs_m": qs_m}
+
+
+def time_differentiable(disc, torch, w, pair_dev, field_dev, kt, reps=5):
+    """Forward (loss) + backward (adjoint gradient) of the SSD form at the finest level."""
+    ct, _ = pair_dev
+    patch = w["patch"]
+    if len(set(patch)) != 1:
+        return None
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    grad = torch.empty_like(field_dev)
+    s = torch.cuda.current_stream()
+
+    def step():
+        disc.k_ssd_loss(ct, kt["zs"], field_dev, loss, patch, kt["qs_m"])
+        disc.k_ssd_grad(ct, kt["zs"], field_dev, grad, patch, kt["qs_m"])
+
+    for _ in range(2):
+        step()
     torch.cuda.synchronize()
-    ev[0].record(s)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
     for _ in range(reps):
-        disc.k_pass_a(ct, zs, field_dev, u, patch, qs_m)
-    ev[1].record(s)
-    ev[2].record(s)
-    for _ in range(reps):
-        disc.k_gauss(u, r2, w["sigma"])
-    ev[3].record(s)
+        step()
+    e1.record(s)
     torch.cuda.synchronize()
-    ta = ev[0].elapsed_time(ev[1]) / reps / 1e3
-    tb = ev[2].elapsed_time(ev[3]) / reps / 1e3
-    return {"pass_a_s": ta, "pass_b_s": tb, "N": N}
+    t = e0.elapsed_time(e1) / reps / 1e3
+    return {"value": kt["N"] / t / 1e9, "unit": "Gvoxel-evaluations/s (forward + backward)",
+            "ms_per_step": t * 1e3, "algorithmic_bytes_per_voxel": 32,
+            "what": "disc_k_ssd_loss + disc_k_ssd_grad on the finest level (256x256x128 for the default "
+                    "workload), patch statistics recomputed in the backward pass"}
 
 
 def run_ours(args, w, rank, world, local_rank):
@@ -309,9 +345,11 @@ def run_ours(args, w, rank, world, local_rank):
     field = torch.empty((3, nz, ny, nx), dtype=torch.float32, device="cuda")
     reg.get_field(field)
     kt = time_kernels(disc, torch, w, (ct, cbct), field)
+    diff_form = time_differentiable(disc, torch, w, (ct, cbct), field, kt)
     peak, peak_kind = load_peaks()
-    a_gbs = PASS_A_BYTES_PER_VOXEL * kt["N"] / kt["pass_a_s"] / 1e9
-    b_gbs = PASS_B_BYTES_PER_VOXEL * kt["N"] / kt["pass_b_s"] / 1e9
+    box_gbs = BOX_BYTES_PER_VOXEL * kt["N"] / kt["box_s"] / 1e9
+    gauss_gbs = GAUSS_BYTES_PER_VOXEL * kt["N"] / kt["gauss_s"] / 1e9
+    warp_gbs = WARP_BYTES_PER_VOXEL * kt["N"] / kt["warp_s"] / 1e9
     traffic = recorded_traffic(args.workload)
 
     # end to end through the public API with host buffers (pinned)
@@ -347,7 +385,9 @@ def run_ours(args, w, rank, world, local_rank):
         if dist:
             dist.destroy_process_group()
         return 0
-    launches = sum(w["iters"]) * 3 + (L - 1)
+    # per level: one warp, then 4 launches per iteration (box, Gaussian xy, Gaussian z
+    # with the next warp, norm); one up-sampling between levels
+    launches = sum(w["iters"]) * 4 + L + (L - 1)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -357,14 +397,20 @@ def run_ours(args, w, rank, world, local_rank):
                    "voxel_iterations_per_step": units, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2: finest-level working set "
                          f"{(9 * nx * ny * nz * 4) / 1e6:.0f} MB > 126 MB"},
-        "roofline": {"bound": "hbm", "kernel": "k_box_pass<kModeIterate> (warp+moments+correction+force)",
-                     "achieved": a_gbs, "peak": peak, "unit": "GB/s", "frac": a_gbs / peak,
+        "roofline": {"bound": "hbm", "kernel": "k_box_h<kModeIterate> (patch moments, correction, force, update)",
+                     "achieved": box_gbs, "peak": peak, "unit": "GB/s", "frac": box_gbs / peak,
                      "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                     "traffic": traffic, "algorithmic_bytes_per_voxel": PASS_A_BYTES_PER_VOXEL,
-                     "launch_ms": kt["pass_a_s"] * 1e3},
-        "kernels": {"pass_b_gauss": {"achieved_gbs": b_gbs, "frac": b_gbs / peak,
-                                      "launch_ms": kt["pass_b_s"] * 1e3,
-                                      "algorithmic_bytes_per_voxel": PASS_B_BYTES_PER_VOXEL}},
+                     "traffic": traffic, "algorithmic_bytes_per_voxel": BOX_BYTES_PER_VOXEL,
+                     "launch_ms": kt["box_s"] * 1e3,
+                     "note": "issue-bound (exact 64-bit patch sums), not HBM-bound; see profiles/"},
+        "kernels": {"gauss_xy_plus_z": {"achieved_gbs": gauss_gbs, "frac": gauss_gbs / peak,
+                                        "launch_ms": kt["gauss_s"] * 1e3,
+                                        "algorithmic_bytes_per_voxel": GAUSS_BYTES_PER_VOXEL},
+                    "warp": {"achieved_gbs": warp_gbs, "frac": warp_gbs / peak, "launch_ms": kt["warp_s"] * 1e3,
+                             "algorithmic_bytes_per_voxel": WARP_BYTES_PER_VOXEL}},
+        "forms": {"plain": {"value": value, "unit": UNIT},
+                  "differentiable": diff_form,
+                  "effective_hbm_frac_32B_model": value * 1e9 * 32 / (peak * 1e9)},
         "e2e": e2e,
         "gpu_launches": launches * args.steps,
         "clocks": clk.summary(),
