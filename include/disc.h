@@ -150,6 +150,50 @@ disc_status disc_get_norm_history(disc_ctx* ctx, int32_t level, float* out,
 disc_status disc_destroy(disc_ctx* ctx);
 
 /* ---------------------------------------------------------------------
+ * Batched registration: many CT/CBCT pairs of uneven size advanced together
+ * (the workloads' batched form; not in the paper).  Each pair runs exactly the
+ * single-pair computation (bit-identical fields), but one iteration of all
+ * pairs is one launch per step of the iteration over a work table of every
+ * pair's tiles, a level's iterations are one CUDA graph, and the tile
+ * scheduling of the moment/force launch is tuned per level at first use.
+ * All pairs share the parameters and the schedule.  Cubic patches of 3..15
+ * voxels and Gaussian radius 1..8 only (DISC_ERR_ARG otherwise).
+ * ------------------------------------------------------------------- */
+typedef struct disc_batch disc_batch;
+
+/* Create a batch of npairs (1..64) pairs on `device`, ordered on `cuda_stream`. */
+disc_status disc_batch_create(const disc_params* p, int device, void* cuda_stream,
+                              int32_t npairs, disc_batch** out);
+
+/* Load pair `pair`'s images (as disc_set_images).  Allowed only before the
+ * batch has iterated (or after disc_batch_restart); DISC_ERR_STATE otherwise. */
+disc_status disc_batch_set_images(disc_batch* b, int32_t pair, const float* ct_moving,
+                                  const float* cbct_static, int32_t nx, int32_t ny,
+                                  int32_t nz, int mem_kind);
+
+/* Reset every pair's field to 0 at the coarsest level and the schedule to its
+ * start (images and patch statistics are kept). */
+disc_status disc_batch_restart(disc_batch* b);
+
+/* Advance the shared schedule by at most max_iters iterations (-1 = to the
+ * end), as disc_iterate does for one pair; *iters_done (may be NULL)
+ * receives the iterations run.  Does not synchronise, except at the first
+ * iteration of a level, where the tuning launches are timed. */
+disc_status disc_batch_iterate(disc_batch* b, int32_t max_iters, int32_t* iters_done);
+
+/* Copy pair `pair`'s field on its finest grid (as disc_get_field). */
+disc_status disc_batch_get_field(disc_batch* b, int32_t pair, float* out, int mem_kind);
+
+/* Tuning chosen for `level`: work items of the moment/force launch, its grid
+ * (equal to items, or one wave of persistent CTAs), and the z-chunk
+ * lengthening factor.  DISC_ERR_STATE before the level has run. */
+disc_status disc_batch_get_tuning(disc_batch* b, int32_t level, int32_t* items, int32_t* grid,
+                                  int32_t* zmult);
+
+/* Release the batch and every pair context.  NULL is accepted. */
+disc_status disc_batch_destroy(disc_batch* b);
+
+/* ---------------------------------------------------------------------
  * Kernel-level calls: one hot-path step on caller-owned device buffers.
  * All pointers are device pointers on the current device; work goes on
  * `stream` (cudaStream_t, NULL = legacy default stream).  `patch` is the

@@ -9,69 +9,9 @@
 #include <new>
 
 #include "internal.cuh"
+#include "context.cuh"
 
 using namespace disc;
-
-namespace {
-
-struct DeviceGuard {
-  int prev = -1;
-  bool ok = true;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
-  }
-  ~DeviceGuard() {
-    int cur = -1;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-  }
-};
-
-struct Level {
-  int nx = 0, ny = 0, nz = 0;
-  size_t N = 0;
-  float* Im = nullptr;   // moving image (CT) at this level
-  float* Is = nullptr;   // static image (CBCT, shifted) at this level
-  float* zs = nullptr;   // (I_s - E(S)) / STD(S) over the patch
-  float* m = nullptr;    // warped CT I_m(x + r(x))
-  float* r = nullptr;    // field [3][N]
-  float* u = nullptr;    // r + dr [3][N]
-  float* t = nullptr;    // xy-filtered field [3][N] (Gaussian scratch)
-  float* hist = nullptr; // l^(k) history
-  int hist_cap = 0;
-  BoxPlan pa{};
-  GaussPlan pb{};
-  cudaGraphExec_t graph = nullptr;
-  int graph_iters = 0;
-};
-
-}  // namespace
-
-struct disc_ctx {
-  disc_params p{};
-  int device = 0;
-  int num_sms = kNumSMs;
-  cudaStream_t user = nullptr;
-  cudaStream_t s = nullptr;
-  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-  int hx = 0, hy = 0, hz = 0, R = 0;
-  float w[2 * DISC_MAX_GAUSS_RADIUS + 1] = {};
-  int nx = 0, ny = 0, nz = 0;
-  int L = 0;
-  bool have_images = false;
-  Level lev[DISC_MAX_LEVELS];
-  float qs_m = 1.0f, qs_s = 1.0f;
-  float* partials = nullptr;
-  int max_parts = 0;
-  int* d_iter = nullptr;     // [DISC_MAX_LEVELS]
-  int* d_stop = nullptr;     // [DISC_MAX_LEVELS]
-  double* d_scratch = nullptr;
-  float* d_maxabs = nullptr; // [2]
-  int cur_level = 0;
-  int cur_iter = 0;
-  disc_status sticky = DISC_OK;
-  bool use_graphs = true;
-};
 
 namespace {
 
@@ -241,6 +181,50 @@ cudaError_t reset_level_counters(disc_ctx* c, int l) {
 }
 
 }  // namespace
+
+namespace disc {
+
+cudaError_t ctx_reset_level_counters(disc_ctx* c, int l) { return reset_level_counters(c, l); }
+
+BoxArgs ctx_box_args(const disc_ctx* c, int l) {
+  const Level& v = c->lev[l];
+  BoxArgs a = box_args(c, v);
+  a.src = v.m;
+  a.zs = v.zs;
+  a.r = v.r;
+  a.out = v.u;
+  a.partials = c->partials;
+  a.stop = c->d_stop + l;
+  a.qscale = c->qs_m;
+  a.inv_qscale = 1.0f / c->qs_m;
+  a.zlen = v.pa.zlen;
+  return a;
+}
+
+GaussArgs ctx_gauss_args(const disc_ctx* c, int l) {
+  const Level& v = c->lev[l];
+  GaussArgs g{};
+  g.u = v.u;
+  g.r = v.r;
+  g.t = v.t;
+  g.Im = v.Im;
+  g.m = v.m;
+  g.stop = c->d_stop + l;
+  g.nx = v.nx;
+  g.ny = v.ny;
+  g.nz = v.nz;
+  g.R = c->R;
+  g.zlen = v.pb.zlen;
+  std::memcpy(g.w, c->w, sizeof(c->w));
+  return g;
+}
+
+NormState ctx_norm_state(const disc_ctx* c, int l) {
+  const Level& v = c->lev[l];
+  return NormState{v.hist, c->d_iter + l, c->d_stop + l, v.hist_cap, c->p.stop_window, c->p.stop_eps};
+}
+
+}  // namespace disc
 
 // ============================================================================
 // Public API

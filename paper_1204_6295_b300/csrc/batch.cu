@@ -1,0 +1,434 @@
+// Batched DISC: many CT/CBCT pairs of uneven size advanced together.
+//
+// Each pair keeps its own registration context (buffers, pyramid, CBCT patch
+// statistics, field), but an iteration of all pairs is four launches in total
+// instead of four per pair: the moment/force pass, the Gaussian xy pass, the
+// Gaussian z pass (with the next warp) and the norm, each over a work table
+// that concatenates the CTA grids of every pair.  A level's iterations are
+// captured once as a CUDA graph and replayed.  The moment/force launch is
+// tuned per level at its first use: the z-chunk length of every pair's tiles
+// and whether the launch has one CTA per work item or a persistent grid of one
+// wave that strides over the table.  Per pair the arithmetic is the one of the
+// single-pair path, so each pair's field is bit-identical to a separate run.
+
+#include <cstring>
+#include <new>
+
+#include "context.cuh"
+
+using namespace disc;
+
+struct disc_batch {
+  disc_params p{};
+  int device = 0;
+  int num_sms = kNumSMs;
+  cudaStream_t user = nullptr, s = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  int npairs = 0;
+  disc_ctx* pair[kMaxBatch] = {};
+  int L = 0, H = 0, R = 0;
+  // device work tables per level
+  BoxBatch* d_box[DISC_MAX_LEVELS] = {};
+  GaussBatch* d_xy[DISC_MAX_LEVELS] = {};
+  GaussBatch* d_z[DISC_MAX_LEVELS] = {};
+  NormBatch* d_norm[DISC_MAX_LEVELS] = {};
+  WarpBatch* d_warp[DISC_MAX_LEVELS] = {};
+  int box_total[DISC_MAX_LEVELS] = {}, box_grid[DISC_MAX_LEVELS] = {}, zmult[DISC_MAX_LEVELS] = {};
+  int xy_total[DISC_MAX_LEVELS] = {}, z_total[DISC_MAX_LEVELS] = {}, warp_total[DISC_MAX_LEVELS] = {};
+  bool ready[DISC_MAX_LEVELS] = {};
+  cudaGraphExec_t graph[DISC_MAX_LEVELS] = {};
+  int graph_iters[DISC_MAX_LEVELS] = {};
+  int cur_level = 0, cur_iter = 0;
+  disc_status sticky = DISC_OK;
+};
+
+namespace {
+
+disc_status bfail(disc_batch* b, cudaError_t e) {
+  cudaGetLastError();
+  if (e == cudaErrorMemoryAllocation) return DISC_ERR_OOM;
+  if (b && b->sticky == DISC_OK) b->sticky = DISC_ERR_CUDA;
+  return DISC_ERR_CUDA;
+}
+
+#define BCK(expr)                                \
+  do {                                           \
+    cudaError_t e_ = (expr);                     \
+    if (e_ != cudaSuccess) return bfail(b, e_);  \
+  } while (0)
+
+cudaError_t benter(disc_batch* b) {
+  cudaError_t e = cudaEventRecord(b->ev_in, b->user);
+  if (e != cudaSuccess) return e;
+  return cudaStreamWaitEvent(b->s, b->ev_in, 0);
+}
+cudaError_t bleave(disc_batch* b) {
+  cudaError_t e = cudaEventRecord(b->ev_out, b->s);
+  if (e != cudaSuccess) return e;
+  return cudaStreamWaitEvent(b->user, b->ev_out, 0);
+}
+
+void drop_level(disc_batch* b, int l) {
+  if (b->graph[l]) cudaGraphExecDestroy(b->graph[l]);
+  b->graph[l] = nullptr;
+  b->graph_iters[l] = 0;
+  b->ready[l] = false;
+}
+
+bool all_images(const disc_batch* b) {
+  for (int i = 0; i < b->npairs; ++i)
+    if (!b->pair[i]->have_images) return false;
+  return true;
+}
+
+// Box-pass work table of level l with every pair's z chunks lengthened zmult times.
+cudaError_t upload_box_table(disc_batch* b, int l, int zmult, int* total) {
+  BoxBatch h;
+  std::memset(&h, 0, sizeof(h));
+  h.count = b->npairs;
+  int off = 0;
+  for (int i = 0; i < b->npairs; ++i) {
+    const disc_ctx* c = b->pair[i];
+    const Level& v = c->lev[l];
+    BoxArgs a = ctx_box_args(c, l);
+    a.zlen = v.pa.zlen * zmult;
+    if (a.zlen > v.nz) a.zlen = v.nz;
+    h.args[i] = a;
+    h.grid[i] = dim3(v.pa.grid.x, v.pa.grid.y, (v.nz + a.zlen - 1) / a.zlen);
+    h.offset[i] = off;
+    off += (int)(h.grid[i].x * h.grid[i].y * h.grid[i].z);
+  }
+  h.offset[b->npairs] = off;
+  *total = off;
+  cudaError_t e = cudaMemcpyAsync(b->d_box[l], &h, sizeof(h), cudaMemcpyHostToDevice, b->s);
+  if (e != cudaSuccess) return e;
+  // norm table: the same CTA counts
+  NormBatch n;
+  std::memset(&n, 0, sizeof(n));
+  n.count = b->npairs;
+  for (int i = 0; i < b->npairs; ++i) {
+    n.partials[i] = b->pair[i]->partials;
+    n.nparts[i] = h.offset[i + 1] - h.offset[i];
+    n.st[i] = ctx_norm_state(b->pair[i], l);
+  }
+  e = cudaMemcpyAsync(b->d_norm[l], &n, sizeof(n), cudaMemcpyHostToDevice, b->s);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(b->s);   // the host tables are stack objects
+}
+
+cudaError_t build_tables(disc_batch* b, int l) {
+  cudaError_t e;
+  if (!b->d_box[l]) {
+    e = cudaMalloc(&b->d_box[l], sizeof(BoxBatch));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_xy[l], sizeof(GaussBatch));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_z[l], sizeof(GaussBatch));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_norm[l], sizeof(NormBatch));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_warp[l], sizeof(WarpBatch));
+    if (e != cudaSuccess) return e;
+  }
+  GaussBatch xy, z;
+  WarpBatch w;
+  std::memset(&xy, 0, sizeof(xy));
+  std::memset(&z, 0, sizeof(z));
+  std::memset(&w, 0, sizeof(w));
+  xy.count = z.count = w.count = b->npairs;
+  int oxy = 0, oz = 0, ow = 0;
+  for (int i = 0; i < b->npairs; ++i) {
+    const disc_ctx* c = b->pair[i];
+    const Level& v = c->lev[l];
+    const GaussArgs g = ctx_gauss_args(c, l);
+    dim3 gxy, gz;
+    gauss_grids(v.nx, v.ny, v.nz, v.pb, &gxy, &gz);
+    xy.args[i] = g;
+    xy.args[i].r = g.t;          // xy pass: u -> t
+    z.args[i] = g;
+    z.args[i].u = g.t;           // z pass: t -> r (and m)
+    xy.grid[i] = gxy;
+    z.grid[i] = gz;
+    xy.offset[i] = oxy;
+    z.offset[i] = oz;
+    oxy += (int)(gxy.x * gxy.y * gxy.z);
+    oz += (int)(gz.x * gz.y * gz.z);
+    w.offset[i] = ow;
+    w.Im[i] = v.Im;
+    w.r[i] = v.r;
+    w.m[i] = v.m;
+    w.nx[i] = v.nx;
+    w.ny[i] = v.ny;
+    w.nz[i] = v.nz;
+    w.stop[i] = c->d_stop + l;
+    ow += ((v.nx + kWarpBatchThreads - 1) / kWarpBatchThreads) * v.ny * v.nz;
+  }
+  xy.offset[b->npairs] = oxy;
+  z.offset[b->npairs] = oz;
+  w.offset[b->npairs] = ow;
+  b->xy_total[l] = oxy;
+  b->z_total[l] = oz;
+  b->warp_total[l] = ow;
+  e = cudaMemcpyAsync(b->d_xy[l], &xy, sizeof(xy), cudaMemcpyHostToDevice, b->s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_z[l], &z, sizeof(z), cudaMemcpyHostToDevice, b->s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_warp[l], &w, sizeof(w), cudaMemcpyHostToDevice, b->s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->s);
+  return e;
+}
+
+size_t box_smem(const disc_batch* b) { return box_fast_smem(kModeIterate, b->H); }
+
+// Autotuner: time the batched box launch for each z-chunk multiplier and for a
+// one-CTA-per-item or one-wave persistent grid; keep the fastest.  Runs on the
+// level's current state: the box pass only writes u and its partials, which the
+// next real iteration overwrites.
+cudaError_t tune_level(disc_batch* b, int l) {
+  const size_t smem = box_smem(b);
+  const int occ = box_fast_occupancy(kModeIterate, b->H, smem);
+  const int slots = b->num_sms * (occ < 1 ? 1 : occ);
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e != cudaSuccess) return e;
+  e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return e;
+  }
+  float best = 1e30f;
+  int best_mult = 1, best_grid = 0;
+  const int mults[3] = {1, 2, 4};
+  for (int mi = 0; mi < 3 && e == cudaSuccess; ++mi) {
+    int total = 0;
+    e = upload_box_table(b, l, mults[mi], &total);
+    if (e != cudaSuccess) break;
+    const int grids[2] = {total, total < slots ? total : slots};
+    for (int gi = 0; gi < 2 && e == cudaSuccess; ++gi) {
+      if (gi == 1 && grids[1] == grids[0]) continue;
+      e = box_fast_launch_batch(b->d_box[l], b->H, total, grids[gi], smem, b->s);   // warm-up
+      if (e == cudaSuccess) e = cudaEventRecord(e0, b->s);
+      for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+        e = box_fast_launch_batch(b->d_box[l], b->H, total, grids[gi], smem, b->s);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, b->s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && ms < best) {
+        best = ms;
+        best_mult = mults[mi];
+        best_grid = grids[gi];
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return e;
+  int total = 0;
+  e = upload_box_table(b, l, best_mult, &total);
+  if (e != cudaSuccess) return e;
+  b->zmult[l] = best_mult;
+  b->box_total[l] = total;
+  b->box_grid[l] = best_grid;
+  return cudaSuccess;
+}
+
+cudaError_t queue_batch_iterations(disc_batch* b, int l, int n) {
+  cudaError_t e = launch_warp_batch(b->d_warp[l], b->warp_total[l], b->s);
+  const size_t smem = box_smem(b);
+  for (int k = 0; k < n && e == cudaSuccess; ++k) {
+    e = box_fast_launch_batch(b->d_box[l], b->H, b->box_total[l], b->box_grid[l], smem, b->s);
+    if (e == cudaSuccess)
+      e = gauss_launch_batch(b->d_xy[l], b->xy_total[l], b->d_z[l], b->z_total[l], b->R, true, b->s);
+    if (e == cudaSuccess) e = launch_norm_finalize_batch(b->d_norm[l], b->npairs, b->s);
+  }
+  return e;
+}
+
+cudaError_t run_batch_iterations(disc_batch* b, int l, int n) {
+  if (n <= 0) return cudaSuccess;
+  if (b->graph[l] == nullptr || b->graph_iters[l] != n) {
+    if (b->graph[l]) {
+      cudaGraphExecDestroy(b->graph[l]);
+      b->graph[l] = nullptr;
+    }
+    cudaGraph_t gph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    e = queue_batch_iterations(b, l, n);
+    cudaError_t e2 = cudaStreamEndCapture(b->s, &gph);
+    if (e != cudaSuccess) {
+      if (gph) cudaGraphDestroy(gph);
+      return e;
+    }
+    if (e2 != cudaSuccess) return e2;
+    e = cudaGraphInstantiate(&b->graph[l], gph, 0);
+    cudaGraphDestroy(gph);
+    if (e != cudaSuccess) {
+      b->graph[l] = nullptr;
+      return e;
+    }
+    b->graph_iters[l] = n;
+  }
+  return cudaGraphLaunch(b->graph[l], b->s);
+}
+
+}  // namespace
+
+extern "C" {
+
+disc_status disc_batch_create(const disc_params* p, int device, void* cuda_stream, int32_t npairs,
+                              disc_batch** out) {
+  if (!out || !p) return DISC_ERR_ARG;
+  *out = nullptr;
+  if (npairs < 1 || npairs > kMaxBatch) return DISC_ERR_ARG;
+  // the batched kernels are specialised for cubic patches and Gaussian radius <= 8
+  if (p->patch[0] != p->patch[1] || p->patch[1] != p->patch[2] || p->patch[0] < 3 || p->patch[0] > 15 ||
+      p->patch[0] % 2 == 0)
+    return DISC_ERR_ARG;
+  if (p->levels < 1 || p->levels > DISC_MAX_LEVELS || !(p->gauss_sigma > 0.0f)) return DISC_ERR_ARG;
+  const int R = gauss_radius(p->gauss_sigma, p->gauss_radius);
+  if (R < 1 || R > 8) return DISC_ERR_ARG;
+  disc_batch* b = new (std::nothrow) disc_batch();
+  if (!b) return DISC_ERR_OOM;
+  b->p = *p;
+  b->device = device;
+  b->npairs = npairs;
+  b->L = p->levels;
+  b->H = (p->patch[0] - 1) / 2;
+  b->R = R;
+  DeviceGuard guard(device);
+  cudaError_t e = cudaStreamCreateWithFlags(&b->s, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+  if (e == cudaSuccess) cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, device);
+  b->user = static_cast<cudaStream_t>(cuda_stream);
+  disc_status st = e == cudaSuccess ? DISC_OK : DISC_ERR_CUDA;
+  for (int i = 0; i < npairs && st == DISC_OK; ++i) st = disc_create(p, device, b->s, &b->pair[i]);
+  if (st != DISC_OK) {
+    disc_batch_destroy(b);
+    return st;
+  }
+  b->cur_level = b->L - 1;
+  *out = b;
+  return DISC_OK;
+}
+
+disc_status disc_batch_destroy(disc_batch* b) {
+  if (!b) return DISC_OK;
+  DeviceGuard guard(b->device);
+  if (b->s) cudaStreamSynchronize(b->s);
+  for (int l = 0; l < DISC_MAX_LEVELS; ++l) {
+    if (b->graph[l]) cudaGraphExecDestroy(b->graph[l]);
+    cudaFree(b->d_box[l]);
+    cudaFree(b->d_xy[l]);
+    cudaFree(b->d_z[l]);
+    cudaFree(b->d_norm[l]);
+    cudaFree(b->d_warp[l]);
+  }
+  for (int i = 0; i < b->npairs; ++i) disc_destroy(b->pair[i]);
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
+  if (b->s) cudaStreamDestroy(b->s);
+  cudaGetLastError();
+  delete b;
+  return DISC_OK;
+}
+
+disc_status disc_batch_set_images(disc_batch* b, int32_t pair, const float* ct, const float* cbct, int32_t nx,
+                                  int32_t ny, int32_t nz, int mem_kind) {
+  if (!b || pair < 0 || pair >= b->npairs) return DISC_ERR_ARG;
+  if (b->sticky != DISC_OK) return DISC_ERR_STATE;
+  if (b->cur_level != b->L - 1 || b->cur_iter != 0) return DISC_ERR_STATE;   // only before iterating
+  if ((double)nx * ny * nz * 3.0 >= 2147483647.0) return DISC_ERR_SHAPE;
+  DeviceGuard guard(b->device);
+  BCK(benter(b));
+  disc_status st = disc_set_images(b->pair[pair], ct, cbct, nx, ny, nz, mem_kind);
+  if (st != DISC_OK) return st;
+  for (int l = 0; l < DISC_MAX_LEVELS; ++l) drop_level(b, l);
+  BCK(bleave(b));
+  return DISC_OK;
+}
+
+disc_status disc_batch_restart(disc_batch* b) {
+  if (!b) return DISC_ERR_ARG;
+  if (b->sticky != DISC_OK) return DISC_ERR_STATE;
+  if (!all_images(b)) return DISC_ERR_STATE;
+  DeviceGuard guard(b->device);
+  BCK(benter(b));
+  const int lc = b->L - 1;
+  for (int i = 0; i < b->npairs; ++i) {
+    disc_ctx* c = b->pair[i];
+    BCK(cudaMemsetAsync(c->lev[lc].r, 0, 3 * c->lev[lc].N * sizeof(float), b->s));
+    for (int l = 0; l < b->L; ++l) BCK(ctx_reset_level_counters(c, l));
+    c->cur_level = lc;
+    c->cur_iter = 0;
+  }
+  b->cur_level = lc;
+  b->cur_iter = 0;
+  BCK(bleave(b));
+  return DISC_OK;
+}
+
+disc_status disc_batch_iterate(disc_batch* b, int32_t max_iters, int32_t* iters_done) {
+  if (!b) return DISC_ERR_ARG;
+  if (b->sticky != DISC_OK) return DISC_ERR_STATE;
+  if (!all_images(b)) return DISC_ERR_STATE;
+  DeviceGuard guard(b->device);
+  BCK(benter(b));
+  long long budget = max_iters < 0 ? (1LL << 40) : max_iters;
+  int done = 0;
+  while (true) {
+    const int l = b->cur_level;
+    const int total = b->p.iters[b->L - 1 - l];
+    const int left = total - b->cur_iter;
+    if (left > 0 && budget > 0) {
+      if (!b->ready[l]) {
+        BCK(build_tables(b, l));
+        BCK(launch_warp_batch(b->d_warp[l], b->warp_total[l], b->s));   // m for the tuning launches
+        BCK(tune_level(b, l));
+        b->ready[l] = true;
+      }
+      const int n = (int)(left < budget ? left : budget);
+      BCK(run_batch_iterations(b, l, n));
+      b->cur_iter += n;
+      budget -= n;
+      done += n;
+      for (int i = 0; i < b->npairs; ++i) b->pair[i]->cur_iter = b->cur_iter;
+    }
+    if (b->cur_iter >= total && l > 0) {
+      for (int i = 0; i < b->npairs; ++i) {
+        disc_ctx* c = b->pair[i];
+        const Level& fine = c->lev[l - 1];
+        BCK(launch_up2(c->lev[l].r, fine.r, fine.nx, fine.ny, fine.nz, b->s));
+        BCK(ctx_reset_level_counters(c, l - 1));
+        c->cur_level = l - 1;
+        c->cur_iter = 0;
+      }
+      b->cur_level = l - 1;
+      b->cur_iter = 0;
+      continue;
+    }
+    break;
+  }
+  if (iters_done) *iters_done = done;
+  BCK(bleave(b));
+  return DISC_OK;
+}
+
+disc_status disc_batch_get_field(disc_batch* b, int32_t pair, float* out, int mem_kind) {
+  if (!b || pair < 0 || pair >= b->npairs) return DISC_ERR_ARG;
+  if (b->sticky != DISC_OK) return DISC_ERR_STATE;
+  DeviceGuard guard(b->device);
+  BCK(benter(b));
+  disc_status st = disc_get_field(b->pair[pair], out, mem_kind);
+  if (st != DISC_OK) return st;
+  BCK(bleave(b));
+  return DISC_OK;
+}
+
+disc_status disc_batch_get_tuning(disc_batch* b, int32_t level, int32_t* items, int32_t* grid,
+                                  int32_t* zmult) {
+  if (!b || level < 0 || level >= b->L) return DISC_ERR_ARG;
+  if (!b->ready[level]) return DISC_ERR_STATE;
+  if (items) *items = b->box_total[level];
+  if (grid) *grid = b->box_grid[level];
+  if (zmult) *zmult = b->zmult[level];
+  return DISC_OK;
+}
+
+}  // extern "C"

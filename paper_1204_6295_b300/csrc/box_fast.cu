@@ -82,8 +82,10 @@ __device__ __forceinline__ float sqrt_approx(float x) {
   return y;
 }
 
+// The CTA body: tile (bx, by) of the 32 x 16 tiling, z chunk bz; part = index
+// of this CTA's norm partials.  Shared by the per-volume and batched launches.
 template <int MODE, int H>
-__global__ void __launch_bounds__(kThreads, 3) k_box_h(BoxArgs a) {
+__device__ __forceinline__ void box_body(const BoxArgs& a, int bx, int by, int bz, size_t part) {
   using B = FastLayout<MODE, H>;
   if (a.stop != nullptr && *(volatile const int*)a.stop != 0) return;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -101,8 +103,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_box_h(BoxArgs a) {
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const int plane = nx * ny;                 // 3 N < 2^31 is checked on the host
   const int N = plane * nz;
-  const int x0 = blockIdx.x * B::TX, y0 = blockIdx.y * B::TY;
-  const int z0 = blockIdx.z * a.zlen;
+  const int x0 = bx * B::TX, y0 = by * B::TY;
+  const int z0 = bz * a.zlen;
   const int z1 = min(nz, z0 + a.zlen);
   const float* __restrict__ src = a.src;
   const float qs = a.qscale, inv_qs = a.inv_qscale, vfl = a.var_floor;
@@ -394,10 +396,33 @@ __global__ void __launch_bounds__(kThreads, 3) k_box_h(BoxArgs a) {
         t0 += red[0][w];
         t1 += red[1][w];
       }
-      const size_t b = (size_t)blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
-      a.partials[2 * b] = t0;
-      a.partials[2 * b + 1] = t1;
+      a.partials[2 * part] = t0;
+      a.partials[2 * part + 1] = t1;
     }
+    __syncthreads();   // red[] is reused by the next body a persistent CTA runs
+  }
+}
+
+template <int MODE, int H>
+__global__ void __launch_bounds__(kThreads, 3) k_box_h(BoxArgs a) {
+  const size_t part = (size_t)blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
+  box_body<MODE, H>(a, blockIdx.x, blockIdx.y, blockIdx.z, part);
+}
+
+// Batched launch over the work table of many volumes: work item i belongs to the
+// volume p with offset[p] <= i < offset[p + 1] and is that volume's CTA
+// i - offset[p] in x-fastest order of its own grid.  With persistent = 1 the
+// grid is smaller than the table and each CTA strides over it.
+template <int MODE, int H>
+__global__ void __launch_bounds__(kThreads, 3) k_box_h_batch(const BoxBatch* __restrict__ bt) {
+  const int total = bt->offset[bt->count];
+  for (int i = blockIdx.x; i < total; i += gridDim.x) {
+    int p = 0;
+    while (p + 1 < bt->count && bt->offset[p + 1] <= i) ++p;
+    const int j = i - bt->offset[p];
+    const dim3 g = bt->grid[p];
+    const int bx = j % g.x, by = (j / g.x) % g.y, bz = j / (g.x * g.y);
+    box_body<MODE, H>(bt->args[p], bx, by, bz, (size_t)j);
   }
 }
 
@@ -499,6 +524,37 @@ size_t box_fast_smem(int mode, int h) {
     case kModeSsdAdjoint: return fast_bytes<kModeSsdAdjoint>(h);
     default: return 0;
   }
+}
+
+cudaError_t box_fast_launch_batch(const BoxBatch* bt_dev, int h, int total, int grid, size_t smem,
+                                  cudaStream_t s) {
+  if (grid < 1) return cudaSuccess;
+  switch (h) {
+#define BCASE(HH)                                                                                   \
+  case HH: {                                                                                        \
+    static int set[kMaxDevices] = {};                                                              \
+    int dev = 0;                                                                                    \
+    cudaError_t e = cudaGetDevice(&dev);                                                            \
+    if (e != cudaSuccess) return e;                                                                 \
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;                               \
+    if (!set[dev]) {                                                                                \
+      e = cudaFuncSetAttribute(k_box_h_batch<kModeIterate, HH>,                                     \
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);            \
+      if (e != cudaSuccess) return e;                                                               \
+      e = cudaFuncSetAttribute(k_box_h_batch<kModeIterate, HH>,                                     \
+                               cudaFuncAttributePreferredSharedMemoryCarveout,                      \
+                               (int)cudaSharedmemCarveoutMaxShared);                                \
+      if (e != cudaSuccess) return e;                                                               \
+      set[dev] = 1;                                                                                 \
+    }                                                                                               \
+    k_box_h_batch<kModeIterate, HH><<<grid, kThreads, smem, s>>>(bt_dev);                           \
+    return cudaGetLastError();                                                                      \
+  }
+    BCASE(1) BCASE(2) BCASE(3) BCASE(4) BCASE(5) BCASE(6) BCASE(7)
+#undef BCASE
+    default: return cudaErrorInvalidValue;
+  }
+  (void)total;
 }
 
 int box_fast_occupancy(int mode, int h, size_t smem) {

@@ -164,7 +164,7 @@ struct XYLayout {
 };
 
 template <int R>
-__global__ void __launch_bounds__(kThreads) k_gauss_xy(GaussArgs a) {
+__device__ __forceinline__ void gauss_xy_body(const GaussArgs& a, int bx, int by, int bz) {
   using X = XYLayout<R>;
   if (a.stop != nullptr && *(volatile const int*)a.stop != 0) return;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(kThreads) k_gauss_xy(GaussArgs a) {
   const int nx = a.nx, ny = a.ny;
   const size_t plane = (size_t)nx * ny;
   const size_t N = plane * a.nz;
-  const int x0 = blockIdx.x * kSX, y0 = blockIdx.y * kSY, z = blockIdx.z;
+  const int x0 = bx * kSX, y0 = by * kSY, z = bz;
   float w[2 * R + 1];
 #pragma unroll
   for (int k = 0; k <= 2 * R; ++k) w[k] = a.w[k];
@@ -301,17 +301,38 @@ __global__ void __launch_bounds__(kThreads) k_gauss_xy(GaussArgs a) {
   }
 }
 
+template <int R>
+__global__ void __launch_bounds__(kThreads) k_gauss_xy(GaussArgs a) {
+  gauss_xy_body<R>(a, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Work item i of a batched launch -> (volume p, CTA coordinates in p's grid).
+__device__ __forceinline__ int batch_find(const int* offset, int count, int i) {
+  int p = 0;
+  while (p + 1 < count && offset[p + 1] <= i) ++p;
+  return p;
+}
+
+template <int R>
+__global__ void __launch_bounds__(kThreads) k_gauss_xy_batch(const GaussBatch* __restrict__ bt) {
+  const int i = blockIdx.x;
+  const int p = batch_find(bt->offset, bt->count, i);
+  const int j = i - bt->offset[p];
+  const dim3 g = bt->grid[p];
+  gauss_xy_body<R>(bt->args[p], j % g.x, (j / g.x) % g.y, j / (g.x * g.y));
+}
+
 // z pass with a register queue; WARP also evaluates m = I_m(x + r(x)).
 template <int R, bool WARP>
-__global__ void __launch_bounds__(kZThreads) k_gauss_z(GaussArgs a) {
+__device__ __forceinline__ void gauss_z_body(const GaussArgs& a, int bx, int by, int bz) {
   constexpr int KZ = 2 * R + 1;
   if (a.stop != nullptr && *(volatile const int*)a.stop != 0) return;
   const int nx = a.nx, ny = a.ny, nz = a.nz;
-  const int x = blockIdx.x * kZThreads + threadIdx.x, y = blockIdx.y;
+  const int x = bx * kZThreads + threadIdx.x, y = by;
   if (x >= nx) return;
   const size_t plane = (size_t)nx * ny;
   const size_t N = plane * nz;
-  const int z0 = blockIdx.z * a.zlen;
+  const int z0 = bz * a.zlen;
   const int z1 = min(nz, z0 + a.zlen);
   float w[KZ];
 #pragma unroll
@@ -377,6 +398,49 @@ __global__ void __launch_bounds__(kZThreads) k_gauss_z(GaussArgs a) {
   }
 }
 
+template <int R, bool WARP>
+__global__ void __launch_bounds__(kZThreads) k_gauss_z(GaussArgs a) {
+  gauss_z_body<R, WARP>(a, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+template <int R, bool WARP>
+__global__ void __launch_bounds__(kZThreads) k_gauss_z_batch(const GaussBatch* __restrict__ bt) {
+  const int i = blockIdx.x;
+  const int p = batch_find(bt->offset, bt->count, i);
+  const int j = i - bt->offset[p];
+  const dim3 g = bt->grid[p];
+  gauss_z_body<R, WARP>(bt->args[p], j % g.x, (j / g.x) % g.y, j / (g.x * g.y));
+}
+
+template <int R>
+cudaError_t launch_batch_r(const GaussBatch* xy, int xy_total, const GaussBatch* z, int z_total, bool warp,
+                           cudaStream_t s) {
+  static int set[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!set[dev]) {
+    e = cudaFuncSetAttribute(k_gauss_xy_batch<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)XYLayout<R>::bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_gauss_xy_batch<R>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    set[dev] = 1;
+  }
+  if (xy_total > 0) k_gauss_xy_batch<R><<<xy_total, kThreads, XYLayout<R>::bytes, s>>>(xy);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (z_total > 0) {
+    if (warp)
+      k_gauss_z_batch<R, true><<<z_total, kZThreads, 0, s>>>(z);
+    else
+      k_gauss_z_batch<R, false><<<z_total, kZThreads, 0, s>>>(z);
+  }
+  return cudaGetLastError();
+}
+
 template <int R>
 cudaError_t launch_split(const GaussArgs& a, const GaussPlan& p, cudaStream_t s) {
   static int set[64] = {};
@@ -421,6 +485,21 @@ cudaError_t launch_split_any(const GaussArgs& a, const GaussPlan& p, cudaStream_
   }
 }
 }  // namespace
+
+cudaError_t gauss_launch_batch(const GaussBatch* xy_dev, int xy_total, const GaussBatch* z_dev, int z_total,
+                               int R, bool warp, cudaStream_t s) {
+  switch (R) {
+#define BCASE(RR) case RR: return launch_batch_r<RR>(xy_dev, xy_total, z_dev, z_total, warp, s);
+    BCASE(1) BCASE(2) BCASE(3) BCASE(4) BCASE(5) BCASE(6) BCASE(7) BCASE(8)
+#undef BCASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+void gauss_grids(int nx, int ny, int nz, const GaussPlan& p, dim3* xy, dim3* z) {
+  *xy = dim3((nx + kSX - 1) / kSX, (ny + kSY - 1) / kSY, nz);
+  *z = dim3((nx + kZThreads - 1) / kZThreads, ny, (nz + p.zlen - 1) / p.zlen);
+}
 
 int gauss_radius(float sigma, int radius) {
   if (radius > 0) return radius;

@@ -63,7 +63,19 @@ struct BoxPlan {
   bool fast;            // cubic-patch kernel specialised on the half size (box_fast.cu)
 };
 
+// Work table of a batched launch over many volumes (pairs): volume p owns the
+// work items offset[p] .. offset[p+1]-1, which are the CTAs of its own grid.
+constexpr int kMaxBatch = 64;
+struct BoxBatch {
+  int count;
+  int offset[kMaxBatch + 1];
+  dim3 grid[kMaxBatch];
+  BoxArgs args[kMaxBatch];
+};
+
 // Specialised cubic-patch path (box_fast.cu)
+cudaError_t box_fast_launch_batch(const BoxBatch* bt_dev, int h, int total, int grid, size_t smem,
+                                  cudaStream_t s);
 bool box_fast_ok(int nx, int ny, int nz, int hx, int hy, int hz);
 size_t box_fast_smem(int mode, int h);
 int box_fast_occupancy(int mode, int h, size_t smem);
@@ -99,6 +111,19 @@ struct GaussPlan {
   int zlen;
   bool queue;           // register-queue kernel (radius 1..8) or the generic one
 };
+struct GaussBatch {
+  int count;
+  int offset[kMaxBatch + 1];
+  dim3 grid[kMaxBatch];
+  GaussArgs args[kMaxBatch];
+};
+// Batched Gaussian passes over many volumes (gauss.cu): the xy pass (u -> t) and
+// the z pass (t -> r, and m if args.m) with one launch each.  Work items follow
+// each volume's own grids (xy: tiles x planes; z: column blocks x rows x chunks).
+cudaError_t gauss_launch_batch(const GaussBatch* xy_dev, int xy_total, const GaussBatch* z_dev, int z_total,
+                               int R, bool warp, cudaStream_t s);
+void gauss_grids(int nx, int ny, int nz, const GaussPlan& p, dim3* xy, dim3* z);
+
 int gauss_radius(float sigma, int radius);
 void gauss_taps(float sigma, int R, float* w);
 GaussPlan gauss_plan(int nx, int ny, int nz, int R, int num_sms);
@@ -133,6 +158,26 @@ struct NormState {
   float eps;
 };
 cudaError_t launch_norm_finalize(const float* partials, int nparts, NormState st, cudaStream_t s);
+// One block per volume: NormState and partials of volume p in the tables.
+struct NormBatch {
+  int count;
+  const float* partials[kMaxBatch];
+  int nparts[kMaxBatch];
+  NormState st[kMaxBatch];
+};
+cudaError_t launch_norm_finalize_batch(const NormBatch* nb_dev, int count, cudaStream_t s);
+// Warp of many volumes in one launch (warp.cu); args: Im, r, m, dims per volume.
+struct WarpBatch {
+  int count;
+  int offset[kMaxBatch + 1];
+  const float* Im[kMaxBatch];
+  const float* r[kMaxBatch];
+  float* m[kMaxBatch];
+  int nx[kMaxBatch], ny[kMaxBatch], nz[kMaxBatch];
+  const int* stop[kMaxBatch];
+};
+cudaError_t launch_warp_batch(const WarpBatch* wb_dev, int total_blocks, cudaStream_t s);
+constexpr int kWarpBatchThreads = 128;
 // Deterministic fixed-order sum of per-CTA float partials (stride 2, component c) into *out.
 cudaError_t launch_partials_sum(const float* partials, int nparts, int comp, double* out,
                                 cudaStream_t s);

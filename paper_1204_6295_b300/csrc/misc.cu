@@ -138,7 +138,7 @@ __global__ void k_up2(const float* __restrict__ rc, float* __restrict__ rf, int 
 }
 
 // l^(k) = sum|dr| / sum|r| (Sec. 2.3) from per-CTA partials; history and stop flag.
-__global__ void k_norm_finalize(const float* partials, int nparts, NormState st) {
+__device__ __forceinline__ void norm_finalize_body(const float* partials, int nparts, const NormState& st) {
   if (*(volatile int*)st.stop != 0) return;
   __shared__ double sh[kRedThreads / 32];
   double sdr = 0.0, sr = 0.0;
@@ -158,6 +158,16 @@ __global__ void k_norm_finalize(const float* partials, int nparts, NormState st)
       if (isfinite(lp) && isfinite(l) && lp - l <= st.eps) *st.stop = 1;
     }
   }
+}
+
+__global__ void k_norm_finalize(const float* partials, int nparts, NormState st) {
+  norm_finalize_body(partials, nparts, st);
+}
+
+// One block per volume of a batch.
+__global__ void k_norm_finalize_batch(const NormBatch* __restrict__ nb) {
+  const int p = blockIdx.x;
+  norm_finalize_body(nb->partials[p], nb->nparts[p], nb->st[p]);
 }
 
 __global__ void k_partials_sum(const float* partials, int nparts, int comp, double* out) {
@@ -208,6 +218,12 @@ cudaError_t launch_up2(const float* rc, float* rf, int nx, int ny, int nz, cudaS
 
 cudaError_t launch_norm_finalize(const float* partials, int nparts, NormState st, cudaStream_t s) {
   k_norm_finalize<<<1, kRedThreads, 0, s>>>(partials, nparts, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_norm_finalize_batch(const NormBatch* nb_dev, int count, cudaStream_t s) {
+  if (count < 1) return cudaSuccess;
+  k_norm_finalize_batch<<<count, kRedThreads, 0, s>>>(nb_dev);
   return cudaGetLastError();
 }
 

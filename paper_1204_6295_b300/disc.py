@@ -71,6 +71,13 @@ _SIGS = {
     "disc_get_norm_history": (_st, [_vp, _i32, _vp, _i32, ctypes.POINTER(_i32)]),
     "disc_destroy": (_st, [_vp]),
     "disc_qscale": (_f32, [_f32, ctypes.POINTER(_i32)]),
+    "disc_batch_create": (_st, [ctypes.POINTER(Params), ctypes.c_int, _vp, _i32, ctypes.POINTER(_vp)]),
+    "disc_batch_set_images": (_st, [_vp, _i32, _vp, _vp, _i32, _i32, _i32, ctypes.c_int]),
+    "disc_batch_restart": (_st, [_vp]),
+    "disc_batch_iterate": (_st, [_vp, _i32, ctypes.POINTER(_i32)]),
+    "disc_batch_get_field": (_st, [_vp, _i32, _vp, ctypes.c_int]),
+    "disc_batch_get_tuning": (_st, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
+    "disc_batch_destroy": (_st, [_vp]),
     "disc_k_max_abs": (_st, [_vp, _i64, _vp, _vp]),
     "disc_k_global_shift": (_st, [_vp, _vp, _vp, _i64, _vp, _vp]),
     "disc_k_downsample2": (_st, [_vp, _vp, _i32, _i32, _i32, _vp]),
@@ -255,6 +262,69 @@ class Registration:
         _check(_lib.disc_get_norm_history(self._h, int(level), out.ctypes.data, cap, ctypes.byref(n)),
                "disc_get_norm_history")
         return out[:n.value].copy()
+
+
+class Batch:
+    """Many pairs advanced together (disc_batch_create .. disc_batch_destroy)."""
+
+    def __init__(self, npairs, params: Params | None = None, device=0, stream=None, **kw):
+        if params is None:
+            params = make_params(**kw)
+        self.params = params
+        self.npairs = int(npairs)
+        h = _vp()
+        _check(_lib.disc_batch_create(ctypes.byref(params), device, _stream(stream), self.npairs,
+                                      ctypes.byref(h)), "disc_batch_create")
+        self._h = h
+        self.dims = [None] * self.npairs
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.disc_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_images(self, pair, ct, cbct):
+        nz, ny, nx = ct.shape
+        _f32_check(ct, (nz, ny, nx), "ct")
+        _f32_check(cbct, (nz, ny, nx), "cbct")
+        kind = _mem_kind(ct)
+        _check(_lib.disc_batch_set_images(self._h, int(pair), _ptr(ct), _ptr(cbct), nx, ny, nz, kind),
+               "disc_batch_set_images")
+        self.dims[pair] = (nx, ny, nz)
+
+    def restart(self):
+        _check(_lib.disc_batch_restart(self._h), "disc_batch_restart")
+
+    def iterate(self, max_iters=-1):
+        done = _i32(0)
+        _check(_lib.disc_batch_iterate(self._h, int(max_iters), ctypes.byref(done)), "disc_batch_iterate")
+        return int(done.value)
+
+    def get_field(self, pair, out=None):
+        nx, ny, nz = self.dims[pair]
+        if out is None:
+            out = np.empty((3, nz, ny, nx), np.float32)
+        _f32_check(out, (3, nz, ny, nx), "out")
+        _check(_lib.disc_batch_get_field(self._h, int(pair), _ptr(out), _mem_kind(out)), "disc_batch_get_field")
+        return out
+
+    def tuning(self, level):
+        items, grid, zmult = _i32(0), _i32(0), _i32(0)
+        _check(_lib.disc_batch_get_tuning(self._h, int(level), ctypes.byref(items), ctypes.byref(grid),
+                                          ctypes.byref(zmult)), "disc_batch_get_tuning")
+        return int(items.value), int(grid.value), int(zmult.value)
 
 
 # ---------------------------------------------------------------------------

@@ -150,13 +150,11 @@ class _HeadAnatomy:
         s_body = radius(self.body)
         in_body = _smooth_inside(s_body, edge_mm / self.body.min())
         # soft tissue: piecewise-constant regions (nearest seed)
-        best = np.full(x.shape, np.inf)
-        tissue = np.full(x.shape, self.body_hu)
-        for k in range(self.seeds.shape[0]):
-            d = (px - self.seeds[k, 0]) ** 2 + (py - self.seeds[k, 1]) ** 2 + (pz - self.seeds[k, 2]) ** 2
-            closer = d < best
-            best = np.where(closer, d, best)
-            tissue = np.where(closer, self.seed_hu[k], tissue)
+        d = ((px[None] - self.seeds[:, 0, None, None, None]) ** 2
+             + (py[None] - self.seeds[:, 1, None, None, None]) ** 2
+             + (pz[None] - self.seeds[:, 2, None, None, None]) ** 2)
+        tissue = self.seed_hu[np.argmin(d, axis=0)]
+        del d
         s_in = radius(self.inner)
         inside_skull = _smooth_inside(s_in, edge_mm / self.inner.min())
         soft = self.body_hu * (1.0 - inside_skull) + tissue * inside_skull
@@ -187,14 +185,22 @@ def _draw_modes(rng, n_modes=6):
 
 
 def _eval_modes(modes, x, y, z, dims):
-    """Raw (unscaled) field components at the given grid points."""
+    """Raw (unscaled) field components at the grid points of a z-slab.
+
+    ``x, y, z`` are the meshgrid coordinates of the slab (only their 1-D axes
+    are used): each mode sin(2 pi (kx x/nx + ky y/ny + kz z/nz) + ph) is the
+    imaginary part of a product of three 1-D complex exponentials.
+    """
     nx, ny, nz = dims
+    xs, ys, zs = x[0, 0, :], y[0, :, 0], z[:, 0, 0]
     out = []
     for k, ph, amp in modes:
         acc = np.zeros(x.shape)
         for i in range(k.shape[0]):
-            acc += amp[i] * np.sin(2 * math.pi * (k[i, 0] * x / nx + k[i, 1] * y / ny
-                                                  + k[i, 2] * z / nz) + ph[i])
+            ex = np.exp(2j * math.pi * k[i, 0] * xs / nx)
+            ey = np.exp(2j * math.pi * k[i, 1] * ys / ny)
+            ez = np.exp(2j * math.pi * k[i, 2] * zs / nz) * (amp[i] * np.exp(1j * ph[i]))
+            acc += (ez[:, None, None] * ey[None, :, None] * ex[None, None, :]).imag
         out.append(acc)
     return out
 
