@@ -292,6 +292,79 @@ def time_differentiable(disc, torch, w, pair_dev, field_dev, kt, reps=5):
                     "workload), patch statistics recomputed in the backward pass"}
 
 
+BATCH_WORKLOAD = dict(patch=(9, 9, 9), sigma=1.5, levels=3, iters=(100, 100, 100))
+
+
+def time_batched(disc, torch, dist, steps=2):
+    """The batched workload: 16 pairs of uneven size advanced together, against
+    the plain per-pair loop over the same pairs (separate contexts, one after the
+    other), both timed with CUDA events on the current stream."""
+    from paper_1204_6295_b300 import phantom
+    images = phantom.batch_pair_images()
+    bw = BATCH_WORKLOAD
+    units = 0
+    for ct, _ in images:
+        nz, ny, nx = ct.shape
+        units += schedule_units(dict(bw, dims=(nx, ny, nz)))
+    s = torch.cuda.current_stream()
+
+    def timed(step):
+        step()                                    # warm-up (the batch also tunes here)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(steps):
+            step()
+        e1.record(s)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / steps / 1e3
+        if dist:
+            tt = torch.tensor([t], device="cuda", dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t = float(tt.item())
+        return t
+
+    batch = disc.Batch(len(images), **bw)
+    for i, (ct, cbct) in enumerate(images):
+        batch.set_images(i, ct, cbct)
+
+    def batch_step():
+        batch.restart()
+        batch.iterate(-1)
+
+    t_batch = timed(batch_step)
+    tuning = [batch.tuning(l) for l in range(bw["levels"])]
+    batch.close()
+    regs = []
+    for ct, cbct in images:
+        reg = disc.Registration(**bw)
+        reg.set_images(ct, cbct)
+        nz, ny, nx = ct.shape
+        cz, cy, cx = level_dims((nx, ny, nz), bw["levels"])[-1][::-1]
+        regs.append((reg, torch.zeros((3, cz, cy, cx), dtype=torch.float32, device="cuda")))
+
+    def loop_step():
+        for reg, z in regs:
+            reg.set_field(bw["levels"] - 1, z)
+            reg.iterate(-1, sync=False)
+
+    t_loop = timed(loop_step)
+    for reg, _ in regs:
+        reg.close()
+    world = dist.get_world_size() if dist else 1
+    return {"value": world * units / t_batch / 1e9, "unit": UNIT,
+            "plain_loop_value": world * units / t_loop / 1e9,
+            "speedup_vs_plain_loop": t_loop / t_batch, "ms_per_step": t_batch * 1e3,
+            "plain_loop_ms_per_step": t_loop * 1e3, "voxel_iterations_per_step": units,
+            "pairs": [list(ct.shape[::-1]) for ct, _ in images],
+            "tuning_items_grid_zmult_per_level_fine_first": tuning,
+            "what": "16 head-and-neck pairs (2s, 2s, s), s in 64..160, patch 9^3, sigma 1.5, "
+                    "3 levels x 100 iterations: disc_batch (one launch per step over all pairs, "
+                    "graph per level) vs 16 separate contexts run one after the other"}
+
+
 def run_ours(args, w, rank, world, local_rank):
     import numpy as np
     import torch
@@ -352,6 +425,8 @@ def run_ours(args, w, rank, world, local_rank):
     warp_gbs = WARP_BYTES_PER_VOXEL * kt["N"] / kt["warp_s"] / 1e9
     traffic = recorded_traffic(args.workload)
 
+    batched = None if args.no_batched else time_batched(disc, torch, dist)
+
     # end to end through the public API with host buffers (pinned)
     ct_h = torch.from_numpy(pair.ct).pin_memory()
     cbct_h = torch.from_numpy(pair.cbct).pin_memory()
@@ -409,6 +484,7 @@ def run_ours(args, w, rank, world, local_rank):
                     "warp": {"achieved_gbs": warp_gbs, "frac": warp_gbs / peak, "launch_ms": kt["warp_s"] * 1e3,
                              "algorithmic_bytes_per_voxel": WARP_BYTES_PER_VOXEL}},
         "forms": {"plain": {"value": value, "unit": UNIT},
+                  "batched": batched,
                   "differentiable": diff_form,
                   "effective_hbm_frac_32B_model": value * 1e9 * 32 / (peak * 1e9)},
         "e2e": e2e,
@@ -457,6 +533,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 16-pair batched form")
     ap.add_argument("--profile-once", action="store_true",
                     help="launch each per-iteration kernel once at the finest level and exit")
     args = ap.parse_args()

@@ -185,8 +185,10 @@ disc_status disc_batch_iterate(disc_batch* b, int32_t max_iters, int32_t* iters_
 disc_status disc_batch_get_field(disc_batch* b, int32_t pair, float* out, int mem_kind);
 
 /* Tuning chosen for `level`: work items of the moment/force launch, its grid
- * (equal to items, or one wave of persistent CTAs), and the z-chunk
- * lengthening factor.  DISC_ERR_STATE before the level has run. */
+ * (equal to items, or one wave of persistent CTAs), and the z chunking: a
+ * positive value k lengthens each pair's single-pair chunk k times, a
+ * negative value -c sets chunks of c planes (capped at each pair's depth).
+ * DISC_ERR_STATE before the level has run. */
 disc_status disc_batch_get_tuning(disc_batch* b, int32_t level, int32_t* items, int32_t* grid,
                                   int32_t* zmult);
 

@@ -27,12 +27,12 @@ struct disc_batch {
   int npairs = 0;
   disc_ctx* pair[kMaxBatch] = {};
   int L = 0, H = 0, R = 0;
-  // device work tables per level
-  BoxBatch* d_box[DISC_MAX_LEVELS] = {};
-  GaussBatch* d_xy[DISC_MAX_LEVELS] = {};
-  GaussBatch* d_z[DISC_MAX_LEVELS] = {};
-  NormBatch* d_norm[DISC_MAX_LEVELS] = {};
-  WarpBatch* d_warp[DISC_MAX_LEVELS] = {};
+  // work tables per level (kernel parameters of the batched launches)
+  BoxBatch box[DISC_MAX_LEVELS];
+  GaussBatch xy[DISC_MAX_LEVELS];
+  GaussBatch zt[DISC_MAX_LEVELS];
+  NormBatch norm[DISC_MAX_LEVELS];
+  WarpBatch warp[DISC_MAX_LEVELS];
   int box_total[DISC_MAX_LEVELS] = {}, box_grid[DISC_MAX_LEVELS] = {}, zmult[DISC_MAX_LEVELS] = {};
   int xy_total[DISC_MAX_LEVELS] = {}, z_total[DISC_MAX_LEVELS] = {}, warp_total[DISC_MAX_LEVELS] = {};
   bool ready[DISC_MAX_LEVELS] = {};
@@ -81,9 +81,11 @@ bool all_images(const disc_batch* b) {
   return true;
 }
 
-// Box-pass work table of level l with every pair's z chunks lengthened zmult times.
-cudaError_t upload_box_table(disc_batch* b, int l, int zmult, int* total) {
-  BoxBatch h;
+// Box-pass work table of level l.  zmult > 0: every pair's single-pair z chunk
+// lengthened zmult times; zmult < 0: chunks of -zmult planes (at least the
+// single-pair chunk, so that no pair gets more CTAs than its partials hold).
+void make_box_table(disc_batch* b, int l, int zmult, int* total) {
+  BoxBatch& h = b->box[l];
   std::memset(&h, 0, sizeof(h));
   h.count = b->npairs;
   int off = 0;
@@ -91,7 +93,7 @@ cudaError_t upload_box_table(disc_batch* b, int l, int zmult, int* total) {
     const disc_ctx* c = b->pair[i];
     const Level& v = c->lev[l];
     BoxArgs a = ctx_box_args(c, l);
-    a.zlen = v.pa.zlen * zmult;
+    a.zlen = zmult > 0 ? v.pa.zlen * zmult : (-zmult > v.pa.zlen ? -zmult : v.pa.zlen);
     if (a.zlen > v.nz) a.zlen = v.nz;
     h.args[i] = a;
     h.grid[i] = dim3(v.pa.grid.x, v.pa.grid.y, (v.nz + a.zlen - 1) / a.zlen);
@@ -100,10 +102,8 @@ cudaError_t upload_box_table(disc_batch* b, int l, int zmult, int* total) {
   }
   h.offset[b->npairs] = off;
   *total = off;
-  cudaError_t e = cudaMemcpyAsync(b->d_box[l], &h, sizeof(h), cudaMemcpyHostToDevice, b->s);
-  if (e != cudaSuccess) return e;
   // norm table: the same CTA counts
-  NormBatch n;
+  NormBatch& n = b->norm[l];
   std::memset(&n, 0, sizeof(n));
   n.count = b->npairs;
   for (int i = 0; i < b->npairs; ++i) {
@@ -111,23 +111,12 @@ cudaError_t upload_box_table(disc_batch* b, int l, int zmult, int* total) {
     n.nparts[i] = h.offset[i + 1] - h.offset[i];
     n.st[i] = ctx_norm_state(b->pair[i], l);
   }
-  e = cudaMemcpyAsync(b->d_norm[l], &n, sizeof(n), cudaMemcpyHostToDevice, b->s);
-  if (e != cudaSuccess) return e;
-  return cudaStreamSynchronize(b->s);   // the host tables are stack objects
 }
 
-cudaError_t build_tables(disc_batch* b, int l) {
-  cudaError_t e;
-  if (!b->d_box[l]) {
-    e = cudaMalloc(&b->d_box[l], sizeof(BoxBatch));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_xy[l], sizeof(GaussBatch));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_z[l], sizeof(GaussBatch));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_norm[l], sizeof(NormBatch));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_warp[l], sizeof(WarpBatch));
-    if (e != cudaSuccess) return e;
-  }
-  GaussBatch xy, z;
-  WarpBatch w;
+void build_tables(disc_batch* b, int l) {
+  GaussBatch& xy = b->xy[l];
+  GaussBatch& z = b->zt[l];
+  WarpBatch& w = b->warp[l];
   std::memset(&xy, 0, sizeof(xy));
   std::memset(&z, 0, sizeof(z));
   std::memset(&w, 0, sizeof(w));
@@ -165,11 +154,6 @@ cudaError_t build_tables(disc_batch* b, int l) {
   b->xy_total[l] = oxy;
   b->z_total[l] = oz;
   b->warp_total[l] = ow;
-  e = cudaMemcpyAsync(b->d_xy[l], &xy, sizeof(xy), cudaMemcpyHostToDevice, b->s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_z[l], &z, sizeof(z), cudaMemcpyHostToDevice, b->s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_warp[l], &w, sizeof(w), cudaMemcpyHostToDevice, b->s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(b->s);
-  return e;
 }
 
 size_t box_smem(const disc_batch* b) { return box_fast_smem(kModeIterate, b->H); }
@@ -192,18 +176,19 @@ cudaError_t tune_level(disc_batch* b, int l) {
   }
   float best = 1e30f;
   int best_mult = 1, best_grid = 0;
-  const int mults[3] = {1, 2, 4};
-  for (int mi = 0; mi < 3 && e == cudaSuccess; ++mi) {
+  // single-pair chunks, twice and four times longer, and common chunk lengths of
+  // 32, 64 planes and whole columns (1 << 20: capped at each pair's depth)
+  const int mults[6] = {1, 2, 4, -32, -64, -(1 << 20)};
+  for (int mi = 0; mi < 6 && e == cudaSuccess; ++mi) {
     int total = 0;
-    e = upload_box_table(b, l, mults[mi], &total);
-    if (e != cudaSuccess) break;
+    make_box_table(b, l, mults[mi], &total);
     const int grids[2] = {total, total < slots ? total : slots};
     for (int gi = 0; gi < 2 && e == cudaSuccess; ++gi) {
       if (gi == 1 && grids[1] == grids[0]) continue;
-      e = box_fast_launch_batch(b->d_box[l], b->H, total, grids[gi], smem, b->s);   // warm-up
+      e = box_fast_launch_batch(b->box[l], b->H, total, grids[gi], smem, b->s);   // warm-up
       if (e == cudaSuccess) e = cudaEventRecord(e0, b->s);
       for (int k = 0; k < 3 && e == cudaSuccess; ++k)
-        e = box_fast_launch_batch(b->d_box[l], b->H, total, grids[gi], smem, b->s);
+        e = box_fast_launch_batch(b->box[l], b->H, total, grids[gi], smem, b->s);
       if (e == cudaSuccess) e = cudaEventRecord(e1, b->s);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
       float ms = 0.0f;
@@ -219,8 +204,7 @@ cudaError_t tune_level(disc_batch* b, int l) {
   cudaEventDestroy(e1);
   if (e != cudaSuccess) return e;
   int total = 0;
-  e = upload_box_table(b, l, best_mult, &total);
-  if (e != cudaSuccess) return e;
+  make_box_table(b, l, best_mult, &total);
   b->zmult[l] = best_mult;
   b->box_total[l] = total;
   b->box_grid[l] = best_grid;
@@ -228,13 +212,13 @@ cudaError_t tune_level(disc_batch* b, int l) {
 }
 
 cudaError_t queue_batch_iterations(disc_batch* b, int l, int n) {
-  cudaError_t e = launch_warp_batch(b->d_warp[l], b->warp_total[l], b->s);
+  cudaError_t e = launch_warp_batch(b->warp[l], b->warp_total[l], b->s);
   const size_t smem = box_smem(b);
   for (int k = 0; k < n && e == cudaSuccess; ++k) {
-    e = box_fast_launch_batch(b->d_box[l], b->H, b->box_total[l], b->box_grid[l], smem, b->s);
+    e = box_fast_launch_batch(b->box[l], b->H, b->box_total[l], b->box_grid[l], smem, b->s);
     if (e == cudaSuccess)
-      e = gauss_launch_batch(b->d_xy[l], b->xy_total[l], b->d_z[l], b->z_total[l], b->R, true, b->s);
-    if (e == cudaSuccess) e = launch_norm_finalize_batch(b->d_norm[l], b->npairs, b->s);
+      e = gauss_launch_batch(b->xy[l], b->xy_total[l], b->zt[l], b->z_total[l], b->R, true, b->s);
+    if (e == cudaSuccess) e = launch_norm_finalize_batch(b->norm[l], b->npairs, b->s);
   }
   return e;
 }
@@ -312,14 +296,8 @@ disc_status disc_batch_destroy(disc_batch* b) {
   if (!b) return DISC_OK;
   DeviceGuard guard(b->device);
   if (b->s) cudaStreamSynchronize(b->s);
-  for (int l = 0; l < DISC_MAX_LEVELS; ++l) {
+  for (int l = 0; l < DISC_MAX_LEVELS; ++l)
     if (b->graph[l]) cudaGraphExecDestroy(b->graph[l]);
-    cudaFree(b->d_box[l]);
-    cudaFree(b->d_xy[l]);
-    cudaFree(b->d_z[l]);
-    cudaFree(b->d_norm[l]);
-    cudaFree(b->d_warp[l]);
-  }
   for (int i = 0; i < b->npairs; ++i) disc_destroy(b->pair[i]);
   if (b->ev_in) cudaEventDestroy(b->ev_in);
   if (b->ev_out) cudaEventDestroy(b->ev_out);
@@ -378,8 +356,8 @@ disc_status disc_batch_iterate(disc_batch* b, int32_t max_iters, int32_t* iters_
     const int left = total - b->cur_iter;
     if (left > 0 && budget > 0) {
       if (!b->ready[l]) {
-        BCK(build_tables(b, l));
-        BCK(launch_warp_batch(b->d_warp[l], b->warp_total[l], b->s));   // m for the tuning launches
+        build_tables(b, l);
+        BCK(launch_warp_batch(b->warp[l], b->warp_total[l], b->s));     // m for the tuning launches
         BCK(tune_level(b, l));
         b->ready[l] = true;
       }

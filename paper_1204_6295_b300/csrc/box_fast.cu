@@ -414,15 +414,15 @@ __global__ void __launch_bounds__(kThreads, 3) k_box_h(BoxArgs a) {
 // i - offset[p] in x-fastest order of its own grid.  With persistent = 1 the
 // grid is smaller than the table and each CTA strides over it.
 template <int MODE, int H>
-__global__ void __launch_bounds__(kThreads, 3) k_box_h_batch(const BoxBatch* __restrict__ bt) {
-  const int total = bt->offset[bt->count];
+__global__ void __launch_bounds__(kThreads, 3) k_box_h_batch(const __grid_constant__ BoxBatch bt) {
+  const int total = bt.offset[bt.count];
   for (int i = blockIdx.x; i < total; i += gridDim.x) {
     int p = 0;
-    while (p + 1 < bt->count && bt->offset[p + 1] <= i) ++p;
-    const int j = i - bt->offset[p];
-    const dim3 g = bt->grid[p];
+    while (p + 1 < bt.count && bt.offset[p + 1] <= i) ++p;
+    const int j = i - bt.offset[p];
+    const dim3 g = bt.grid[p];
     const int bx = j % g.x, by = (j / g.x) % g.y, bz = j / (g.x * g.y);
-    box_body<MODE, H>(bt->args[p], bx, by, bz, (size_t)j);
+    box_body<MODE, H>(bt.args[p], bx, by, bz, (size_t)j);
   }
 }
 
@@ -526,7 +526,7 @@ size_t box_fast_smem(int mode, int h) {
   }
 }
 
-cudaError_t box_fast_launch_batch(const BoxBatch* bt_dev, int h, int total, int grid, size_t smem,
+cudaError_t box_fast_launch_batch(const BoxBatch& bt, int h, int total, int grid, size_t smem,
                                   cudaStream_t s) {
   if (grid < 1) return cudaSuccess;
   switch (h) {
@@ -547,7 +547,7 @@ cudaError_t box_fast_launch_batch(const BoxBatch* bt_dev, int h, int total, int 
       if (e != cudaSuccess) return e;                                                               \
       set[dev] = 1;                                                                                 \
     }                                                                                               \
-    k_box_h_batch<kModeIterate, HH><<<grid, kThreads, smem, s>>>(bt_dev);                           \
+    k_box_h_batch<kModeIterate, HH><<<grid, kThreads, smem, s>>>(bt);                               \
     return cudaGetLastError();                                                                      \
   }
     BCASE(1) BCASE(2) BCASE(3) BCASE(4) BCASE(5) BCASE(6) BCASE(7)

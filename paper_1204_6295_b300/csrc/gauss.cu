@@ -314,12 +314,12 @@ __device__ __forceinline__ int batch_find(const int* offset, int count, int i) {
 }
 
 template <int R>
-__global__ void __launch_bounds__(kThreads) k_gauss_xy_batch(const GaussBatch* __restrict__ bt) {
+__global__ void __launch_bounds__(kThreads) k_gauss_xy_batch(const __grid_constant__ GaussBatch bt) {
   const int i = blockIdx.x;
-  const int p = batch_find(bt->offset, bt->count, i);
-  const int j = i - bt->offset[p];
-  const dim3 g = bt->grid[p];
-  gauss_xy_body<R>(bt->args[p], j % g.x, (j / g.x) % g.y, j / (g.x * g.y));
+  const int p = batch_find(bt.offset, bt.count, i);
+  const int j = i - bt.offset[p];
+  const dim3 g = bt.grid[p];
+  gauss_xy_body<R>(bt.args[p], j % g.x, (j / g.x) % g.y, j / (g.x * g.y));
 }
 
 // z pass with a register queue; WARP also evaluates m = I_m(x + r(x)).
@@ -399,21 +399,21 @@ __device__ __forceinline__ void gauss_z_body(const GaussArgs& a, int bx, int by,
 }
 
 template <int R, bool WARP>
-__global__ void __launch_bounds__(kZThreads) k_gauss_z(GaussArgs a) {
+__global__ void __launch_bounds__(kZThreads, 4) k_gauss_z(GaussArgs a) {
   gauss_z_body<R, WARP>(a, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 template <int R, bool WARP>
-__global__ void __launch_bounds__(kZThreads) k_gauss_z_batch(const GaussBatch* __restrict__ bt) {
+__global__ void __launch_bounds__(kZThreads, 4) k_gauss_z_batch(const __grid_constant__ GaussBatch bt) {
   const int i = blockIdx.x;
-  const int p = batch_find(bt->offset, bt->count, i);
-  const int j = i - bt->offset[p];
-  const dim3 g = bt->grid[p];
-  gauss_z_body<R, WARP>(bt->args[p], j % g.x, (j / g.x) % g.y, j / (g.x * g.y));
+  const int p = batch_find(bt.offset, bt.count, i);
+  const int j = i - bt.offset[p];
+  const dim3 g = bt.grid[p];
+  gauss_z_body<R, WARP>(bt.args[p], j % g.x, (j / g.x) % g.y, j / (g.x * g.y));
 }
 
 template <int R>
-cudaError_t launch_batch_r(const GaussBatch* xy, int xy_total, const GaussBatch* z, int z_total, bool warp,
+cudaError_t launch_batch_r(const GaussBatch& xy, int xy_total, const GaussBatch& z, int z_total, bool warp,
                            cudaStream_t s) {
   static int set[64] = {};
   int dev = 0;
@@ -486,10 +486,10 @@ cudaError_t launch_split_any(const GaussArgs& a, const GaussPlan& p, cudaStream_
 }
 }  // namespace
 
-cudaError_t gauss_launch_batch(const GaussBatch* xy_dev, int xy_total, const GaussBatch* z_dev, int z_total,
+cudaError_t gauss_launch_batch(const GaussBatch& xy, int xy_total, const GaussBatch& z, int z_total,
                                int R, bool warp, cudaStream_t s) {
   switch (R) {
-#define BCASE(RR) case RR: return launch_batch_r<RR>(xy_dev, xy_total, z_dev, z_total, warp, s);
+#define BCASE(RR) case RR: return launch_batch_r<RR>(xy, xy_total, z, z_total, warp, s);
     BCASE(1) BCASE(2) BCASE(3) BCASE(4) BCASE(5) BCASE(6) BCASE(7) BCASE(8)
 #undef BCASE
     default: return cudaErrorInvalidValue;

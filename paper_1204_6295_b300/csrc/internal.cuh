@@ -65,6 +65,7 @@ struct BoxPlan {
 
 // Work table of a batched launch over many volumes (pairs): volume p owns the
 // work items offset[p] .. offset[p+1]-1, which are the CTAs of its own grid.
+// Tables are passed by value as kernel parameters (constant bank).
 constexpr int kMaxBatch = 64;
 struct BoxBatch {
   int count;
@@ -74,7 +75,7 @@ struct BoxBatch {
 };
 
 // Specialised cubic-patch path (box_fast.cu)
-cudaError_t box_fast_launch_batch(const BoxBatch* bt_dev, int h, int total, int grid, size_t smem,
+cudaError_t box_fast_launch_batch(const BoxBatch& bt, int h, int total, int grid, size_t smem,
                                   cudaStream_t s);
 bool box_fast_ok(int nx, int ny, int nz, int hx, int hy, int hz);
 size_t box_fast_smem(int mode, int h);
@@ -120,7 +121,7 @@ struct GaussBatch {
 // Batched Gaussian passes over many volumes (gauss.cu): the xy pass (u -> t) and
 // the z pass (t -> r, and m if args.m) with one launch each.  Work items follow
 // each volume's own grids (xy: tiles x planes; z: column blocks x rows x chunks).
-cudaError_t gauss_launch_batch(const GaussBatch* xy_dev, int xy_total, const GaussBatch* z_dev, int z_total,
+cudaError_t gauss_launch_batch(const GaussBatch& xy, int xy_total, const GaussBatch& z, int z_total,
                                int R, bool warp, cudaStream_t s);
 void gauss_grids(int nx, int ny, int nz, const GaussPlan& p, dim3* xy, dim3* z);
 
@@ -165,7 +166,7 @@ struct NormBatch {
   int nparts[kMaxBatch];
   NormState st[kMaxBatch];
 };
-cudaError_t launch_norm_finalize_batch(const NormBatch* nb_dev, int count, cudaStream_t s);
+cudaError_t launch_norm_finalize_batch(const NormBatch& nb, int count, cudaStream_t s);
 // Warp of many volumes in one launch (warp.cu); args: Im, r, m, dims per volume.
 struct WarpBatch {
   int count;
@@ -176,7 +177,7 @@ struct WarpBatch {
   int nx[kMaxBatch], ny[kMaxBatch], nz[kMaxBatch];
   const int* stop[kMaxBatch];
 };
-cudaError_t launch_warp_batch(const WarpBatch* wb_dev, int total_blocks, cudaStream_t s);
+cudaError_t launch_warp_batch(const WarpBatch& wb, int total_blocks, cudaStream_t s);
 constexpr int kWarpBatchThreads = 128;
 // Deterministic fixed-order sum of per-CTA float partials (stride 2, component c) into *out.
 cudaError_t launch_partials_sum(const float* partials, int nparts, int comp, double* out,

@@ -165,9 +165,9 @@ __global__ void k_norm_finalize(const float* partials, int nparts, NormState st)
 }
 
 // One block per volume of a batch.
-__global__ void k_norm_finalize_batch(const NormBatch* __restrict__ nb) {
+__global__ void k_norm_finalize_batch(const __grid_constant__ NormBatch nb) {
   const int p = blockIdx.x;
-  norm_finalize_body(nb->partials[p], nb->nparts[p], nb->st[p]);
+  norm_finalize_body(nb.partials[p], nb.nparts[p], nb.st[p]);
 }
 
 __global__ void k_partials_sum(const float* partials, int nparts, int comp, double* out) {
@@ -221,9 +221,9 @@ cudaError_t launch_norm_finalize(const float* partials, int nparts, NormState st
   return cudaGetLastError();
 }
 
-cudaError_t launch_norm_finalize_batch(const NormBatch* nb_dev, int count, cudaStream_t s) {
+cudaError_t launch_norm_finalize_batch(const NormBatch& nb, int count, cudaStream_t s) {
   if (count < 1) return cudaSuccess;
-  k_norm_finalize_batch<<<count, kRedThreads, 0, s>>>(nb_dev);
+  k_norm_finalize_batch<<<count, kRedThreads, 0, s>>>(nb);
   return cudaGetLastError();
 }
 

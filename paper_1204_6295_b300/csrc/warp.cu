@@ -25,26 +25,26 @@ __global__ void __launch_bounds__(kWarpThreads) k_warp(const float* __restrict__
 }
 }  // namespace
 
-__global__ void __launch_bounds__(kWarpBatchThreads) k_warp_batch(const WarpBatch* __restrict__ wb) {
+__global__ void __launch_bounds__(kWarpBatchThreads) k_warp_batch(const __grid_constant__ WarpBatch wb) {
   const int i = blockIdx.x;
   int p = 0;
-  while (p + 1 < wb->count && wb->offset[p + 1] <= i) ++p;
-  if (wb->stop[p] != nullptr && *(volatile const int*)wb->stop[p] != 0) return;
-  const int nx = wb->nx[p], ny = wb->ny[p], nz = wb->nz[p];
-  const int j = i - wb->offset[p];
+  while (p + 1 < wb.count && wb.offset[p + 1] <= i) ++p;
+  if (wb.stop[p] != nullptr && *(volatile const int*)wb.stop[p] != 0) return;
+  const int nx = wb.nx[p], ny = wb.ny[p], nz = wb.nz[p];
+  const int j = i - wb.offset[p];
   const int gxb = (nx + kWarpBatchThreads - 1) / kWarpBatchThreads;
   const int x = (j % gxb) * kWarpBatchThreads + threadIdx.x;
   const int y = (j / gxb) % ny, z = j / (gxb * ny);
   if (x >= nx) return;
   const size_t N = (size_t)nx * ny * nz;
   const size_t g = ((size_t)z * ny + y) * nx + x;
-  const float* r = wb->r[p];
-  wb->m[p][g] = warp_at(wb->Im[p], x, y, z, __ldg(r + g), __ldg(r + N + g), __ldg(r + 2 * N + g), nx, ny, nz);
+  const float* r = wb.r[p];
+  wb.m[p][g] = warp_at(wb.Im[p], x, y, z, __ldg(r + g), __ldg(r + N + g), __ldg(r + 2 * N + g), nx, ny, nz);
 }
 
-cudaError_t launch_warp_batch(const WarpBatch* wb_dev, int total_blocks, cudaStream_t s) {
+cudaError_t launch_warp_batch(const WarpBatch& wb, int total_blocks, cudaStream_t s) {
   if (total_blocks < 1) return cudaSuccess;
-  k_warp_batch<<<total_blocks, kWarpBatchThreads, 0, s>>>(wb_dev);
+  k_warp_batch<<<total_blocks, kWarpBatchThreads, 0, s>>>(wb);
   return cudaGetLastError();
 }
 

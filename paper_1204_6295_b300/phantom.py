@@ -264,12 +264,29 @@ def batch_sizes(n_pairs=16, seed=SEED_BASE + 4, choices=(64, 80, 96, 112, 128, 1
     return [(int(2 * v), int(2 * v), int(v)) for v in s]
 
 
-def batch_pairs(n_pairs=16, seed=SEED_BASE + 4):
-    """16 head-and-neck pairs of uneven size from 128x128x64 to 320x320x160."""
-    out = []
-    for i, (nx, ny, nz) in enumerate(batch_sizes(n_pairs, seed)):
-        out.append(head_neck_pair(nx, ny, nz, seed=seed + 1000 * (i + 1)))
-    return out
+def _batch_pair_images(args):
+    i, (nx, ny, nz), seed = args
+    p = head_neck_pair(nx, ny, nz, seed=seed + 1000 * (i + 1))
+    return p.ct, p.cbct
+
+
+def batch_pair_images(n_pairs=16, seed=SEED_BASE + 4, workers=None):
+    """(CT, CBCT) of the batched workload's pairs, drawn in parallel processes.
+
+    16 head-and-neck pairs of uneven size (2s, 2s, s), s from 64 to 160.  The
+    worker processes are started with 'spawn' (safe after CUDA is initialised).
+    """
+    import multiprocessing as mp
+    import os
+    from concurrent.futures import ProcessPoolExecutor
+    sizes = batch_sizes(n_pairs, seed)
+    jobs = [(i, d, seed) for i, d in enumerate(sizes)]
+    if workers is None:
+        workers = max(1, min(len(jobs), os.cpu_count() or 1))
+    if workers == 1:
+        return [_batch_pair_images(j) for j in jobs]
+    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_batch_pair_images, jobs))
 
 
 def random_volume(shape, seed, lo=-1000.0, hi=1000.0):
