@@ -319,12 +319,7 @@ def time_batched(disc, torch, dist, steps=2):
             step()
         e1.record(s)
         torch.cuda.synchronize()
-        t = e0.elapsed_time(e1) / steps / 1e3
-        if dist:
-            tt = torch.tensor([t], device="cuda", dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t = float(tt.item())
-        return t
+        return reduce_max(dist, e0.elapsed_time(e1) / steps / 1e3)
 
     batch = disc.Batch(len(images), **bw)
     for i, (ct, cbct) in enumerate(images):
@@ -363,6 +358,21 @@ def time_batched(disc, torch, dist, steps=2):
             "what": "16 head-and-neck pairs (2s, 2s, s), s in 64..160, patch 9^3, sigma 1.5, "
                     "3 levels x 100 iterations: disc_batch (one launch per step over all pairs, "
                     "graph per level) vs 16 separate contexts run one after the other"}
+
+
+def reduce_max(dist, seconds, device="cuda"):
+    """Largest value over the ranks of the process group (the step time of the job)."""
+    if dist is None:
+        return seconds
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, seconds):
+    """Whole-job Gvoxel-iterations/s: every rank processes units_per_rank per step (weak scaling)."""
+    return world * units_per_rank / seconds / 1e9
 
 
 def run_ours(args, w, rank, world, local_rank):
@@ -407,12 +417,8 @@ def run_ours(args, w, rank, world, local_rank):
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * units / (ms / 1e3) / 1e9
+    ms = reduce_max(dist, e0.elapsed_time(e1) / args.steps)
+    value = job_throughput(units, world, ms / 1e3)
 
     # kernel timing for the roofline at the finest level, on the final field
     field = torch.empty((3, nz, ny, nx), dtype=torch.float32, device="cuda")
@@ -445,12 +451,8 @@ def run_ours(args, w, rank, world, local_rank):
         reg.iterate(-1, sync=False)
         reg.get_field(out_np)
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * units / e2e_s / 1e9, "unit": UNIT,
+    e2e_s = reduce_max(dist, (time.perf_counter() - t0) / e2e_steps)
+    e2e = {"value": job_throughput(units, world, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": int(2 * nx * ny * nz * 4), "d2h_bytes_per_step": int(3 * nx * ny * nz * 4),
            "ms_per_step": e2e_s * 1e3,
            "what": "disc_set_images(host CT, CBCT) + disc_iterate(full schedule) + disc_get_field(host)"}
