@@ -318,6 +318,17 @@ disc_status disc_k_pass_a_static(const float* Im, const float* zs, const float* 
 disc_status disc_k_gauss(const float* u, float* r, int32_t nx, int32_t ny, int32_t nz,
                          float sigma, int32_t radius, void* stream);
 
+/* Error word of the kernel-level calls above.  Their moment passes read
+ * the volume through bulk tensor copies completed on shared-memory
+ * barriers; a wait for such a copy is bounded (about one second), and one
+ * that gives up abandons its tile and sets a device-wide error word instead
+ * of hanging.  This call synchronises `stream`, returns DISC_ERR_TIMEOUT if
+ * the word is set (and clears it), else DISC_OK.  (Registration and batch
+ * contexts keep their own word and report DISC_ERR_TIMEOUT themselves at
+ * their next synchronising call.)  The paper has no counterpart: it is the
+ * failure report of this implementation's bounded waits. */
+disc_status disc_k_check_error(void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,6 +30,25 @@ disc_status fail(disc_ctx* c, cudaError_t e) {
     if (e_ != cudaSuccess) return fail(ctx, e_); \
   } while (0)
 
+// After the stream has been synchronised: a bulk-copy wait of a box kernel that
+// timed out makes the context fail with DISC_ERR_TIMEOUT.
+disc_status check_device_error(disc_ctx* ctx) {
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+  CK(cudaStreamSynchronize(ctx->s));
+  if (flag != 0) {
+    if (ctx->sticky == DISC_OK) ctx->sticky = DISC_ERR_TIMEOUT;
+    return DISC_ERR_TIMEOUT;
+  }
+  return DISC_OK;
+}
+
+#define CK_DEV(ctx)                                   \
+  do {                                                \
+    disc_status s_ = check_device_error(ctx);         \
+    if (s_ != DISC_OK) return s_;                     \
+  } while (0)
+
 disc_status check_params(const disc_params* p) {
   if (!p) return DISC_ERR_ARG;
   for (int a = 0; a < 3; ++a)
@@ -92,6 +111,7 @@ cudaError_t memcpy_kind(void* dst, const void* src, size_t bytes, int dst_kind, 
 
 BoxArgs box_args(const disc_ctx* c, const Level& v) {
   BoxArgs a{};
+  a.err = c->d_err;
   a.nx = v.nx;
   a.ny = v.ny;
   a.nz = v.nz;
@@ -290,11 +310,12 @@ disc_status disc_create(const disc_params* p, int device, void* cuda_stream, dis
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming);
   ctx->user = static_cast<cudaStream_t>(cuda_stream);   // NULL: the legacy default stream
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_iter, sizeof(int) * DISC_MAX_LEVELS);
-  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_stop, sizeof(int) * DISC_MAX_LEVELS);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_stop, sizeof(int) * (DISC_MAX_LEVELS + 1));
+  if (e == cudaSuccess) ctx->d_err = ctx->d_stop + DISC_MAX_LEVELS;
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_scratch, sizeof(double) * (2 * kShiftBlocks + 2));
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_maxabs, sizeof(float) * 2);
   if (e == cudaSuccess) e = cudaMemset(ctx->d_iter, 0, sizeof(int) * DISC_MAX_LEVELS);
-  if (e == cudaSuccess) e = cudaMemset(ctx->d_stop, 0, sizeof(int) * DISC_MAX_LEVELS);
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_stop, 0, sizeof(int) * (DISC_MAX_LEVELS + 1));
   if (e != cudaSuccess) {
     disc_destroy(ctx);
     cudaGetLastError();
@@ -474,6 +495,7 @@ disc_status disc_iterate(disc_ctx* ctx, int32_t max_iters, int32_t* iters_done, 
     int after[DISC_MAX_LEVELS] = {0};
     CK(cudaMemcpyAsync(after, ctx->d_iter, sizeof(int) * DISC_MAX_LEVELS, cudaMemcpyDeviceToHost, ctx->s));
     CK(cudaStreamSynchronize(ctx->s));
+    CK_DEV(ctx);
     int done = 0;
     float l_last = INFINITY;
     for (int i = 0; i < ntouched; ++i) {
@@ -510,7 +532,7 @@ disc_status disc_get_field(disc_ctx* ctx, float* out, int mem_kind) {
     src = fine.u;
   }
   CK(memcpy_kind(out, src, 3 * ctx->lev[0].N * sizeof(float), mem_kind, DISC_MEM_DEVICE, ctx->s));
-  if (mem_kind == DISC_MEM_HOST) CK(cudaStreamSynchronize(ctx->s));
+  if (mem_kind == DISC_MEM_HOST) CK_DEV(ctx);
   CK(leave(ctx));
   return DISC_OK;
 }
@@ -534,7 +556,7 @@ disc_status disc_get_corrected(disc_ctx* ctx, float* out, int mem_kind) {
   BoxPlan pc = box_plan(kModeCorrected, v.nx, v.ny, v.nz, ctx->hx, ctx->hy, ctx->hz, ctx->num_sms);
   CK(box_launch(kModeCorrected, a, pc, ctx->s));
   CK(memcpy_kind(out, v.u, v.N * sizeof(float), mem_kind, DISC_MEM_DEVICE, ctx->s));
-  if (mem_kind == DISC_MEM_HOST) CK(cudaStreamSynchronize(ctx->s));
+  if (mem_kind == DISC_MEM_HOST) CK_DEV(ctx);
   CK(leave(ctx));
   return DISC_OK;
 }
@@ -591,6 +613,15 @@ disc_status disc_get_norm_history(disc_ctx* ctx, int32_t level, float* out, int3
 // ============================================================================
 // Kernel-level entry points
 // ============================================================================
+
+disc_status disc_k_check_error(void* stream) {
+  int flag = 0;
+  if (box_tma_error((cudaStream_t)stream, &flag) != cudaSuccess) {
+    cudaGetLastError();
+    return DISC_ERR_CUDA;
+  }
+  return flag != 0 ? DISC_ERR_TIMEOUT : DISC_OK;
+}
 
 float disc_qscale(float max_abs, const int32_t patch[3]) {
   if (!patch || !(max_abs >= 0.0f) || !std::isfinite(max_abs)) return 0.0f;

@@ -13,6 +13,7 @@
 
 #include <cuda_runtime.h>
 
+#include "box_dev.cuh"
 #include "internal.cuh"
 
 namespace disc {
@@ -51,24 +52,6 @@ struct FastLayout {
   static constexpr size_t bytes = ((o_ro + (EXT ? 4 * 3 * (size_t)TN : 0)) + 15) & ~(size_t)15;
 };
 
-// Patch moments from exact integer sums (see box_pass.cu for the derivation):
-// dc = E(X) - v_c; sigma = STD(X), 0 when Var(X) <= var_floor.
-// T = sum (q - k)^2 = S2 - k (S1 + e) with k = round(S1/n), e = S1 - n k.
-__device__ __forceinline__ void moments_fast(long long S1, long long S2, int n, float inv_n, int qc,
-                                             float inv_qs, float var_floor, float& dc, float& sigma) {
-  const int k = __float2int_rn((float)S1 * inv_n);       // ~ mean of q (within a few units)
-  const int e = (int)(S1 - (long long)n * k);            // |e| < 2^31: a few times n
-  const float ef = (float)e * inv_n;
-  dc = ((float)(k - qc) + ef) * inv_qs;                   // E(X) - v_c
-  const unsigned long long T = (unsigned long long)S2 - (unsigned long long)(long long)k *
-                                                            (unsigned long long)(S1 + e);
-  const float varq = fmaf((float)(long long)T, inv_n, -ef * ef);
-  const float var = varq * (inv_qs * inv_qs);
-  float sq;
-  asm("sqrt.approx.f32 %0, %1;" : "=f"(sq) : "f"(var));
-  sigma = var > var_floor ? sq : 0.0f;
-}
-
 __device__ __forceinline__ float diff1(float vm, float v0, float vp, int c, int n) {
   if (n < 2) return 0.0f;
   if (c == 0) return vp - v0;
@@ -76,11 +59,6 @@ __device__ __forceinline__ float diff1(float vm, float v0, float vp, int c, int 
   return 0.5f * (vp - vm);
 }
 
-__device__ __forceinline__ float sqrt_approx(float x) {
-  float y;
-  asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
 
 // The CTA body: tile (bx, by) of the 32 x 16 tiling, z chunk bz; part = index
 // of this CTA's norm partials.  Shared by the per-volume and batched launches.
@@ -224,12 +202,7 @@ __device__ __forceinline__ void box_body(const BoxArgs& a, int bx, int by, int b
       const int fx0 = sg * B::SX;
       const int* r1 = s1z + wy * B::WXP + fx0;
       const long long* r2 = s2z + wy * B::WXP + fx0;
-      long long b1 = 0, b2 = 0;
-#pragma unroll
-      for (int k = 0; k <= 2 * H; ++k) {
-        b1 += r1[k];
-        b2 += r2[k];
-      }
+      long long b1 = tree_sum<2 * H + 1, int>(r1, 1), b2 = tree_sum<2 * H + 1, long long>(r2, 1);
       long long* o1 = xb1 + wy * B::FX + fx0;
       long long* o2 = xb2 + wy * B::FX + fx0;
       o1[0] = b1;
@@ -258,12 +231,8 @@ __device__ __forceinline__ void box_body(const BoxArgs& a, int bx, int by, int b
       const int fy0 = sy * B::SY;
       const bool xin = gx >= H && gx < nx - H;
       const int nxc = box_count(gx, nx, H);
-      long long b1 = 0, b2 = 0;
-#pragma unroll
-      for (int k = 0; k <= 2 * H; ++k) {
-        b1 += xb1[(fy0 + k) * B::FX + fx];
-        b2 += xb2[(fy0 + k) * B::FX + fx];
-      }
+      long long b1 = tree_sum<2 * H + 1, long long>(xb1 + fy0 * B::FX + fx, B::FX);
+      long long b2 = tree_sum<2 * H + 1, long long>(xb2 + fy0 * B::FX + fx, B::FX);
 #pragma unroll
       for (int j = 0; j < B::SY; ++j) {
         const int fy = fy0 + j;
@@ -286,7 +255,7 @@ __device__ __forceinline__ void box_body(const BoxArgs& a, int bx, int by, int b
         const int fi = fy * B::FX + fx;
         const float vc = mr[fi];
         float dc, sg_;
-        moments_fast(b1, b2, n, inv_n, __float2int_rn(vc * qs), inv_qs, vfl, dc, sg_);
+        patch_moments(b1, b2, n, inv_n, __float2int_rn(vc * qs), inv_qs, vfl, dc, sg_);
         const size_t gz = (size_t)zc * plane + (size_t)gy * nx + gx;
         if (MODE == kModeStatic) {
           a.out[gz] = sg_ > 0.0f ? -dc / sg_ : 0.0f;   // (I_s - E(S)) / STD(S)

@@ -366,8 +366,12 @@ BoxPlan box_plan(int mode, int nx, int ny, int nz, int hx, int hy, int hz, int n
   p.tx = kTX;
   p.ty = kTY;
   p.fast = box_fast_ok(nx, ny, nz, hx, hy, hz);
+  p.tma = p.fast && box_tma_ok(mode, nx, ny, nz, hx, hy, hz);
   int per_sm;
-  if (p.fast) {
+  if (p.tma) {
+    p.smem = box_tma_smem(mode, hx);
+    per_sm = box_tma_occupancy(mode, hx, p.smem);
+  } else if (p.fast) {
     p.smem = box_fast_smem(mode, hx);
     per_sm = box_fast_occupancy(mode, hx, p.smem);
   } else {
@@ -401,6 +405,12 @@ cudaError_t box_launch(int mode, const BoxArgs& a, const BoxPlan& p, cudaStream_
   if (p.grid.x == 0) return cudaErrorInvalidConfiguration;
   BoxArgs b = a;
   b.zlen = p.zlen;
+  if (p.tma) {
+    if (box_tma_aligned(mode, b)) return box_tma_launch(mode, b, p, s);
+    BoxPlan q = p;                            // unaligned buffers: same grid, plain loads
+    q.smem = box_fast_smem(mode, a.hx);
+    return box_fast_launch(mode, b, q, s);
+  }
   if (p.fast) return box_fast_launch(mode, b, p, s);
   switch (mode) {
     case kModeStatic: return launch_mode<kModeStatic>(b, p, s);

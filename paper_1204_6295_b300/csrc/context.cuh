@@ -59,6 +59,7 @@ struct disc_ctx {
   int max_parts = 0;
   int* d_iter = nullptr;     // [DISC_MAX_LEVELS]
   int* d_stop = nullptr;     // [DISC_MAX_LEVELS]
+  int* d_err = nullptr;      // device error word of the box kernels (d_stop + DISC_MAX_LEVELS)
   double* d_scratch = nullptr;
   float* d_maxabs = nullptr; // [2]
   int cur_level = 0;

@@ -53,6 +53,7 @@ struct BoxArgs {
   float qscale, inv_qscale, var_floor;
   int force_mode;
   int zlen;             // output planes per CTA (z chunk)
+  int* err;             // device error word (bit 0: a bulk-copy wait timed out); NULL: the library's own
 };
 
 struct BoxPlan {
@@ -61,6 +62,7 @@ struct BoxPlan {
   int zlen;
   int tx, ty;
   bool fast;            // cubic-patch kernel specialised on the half size (box_fast.cu)
+  bool tma;             // the same kernel fed by bulk tensor copies (box_tma.cu)
 };
 
 // Work table of a batched launch over many volumes (pairs): volume p owns the
@@ -81,6 +83,18 @@ bool box_fast_ok(int nx, int ny, int nz, int hx, int hy, int hz);
 size_t box_fast_smem(int mode, int h);
 int box_fast_occupancy(int mode, int h, size_t smem);
 cudaError_t box_fast_launch(int mode, const BoxArgs& a, const BoxPlan& p, cudaStream_t s);
+
+// Bulk-tensor-copy path (box_tma.cu): usable when box_tma_ok (cubic patch, nx a
+// multiple of 4, extents at least one staging box) and, per launch, when the
+// buffers are 16-byte aligned (box_tma_aligned); DISC_NO_TMA=1 in the
+// environment turns it off.
+bool box_tma_ok(int mode, int nx, int ny, int nz, int hx, int hy, int hz);
+bool box_tma_aligned(int mode, const BoxArgs& a);
+size_t box_tma_smem(int mode, int h);
+int box_tma_occupancy(int mode, int h, size_t smem);
+cudaError_t box_tma_launch(int mode, const BoxArgs& a, const BoxPlan& p, cudaStream_t s);
+// Reads (synchronising s) and clears the library's own error word into *flag.
+cudaError_t box_tma_error(cudaStream_t s, int* flag);
 
 // Plan a launch (grid, z chunk, dynamic shared memory) for a volume and patch.
 BoxPlan box_plan(int mode, int nx, int ny, int nz, int hx, int hy, int hz, int num_sms);

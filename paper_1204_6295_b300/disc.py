@@ -89,6 +89,7 @@ _SIGS = {
     "disc_k_pass_a_static": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _i32, _i32,
                                    ctypes.POINTER(_i32), _f32, _f32, _i32, _vp]),
     "disc_k_gauss": (_st, [_vp, _vp, _i32, _i32, _i32, _f32, _i32, _vp]),
+    "disc_k_check_error": (_st, [_vp]),
     "disc_k_force_update": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _i32, _i32, _i32,
                                   ctypes.POINTER(_i32), _f32, _f32, _i32, _vp]),
     "disc_k_ssd_loss": (_st, [_vp, _vp, _vp, _vp, _i32, _i32, _i32, ctypes.POINTER(_i32), _f32, _f32, _vp]),
@@ -392,6 +393,11 @@ def k_gauss(u, r, sigma, radius=0, stream=None):
     _, nz, ny, nx = u.shape
     _check(_lib.disc_k_gauss(_ptr(u), _ptr(r), nx, ny, nz, float(sigma), int(radius), _stream(stream)),
            "disc_k_gauss")
+
+
+def k_check_error(stream=None):
+    """Synchronise the stream; raise DiscError if a bounded device wait gave up."""
+    _check(_lib.disc_k_check_error(_stream(stream)), "disc_k_check_error")
 
 
 def k_force_update(m, zs, r, u, patch, qs, d_out=None, norms_out=None, var_floor=1e-6,

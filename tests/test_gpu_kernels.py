@@ -28,6 +28,8 @@ SHAPES_PATCHES = [
     ((2, 17, 1), (5, 5, 5)),        # degenerate axes
     ((6, 6, 6), (1, 1, 1)),         # 1x1x1 patch: variance 0 everywhere
     ((5, 1, 64), (3, 3, 3)),
+    ((24, 52, 64), (11, 11, 11)),   # these two take the bulk-tensor-copy (TMA) form
+    ((17, 33, 100), (7, 7, 7)),
 ]
 
 

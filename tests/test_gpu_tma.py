@@ -1,0 +1,142 @@
+"""The bulk-tensor-copy (TMA) form of the moment pass against the plain-load form.
+
+Both forms run the same arithmetic in the same order; only the way the z march
+reads global memory differs (bulk tensor copies into shared memory, with zeros
+outside the volume, versus per-thread loads with bounds tests).  Their outputs
+must therefore be bitwise equal.  DISC_NO_TMA=1 selects the plain-load form at
+planning time.  The TMA form needs nx a multiple of 4 and extents of at least
+one staging box (48 x 30 voxels for patch 11 in iteration mode); the shapes
+below meet that with ragged tiles in x, y and z.  (The per-kernel oracle
+tests include shapes that take the TMA form as well.)
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_1204_6295_b300 import phantom
+
+from gpu_util import ct_like, dev, empty, host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def disc():
+    from paper_1204_6295_b300 import disc as d
+    return d
+
+
+class _NoTma:
+    def __enter__(self):
+        self.old = os.environ.get("DISC_NO_TMA")
+        os.environ["DISC_NO_TMA"] = "1"
+
+    def __exit__(self, *exc):
+        if self.old is None:
+            del os.environ["DISC_NO_TMA"]
+        else:
+            os.environ["DISC_NO_TMA"] = self.old
+
+
+CASES = [
+    ((20, 40, 64), 3),      # (nz, ny, nx), patch
+    ((33, 47, 100), 11),    # ragged in all three axes
+    ((9, 64, 48), 15),      # patch wider than the chunk, exact box width
+    ((40, 31, 52), 7),
+    ((17, 52, 96), 5),
+]
+
+
+def _inputs(shape, patch, seed):
+    ct = ct_like(shape, seed, noise=15.0)
+    cbct = ct_like(shape, seed + 1, noise=25.0)
+    r = phantom.smooth_random_field(shape, seed + 2, amp=2.5).astype(np.float32)
+    return ct, cbct, r
+
+
+@pytest.mark.parametrize("shape,patch", CASES)
+@pytest.mark.parametrize("force_mode", [0, 1])
+def test_force_update_bitwise(disc, shape, patch, force_mode):
+    P = (patch,) * 3
+    ct, cbct, r = _inputs(shape, patch, 40 + patch)
+    qs_m = disc.qscale(float(np.abs(ct).max()), P)
+    qs_s = disc.qscale(float(np.abs(cbct).max()), P)
+    Im, Is, rd = dev(ct), dev(cbct), dev(r)
+    zs = empty(*shape)
+    m = empty(*shape)
+    disc.k_static_norm(Is, zs, P, qs_s)
+    disc.k_warp(Im, rd, m)
+    outs = []
+    for plain in (False, True):
+        u = empty(3, *shape)
+        d = empty(*shape)
+        norms = empty(2).double()
+        if plain:
+            with _NoTma():
+                disc.k_force_update(m, zs, rd, u, P, qs_m, d_out=d, norms_out=norms, force_mode=force_mode)
+        else:
+            disc.k_force_update(m, zs, rd, u, P, qs_m, d_out=d, norms_out=norms, force_mode=force_mode)
+        outs.append((host(u), host(d), host(norms)))
+    disc.k_check_error()
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])
+    # the norm partials are per CTA, and the two forms may chunk z differently
+    np.testing.assert_allclose(outs[0][2], outs[1][2], rtol=1e-6)
+
+
+@pytest.mark.parametrize("shape,patch", CASES[:3])
+def test_static_norm_bitwise(disc, shape, patch):
+    P = (patch,) * 3
+    _, cbct, _ = _inputs(shape, patch, 7)
+    qs = disc.qscale(float(np.abs(cbct).max()), P)
+    Is = dev(cbct)
+    z1, z2 = empty(*shape), empty(*shape)
+    disc.k_static_norm(Is, z1, P, qs)
+    with _NoTma():
+        disc.k_static_norm(Is, z2, P, qs)
+    np.testing.assert_array_equal(host(z1), host(z2))
+
+
+@pytest.mark.parametrize("shape,patch", [((20, 40, 64), 3), ((18, 34, 56), 9)])
+def test_ssd_bitwise(disc, shape, patch):
+    P = (patch,) * 3
+    ct, cbct, r = _inputs(shape, patch, 90)
+    qs_m = disc.qscale(float(np.abs(ct).max()), P)
+    qs_s = disc.qscale(float(np.abs(cbct).max()), P)
+    Im, Is, rd = dev(ct), dev(cbct), dev(r)
+    zs = empty(*shape)
+    disc.k_static_norm(Is, zs, P, qs_s)
+    res = []
+    for plain in (False, True):
+        g = empty(3, *shape)
+        loss = empty(1).double()
+        if plain:
+            with _NoTma():
+                disc.k_ssd_grad(Im, zs, rd, g, P, qs_m, loss_out=loss)
+        else:
+            disc.k_ssd_grad(Im, zs, rd, g, P, qs_m, loss_out=loss)
+        res.append((host(g), host(loss)))
+    np.testing.assert_array_equal(res[0][0], res[1][0])
+    np.testing.assert_allclose(res[0][1], res[1][1], rtol=1e-6)   # per-CTA partial sums
+
+
+def test_registration_bitwise(disc):
+    """A whole two-level schedule through the context, TMA form vs plain loads."""
+    shape = (32, 64, 64)
+    ct, cbct, _ = _inputs(shape, 9, 11)
+    fields = []
+    for plain in (False, True):
+        def run():
+            reg = disc.Registration(patch=(9, 9, 9), sigma=1.0, levels=2, iters=(6, 5))
+            reg.set_images(dev(ct), dev(cbct))
+            reg.iterate(-1)
+            out = empty(3, *shape)
+            reg.get_field(out)
+            return host(out)
+        if plain:
+            with _NoTma():
+                fields.append(run())
+        else:
+            fields.append(run())
+    np.testing.assert_array_equal(fields[0], fields[1])
