@@ -61,7 +61,8 @@ struct TmaLayout {
   static constexpr int TN = TX * TY;
   static constexpr int KO = TN / kThreads;                      // tile voxels per thread
   static_assert(TN % kThreads == 0 && kThreads % TX == 0, "tile and CTA shape");
-  static constexpr int NSX0 = (kThreads / WY) < 1 ? 1 : (kThreads / WY);
+  // about half as many x tasks as threads: longer slides amortise the initial window
+  static constexpr int NSX0 = (kThreads / 2 / WY) < 1 ? 1 : (kThreads / 2 / WY);
   static constexpr int SX = (FX + NSX0 - 1) / NSX0;             // x outputs per sliding task
   static constexpr int NSX = (FX + SX - 1) / SX;
   static constexpr int NSY0 = (kThreads / FX) < 1 ? 1 : (kThreads / FX);
@@ -163,7 +164,7 @@ __device__ __forceinline__ uint32_t bytes_b(const March& s, int zi) {
   using B = TmaLayout<MODE, H>;
   const int zc = zi - H, zf = zc - 1;
   const bool do2 = zc >= s.zc_lo && zc <= s.zc_hi;
-  const bool do3 = MODE == kModeIterate && do2 && zf >= s.z0 && zf < s.z1;
+  const bool do3 = MODE == kModeIterate && zf >= s.z0 && zf < s.z1;
   return (do2 && MODE != kModeStatic ? B::FB : 0u) + (do3 ? B::RB : 0u);
 }
 
@@ -204,7 +205,10 @@ __global__ void __launch_bounds__(kThreads, 3)
   st.zc_lo = max(0, st.z0 - B::EXT);
   st.zc_hi = min(nz - 1, st.z1 - 1 + B::EXT);
   st.zi0 = max(0, st.zc_lo - H);
-  st.zi1 = st.zc_hi + H;
+  // iteration mode: the force of plane zf is computed in the step whose centre
+  // plane is zf + 1, so the march runs to centre plane z1 (a step without
+  // moments when z1 = nz)
+  st.zi1 = (MODE == kModeIterate ? st.z1 : st.zc_hi) + H;
   const int z0 = st.z0, z1 = st.z1;
   const float qs = a.qscale, inv_qs = a.inv_qscale, vfl = a.var_floor;
 
@@ -223,15 +227,16 @@ __global__ void __launch_bounds__(kThreads, 3)
     if (zi < nz) tma_load_3d(wn, &map_w, x0 - B::XW, y0 - B::EXT - H, zi, &bar[0]);
     if (zo >= st.zi0) tma_load_3d(wo, &map_w, x0 - B::XW, y0 - B::EXT - H, zo, &bar[0]);
     if (zc >= st.zc_lo && zc <= st.zc_hi)
-      tma_load_3d(mring + (zc % B::NMS) * B::MS, &map_f, x0 - B::XF, y0 - B::EXT, zc, &bar[0]);
+      tma_load_3d(mring + ((unsigned)zc % B::NMS) * B::MS, &map_f, x0 - B::XF, y0 - B::EXT, zc, &bar[0]);
   };
   auto issue_b = [&](int zi) {               // thread 0 only
     const uint32_t nb = bytes_b<MODE, H>(st, zi);
     if (nb == 0) return;
     mbar_expect_tx(&bar[1], nb);
     const int zc = zi - H, zf = zc - 1;
-    const bool do3 = MODE == kModeIterate && zf >= st.z0 && zf < st.z1;   // nb != 0: zc is a centre plane
-    if (MODE != kModeStatic) tma_load_3d(zsf, &map_z, x0 - B::XF, y0 - B::EXT, zc, &bar[1]);
+    const bool do2 = zc >= st.zc_lo && zc <= st.zc_hi;
+    const bool do3 = MODE == kModeIterate && zf >= st.z0 && zf < st.z1;
+    if (MODE != kModeStatic && do2) tma_load_3d(zsf, &map_z, x0 - B::XF, y0 - B::EXT, zc, &bar[1]);
     if (do3) tma_load_4d(ro, &map_r, x0, y0, zf, 0, &bar[1]);
   };
 
@@ -271,10 +276,13 @@ __global__ void __launch_bounds__(kThreads, 3)
   uint32_t pa = 0, pb = 0;                   // phase parities of the two barriers
   if (tid == 0) issue_a(st.zi0);
 
-  for (int zi = st.zi0; zi <= st.zi1; ++zi) {
+  // slot of the centre plane in the ring of d planes, kept incrementally
+  int zc3 = ((st.zi0 - H) % 3 + 3) % 3;
+  for (int zi = st.zi0; zi <= st.zi1; ++zi, zc3 = (zc3 == 2 ? 0 : zc3 + 1)) {
     const int zc = zi - H;                   // centre plane of the patch window
     const bool do2 = zc >= st.zc_lo && zc <= st.zc_hi;
     const int zf = zc - 1;                   // plane whose force is computed this step
+    const bool do3 = MODE == kModeIterate && zf >= z0 && zf < z1;
     // ---- top of the step: group A of this step has landed -----------------------
     {
       int bad = 0;
@@ -308,10 +316,10 @@ __global__ void __launch_bounds__(kThreads, 3)
     }
     __syncthreads();
     if (tid == 0 && zi < st.zi1) issue_a(zi + 1);   // the W boxes are consumed
-    if (!do2) continue;                      // uniform; group B was not armed
+    if (!do2 && !do3) continue;              // uniform; group B was not armed
 
     // ---- stage 2a: x window sums, sliding, one task per (segment, row) ---------
-    for (int t = tid; t < B::NSX * B::WY; t += kThreads) {
+    for (int t = do2 ? tid : B::NSX * B::WY; t < B::NSX * B::WY; t += kThreads) {
       const int sg = t / B::WY, wy = t - sg * B::WY;
       const int fx0 = sg * B::SX;
       const int* r1 = s1z + wy * B::WXP + fx0;
@@ -350,8 +358,9 @@ __global__ void __launch_bounds__(kThreads, 3)
     const bool zin = zc >= H && zc < nz - H;
     const int nzc = box_count(zc, nz, H);
     const bool out_plane = zc >= z0 && zc < z1;
-    const float* mr = mring + (zc % B::NMS) * B::MS;
-    for (int t = tid; t < B::NSY * B::FX; t += kThreads) {
+    const float* mr = mring + ((unsigned)zc % B::NMS) * B::MS;
+    float* dcur = dring + zc3 * B::FN;
+    for (int t = do2 ? tid : B::NSY * B::FX; t < B::NSY * B::FX; t += kThreads) {
       const int sy = t / B::FX, fx = t - sy * B::FX;
       const int gx = x0 - B::EXT + fx;
       if (gx < 0 || gx >= nx) continue;
@@ -391,7 +400,7 @@ __global__ void __launch_bounds__(kThreads, 3)
         const float zsv = zsf[fi];
         const float d = fmaf(zsv, sg_, dc);               // I'_s - I_m^(k)
         if (MODE == kModeIterate) {
-          dring[(zc % 3) * B::FN + fi] = d;
+          dcur[fi] = d;
           if (a.f_tap && out_plane && fx >= 1 && fx <= B::TX && fy >= 1 && fy <= B::TY) a.f_tap[gz] = d;
         } else if (MODE == kModeCorrected) {
           a.out[gz] = vc + d;
@@ -408,64 +417,53 @@ __global__ void __launch_bounds__(kThreads, 3)
         }
       }
     }
-    if (MODE == kModeIterate) {
+    if (do3) {
       __syncthreads();
-      // ---- stage 3: demons force (Eq. 1) and update ----------------------------
+      // ---- stage 3: demons force (Eq. 1) and update of plane zf = zc - 1 -------
+      const int zo = zf;
+      const bool zlo = zo > 0, zhi = zo < nz - 1;
+      const float sz = (zlo && zhi) ? 0.5f : ((zlo || zhi) ? 1.0f : 0.0f);
+      const int s_m1 = zc3 == 2 ? 0 : zc3 + 1;      // slot of zc - 2
+      const int s_0 = zc3 == 0 ? 2 : zc3 - 1;       // slot of zc - 1 = zo
+      const float* dp = dring + s_0 * B::FN;
+      const float* dzm = dring + (zlo ? s_m1 : s_0) * B::FN;
+      const float* dzp = dring + (zhi ? zc3 : s_0) * B::FN;
+      const float* mp = mring + ((unsigned)zo % B::NMS) * B::MS;
+      const float* mzm = mring + ((unsigned)(zlo ? zo - 1 : zo) % B::NMS) * B::MS;
+      const float* mzp = mring + ((unsigned)(zhi ? zo + 1 : zo) % B::NMS) * B::MS;
+      float* out0 = a.out + (size_t)zo * plane;
 #pragma unroll
-      for (int back = 1; back >= 0; --back) {
-        const int zo = zc - back;
-        if (zo < z0 || zo >= z1) continue;
-        if (back == 0 && zc != nz - 1) continue;
-        const bool zlo = zo > 0, zhi = zo < nz - 1;
-        const float sz = (zlo && zhi) ? 0.5f : ((zlo || zhi) ? 1.0f : 0.0f);
-        const float* dp = dring + (zo % 3) * B::FN;
-        const float* mp = mring + (zo % B::NMS) * B::MS;
-        const float* dzm = dring + ((zlo ? zo - 1 : zo) % 3) * B::FN;
-        const float* dzp = dring + ((zhi ? zo + 1 : zo) % 3) * B::FN;
-        const float* mzm = mring + ((zlo ? zo - 1 : zo) % B::NMS) * B::MS;
-        const float* mzp = mring + ((zhi ? zo + 1 : zo) % B::NMS) * B::MS;
-#pragma unroll
-        for (int i = 0; i < B::KO; ++i) {
-          const int fi = fo3[i];
-          if (fi < 0) continue;
-          const float d0 = dp[fi];
-          const float gdx = sxo * (dp[fi + rxo] - dp[fi + lxo]);
-          const float gmx = sxo * (mp[fi + rxo] - mp[fi + lxo]);
-          const float gdy = syo[i] * (dp[fi + ryo[i]] - dp[fi + lyo[i]]);
-          const float gmy = syo[i] * (mp[fi + ryo[i]] - mp[fi + lyo[i]]);
-          const float gdz = sz * (dzp[fi] - dzm[fi]);
-          const float gmz = sz * (mzp[fi] - mzm[fi]);
-          const float gfx = gdx + gmx, gfy = gdy + gmy, gfz = gdz + gmz;
-          const float diff = d0;
-          const float d2 = diff * diff;
-          const float den = fmaf(gfx, gfx, fmaf(gfy, gfy, fmaf(gfz, gfz, d2)));
-          const float s = den > 1e-9f ? __fdividef(diff, den) : 0.0f;
-          float drx = s * gfx, dry = s * gfy, drz = s * gfz;
-          if (a.force_mode == DISC_FORCE_DOUBLE) {
-            const float den2 = fmaf(gmx, gmx, fmaf(gmy, gmy, fmaf(gmz, gmz, d2)));
-            const float s2 = den2 > 1e-9f ? __fdividef(diff, den2) : 0.0f;
-            drx = fmaf(s2, gmx, drx);
-            dry = fmaf(s2, gmy, dry);
-            drz = fmaf(s2, gmz, drz);
-          }
-          const size_t g = (size_t)zo * plane + goff3[i];
-          const int o = tid + i * kThreads;
-          float rx, ry, rz;
-          if (back == 1) {                     // the r tile staged by group B
-            rx = ro[o];
-            ry = ro[B::TN + o];
-            rz = ro[2 * B::TN + o];
-          } else {                             // last plane of the volume only
-            rx = __ldg(a.r + g);
-            ry = __ldg(a.r + (size_t)N + g);
-            rz = __ldg(a.r + 2 * (size_t)N + g);
-          }
-          a.out[g] = rx + drx;
-          a.out[(size_t)N + g] = ry + dry;
-          a.out[2 * (size_t)N + g] = rz + drz;
-          acc0 += sqrt_approx(fmaf(drx, drx, fmaf(dry, dry, drz * drz)));
-          acc1 += sqrt_approx(fmaf(rx, rx, fmaf(ry, ry, rz * rz)));
+      for (int i = 0; i < B::KO; ++i) {
+        const int fi = fo3[i];
+        if (fi < 0) continue;
+        const float d0 = dp[fi];
+        const float gdx = sxo * (dp[fi + rxo] - dp[fi + lxo]);
+        const float gmx = sxo * (mp[fi + rxo] - mp[fi + lxo]);
+        const float gdy = syo[i] * (dp[fi + ryo[i]] - dp[fi + lyo[i]]);
+        const float gmy = syo[i] * (mp[fi + ryo[i]] - mp[fi + lyo[i]]);
+        const float gdz = sz * (dzp[fi] - dzm[fi]);
+        const float gmz = sz * (mzp[fi] - mzm[fi]);
+        const float gfx = gdx + gmx, gfy = gdy + gmy, gfz = gdz + gmz;
+        const float diff = d0;
+        const float d2 = diff * diff;
+        const float den = fmaf(gfx, gfx, fmaf(gfy, gfy, fmaf(gfz, gfz, d2)));
+        const float sc = den > 1e-9f ? __fdividef(diff, den) : 0.0f;
+        float drx = sc * gfx, dry = sc * gfy, drz = sc * gfz;
+        if (a.force_mode == DISC_FORCE_DOUBLE) {
+          const float den2 = fmaf(gmx, gmx, fmaf(gmy, gmy, fmaf(gmz, gmz, d2)));
+          const float s2 = den2 > 1e-9f ? __fdividef(diff, den2) : 0.0f;
+          drx = fmaf(s2, gmx, drx);
+          dry = fmaf(s2, gmy, dry);
+          drz = fmaf(s2, gmz, drz);
         }
+        const int o = tid + i * kThreads;
+        const float rx = ro[o], ry = ro[B::TN + o], rz = ro[2 * B::TN + o];   // staged by group B
+        float* po = out0 + goff3[i];
+        po[0] = rx + drx;
+        po[(size_t)N] = ry + dry;
+        po[2 * (size_t)N] = rz + drz;
+        acc0 += sqrt_approx(fmaf(drx, drx, fmaf(dry, dry, drz * drz)));
+        acc1 += sqrt_approx(fmaf(rx, rx, fmaf(ry, ry, rz * rz)));
       }
     }
     // the next step's stage 1 rewrites the z sums, group B the zs and r slots,
