@@ -8,8 +8,11 @@
 // captured once as a CUDA graph and replayed.  The moment/force launch is
 // tuned per level at its first use: the z-chunk length of every pair's tiles
 // and whether the launch has one CTA per work item or a persistent grid of one
-// wave that strides over the table.  Per pair the arithmetic is the one of the
-// single-pair path, so each pair's field is bit-identical to a separate run.
+// wave that strides over the table.  When every pair's level meets the
+// bulk-tensor-copy conditions, the moment/force launch is the TMA-fed kernel,
+// with each pair's four tensor maps in device memory.  Per pair the arithmetic
+// is the one of the single-pair path, so each pair's field is bit-identical to
+// a separate run.
 
 #include <cstring>
 #include <new>
@@ -36,6 +39,10 @@ struct disc_batch {
   int box_total[DISC_MAX_LEVELS] = {}, box_grid[DISC_MAX_LEVELS] = {}, zmult[DISC_MAX_LEVELS] = {};
   int xy_total[DISC_MAX_LEVELS] = {}, z_total[DISC_MAX_LEVELS] = {}, warp_total[DISC_MAX_LEVELS] = {};
   bool ready[DISC_MAX_LEVELS] = {};
+  // bulk-tensor-copy box pass at level l (every pair eligible): tensor maps of
+  // all pairs in device memory, 4 per pair
+  bool tma[DISC_MAX_LEVELS] = {};
+  void* d_maps[DISC_MAX_LEVELS] = {};
   cudaGraphExec_t graph[DISC_MAX_LEVELS] = {};
   int graph_iters[DISC_MAX_LEVELS] = {};
   int cur_level = 0, cur_iter = 0;
@@ -113,6 +120,31 @@ void make_box_table(disc_batch* b, int l, int zmult, int* total) {
   }
 }
 
+// Whether level l takes the bulk-tensor-copy box pass, and its tensor maps.
+cudaError_t prepare_tma(disc_batch* b, int l) {
+  b->tma[l] = false;
+  for (int i = 0; i < b->npairs; ++i) {
+    const disc_ctx* c = b->pair[i];
+    const Level& v = c->lev[l];
+    if (!box_tma_ok(kModeIterate, v.nx, v.ny, v.nz, b->H, b->H, b->H) ||
+        !box_tma_aligned(kModeIterate, ctx_box_args(c, l)))
+      return cudaSuccess;
+  }
+  alignas(128) unsigned char maps[kMaxBatch * 4 * kTmaMapBytes];
+  for (int i = 0; i < b->npairs; ++i)
+    if (!box_tma_encode(kModeIterate, ctx_box_args(b->pair[i], l), maps + i * 4 * kTmaMapBytes))
+      return cudaSuccess;
+  if (!b->d_maps[l]) {
+    cudaError_t e = cudaMalloc(&b->d_maps[l], kMaxBatch * 4 * kTmaMapBytes);
+    if (e != cudaSuccess) return e;
+  }
+  // pageable source: staged before the call returns; stream order publishes it
+  cudaError_t e = cudaMemcpyAsync(b->d_maps[l], maps, b->npairs * 4 * kTmaMapBytes, cudaMemcpyHostToDevice, b->s);
+  if (e != cudaSuccess) return e;
+  b->tma[l] = true;
+  return cudaSuccess;
+}
+
 void build_tables(disc_batch* b, int l) {
   GaussBatch& xy = b->xy[l];
   GaussBatch& z = b->zt[l];
@@ -156,15 +188,22 @@ void build_tables(disc_batch* b, int l) {
   b->warp_total[l] = ow;
 }
 
-size_t box_smem(const disc_batch* b) { return box_fast_smem(kModeIterate, b->H); }
+size_t box_smem(const disc_batch* b, int l) {
+  return b->tma[l] ? box_tma_smem(kModeIterate, b->H) : box_fast_smem(kModeIterate, b->H);
+}
+
+cudaError_t launch_box(disc_batch* b, int l, int total, int grid) {
+  if (b->tma[l]) return box_tma_launch_batch(b->box[l], b->d_maps[l], b->H, grid, b->s);
+  return box_fast_launch_batch(b->box[l], b->H, total, grid, box_smem(b, l), b->s);
+}
 
 // Autotuner: time the batched box launch for each z-chunk multiplier and for a
 // one-CTA-per-item or one-wave persistent grid; keep the fastest.  Runs on the
 // level's current state: the box pass only writes u and its partials, which the
 // next real iteration overwrites.
 cudaError_t tune_level(disc_batch* b, int l) {
-  const size_t smem = box_smem(b);
-  const int occ = box_fast_occupancy(kModeIterate, b->H, smem);
+  const size_t smem = box_smem(b, l);
+  const int occ = b->tma[l] ? box_tma_batch_occupancy(b->H, smem) : box_fast_occupancy(kModeIterate, b->H, smem);
   const int slots = b->num_sms * (occ < 1 ? 1 : occ);
   cudaEvent_t e0, e1;
   cudaError_t e = cudaEventCreate(&e0);
@@ -185,10 +224,9 @@ cudaError_t tune_level(disc_batch* b, int l) {
     const int grids[2] = {total, total < slots ? total : slots};
     for (int gi = 0; gi < 2 && e == cudaSuccess; ++gi) {
       if (gi == 1 && grids[1] == grids[0]) continue;
-      e = box_fast_launch_batch(b->box[l], b->H, total, grids[gi], smem, b->s);   // warm-up
+      e = launch_box(b, l, total, grids[gi]);   // warm-up
       if (e == cudaSuccess) e = cudaEventRecord(e0, b->s);
-      for (int k = 0; k < 3 && e == cudaSuccess; ++k)
-        e = box_fast_launch_batch(b->box[l], b->H, total, grids[gi], smem, b->s);
+      for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = launch_box(b, l, total, grids[gi]);
       if (e == cudaSuccess) e = cudaEventRecord(e1, b->s);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
       float ms = 0.0f;
@@ -213,9 +251,8 @@ cudaError_t tune_level(disc_batch* b, int l) {
 
 cudaError_t queue_batch_iterations(disc_batch* b, int l, int n) {
   cudaError_t e = launch_warp_batch(b->warp[l], b->warp_total[l], b->s);
-  const size_t smem = box_smem(b);
   for (int k = 0; k < n && e == cudaSuccess; ++k) {
-    e = box_fast_launch_batch(b->box[l], b->H, b->box_total[l], b->box_grid[l], smem, b->s);
+    e = launch_box(b, l, b->box_total[l], b->box_grid[l]);
     if (e == cudaSuccess)
       e = gauss_launch_batch(b->xy[l], b->xy_total[l], b->zt[l], b->z_total[l], b->R, true, b->s);
     if (e == cudaSuccess) e = launch_norm_finalize_batch(b->norm[l], b->npairs, b->s);
@@ -296,8 +333,10 @@ disc_status disc_batch_destroy(disc_batch* b) {
   if (!b) return DISC_OK;
   DeviceGuard guard(b->device);
   if (b->s) cudaStreamSynchronize(b->s);
-  for (int l = 0; l < DISC_MAX_LEVELS; ++l)
+  for (int l = 0; l < DISC_MAX_LEVELS; ++l) {
     if (b->graph[l]) cudaGraphExecDestroy(b->graph[l]);
+    if (b->d_maps[l]) cudaFree(b->d_maps[l]);
+  }
   for (int i = 0; i < b->npairs; ++i) disc_destroy(b->pair[i]);
   if (b->ev_in) cudaEventDestroy(b->ev_in);
   if (b->ev_out) cudaEventDestroy(b->ev_out);
@@ -356,6 +395,7 @@ disc_status disc_batch_iterate(disc_batch* b, int32_t max_iters, int32_t* iters_
     const int left = total - b->cur_iter;
     if (left > 0 && budget > 0) {
       if (!b->ready[l]) {
+        BCK(prepare_tma(b, l));
         build_tables(b, l);
         BCK(launch_warp_batch(b->warp[l], b->warp_total[l], b->s));     // m for the tuning launches
         BCK(tune_level(b, l));

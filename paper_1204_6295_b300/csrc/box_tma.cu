@@ -168,18 +168,19 @@ __device__ __forceinline__ uint32_t bytes_b(const March& s, int zi) {
   return (do2 && MODE != kModeStatic ? B::FB : 0u) + (do3 ? B::RB : 0u);
 }
 
+// The CTA body: tile (bx, by), z chunk bz of the volume described by `a`;
+// `part` indexes this CTA's norm partials.  The two mbarriers at B::o_bar are
+// initialised by the kernel; pa and pb are their phase parities, carried over
+// the bodies a persistent CTA runs (every phase armed in a body is awaited in
+// it).  Returns false when a copy wait gave up: the CTA must stop.
 template <int MODE, int H>
-__global__ void __launch_bounds__(kThreads, 3)
-    k_box_tma(const BoxArgs a, const __grid_constant__ CUtensorMap map_w, const __grid_constant__ CUtensorMap map_f,
-              const __grid_constant__ CUtensorMap map_z, const __grid_constant__ CUtensorMap map_r) {
+__device__ __forceinline__ bool box_tma_body(const BoxArgs& a, int bx, int by, int bz, size_t part,
+                                             const CUtensorMap* map_w, const CUtensorMap* map_f,
+                                             const CUtensorMap* map_z, const CUtensorMap* map_r,
+                                             unsigned char* smem, uint32_t& pa, uint32_t& pb) {
   using B = TmaLayout<MODE, H>;
-  if (a.stop != nullptr && *(volatile const int*)a.stop != 0) return;
-  extern __shared__ __align__(128) unsigned char smem[];
+  if (a.stop != nullptr && *(volatile const int*)a.stop != 0) return true;
   int* err = a.err ? a.err : &g_box_err;
-  if ((smem_addr(smem) & 127u) != 0u) {       // TMA destinations need 128-byte alignment
-    if (threadIdx.x == 0) atomicOr(err, 2);
-    return;
-  }
   float* wn = reinterpret_cast<float*>(smem + B::o_wn);
   float* wo = reinterpret_cast<float*>(smem + B::o_wo);
   float* mring = reinterpret_cast<float*>(smem + B::o_mr);
@@ -197,10 +198,10 @@ __global__ void __launch_bounds__(kThreads, 3)
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const int plane = nx * ny;                  // 3 N < 2^31 is checked on the host
   const int N = plane * nz;
-  const int x0 = blockIdx.x * B::TX, y0 = blockIdx.y * B::TY;
+  const int x0 = bx * B::TX, y0 = by * B::TY;
   March st;
   st.nz = nz;
-  st.z0 = blockIdx.z * a.zlen;
+  st.z0 = bz * a.zlen;
   st.z1 = min(nz, st.z0 + a.zlen);
   st.zc_lo = max(0, st.z0 - B::EXT);
   st.zc_hi = min(nz - 1, st.z1 - 1 + B::EXT);
@@ -212,22 +213,15 @@ __global__ void __launch_bounds__(kThreads, 3)
   const int z0 = st.z0, z1 = st.z1;
   const float qs = a.qscale, inv_qs = a.inv_qscale, vfl = a.var_floor;
 
-  if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    fence_proxy_async();
-  }
-  __syncthreads();
-
   auto issue_a = [&](int zi) {               // thread 0 only
     const uint32_t nb = bytes_a<MODE, H>(st, zi);
     if (nb == 0) return;
     mbar_expect_tx(&bar[0], nb);
     const int zo = zi - (2 * H + 1), zc = zi - H;
-    if (zi < nz) tma_load_3d(wn, &map_w, x0 - B::XW, y0 - B::EXT - H, zi, &bar[0]);
-    if (zo >= st.zi0) tma_load_3d(wo, &map_w, x0 - B::XW, y0 - B::EXT - H, zo, &bar[0]);
+    if (zi < nz) tma_load_3d(wn, map_w, x0 - B::XW, y0 - B::EXT - H, zi, &bar[0]);
+    if (zo >= st.zi0) tma_load_3d(wo, map_w, x0 - B::XW, y0 - B::EXT - H, zo, &bar[0]);
     if (zc >= st.zc_lo && zc <= st.zc_hi)
-      tma_load_3d(mring + ((unsigned)zc % B::NMS) * B::MS, &map_f, x0 - B::XF, y0 - B::EXT, zc, &bar[0]);
+      tma_load_3d(mring + ((unsigned)zc % B::NMS) * B::MS, map_f, x0 - B::XF, y0 - B::EXT, zc, &bar[0]);
   };
   auto issue_b = [&](int zi) {               // thread 0 only
     const uint32_t nb = bytes_b<MODE, H>(st, zi);
@@ -236,8 +230,8 @@ __global__ void __launch_bounds__(kThreads, 3)
     const int zc = zi - H, zf = zc - 1;
     const bool do2 = zc >= st.zc_lo && zc <= st.zc_hi;
     const bool do3 = MODE == kModeIterate && zf >= st.z0 && zf < st.z1;
-    if (MODE != kModeStatic && do2) tma_load_3d(zsf, &map_z, x0 - B::XF, y0 - B::EXT, zc, &bar[1]);
-    if (do3) tma_load_4d(ro, &map_r, x0, y0, zf, 0, &bar[1]);
+    if (MODE != kModeStatic && do2) tma_load_3d(zsf, map_z, x0 - B::XF, y0 - B::EXT, zc, &bar[1]);
+    if (do3) tma_load_4d(ro, map_r, x0, y0, zf, 0, &bar[1]);
   };
 
   // ---- per-thread maps, fixed for the whole march ------------------------------
@@ -273,7 +267,6 @@ __global__ void __launch_bounds__(kThreads, 3)
   }
 
   float acc0 = 0.0f, acc1 = 0.0f;
-  uint32_t pa = 0, pb = 0;                   // phase parities of the two barriers
   if (tid == 0) issue_a(st.zi0);
 
   // slot of the centre plane in the ring of d planes, kept incrementally
@@ -294,7 +287,7 @@ __global__ void __launch_bounds__(kThreads, 3)
           mbar_wait(&bar[0], pa);            // bounded: let this CTA's copies drain
         }
         __syncthreads();
-        return;
+        return false;
       }
       if (armed) pa ^= 1u;
     }
@@ -349,7 +342,7 @@ __global__ void __launch_bounds__(kThreads, 3)
           if (zi < st.zi1 && bytes_a<MODE, H>(st, zi + 1) != 0) mbar_wait(&bar[0], pa);
         }
         __syncthreads();
-        return;
+        return false;
       }
       if (nbb != 0) pb ^= 1u;
     }
@@ -488,10 +481,72 @@ __global__ void __launch_bounds__(kThreads, 3)
         t0 += red[w];
         t1 += red[kThreads / 32 + w];
       }
-      const size_t part = (size_t)blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
       a.partials[2 * part] = t0;
       a.partials[2 * part + 1] = t1;
     }
+  }
+  return true;
+}
+
+// Shared-memory base check (TMA destinations need 128-byte alignment) and
+// barrier set-up, once per CTA.
+template <int MODE, int H>
+__device__ __forceinline__ bool tma_cta_setup(unsigned char* smem, int* err) {
+  using B = TmaLayout<MODE, H>;
+  if ((smem_addr(smem) & 127u) != 0u) {
+    if (threadIdx.x == 0) atomicOr(err ? err : &g_box_err, 2);
+    return false;
+  }
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + B::o_bar);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_proxy_async();
+  }
+  __syncthreads();
+  return true;
+}
+
+template <int MODE, int H>
+__global__ void __launch_bounds__(kThreads, 3)
+    k_box_tma(const BoxArgs a, const __grid_constant__ CUtensorMap map_w, const __grid_constant__ CUtensorMap map_f,
+              const __grid_constant__ CUtensorMap map_z, const __grid_constant__ CUtensorMap map_r) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  if (a.stop != nullptr && *(volatile const int*)a.stop != 0) return;
+  if (!tma_cta_setup<MODE, H>(smem, a.err)) return;
+  uint32_t pa = 0, pb = 0;
+  const size_t part = (size_t)blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
+  box_tma_body<MODE, H>(a, blockIdx.x, blockIdx.y, blockIdx.z, part, &map_w, &map_f, &map_z, &map_r, smem, pa,
+                        pb);
+}
+
+// Batched launch over the work table of many volumes (as k_box_h_batch): work
+// item i belongs to volume p with offset[p] <= i < offset[p + 1].  The tensor
+// maps of volume p are maps[4p .. 4p + 3] (W box, F box of m, F box of zs, r
+// tile) in global memory, written by the host before the launch.
+template <int MODE, int H>
+__global__ void __launch_bounds__(kThreads, 3)
+    k_box_tma_batch(const __grid_constant__ BoxBatch bt, const CUtensorMap* __restrict__ maps) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  if (!tma_cta_setup<MODE, H>(smem, nullptr)) return;
+  uint32_t pa = 0, pb = 0;
+  const int total = bt.offset[bt.count];
+  for (int i = blockIdx.x; i < total; i += gridDim.x) {
+    int p = 0;
+    while (p + 1 < bt.count && bt.offset[p + 1] <= i) ++p;
+    const int j = i - bt.offset[p];
+    const dim3 g = bt.grid[p];
+    const int bx = j % g.x, by = (j / g.x) % g.y, bz = j / (g.x * g.y);
+    const CUtensorMap* m = maps + 4 * p;
+    if (threadIdx.x == 0) {
+      // the maps reach the tensor-map proxy through global memory
+      for (int k = 0; k < 4; ++k)
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                         reinterpret_cast<uint64_t>(m + k))
+                     : "memory");
+    }
+    __syncthreads();   // the previous body's last reads of the staging buffers are done
+    if (!box_tma_body<MODE, H>(bt.args[p], bx, by, bz, (size_t)j, m, m + 1, m + 2, m + 3, smem, pa, pb)) return;
   }
 }
 
@@ -528,49 +583,77 @@ bool encode(CUtensorMap* m, const float* base, int rank, int nx, int ny, int nz,
 
 constexpr int kMaxDevices = 64;
 
+// The four tensor maps of a volume: W box of src, F box of src, F box of zs, r tile.
 template <int MODE, int H>
-cudaError_t launch_tma(const BoxArgs& a, const BoxPlan& p, cudaStream_t s) {
+bool encode_maps(const BoxArgs& a, CUtensorMap* m) {
   using B = TmaLayout<MODE, H>;
-  static int set[kMaxDevices] = {};
-  CUtensorMap mw{}, mf{}, mz{}, mr{};
-  if (!encode(&mw, a.src, 3, a.nx, a.ny, a.nz, B::WXT, B::WY, 1) ||
-      !encode(&mf, a.src, 3, a.nx, a.ny, a.nz, B::FXT, B::FY, 1))
-    return cudaErrorInvalidValue;
-  if (MODE != kModeStatic && !encode(&mz, a.zs, 3, a.nx, a.ny, a.nz, B::FXT, B::FY, 1))
-    return cudaErrorInvalidValue;
-  if (MODE == kModeIterate && !encode(&mr, a.r, 4, a.nx, a.ny, a.nz, B::TX, B::TY, 3))
-    return cudaErrorInvalidValue;
+  for (int k = 0; k < 4; ++k) m[k] = CUtensorMap{};
+  if (!encode(&m[0], a.src, 3, a.nx, a.ny, a.nz, B::WXT, B::WY, 1) ||
+      !encode(&m[1], a.src, 3, a.nx, a.ny, a.nz, B::FXT, B::FY, 1))
+    return false;
+  if (MODE != kModeStatic && !encode(&m[2], a.zs, 3, a.nx, a.ny, a.nz, B::FXT, B::FY, 1)) return false;
+  if (MODE == kModeIterate && !encode(&m[3], a.r, 4, a.nx, a.ny, a.nz, B::TX, B::TY, 3)) return false;
+  return true;
+}
+
+// Opt-in shared memory and the shared-memory carveout, once per device and kernel.
+template <typename K>
+cudaError_t prepare(K kernel, size_t smem, int* set) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  if (!set[dev]) {
-    e = cudaFuncSetAttribute(k_box_tma<MODE, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B::bytes);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_box_tma<MODE, H>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             (int)cudaSharedmemCarveoutMaxShared);
-    if (e != cudaSuccess) return e;
-    set[dev] = 1;
-  }
-  k_box_tma<MODE, H><<<p.grid, kThreads, B::bytes, s>>>(a, mw, mf, mz, mr);
+  if (set[dev]) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           (int)cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  set[dev] = 1;
+  return cudaSuccess;
+}
+
+template <int MODE, int H>
+cudaError_t launch_tma(const BoxArgs& a, const BoxPlan& p, cudaStream_t s) {
+  using B = TmaLayout<MODE, H>;
+  static int set[kMaxDevices] = {};
+  CUtensorMap m[4];
+  if (!encode_maps<MODE, H>(a, m)) return cudaErrorInvalidValue;
+  cudaError_t e = prepare(k_box_tma<MODE, H>, B::bytes, set);
+  if (e != cudaSuccess) return e;
+  k_box_tma<MODE, H><<<p.grid, kThreads, B::bytes, s>>>(a, m[0], m[1], m[2], m[3]);
   return cudaGetLastError();
 }
 
 template <int MODE, int H>
-int occ_tma(size_t smem) {
-  if (cudaFuncSetAttribute(k_box_tma<MODE, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(k_box_tma<MODE, H>, cudaFuncAttributePreferredSharedMemoryCarveout,
+cudaError_t launch_tma_batch(const BoxBatch* bt, const CUtensorMap* maps, int grid, cudaStream_t s) {
+  using B = TmaLayout<MODE, H>;
+  static int set[kMaxDevices] = {};
+  cudaError_t e = prepare(k_box_tma_batch<MODE, H>, B::bytes, set);
+  if (e != cudaSuccess) return e;
+  k_box_tma_batch<MODE, H><<<grid, kThreads, B::bytes, s>>>(*bt, maps);
+  return cudaGetLastError();
+}
+
+template <typename K>
+int occupancy(K kernel, size_t smem) {
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                            (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess) {
     cudaGetLastError();
     return 1;
   }
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_box_tma<MODE, H>, kThreads, smem) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, kThreads, smem) != cudaSuccess) {
     cudaGetLastError();
     return 1;
   }
   return n < 1 ? 1 : n;
+}
+
+template <int MODE, int H>
+int occ_tma(size_t smem) {
+  return occupancy(k_box_tma<MODE, H>, smem);
 }
 
 // Compile-time table over (mode, H): fn(mode, h) dispatches to F<MODE, H>.
@@ -611,6 +694,20 @@ struct Launch {
   static cudaError_t run(const BoxArgs* a, const BoxPlan* p, cudaStream_t s) { return launch_tma<MODE, H>(*a, *p, s); }
 };
 template <int MODE, int H>
+struct Maps {
+  static bool run(const BoxArgs* a, CUtensorMap* m) { return encode_maps<MODE, H>(*a, m); }
+};
+template <int MODE, int H>
+struct LaunchBatch {   // iteration mode only
+  static cudaError_t run(const BoxBatch* bt, const CUtensorMap* maps, int grid, cudaStream_t s) {
+    return MODE == kModeIterate ? launch_tma_batch<kModeIterate, H>(bt, maps, grid, s) : cudaErrorInvalidValue;
+  }
+};
+template <int MODE, int H>
+struct OccBatch {
+  static int run(size_t smem) { return occupancy(k_box_tma_batch<kModeIterate, H>, smem); }
+};
+template <int MODE, int H>
 struct Extent {   // smallest volume extents that hold every TMA box of this kernel
   static int run(int axis) {
     using B = TmaLayout<MODE, H>;
@@ -647,6 +744,18 @@ int box_tma_occupancy(int mode, int h, size_t smem) { return dispatch<Occ, int>(
 
 cudaError_t box_tma_launch(int mode, const BoxArgs& a, const BoxPlan& p, cudaStream_t s) {
   return dispatch<Launch, cudaError_t>(mode, a.hx, cudaErrorInvalidValue, &a, &p, s);
+}
+
+bool box_tma_encode(int mode, const BoxArgs& a, void* maps) {
+  return dispatch<Maps, bool>(mode, a.hx, false, &a, static_cast<CUtensorMap*>(maps));
+}
+
+int box_tma_batch_occupancy(int h, size_t smem) { return dispatch<OccBatch, int>(kModeIterate, h, 1, smem); }
+
+cudaError_t box_tma_launch_batch(const BoxBatch& bt, const void* maps, int h, int grid, cudaStream_t s) {
+  if (grid < 1) return cudaSuccess;
+  return dispatch<LaunchBatch, cudaError_t>(kModeIterate, h, cudaErrorInvalidValue, &bt,
+                                            static_cast<const CUtensorMap*>(maps), grid, s);
 }
 
 cudaError_t box_tma_error(cudaStream_t s, int* flag) {

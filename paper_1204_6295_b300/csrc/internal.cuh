@@ -95,6 +95,12 @@ int box_tma_occupancy(int mode, int h, size_t smem);
 cudaError_t box_tma_launch(int mode, const BoxArgs& a, const BoxPlan& p, cudaStream_t s);
 // Reads (synchronising s) and clears the library's own error word into *flag.
 cudaError_t box_tma_error(cudaStream_t s, int* flag);
+// Batched iteration-mode launch: the tensor maps of volume p are maps[4p .. 4p+3]
+// (kTmaMapBytes each, in device memory), written by box_tma_encode on the host.
+constexpr size_t kTmaMapBytes = 128;
+bool box_tma_encode(int mode, const BoxArgs& a, void* maps /* 4 x kTmaMapBytes, 64-byte aligned */);
+int box_tma_batch_occupancy(int h, size_t smem);
+cudaError_t box_tma_launch_batch(const BoxBatch& bt, const void* maps, int h, int grid, cudaStream_t s);
 
 // Plan a launch (grid, z chunk, dynamic shared memory) for a volume and patch.
 BoxPlan box_plan(int mode, int nx, int ny, int nz, int hx, int hy, int hz, int num_sms);
