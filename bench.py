@@ -292,6 +292,7 @@ def time_differentiable(disc, torch, w, pair_dev, field_dev, kt, reps=5):
                     "workload), patch statistics recomputed in the backward pass"}
 
 
+BATCH_PAIRS_PER_RANK = 16
 BATCH_WORKLOAD = dict(patch=(9, 9, 9), sigma=1.5, levels=3, iters=(100, 100, 100))
 
 
@@ -299,13 +300,18 @@ def time_batched(disc, torch, dist, steps=2):
     """The batched workload: 16 pairs of uneven size advanced together, against
     the plain per-pair loop over the same pairs (separate contexts, one after the
     other), both timed with CUDA events on the current stream."""
-    from paper_1204_6295_b300 import phantom
-    images = phantom.batch_pair_images()
+    from paper_1204_6295_b300 import phantom, shard
     bw = BATCH_WORKLOAD
-    units = 0
-    for ct, _ in images:
-        nz, ny, nx = ct.shape
-        units += schedule_units(dict(bw, dims=(nx, ny, nz)))
+    world = dist.get_world_size() if dist else 1
+    rank = dist.get_rank() if dist else 0
+    # 16 pairs per rank (weak scaling), sharded across ranks by the
+    # longest-processing-time rule on their voxel-iterations; no exchange
+    n_pairs = BATCH_PAIRS_PER_RANK * world
+    sizes = phantom.batch_sizes(n_pairs)
+    loads = [schedule_units(dict(bw, dims=d)) for d in sizes]
+    share = shard.lpt_assign(loads, world)
+    images = phantom.batch_pair_images(n_pairs, indices=share[rank])
+    units = sum(loads)                            # the whole job's voxel-iterations
     s = torch.cuda.current_stream()
 
     def timed(step):
@@ -348,16 +354,19 @@ def time_batched(disc, torch, dist, steps=2):
     t_loop = timed(loop_step)
     for reg, _ in regs:
         reg.close()
-    world = dist.get_world_size() if dist else 1
-    return {"value": world * units / t_batch / 1e9, "unit": UNIT,
-            "plain_loop_value": world * units / t_loop / 1e9,
+    return {"value": units / t_batch / 1e9, "unit": UNIT,
+            "plain_loop_value": units / t_loop / 1e9,
             "speedup_vs_plain_loop": t_loop / t_batch, "ms_per_step": t_batch * 1e3,
             "plain_loop_ms_per_step": t_loop * 1e3, "voxel_iterations_per_step": units,
-            "pairs": [list(ct.shape[::-1]) for ct, _ in images],
+            "pairs": [list(d) for d in sizes],
+            "pairs_per_rank": [len(x) for x in share],
+            "max_over_mean_rank_load": max(shard.rank_loads(loads, share)) * world / units,
             "tuning_items_grid_zmult_per_level_fine_first": tuning,
-            "what": "16 head-and-neck pairs (2s, 2s, s), s in 64..160, patch 9^3, sigma 1.5, "
-                    "3 levels x 100 iterations: disc_batch (one launch per step over all pairs, "
-                    "graph per level) vs 16 separate contexts run one after the other"}
+            "what": "16 head-and-neck pairs (2s, 2s, s) per rank, s in 64..160, patch 9^3, "
+                    "sigma 1.5, 3 levels x 100 iterations, pairs sharded across ranks by the "
+                    "longest-processing-time rule (no exchange): disc_batch (one launch per step "
+                    "over a rank's pairs, graph per level) vs its pairs' separate contexts run one "
+                    "after the other; value = all ranks' voxel-iterations / slowest rank's time"}
 
 
 def reduce_max(dist, seconds, device="cuda"):
