@@ -7,7 +7,7 @@ calls it and shares no code with it.
 Every function follows one passage of the paper, in the paper's notation, with
 numpy float64 arrays and no blocking, fusion or reordering beyond what the
 definition states.  Where the paper is silent or garbled the reading used is
-stated in the docstring (readings R1..R16, listed with their reasons in the
+stated in the docstring (readings R1..R20, listed with their reasons in the
 design notes of the repository).
 
 Layout: images are ``[nz][ny][nx]`` (x fastest); fields are ``[3][nz][ny][nx]``
@@ -17,8 +17,9 @@ Roles (Sec. 2.2): the moving image ``I_m`` is the planning CT, the static image
 ``I_s`` is the CBCT; the field ``r`` relates them by ``I_m(x + r(x)) = I_s(x)``
 (Sec. 2.1).
 
-Pins: every function here is checked in ``tests/test_oracle_pins.py`` against
-brute force, closed forms, library special cases or invariants.  The one
+Pins: every function here is checked in ``tests/test_oracle_pins.py`` and
+``tests/test_oracle_mask.py`` against brute force, closed forms, library
+special cases or invariants.  The one
 function without an independent pin is noted as "parity unpinned" below
 (none at present).
 """
@@ -370,6 +371,135 @@ def should_stop(history, eps, window=10):
 # Algorithm A1: one iteration at one level, and the whole driver
 # ---------------------------------------------------------------------------
 
+# ---------------------------------------------------------------------------
+# Eqs. (7)-(10), Sec. 2.3 and Algorithm A1 step 2: the mask xi of the voxels
+# whose a, b (Eqs. 5-6) cannot be trusted, and their interpolation from the
+# trusted ones, weighted by CBCT intensity similarity.
+# Readings (R17-R20):
+#  R17 xi = 1 also where Var(S) <= var_floor, where a is undefined.
+#  R18 HU0 = hu0_factor |dHU| with dHU the global shift of Sec. 2.3 (factor 2);
+#      a_m is the median of a over the voxels with Var(S) > var_floor, at the
+#      finest level with r = 0, before the first iteration; a_min = a_lo a_m,
+#      a_max = a_hi a_m (0.5 and 1.5).
+#  R19 Fill passes are Jacobi sweeps: a pass averages over the neighbours in T
+#      that were known before it (xi = 0, or filled by an earlier pass); a
+#      voxel without such a neighbour waits for a later pass.  Passes stop when
+#      no voxel is left, when a pass fills nothing, or after max_passes; a
+#      voxel never filled keeps a = b = 0 (the paper's initial value).
+#  R20 The weight exponent (I_s(i) - I_s(x))^2 / h^2 is capped at 80, so that
+#      a voxel with a known neighbour always gets a positive weight sum in any
+#      floating-point precision (exp(-80) ~ 1.8e-35 is a normal float).
+# ---------------------------------------------------------------------------
+
+FILL_EXP_CAP = 80.0
+
+
+def ratio_median(I_m, I_s, half, var_floor=1e-6):
+    """a_m of Sec. 2.3: median of a = STD(M)/STD(S) with r = 0 (m = I_m).
+
+    Over the voxels with Var(S) > var_floor (reading R18)."""
+    EM, EM2 = patch_moments(I_m, half)
+    ES, ES2 = patch_moments(I_s, half)
+    var_m = np.maximum(EM2 - EM * EM, 0.0)
+    var_s = np.maximum(ES2 - ES * ES, 0.0)
+    ok = var_s > var_floor
+    std_m = np.where(var_m > var_floor, np.sqrt(var_m), 0.0)
+    a = std_m[ok] / np.sqrt(var_s[ok])
+    return float(np.median(a)) if a.size else 0.0
+
+
+def mask_xi(m, I_s, a, valid, hu0, a_min, a_max):
+    """xi of Eq. (7): 1 where |I_m^(k) - I_s| > HU0 or a is outside
+    [a_min, a_max]; also where a is undefined (valid false, reading R17)."""
+    m = np.asarray(m, np.float64)
+    I_s = np.asarray(I_s, np.float64)
+    return (np.abs(m - I_s) > hu0) | (~valid) | (a < a_min) | (a > a_max)
+
+
+def _shifted(X, d, fill):
+    """Y[i] = X[i + d] where i + d is inside the volume, else `fill`."""
+    Y = np.full(X.shape, fill, dtype=X.dtype)
+    src, dst = [], []
+    for ax, dd in zip((2, 1, 0), d):
+        n = X.shape[ax]
+        lo, hi = max(0, -dd), min(n, n - dd)
+        if lo >= hi:
+            return Y
+        src.append((ax, slice(lo + dd, hi + dd)))
+        dst.append((ax, slice(lo, hi)))
+    s_src = [slice(None)] * 3
+    s_dst = [slice(None)] * 3
+    for (ax, sl_s), (_, sl_d) in zip(src, dst):
+        s_src[ax] = sl_s
+        s_dst[ax] = sl_d
+    Y[tuple(s_dst)] = X[tuple(s_src)]
+    return Y
+
+
+def fill_coefficients(a, b, xi, I_s, h, t_half=(3, 3, 1), max_passes=32):
+    """Eqs. (8)-(10): a, b at xi = 1 from the known voxels of the box T.
+
+    T has half sizes t_half = (tx, ty, tz) (7 x 7 x 3 in Sec. 2.3 -> (3, 3, 1)),
+    truncated at the volume.  Weights w_i = exp(-(I_s(i) - I_s(x))^2 / h^2)
+    (exponent capped, R20).  Jacobi passes (R19).  Returns (a, b, stamp):
+    stamp is 0 where xi = 0, the pass that filled the voxel, or -1.
+    """
+    xi = np.asarray(xi, bool)
+    I_s = np.asarray(I_s, np.float64)
+    a = np.where(xi, 0.0, np.asarray(a, np.float64))
+    b = np.where(xi, 0.0, np.asarray(b, np.float64))
+    stamp = np.where(xi, -1, 0).astype(np.int64)
+    offsets = [(dx, dy, dz) for dz in range(-t_half[2], t_half[2] + 1)
+               for dy in range(-t_half[1], t_half[1] + 1)
+               for dx in range(-t_half[0], t_half[0] + 1)]
+    for p in range(1, max_passes + 1):
+        todo = stamp < 0
+        if not todo.any():
+            break
+        known = (stamp >= 0).astype(np.float64)
+        num_a = np.zeros(a.shape)
+        num_b = np.zeros(a.shape)
+        den = np.zeros(a.shape)
+        for d in offsets:
+            k = _shifted(known, d, 0.0)
+            e = ((_shifted(I_s, d, 0.0) - I_s) / h) ** 2
+            w = np.exp(-np.minimum(e, FILL_EXP_CAP)) * k     # Eq. (10), known neighbours only
+            num_a += w * _shifted(a, d, 0.0)
+            num_b += w * _shifted(b, d, 0.0)
+            den += w
+        fill = todo & (den > 0.0)
+        if not fill.any():
+            break
+        a[fill] = num_a[fill] / den[fill]                  # Eq. (8)
+        b[fill] = num_b[fill] / den[fill]                  # Eq. (9)
+        stamp[fill] = p
+    return a, b, stamp
+
+
+@dataclass
+class MaskState:
+    """Thresholds of Eq. (7) fixed before the first iteration (reading R18)."""
+    hu0: float
+    a_min: float
+    a_max: float
+
+
+def correct_masked(m, I_s, half, mask: MaskState, h, t_half=(3, 3, 1), max_passes=32,
+                   var_floor=1e-6):
+    """I'_s = a I_s + b with a, b from Eqs. (5)-(6) where xi = 0 and from the
+    fill of Eqs. (8)-(10) where xi = 1 (Algorithm A1 steps 1-3).
+
+    Returns (I'_s, xi, stamp)."""
+    EM, EM2 = patch_moments(m, half)
+    ES, ES2 = patch_moments(I_s, half)
+    var_s = np.maximum(ES2 - ES * ES, 0.0)
+    valid = var_s > var_floor
+    a, b = intensity_coefficients(m, I_s, half, var_floor)
+    xi = mask_xi(m, I_s, a, valid, mask.hu0, mask.a_min, mask.a_max)
+    a, b, stamp = fill_coefficients(a, b, xi, I_s, h, t_half, max_passes)
+    return a * np.asarray(I_s, np.float64) + b, xi, stamp
+
+
 @dataclass
 class Params:
     patch: tuple = (3, 3, 3)       # odd sizes (px, py, pz); Sec. 3.3 uses 3x3x3
@@ -383,21 +513,37 @@ class Params:
     global_shift: bool = True
     var_floor: float = 1e-6
     den_floor: float = 1e-9
+    # Eqs. (7)-(10); mask_mode 0 keeps xi = 0 everywhere
+    mask_mode: int = 0
+    hu0_factor: float = 2.0        # HU0 = hu0_factor |dHU| (Sec. 2.3)
+    a_lo: float = 0.5              # a_min = a_lo a_m
+    a_hi: float = 1.5              # a_max = a_hi a_m
+    fill_h: float = 50.0           # h of Eq. (10), HU (not given by the paper)
+    fill_t: tuple = (7, 7, 3)      # T (Sec. 2.3)
+    fill_passes: int = 32
 
     @property
     def half(self):
         return tuple((p - 1) // 2 for p in self.patch)
 
+    @property
+    def fill_half(self):
+        return tuple((t - 1) // 2 for t in self.fill_t)
 
-def iteration(I_m, I_s, r, p: Params):
+
+def iteration(I_m, I_s, r, p: Params, mask: MaskState = None):
     """One pass of Algorithm A1 steps 1-6 at one level.
 
     Returns (r_new, dr, l, extras) where extras holds m = I_m^(k) and f = I'_s.
-    Step 2 (interpolation of a, b where xi = 1, Eqs. 7-10) is not part of this
-    path: the mask is taken as all-zero.
+    Step 2 (interpolation of a, b where xi = 1, Eqs. 7-10) runs when
+    p.mask_mode is set (thresholds in `mask`); otherwise xi = 0 everywhere.
     """
     m = warp(I_m, r)                                   # update the moving image
-    f = correct(m, I_s, p.half, p.var_floor)           # steps 1 and 3
+    if p.mask_mode:
+        f, _xi, _st = correct_masked(m, I_s, p.half, mask, p.fill_h, p.fill_half, p.fill_passes,
+                                     p.var_floor)      # steps 1-3
+    else:
+        f = correct(m, I_s, p.half, p.var_floor)       # steps 1 and 3
     dr = force(m, f, p.force_mode, p.den_floor)        # step 4
     u = r + dr                                         # step 5
     r_new = gaussian_smooth_field(u, p.sigma, p.radius)  # step 6
@@ -421,8 +567,13 @@ def register(I_m, I_s, p: Params, return_history=False):
     """
     I_m = np.asarray(I_m, np.float64)
     I_s = np.asarray(I_s, np.float64)
+    shifted, dhu = global_shift(I_m, I_s)
     if p.global_shift:
-        I_s, _ = global_shift(I_m, I_s)
+        I_s = shifted
+    mask = None
+    if p.mask_mode:                                     # reading R18
+        a_m = ratio_median(I_m, I_s, p.half, p.var_floor)
+        mask = MaskState(p.hu0_factor * abs(dhu), p.a_lo * a_m, p.a_hi * a_m)
     pm = build_pyramid(I_m, p.levels)
     ps = build_pyramid(I_s, p.levels)
     r = np.zeros((3,) + pm[-1].shape)
@@ -432,7 +583,7 @@ def register(I_m, I_s, p: Params, return_history=False):
         n_it = p.iters[p.levels - 1 - lev]
         hist = []
         for _k in range(n_it):
-            r, _dr, l, ex = iteration(pm[lev], ps[lev], r, p)
+            r, _dr, l, ex = iteration(pm[lev], ps[lev], r, p, mask)
             f = ex["f"]
             hist.append(l)
             if should_stop(hist, p.stop_eps, p.stop_window):
