@@ -80,11 +80,28 @@ typedef struct {
   int32_t force_mode;    /* DISC_FORCE_THIRION or DISC_FORCE_DOUBLE            */
   int32_t global_shift;  /* 1 = shift I_s by mean(I_m) - mean(I_s) (Sec. 2.3)  */
   float var_floor;       /* patch variance (HU^2) at or below which STD = 0    */
+  /* Mask and fill of a, b (Eqs. 7-10, Algorithm A1 step 2).  With mask_mode 1
+   * every iteration sets xi = 1 where |I_m^(k) - I_s| > HU0, where a is outside
+   * [a_min, a_max] or undefined (STD(S) = 0), and replaces a, b there by the
+   * weighted mean of Eqs. 8-10 over the known voxels of the box T, in Jacobi
+   * passes (a pass uses the voxels known before it) until none is left, a pass
+   * fills nothing, or fill_passes passes have run; a voxel never filled keeps
+   * a = b = 0.  HU0 = hu0_factor |dHU| (dHU the global shift, computed even
+   * when it is not applied); a_min = a_lo a_m, a_max = a_hi a_m with a_m the
+   * median of STD(M)/STD(S) at the finest level with r = 0, fixed at
+   * disc_set_images.  Weights exp(-min((I_s(i) - I_s(x))^2 / h^2, 80)). */
+  int32_t mask_mode;     /* 0: off (xi = 0 everywhere); 1: on                  */
+  float hu0_factor;      /* Sec. 2.3: 2                                         */
+  float a_lo, a_hi;      /* Sec. 2.3: 0.5, 1.5                                  */
+  float fill_h;          /* h of Eq. 10, HU (the paper gives none): 50          */
+  int32_t fill_t[3];     /* odd box T sizes (x, y, z), Sec. 2.3: 7, 7, 3         */
+  int32_t fill_passes;   /* at most this many fill passes per iteration: 32     */
 } disc_params;
 
 /* Fill *p with defaults: patch 3x3x3, sigma 1, radius 0, 2 levels of 50
  * iterations, stop_eps 0 (fixed counts), window 10, THIRION, global shift on,
- * var_floor 1e-6.  Returns DISC_ERR_ARG for NULL. */
+ * var_floor 1e-6, mask off (hu0_factor 2, a_lo 0.5, a_hi 1.5, fill_h 50,
+ * fill_t 7x7x3, fill_passes 32).  Returns DISC_ERR_ARG for NULL. */
 disc_status disc_params_default(disc_params* p);
 
 /* Human-readable name of a status code (static storage, never NULL). */
@@ -146,6 +163,11 @@ disc_status disc_get_progress(disc_ctx* ctx, int32_t* level, int32_t* iter,
 disc_status disc_get_norm_history(disc_ctx* ctx, int32_t level, float* out,
                                   int32_t cap, int32_t* count);
 
+/* The mask thresholds fixed by disc_set_images (mask_mode 1): HU0 and a_m
+ * (a_min = a_lo a_m, a_max = a_hi a_m).  DISC_ERR_STATE before images or
+ * with the mask off.  Any pointer may be NULL. */
+disc_status disc_get_mask_constants(disc_ctx* ctx, float* hu0, float* a_m);
+
 /* Release every resource of the context.  NULL is accepted. */
 disc_status disc_destroy(disc_ctx* ctx);
 
@@ -157,7 +179,7 @@ disc_status disc_destroy(disc_ctx* ctx);
  * pair's tiles, a level's iterations are one CUDA graph, and the tile
  * scheduling of the moment/force launch is tuned per level at first use.
  * All pairs share the parameters and the schedule.  Cubic patches of 3..15
- * voxels and Gaussian radius 1..8 only (DISC_ERR_ARG otherwise).
+ * voxels, Gaussian radius 1..8 and mask_mode 0 only (DISC_ERR_ARG otherwise).
  * ------------------------------------------------------------------- */
 typedef struct disc_batch disc_batch;
 
@@ -317,6 +339,41 @@ disc_status disc_k_pass_a_static(const float* Im, const float* zs, const float* 
  * alias u. */
 disc_status disc_k_gauss(const float* u, float* r, int32_t nx, int32_t ny, int32_t nz,
                          float sigma, int32_t radius, void* stream);
+
+/* The CBCT normalisation of disc_k_static_norm, and sd = STD(S) per voxel
+ * (0 where Var(S) <= var_floor): the static patch statistics the mask of
+ * Eq. 7 needs.  sd may be NULL. */
+disc_status disc_k_static_stats(const float* Is, float* zs, float* sd, int32_t nx, int32_t ny,
+                                int32_t nz, const int32_t patch[3], float qscale, float var_floor,
+                                void* stream);
+
+/* a_m of Sec. 2.3: the median of a = STD(M)/STD(S) (Eq. 5) over the voxels
+ * with STD(S) > 0, for the image m (m = I_m for r = 0), with zs and sd from
+ * disc_k_static_stats.  a_work (N floats, caller-owned) receives a, -1 where
+ * STD(S) = 0.  *median_out (device double) receives the mean of the lower and
+ * upper medians, -1 if no voxel qualifies. */
+disc_status disc_k_ratio_median(const float* m, const float* zs, const float* sd, float* a_work,
+                                double* median_out, int32_t nx, int32_t ny, int32_t nz,
+                                const int32_t patch[3], float qscale, float var_floor, void* stream);
+
+/* Algorithm A1 steps 1-3 with the mask: for the warped image m, a and b of
+ * Eqs. 5-6, the mask xi of Eq. 7 (thresholds hu0, a_min, a_max) and the fill
+ * of Eqs. 8-10 (box fill_t, weight scale fill_h, at most fill_passes Jacobi
+ * passes).  Outputs (N each, caller-owned): a, b; d = I'_s - m with
+ * I'_s = a I_s + b; stamp = 0 where xi = 0, the pass that filled the voxel, or
+ * -1.  *remaining_out (device int32, may be NULL): voxels left unfilled. */
+disc_status disc_k_correct_masked(const float* m, const float* Is, const float* zs, const float* sd,
+                                  float* a, float* b, float* d, int32_t* stamp, int32_t* remaining_out,
+                                  int32_t nx, int32_t ny, int32_t nz, const int32_t patch[3],
+                                  float qscale, float var_floor, float hu0, float a_min, float a_max,
+                                  float fill_h, const int32_t fill_t[3], int32_t fill_passes,
+                                  void* stream);
+
+/* Demons force (Eq. 1, Algorithm A1 steps 4-5) from d = I'_s - m and m:
+ * grad I'_s = grad d + grad m by the path's differences, u = r + dr;
+ * norms_out (device double[2], may be NULL): sum |dr|, sum |r|. */
+disc_status disc_k_force(const float* m, const float* d, const float* r, float* u, double* norms_out,
+                         int32_t nx, int32_t ny, int32_t nz, int32_t force_mode, void* stream);
 
 /* Error word of the kernel-level calls above.  Their moment passes read
  * the volume through bulk tensor copies completed on shared-memory

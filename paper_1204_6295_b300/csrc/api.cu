@@ -49,6 +49,52 @@ disc_status check_device_error(disc_ctx* ctx) {
     if (s_ != DISC_OK) return s_;                     \
   } while (0)
 
+disc_status check_patch(const int32_t patch[3], int* h) {
+  if (!patch) return DISC_ERR_ARG;
+  for (int a = 0; a < 3; ++a) {
+    if (patch[a] < 1 || patch[a] > 2 * DISC_MAX_HALF_PATCH + 1 || patch[a] % 2 == 0) return DISC_ERR_ARG;
+    h[a] = (patch[a] - 1) / 2;
+  }
+  return DISC_OK;
+}
+
+// Common argument checks and launch of the kernel-level box-pass calls.
+disc_status kcheck(int32_t nx, int32_t ny, int32_t nz, const int32_t patch[3], float qscale,
+                          float var_floor, int* h) {
+  if (!(qscale > 0.0f) || !(var_floor >= 0.0f)) return DISC_ERR_ARG;
+  disc_status st = check_patch(patch, h);
+  if (st != DISC_OK) return st;
+  if (nx < 1 || ny < 1 || nz < 1 || (double)nx * ny * nz * 3.0 >= 2147483647.0) return DISC_ERR_SHAPE;
+  return DISC_OK;
+}
+
+BoxArgs kargs(int32_t nx, int32_t ny, int32_t nz, const int* h, float qscale, float var_floor) {
+  BoxArgs a{};
+  a.nx = nx;
+  a.ny = ny;
+  a.nz = nz;
+  a.hx = h[0];
+  a.hy = h[1];
+  a.hz = h[2];
+  a.qscale = qscale;
+  a.inv_qscale = 1.0f / qscale;
+  a.var_floor = var_floor;
+  return a;
+}
+
+disc_status klaunch(int mode, const BoxArgs& a, cudaStream_t s) {
+  int dev = 0, sms = kNumSMs;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const BoxPlan p = box_plan(mode, a.nx, a.ny, a.nz, a.hx, a.hy, a.hz, sms);
+  if (p.grid.x == 0) return DISC_ERR_SHAPE;
+  if (box_launch(mode, a, p, s) != cudaSuccess) {
+    cudaGetLastError();
+    return DISC_ERR_CUDA;
+  }
+  return DISC_OK;
+}
+
 disc_status check_params(const disc_params* p) {
   if (!p) return DISC_ERR_ARG;
   for (int a = 0; a < 3; ++a)
@@ -63,6 +109,15 @@ disc_status check_params(const disc_params* p) {
   if (p->force_mode != DISC_FORCE_THIRION && p->force_mode != DISC_FORCE_DOUBLE) return DISC_ERR_ARG;
   if (!(p->var_floor >= 0.0f)) return DISC_ERR_ARG;
   if (p->stop_window < 1) return DISC_ERR_ARG;
+  if (p->mask_mode != 0 && p->mask_mode != 1) return DISC_ERR_ARG;
+  if (p->mask_mode) {
+    if (!(p->hu0_factor >= 0.0f) || !(p->a_lo >= 0.0f) || !(p->a_hi >= p->a_lo) || !(p->fill_h > 0.0f) ||
+        !std::isfinite(p->hu0_factor) || !std::isfinite(p->a_hi) || !std::isfinite(p->fill_h))
+      return DISC_ERR_ARG;
+    for (int a = 0; a < 3; ++a)
+      if (p->fill_t[a] < 1 || p->fill_t[a] > 15 || p->fill_t[a] % 2 == 0) return DISC_ERR_ARG;
+    if (p->fill_passes < 1 || p->fill_passes > 1024) return DISC_ERR_ARG;
+  }
   return DISC_OK;
 }
 
@@ -78,8 +133,16 @@ void free_levels(disc_ctx* c) {
     cudaFree(v.u);
     cudaFree(v.t);
     cudaFree(v.hist);
+    cudaFree(v.sd);
+    cudaFree(v.ab);
+    cudaFree(v.dm);
+    cudaFree(v.stamp);
+    cudaFree(v.list);
+    cudaFree(v.cnt);
     v = Level{};
   }
+  cudaFree(c->d_mwork);
+  c->d_mwork = nullptr;
   cudaFree(c->partials);
   c->partials = nullptr;
   c->max_parts = 0;
@@ -123,6 +186,81 @@ BoxArgs box_args(const disc_ctx* c, const Level& v) {
   return a;
 }
 
+// Mask-and-fill correction of level l for the current m (Algorithm A1 steps
+// 1-3 with Eqs. 7-10): d = I'_s - m in v.dm.  stop: the level's stop flag, or
+// NULL to run regardless.
+cudaError_t queue_mask_fill(disc_ctx* c, int l, const int* stop) {
+  Level& v = c->lev[l];
+  cudaError_t e = cudaMemsetAsync(v.cnt, 0, (c->p.fill_passes + 1) * sizeof(int), c->s);
+  if (e != cudaSuccess) return e;
+  BoxArgs a = box_args(c, v);
+  a.src = v.m;
+  a.zs = v.zs;
+  a.is = v.Is;
+  a.sd = v.sd;
+  a.out = v.dm;
+  a.a_out = v.ab;
+  a.b_out = v.ab + v.N;
+  a.stamp = v.stamp;
+  a.list = v.list;
+  a.count = v.cnt;
+  a.hu0 = c->mask_hu0;
+  a.a_min = c->p.a_lo * c->mask_am;
+  a.a_max = c->p.a_hi * c->mask_am;
+  a.stop = stop;
+  a.qscale = c->qs_m;
+  a.inv_qscale = 1.0f / c->qs_m;
+  e = box_launch(kModeMaskAB, a, v.pm, c->s);
+  FillArgs f{};
+  f.is = v.Is;
+  f.m = v.m;
+  f.a = v.ab;
+  f.b = v.ab + v.N;
+  f.d = v.dm;
+  f.stamp = v.stamp;
+  f.cnt = v.cnt;
+  f.nx = v.nx;
+  f.ny = v.ny;
+  f.nz = v.nz;
+  f.tx = (c->p.fill_t[0] - 1) / 2;
+  f.ty = (c->p.fill_t[1] - 1) / 2;
+  f.tz = (c->p.fill_t[2] - 1) / 2;
+  f.inv_h = 1.0f / c->p.fill_h;
+  f.stop = stop;
+  for (int p = 1; p <= c->p.fill_passes && e == cudaSuccess; ++p) {
+    f.pass = p;
+    f.list_in = v.list + ((p - 1) % 2) * v.N;
+    f.list_out = v.list + (p % 2) * v.N;
+    e = launch_fill_pass(f, (int)v.N, c->s);
+  }
+  return e;
+}
+
+// The masked iteration: mask and fill, force from d and m, Gaussian (+ warp), norm.
+cudaError_t queue_masked(disc_ctx* c, int l, int n, const GaussArgs& g, const NormState& st) {
+  Level& v = c->lev[l];
+  ForceArgs fa{};
+  fa.d = v.dm;
+  fa.m = v.m;
+  fa.r = v.r;
+  fa.u = v.u;
+  fa.partials = c->partials;
+  fa.stop = c->d_stop + l;
+  fa.nx = v.nx;
+  fa.ny = v.ny;
+  fa.nz = v.nz;
+  fa.force_mode = c->p.force_mode;
+  const int blocks = force_blocks((int64_t)v.N, c->max_parts);
+  for (int k = 0; k < n; ++k) {
+    cudaError_t e = queue_mask_fill(c, l, c->d_stop + l);
+    if (e == cudaSuccess) e = launch_force_dm(fa, blocks, c->s);
+    if (e == cudaSuccess) e = gauss_launch(g, v.pb, c->s);
+    if (e == cudaSuccess) e = launch_norm_finalize(c->partials, blocks, st, c->s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 // Queue `n` iterations of level l (box pass, Gaussian pass, norm) on c->s.
 cudaError_t queue_iterations(disc_ctx* c, int l, int n) {
   Level& v = c->lev[l];
@@ -153,6 +291,7 @@ cudaError_t queue_iterations(disc_ctx* c, int l, int n) {
   // from the fused warp of the Gaussian z pass
   cudaError_t e0 = launch_warp(v.Im, v.r, v.m, v.nx, v.ny, v.nz, c->d_stop + l, c->s);
   if (e0 != cudaSuccess) return e0;
+  if (c->p.mask_mode) return queue_masked(c, l, n, g, st);
   for (int k = 0; k < n; ++k) {
     cudaError_t e = box_launch(kModeIterate, a, v.pa, c->s);
     if (e != cudaSuccess) return e;
@@ -278,6 +417,14 @@ disc_status disc_params_default(disc_params* p) {
   p->force_mode = DISC_FORCE_THIRION;
   p->global_shift = 1;
   p->var_floor = 1e-6f;
+  p->mask_mode = 0;
+  p->hu0_factor = 2.0f;
+  p->a_lo = 0.5f;
+  p->a_hi = 1.5f;
+  p->fill_h = 50.0f;
+  p->fill_t[0] = p->fill_t[1] = 7;
+  p->fill_t[2] = 3;
+  p->fill_passes = 32;
   return DISC_OK;
 }
 
@@ -387,6 +534,23 @@ disc_status disc_set_images(disc_ctx* ctx, const float* ct, const float* cbct, i
       if (e == cudaSuccess) e = cudaMalloc(&v.u, 3 * v.N * sizeof(float));
       if (e == cudaSuccess) e = cudaMalloc(&v.t, 3 * v.N * sizeof(float));
       if (e == cudaSuccess) e = cudaMalloc(&v.hist, v.hist_cap * sizeof(float));
+      if (e == cudaSuccess && ctx->p.mask_mode) {
+        v.pm = box_plan(kModeMaskAB, v.nx, v.ny, v.nz, ctx->hx, ctx->hy, ctx->hz, ctx->num_sms);
+        if (v.pm.grid.x == 0) e = cudaErrorInvalidConfiguration;
+        if (e == cudaSuccess) e = cudaMalloc(&v.sd, v.N * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&v.ab, 2 * v.N * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&v.dm, v.N * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&v.stamp, v.N * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&v.list, 2 * v.N * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&v.cnt, (ctx->p.fill_passes + 1) * sizeof(int));
+      }
+      if (e != cudaSuccess) {
+        free_levels(ctx);
+        return e == cudaErrorInvalidConfiguration ? DISC_ERR_SHAPE : fail(ctx, e);
+      }
+    }
+    if (ctx->p.mask_mode) {
+      cudaError_t e = cudaMalloc(&ctx->d_mwork, median_work_words() * sizeof(unsigned));
       if (e != cudaSuccess) {
         free_levels(ctx);
         return fail(ctx, e);
@@ -416,6 +580,8 @@ disc_status disc_set_images(disc_ctx* ctx, const float* ct, const float* cbct, i
   CK(memcpy_kind(f.Is, cbct, f.N * sizeof(float), DISC_MEM_DEVICE, mem_kind, ctx->s));
   if (ctx->p.global_shift)
     CK(launch_global_shift(f.Im, f.Is, f.Is, (int64_t)f.N, ctx->d_scratch, nullptr, ctx->s));
+  else if (ctx->p.mask_mode)   // dHU for HU0 only: the shifted copy goes to scratch
+    CK(launch_global_shift(f.Im, f.Is, f.m, (int64_t)f.N, ctx->d_scratch, nullptr, ctx->s));
   for (int l = 1; l < L; ++l) {
     const Level& a = ctx->lev[l - 1];
     CK(launch_down2(a.Im, ctx->lev[l].Im, a.nx, a.ny, a.nz, ctx->s));
@@ -439,8 +605,35 @@ disc_status disc_set_images(disc_ctx* ctx, const float* ct, const float* cbct, i
     a.out = v.zs;
     a.qscale = ctx->qs_s;
     a.inv_qscale = 1.0f / ctx->qs_s;
+    a.sd_out = v.sd;                           // NULL unless the mask is on
     BoxPlan ps = box_plan(kModeStatic, v.nx, v.ny, v.nz, ctx->hx, ctx->hy, ctx->hz, ctx->num_sms);
     CK(box_launch(kModeStatic, a, ps, ctx->s));
+  }
+  if (ctx->p.mask_mode) {
+    // a_m: median of STD(M)/STD(S) at the finest level with r = 0 (m = I_m), and
+    // HU0 from the global shift dHU (reading R18)
+    BoxArgs a = box_args(ctx, f);
+    a.src = f.Im;
+    a.zs = f.zs;
+    a.sd = f.sd;
+    a.a_out = f.ab;
+    a.ratio_only = 1;
+    a.qscale = ctx->qs_m;
+    a.inv_qscale = 1.0f / ctx->qs_m;
+    CK(box_launch(kModeMaskAB, a, f.pm, ctx->s));
+    CK(launch_median(f.ab, (int64_t)f.N, ctx->d_mwork, ctx->s));
+    unsigned res[9] = {};
+    double dhu = 0.0;
+    CK(cudaMemcpyAsync(res, ctx->d_mwork + median_work_words() - 9, sizeof(res), cudaMemcpyDeviceToHost,
+                       ctx->s));
+    CK(cudaMemcpyAsync(&dhu, ctx->d_scratch + 2 * kShiftBlocks, sizeof(double), cudaMemcpyDeviceToHost,
+                       ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    float lo = 0.0f, hi = 0.0f;
+    std::memcpy(&lo, &res[4], sizeof(float));
+    std::memcpy(&hi, &res[8], sizeof(float));
+    ctx->mask_am = res[0] > 0 ? (float)(0.5 * ((double)lo + (double)hi)) : 0.0f;
+    ctx->mask_hu0 = ctx->p.hu0_factor * (float)std::fabs(dhu);
   }
   const Level& c = ctx->lev[L - 1];
   CK(cudaMemsetAsync(c.r, 0, 3 * c.N * sizeof(float), ctx->s));
@@ -546,6 +739,14 @@ disc_status disc_get_corrected(disc_ctx* ctx, float* out, int mem_kind) {
   CK(enter(ctx));
   Level& v = ctx->lev[ctx->cur_level];
   CK(launch_warp(v.Im, v.r, v.m, v.nx, v.ny, v.nz, nullptr, ctx->s));
+  if (ctx->p.mask_mode) {                  // I'_s = m + d of the masked correction
+    CK(queue_mask_fill(ctx, ctx->cur_level, nullptr));
+    CK(launch_add(v.m, v.dm, v.u, (int64_t)v.N, ctx->s));
+    CK(memcpy_kind(out, v.u, v.N * sizeof(float), mem_kind, DISC_MEM_DEVICE, ctx->s));
+    if (mem_kind == DISC_MEM_HOST) CK_DEV(ctx);
+    CK(leave(ctx));
+    return DISC_OK;
+  }
   BoxArgs a = box_args(ctx, v);
   a.src = v.m;
   a.zs = v.zs;
@@ -614,6 +815,161 @@ disc_status disc_get_norm_history(disc_ctx* ctx, int32_t level, float* out, int3
 // Kernel-level entry points
 // ============================================================================
 
+disc_status disc_get_mask_constants(disc_ctx* ctx, float* hu0, float* a_m) {
+  if (!ctx) return DISC_ERR_ARG;
+  if (!ctx->have_images || !ctx->p.mask_mode) return DISC_ERR_STATE;
+  if (hu0) *hu0 = ctx->mask_hu0;
+  if (a_m) *a_m = ctx->mask_am;
+  return DISC_OK;
+}
+
+disc_status disc_k_static_stats(const float* Is, float* zs, float* sd, int32_t nx, int32_t ny, int32_t nz,
+                                const int32_t patch[3], float qscale, float var_floor, void* stream) {
+  int h[3];
+  disc_status st = kcheck(nx, ny, nz, patch, qscale, var_floor, h);
+  if (st != DISC_OK) return st;
+  if (!Is || !zs || zs == Is || (sd && (sd == Is || sd == zs))) return DISC_ERR_ARG;
+  BoxArgs a = kargs(nx, ny, nz, h, qscale, var_floor);
+  a.src = Is;
+  a.out = zs;
+  a.sd_out = sd;
+  return klaunch(kModeStatic, a, (cudaStream_t)stream);
+}
+
+disc_status disc_k_ratio_median(const float* m, const float* zs, const float* sd, float* a_work,
+                                double* median_out, int32_t nx, int32_t ny, int32_t nz, const int32_t patch[3],
+                                float qscale, float var_floor, void* stream) {
+  int h[3];
+  disc_status st = kcheck(nx, ny, nz, patch, qscale, var_floor, h);
+  if (st != DISC_OK) return st;
+  if (!m || !zs || !sd || !a_work || !median_out) return DISC_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  BoxArgs a = kargs(nx, ny, nz, h, qscale, var_floor);
+  a.src = m;
+  a.zs = zs;
+  a.sd = sd;
+  a.a_out = a_work;
+  a.ratio_only = 1;
+  st = klaunch(kModeMaskAB, a, s);
+  if (st != DISC_OK) return st;
+  unsigned* work = nullptr;
+  if (cudaMallocAsync(&work, median_work_words() * sizeof(unsigned), s) != cudaSuccess) {
+    cudaGetLastError();
+    return DISC_ERR_OOM;
+  }
+  cudaError_t e = launch_median(a_work, (int64_t)nx * ny * nz, work, s);
+  if (e == cudaSuccess) e = launch_median_finish(work, median_out, s);
+  cudaError_t e2 = cudaFreeAsync(work, s);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    cudaGetLastError();
+    return DISC_ERR_CUDA;
+  }
+  return DISC_OK;
+}
+
+disc_status disc_k_correct_masked(const float* m, const float* Is, const float* zs, const float* sd, float* av,
+                                  float* bv, float* d, int32_t* stamp, int32_t* remaining_out, int32_t nx,
+                                  int32_t ny, int32_t nz, const int32_t patch[3], float qscale, float var_floor,
+                                  float hu0, float a_min, float a_max, float fill_h, const int32_t fill_t[3],
+                                  int32_t fill_passes, void* stream) {
+  int h[3];
+  disc_status st = kcheck(nx, ny, nz, patch, qscale, var_floor, h);
+  if (st != DISC_OK) return st;
+  if (!m || !Is || !zs || !sd || !av || !bv || !d || !stamp || !fill_t) return DISC_ERR_ARG;
+  if (!(fill_h > 0.0f) || fill_passes < 1 || fill_passes > 1024 || !(hu0 >= 0.0f)) return DISC_ERR_ARG;
+  for (int k = 0; k < 3; ++k)
+    if (fill_t[k] < 1 || fill_t[k] > 15 || fill_t[k] % 2 == 0) return DISC_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t N = (size_t)nx * ny * nz;
+  int* work = nullptr;   // two lists [2][N] and the counters [fill_passes + 1]
+  if (cudaMallocAsync(&work, sizeof(int) * (2 * N + fill_passes + 1), s) != cudaSuccess) {
+    cudaGetLastError();
+    return DISC_ERR_OOM;
+  }
+  int* cnt = work + 2 * N;
+  cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int) * (fill_passes + 1), s);
+  BoxArgs a = kargs(nx, ny, nz, h, qscale, var_floor);
+  a.src = m;
+  a.zs = zs;
+  a.is = Is;
+  a.sd = sd;
+  a.out = d;
+  a.a_out = av;
+  a.b_out = bv;
+  a.stamp = stamp;
+  a.list = work;
+  a.count = cnt;
+  a.hu0 = hu0;
+  a.a_min = a_min;
+  a.a_max = a_max;
+  if (e == cudaSuccess) st = klaunch(kModeMaskAB, a, s);
+  FillArgs f{};
+  f.is = Is;
+  f.m = m;
+  f.a = av;
+  f.b = bv;
+  f.d = d;
+  f.stamp = stamp;
+  f.cnt = cnt;
+  f.nx = nx;
+  f.ny = ny;
+  f.nz = nz;
+  f.tx = (fill_t[0] - 1) / 2;
+  f.ty = (fill_t[1] - 1) / 2;
+  f.tz = (fill_t[2] - 1) / 2;
+  f.inv_h = 1.0f / fill_h;
+  for (int p = 1; p <= fill_passes && e == cudaSuccess && st == DISC_OK; ++p) {
+    f.pass = p;
+    f.list_in = work + ((p - 1) % 2) * N;
+    f.list_out = work + (p % 2) * N;
+    e = launch_fill_pass(f, (int)N, s);
+  }
+  if (e == cudaSuccess && st == DISC_OK && remaining_out) e = launch_fill_remaining(cnt, fill_passes, remaining_out, s);
+  cudaError_t e2 = cudaFreeAsync(work, s);
+  if (st != DISC_OK) return st;
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    cudaGetLastError();
+    return DISC_ERR_CUDA;
+  }
+  return DISC_OK;
+}
+
+disc_status disc_k_force(const float* m, const float* d, const float* r, float* u, double* norms_out, int32_t nx,
+                         int32_t ny, int32_t nz, int32_t force_mode, void* stream) {
+  if (!m || !d || !r || !u || u == r) return DISC_ERR_ARG;
+  if (force_mode != DISC_FORCE_THIRION && force_mode != DISC_FORCE_DOUBLE) return DISC_ERR_ARG;
+  if (nx < 1 || ny < 1 || nz < 1 || (double)nx * ny * nz * 3.0 >= 2147483647.0) return DISC_ERR_SHAPE;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t N = (int64_t)nx * ny * nz;
+  const int blocks = force_blocks(N, 148 * 8);
+  float* parts = nullptr;
+  if (cudaMallocAsync(&parts, sizeof(float) * 2 * blocks, s) != cudaSuccess) {
+    cudaGetLastError();
+    return DISC_ERR_OOM;
+  }
+  ForceArgs f{};
+  f.d = d;
+  f.m = m;
+  f.r = r;
+  f.u = u;
+  f.partials = parts;
+  f.nx = nx;
+  f.ny = ny;
+  f.nz = nz;
+  f.force_mode = force_mode;
+  cudaError_t e = launch_force_dm(f, blocks, s);
+  if (e == cudaSuccess && norms_out) {
+    e = launch_partials_sum(parts, blocks, 0, norms_out, s);
+    if (e == cudaSuccess) e = launch_partials_sum(parts, blocks, 1, norms_out + 1, s);
+  }
+  cudaError_t e2 = cudaFreeAsync(parts, s);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    cudaGetLastError();
+    return DISC_ERR_CUDA;
+  }
+  return DISC_OK;
+}
+
 disc_status disc_k_check_error(void* stream) {
   int flag = 0;
   if (box_tma_error((cudaStream_t)stream, &flag) != cudaSuccess) {
@@ -680,14 +1036,6 @@ disc_status disc_k_upsample_field2(const float* rc, float* rf, int32_t nx, int32
   return DISC_OK;
 }
 
-static disc_status check_patch(const int32_t patch[3], int* h) {
-  if (!patch) return DISC_ERR_ARG;
-  for (int a = 0; a < 3; ++a) {
-    if (patch[a] < 1 || patch[a] > 2 * DISC_MAX_HALF_PATCH + 1 || patch[a] % 2 == 0) return DISC_ERR_ARG;
-    h[a] = (patch[a] - 1) / 2;
-  }
-  return DISC_OK;
-}
 
 disc_status disc_k_static_norm(const float* Is, float* zs, int32_t nx, int32_t ny, int32_t nz,
                                const int32_t patch[3], float qscale, float var_floor, void* stream) {

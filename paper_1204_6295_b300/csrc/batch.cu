@@ -302,6 +302,7 @@ disc_status disc_batch_create(const disc_params* p, int device, void* cuda_strea
       p->patch[0] % 2 == 0)
     return DISC_ERR_ARG;
   if (p->levels < 1 || p->levels > DISC_MAX_LEVELS || !(p->gauss_sigma > 0.0f)) return DISC_ERR_ARG;
+  if (p->mask_mode != 0) return DISC_ERR_ARG;   // the batched tables carry the unmasked pass only
   const int R = gauss_radius(p->gauss_sigma, p->gauss_radius);
   if (R < 1 || R > 8) return DISC_ERR_ARG;
   disc_batch* b = new (std::nothrow) disc_batch();

@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include "internal.cuh"
+
 namespace disc {
 
 // 64-bit integers to float through their two 32-bit halves (two exact 32-bit
@@ -52,6 +54,37 @@ static __device__ __forceinline__ void patch_moments(long long S1, long long S2,
   const float varq = fmaf(u64_to_float(T), inv_n, -ef * ef);
   const float var = varq * (inv_qs * inv_qs);
   sigma = var > var_floor ? sqrt_approx(var) : 0.0f;
+}
+
+// kModeMaskAB epilogue at voxel g (Eqs. 5-7; readings R17, R18), shared by the
+// box kernels.  vc = m at the voxel, dc = E(M) - m, sg = STD(M), zsv = zs.
+//   a = STD(M) / STD(S), b = E(M) - a E(S) with E(S) = I_s - zs STD(S);
+//   xi = 1 where STD(S) = 0, |m - I_s| > HU0, or a outside [a_min, a_max].
+// Unmasked voxels keep d = zs STD(M) + dc (the path's deviation form); masked
+// ones start from the paper's a = b = 0 (d = -m), stamp -1, and join the list
+// of voxels for the fill passes.
+static __device__ __forceinline__ void mask_epilogue(const BoxArgs& a, size_t g, float vc, float dc, float sg,
+                                                     float zsv) {
+  const float sd = __ldg(a.sd + g);
+  if (a.ratio_only) {
+    a.a_out[g] = sd > 0.0f ? sg / sd : -1.0f;
+    return;
+  }
+  const float is = __ldg(a.is + g);
+  const float av = sd > 0.0f ? sg / sd : 0.0f;
+  const bool xi = !(sd > 0.0f) || fabsf(vc - is) > a.hu0 || av < a.a_min || av > a.a_max;
+  if (!xi) {
+    a.a_out[g] = av;
+    a.b_out[g] = (vc + dc) - av * fmaf(-zsv, sd, is);
+    a.out[g] = fmaf(zsv, sg, dc);
+    a.stamp[g] = 0;
+  } else {
+    a.a_out[g] = 0.0f;
+    a.b_out[g] = 0.0f;
+    a.out[g] = -vc;
+    a.stamp[g] = -1;
+    a.list[atomicAdd(a.count, 1)] = (int)g;
+  }
 }
 
 }  // namespace disc

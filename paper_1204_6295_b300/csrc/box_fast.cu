@@ -259,6 +259,7 @@ __device__ __forceinline__ void box_body(const BoxArgs& a, int bx, int by, int b
         const size_t gz = (size_t)zc * plane + (size_t)gy * nx + gx;
         if (MODE == kModeStatic) {
           a.out[gz] = sg_ > 0.0f ? -dc / sg_ : 0.0f;   // (I_s - E(S)) / STD(S)
+          if (a.sd_out) a.sd_out[gz] = sg_;
           continue;
         }
         const float zsv = zsf[fi];
@@ -266,6 +267,8 @@ __device__ __forceinline__ void box_body(const BoxArgs& a, int bx, int by, int b
         if (MODE == kModeIterate) {
           dring[(zc % 3) * B::FN + fi] = d;
           if (a.f_tap && out_plane && fx >= 1 && fx <= B::TX && fy >= 1 && fy <= B::TY) a.f_tap[gz] = d;
+        } else if (MODE == kModeMaskAB) {
+          mask_epilogue(a, gz, vc, dc, sg_, zsv);
         } else if (MODE == kModeCorrected) {
           a.out[gz] = vc + d;
         } else if (MODE == kModeSsdLoss) {
@@ -491,6 +494,7 @@ size_t box_fast_smem(int mode, int h) {
     case kModeCorrected: return fast_bytes<kModeCorrected>(h);
     case kModeSsdLoss: return fast_bytes<kModeSsdLoss>(h);
     case kModeSsdAdjoint: return fast_bytes<kModeSsdAdjoint>(h);
+    case kModeMaskAB: return fast_bytes<kModeMaskAB>(h);
     default: return 0;
   }
 }
@@ -533,6 +537,7 @@ int box_fast_occupancy(int mode, int h, size_t smem) {
     case kModeCorrected: return fast_occ<kModeCorrected>(h, smem);
     case kModeSsdLoss: return fast_occ<kModeSsdLoss>(h, smem);
     case kModeSsdAdjoint: return fast_occ<kModeSsdAdjoint>(h, smem);
+    case kModeMaskAB: return fast_occ<kModeMaskAB>(h, smem);
     default: return 1;
   }
 }
@@ -544,6 +549,7 @@ cudaError_t box_fast_launch(int mode, const BoxArgs& a, const BoxPlan& p, cudaSt
     case kModeCorrected: return launch_fast_h<kModeCorrected>(a, p, s);
     case kModeSsdLoss: return launch_fast_h<kModeSsdLoss>(a, p, s);
     case kModeSsdAdjoint: return launch_fast_h<kModeSsdAdjoint>(a, p, s);
+    case kModeMaskAB: return launch_fast_h<kModeMaskAB>(a, p, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -31,6 +31,7 @@
 
 #include <cuda_runtime.h>
 
+#include "box_dev.cuh"
 #include "internal.cuh"
 
 namespace disc {
@@ -227,6 +228,7 @@ __global__ void __launch_bounds__(kThreads) k_box_pass(BoxArgs a) {
         patch_moments(b1, b2, n, qc, a.inv_qscale, a.var_floor, dc, sg_);
         if (MODE == kModeStatic) {
           a.out[g] = sg_ > 0.0f ? -dc / sg_ : 0.0f;   // (I_s - E(S)) / STD(S)
+          if (a.sd_out) a.sd_out[g] = sg_;
           continue;
         }
         const float zsv = __ldg(a.zs + g);
@@ -235,6 +237,8 @@ __global__ void __launch_bounds__(kThreads) k_box_pass(BoxArgs a) {
           dring[(zc % 3) * FN + fy * FX + fx] = d;
           const bool inner = fx >= 1 && fx <= TX && fy >= 1 && fy <= TY;
           if (inner && out_plane && a.f_tap) a.f_tap[g] = d;
+        } else if (MODE == kModeMaskAB) {
+          mask_epilogue(a, g, vc, dc, sg_, zsv);
         } else if (MODE == kModeCorrected) {
           a.out[g] = vc + d;
         } else if (MODE == kModeSsdLoss) {
@@ -418,6 +422,7 @@ cudaError_t box_launch(int mode, const BoxArgs& a, const BoxPlan& p, cudaStream_
     case kModeCorrected: return launch_mode<kModeCorrected>(b, p, s);
     case kModeSsdLoss: return launch_mode<kModeSsdLoss>(b, p, s);
     case kModeSsdAdjoint: return launch_mode<kModeSsdAdjoint>(b, p, s);
+    case kModeMaskAB: return launch_mode<kModeMaskAB>(b, p, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -388,6 +388,7 @@ __device__ __forceinline__ bool box_tma_body(const BoxArgs& a, int bx, int by, i
         const size_t gz = (size_t)zc * plane + (size_t)gy * nx + gx;
         if (MODE == kModeStatic) {
           a.out[gz] = sg_ > 0.0f ? -dc / sg_ : 0.0f;   // (I_s - E(S)) / STD(S)
+          if (a.sd_out) a.sd_out[gz] = sg_;
           continue;
         }
         const float zsv = zsf[fi];
@@ -395,6 +396,8 @@ __device__ __forceinline__ bool box_tma_body(const BoxArgs& a, int bx, int by, i
         if (MODE == kModeIterate) {
           dcur[fi] = d;
           if (a.f_tap && out_plane && fx >= 1 && fx <= B::TX && fy >= 1 && fy <= B::TY) a.f_tap[gz] = d;
+        } else if (MODE == kModeMaskAB) {
+          mask_epilogue(a, gz, vc, dc, sg_, zsv);
         } else if (MODE == kModeCorrected) {
           a.out[gz] = vc + d;
         } else if (MODE == kModeSsdLoss) {
@@ -676,6 +679,7 @@ R dispatch(int mode, int h, R fallback, Args... args) {
     case kModeCorrected: DISC_TMA_H(kModeCorrected)
     case kModeSsdLoss: DISC_TMA_H(kModeSsdLoss)
     case kModeSsdAdjoint: DISC_TMA_H(kModeSsdAdjoint)
+    case kModeMaskAB: DISC_TMA_H(kModeMaskAB)
     default: return fallback;
   }
 #undef DISC_TMA_H

@@ -32,7 +32,15 @@ struct Level {
   float* t = nullptr;    // xy-filtered field [3][N] (Gaussian scratch)
   float* hist = nullptr; // l^(k) history
   int hist_cap = 0;
+  // mask and fill (mask_mode 1)
+  float* sd = nullptr;   // STD(S)
+  float* ab = nullptr;   // a [N] then b [N]
+  float* dm = nullptr;   // I'_s - m of the masked correction
+  int* stamp = nullptr;  // 0 known, p filled by pass p, -1 not filled
+  int* list = nullptr;   // two lists of unfilled voxels [2][N]
+  int* cnt = nullptr;    // [fill_passes + 1] list lengths
   BoxPlan pa{};
+  BoxPlan pm{};          // kModeMaskAB
   GaussPlan pb{};
   cudaGraphExec_t graph = nullptr;
   int graph_iters = 0;
@@ -62,6 +70,8 @@ struct disc_ctx {
   int* d_err = nullptr;      // device error word of the box kernels (d_stop + DISC_MAX_LEVELS)
   double* d_scratch = nullptr;
   float* d_maxabs = nullptr; // [2]
+  float mask_hu0 = 0.0f, mask_am = 0.0f;   // Eq. 7 thresholds (mask_mode 1)
+  unsigned* d_mwork = nullptr;              // median work words
   int cur_level = 0;
   int cur_iter = 0;
   disc_status sticky = DISC_OK;

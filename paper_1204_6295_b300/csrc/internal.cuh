@@ -36,7 +36,8 @@ enum BoxMode : int {
   kModeIterate = 1,    // moments of m, correction, force, u = r + dr, norms
   kModeCorrected = 2,  // moments of m, I'_s written out
   kModeSsdLoss = 3,    // moments of m, per-CTA partial sum of (m - I'_s)^2
-  kModeSsdAdjoint = 4  // moments of m, per-voxel adjoint coefficients (A, B, C, D)
+  kModeSsdAdjoint = 4, // moments of m, per-voxel adjoint coefficients (A, B, C, D)
+  kModeMaskAB = 5      // moments of m: a, b of Eqs. 5-6, the mask xi of Eq. 7, d = I'_s - m
 };
 
 struct BoxArgs {
@@ -54,6 +55,19 @@ struct BoxArgs {
   int force_mode;
   int zlen;             // output planes per CTA (z chunk)
   int* err;             // device error word (bit 0: a bulk-copy wait timed out); NULL: the library's own
+  float* sd_out;        // optional (kModeStatic): STD(S) per voxel
+  // kModeMaskAB (Eqs. 5-7): is = I_s, sd = STD(S); out = d = I'_s - m.  Outputs a, b,
+  // stamp (0 where xi = 0, -1 where xi = 1) and the list of xi = 1 voxels (count[0]).
+  // ratio_only: write only a = STD(M)/STD(S) (-1 where undefined) into a_out.
+  const float* is;
+  const float* sd;
+  float* a_out;
+  float* b_out;
+  int* stamp;
+  int* list;
+  int* count;
+  float hu0, a_min, a_max;
+  int ratio_only;
 };
 
 struct BoxPlan {
@@ -157,6 +171,50 @@ cudaError_t gauss_launch(const GaussArgs& a, const GaussPlan& plan, cudaStream_t
 // adjoint of the SSD loss (D, and the patch sums S of the coefficients A, B, C).
 cudaError_t launch_ssd_final(const float* Im, const float* r, const float* m, const float* D,
                              const float* S, float* grad, int nx, int ny, int nz, cudaStream_t s);
+
+// ----------------------------------------------------------------------------
+// Mask and fill of a, b (Eqs. 7-10), mask.cu
+// ----------------------------------------------------------------------------
+struct FillArgs {
+  const float* is;      // I_s
+  const float* m;       // I_m^(k)
+  float* a;             // a, b: known values in, filled values out
+  float* b;
+  float* d;             // I'_s - m, written where a voxel is filled
+  int* stamp;           // 0: xi = 0; p: filled by pass p; -1: not yet
+  const int* list_in;   // voxels still without a, b (cnt[pass - 1] of them)
+  int* list_out;        // those this pass leaves (cnt[pass] counts them)
+  int* cnt;             // [passes + 1], cnt[0] from the mask pass, the rest zero
+  int nx, ny, nz;
+  int tx, ty, tz;       // half sizes of T
+  float inv_h;          // 1 / h of Eq. 10
+  int pass;             // 1, 2, ...
+  const int* stop;
+};
+cudaError_t launch_fill_pass(const FillArgs& f, int max_items, cudaStream_t s);
+struct ForceArgs {
+  const float* d;       // I'_s - m
+  const float* m;
+  const float* r;
+  float* u;             // r + dr
+  float* partials;      // per CTA: sum |dr|, sum |r|
+  const int* stop;
+  int nx, ny, nz;
+  int force_mode;
+};
+int force_blocks(int64_t n, int max_parts);
+cudaError_t launch_force_dm(const ForceArgs& f, int blocks, cudaStream_t s);
+// Lower and upper median of the non-negative entries of a (radix select).
+// work: median_work_words() unsigned words; results: work[65536] = count,
+// work[65537 + 3] = lower median bits, work[65537 + 7] = upper median bits.
+size_t median_work_words();
+cudaError_t launch_median(const float* a, int64_t n, unsigned* work, cudaStream_t s);
+// *out = mean of the two medians in work (double), -1 when there are none.
+cudaError_t launch_median_finish(const unsigned* work, double* out, cudaStream_t s);
+// *out = voxels the fill left unfilled, from its counters.
+cudaError_t launch_fill_remaining(const int* cnt, int passes, int* out, cudaStream_t s);
+// out = a + b elementwise.
+cudaError_t launch_add(const float* a, const float* b, float* out, int64_t n, cudaStream_t s);
 
 // ----------------------------------------------------------------------------
 // Small kernels, misc.cu

@@ -49,6 +49,13 @@ class Params(ctypes.Structure):
         ("force_mode", ctypes.c_int32),
         ("global_shift", ctypes.c_int32),
         ("var_floor", ctypes.c_float),
+        ("mask_mode", ctypes.c_int32),
+        ("hu0_factor", ctypes.c_float),
+        ("a_lo", ctypes.c_float),
+        ("a_hi", ctypes.c_float),
+        ("fill_h", ctypes.c_float),
+        ("fill_t", ctypes.c_int32 * 3),
+        ("fill_passes", ctypes.c_int32),
     ]
 
 
@@ -90,6 +97,14 @@ _SIGS = {
                                    ctypes.POINTER(_i32), _f32, _f32, _i32, _vp]),
     "disc_k_gauss": (_st, [_vp, _vp, _i32, _i32, _i32, _f32, _i32, _vp]),
     "disc_k_check_error": (_st, [_vp]),
+    "disc_get_mask_constants": (_st, [_vp, ctypes.POINTER(_f32), ctypes.POINTER(_f32)]),
+    "disc_k_static_stats": (_st, [_vp, _vp, _vp, _i32, _i32, _i32, ctypes.POINTER(_i32), _f32, _f32, _vp]),
+    "disc_k_ratio_median": (_st, [_vp, _vp, _vp, _vp, _vp, _i32, _i32, _i32, ctypes.POINTER(_i32), _f32, _f32,
+                                  _vp]),
+    "disc_k_correct_masked": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _i32, _i32,
+                                    ctypes.POINTER(_i32), _f32, _f32, _f32, _f32, _f32, _f32,
+                                    ctypes.POINTER(_i32), _i32, _vp]),
+    "disc_k_force": (_st, [_vp, _vp, _vp, _vp, _vp, _i32, _i32, _i32, _i32, _vp]),
     "disc_k_force_update": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _i32, _i32, _i32,
                                   ctypes.POINTER(_i32), _f32, _f32, _i32, _vp]),
     "disc_k_ssd_loss": (_st, [_vp, _vp, _vp, _vp, _i32, _i32, _i32, ctypes.POINTER(_i32), _f32, _f32, _vp]),
@@ -155,7 +170,9 @@ def _f32_check(t, shape, name):
 
 
 def make_params(patch=(3, 3, 3), sigma=1.0, radius=0, levels=2, iters=(50, 50), stop_eps=0.0,
-                stop_window=10, force_mode=FORCE_THIRION, global_shift=True, var_floor=1e-6):
+                stop_window=10, force_mode=FORCE_THIRION, global_shift=True, var_floor=1e-6,
+                mask_mode=0, hu0_factor=2.0, a_lo=0.5, a_hi=1.5, fill_h=50.0, fill_t=(7, 7, 3),
+                fill_passes=32):
     p = Params()
     _check(_lib.disc_params_default(ctypes.byref(p)), "disc_params_default")
     for a in range(3):
@@ -173,6 +190,14 @@ def make_params(patch=(3, 3, 3), sigma=1.0, radius=0, levels=2, iters=(50, 50), 
     p.force_mode = int(force_mode)
     p.global_shift = 1 if global_shift else 0
     p.var_floor = float(var_floor)
+    p.mask_mode = int(mask_mode)
+    p.hu0_factor = float(hu0_factor)
+    p.a_lo = float(a_lo)
+    p.a_hi = float(a_hi)
+    p.fill_h = float(fill_h)
+    for a in range(3):
+        p.fill_t[a] = int(fill_t[a])
+    p.fill_passes = int(fill_passes)
     return p
 
 
@@ -263,6 +288,13 @@ class Registration:
         _check(_lib.disc_get_norm_history(self._h, int(level), out.ctypes.data, cap, ctypes.byref(n)),
                "disc_get_norm_history")
         return out[:n.value].copy()
+
+    def mask_constants(self):
+        """(HU0, a_m) fixed at set_images when the mask is on (Eq. 7, Sec. 2.3)."""
+        hu0, am = _f32(0.0), _f32(0.0)
+        _check(_lib.disc_get_mask_constants(self._h, ctypes.byref(hu0), ctypes.byref(am)),
+               "disc_get_mask_constants")
+        return hu0.value, am.value
 
 
 class Batch:
@@ -393,6 +425,41 @@ def k_gauss(u, r, sigma, radius=0, stream=None):
     _, nz, ny, nx = u.shape
     _check(_lib.disc_k_gauss(_ptr(u), _ptr(r), nx, ny, nz, float(sigma), int(radius), _stream(stream)),
            "disc_k_gauss")
+
+
+def k_static_stats(Is, zs, sd, patch, qs, var_floor=1e-6, stream=None):
+    """CBCT normalisation zs and STD(S) per voxel (sd may be None)."""
+    nz, ny, nx = Is.shape
+    p = (_i32 * 3)(*patch)
+    _check(_lib.disc_k_static_stats(_ptr(Is), _ptr(zs), _ptr(sd), nx, ny, nz, p, float(qs), float(var_floor),
+                                    _stream(stream)), "disc_k_static_stats")
+
+
+def k_ratio_median(m, zs, sd, a_work, median_out, patch, qs, var_floor=1e-6, stream=None):
+    """a = STD(M)/STD(S) into a_work (-1 where undefined) and its median (device double)."""
+    nz, ny, nx = m.shape
+    p = (_i32 * 3)(*patch)
+    _check(_lib.disc_k_ratio_median(_ptr(m), _ptr(zs), _ptr(sd), _ptr(a_work), _ptr(median_out), nx, ny, nz, p,
+                                    float(qs), float(var_floor), _stream(stream)), "disc_k_ratio_median")
+
+
+def k_correct_masked(m, Is, zs, sd, a, b, d, stamp, patch, qs, hu0, a_min, a_max, fill_h=50.0,
+                     fill_t=(7, 7, 3), fill_passes=32, remaining_out=None, var_floor=1e-6, stream=None):
+    """Mask (Eq. 7) and fill (Eqs. 8-10) of one correction; d = I'_s - m, stamp int32."""
+    nz, ny, nx = m.shape
+    p = (_i32 * 3)(*patch)
+    t = (_i32 * 3)(*fill_t)
+    _check(_lib.disc_k_correct_masked(_ptr(m), _ptr(Is), _ptr(zs), _ptr(sd), _ptr(a), _ptr(b), _ptr(d),
+                                      _ptr(stamp), _ptr(remaining_out), nx, ny, nz, p, float(qs),
+                                      float(var_floor), float(hu0), float(a_min), float(a_max), float(fill_h),
+                                      t, int(fill_passes), _stream(stream)), "disc_k_correct_masked")
+
+
+def k_force(m, d, r, u, norms_out=None, force_mode=FORCE_THIRION, stream=None):
+    """Demons force and update from d = I'_s - m and m."""
+    nz, ny, nx = m.shape
+    _check(_lib.disc_k_force(_ptr(m), _ptr(d), _ptr(r), _ptr(u), _ptr(norms_out), nx, ny, nz, int(force_mode),
+                             _stream(stream)), "disc_k_force")
 
 
 def k_check_error(stream=None):
