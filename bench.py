@@ -292,6 +292,41 @@ def time_differentiable(disc, torch, w, pair_dev, field_dev, kt, reps=5):
                     "workload), patch statistics recomputed in the backward pass"}
 
 
+def time_masked(disc, torch, w, pair_dev, dist, steps=1):
+    """The same schedule with the mask and fill of Eqs. 7-10 on (mask_mode 1)."""
+    ct, cbct = pair_dev
+    nx, ny, nz = w["dims"]
+    reg = disc.Registration(patch=w["patch"], sigma=w["sigma"], levels=w["levels"], iters=w["iters"],
+                            mask_mode=1)
+    reg.set_images(ct, cbct)
+    hu0, a_m = reg.mask_constants()
+    cx, cy, cz = level_dims(w["dims"], w["levels"])[-1]
+    zeros = torch.zeros((3, cz, cy, cx), dtype=torch.float32, device="cuda")
+    s = torch.cuda.current_stream()
+
+    def step():
+        reg.set_field(w["levels"] - 1, zeros)
+        reg.iterate(-1, sync=False)
+
+    step()                                        # warm-up (captures the graphs)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(steps):
+        step()
+    e1.record(s)
+    torch.cuda.synchronize()
+    t = reduce_max(dist, e0.elapsed_time(e1) / steps / 1e3)
+    reg.close()
+    world = dist.get_world_size() if dist else 1
+    return {"value": job_throughput(schedule_units(w), world, t), "unit": UNIT, "ms_per_step": t * 1e3,
+            "hu0": hu0, "a_m": a_m,
+            "what": "the plain workload with the xi mask of Eq. 7 and the Jacobi fill of Eqs. 8-10 "
+                    "every iteration (HU0 = 2|dHU|, a in [0.5, 1.5] a_m, T 7x7x3, h 50 HU, <= 32 passes)"}
+
+
 BATCH_PAIRS_PER_RANK = 16
 BATCH_WORKLOAD = dict(patch=(9, 9, 9), sigma=1.5, levels=3, iters=(100, 100, 100))
 
@@ -441,6 +476,7 @@ def run_ours(args, w, rank, world, local_rank):
     traffic = recorded_traffic(args.workload)
 
     batched = None if args.no_batched else time_batched(disc, torch, dist)
+    masked = time_masked(disc, torch, w, (ct, cbct), dist)
 
     # end to end through the public API with host buffers (pinned)
     ct_h = torch.from_numpy(pair.ct).pin_memory()
@@ -497,6 +533,7 @@ def run_ours(args, w, rank, world, local_rank):
         "forms": {"plain": {"value": value, "unit": UNIT},
                   "batched": batched,
                   "differentiable": diff_form,
+                  "masked": masked,
                   "effective_hbm_frac_32B_model": value * 1e9 * 32 / (peak * 1e9)},
         "e2e": e2e,
         "gpu_launches": launches * args.steps,

@@ -378,8 +378,10 @@ def should_stop(history, eps, window=10):
 # Readings (R17-R20):
 #  R17 xi = 1 also where Var(S) <= var_floor, where a is undefined.
 #  R18 HU0 = hu0_factor |dHU| with dHU the global shift of Sec. 2.3 (factor 2);
-#      a_m is the median of a over the voxels with Var(S) > var_floor, at the
-#      finest level with r = 0, before the first iteration; a_min = a_lo a_m,
+#      a_m is the median of a over the voxels where both patch variances exceed
+#      var_floor (a patch where the CT is constant gives a = 0 whatever the
+#      CBCT, which says nothing about their intensity scale), at the finest
+#      level with r = 0, before the first iteration; a_min = a_lo a_m,
 #      a_max = a_hi a_m (0.5 and 1.5).
 #  R19 Fill passes are Jacobi sweeps: a pass averages over the neighbours in T
 #      that were known before it (xi = 0, or filled by an earlier pass); a
@@ -397,14 +399,13 @@ FILL_EXP_CAP = 80.0
 def ratio_median(I_m, I_s, half, var_floor=1e-6):
     """a_m of Sec. 2.3: median of a = STD(M)/STD(S) with r = 0 (m = I_m).
 
-    Over the voxels with Var(S) > var_floor (reading R18)."""
+    Over the voxels where Var(M) and Var(S) both exceed var_floor (reading R18)."""
     EM, EM2 = patch_moments(I_m, half)
     ES, ES2 = patch_moments(I_s, half)
     var_m = np.maximum(EM2 - EM * EM, 0.0)
     var_s = np.maximum(ES2 - ES * ES, 0.0)
-    ok = var_s > var_floor
-    std_m = np.where(var_m > var_floor, np.sqrt(var_m), 0.0)
-    a = std_m[ok] / np.sqrt(var_s[ok])
+    ok = (var_s > var_floor) & (var_m > var_floor)
+    a = np.sqrt(var_m[ok]) / np.sqrt(var_s[ok])
     return float(np.median(a)) if a.size else 0.0
 
 

