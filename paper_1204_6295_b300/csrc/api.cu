@@ -125,6 +125,7 @@ void free_levels(disc_ctx* c) {
   for (int l = 0; l < DISC_MAX_LEVELS; ++l) {
     Level& v = c->lev[l];
     if (v.graph) cudaGraphExecDestroy(v.graph);
+    if (v.loop) cudaGraphExecDestroy(v.loop);
     cudaFree(v.Im);
     cudaFree(v.Is);
     cudaFree(v.zs);
@@ -261,8 +262,16 @@ cudaError_t queue_masked(disc_ctx* c, int l, int n, const GaussArgs& g, const No
   return cudaSuccess;
 }
 
+// In-graph loop control: the norm kernel decrements *budget and sets `cond`.
+struct LoopCond {
+  int* budget;
+  cudaGraphConditionalHandle cond;
+};
+
 // Queue `n` iterations of level l (box pass, Gaussian pass, norm) on c->s.
-cudaError_t queue_iterations(disc_ctx* c, int l, int n) {
+// With `loop`, the norm kernel also drives the loop graph's condition and the
+// level-start warp is left to the caller.
+cudaError_t queue_iterations(disc_ctx* c, int l, int n, const LoopCond* loop) {
   Level& v = c->lev[l];
   BoxArgs a = box_args(c, v);
   a.src = v.m;
@@ -286,11 +295,18 @@ cudaError_t queue_iterations(disc_ctx* c, int l, int n) {
   g.R = c->R;
   std::memcpy(g.w, c->w, sizeof(c->w));
   NormState st{v.hist, c->d_iter + l, c->d_stop + l, v.hist_cap, c->p.stop_window, c->p.stop_eps};
+  if (loop) {
+    st.budget = loop->budget;
+    st.cond = loop->cond;
+    st.use_cond = 1;
+  }
   const int nparts = (int)(v.pa.grid.x * v.pa.grid.y * v.pa.grid.z);
   // m for the field the first iteration starts from; later iterations get it
   // from the fused warp of the Gaussian z pass
-  cudaError_t e0 = launch_warp(v.Im, v.r, v.m, v.nx, v.ny, v.nz, c->d_stop + l, c->s);
-  if (e0 != cudaSuccess) return e0;
+  if (!loop) {
+    cudaError_t e0 = launch_warp(v.Im, v.r, v.m, v.nx, v.ny, v.nz, c->d_stop + l, c->s);
+    if (e0 != cudaSuccess) return e0;
+  }
   if (c->p.mask_mode) return queue_masked(c, l, n, g, st);
   for (int k = 0; k < n; ++k) {
     cudaError_t e = box_launch(kModeIterate, a, v.pa, c->s);
@@ -303,10 +319,55 @@ cudaError_t queue_iterations(disc_ctx* c, int l, int n) {
   return cudaSuccess;
 }
 
+// The loop graph of level l: a conditional WHILE node whose body is one
+// iteration; the body's norm kernel leaves the loop when the launch's budget
+// of iterations is spent or the stop rule fires (Sec. 2.3), so a stopped level
+// runs no further kernels.
+cudaError_t build_loop_graph(disc_ctx* c, int l) {
+  Level& v = c->lev[l];
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e != cudaSuccess) return e;
+  cudaGraphConditionalHandle h = 0;
+  e = cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp);
+  if (e == cudaSuccess) {
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(c->s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      const LoopCond lc{c->d_budget + l, h};
+      const cudaError_t e1 = queue_iterations(c, l, 1, &lc);
+      cudaGraph_t captured = nullptr;
+      const cudaError_t e2 = cudaStreamEndCapture(c->s, &captured);
+      e = e1 != cudaSuccess ? e1 : e2;
+    }
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&v.loop, g, 0);
+  if (e != cudaSuccess) v.loop = nullptr;
+  cudaGraphDestroy(g);
+  return e;
+}
+
 cudaError_t run_iterations(disc_ctx* c, int l, int n) {
   if (n <= 0) return cudaSuccess;
   Level& v = c->lev[l];
-  if (!c->use_graphs) return queue_iterations(c, l, n);
+  if (!c->use_graphs) return queue_iterations(c, l, n, nullptr);
+  if (c->use_loop) {
+    if (v.loop == nullptr) {
+      const cudaError_t e = build_loop_graph(c, l);
+      if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = launch_warp(v.Im, v.r, v.m, v.nx, v.ny, v.nz, c->d_stop + l, c->s);
+    if (e == cudaSuccess) e = launch_set_int(c->d_budget + l, n, c->s);
+    if (e == cudaSuccess) e = cudaGraphLaunch(v.loop, c->s);
+    return e;
+  }
   if (v.graph == nullptr || v.graph_iters != n) {
     if (v.graph) {
       cudaGraphExecDestroy(v.graph);
@@ -315,7 +376,7 @@ cudaError_t run_iterations(disc_ctx* c, int l, int n) {
     cudaGraph_t gph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
-    e = queue_iterations(c, l, n);
+    e = queue_iterations(c, l, n, nullptr);
     cudaError_t e2 = cudaStreamEndCapture(c->s, &gph);
     if (e != cudaSuccess) {
       if (gph) cudaGraphDestroy(gph);
@@ -451,6 +512,10 @@ disc_status disc_create(const disc_params* p, int device, void* cuda_stream, dis
   gauss_taps(p->gauss_sigma, ctx->R, ctx->w);
   const char* ng = std::getenv("DISC_NO_GRAPH");
   ctx->use_graphs = !(ng && ng[0] == '1');
+  // the loop graph pays a few microseconds per iteration for its condition; it
+  // is used where it saves work, when the stop rule can end a level early
+  const char* ul = std::getenv("DISC_UNROLLED_GRAPH");
+  ctx->use_loop = p->stop_eps > 0.0f && !(ul && ul[0] == '1');
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
   cudaError_t e = cudaStreamCreateWithFlags(&ctx->s, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming);
@@ -459,6 +524,7 @@ disc_status disc_create(const disc_params* p, int device, void* cuda_stream, dis
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_iter, sizeof(int) * DISC_MAX_LEVELS);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_stop, sizeof(int) * (DISC_MAX_LEVELS + 1));
   if (e == cudaSuccess) ctx->d_err = ctx->d_stop + DISC_MAX_LEVELS;
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_budget, sizeof(int) * DISC_MAX_LEVELS);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_scratch, sizeof(double) * (2 * kShiftBlocks + 2));
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_maxabs, sizeof(float) * 2);
   if (e == cudaSuccess) e = cudaMemset(ctx->d_iter, 0, sizeof(int) * DISC_MAX_LEVELS);
@@ -479,6 +545,7 @@ disc_status disc_destroy(disc_ctx* ctx) {
   free_levels(ctx);
   cudaFree(ctx->d_iter);
   cudaFree(ctx->d_stop);
+  cudaFree(ctx->d_budget);
   cudaFree(ctx->d_scratch);
   cudaFree(ctx->d_maxabs);
   if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
@@ -569,7 +636,9 @@ disc_status disc_set_images(disc_ctx* ctx, const float* ct, const float* cbct, i
   } else {
     for (int l = 0; l < L; ++l) {
       if (ctx->lev[l].graph) cudaGraphExecDestroy(ctx->lev[l].graph);
+      if (ctx->lev[l].loop) cudaGraphExecDestroy(ctx->lev[l].loop);
       ctx->lev[l].graph = nullptr;
+      ctx->lev[l].loop = nullptr;
       ctx->lev[l].graph_iters = 0;
     }
   }

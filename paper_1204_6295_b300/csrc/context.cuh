@@ -42,8 +42,9 @@ struct Level {
   BoxPlan pa{};
   BoxPlan pm{};          // kModeMaskAB
   GaussPlan pb{};
-  cudaGraphExec_t graph = nullptr;
+  cudaGraphExec_t graph = nullptr;   // n iterations unrolled (graph_iters = n)
   int graph_iters = 0;
+  cudaGraphExec_t loop = nullptr;    // one iteration inside a conditional WHILE node
 };
 
 
@@ -68,6 +69,7 @@ struct disc_ctx {
   int* d_iter = nullptr;     // [DISC_MAX_LEVELS]
   int* d_stop = nullptr;     // [DISC_MAX_LEVELS]
   int* d_err = nullptr;      // device error word of the box kernels (d_stop + DISC_MAX_LEVELS)
+  int* d_budget = nullptr;   // [DISC_MAX_LEVELS] iterations left in the running loop graph
   double* d_scratch = nullptr;
   float* d_maxabs = nullptr; // [2]
   float mask_hu0 = 0.0f, mask_am = 0.0f;   // Eq. 7 thresholds (mask_mode 1)
@@ -76,6 +78,7 @@ struct disc_ctx {
   int cur_iter = 0;
   disc_status sticky = DISC_OK;
   bool use_graphs = true;
+  bool use_loop = true;      // conditional-node loop graphs (with a stop rule; else unrolled graphs)
 };
 
 

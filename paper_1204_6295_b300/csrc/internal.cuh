@@ -235,7 +235,14 @@ struct NormState {
   int cap;
   int window;
   float eps;
+  // in-graph loop (conditional WHILE node): iterations left in this launch; the
+  // kernel decrements it and sets the loop condition to (left > 0 and not stopped)
+  int* budget;
+  cudaGraphConditionalHandle cond;
+  int use_cond;
 };
+// *p = v (a one-thread kernel, stream-ordered)
+cudaError_t launch_set_int(int* p, int v, cudaStream_t s);
 cudaError_t launch_norm_finalize(const float* partials, int nparts, NormState st, cudaStream_t s);
 // One block per volume: NormState and partials of volume p in the tables.
 struct NormBatch {

@@ -139,7 +139,10 @@ __global__ void k_up2(const float* __restrict__ rc, float* __restrict__ rf, int 
 
 // l^(k) = sum|dr| / sum|r| (Sec. 2.3) from per-CTA partials; history and stop flag.
 __device__ __forceinline__ void norm_finalize_body(const float* partials, int nparts, const NormState& st) {
-  if (*(volatile int*)st.stop != 0) return;
+  if (*(volatile int*)st.stop != 0) {
+    if (st.use_cond && threadIdx.x == 0) cudaGraphSetConditional(st.cond, 0u);   // leave the loop
+    return;
+  }
   __shared__ double sh[kRedThreads / 32];
   double sdr = 0.0, sr = 0.0;
   for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
@@ -153,9 +156,18 @@ __device__ __forceinline__ void norm_finalize_body(const float* partials, int np
     const float l = sr > 0.0 ? (float)(sdr / sr) : INFINITY;
     if (k < st.cap) st.hist[k] = l;
     *st.iter = k + 1;
+    bool stop = false;
     if (st.eps > 0.0f && k >= st.window && k < st.cap) {
       const float lp = st.hist[k - st.window];
-      if (isfinite(lp) && isfinite(l) && lp - l <= st.eps) *st.stop = 1;
+      if (isfinite(lp) && isfinite(l) && lp - l <= st.eps) {
+        *st.stop = 1;
+        stop = true;
+      }
+    }
+    if (st.use_cond) {
+      const int left = *st.budget - 1;
+      *st.budget = left;
+      cudaGraphSetConditional(st.cond, (left > 0 && !stop) ? 1u : 0u);
     }
   }
 }
@@ -177,6 +189,8 @@ __global__ void k_partials_sum(const float* partials, int nparts, int comp, doub
   s = block_sum_d(s, sh);
   if (threadIdx.x == 0) *out = s;
 }
+
+__global__ void k_set_int(int* p, int v) { *p = v; }
 
 int grid_for(int64_t n) {
   int64_t b = (n + kRedThreads - 1) / kRedThreads;
@@ -213,6 +227,11 @@ cudaError_t launch_down2(const float* in, float* out, int nx, int ny, int nz, cu
 cudaError_t launch_up2(const float* rc, float* rf, int nx, int ny, int nz, cudaStream_t s) {
   const int cx = (nx + 1) / 2, cy = (ny + 1) / 2, cz = (nz + 1) / 2;
   k_up2<<<grid_for((int64_t)nx * ny * nz), kRedThreads, 0, s>>>(rc, rf, nx, ny, nz, cx, cy, cz);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_int(int* p, int v, cudaStream_t s) {
+  k_set_int<<<1, 1, 0, s>>>(p, v);
   return cudaGetLastError();
 }
 
