@@ -96,12 +96,16 @@ typedef struct {
   float fill_h;          /* h of Eq. 10, HU (the paper gives none): 50          */
   int32_t fill_t[3];     /* odd box T sizes (x, y, z), Sec. 2.3: 7, 7, 3         */
   int32_t fill_passes;   /* at most this many fill passes per iteration: 32     */
+  /* What the Gaussian regularises: 0 = the total field, r <- G * (r + dr)
+   * (Algorithm A1 steps 5-6); 1 = the increment, r <- r + G * dr (the order of
+   * Sec. 2.1: smooth dr, then add it to the field). */
+  int32_t smooth_mode;
 } disc_params;
 
 /* Fill *p with defaults: patch 3x3x3, sigma 1, radius 0, 2 levels of 50
  * iterations, stop_eps 0 (fixed counts), window 10, THIRION, global shift on,
  * var_floor 1e-6, mask off (hu0_factor 2, a_lo 0.5, a_hi 1.5, fill_h 50,
- * fill_t 7x7x3, fill_passes 32).  Returns DISC_ERR_ARG for NULL. */
+ * fill_t 7x7x3, fill_passes 32), smooth_mode 0.  Returns DISC_ERR_ARG for NULL. */
 disc_status disc_params_default(disc_params* p);
 
 /* Human-readable name of a status code (static storage, never NULL). */

@@ -522,6 +522,9 @@ class Params:
     fill_h: float = 50.0           # h of Eq. (10), HU (not given by the paper)
     fill_t: tuple = (7, 7, 3)      # T (Sec. 2.3)
     fill_passes: int = 32
+    # reading R4: 0 smooths r + dr (Algorithm A1 step 6); 1 smooths dr and adds it
+    # to r (the order of Sec. 2.1)
+    smooth_mode: int = 0
 
     @property
     def half(self):
@@ -546,8 +549,11 @@ def iteration(I_m, I_s, r, p: Params, mask: MaskState = None):
     else:
         f = correct(m, I_s, p.half, p.var_floor)       # steps 1 and 3
     dr = force(m, f, p.force_mode, p.den_floor)        # step 4
-    u = r + dr                                         # step 5
-    r_new = gaussian_smooth_field(u, p.sigma, p.radius)  # step 6
+    if p.smooth_mode:                                  # Sec. 2.1 order
+        r_new = r + gaussian_smooth_field(dr, p.sigma, p.radius)
+    else:
+        u = r + dr                                     # step 5
+        r_new = gaussian_smooth_field(u, p.sigma, p.radius)  # step 6
     l = relative_norm(dr, r)
     return r_new, dr, l, {"m": m, "f": f}
 

@@ -110,6 +110,7 @@ disc_status check_params(const disc_params* p) {
   if (!(p->var_floor >= 0.0f)) return DISC_ERR_ARG;
   if (p->stop_window < 1) return DISC_ERR_ARG;
   if (p->mask_mode != 0 && p->mask_mode != 1) return DISC_ERR_ARG;
+  if (p->smooth_mode != 0 && p->smooth_mode != 1) return DISC_ERR_ARG;
   if (p->mask_mode) {
     if (!(p->hu0_factor >= 0.0f) || !(p->a_lo >= 0.0f) || !(p->a_hi >= p->a_lo) || !(p->fill_h > 0.0f) ||
         !std::isfinite(p->hu0_factor) || !std::isfinite(p->a_hi) || !std::isfinite(p->fill_h))
@@ -176,6 +177,7 @@ cudaError_t memcpy_kind(void* dst, const void* src, size_t bytes, int dst_kind, 
 BoxArgs box_args(const disc_ctx* c, const Level& v) {
   BoxArgs a{};
   a.err = c->d_err;
+  a.u_is_dr = c->p.smooth_mode;
   a.nx = v.nx;
   a.ny = v.ny;
   a.nz = v.nz;
@@ -251,6 +253,7 @@ cudaError_t queue_masked(disc_ctx* c, int l, int n, const GaussArgs& g, const No
   fa.ny = v.ny;
   fa.nz = v.nz;
   fa.force_mode = c->p.force_mode;
+  fa.u_is_dr = c->p.smooth_mode;
   const int blocks = force_blocks((int64_t)v.N, c->max_parts);
   for (int k = 0; k < n; ++k) {
     cudaError_t e = queue_mask_fill(c, l, c->d_stop + l);
@@ -288,6 +291,7 @@ cudaError_t queue_iterations(disc_ctx* c, int l, int n, const LoopCond* loop) {
   g.t = v.t;
   g.Im = v.Im;
   g.m = v.m;                // the z pass also warps I_m for the next iteration
+  g.add = c->p.smooth_mode ? v.r : nullptr;   // r <- r + G * dr (Sec. 2.1 order)
   g.stop = c->d_stop + l;
   g.nx = v.nx;
   g.ny = v.ny;
@@ -429,6 +433,7 @@ GaussArgs ctx_gauss_args(const disc_ctx* c, int l) {
   g.t = v.t;
   g.Im = v.Im;
   g.m = v.m;
+  g.add = c->p.smooth_mode ? v.r : nullptr;
   g.stop = c->d_stop + l;
   g.nx = v.nx;
   g.ny = v.ny;
@@ -486,6 +491,7 @@ disc_status disc_params_default(disc_params* p) {
   p->fill_t[0] = p->fill_t[1] = 7;
   p->fill_t[2] = 3;
   p->fill_passes = 32;
+  p->smooth_mode = 0;
   return DISC_OK;
 }
 

@@ -337,9 +337,10 @@ __device__ __forceinline__ void box_body(const BoxArgs& a, int bx, int by, int b
           ry = __ldg(a.r + (size_t)N + g);
           rz = __ldg(a.r + 2 * (size_t)N + g);
         }
-        a.out[g] = rx + drx;
-        a.out[(size_t)N + g] = ry + dry;
-        a.out[2 * (size_t)N + g] = rz + drz;
+        const float keep = a.u_is_dr ? 0.0f : 1.0f;   // u = r + dr, or dr alone
+        a.out[g] = fmaf(keep, rx, drx);
+        a.out[(size_t)N + g] = fmaf(keep, ry, dry);
+        a.out[2 * (size_t)N + g] = fmaf(keep, rz, drz);
         acc0 += sqrt_approx(fmaf(drx, drx, fmaf(dry, dry, drz * drz)));
         acc1 += sqrt_approx(fmaf(rx, rx, fmaf(ry, ry, rz * rz)));
       }

@@ -300,9 +300,10 @@ __global__ void __launch_bounds__(kThreads) k_box_pass(BoxArgs a) {
           drz = fmaf(s2, gmz, drz);
         }
         const float rx = __ldg(a.r + g), ry = __ldg(a.r + N + g), rz = __ldg(a.r + 2 * N + g);
-        a.out[g] = rx + drx;
-        a.out[N + g] = ry + dry;
-        a.out[2 * N + g] = rz + drz;
+        const float keep = a.u_is_dr ? 0.0f : 1.0f;   // u = r + dr, or dr alone
+        a.out[g] = fmaf(keep, rx, drx);
+        a.out[N + g] = fmaf(keep, ry, dry);
+        a.out[2 * N + g] = fmaf(keep, rz, drz);
         acc0 += sqrtf(fmaf(drx, drx, fmaf(dry, dry, drz * drz)));
         acc1 += sqrtf(fmaf(rx, rx, fmaf(ry, ry, rz * rz)));
       }

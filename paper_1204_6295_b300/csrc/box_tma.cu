@@ -455,9 +455,10 @@ __device__ __forceinline__ bool box_tma_body(const BoxArgs& a, int bx, int by, i
         const int o = tid + i * kThreads;
         const float rx = ro[o], ry = ro[B::TN + o], rz = ro[2 * B::TN + o];   // staged by group B
         float* po = out0 + goff3[i];
-        po[0] = rx + drx;
-        po[(size_t)N] = ry + dry;
-        po[2 * (size_t)N] = rz + drz;
+        const float keep = a.u_is_dr ? 0.0f : 1.0f;   // u = r + dr, or dr alone
+        po[0] = fmaf(keep, rx, drx);
+        po[(size_t)N] = fmaf(keep, ry, dry);
+        po[2 * (size_t)N] = fmaf(keep, rz, drz);
         acc0 += sqrt_approx(fmaf(drx, drx, fmaf(dry, dry, drz * drz)));
         acc1 += sqrt_approx(fmaf(rx, rx, fmaf(ry, ry, rz * rz)));
       }

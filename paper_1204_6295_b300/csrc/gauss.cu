@@ -126,7 +126,9 @@ __global__ void __launch_bounds__(kThreads) k_gauss(GaussArgs a) {
         if (gx >= nx || gy >= ny) continue;
         float acc = 0.0f;
         for (int k = klo; k <= khi; ++k) acc = fmaf(w[k + R], ring[((zo + k) % KZ) * 3 * OP + e], acc);
-        a.r[c * N + vix(gx, gy, zo, nx, ny)] = nrm == 1.0f ? acc : acc / nrm;
+        const size_t o = c * N + vix(gx, gy, zo, nx, ny);
+        const float v = nrm == 1.0f ? acc : acc / nrm;
+        a.r[o] = a.add ? a.add[o] + v : v;
       }
     }
   }
@@ -387,6 +389,12 @@ __device__ __forceinline__ void gauss_z_body(const GaussArgs& a, int bx, int by,
           oz = oz / nrm;
         }
         float* rp = rb + (size_t)j * plane;
+        if (a.add) {                          // r = r_prev + G * dr (in place: same element)
+          const float* ap = a.add + (rp - a.r);
+          o2.x += ap[0];
+          o2.y += ap[N];
+          oz += ap[2 * N];
+        }
         rp[0] = o2.x;
         rp[N] = o2.y;
         rp[2 * N] = oz;
@@ -569,7 +577,10 @@ cudaError_t gauss_launch(const GaussArgs& a, const GaussPlan& p, cudaStream_t s)
     g_smem_set[dev] = (int)kMaxSmem;
   }
   k_gauss<<<p.grid, kThreads, p.smem, s>>>(b);
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  // the generic kernel does not fuse the warp of the next iteration
+  if (e == cudaSuccess && a.m != nullptr) e = launch_warp(a.Im, a.r, a.m, a.nx, a.ny, a.nz, a.stop, s);
+  return e;
 }
 
 }  // namespace disc

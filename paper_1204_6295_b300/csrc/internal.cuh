@@ -68,6 +68,7 @@ struct BoxArgs {
   int* count;
   float hu0, a_min, a_max;
   int ratio_only;
+  int u_is_dr;          // kModeIterate: write u = dr instead of r + dr (smoothing of dr, Sec. 2.1)
 };
 
 struct BoxPlan {
@@ -138,6 +139,7 @@ struct GaussArgs {
   int R;
   int zlen;
   int box_sum;          // 1: plain truncated sums (no renormalisation at the borders)
+  const float* add;     // optional [3][N]: the z pass writes r = add + G * u (add may be r itself)
   float w[2 * DISC_MAX_GAUSS_RADIUS + 1];   // normalised taps (sum 1), or all 1 for box sums
 };
 struct GaussPlan {
@@ -201,6 +203,7 @@ struct ForceArgs {
   const int* stop;
   int nx, ny, nz;
   int force_mode;
+  int u_is_dr;          // write u = dr instead of r + dr
 };
 int force_blocks(int64_t n, int max_parts);
 cudaError_t launch_force_dm(const ForceArgs& f, int blocks, cudaStream_t s);

@@ -113,9 +113,10 @@ __global__ void __launch_bounds__(kForceThreads) k_force_dm(ForceArgs f) {
       drz = fmaf(s2, gmz, drz);
     }
     const float rxv = __ldg(f.r + g), ryv = __ldg(f.r + (size_t)N + g), rzv = __ldg(f.r + 2 * (size_t)N + g);
-    f.u[g] = rxv + drx;
-    f.u[(size_t)N + g] = ryv + dry;
-    f.u[2 * (size_t)N + g] = rzv + drz;
+    const float keep = f.u_is_dr ? 0.0f : 1.0f;   // u = r + dr, or dr alone
+    f.u[g] = fmaf(keep, rxv, drx);
+    f.u[(size_t)N + g] = fmaf(keep, ryv, dry);
+    f.u[2 * (size_t)N + g] = fmaf(keep, rzv, drz);
     acc0 += sqrt_approx(fmaf(drx, drx, fmaf(dry, dry, drz * drz)));
     acc1 += sqrt_approx(fmaf(rxv, rxv, fmaf(ryv, ryv, rzv * rzv)));
   }

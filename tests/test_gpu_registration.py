@@ -33,7 +33,7 @@ def _run_gpu(disc, ct, cbct, **kw):
 def _oracle(ct, cbct, **kw):
     P = O.Params(patch=kw["patch"], sigma=kw["sigma"], radius=kw.get("radius", 0), levels=kw["levels"],
                  iters=list(kw["iters"]), force_mode=kw.get("force_mode", 0),
-                 global_shift=kw.get("global_shift", True))
+                 global_shift=kw.get("global_shift", True), smooth_mode=kw.get("smooth_mode", 0))
     return O.register(ct, cbct, P, return_history=True)
 
 
@@ -159,3 +159,16 @@ def test_errors_are_reported(disc):
         reg.set_images(ok, ok)
         reg.iterate(-1)
         assert np.all(reg.get_field() == 0.0)
+
+
+@pytest.mark.parametrize("kw", [
+    dict(patch=(5, 5, 5), sigma=1.0, levels=2, iters=(15, 10), smooth_mode=1),   # Sec. 2.1 order
+    dict(patch=(5, 5, 5), sigma=3.0, levels=2, iters=(10, 8)),                   # radius 9: generic Gaussian
+])
+def test_schedule_variants_match_oracle(disc, kw):
+    p = phantom.ellipsoid_pair(48, 40, 24, seed=13)
+    r, done, last, hist, _ = _run_gpu(disc, p.ct, p.cbct, **kw)
+    r_ref, hist_ref, _ = _oracle(p.ct, p.cbct, **kw)
+    mx, mean = _field_diff(r, r_ref)
+    assert mx <= MAX_TOL and mean <= MEAN_TOL, (mx, mean)
+    assert done == sum(kw["iters"])

@@ -438,3 +438,21 @@ def test_ssd_adjoint_matches_torch_autograd():
     loss.backward()
     assert float(loss.detach()) == pytest.approx(O.ssd_loss(I_m, I_s, r, half), rel=1e-12)
     np.testing.assert_allclose(g, rt.grad.numpy(), rtol=1e-8, atol=1e-8 * np.abs(g).max())
+
+
+def test_smoothing_order_variant_linearity():
+    """Sec. 2.1 order (r + G*dr) against A1's (G*(r + dr)): the Gaussian is linear,
+    so the two differ by exactly r - G*r; with r = 0 they coincide."""
+    rng = np.random.default_rng(31)
+    shape = (6, 8, 10)
+    I_m = rng.normal(0.0, 100.0, shape)
+    I_s = 0.9 * np.roll(I_m, 1, axis=2) + 5.0
+    r = rng.normal(0.0, 0.5, (3,) + shape)
+    pa = O.Params(patch=(3, 3, 3), sigma=1.0, levels=1, iters=[1])
+    pb = O.Params(patch=(3, 3, 3), sigma=1.0, levels=1, iters=[1], smooth_mode=1)
+    ra, dra, _, _ = O.iteration(I_m, I_s, r, pa)
+    rb, drb, _, _ = O.iteration(I_m, I_s, r, pb)
+    np.testing.assert_array_equal(dra, drb)
+    np.testing.assert_allclose(rb - ra, r - O.gaussian_smooth_field(r, 1.0), atol=1e-12)
+    z = np.zeros_like(r)
+    np.testing.assert_allclose(O.iteration(I_m, I_s, z, pa)[0], O.iteration(I_m, I_s, z, pb)[0], atol=1e-12)
