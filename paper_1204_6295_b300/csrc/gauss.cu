@@ -160,9 +160,10 @@ struct XYLayout {
   static constexpr int NXT = IY * (kSX / kBX);         // x-filter tasks (row, x quad)
   static constexpr size_t o_in2 = 0;                   // float2 [IY][IXP]  (ux, uy)
   static constexpr size_t o_inz = o_in2 + 8 * (size_t)IY * IXP;   // float [IY][IXP]
-  static constexpr size_t o_x2 = o_inz + 4 * (size_t)IY * IXP;    // float2 [IY][kSX]
-  static constexpr size_t o_xz = o_x2 + 8 * (size_t)IY * kSX;     // float [IY][kSX]
-  static constexpr size_t bytes = o_xz + 4 * (size_t)IY * kSX;
+  static constexpr int XP = kSX + 1;                   // row stride of the x-filtered planes (odd)
+  static constexpr size_t o_x2 = o_inz + 4 * (size_t)IY * IXP;    // float2 [IY][XP]
+  static constexpr size_t o_xz = o_x2 + 8 * (size_t)IY * XP;      // float [IY][XP]
+  static constexpr size_t bytes = o_xz + 4 * (size_t)IY * XP;
 };
 
 template <int R>
@@ -216,7 +217,9 @@ __device__ __forceinline__ void gauss_xy_body(const GaussArgs& a, int bx, int by
   // x filter: each task computes kBX adjacent outputs of one row from a window
   // of kBX + 2R inputs held in registers
   for (int t = tid; t < X::NXT; t += kThreads) {
-    const int iy = t / (kSX / kBX), j = t - iy * (kSX / kBX);
+    // consecutive tasks take consecutive rows: the odd row strides then spread a
+    // warp's loads and stores over all shared-memory banks
+    const int j = t / X::IY, iy = t - j * X::IY;
     const float2* r2 = in2 + iy * X::IXP + kBX * j;
     const float* rz = inz + iy * X::IXP + kBX * j;
     float2 acc[kBX];
@@ -249,8 +252,8 @@ __device__ __forceinline__ void gauss_xy_body(const GaussArgs& a, int bx, int by
           accz[b] = accz[b] / n;
         }
       }
-      x2[iy * kSX + kBX * j + b] = acc[b];
-      xz[iy * kSX + kBX * j + b] = accz[b];
+      x2[iy * X::XP + kBX * j + b] = acc[b];
+      xz[iy * X::XP + kBX * j + b] = accz[b];
     }
   }
   __syncthreads();
@@ -258,8 +261,8 @@ __device__ __forceinline__ void gauss_xy_body(const GaussArgs& a, int bx, int by
   {
     const int ox = tid & (kSX - 1), jy = tid >> 5;      // 32 columns x 8 row groups
     const int gx = x0 + ox;
-    const float2* c2 = x2 + kBY * jy * kSX + ox;
-    const float* cz = xz + kBY * jy * kSX + ox;
+    const float2* c2 = x2 + kBY * jy * X::XP + ox;
+    const float* cz = xz + kBY * jy * X::XP + ox;
     float2 acc[kBY];
     float accz[kBY];
 #pragma unroll
@@ -269,8 +272,8 @@ __device__ __forceinline__ void gauss_xy_body(const GaussArgs& a, int bx, int by
     }
 #pragma unroll
     for (int i = 0; i < kBY + 2 * R; ++i) {
-      const float2 v = c2[i * kSX];
-      const float vzz = cz[i * kSX];
+      const float2 v = c2[i * X::XP];
+      const float vzz = cz[i * X::XP];
 #pragma unroll
       for (int b = 0; b < kBY; ++b) {
         const int k = i - b;
