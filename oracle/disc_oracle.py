@@ -685,3 +685,156 @@ def ssd_grad(I_m, I_s, r, half, var_floor=1e-6):
     C = B * EM
     g_m = 2.0 * (m - f) + box_sum(A, half) + m * box_sum(B, half) - box_sum(C, half)
     return g_m[None] * warp_coord_gradient(I_m, r)
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2.4.3: evaluation metrics between two images (not on the iteration
+# path): normalised mutual information and the RMSE of binary Canny edge
+# images, Eq. (11).  Readings:
+#  R21 NMI = 2 I(A;B) / (H(A) + H(B)) (it ranges over [0, 1] as the paper says),
+#      entropies of a joint histogram with `bins` bins per image over each
+#      image's [min, max]; bin(v) = floor((v - min) * (bins / (max - min))),
+#      clamped to bins - 1, the bin index taken in float32 (the GPU's
+#      precision: a floating-point decision of an integer); NMI = 1 when both
+#      images are constant.
+#  R22 Canny edges per transverse slice (2-D): Gaussian smoothing (sigma,
+#      taps |i| <= ceil(3 sigma), renormalised over in-slice taps, x then y),
+#      central-difference gradient (one-sided at the borders), magnitude
+#      M = sqrt(gx^2 + gy^2); non-maximum suppression along the gradient
+#      direction quantised to 0, 45, 90, 135 degrees (tan 22.5 = sqrt(2) - 1),
+#      neighbours outside the slice count as 0, a pixel is kept when M is above
+#      1e-5 max_slice |I| (a constant slice smoothed in float32 has rounding-level
+#      gradients, which relative thresholds would otherwise turn into edges) and
+#      M >= both neighbours; strong where M >= t_high max_slice(M), weak where
+#      M >= t_low * that threshold; edges = 8-connected components of the kept
+#      strong and weak pixels that contain a strong pixel.  Every
+#      floating-point step is taken in float32 with the GPU's operation order
+#      (separate multiply and add, no fused multiply-add), so the edge maps are
+#      the same bit for bit.
+# ---------------------------------------------------------------------------
+
+def _f32(x):
+    return np.float32(x)
+
+
+def nmi(A, B, bins=64):
+    """Normalised mutual information of two images (reading R21)."""
+    A = np.asarray(A, np.float32).ravel()
+    B = np.asarray(B, np.float32).ravel()
+
+    def binned(X):
+        mn, mx = X.min(), X.max()
+        if mx == mn:
+            return np.zeros(X.shape, np.int64)
+        s = np.float32(bins) / np.float32(mx - mn)
+        t = np.float32(X - mn) * s                          # float32 throughout
+        return np.minimum(np.floor(t).astype(np.int64), bins - 1)
+
+    ia, ib = binned(A), binned(B)
+    joint = np.zeros((bins, bins))
+    np.add.at(joint, (ia, ib), 1.0)
+    p = joint / A.size
+    pa, pb = p.sum(1), p.sum(0)
+
+    def ent(q):
+        q = q[q > 0]
+        return float(-(q * np.log(q)).sum())
+
+    ha, hb, hab = ent(pa), ent(pb), ent(p.ravel())
+    if ha + hb == 0.0:
+        return 1.0
+    return 2.0 * (ha + hb - hab) / (ha + hb)
+
+
+def _canny_taps(sigma):
+    R = int(math.ceil(3.0 * sigma))
+    i = np.arange(-R, R + 1, dtype=np.float64)
+    w = np.exp(-i * i / (2.0 * sigma * sigma))
+    return (w / w.sum()).astype(np.float32), R
+
+
+def _smooth_axis(P, w, R, axis):
+    """One separable pass in float32: taps in ascending order, then the
+    renormalisation over the in-slice taps (product, sum, division in float32)."""
+    n = P.shape[axis]
+    out = np.zeros(P.shape, np.float32)
+    nrm = np.zeros(n, np.float32)
+    for c in range(n):
+        s = np.float32(0.0)
+        for k in range(-R, R + 1):
+            if 0 <= c + k < n:
+                s = np.float32(s + w[k + R])
+        nrm[c] = s
+    acc = np.zeros(P.shape, np.float32)
+    for k in range(-R, R + 1):
+        lo, hi = max(0, -k), min(n, n - k)
+        if lo >= hi:
+            continue
+        src = [slice(None)] * P.ndim
+        dst = [slice(None)] * P.ndim
+        src[axis] = slice(lo + k, hi + k)
+        dst[axis] = slice(lo, hi)
+        acc[tuple(dst)] = acc[tuple(dst)] + w[k + R] * P[tuple(src)]   # float32 mul, then add
+    shape = [1] * P.ndim
+    shape[axis] = n
+    nr = nrm.reshape(shape)
+    out[...] = np.where(nr == np.float32(1.0), acc, acc / nr)
+    return out
+
+
+def _diff_axis(S, axis):
+    n = S.shape[axis]
+    g = np.zeros(S.shape, np.float32)
+    if n < 2:
+        return g
+    sl = lambda a, b: tuple(slice(a, b) if ax == axis else slice(None) for ax in range(S.ndim))
+    g[sl(1, n - 1)] = np.float32(0.5) * (S[sl(2, n)] - S[sl(0, n - 2)])
+    g[sl(0, 1)] = S[sl(1, 2)] - S[sl(0, 1)]
+    g[sl(n - 1, n)] = S[sl(n - 1, n)] - S[sl(n - 2, n - 1)]
+    return g
+
+
+def canny(img, sigma=1.0, t_low=0.4, t_high=0.2):
+    """Binary Canny edge image, slice by slice (reading R22); bool [nz][ny][nx]."""
+    from scipy import ndimage
+    img = np.asarray(img, np.float32)
+    w, R = _canny_taps(sigma)
+    edges = np.zeros(img.shape, bool)
+    t1 = _f32(math.sqrt(2.0) - 1.0)
+    t2 = _f32(math.sqrt(2.0) + 1.0)
+    for z in range(img.shape[0]):
+        P = img[z]
+        S = _smooth_axis(_smooth_axis(P, w, R, 1), w, R, 0)
+        gx = _diff_axis(S, 1)
+        gy = _diff_axis(S, 0)
+        M = np.sqrt(gx * gx + gy * gy).astype(np.float32)
+        Mp = np.pad(M, 1)                                    # neighbours outside count as 0
+
+        def nb(dy, dx):
+            return Mp[1 + dy:1 + dy + M.shape[0], 1 + dx:1 + dx + M.shape[1]]
+
+        ax, ay = np.abs(gx), np.abs(gy)
+        horiz = ay <= t1 * ax
+        vert = ay >= t2 * ax
+        diag_pos = (gx * gy) > 0
+        n1 = np.where(horiz, nb(0, 1), np.where(vert, nb(1, 0), np.where(diag_pos, nb(1, 1), nb(1, -1))))
+        n2 = np.where(horiz, nb(0, -1), np.where(vert, nb(-1, 0), np.where(diag_pos, nb(-1, -1), nb(-1, 1))))
+        floor = _f32(1e-5) * np.abs(P).max()
+        keep = (M > floor) & (M >= n1) & (M >= n2)
+        hi = _f32(t_high) * M.max()
+        lo = _f32(t_low) * hi
+        strong = keep & (M >= hi)
+        cand = keep & (M >= lo)
+        if not strong.any():
+            continue
+        lab, _ = ndimage.label(cand, structure=np.ones((3, 3), int))
+        good = np.unique(lab[strong])
+        edges[z] = np.isin(lab, good[good > 0])
+    return edges
+
+
+def edge_rmse(E1, E2):
+    """Eq. (11): sqrt(sum_i (E1(i) - E2(i))^2 / N) of two binary edge images."""
+    E1 = np.asarray(E1, bool)
+    E2 = np.asarray(E2, bool)
+    return math.sqrt(np.count_nonzero(E1 != E2) / E1.size)
