@@ -172,6 +172,13 @@ disc_status disc_get_norm_history(disc_ctx* ctx, int32_t level, float* out,
  * with the mask off.  Any pointer may be NULL. */
 disc_status disc_get_mask_constants(disc_ctx* ctx, float* hu0, float* a_m);
 
+/* Sec. 2.4.3 metrics of the registration at its current level: NMI (bins)
+ * and the Canny edge RMSE of Eq. 11 (sigma, t_low, t_high; see
+ * disc_k_canny) between the warped CT I_m(x + r(x)) and the corrected CBCT
+ * I'_s.  Host outputs (either may be NULL); synchronises. */
+disc_status disc_get_metrics(disc_ctx* ctx, int32_t bins, float sigma, float t_low, float t_high,
+                             double* nmi, double* rmse_edge);
+
 /* Release every resource of the context.  NULL is accepted. */
 disc_status disc_destroy(disc_ctx* ctx);
 
@@ -378,6 +385,33 @@ disc_status disc_k_correct_masked(const float* m, const float* Is, const float* 
  * norms_out (device double[2], may be NULL): sum |dr|, sum |r|. */
 disc_status disc_k_force(const float* m, const float* d, const float* r, float* u, double* norms_out,
                          int32_t nx, int32_t ny, int32_t nz, int32_t force_mode, void* stream);
+
+/* ---------------------------------------------------------------------
+ * Evaluation metrics (Sec. 2.4.3), between two images; not part of the
+ * iteration.
+ * ------------------------------------------------------------------- */
+
+/* Normalised mutual information 2 I(A;B) / (H(A) + H(B)) in [0, 1] from a
+ * joint histogram of `bins` (2..128) bins per image over each image's
+ * [min, max] (bin = floor((v - min) * bins / (max - min)), in float32);
+ * 1 when both images are constant.  *nmi_out: device double. */
+disc_status disc_k_nmi(const float* a, const float* b, int64_t n, int32_t bins, double* nmi_out,
+                       void* stream);
+
+/* Binary Canny edge image (edges: N bytes, 1 = edge), slice by slice in z:
+ * Gaussian smoothing (sigma, taps |i| <= ceil(3 sigma) <= 16, renormalised at
+ * the borders), central-difference gradient, non-maximum suppression along
+ * the gradient direction quantised to 45 degrees (a pixel needs M above
+ * 1e-5 max|slice|), strong pixels M >= t_high max_slice(M), weak ones
+ * M >= t_low times that, hysteresis over 8-connected weak pixels.  Every
+ * decision is taken in float32 with explicitly rounded operations.
+ * Synchronises `stream`. */
+disc_status disc_k_canny(const float* img, uint8_t* edges, int32_t nx, int32_t ny, int32_t nz,
+                         float sigma, float t_low, float t_high, void* stream);
+
+/* Eq. (11): sqrt(sum_i (E1(i) - E2(i))^2 / N) of two binary edge images
+ * (bytes, non-zero = edge).  *out: device double. */
+disc_status disc_k_edge_rmse(const uint8_t* e1, const uint8_t* e2, int64_t n, double* out, void* stream);
 
 /* Error word of the kernel-level calls above.  Their moment passes read
  * the volume through bulk tensor copies completed on shared-memory

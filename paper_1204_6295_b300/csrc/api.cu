@@ -805,22 +805,19 @@ disc_status disc_get_field(disc_ctx* ctx, float* out, int mem_kind) {
   return DISC_OK;
 }
 
-disc_status disc_get_corrected(disc_ctx* ctx, float* out, int mem_kind) {
-  if (!ctx || !out) return DISC_ERR_ARG;
-  if (mem_kind != DISC_MEM_HOST && mem_kind != DISC_MEM_DEVICE) return DISC_ERR_ARG;
-  if (ctx->sticky != DISC_OK) return DISC_ERR_STATE;
-  if (!ctx->have_images) return DISC_ERR_STATE;
-  DeviceGuard guard(ctx->device);
-  CK(enter(ctx));
+}  // extern "C"
+
+namespace {
+
+// The warped CT m = I_m(x + r(x)) into v.m and the corrected CBCT I'_s into
+// v.u (first N floats) at the current level, on ctx->s.
+cudaError_t corrected_into_u(disc_ctx* ctx) {
   Level& v = ctx->lev[ctx->cur_level];
-  CK(launch_warp(v.Im, v.r, v.m, v.nx, v.ny, v.nz, nullptr, ctx->s));
+  cudaError_t e = launch_warp(v.Im, v.r, v.m, v.nx, v.ny, v.nz, nullptr, ctx->s);
+  if (e != cudaSuccess) return e;
   if (ctx->p.mask_mode) {                  // I'_s = m + d of the masked correction
-    CK(queue_mask_fill(ctx, ctx->cur_level, nullptr));
-    CK(launch_add(v.m, v.dm, v.u, (int64_t)v.N, ctx->s));
-    CK(memcpy_kind(out, v.u, v.N * sizeof(float), mem_kind, DISC_MEM_DEVICE, ctx->s));
-    if (mem_kind == DISC_MEM_HOST) CK_DEV(ctx);
-    CK(leave(ctx));
-    return DISC_OK;
+    e = queue_mask_fill(ctx, ctx->cur_level, nullptr);
+    return e != cudaSuccess ? e : launch_add(v.m, v.dm, v.u, (int64_t)v.N, ctx->s);
   }
   BoxArgs a = box_args(ctx, v);
   a.src = v.m;
@@ -830,9 +827,55 @@ disc_status disc_get_corrected(disc_ctx* ctx, float* out, int mem_kind) {
   a.qscale = ctx->qs_m;
   a.inv_qscale = 1.0f / ctx->qs_m;
   BoxPlan pc = box_plan(kModeCorrected, v.nx, v.ny, v.nz, ctx->hx, ctx->hy, ctx->hz, ctx->num_sms);
-  CK(box_launch(kModeCorrected, a, pc, ctx->s));
+  return box_launch(kModeCorrected, a, pc, ctx->s);
+}
+
+}  // namespace
+
+extern "C" {
+
+disc_status disc_get_corrected(disc_ctx* ctx, float* out, int mem_kind) {
+  if (!ctx || !out) return DISC_ERR_ARG;
+  if (mem_kind != DISC_MEM_HOST && mem_kind != DISC_MEM_DEVICE) return DISC_ERR_ARG;
+  if (ctx->sticky != DISC_OK) return DISC_ERR_STATE;
+  if (!ctx->have_images) return DISC_ERR_STATE;
+  DeviceGuard guard(ctx->device);
+  CK(enter(ctx));
+  Level& v = ctx->lev[ctx->cur_level];
+  CK(corrected_into_u(ctx));
   CK(memcpy_kind(out, v.u, v.N * sizeof(float), mem_kind, DISC_MEM_DEVICE, ctx->s));
   if (mem_kind == DISC_MEM_HOST) CK_DEV(ctx);
+  CK(leave(ctx));
+  return DISC_OK;
+}
+
+disc_status disc_get_metrics(disc_ctx* ctx, int32_t bins, float sigma, float t_low, float t_high, double* nmi,
+                             double* rmse_edge) {
+  if (!ctx) return DISC_ERR_ARG;
+  if (bins < 2 || bins > 128 || !(sigma > 0.0f) || std::ceil(3.0 * sigma) > 16) return DISC_ERR_ARG;
+  if (ctx->sticky != DISC_OK) return DISC_ERR_STATE;
+  if (!ctx->have_images) return DISC_ERR_STATE;
+  DeviceGuard guard(ctx->device);
+  CK(enter(ctx));
+  Level& v = ctx->lev[ctx->cur_level];
+  CK(corrected_into_u(ctx));
+  const int64_t N = (int64_t)v.N;
+  double* d = nullptr;   // nmi, rmse
+  uint8_t* edges = nullptr;
+  CK(cudaMallocAsync(reinterpret_cast<void**>(&d), 2 * sizeof(double), ctx->s));
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&edges), 2 * N, ctx->s);
+  if (e == cudaSuccess) e = metric_nmi(v.m, v.u, N, bins, d, ctx->s);
+  if (e == cudaSuccess) e = metric_canny(v.m, edges, v.nx, v.ny, v.nz, sigma, t_low, t_high, ctx->s);
+  if (e == cudaSuccess) e = metric_canny(v.u, edges + N, v.nx, v.ny, v.nz, sigma, t_low, t_high, ctx->s);
+  if (e == cudaSuccess) e = metric_edge_rmse(edges, edges + N, N, d + 1, ctx->s);
+  double h[2] = {0.0, 0.0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, ctx->s);
+  if (edges) cudaFreeAsync(edges, ctx->s);
+  cudaFreeAsync(d, ctx->s);
+  CK(e);
+  CK_DEV(ctx);
+  if (nmi) *nmi = h[0];
+  if (rmse_edge) *rmse_edge = h[1];
   CK(leave(ctx));
   return DISC_OK;
 }
@@ -1039,6 +1082,36 @@ disc_status disc_k_force(const float* m, const float* d, const float* r, float* 
   }
   cudaError_t e2 = cudaFreeAsync(parts, s);
   if (e != cudaSuccess || e2 != cudaSuccess) {
+    cudaGetLastError();
+    return DISC_ERR_CUDA;
+  }
+  return DISC_OK;
+}
+
+disc_status disc_k_nmi(const float* a, const float* b, int64_t n, int32_t bins, double* nmi_out, void* stream) {
+  if (!a || !b || !nmi_out || n < 1 || bins < 2 || bins > 128) return DISC_ERR_ARG;
+  if (metric_nmi(a, b, n, bins, nmi_out, (cudaStream_t)stream) != cudaSuccess) {
+    cudaGetLastError();
+    return DISC_ERR_CUDA;
+  }
+  return DISC_OK;
+}
+
+disc_status disc_k_canny(const float* img, uint8_t* edges, int32_t nx, int32_t ny, int32_t nz, float sigma,
+                         float t_low, float t_high, void* stream) {
+  if (!img || !edges || !(sigma > 0.0f) || std::ceil(3.0 * sigma) > 16) return DISC_ERR_ARG;
+  if (!(t_low >= 0.0f) || !(t_high >= 0.0f)) return DISC_ERR_ARG;
+  if (nx < 1 || ny < 1 || nz < 1 || (double)nx * ny * nz >= 2147483647.0) return DISC_ERR_SHAPE;
+  if (metric_canny(img, edges, nx, ny, nz, sigma, t_low, t_high, (cudaStream_t)stream) != cudaSuccess) {
+    cudaGetLastError();
+    return DISC_ERR_CUDA;
+  }
+  return DISC_OK;
+}
+
+disc_status disc_k_edge_rmse(const uint8_t* e1, const uint8_t* e2, int64_t n, double* out, void* stream) {
+  if (!e1 || !e2 || !out || n < 1) return DISC_ERR_ARG;
+  if (metric_edge_rmse(e1, e2, n, out, (cudaStream_t)stream) != cudaSuccess) {
     cudaGetLastError();
     return DISC_ERR_CUDA;
   }

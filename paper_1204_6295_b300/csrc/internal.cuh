@@ -220,6 +220,15 @@ cudaError_t launch_fill_remaining(const int* cnt, int passes, int* out, cudaStre
 cudaError_t launch_add(const float* a, const float* b, float* out, int64_t n, cudaStream_t s);
 
 // ----------------------------------------------------------------------------
+// Evaluation metrics, metrics.cu (Sec. 2.4.3)
+// ----------------------------------------------------------------------------
+cudaError_t metric_nmi(const float* a, const float* b, int64_t n, int bins, double* out, cudaStream_t s);
+// synchronises s (the hysteresis passes run until nothing changes)
+cudaError_t metric_canny(const float* img, uint8_t* edges, int nx, int ny, int nz, float sigma, float t_low,
+                         float t_high, cudaStream_t s);
+cudaError_t metric_edge_rmse(const uint8_t* a, const uint8_t* b, int64_t n, double* out, cudaStream_t s);
+
+// ----------------------------------------------------------------------------
 // Small kernels, misc.cu
 // ----------------------------------------------------------------------------
 cudaError_t launch_max_abs(const float* v, int64_t n, float* out, cudaStream_t s);

@@ -106,6 +106,11 @@ _SIGS = {
                                     ctypes.POINTER(_i32), _f32, _f32, _f32, _f32, _f32, _f32,
                                     ctypes.POINTER(_i32), _i32, _vp]),
     "disc_k_force": (_st, [_vp, _vp, _vp, _vp, _vp, _i32, _i32, _i32, _i32, _vp]),
+    "disc_k_nmi": (_st, [_vp, _vp, _i64, _i32, _vp, _vp]),
+    "disc_k_canny": (_st, [_vp, _vp, _i32, _i32, _i32, _f32, _f32, _f32, _vp]),
+    "disc_k_edge_rmse": (_st, [_vp, _vp, _i64, _vp, _vp]),
+    "disc_get_metrics": (_st, [_vp, _i32, _f32, _f32, _f32, ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_double)]),
     "disc_k_force_update": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _i32, _i32, _i32,
                                   ctypes.POINTER(_i32), _f32, _f32, _i32, _vp]),
     "disc_k_ssd_loss": (_st, [_vp, _vp, _vp, _vp, _i32, _i32, _i32, ctypes.POINTER(_i32), _f32, _f32, _vp]),
@@ -291,6 +296,13 @@ class Registration:
                "disc_get_norm_history")
         return out[:n.value].copy()
 
+    def metrics(self, bins=64, sigma=1.0, t_low=0.4, t_high=0.2):
+        """(NMI, edge RMSE of Eq. 11) between I_m(x + r(x)) and I'_s at the current level."""
+        nmi, rmse = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        _check(_lib.disc_get_metrics(self._h, int(bins), float(sigma), float(t_low), float(t_high),
+                                     ctypes.byref(nmi), ctypes.byref(rmse)), "disc_get_metrics")
+        return nmi.value, rmse.value
+
     def mask_constants(self):
         """(HU0, a_m) fixed at set_images when the mask is on (Eq. 7, Sec. 2.3)."""
         hu0, am = _f32(0.0), _f32(0.0)
@@ -462,6 +474,24 @@ def k_force(m, d, r, u, norms_out=None, force_mode=FORCE_THIRION, stream=None):
     nz, ny, nx = m.shape
     _check(_lib.disc_k_force(_ptr(m), _ptr(d), _ptr(r), _ptr(u), _ptr(norms_out), nx, ny, nz, int(force_mode),
                              _stream(stream)), "disc_k_force")
+
+
+def k_nmi(a, b, out, bins=64, stream=None):
+    """Normalised mutual information of two images into out (device double)."""
+    _check(_lib.disc_k_nmi(_ptr(a), _ptr(b), int(a.numel()), int(bins), _ptr(out), _stream(stream)), "disc_k_nmi")
+
+
+def k_canny(img, edges, sigma=1.0, t_low=0.4, t_high=0.2, stream=None):
+    """Binary Canny edges (uint8 tensor like img), slice by slice."""
+    nz, ny, nx = img.shape
+    _check(_lib.disc_k_canny(_ptr(img), _ptr(edges), nx, ny, nz, float(sigma), float(t_low), float(t_high),
+                             _stream(stream)), "disc_k_canny")
+
+
+def k_edge_rmse(e1, e2, out, stream=None):
+    """Eq. (11) of two binary edge images into out (device double)."""
+    _check(_lib.disc_k_edge_rmse(_ptr(e1), _ptr(e2), int(e1.numel()), _ptr(out), _stream(stream)),
+           "disc_k_edge_rmse")
 
 
 def k_check_error(stream=None):
