@@ -267,6 +267,7 @@ __device__ __forceinline__ bool box_tma_body(const BoxArgs& a, int bx, int by, i
   }
 
   float acc0 = 0.0f, acc1 = 0.0f;
+  const float keep = a.u_is_dr ? 0.0f : 1.0f;   // the force stage writes u = keep r + dr
   if (tid == 0) issue_a(st.zi0);
 
   // slot of the centre plane in the ring of d planes, kept incrementally
@@ -455,7 +456,6 @@ __device__ __forceinline__ bool box_tma_body(const BoxArgs& a, int bx, int by, i
         const int o = tid + i * kThreads;
         const float rx = ro[o], ry = ro[B::TN + o], rz = ro[2 * B::TN + o];   // staged by group B
         float* po = out0 + goff3[i];
-        const float keep = a.u_is_dr ? 0.0f : 1.0f;   // u = r + dr, or dr alone
         po[0] = fmaf(keep, rx, drx);
         po[(size_t)N] = fmaf(keep, ry, dry);
         po[2 * (size_t)N] = fmaf(keep, rz, drz);
