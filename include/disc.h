@@ -100,12 +100,20 @@ typedef struct {
    * (Algorithm A1 steps 5-6); 1 = the increment, r <- r + G * dr (the order of
    * Sec. 2.1: smooth dr, then add it to the field). */
   int32_t smooth_mode;
+  /* Bounds of |I_m| and |I_s| (after the global shift) from which the
+   * fixed-point scales of the patch sums are derived (disc_qscale); 0 = the
+   * images' own largest magnitudes.  A z slab of a larger volume passes the
+   * whole volume's maxima so that its sums and moments are those of the whole
+   * volume bit for bit.  A bound below the images' own maximum is rejected
+   * by disc_set_images (DISC_ERR_ARG): the sums could overflow. */
+  float quant_max[2];
 } disc_params;
 
 /* Fill *p with defaults: patch 3x3x3, sigma 1, radius 0, 2 levels of 50
  * iterations, stop_eps 0 (fixed counts), window 10, THIRION, global shift on,
  * var_floor 1e-6, mask off (hu0_factor 2, a_lo 0.5, a_hi 1.5, fill_h 50,
- * fill_t 7x7x3, fill_passes 32), smooth_mode 0.  Returns DISC_ERR_ARG for NULL. */
+ * fill_t 7x7x3, fill_passes 32), smooth_mode 0, quant_max 0 0.  Returns
+ * DISC_ERR_ARG for NULL. */
 disc_status disc_params_default(disc_params* p);
 
 /* Human-readable name of a status code (static storage, never NULL). */

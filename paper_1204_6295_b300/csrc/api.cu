@@ -111,6 +111,8 @@ disc_status check_params(const disc_params* p) {
   if (p->stop_window < 1) return DISC_ERR_ARG;
   if (p->mask_mode != 0 && p->mask_mode != 1) return DISC_ERR_ARG;
   if (p->smooth_mode != 0 && p->smooth_mode != 1) return DISC_ERR_ARG;
+  for (int i = 0; i < 2; ++i)
+    if (!(p->quant_max[i] >= 0.0f) || !std::isfinite(p->quant_max[i])) return DISC_ERR_ARG;
   if (p->mask_mode) {
     if (!(p->hu0_factor >= 0.0f) || !(p->a_lo >= 0.0f) || !(p->a_hi >= p->a_lo) || !(p->fill_h > 0.0f) ||
         !std::isfinite(p->hu0_factor) || !std::isfinite(p->a_hi) || !std::isfinite(p->fill_h))
@@ -669,6 +671,12 @@ disc_status disc_set_images(disc_ctx* ctx, const float* ct, const float* cbct, i
   CK(cudaMemcpyAsync(mx, ctx->d_maxabs, sizeof(mx), cudaMemcpyDeviceToHost, ctx->s));
   CK(cudaStreamSynchronize(ctx->s));
   if (!std::isfinite(mx[0]) || !std::isfinite(mx[1])) return DISC_ERR_ARG;   // NaN/Inf input
+  for (int i = 0; i < 2; ++i) {
+    if (ctx->p.quant_max[i] > 0.0f) {                   // a caller's bound (a slab of a larger volume)
+      if (ctx->p.quant_max[i] < mx[i]) return DISC_ERR_ARG;
+      mx[i] = ctx->p.quant_max[i];
+    }
+  }
   const int32_t patch[3] = {ctx->p.patch[0], ctx->p.patch[1], ctx->p.patch[2]};
   ctx->qs_m = disc_qscale(mx[0], patch);
   ctx->qs_s = disc_qscale(mx[1], patch);

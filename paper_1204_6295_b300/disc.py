@@ -57,6 +57,7 @@ class Params(ctypes.Structure):
         ("fill_t", ctypes.c_int32 * 3),
         ("fill_passes", ctypes.c_int32),
         ("smooth_mode", ctypes.c_int32),
+        ("quant_max", ctypes.c_float * 2),
     ]
 
 
@@ -178,7 +179,7 @@ def _f32_check(t, shape, name):
 def make_params(patch=(3, 3, 3), sigma=1.0, radius=0, levels=2, iters=(50, 50), stop_eps=0.0,
                 stop_window=10, force_mode=FORCE_THIRION, global_shift=True, var_floor=1e-6,
                 mask_mode=0, hu0_factor=2.0, a_lo=0.5, a_hi=1.5, fill_h=50.0, fill_t=(7, 7, 3),
-                fill_passes=32, smooth_mode=0):
+                fill_passes=32, smooth_mode=0, quant_max=(0.0, 0.0)):
     p = Params()
     _check(_lib.disc_params_default(ctypes.byref(p)), "disc_params_default")
     for a in range(3):
@@ -205,6 +206,8 @@ def make_params(patch=(3, 3, 3), sigma=1.0, radius=0, levels=2, iters=(50, 50), 
         p.fill_t[a] = int(fill_t[a])
     p.fill_passes = int(fill_passes)
     p.smooth_mode = int(smooth_mode)
+    p.quant_max[0] = float(quant_max[0])
+    p.quant_max[1] = float(quant_max[1])
     return p
 
 

@@ -1,0 +1,81 @@
+"""Z-slab decomposition on the GPU: a volume registered as 2 or 3 slab contexts
+with halo exchanges of r after every iteration gives the whole-volume
+context's field bit for bit (same kernels, same fixed-point scales through
+quant_max, same global shift); a halo one plane short of an iteration's reach
+does not.  quant_max below an image's own maximum is rejected.
+"""
+import numpy as np
+import pytest
+
+from paper_1204_6295_b300 import phantom
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def disc():
+    from paper_1204_6295_b300 import disc as d
+    return d
+
+
+@pytest.fixture(scope="module")
+def pair():
+    return phantom.ellipsoid_pair(48, 40, 64, seed=23)
+
+
+ITERS = 8
+
+
+def _whole(disc, pair, **kw):
+    with disc.Registration(levels=1, iters=(ITERS,), **kw) as reg:
+        reg.set_images(pair.ct, pair.cbct)
+        reg.iterate(-1)
+        return reg.get_field()
+
+
+@pytest.mark.parametrize("nslabs,kw", [
+    (2, dict(patch=(5, 5, 5), sigma=1.0)),
+    (3, dict(patch=(3, 3, 7), sigma=1.5, force_mode=1)),
+    (2, dict(patch=(5, 5, 3), sigma=1.0, smooth_mode=1)),
+])
+def test_slabs_equal_whole_volume(disc, pair, nslabs, kw):
+    import torch
+    from paper_1204_6295_b300.slab import SlabRegistration
+    whole = _whole(disc, pair, **kw)
+    assert np.abs(whole[2]).max() < 6.0
+    ct, cbct = torch.from_numpy(pair.ct).cuda(), torch.from_numpy(pair.cbct).cuda()
+    with SlabRegistration(nslabs, max_disp_z=6.0, **kw) as sr:
+        sr.set_images(ct, cbct)
+        assert all(b1 - b0 < 64 for _, _, b0, b1 in sr.plan)    # every slab is a proper part
+        sr.iterate(ITERS)
+        got = sr.get_field().cpu().numpy()
+    np.testing.assert_array_equal(got, whole)
+
+
+def test_short_halo_differs(disc, pair):
+    import torch
+    from paper_1204_6295_b300.slab import SlabRegistration
+    kw = dict(patch=(5, 5, 5), sigma=1.0)
+    whole = _whole(disc, pair, **kw)
+    ct, cbct = torch.from_numpy(pair.ct).cuda(), torch.from_numpy(pair.cbct).cuda()
+    with SlabRegistration(2, halo=3 + 1 + 2 - 1, **kw) as sr:
+        sr.set_images(ct, cbct)
+        sr.iterate(ITERS)
+        got = sr.get_field().cpu().numpy()
+    assert np.abs(got - whole).max() > 1e-4
+
+
+def test_quant_max_bounds(disc, pair):
+    mx = float(np.abs(pair.ct).max())
+    with disc.Registration(levels=1, iters=(2,), patch=(3, 3, 3), global_shift=False,
+                           quant_max=(0.5 * mx, 0.0)) as reg:
+        with pytest.raises(disc.DiscError):
+            reg.set_images(pair.ct, pair.cbct)
+    # a bound equal to the maximum gives the default scales: the same field
+    fields = []
+    for q in ((0.0, 0.0), (mx, float(np.abs(pair.cbct).max()))):
+        with disc.Registration(levels=1, iters=(3,), patch=(3, 3, 3), global_shift=False, quant_max=q) as reg:
+            reg.set_images(pair.ct, pair.cbct)
+            reg.iterate(-1)
+            fields.append(reg.get_field())
+    np.testing.assert_array_equal(fields[0], fields[1])
