@@ -141,7 +141,8 @@ void free_levels(disc_ctx* c) {
     cudaFree(v.ab);
     cudaFree(v.dm);
     cudaFree(v.stamp);
-    cudaFree(v.list);
+    cudaFree(v.kbits);
+    cudaFree(v.flist);
     cudaFree(v.cnt);
     v = Level{};
   }
@@ -207,7 +208,6 @@ cudaError_t queue_mask_fill(disc_ctx* c, int l, const int* stop) {
   a.a_out = v.ab;
   a.b_out = v.ab + v.N;
   a.stamp = v.stamp;
-  a.list = v.list;
   a.count = v.cnt;
   a.hu0 = c->mask_hu0;
   a.a_min = c->p.a_lo * c->mask_am;
@@ -224,6 +224,13 @@ cudaError_t queue_mask_fill(disc_ctx* c, int l, const int* stop) {
   f.d = v.dm;
   f.stamp = v.stamp;
   f.cnt = v.cnt;
+  f.passes = c->p.fill_passes;
+  f.nwx = (v.nx + 31) / 32;
+  f.list = v.flist;
+  f.boff = v.flist + v.N;
+  f.nfront = f.boff + fill_front_blocks(v.nx, v.ny, v.nz);
+  const size_t W = (size_t)fill_words(v.nx, v.ny, v.nz);
+  if (e == cudaSuccess) e = launch_fill_pack(v.stamp, v.kbits, v.nx, v.ny, v.nz, c->s);
   f.nx = v.nx;
   f.ny = v.ny;
   f.nz = v.nz;
@@ -234,9 +241,9 @@ cudaError_t queue_mask_fill(disc_ctx* c, int l, const int* stop) {
   f.stop = stop;
   for (int p = 1; p <= c->p.fill_passes && e == cudaSuccess; ++p) {
     f.pass = p;
-    f.list_in = v.list + ((p - 1) % 2) * v.N;
-    f.list_out = v.list + (p % 2) * v.N;
-    e = launch_fill_pass(f, (int)v.N, c->s);
+    f.kin = v.kbits + ((p - 1) % 2) * W;
+    f.kout = v.kbits + (p % 2) * W;
+    e = launch_fill_pass(f, c->s);
   }
   return e;
 }
@@ -616,7 +623,9 @@ disc_status disc_set_images(disc_ctx* ctx, const float* ct, const float* cbct, i
         if (e == cudaSuccess) e = cudaMalloc(&v.ab, 2 * v.N * sizeof(float));
         if (e == cudaSuccess) e = cudaMalloc(&v.dm, v.N * sizeof(float));
         if (e == cudaSuccess) e = cudaMalloc(&v.stamp, v.N * sizeof(int));
-        if (e == cudaSuccess) e = cudaMalloc(&v.list, 2 * v.N * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&v.kbits, 2 * sizeof(unsigned) * (size_t)fill_words(v.nx, v.ny, v.nz));
+        if (e == cudaSuccess)
+          e = cudaMalloc(&v.flist, sizeof(int) * (v.N + (size_t)fill_front_blocks(v.nx, v.ny, v.nz) + 1));
         if (e == cudaSuccess) e = cudaMalloc(&v.cnt, (ctx->p.fill_passes + 1) * sizeof(int));
       }
       if (e != cudaSuccess) {
@@ -1006,13 +1015,18 @@ disc_status disc_k_correct_masked(const float* m, const float* Is, const float* 
   for (int k = 0; k < 3; ++k)
     if (fill_t[k] < 1 || fill_t[k] > 15 || fill_t[k] % 2 == 0) return DISC_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
+  const size_t W = (size_t)fill_words(nx, ny, nz);
   const size_t N = (size_t)nx * ny * nz;
-  int* work = nullptr;   // two lists [2][N] and the counters [fill_passes + 1]
-  if (cudaMallocAsync(&work, sizeof(int) * (2 * N + fill_passes + 1), s) != cudaSuccess) {
+  const size_t FB = (size_t)fill_front_blocks(nx, ny, nz);
+  // the counters [fill_passes + 1], two known-voxel bit masks [2][W], the front
+  // list [N], its block offsets [FB] and length [1]
+  int* work = nullptr;
+  if (cudaMallocAsync(&work, sizeof(int) * (fill_passes + 1 + 2 * W + N + FB + 1), s) != cudaSuccess) {
     cudaGetLastError();
     return DISC_ERR_OOM;
   }
-  int* cnt = work + 2 * N;
+  int* cnt = work;
+  unsigned* kbits = reinterpret_cast<unsigned*>(work + fill_passes + 1);
   cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int) * (fill_passes + 1), s);
   BoxArgs a = kargs(nx, ny, nz, h, qscale, var_floor);
   a.src = m;
@@ -1023,7 +1037,6 @@ disc_status disc_k_correct_masked(const float* m, const float* Is, const float* 
   a.a_out = av;
   a.b_out = bv;
   a.stamp = stamp;
-  a.list = work;
   a.count = cnt;
   a.hu0 = hu0;
   a.a_min = a_min;
@@ -1037,6 +1050,12 @@ disc_status disc_k_correct_masked(const float* m, const float* Is, const float* 
   f.d = d;
   f.stamp = stamp;
   f.cnt = cnt;
+  f.passes = fill_passes;
+  f.nwx = (nx + 31) / 32;
+  f.list = reinterpret_cast<int*>(kbits + 2 * W);
+  f.boff = f.list + N;
+  f.nfront = f.boff + FB;
+  if (e == cudaSuccess && st == DISC_OK) e = launch_fill_pack(stamp, kbits, nx, ny, nz, s);
   f.nx = nx;
   f.ny = ny;
   f.nz = nz;
@@ -1046,9 +1065,9 @@ disc_status disc_k_correct_masked(const float* m, const float* Is, const float* 
   f.inv_h = 1.0f / fill_h;
   for (int p = 1; p <= fill_passes && e == cudaSuccess && st == DISC_OK; ++p) {
     f.pass = p;
-    f.list_in = work + ((p - 1) % 2) * N;
-    f.list_out = work + (p % 2) * N;
-    e = launch_fill_pass(f, (int)N, s);
+    f.kin = kbits + ((p - 1) % 2) * W;
+    f.kout = kbits + (p % 2) * W;
+    e = launch_fill_pass(f, s);
   }
   if (e == cudaSuccess && st == DISC_OK && remaining_out) e = launch_fill_remaining(cnt, fill_passes, remaining_out, s);
   cudaError_t e2 = cudaFreeAsync(work, s);

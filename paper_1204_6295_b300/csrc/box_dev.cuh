@@ -61,8 +61,8 @@ static __device__ __forceinline__ void patch_moments(long long S1, long long S2,
 //   a = STD(M) / STD(S), b = E(M) - a E(S) with E(S) = I_s - zs STD(S);
 //   xi = 1 where STD(S) = 0, |m - I_s| > HU0, or a outside [a_min, a_max].
 // Unmasked voxels keep d = zs STD(M) + dc (the path's deviation form); masked
-// ones start from the paper's a = b = 0 (d = -m), stamp -1, and join the list
-// of voxels for the fill passes.
+// ones start from the paper's a = b = 0 (d = -m) and stamp -1, and are counted
+// for the fill passes.
 static __device__ __forceinline__ void mask_epilogue(const BoxArgs& a, size_t g, float vc, float dc, float sg,
                                                      float zsv) {
   const float sd = __ldg(a.sd + g);
@@ -83,7 +83,7 @@ static __device__ __forceinline__ void mask_epilogue(const BoxArgs& a, size_t g,
     a.b_out[g] = 0.0f;
     a.out[g] = -vc;
     a.stamp[g] = -1;
-    a.list[atomicAdd(a.count, 1)] = (int)g;
+    atomicAdd(a.count, 1);
   }
 }
 

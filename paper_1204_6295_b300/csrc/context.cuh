@@ -37,8 +37,9 @@ struct Level {
   float* ab = nullptr;   // a [N] then b [N]
   float* dm = nullptr;   // I'_s - m of the masked correction
   int* stamp = nullptr;  // 0 known, p filled by pass p, -1 not filled
-  int* list = nullptr;   // two lists of unfilled voxels [2][N]
-  int* cnt = nullptr;    // [fill_passes + 1] list lengths
+  unsigned* kbits = nullptr;   // [2][fill_words] known-voxel bit masks of the fill passes
+  int* flist = nullptr;        // [N] a fill pass's front; then [fill_front_blocks + 1] block offsets, length
+  int* cnt = nullptr;    // [fill_passes + 1] masked voxels, voxels filled per pass
   BoxPlan pa{};
   BoxPlan pm{};          // kModeMaskAB
   GaussPlan pb{};

@@ -57,14 +57,13 @@ struct BoxArgs {
   int* err;             // device error word (bit 0: a bulk-copy wait timed out); NULL: the library's own
   float* sd_out;        // optional (kModeStatic): STD(S) per voxel
   // kModeMaskAB (Eqs. 5-7): is = I_s, sd = STD(S); out = d = I'_s - m.  Outputs a, b,
-  // stamp (0 where xi = 0, -1 where xi = 1) and the list of xi = 1 voxels (count[0]).
+  // stamp (0 where xi = 0, -1 where xi = 1) and the number of xi = 1 voxels (added to *count).
   // ratio_only: write only a = STD(M)/STD(S) (-1 where undefined) into a_out.
   const float* is;
   const float* sd;
   float* a_out;
   float* b_out;
   int* stamp;
-  int* list;
   int* count;
   float hu0, a_min, a_max;
   int ratio_only;
@@ -184,16 +183,26 @@ struct FillArgs {
   float* b;
   float* d;             // I'_s - m, written where a voxel is filled
   int* stamp;           // 0: xi = 0; p: filled by pass p; -1: not yet
-  const int* list_in;   // voxels still without a, b (cnt[pass - 1] of them)
-  int* list_out;        // those this pass leaves (cnt[pass] counts them)
-  int* cnt;             // [passes + 1], cnt[0] from the mask pass, the rest zero
+  const unsigned* kin;  // known before this pass: bit masks, fill_words() words
+  unsigned* kout;       // known after it (this pass writes it)
+  int nwx;              // words per row, (nx + 31) / 32
+  int* list;            // [N] the front of this pass, in voxel order
+  int* boff;            // [fill_front_blocks] front counts, then offsets, per block of mask words
+  int* nfront;          // [1] length of the list
+  int* cnt;             // [passes + 1]: cnt[0] masked voxels (from the mask pass), cnt[p] filled by pass p
+  int passes;           // passes of this fill
   int nx, ny, nz;
   int tx, ty, tz;       // half sizes of T
   float inv_h;          // 1 / h of Eq. 10
   int pass;             // 1, 2, ...
   const int* stop;
 };
-cudaError_t launch_fill_pass(const FillArgs& f, int max_items, cudaStream_t s);
+// One fill pass: the dilation of the known mask kin into kout, then the voxels
+// of kout not in kin.  Before pass 1, launch_fill_pack sets kin from the stamps.
+cudaError_t launch_fill_pass(const FillArgs& f, cudaStream_t s);
+int fill_words(int nx, int ny, int nz);
+int fill_front_blocks(int nx, int ny, int nz);
+cudaError_t launch_fill_pack(const int* stamp, unsigned* k, int nx, int ny, int nz, cudaStream_t s);
 struct ForceArgs {
   const float* d;       // I'_s - m
   const float* m;

@@ -1,14 +1,21 @@
 // The mask-and-fill completion of the intensity correction (sm_103a):
 // Eqs. (7)-(10), Sec. 2.3 and Algorithm A1 step 2.
 //
-//  k_fill_pass   one Jacobi pass of Eqs. (8)-(10) over the list of voxels still
-//                without a, b: each averages the a, b of the neighbours in the
-//                box T that were known before the pass (stamp in [0, pass)),
-//                weighted by exp(-(I_s(i) - I_s(x))^2 / h^2) with the exponent
-//                capped at 80 (reading R20); filled voxels get stamp = pass and
-//                d = a I_s + b - m, the others go to the next pass's list.
-//                A pass returns at once when no voxel is left or the previous
-//                pass filled nothing (reading R19).
+//  fill pass     one Jacobi pass of Eqs. (8)-(10) over the voxels without a, b:
+//                each averages the a, b of the neighbours in the box T that
+//                were known before the pass, weighted by
+//                exp(-(I_s(i) - I_s(x))^2 / h^2) with the exponent capped at 80
+//                (reading R20); a filled voxel gets stamp = pass and
+//                d = a I_s + b - m.  A voxel is filled in the first pass after
+//                one of its box neighbours is known, so the voxels a pass fills
+//                (its front) are the box dilation of the known set less that
+//                set.  Bit masks of the known voxels (k_fill_pack before pass 1)
+//                are dilated once per pass, the front is listed in voxel order
+//                (count, scan, list), and k_fill_pass sums each listed voxel's
+//                known neighbours, found from the mask bits: only the front is
+//                visited, with the sums a pass over every unknown voxel would
+//                form.  A pass returns at once when nothing is masked or the
+//                previous pass filled nothing (reading R19).
 //  k_force_dm    the demons force (Eq. 1) and update u = r + dr from d = I'_s - m
 //                and m, with the arithmetic of the force stage of the box pass.
 //  median        a_m of Sec. 2.3: lower and upper median of the non-negative
@@ -26,35 +33,166 @@ namespace {
 constexpr int kFillThreads = 128;
 constexpr int kForceThreads = 256;
 
+// Bit masks of the known voxels, one 32-bit word per 32 voxels of a row (bit i of
+// word w of row (y, z) is voxel x = 32 w + i; bits past nx stay zero).  The
+// voxels known before pass p + 1 are the box-T dilation of those known before
+// pass p: a voxel is filled in the first pass after a box neighbour is known
+// (every weight of Eq. 10 is at least exp(-80) > 0), so the masks follow from
+// the mask pass's stamps by dilations alone, and pass p tries exactly the
+// voxels it fills.
+
+// K_1: the voxels with xi = 0 (stamp 0).  One warp per word.
+__global__ void k_fill_pack(const int* __restrict__ stamp, unsigned* __restrict__ k, int nx, int nwx, long long words) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long w = t >> 5;
+  if (w >= words) return;                                  // whole warps leave together
+  const int lane = threadIdx.x & 31;
+  const long long row = w / nwx;
+  const int x = (int)(w - row * nwx) * 32 + lane;
+  const bool known = x < nx && stamp[row * nx + x] == 0;
+  const unsigned bits = __ballot_sync(0xffffffffu, known);
+  if (lane == 0) k[w] = bits;
+}
+
+// Dilation word i of K_{p+1}: K_p dilated by the box T, clipped to the volume.
+__device__ __forceinline__ unsigned dilate_word(const FillArgs& f, long long i, unsigned tail) {
+  const int nwx = f.nwx, ny = f.ny, nz = f.nz;
+  const int w = (int)(i % nwx);
+  const long long row = i / nwx;
+  const int y = (int)(row % ny), z = (int)(row / ny);
+  unsigned acc = 0u;
+  for (int zz = max(0, z - f.tz); zz <= min(nz - 1, z + f.tz); ++zz)
+    for (int yy = max(0, y - f.ty); yy <= min(ny - 1, y + f.ty); ++yy) {
+      const unsigned* r = f.kin + ((long long)zz * ny + yy) * nwx;
+      const unsigned c = r[w], l = w > 0 ? r[w - 1] : 0u, h = w + 1 < nwx ? r[w + 1] : 0u;
+      acc |= c;
+      for (int d = 1; d <= f.tx; ++d) acc |= (c << d) | (l >> (32 - d)) | (c >> d) | (h << (32 - d));
+    }
+  return w == nwx - 1 ? (acc & tail) : acc;
+}
+
+// The pass's front F_p = K_{p+1} minus K_p, listed in voxel order: (1) dilation
+// and front counts per block of kFrontWords words, (2) one CTA scans the block
+// counts, (3) each block lists its front voxels from its offset.
+constexpr int kFrontWords = 256;
+constexpr int kScanThreads = 1024;
+
+__device__ __forceinline__ bool pass_idle(const FillArgs& f) {
+  return (f.stop != nullptr && *(volatile const int*)f.stop != 0) || f.cnt[f.pass - 1] == 0;
+}
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int* red, int& total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int incl = v;
+  for (int off = 1; off < 32; off <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += t;
+  }
+  if (lane == 31) red[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    int s = lane < nw ? red[lane] : 0;
+    for (int off = 1; off < 32; off <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, s, off);
+      if (lane >= off) s += t;
+    }
+    if (lane < nw) red[lane] = s;                          // inclusive warp totals
+  }
+  __syncthreads();
+  total = red[nw - 1];
+  const int before = wid > 0 ? red[wid - 1] : 0;
+  __syncthreads();                                         // red is reused by the caller
+  return before + incl - v;
+}
+
+__global__ void __launch_bounds__(kFrontWords) k_fill_front_count(FillArgs f) {
+  if (pass_idle(f)) return;
+  __shared__ int red[32];
+  const long long words = (long long)f.nwx * f.ny * f.nz;
+  const long long i = (long long)blockIdx.x * kFrontWords + threadIdx.x;
+  const unsigned tail = (f.nx & 31) ? (1u << (f.nx & 31)) - 1u : 0xffffffffu;
+  int c = 0;
+  if (i < words) {
+    const unsigned k = dilate_word(f, i, tail);
+    f.kout[i] = k;
+    c = __popc(k & ~f.kin[i]);
+  }
+  int total = 0;
+  block_exclusive_scan(c, red, total);
+  if (threadIdx.x == 0) f.boff[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_fill_front_scan(FillArgs f, int nblocks) {
+  if (pass_idle(f)) return;
+  __shared__ int red[32];
+  int carry = 0;
+  for (int base = 0; base < nblocks; base += kScanThreads) {
+    const int j = base + threadIdx.x;
+    const int v = j < nblocks ? f.boff[j] : 0;
+    int total = 0;
+    const int ex = block_exclusive_scan(v, red, total);
+    if (j < nblocks) f.boff[j] = carry + ex;
+    carry += total;
+  }
+  if (threadIdx.x == 0) f.nfront[0] = carry;
+}
+
+__global__ void __launch_bounds__(kFrontWords) k_fill_front_list(FillArgs f) {
+  if (pass_idle(f)) return;
+  __shared__ int red[32];
+  const long long words = (long long)f.nwx * f.ny * f.nz;
+  const long long i = (long long)blockIdx.x * kFrontWords + threadIdx.x;
+  unsigned b = 0u;
+  if (i < words) b = f.kout[i] & ~f.kin[i];
+  int total = 0;
+  int pos = f.boff[blockIdx.x] + block_exclusive_scan(__popc(b), red, total);
+  if (b) {
+    const long long row = i / f.nwx;
+    const int x0 = (int)(i - row * f.nwx) * 32;
+    const long long g0 = row * f.nx + x0;
+    while (b) {
+      const int j = __ffs(b) - 1;
+      b &= b - 1u;
+      f.list[pos++] = (int)(g0 + j);
+    }
+  }
+}
+
+// Eqs. (8)-(10) for the listed front voxels, summing the neighbours known before
+// the pass (the set bits of K_p in the voxel's box, rows in z, y order and each
+// row in increasing x).
 __global__ void __launch_bounds__(kFillThreads) k_fill_pass(FillArgs f) {
-  if (f.stop != nullptr && *(volatile const int*)f.stop != 0) return;
-  const int n_in = f.cnt[f.pass - 1];
-  if (n_in == 0) return;
-  if (f.pass >= 2 && n_in == f.cnt[f.pass - 2]) return;   // the last pass filled nothing
-  const int nx = f.nx, ny = f.ny, nz = f.nz;
+  if (pass_idle(f)) return;
+  const int n = f.nfront[0];
+  const int nx = f.nx, ny = f.ny, nz = f.nz, nwx = f.nwx;
   const size_t plane = (size_t)nx * ny;
-  for (int i = blockIdx.x * kFillThreads + threadIdx.x; i < n_in; i += gridDim.x * kFillThreads) {
-    const int g = f.list_in[i];
+  int nfilled = 0;
+  for (int k = blockIdx.x * kFillThreads + threadIdx.x; k < n; k += gridDim.x * kFillThreads) {
+    const size_t g = (size_t)f.list[k];
     const int z = (int)(g / plane);
-    const int rem = g - (int)((size_t)z * plane);
+    const int rem = (int)(g - (size_t)z * plane);
     const int y = rem / nx, x = rem - y * nx;
     const float isx = __ldg(f.is + g);
     float num_a = 0.0f, num_b = 0.0f, den = 0.0f;
-    const int z_lo = max(0, z - f.tz), z_hi = min(nz - 1, z + f.tz);
-    const int y_lo = max(0, y - f.ty), y_hi = min(ny - 1, y + f.ty);
     const int x_lo = max(0, x - f.tx), x_hi = min(nx - 1, x + f.tx);
-    for (int zz = z_lo; zz <= z_hi; ++zz)
-      for (int yy = y_lo; yy <= y_hi; ++yy) {
-        const size_t row = (size_t)zz * plane + (size_t)yy * nx;
-        for (int xx = x_lo; xx <= x_hi; ++xx) {
-          const size_t gi = row + xx;
-          const int st = f.stamp[gi];
-          if (st < 0 || st >= f.pass) continue;           // known before this pass only
+    const int w0 = x_lo >> 5, w1 = x_hi >> 5, sh = x_lo & 31;
+    const unsigned long long span = (1ull << (x_hi - x_lo + 1)) - 1ull;
+    for (int zz = max(0, z - f.tz); zz <= min(nz - 1, z + f.tz); ++zz)
+      for (int yy = max(0, y - f.ty); yy <= min(ny - 1, y + f.ty); ++yy) {
+        const size_t rw = ((size_t)zz * ny + yy) * nwx;
+        unsigned long long bits = f.kin[rw + w0];
+        if (w1 != w0) bits |= (unsigned long long)f.kin[rw + w1] << 32;
+        bits = (bits >> sh) & span;
+        const size_t row = (size_t)zz * plane + (size_t)yy * nx + x_lo;
+        while (bits) {
+          const int j = __ffsll((long long)bits) - 1;
+          bits &= bits - 1ull;
+          const size_t gi = row + j;
           const float e = (__ldg(f.is + gi) - isx) * f.inv_h;
-          const float w = expf(-fminf(e * e, 80.0f));     // Eq. (10), exponent capped
-          num_a = fmaf(w, f.a[gi], num_a);
-          num_b = fmaf(w, f.b[gi], num_b);
-          den += w;
+          const float wt = expf(-fminf(e * e, 80.0f));    // Eq. (10), exponent capped
+          num_a = fmaf(wt, f.a[gi], num_a);
+          num_b = fmaf(wt, f.b[gi], num_b);
+          den += wt;
         }
       }
     if (den > 0.0f) {
@@ -63,10 +201,11 @@ __global__ void __launch_bounds__(kFillThreads) k_fill_pass(FillArgs f) {
       f.b[g] = bv;
       f.d[g] = fmaf(av, isx, bv) - __ldg(f.m + g);        // d = I'_s - m
       f.stamp[g] = f.pass;
-    } else {
-      f.list_out[atomicAdd(&f.cnt[f.pass], 1)] = g;
+      ++nfilled;
     }
   }
+  for (int off = 16; off > 0; off >>= 1) nfilled += __shfl_down_sync(0xffffffffu, nfilled, off);
+  if ((threadIdx.x & 31) == 0 && nfilled) atomicAdd(&f.cnt[f.pass], nfilled);
 }
 
 // One-sided differences at the faces as s * (v[+r] - v[-l]), l, r in {0, 1}.
@@ -205,14 +344,11 @@ __global__ void k_median_finish(const unsigned* work, double* out) {
   *out = n > 0 ? 0.5 * ((double)lo + (double)hi) : -1.0;
 }
 
-// Voxels the fill left: the count of the last pass that ran.
+// Voxels the fill left: the masked ones less those the passes filled.
 __global__ void k_fill_remaining(const int* cnt, int passes, int* out) {
-  int last = cnt[0];
-  for (int p = 1; p <= passes; ++p) {
-    if (last == 0 || (p >= 2 && cnt[p - 1] == cnt[p - 2])) break;   // this pass returned at once
-    last = cnt[p];
-  }
-  *out = last;
+  int left = cnt[0];
+  for (int p = 1; p <= passes; ++p) left -= cnt[p];
+  *out = left;
 }
 
 __global__ void k_add(const float* __restrict__ a, const float* __restrict__ b, float* out, int64_t n) {
@@ -240,11 +376,31 @@ cudaError_t launch_add(const float* a, const float* b, float* out, int64_t n, cu
   return cudaGetLastError();
 }
 
-cudaError_t launch_fill_pass(const FillArgs& f, int max_items, cudaStream_t s) {
-  int blocks = (max_items + kFillThreads - 1) / kFillThreads;
+int fill_words(int nx, int ny, int nz) { return ((nx + 31) / 32) * ny * nz; }
+
+cudaError_t launch_fill_pack(const int* stamp, unsigned* k, int nx, int ny, int nz, cudaStream_t s) {
+  const int nwx = (nx + 31) / 32;
+  const long long words = (long long)nwx * ny * nz;
+  const long long blocks = (words * 32 + 255) / 256;
+  if (blocks < 1 || blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  k_fill_pack<<<(int)blocks, 256, 0, s>>>(stamp, k, nx, nwx, words);
+  return cudaGetLastError();
+}
+
+int fill_front_blocks(int nx, int ny, int nz) {
+  return (fill_words(nx, ny, nz) + kFrontWords - 1) / kFrontWords;
+}
+
+cudaError_t launch_fill_pass(const FillArgs& f, cudaStream_t s) {
+  const int nb = fill_front_blocks(f.nx, f.ny, f.nz);
+  k_fill_front_count<<<nb, kFrontWords, 0, s>>>(f);
+  k_fill_front_scan<<<1, kScanThreads, 0, s>>>(f, nb);
+  k_fill_front_list<<<nb, kFrontWords, 0, s>>>(f);
+  const long long n = (long long)f.nx * f.ny * f.nz;
+  long long blocks = (n + kFillThreads - 1) / kFillThreads;
   if (blocks > 148 * 16) blocks = 148 * 16;
   if (blocks < 1) blocks = 1;
-  k_fill_pass<<<blocks, kFillThreads, 0, s>>>(f);
+  k_fill_pass<<<(int)blocks, kFillThreads, 0, s>>>(f);
   return cudaGetLastError();
 }
 
