@@ -155,6 +155,12 @@ disc_status disc_iterate(disc_ctx* ctx, int32_t max_iters, int32_t* iters_done,
  * through the remaining levels first. */
 disc_status disc_get_field(disc_ctx* ctx, float* out, int mem_kind);
 
+/* Copy the field r of pyramid level `level` (0 = finest) as the context holds
+ * it: [3][nz][ny][nx] of that level's grid, in that level's voxel units (the
+ * layout disc_set_field takes).  No up-sampling; host or device `out`.
+ * DISC_ERR_ARG for a level outside [0, levels). */
+disc_status disc_get_level_field(disc_ctx* ctx, int32_t level, float* out, int mem_kind);
+
 /* Copy the corrected CBCT I'_s (Sec. 2.2, last paragraph), computed from
  * the current field at the current level, [nz][ny][nx] of that level. */
 disc_status disc_get_corrected(disc_ctx* ctx, float* out, int mem_kind);

@@ -897,6 +897,21 @@ disc_status disc_get_metrics(disc_ctx* ctx, int32_t bins, float sigma, float t_l
   return DISC_OK;
 }
 
+disc_status disc_get_level_field(disc_ctx* ctx, int32_t level, float* out, int mem_kind) {
+  if (!ctx || !out) return DISC_ERR_ARG;
+  if (mem_kind != DISC_MEM_HOST && mem_kind != DISC_MEM_DEVICE) return DISC_ERR_ARG;
+  if (ctx->sticky != DISC_OK) return DISC_ERR_STATE;
+  if (!ctx->have_images) return DISC_ERR_STATE;
+  if (level < 0 || level >= ctx->L) return DISC_ERR_ARG;
+  DeviceGuard guard(ctx->device);
+  CK(enter(ctx));
+  const Level& v = ctx->lev[level];
+  CK(memcpy_kind(out, v.r, 3 * v.N * sizeof(float), mem_kind, DISC_MEM_DEVICE, ctx->s));
+  if (mem_kind == DISC_MEM_HOST) CK_DEV(ctx);
+  CK(leave(ctx));
+  return DISC_OK;
+}
+
 disc_status disc_set_field(disc_ctx* ctx, int32_t level, const float* r, int mem_kind) {
   if (!ctx || !r) return DISC_ERR_ARG;
   if (mem_kind != DISC_MEM_HOST && mem_kind != DISC_MEM_DEVICE) return DISC_ERR_ARG;

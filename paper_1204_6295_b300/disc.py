@@ -76,6 +76,7 @@ _SIGS = {
     "disc_get_field": (_st, [_vp, _vp, ctypes.c_int]),
     "disc_get_corrected": (_st, [_vp, _vp, ctypes.c_int]),
     "disc_set_field": (_st, [_vp, _i32, _vp, ctypes.c_int]),
+    "disc_get_level_field": (_st, [_vp, _i32, _vp, ctypes.c_int]),
     "disc_get_progress": (_st, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "disc_get_norm_history": (_st, [_vp, _i32, _vp, _i32, ctypes.POINTER(_i32)]),
     "disc_destroy": (_st, [_vp]),
@@ -287,6 +288,11 @@ class Registration:
             out = np.empty((nz, ny, nx), np.float32)
         _f32_check(out, (nz, ny, nx), "out")
         _check(_lib.disc_get_corrected(self._h, _ptr(out), _mem_kind(out)), "disc_get_corrected")
+        return out
+
+    def get_level_field(self, level, out):
+        """Level `level`'s own field ([3][nz][ny][nx] of that level, its voxel units) into `out`."""
+        _check(_lib.disc_get_level_field(self._h, int(level), _ptr(out), _mem_kind(out)), "disc_get_level_field")
         return out
 
     def set_field(self, level, r):

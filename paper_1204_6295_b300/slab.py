@@ -25,9 +25,16 @@ the volume's own faces the buffer ends where the volume does, so the
 truncations are the whole volume's.  The global intensity shift and the
 fixed-point scales are taken from the whole volume (``quant_max``), which
 makes every interior voxel of every slab bit-identical to the whole-volume
-run.  Scope: one pyramid level, fixed iteration counts (the convergence
-norm's sums are per slab) and the mask off (its median a_m is a whole-volume
-statistic).
+run.
+
+Pyramid levels: level l halves the grid l times (2 x 2 x 2 means), so slab
+cuts and buffer starts sit on multiples of 2^(L-1) planes and a slab's coarse
+planes are the whole volume's; the halo must cover the reach at every level,
+2^l (R + p_z + ceil(d / 2^l) + 3) fine planes at level l.  At a level's end
+every slab up-samples its own buffer (the fine planes of its interior read
+coarse planes at most one away) and the fine level starts with an exchange.
+Scope: fixed iteration counts (the convergence norm's sums are per slab) and
+the mask off (its median a_m is a whole-volume statistic).
 """
 from __future__ import annotations
 
@@ -36,28 +43,46 @@ import math
 from . import disc
 
 
-def halo_planes(patch, sigma, radius=0, max_disp_z=8.0):
-    """Halo depth (planes per side) that keeps a slab's interior exact while
-    |r_z| <= max_disp_z voxels (see the module docstring)."""
+def halo_planes(patch, sigma, radius=0, max_disp_z=8.0, levels=1):
+    """Halo depth (fine planes per side, a multiple of 2^(levels-1)) that keeps
+    a slab's interior exact at every level while |r_z| <= max_disp_z fine
+    voxels (see the module docstring)."""
     R = int(radius) if radius > 0 else int(math.ceil(3.0 * float(sigma)))
     pz = (int(patch[2]) - 1) // 2
-    return R + pz + int(math.ceil(float(max_disp_z))) + 3
+    h = max((1 << l) * (R + pz + int(math.ceil(float(max_disp_z) / (1 << l))) + 3) for l in range(levels))
+    align = 1 << (levels - 1)
+    return (h + align - 1) // align * align
 
 
-def slab_plan(nz, nslabs, halo):
+def slab_plan(nz, nslabs, halo, align=1):
     """[(z0, z1, b0, b1)]: interior planes [z0, z1) and buffer planes [b0, b1)
-    of each slab; interiors tile [0, nz) in order, as equal as possible."""
-    if nslabs < 1 or nz < nslabs:
-        raise ValueError("need 1 <= nslabs <= nz")
+    of each slab; interiors tile [0, nz) in order, as equal as possible in
+    units of `align` planes, and every cut and buffer start is a multiple of
+    `align` (halo must be one)."""
+    if align < 1 or halo % align:
+        raise ValueError("align >= 1 and halo a multiple of it")
+    units = (nz + align - 1) // align
+    if nslabs < 1 or units < nslabs:
+        raise ValueError("need 1 <= nslabs <= ceil(nz / align)")
     if halo < 0:
         raise ValueError("halo must be >= 0")
-    base, extra = divmod(nz, nslabs)
-    plan, z0 = [], 0
+    base, extra = divmod(units, nslabs)
+    plan, u0 = [], 0
     for s in range(nslabs):
-        z1 = z0 + base + (1 if s < extra else 0)
+        u1 = u0 + base + (1 if s < extra else 0)
+        z0, z1 = u0 * align, min(nz, u1 * align)
         plan.append((z0, z1, max(0, z0 - halo), min(nz, z1 + halo)))
-        z0 = z1
+        u0 = u1
     return plan
+
+
+def level_plan(plan, nz, level):
+    """The plan in the planes of pyramid level `level` (cuts halved `level` times)."""
+    def down(z):
+        for _ in range(level):
+            z = (z + 1) // 2
+        return z
+    return [(down(z0), down(z1), down(b0), down(b1)) for z0, z1, b0, b1 in plan]
 
 
 def exchange_sources(plan, s):
@@ -73,27 +98,32 @@ def exchange_sources(plan, s):
 
 
 class SlabRegistration:
-    """One volume registered as ``nslabs`` z slabs (one level, fixed counts).
+    """One volume registered as ``nslabs`` z slabs (fixed counts, mask off).
 
-    ``max_disp_z`` bounds |r_z| (voxels) over the run; ``halo`` overrides the
-    depth derived from it.  Images are float32 [nz][ny][nx] torch CUDA tensors.
+    ``levels`` and ``iters`` (coarsest first) give the schedule, as for
+    Registration; ``max_disp_z`` bounds |r_z| (fine voxels) over the run and
+    ``halo`` overrides the depth derived from it.  Images are float32
+    [nz][ny][nx] torch CUDA tensors.
     """
 
-    def __init__(self, nslabs=2, max_disp_z=8.0, halo=None, **kw):
+    def __init__(self, nslabs=2, max_disp_z=8.0, halo=None, levels=1, iters=(50,), **kw):
         import torch
         self._torch = torch
         kw = dict(kw)
-        if kw.get("levels", 1) != 1:
-            raise ValueError("the slab decomposition runs one pyramid level")
         if kw.get("mask_mode", 0) or kw.get("stop_eps", 0.0) > 0.0:
             raise ValueError("the slab decomposition runs with the mask off and fixed counts")
-        kw["levels"] = 1
-        kw["iters"] = (1 << 30,)                 # counts are driven here
+        if len(iters) != levels:
+            raise ValueError("one iteration count per level (coarsest first)")
+        self.levels = int(levels)
+        self.iters = [int(n) for n in iters]
+        kw["levels"] = self.levels
+        kw["iters"] = (1 << 30,) * self.levels   # no level completes inside a context: counts are driven here
         self.shift = bool(kw.pop("global_shift", True))
         self.kw = kw
         self.nslabs = int(nslabs)
-        self.halo = int(halo) if halo is not None else halo_planes(kw.get("patch", (3, 3, 3)), kw.get("sigma", 1.0),
-                                                                    kw.get("radius", 0), max_disp_z)
+        self.align = 1 << (self.levels - 1)
+        self.halo = int(halo) if halo is not None else halo_planes(
+            kw.get("patch", (3, 3, 3)), kw.get("sigma", 1.0), kw.get("radius", 0), max_disp_z, self.levels)
         self.regs = []
         self.plan = None
         self.dims = None
@@ -121,7 +151,7 @@ class SlabRegistration:
         disc.k_max_abs(is_shift, mx[1:2])
         qmax = [float(v) for v in mx.cpu()]
         self.close()
-        self.plan = slab_plan(nz, self.nslabs, self.halo)
+        self.plan = slab_plan(nz, self.nslabs, self.halo, self.align)
         for (_, _, b0, b1) in self.plan:
             p = disc.make_params(global_shift=False, quant_max=qmax, **self.kw)
             reg = disc.Registration(p)
@@ -129,39 +159,60 @@ class SlabRegistration:
             self.regs.append(reg)
         self.dims = (nx, ny, nz)
 
-    def _fields(self):
-        torch = self._torch
+    def _level_dims(self, level):
         nx, ny, _ = self.dims
+        for _ in range(level):
+            nx, ny = (nx + 1) // 2, (ny + 1) // 2
+        return nx, ny
+
+    def _fields(self, level):
+        """Each slab's field at `level`."""
+        torch = self._torch
+        nx, ny = self._level_dims(level)
         out = []
-        for reg, (_, _, b0, b1) in zip(self.regs, self.plan):
+        for reg, (_, _, b0, b1) in zip(self.regs, level_plan(self.plan, self.dims[2], level)):
             f = torch.empty((3, b1 - b0, ny, nx), dtype=torch.float32, device="cuda")
-            reg.get_field(f)
+            reg.get_level_field(level, f)
             out.append(f)
         return out
 
-    def exchange(self):
-        """Refill every slab's buffer field from the owners of its planes."""
+    def exchange(self, level, fields=None):
+        """Refill every slab's buffer field at `level` from the owners of its
+        planes (fields: the slabs' fields at that level, else read back)."""
         torch = self._torch
-        fields = self._fields()
+        if fields is None:
+            fields = self._fields(level)
+        plan = level_plan(self.plan, self.dims[2], level)
         for s, reg in enumerate(self.regs):
-            _, _, b0, b1 = self.plan[s]
+            _, _, b0, b1 = plan[s]
             buf = torch.empty_like(fields[s])
-            for t, lo, hi in exchange_sources(self.plan, s):
-                tb0 = self.plan[t][2]
+            for t, lo, hi in exchange_sources(plan, s):
+                tb0 = plan[t][2]
                 buf[:, lo - b0:hi - b0] = fields[t][:, lo - tb0:hi - tb0]
-            reg.set_field(0, buf)
+            reg.set_field(level, buf)
 
-    def iterate(self, n):
-        for _ in range(int(n)):
-            for reg in self.regs:
-                reg.iterate(1, sync=False)
-            self.exchange()
+    def iterate(self):
+        """The whole schedule, coarsest level first."""
+        torch = self._torch
+        for level in range(self.levels - 1, -1, -1):
+            for _ in range(self.iters[self.levels - 1 - level]):
+                for reg in self.regs:
+                    reg.iterate(1, sync=False)
+                self.exchange(level)
+            if level > 0:                        # Algorithm A1: up-sample to the next finer level
+                nx, ny = self._level_dims(level - 1)
+                fine = []
+                for f, (_, _, b0, b1) in zip(self._fields(level), level_plan(self.plan, self.dims[2], level - 1)):
+                    rf = torch.empty((3, b1 - b0, ny, nx), dtype=torch.float32, device="cuda")
+                    disc.k_upsample_field2(f, rf)
+                    fine.append(rf)
+                self.exchange(level - 1, fine)
 
     def get_field(self):
-        """The assembled field [3][nz][ny][nx] (device tensor): each slab's interior."""
+        """The assembled finest-level field [3][nz][ny][nx] (device tensor): each slab's interior."""
         torch = self._torch
         nx, ny, nz = self.dims
         out = torch.empty((3, nz, ny, nx), dtype=torch.float32, device="cuda")
-        for f, (z0, z1, b0, _) in zip(self._fields(), self.plan):
+        for f, (z0, z1, b0, _) in zip(self._fields(0), self.plan):
             out[:, z0:z1] = f[:, z0 - b0:z1 - b0]
         return out

@@ -1,8 +1,10 @@
 """Z-slab decomposition on the GPU: a volume registered as 2 or 3 slab contexts
 with halo exchanges of r after every iteration gives the whole-volume
 context's field bit for bit (same kernels, same fixed-point scales through
-quant_max, same global shift); a halo one plane short of an iteration's reach
-does not.  quant_max below an image's own maximum is rejected.
+quant_max, same global shift), on one pyramid level and on two (slab cuts on
+even planes, each slab up-sampling its own buffer at the level's end); a halo
+one plane short of an iteration's reach does not.  quant_max below an image's
+own maximum is rejected; disc_get_level_field returns a level's own field.
 """
 import numpy as np
 import pytest
@@ -26,8 +28,8 @@ def pair():
 ITERS = 8
 
 
-def _whole(disc, pair, **kw):
-    with disc.Registration(levels=1, iters=(ITERS,), **kw) as reg:
+def _whole(disc, pair, levels=1, iters=(ITERS,), **kw):
+    with disc.Registration(levels=levels, iters=iters, **kw) as reg:
         reg.set_images(pair.ct, pair.cbct)
         reg.iterate(-1)
         return reg.get_field()
@@ -44,12 +46,42 @@ def test_slabs_equal_whole_volume(disc, pair, nslabs, kw):
     whole = _whole(disc, pair, **kw)
     assert np.abs(whole[2]).max() < 6.0
     ct, cbct = torch.from_numpy(pair.ct).cuda(), torch.from_numpy(pair.cbct).cuda()
-    with SlabRegistration(nslabs, max_disp_z=6.0, **kw) as sr:
+    with SlabRegistration(nslabs, max_disp_z=6.0, iters=(ITERS,), **kw) as sr:
         sr.set_images(ct, cbct)
         assert all(b1 - b0 < 64 for _, _, b0, b1 in sr.plan)    # every slab is a proper part
-        sr.iterate(ITERS)
+        sr.iterate()
         got = sr.get_field().cpu().numpy()
     np.testing.assert_array_equal(got, whole)
+
+
+@pytest.mark.parametrize("kw", [dict(patch=(5, 5, 5), sigma=1.0), dict(patch=(3, 3, 3), sigma=1.0, force_mode=1)])
+def test_two_level_slabs_equal_whole_volume(disc, pair, kw):
+    import torch
+    from paper_1204_6295_b300.slab import SlabRegistration
+    iters = (5, 4)
+    whole = _whole(disc, pair, levels=2, iters=iters, **kw)
+    ct, cbct = torch.from_numpy(pair.ct).cuda(), torch.from_numpy(pair.cbct).cuda()
+    with SlabRegistration(2, max_disp_z=6.0, levels=2, iters=iters, **kw) as sr:
+        sr.set_images(ct, cbct)
+        assert all(b1 - b0 < 64 and b0 % 2 == 0 for _, _, b0, b1 in sr.plan)
+        sr.iterate()
+        got = sr.get_field().cpu().numpy()
+    np.testing.assert_array_equal(got, whole)
+
+
+def test_level_field(disc, pair):
+    import torch
+    with disc.Registration(levels=2, iters=(3, 2), patch=(3, 3, 3)) as reg:
+        reg.set_images(pair.ct, pair.cbct)
+        reg.iterate(3)                                   # the coarse level, then up-sampled to the fine one
+        fine = reg.get_level_field(0, torch.empty((3, 64, 40, 48), device="cuda"))
+        np.testing.assert_array_equal(fine.cpu().numpy(), reg.get_field())
+        coarse = reg.get_level_field(1, np.empty((3, 32, 20, 24), np.float32))
+        up = torch.empty((3, 64, 40, 48), device="cuda")
+        disc.k_upsample_field2(torch.from_numpy(coarse).cuda(), up)
+        np.testing.assert_array_equal(up.cpu().numpy(), fine.cpu().numpy())
+        with pytest.raises(disc.DiscError):
+            reg.get_level_field(2, np.empty((3, 16, 10, 12), np.float32))
 
 
 def test_short_halo_differs(disc, pair):
@@ -58,9 +90,9 @@ def test_short_halo_differs(disc, pair):
     kw = dict(patch=(5, 5, 5), sigma=1.0)
     whole = _whole(disc, pair, **kw)
     ct, cbct = torch.from_numpy(pair.ct).cuda(), torch.from_numpy(pair.cbct).cuda()
-    with SlabRegistration(2, halo=3 + 1 + 2 - 1, **kw) as sr:
+    with SlabRegistration(2, halo=3 + 1 + 2 - 1, iters=(ITERS,), **kw) as sr:
         sr.set_images(ct, cbct)
-        sr.iterate(ITERS)
+        sr.iterate()
         got = sr.get_field().cpu().numpy()
     assert np.abs(got - whole).max() > 1e-4
 

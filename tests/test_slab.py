@@ -12,7 +12,7 @@ import pytest
 
 from oracle import disc_oracle as O
 from paper_1204_6295_b300 import phantom
-from paper_1204_6295_b300.slab import exchange_sources, halo_planes, slab_plan
+from paper_1204_6295_b300.slab import exchange_sources, halo_planes, level_plan, slab_plan
 
 
 @pytest.mark.parametrize("nz,ns,h", [(10, 1, 3), (10, 2, 3), (11, 3, 0), (64, 4, 14), (5, 5, 9), (7, 2, 100)])
@@ -33,6 +33,25 @@ def test_slab_plan_tiles_and_clips(nz, ns, h):
             assert plan[t][0] <= lo < hi <= plan[t][1]      # from the owner's interior
 
 
+@pytest.mark.parametrize("nz,ns,h,align", [(64, 2, 22, 2), (63, 3, 8, 4), (100, 4, 16, 8), (9, 2, 4, 4)])
+def test_slab_plan_aligned(nz, ns, h, align):
+    plan = slab_plan(nz, ns, h, align)
+    assert plan[0][0] == 0 and plan[-1][1] == nz
+    for z0, z1, b0, b1 in plan:
+        assert z0 % align == 0 and b0 % align == 0 and (z1 % align == 0 or z1 == nz)
+        assert b0 == max(0, z0 - h) and b1 == min(nz, z1 + h)
+    # at level l the cuts are the whole volume's level-l planes: halved with rounding up
+    for level in range(1, align.bit_length()):
+        lp = level_plan(plan, nz, level)
+        nzl = nz
+        for _ in range(level):
+            nzl = (nzl + 1) // 2
+        assert lp[0][0] == 0 and lp[-1][1] == nzl
+        for (z0, z1, b0, b1), (c0, c1, d0, d1) in zip(plan, lp):
+            assert c0 * (1 << level) == z0 and d0 * (1 << level) == b0
+            assert d1 == (nzl if b1 == nz else b1 >> level)
+
+
 def test_slab_plan_rejects():
     with pytest.raises(ValueError):
         slab_plan(3, 4, 1)
@@ -40,12 +59,19 @@ def test_slab_plan_rejects():
         slab_plan(8, 0, 1)
     with pytest.raises(ValueError):
         slab_plan(8, 2, -1)
+    with pytest.raises(ValueError):
+        slab_plan(16, 2, 3, 2)                              # halo not a multiple of the alignment
+    with pytest.raises(ValueError):
+        slab_plan(8, 3, 4, 4)                               # fewer alignment units than slabs
 
 
 def test_halo_planes():
     assert halo_planes((5, 5, 5), 1.0, 0, 6.0) == 3 + 2 + 6 + 3
     assert halo_planes((11, 11, 11), 1.5, 0, 4.0) == 5 + 5 + 4 + 3
     assert halo_planes((3, 3, 7), 2.0, 2, 0.5) == 2 + 3 + 1 + 3
+    # two levels: the coarse reach counts twice in fine planes, rounded up to even
+    assert halo_planes((5, 5, 5), 1.0, 0, 6.0, 2) == max(14, 2 * (3 + 2 + 3 + 3))
+    assert halo_planes((3, 3, 3), 1.0, 0, 5.0, 3) == 4 * (3 + 1 + 2 + 3)
 
 
 def _slab_run(I_m, I_s, r0, p, plan, iters):
