@@ -107,12 +107,18 @@ typedef struct {
    * volume bit for bit.  A bound below the images' own maximum is rejected
    * by disc_set_images (DISC_ERR_ARG): the sums could overflow. */
   float quant_max[2];
+  /* Finest-level z planes [lo, hi) whose voxels enter the sums of l^(k)
+   * (Sec. 2.3), halved (rounding up) at each coarser level; 0 0 = every
+   * plane.  A z slab of a larger volume counts its interior only, so that the
+   * slabs' sums add up to the whole volume's (disc_get_norm_sums). */
+  int32_t norm_planes[2];
 } disc_params;
 
 /* Fill *p with defaults: patch 3x3x3, sigma 1, radius 0, 2 levels of 50
  * iterations, stop_eps 0 (fixed counts), window 10, THIRION, global shift on,
  * var_floor 1e-6, mask off (hu0_factor 2, a_lo 0.5, a_hi 1.5, fill_h 50,
- * fill_t 7x7x3, fill_passes 32), smooth_mode 0, quant_max 0 0.  Returns
+ * fill_t 7x7x3, fill_passes 32), smooth_mode 0, quant_max 0 0, norm_planes
+ * 0 0.  Returns
  * DISC_ERR_ARG for NULL. */
 disc_status disc_params_default(disc_params* p);
 
@@ -180,6 +186,12 @@ disc_status disc_get_progress(disc_ctx* ctx, int32_t* level, int32_t* iter,
  * run there) into host memory; *count receives the number written. */
 disc_status disc_get_norm_history(disc_ctx* ctx, int32_t level, float* out,
                                   int32_t cap, int32_t* count);
+
+/* The two sums behind each l^(k) of `level`, sum_x |dr(x)| and sum_x |r(x)|
+ * over the planes of norm_planes, as doubles: out[2k], out[2k + 1] for each
+ * iteration k run there (up to `cap` iterations), *count receives the number
+ * of iterations written.  Host memory. */
+disc_status disc_get_norm_sums(disc_ctx* ctx, int32_t level, double* out, int32_t cap, int32_t* count);
 
 /* The mask thresholds fixed by disc_set_images (mask_mode 1): HU0 and a_m
  * (a_min = a_lo a_m, a_max = a_hi a_m).  DISC_ERR_STATE before images or

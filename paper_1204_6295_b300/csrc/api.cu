@@ -113,6 +113,7 @@ disc_status check_params(const disc_params* p) {
   if (p->smooth_mode != 0 && p->smooth_mode != 1) return DISC_ERR_ARG;
   for (int i = 0; i < 2; ++i)
     if (!(p->quant_max[i] >= 0.0f) || !std::isfinite(p->quant_max[i])) return DISC_ERR_ARG;
+  if (p->norm_planes[0] < 0 || p->norm_planes[1] < 0) return DISC_ERR_ARG;
   if (p->mask_mode) {
     if (!(p->hu0_factor >= 0.0f) || !(p->a_lo >= 0.0f) || !(p->a_hi >= p->a_lo) || !(p->fill_h > 0.0f) ||
         !std::isfinite(p->hu0_factor) || !std::isfinite(p->a_hi) || !std::isfinite(p->fill_h))
@@ -137,6 +138,7 @@ void free_levels(disc_ctx* c) {
     cudaFree(v.u);
     cudaFree(v.t);
     cudaFree(v.hist);
+    cudaFree(v.hsum);
     cudaFree(v.sd);
     cudaFree(v.ab);
     cudaFree(v.dm);
@@ -189,6 +191,8 @@ BoxArgs box_args(const disc_ctx* c, const Level& v) {
   a.hz = c->hz;
   a.var_floor = c->p.var_floor;
   a.force_mode = c->p.force_mode;
+  a.norm_lo = v.norm_lo;
+  a.norm_hi = v.norm_hi;
   return a;
 }
 
@@ -257,6 +261,8 @@ cudaError_t queue_masked(disc_ctx* c, int l, int n, const GaussArgs& g, const No
   fa.r = v.r;
   fa.u = v.u;
   fa.partials = c->partials;
+  fa.norm_lo = v.norm_lo;
+  fa.norm_hi = v.norm_hi;
   fa.stop = c->d_stop + l;
   fa.nx = v.nx;
   fa.ny = v.ny;
@@ -307,7 +313,7 @@ cudaError_t queue_iterations(disc_ctx* c, int l, int n, const LoopCond* loop) {
   g.nz = v.nz;
   g.R = c->R;
   std::memcpy(g.w, c->w, sizeof(c->w));
-  NormState st{v.hist, c->d_iter + l, c->d_stop + l, v.hist_cap, c->p.stop_window, c->p.stop_eps};
+  NormState st{v.hist, v.hsum, c->d_iter + l, c->d_stop + l, v.hist_cap, c->p.stop_window, c->p.stop_eps};
   if (loop) {
     st.budget = loop->budget;
     st.cond = loop->cond;
@@ -455,7 +461,7 @@ GaussArgs ctx_gauss_args(const disc_ctx* c, int l) {
 
 NormState ctx_norm_state(const disc_ctx* c, int l) {
   const Level& v = c->lev[l];
-  return NormState{v.hist, c->d_iter + l, c->d_stop + l, v.hist_cap, c->p.stop_window, c->p.stop_eps};
+  return NormState{v.hist, v.hsum, c->d_iter + l, c->d_stop + l, v.hist_cap, c->p.stop_window, c->p.stop_eps};
 }
 
 }  // namespace disc
@@ -608,6 +614,13 @@ disc_status disc_set_images(disc_ctx* ctx, const float* ct, const float* cbct, i
       const int np = (int)(v.pa.grid.x * v.pa.grid.y * v.pa.grid.z);
       if (np > max_parts) max_parts = np;
       v.hist_cap = ctx->p.iters[L - 1 - l] > 0 ? ctx->p.iters[L - 1 - l] : 1;
+      int lo = ctx->p.norm_planes[0], hi = ctx->p.norm_planes[1];
+      for (int k = 0; k < l; ++k) {
+        lo = (lo + 1) / 2;
+        hi = (hi + 1) / 2;
+      }
+      v.norm_lo = lo;
+      v.norm_hi = hi;
       cudaError_t e = cudaMalloc(&v.Im, v.N * sizeof(float));
       if (e == cudaSuccess) e = cudaMalloc(&v.Is, v.N * sizeof(float));
       if (e == cudaSuccess) e = cudaMalloc(&v.zs, v.N * sizeof(float));
@@ -616,6 +629,7 @@ disc_status disc_set_images(disc_ctx* ctx, const float* ct, const float* cbct, i
       if (e == cudaSuccess) e = cudaMalloc(&v.u, 3 * v.N * sizeof(float));
       if (e == cudaSuccess) e = cudaMalloc(&v.t, 3 * v.N * sizeof(float));
       if (e == cudaSuccess) e = cudaMalloc(&v.hist, v.hist_cap * sizeof(float));
+      if (e == cudaSuccess) e = cudaMalloc(&v.hsum, 2 * (size_t)v.hist_cap * sizeof(double));
       if (e == cudaSuccess && ctx->p.mask_mode) {
         v.pm = box_plan(kModeMaskAB, v.nx, v.ny, v.nz, ctx->hx, ctx->hy, ctx->hz, ctx->num_sms);
         if (v.pm.grid.x == 0) e = cudaErrorInvalidConfiguration;
@@ -957,6 +971,23 @@ disc_status disc_get_norm_history(disc_ctx* ctx, int32_t level, float* out, int3
   int n = k < v.hist_cap ? k : v.hist_cap;
   if (n > cap) n = cap;
   if (n > 0) CK(cudaMemcpy(out, v.hist, n * sizeof(float), cudaMemcpyDeviceToHost));
+  *count = n;
+  return DISC_OK;
+}
+
+disc_status disc_get_norm_sums(disc_ctx* ctx, int32_t level, double* out, int32_t cap, int32_t* count) {
+  if (!ctx || !out || !count || cap < 0) return DISC_ERR_ARG;
+  if (ctx->sticky != DISC_OK) return DISC_ERR_STATE;
+  if (!ctx->have_images) return DISC_ERR_STATE;
+  if (level < 0 || level >= ctx->L) return DISC_ERR_ARG;
+  DeviceGuard guard(ctx->device);
+  int k = 0;
+  CK(cudaMemcpyAsync(&k, ctx->d_iter + level, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+  CK(cudaStreamSynchronize(ctx->s));
+  const Level& v = ctx->lev[level];
+  int n = k < v.hist_cap ? k : v.hist_cap;
+  if (n > cap) n = cap;
+  if (n > 0) CK(cudaMemcpy(out, v.hsum, 2 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost));
   *count = n;
   return DISC_OK;
 }

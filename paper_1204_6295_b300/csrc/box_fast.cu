@@ -341,8 +341,9 @@ __device__ __forceinline__ void box_body(const BoxArgs& a, int bx, int by, int b
         a.out[g] = fmaf(keep, rx, drx);
         a.out[(size_t)N + g] = fmaf(keep, ry, dry);
         a.out[2 * (size_t)N + g] = fmaf(keep, rz, drz);
-        acc0 += sqrt_approx(fmaf(drx, drx, fmaf(dry, dry, drz * drz)));
-        acc1 += sqrt_approx(fmaf(rx, rx, fmaf(ry, ry, rz * rz)));
+        const bool nin = a.norm_hi <= a.norm_lo || (zo >= a.norm_lo && zo < a.norm_hi);   // the plane enters the norm sums
+        acc0 += nin ? sqrt_approx(fmaf(drx, drx, fmaf(dry, dry, drz * drz))) : 0.0f;
+        acc1 += nin ? sqrt_approx(fmaf(rx, rx, fmaf(ry, ry, rz * rz))) : 0.0f;
       }
     }
     }

@@ -304,8 +304,9 @@ __global__ void __launch_bounds__(kThreads) k_box_pass(BoxArgs a) {
         a.out[g] = fmaf(keep, rx, drx);
         a.out[N + g] = fmaf(keep, ry, dry);
         a.out[2 * N + g] = fmaf(keep, rz, drz);
-        acc0 += sqrtf(fmaf(drx, drx, fmaf(dry, dry, drz * drz)));
-        acc1 += sqrtf(fmaf(rx, rx, fmaf(ry, ry, rz * rz)));
+        const bool nin = a.norm_hi <= a.norm_lo || (zo >= a.norm_lo && zo < a.norm_hi);   // the plane enters the norm sums
+        acc0 += nin ? sqrtf(fmaf(drx, drx, fmaf(dry, dry, drz * drz))) : 0.0f;
+        acc1 += nin ? sqrtf(fmaf(rx, rx, fmaf(ry, ry, rz * rz))) : 0.0f;
       }
     }
     // the next plane's stage 1 and 2a do not touch the d ring; stage 2b's write

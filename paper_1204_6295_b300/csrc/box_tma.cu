@@ -429,6 +429,7 @@ __device__ __forceinline__ bool box_tma_body(const BoxArgs& a, int bx, int by, i
       const float* mzm = mring + ((unsigned)(zlo ? zo - 1 : zo) % B::NMS) * B::MS;
       const float* mzp = mring + ((unsigned)(zhi ? zo + 1 : zo) % B::NMS) * B::MS;
       float* out0 = a.out + (size_t)zo * plane;
+      const bool nin = a.norm_hi <= a.norm_lo || (zo >= a.norm_lo && zo < a.norm_hi);   // the plane enters the norm sums
 #pragma unroll
       for (int i = 0; i < B::KO; ++i) {
         const int fi = fo3[i];
@@ -459,8 +460,8 @@ __device__ __forceinline__ bool box_tma_body(const BoxArgs& a, int bx, int by, i
         po[0] = fmaf(keep, rx, drx);
         po[(size_t)N] = fmaf(keep, ry, dry);
         po[2 * (size_t)N] = fmaf(keep, rz, drz);
-        acc0 += sqrt_approx(fmaf(drx, drx, fmaf(dry, dry, drz * drz)));
-        acc1 += sqrt_approx(fmaf(rx, rx, fmaf(ry, ry, rz * rz)));
+        acc0 += nin ? sqrt_approx(fmaf(drx, drx, fmaf(dry, dry, drz * drz))) : 0.0f;
+        acc1 += nin ? sqrt_approx(fmaf(rx, rx, fmaf(ry, ry, rz * rz))) : 0.0f;
       }
     }
     // the next step's stage 1 rewrites the z sums, group B the zs and r slots,

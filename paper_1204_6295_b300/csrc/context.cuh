@@ -31,7 +31,9 @@ struct Level {
   float* u = nullptr;    // r + dr [3][N]
   float* t = nullptr;    // xy-filtered field [3][N] (Gaussian scratch)
   float* hist = nullptr; // l^(k) history
+  double* hsum = nullptr;   // [hist_cap][2] sum |dr|, sum |r| behind each l^(k)
   int hist_cap = 0;
+  int norm_lo = 0, norm_hi = 0;   // planes entering those sums (all when norm_hi <= norm_lo)
   // mask and fill (mask_mode 1)
   float* sd = nullptr;   // STD(S)
   float* ab = nullptr;   // a [N] then b [N]

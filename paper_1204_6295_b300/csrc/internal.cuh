@@ -48,6 +48,8 @@ struct BoxArgs {
                         // kModeSsdAdjoint: [4][N] (A, B, C, D)
   float* f_tap;         // optional (kModeIterate): I'_s - m
   float* partials;      // per-CTA float[2] (kModeIterate: sum|dr|, sum|r|; kModeSsdLoss: loss)
+  int norm_lo, norm_hi; // kModeIterate: only planes [norm_lo, norm_hi) enter sum|dr|, sum|r|
+                        // (all planes when norm_hi <= norm_lo, as zero-initialised)
   const int* stop;      // device flag: when non-zero the kernel returns at once
   int nx, ny, nz;
   int hx, hy, hz;       // patch half sizes
@@ -209,6 +211,7 @@ struct ForceArgs {
   const float* r;
   float* u;             // r + dr
   float* partials;      // per CTA: sum |dr|, sum |r|
+  int norm_lo, norm_hi; // only planes [norm_lo, norm_hi) enter those sums (all if norm_hi <= norm_lo)
   const int* stop;
   int nx, ny, nz;
   int force_mode;
@@ -251,6 +254,7 @@ cudaError_t launch_up2(const float* rc, float* rf, int nx, int ny, int nz, cudaS
 // Reduce per-CTA partial norms to l^(k), append to the level history, update the stop flag.
 struct NormState {
   float* hist;          // [cap] l values of the current level
+  double* sums;         // [cap][2] sum |dr|, sum |r| behind each l
   int* iter;            // iterations run at the current level
   int* stop;            // stop flag
   int cap;

@@ -256,8 +256,9 @@ __global__ void __launch_bounds__(kForceThreads) k_force_dm(ForceArgs f) {
     f.u[g] = fmaf(keep, rxv, drx);
     f.u[(size_t)N + g] = fmaf(keep, ryv, dry);
     f.u[2 * (size_t)N + g] = fmaf(keep, rzv, drz);
-    acc0 += sqrt_approx(fmaf(drx, drx, fmaf(dry, dry, drz * drz)));
-    acc1 += sqrt_approx(fmaf(rxv, rxv, fmaf(ryv, ryv, rzv * rzv)));
+    const bool nin = f.norm_hi <= f.norm_lo || (z >= f.norm_lo && z < f.norm_hi);   // the plane enters the norm sums
+    acc0 += nin ? sqrt_approx(fmaf(drx, drx, fmaf(dry, dry, drz * drz))) : 0.0f;
+    acc1 += nin ? sqrt_approx(fmaf(rxv, rxv, fmaf(ryv, ryv, rzv * rzv))) : 0.0f;
   }
   __shared__ float red[2][kForceThreads / 32];
   for (int off = 16; off > 0; off >>= 1) {

@@ -154,7 +154,13 @@ __device__ __forceinline__ void norm_finalize_body(const float* partials, int np
   if (threadIdx.x == 0) {
     const int k = *st.iter;
     const float l = sr > 0.0 ? (float)(sdr / sr) : INFINITY;
-    if (k < st.cap) st.hist[k] = l;
+    if (k < st.cap) {
+      st.hist[k] = l;
+      if (st.sums) {
+        st.sums[2 * k] = sdr;
+        st.sums[2 * k + 1] = sr;
+      }
+    }
     *st.iter = k + 1;
     bool stop = false;
     if (st.eps > 0.0f && k >= st.window && k < st.cap) {

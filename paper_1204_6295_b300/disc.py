@@ -58,6 +58,7 @@ class Params(ctypes.Structure):
         ("fill_passes", ctypes.c_int32),
         ("smooth_mode", ctypes.c_int32),
         ("quant_max", ctypes.c_float * 2),
+        ("norm_planes", ctypes.c_int32 * 2),
     ]
 
 
@@ -79,6 +80,7 @@ _SIGS = {
     "disc_get_level_field": (_st, [_vp, _i32, _vp, ctypes.c_int]),
     "disc_get_progress": (_st, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "disc_get_norm_history": (_st, [_vp, _i32, _vp, _i32, ctypes.POINTER(_i32)]),
+    "disc_get_norm_sums": (_st, [_vp, _i32, _vp, _i32, ctypes.POINTER(_i32)]),
     "disc_destroy": (_st, [_vp]),
     "disc_qscale": (_f32, [_f32, ctypes.POINTER(_i32)]),
     "disc_batch_create": (_st, [ctypes.POINTER(Params), ctypes.c_int, _vp, _i32, ctypes.POINTER(_vp)]),
@@ -180,7 +182,7 @@ def _f32_check(t, shape, name):
 def make_params(patch=(3, 3, 3), sigma=1.0, radius=0, levels=2, iters=(50, 50), stop_eps=0.0,
                 stop_window=10, force_mode=FORCE_THIRION, global_shift=True, var_floor=1e-6,
                 mask_mode=0, hu0_factor=2.0, a_lo=0.5, a_hi=1.5, fill_h=50.0, fill_t=(7, 7, 3),
-                fill_passes=32, smooth_mode=0, quant_max=(0.0, 0.0)):
+                fill_passes=32, smooth_mode=0, quant_max=(0.0, 0.0), norm_planes=(0, 0)):
     p = Params()
     _check(_lib.disc_params_default(ctypes.byref(p)), "disc_params_default")
     for a in range(3):
@@ -209,6 +211,8 @@ def make_params(patch=(3, 3, 3), sigma=1.0, radius=0, levels=2, iters=(50, 50), 
     p.smooth_mode = int(smooth_mode)
     p.quant_max[0] = float(quant_max[0])
     p.quant_max[1] = float(quant_max[1])
+    p.norm_planes[0] = int(norm_planes[0])
+    p.norm_planes[1] = int(norm_planes[1])
     return p
 
 
@@ -303,6 +307,14 @@ class Registration:
         n = _i32(0)
         _check(_lib.disc_get_norm_history(self._h, int(level), out.ctypes.data, cap, ctypes.byref(n)),
                "disc_get_norm_history")
+        return out[:n.value].copy()
+
+    def norm_sums(self, level, cap=100000):
+        """[k][2]: sum |dr|, sum |r| behind each l^(k) of `level` (float64)."""
+        out = np.empty((cap, 2), np.float64)
+        n = _i32(0)
+        _check(_lib.disc_get_norm_sums(self._h, int(level), out.ctypes.data, cap, ctypes.byref(n)),
+               "disc_get_norm_sums")
         return out[:n.value].copy()
 
     def metrics(self, bins=64, sigma=1.0, t_low=0.4, t_high=0.2):

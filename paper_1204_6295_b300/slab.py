@@ -33,12 +33,18 @@ planes are the whole volume's; the halo must cover the reach at every level,
 2^l (R + p_z + ceil(d / 2^l) + 3) fine planes at level l.  At a level's end
 every slab up-samples its own buffer (the fine planes of its interior read
 coarse planes at most one away) and the fine level starts with an exchange.
-Scope: fixed iteration counts (the convergence norm's sums are per slab) and
-the mask off (its median a_m is a whole-volume statistic).
+
+The convergence norm l^(k) = sum |dr| / sum |r| (Sec. 2.3) is a ratio of two
+whole-volume sums: each slab sums its interior only (``norm_planes``), the two
+sums are added over the slabs (the allreduce of a multi-device run) and the
+stop rule is applied to the ratio, ending the level in every slab at once.
+Scope: the mask off (its median a_m is a whole-volume statistic).
 """
 from __future__ import annotations
 
 import math
+
+import numpy as np
 
 from . import disc
 
@@ -110,14 +116,18 @@ class SlabRegistration:
         import torch
         self._torch = torch
         kw = dict(kw)
-        if kw.get("mask_mode", 0) or kw.get("stop_eps", 0.0) > 0.0:
-            raise ValueError("the slab decomposition runs with the mask off and fixed counts")
+        if kw.get("mask_mode", 0):
+            raise ValueError("the slab decomposition runs with the mask off")
         if len(iters) != levels:
             raise ValueError("one iteration count per level (coarsest first)")
         self.levels = int(levels)
         self.iters = [int(n) for n in iters]
+        # the stop rule is applied here, to the slabs' summed norms
+        self.stop_eps = float(kw.pop("stop_eps", 0.0))
+        self.stop_window = int(kw.get("stop_window", 10))
         kw["levels"] = self.levels
-        kw["iters"] = (1 << 30,) * self.levels   # no level completes inside a context: counts are driven here
+        kw["iters"] = tuple(max(1, n) for n in self.iters)   # each exchange restarts a context's count
+        self.hist = [[] for _ in range(self.levels)]
         self.shift = bool(kw.pop("global_shift", True))
         self.kw = kw
         self.nslabs = int(nslabs)
@@ -152,8 +162,9 @@ class SlabRegistration:
         qmax = [float(v) for v in mx.cpu()]
         self.close()
         self.plan = slab_plan(nz, self.nslabs, self.halo, self.align)
-        for (_, _, b0, b1) in self.plan:
-            p = disc.make_params(global_shift=False, quant_max=qmax, **self.kw)
+        self.hist = [[] for _ in range(self.levels)]
+        for (z0, z1, b0, b1) in self.plan:
+            p = disc.make_params(global_shift=False, quant_max=qmax, norm_planes=(z0 - b0, z1 - b0), **self.kw)
             reg = disc.Registration(p)
             reg.set_images(ct[b0:b1].contiguous(), is_shift[b0:b1].contiguous())
             self.regs.append(reg)
@@ -191,14 +202,40 @@ class SlabRegistration:
                 buf[:, lo - b0:hi - b0] = fields[t][:, lo - tb0:hi - tb0]
             reg.set_field(level, buf)
 
+    def _norm_step(self, level):
+        """l^(k) of the iteration just run from the slabs' summed interior sums;
+        True when the stop rule of Sec. 2.3 ends the level."""
+        sdr = sr = 0.0
+        for reg in self.regs:
+            s = reg.norm_sums(level, cap=1)      # each exchange restarts the count: this iteration's sums
+            sdr += float(s[0, 0])
+            sr += float(s[0, 1])
+        h = self.hist[level]
+        lk = np.float32(sdr / sr) if sr > 0.0 else np.float32(np.inf)
+        k = len(h)
+        h.append(lk)
+        if self.stop_eps > 0.0 and k >= self.stop_window:
+            lp = h[k - self.stop_window]
+            return bool(np.isfinite(lp) and np.isfinite(lk) and lp - lk <= np.float32(self.stop_eps))
+        return False
+
+    def norm_history(self, level):
+        """l^(k) of the iterations run at `level` (float32, as a context reports it)."""
+        return np.array(self.hist[level], np.float32)
+
     def iterate(self):
-        """The whole schedule, coarsest level first."""
+        """The whole schedule, coarsest level first; returns the iterations run."""
         torch = self._torch
+        done = 0
         for level in range(self.levels - 1, -1, -1):
             for _ in range(self.iters[self.levels - 1 - level]):
                 for reg in self.regs:
                     reg.iterate(1, sync=False)
+                done += 1
+                stop = self._norm_step(level)
                 self.exchange(level)
+                if stop:
+                    break
             if level > 0:                        # Algorithm A1: up-sample to the next finer level
                 nx, ny = self._level_dims(level - 1)
                 fine = []
@@ -207,6 +244,7 @@ class SlabRegistration:
                     disc.k_upsample_field2(f, rf)
                     fine.append(rf)
                 self.exchange(level - 1, fine)
+        return done
 
     def get_field(self):
         """The assembled finest-level field [3][nz][ny][nx] (device tensor): each slab's interior."""

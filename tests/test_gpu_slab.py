@@ -3,8 +3,11 @@ with halo exchanges of r after every iteration gives the whole-volume
 context's field bit for bit (same kernels, same fixed-point scales through
 quant_max, same global shift), on one pyramid level and on two (slab cuts on
 even planes, each slab up-sampling its own buffer at the level's end); a halo
-one plane short of an iteration's reach does not.  quant_max below an image's
-own maximum is rejected; disc_get_level_field returns a level's own field.
+one plane short of an iteration's reach does not.  The slabs' interior norm
+sums (norm_planes) add up to the whole volume's l^(k), and the stop rule on
+the summed norms ends each level at the whole-volume run's iteration.
+quant_max below an image's own maximum is rejected; disc_get_level_field
+returns a level's own field.
 """
 import numpy as np
 import pytest
@@ -66,6 +69,42 @@ def test_two_level_slabs_equal_whole_volume(disc, pair, kw):
         assert all(b1 - b0 < 64 and b0 % 2 == 0 for _, _, b0, b1 in sr.plan)
         sr.iterate()
         got = sr.get_field().cpu().numpy()
+    np.testing.assert_array_equal(got, whole)
+
+
+def test_summed_norms_and_stop_rule(disc, pair):
+    import torch
+    from paper_1204_6295_b300.slab import SlabRegistration
+    kw = dict(patch=(5, 5, 5), sigma=1.0)
+    ct, cbct = torch.from_numpy(pair.ct).cuda(), torch.from_numpy(pair.cbct).cuda()
+    # fixed counts: l^(k) of the summed interior sums against the whole volume's
+    with disc.Registration(levels=2, iters=(6, 5), **kw) as reg:
+        reg.set_images(pair.ct, pair.cbct)
+        reg.iterate(-1)
+        ref = [reg.norm_history(l) for l in range(2)]
+        sums = reg.norm_sums(0)
+    assert sums.shape == (5, 2) and np.all(sums > 0)
+    np.testing.assert_allclose(ref[0], (sums[:, 0] / sums[:, 1]).astype(np.float32), rtol=1e-6)
+    with SlabRegistration(2, max_disp_z=6.0, levels=2, iters=(6, 5), **kw) as sr:
+        sr.set_images(ct, cbct)
+        assert sr.iterate() == 11
+        for l in range(2):
+            np.testing.assert_allclose(sr.norm_history(l), ref[l], rtol=1e-5)
+    # the stop rule ends the fine level early, at the same iteration in both runs
+    kw2 = dict(kw, stop_eps=2e-3)
+    with disc.Registration(levels=2, iters=(40, 200), **kw2) as reg:
+        reg.set_images(pair.ct, pair.cbct)
+        done_w, _ = reg.iterate(-1)
+        whole = reg.get_field()
+        hist_w = reg.norm_history(0)
+    assert done_w < 240
+    with SlabRegistration(2, max_disp_z=6.0, levels=2, iters=(40, 200), **kw2) as sr:
+        sr.set_images(ct, cbct)
+        done_s = sr.iterate()
+        got = sr.get_field().cpu().numpy()
+        hist_s = sr.norm_history(0)
+    assert done_s == done_w and len(hist_s) == len(hist_w)
+    np.testing.assert_allclose(hist_s, hist_w, rtol=1e-5)
     np.testing.assert_array_equal(got, whole)
 
 
