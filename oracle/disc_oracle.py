@@ -7,7 +7,7 @@ calls it and shares no code with it.
 Every function follows one passage of the paper, in the paper's notation, with
 numpy float64 arrays and no blocking, fusion or reordering beyond what the
 definition states.  Where the paper is silent or garbled the reading used is
-stated in the docstring (readings R1..R20, listed with their reasons in the
+stated in the docstring (readings R1..R22, listed with their reasons in the
 design notes of the repository).
 
 Layout: images are ``[nz][ny][nx]`` (x fastest); fields are ``[3][nz][ny][nx]``
@@ -17,11 +17,11 @@ Roles (Sec. 2.2): the moving image ``I_m`` is the planning CT, the static image
 ``I_s`` is the CBCT; the field ``r`` relates them by ``I_m(x + r(x)) = I_s(x)``
 (Sec. 2.1).
 
-Pins: every function here is checked in ``tests/test_oracle_pins.py`` and
-``tests/test_oracle_mask.py`` against brute force, closed forms, library
-special cases or invariants.  The one
-function without an independent pin is noted as "parity unpinned" below
-(none at present).
+Pins: every function here is checked in ``tests/test_oracle_pins.py``,
+``tests/test_oracle_mask.py`` and ``tests/test_oracle_metrics.py`` against
+brute force, closed forms, library special cases or invariants.  A function
+without an independent pin would be noted as "parity unpinned" below (none at
+present).
 """
 from __future__ import annotations
 
