@@ -85,8 +85,15 @@ def _near(x, t, rel=1e-4):
     return np.abs(x - t) <= rel * max(abs(t), 1.0)
 
 
+FILLS = [((7, 7, 3), 32),                # Sec. 2.3's box T, every masked voxel reached
+         ((15, 9, 5), 32),               # wide x span: the known-voxel bits cross mask words
+         ((3, 3, 1), 2),                 # a pass cap that leaves voxels unfilled
+         ((1, 3, 3), 1)]                 # a box one voxel wide in x
+
+
+@pytest.mark.parametrize("fill_t,passes", FILLS)
 @pytest.mark.parametrize("shape,patch", SHAPES)
-def test_mask_and_fill(disc, shape, patch):
+def test_mask_and_fill(disc, shape, patch, fill_t, passes):
     ct, Is = _pair(shape, 3)
     r = phantom.smooth_random_field(shape, 4, amp=1.5).astype(np.float32)
     zs, sd = _static(disc, Is, patch)
@@ -103,7 +110,7 @@ def test_mask_and_fill(disc, shape, patch):
     stamp = torch.empty(shape, dtype=torch.int32, device="cuda")
     left = torch.zeros(1, dtype=torch.int32, device="cuda")
     disc.k_correct_masked(m, dev(Is), zs, sd, a, b, d, stamp, patch, qs, hu0, a_min, a_max,
-                          fill_h=50.0, fill_t=(7, 7, 3), fill_passes=32, remaining_out=left)
+                          fill_h=50.0, fill_t=fill_t, fill_passes=passes, remaining_out=left)
     disc.k_check_error()
     m64, Is64 = host(m), Is.astype(np.float64)
     st = stamp.cpu().numpy()
@@ -118,9 +125,11 @@ def test_mask_and_fill(disc, shape, patch):
     ambiguous = _near(np.abs(m64 - Is64), hu0) | _near(a_o, a_min) | _near(a_o, a_max)
     assert np.array_equal(xi_g[~ambiguous], xi_o[~ambiguous])
     # the fill from the GPU's own decisions: stamps exact, values to float32 accuracy
-    fa, fb, fst = O.fill_coefficients(a_o, b_o, xi_g, Is64, 50.0, (3, 3, 1), 32)
+    fa, fb, fst = O.fill_coefficients(a_o, b_o, xi_g, Is64, 50.0, tuple((t - 1) // 2 for t in fill_t), passes)
     np.testing.assert_array_equal(st, fst)
     assert int(left.cpu()[0]) == int((fst < 0).sum())
+    if passes < 32:
+        assert (fst < 0).any()                   # the cap left some voxels unfilled
     assert rel_err(host(a), fa) <= 1e-4
     # b = E(M) - a E(S) cancels: its error scales with the intensities, not with b
     assert np.abs(host(b) - fb).max() <= 1e-4 * np.abs(fa * Is64).max()
