@@ -272,9 +272,8 @@ def time_differentiable(disc, torch, w, pair_dev, field_dev, kt, reps=5):
     grad = torch.empty_like(field_dev)
     s = torch.cuda.current_stream()
 
-    def step():
-        disc.k_ssd_loss(ct, kt["zs"], field_dev, loss, patch, kt["qs_m"])
-        disc.k_ssd_grad(ct, kt["zs"], field_dev, grad, patch, kt["qs_m"])
+    def step():                               # loss and gradient from one adjoint pass
+        disc.k_ssd_grad(ct, kt["zs"], field_dev, grad, patch, kt["qs_m"], loss_out=loss)
 
     for _ in range(2):
         step()
@@ -288,8 +287,9 @@ def time_differentiable(disc, torch, w, pair_dev, field_dev, kt, reps=5):
     t = e0.elapsed_time(e1) / reps / 1e3
     return {"value": kt["N"] / t / 1e9, "unit": "Gvoxel-evaluations/s (forward + backward)",
             "ms_per_step": t * 1e3, "algorithmic_bytes_per_voxel": 32,
-            "what": "disc_k_ssd_loss + disc_k_ssd_grad on the finest level (256x256x128 for the default "
-                    "workload), patch statistics recomputed in the backward pass"}
+            "what": "disc_k_ssd_grad with loss_out on the finest level (256x256x128 for the default "
+                    "workload): warp, moments, loss and adjoint coefficients in one pass, their box sums, "
+                    "the warp's adjoint; patch statistics recomputed, not stored"}
 
 
 def time_masked(disc, torch, w, pair_dev, dist, steps=1):

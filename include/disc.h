@@ -343,7 +343,9 @@ disc_status disc_k_ssd_loss(const float* Im, const float* zs, const float* r,
  * and the warp's adjoint is the analytic trilinear derivative (zero along an
  * axis whose sample position is clamped).  Cubic patches only (half size 1..8;
  * other patches return DISC_ERR_SHAPE).  loss_out (may be NULL) also receives
- * L.  grad must not alias r. */
+ * L, summed in the same pass from the same d = I'_s - m (its float partial
+ * sums are grouped by that pass's CTAs, so it can differ from
+ * disc_k_ssd_loss's value in the last bits).  grad must not alias r. */
 disc_status disc_k_ssd_grad(const float* Im, const float* zs, const float* r, float* grad,
                             double* loss_out, int32_t nx, int32_t ny, int32_t nz,
                             const int32_t patch[3], float qscale, float var_floor,

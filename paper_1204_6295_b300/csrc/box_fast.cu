@@ -274,6 +274,7 @@ __device__ __forceinline__ void box_body(const BoxArgs& a, int bx, int by, int b
         } else if (MODE == kModeSsdLoss) {
           acc0 = fmaf(d, d, acc0);
         } else if (MODE == kModeSsdAdjoint) {
+          acc0 = fmaf(d, d, acc0);                       // the loss, when partials are given
           const float D = -2.0f * d;
           const float A = -D * inv_n;
           const float Bc = sg_ > 0.0f ? -D * zsv * inv_n / sg_ : 0.0f;
@@ -352,7 +353,7 @@ __device__ __forceinline__ void box_body(const BoxArgs& a, int bx, int by, int b
     __syncthreads();
   }
 
-  if (MODE == kModeIterate || MODE == kModeSsdLoss) {
+  if (MODE == kModeIterate || MODE == kModeSsdLoss || MODE == kModeSsdAdjoint) {
     __shared__ float red[2][kThreads / 32];
     for (int off = 16; off > 0; off >>= 1) {
       acc0 += __shfl_down_sync(0xffffffffu, acc0, off);
@@ -364,7 +365,7 @@ __device__ __forceinline__ void box_body(const BoxArgs& a, int bx, int by, int b
       red[1][wid] = acc1;
     }
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && a.partials != nullptr) {
       float t0 = 0.0f, t1 = 0.0f;
       for (int w = 0; w < kThreads / 32; ++w) {
         t0 += red[0][w];

@@ -245,6 +245,7 @@ __global__ void __launch_bounds__(kThreads) k_box_pass(BoxArgs a) {
           acc0 = fmaf(d, d, acc0);
         } else if (MODE == kModeSsdAdjoint) {
           // L = sum (m - f)^2: D = dL/dm direct; A, B, C the patch-sum coefficients
+          acc0 = fmaf(d, d, acc0);                       // the loss, when partials are given
           const float D = -2.0f * d;
           const float inv_n = 1.0f / (float)n;
           const float A = -D * inv_n;
@@ -313,7 +314,7 @@ __global__ void __launch_bounds__(kThreads) k_box_pass(BoxArgs a) {
     // of the ring slot read above comes after two more barriers
   }
 
-  if (MODE == kModeIterate || MODE == kModeSsdLoss) {
+  if (MODE == kModeIterate || MODE == kModeSsdLoss || MODE == kModeSsdAdjoint) {
     // fixed-order CTA reduction: warp shuffles, then thread 0 over the warp sums
     __shared__ float red[2][kThreads / 32];
     for (int off = 16; off > 0; off >>= 1) {
@@ -326,7 +327,7 @@ __global__ void __launch_bounds__(kThreads) k_box_pass(BoxArgs a) {
       red[1][wid] = acc1;
     }
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && a.partials != nullptr) {
       float s0 = 0.0f, s1 = 0.0f;
       for (int w = 0; w < kThreads / 32; ++w) {
         s0 += red[0][w];

@@ -404,6 +404,7 @@ __device__ __forceinline__ bool box_tma_body(const BoxArgs& a, int bx, int by, i
         } else if (MODE == kModeSsdLoss) {
           acc0 = fmaf(d, d, acc0);
         } else if (MODE == kModeSsdAdjoint) {
+          acc0 = fmaf(d, d, acc0);                       // the loss, when partials are given
           const float D = -2.0f * d;
           const float A = -D * inv_n;
           const float Bc = sg_ > 0.0f ? -D * zsv * inv_n / sg_ : 0.0f;
@@ -469,7 +470,7 @@ __device__ __forceinline__ bool box_tma_body(const BoxArgs& a, int bx, int by, i
     // barrier separates them
   }
 
-  if (MODE == kModeIterate || MODE == kModeSsdLoss) {
+  if (MODE == kModeIterate || MODE == kModeSsdLoss || MODE == kModeSsdAdjoint) {
     for (int off = 16; off > 0; off >>= 1) {
       acc0 += __shfl_down_sync(0xffffffffu, acc0, off);
       acc1 += __shfl_down_sync(0xffffffffu, acc1, off);
@@ -480,7 +481,7 @@ __device__ __forceinline__ bool box_tma_body(const BoxArgs& a, int bx, int by, i
       red[kThreads / 32 + wid] = acc1;
     }
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && a.partials != nullptr) {
       float t0 = 0.0f, t1 = 0.0f;
       for (int w = 0; w < kThreads / 32; ++w) {
         t0 += red[w];

@@ -164,12 +164,19 @@ disc_status disc_k_ssd_grad(const float* Im, const float* zs, const float* r, fl
   float* abcd = work + N;
   float* sums = work + 5 * N;
   float* tmp = work + 8 * N;
-  cudaError_t e = cudaSuccess;
-  if (loss_out) e = ssd_loss_into(Im, zs, r, m, loss_out, nx, ny, nz, h, qscale, var_floor, s);
-  else e = launch_warp(Im, r, m, nx, ny, nz, nullptr, s);
+  const int nparts = (int)(p.grid.x * p.grid.y * p.grid.z);
+  float* parts = nullptr;   // the loss from the adjoint pass's own d (one pass for both)
+  cudaError_t e = loss_out ? cudaMallocAsync(&parts, sizeof(float) * 2 * nparts, s) : cudaSuccess;
+  if (e == cudaSuccess) e = launch_warp(Im, r, m, nx, ny, nz, nullptr, s);
   BoxArgs a = ssd_args(m, zs, nx, ny, nz, h, qscale, var_floor);
   a.out = abcd;
+  a.partials = parts;
   if (e == cudaSuccess) e = box_launch(kModeSsdAdjoint, a, p, s);
+  if (e == cudaSuccess && loss_out) e = launch_partials_sum(parts, nparts, 0, loss_out, s);
+  if (parts) {
+    const cudaError_t ef = cudaFreeAsync(parts, s);
+    if (e == cudaSuccess) e = ef;
+  }
   GaussArgs g{};
   g.u = abcd;
   g.r = sums;

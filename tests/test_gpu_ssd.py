@@ -43,7 +43,8 @@ def _gpu_loss_grad(disc, ct, cbct, r, patch):
     disc.k_ssd_loss(ct_d, zs, r_d, loss, patch, qs)
     disc.k_ssd_grad(ct_d, zs, r_d, grad, patch, qs, loss_out=loss2)
     torch.cuda.synchronize()
-    assert float(loss.item()) == float(loss2.item())
+    # the same d^2 terms, grouped by the adjoint pass's CTAs
+    assert float(loss2.item()) == pytest.approx(float(loss.item()), rel=1e-6)
     return float(loss.item()), host(grad)
 
 
