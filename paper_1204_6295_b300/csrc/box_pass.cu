@@ -399,7 +399,7 @@ BoxPlan box_plan(int mode, int nx, int ny, int nz, int hx, int hy, int hz, int n
   const long long slots = (long long)num_sms * per_sm;
   long long chunks = slots / ((long long)gx * gy);
   if (chunks < 1) chunks = 1;
-  long long max_chunks = (nz + 3) / 4;       // at least 4 output planes per chunk
+  long long max_chunks = (nz + 1) / 2;       // at least 2 output planes per chunk
   if (max_chunks < 1) max_chunks = 1;
   if (chunks > max_chunks) chunks = max_chunks;
   p.zlen = (int)((nz + chunks - 1) / chunks);
