@@ -259,7 +259,9 @@ disc_status disc_batch_destroy(disc_batch* b);
  * All pointers are device pointers on the current device; work goes on
  * `stream` (cudaStream_t, NULL = legacy default stream).  `patch` is the
  * odd patch size per axis; `qscale` is the fixed-point scale (a power of
- * two, see disc_qscale).  Buffers may not overlap unless stated.
+ * two, see disc_qscale).  Buffers may not overlap unless stated.  Calls that
+ * need scratch take it stream-ordered from the device's default memory pool
+ * and raise that pool's release threshold, so that repeated calls reuse it.
  * ------------------------------------------------------------------- */
 
 /* Fixed-point scale 2^e used for exact integer patch sums of an image

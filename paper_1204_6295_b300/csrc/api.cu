@@ -1066,6 +1066,7 @@ disc_status disc_k_correct_masked(const float* m, const float* Is, const float* 
   const size_t FB = (size_t)fill_front_blocks(nx, ny, nz);
   // the counters [fill_passes + 1], two known-voxel bit masks [2][W], the front
   // list [N], its block offsets [FB] and length [1]
+  keep_pool_memory();
   int* work = nullptr;
   if (cudaMallocAsync(&work, sizeof(int) * (fill_passes + 1 + 2 * W + N + FB + 1), s) != cudaSuccess) {
     cudaGetLastError();
@@ -1424,6 +1425,7 @@ disc_status disc_k_gauss(const float* u, float* r, int32_t nx, int32_t ny, int32
   disc_ctx* ctx = nullptr;
   cudaStream_t s = (cudaStream_t)stream;
   float* t = nullptr;
+  keep_pool_memory();
   if (p.queue) CK(cudaMallocAsync(&t, sizeof(float) * 3 * (size_t)nx * ny * nz, s));
   g.t = t;
   cudaError_t e = gauss_launch(g, p, s);

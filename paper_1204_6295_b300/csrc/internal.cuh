@@ -268,6 +268,10 @@ struct NormState {
 };
 // *p = v (a one-thread kernel, stream-ordered)
 cudaError_t launch_set_int(int* p, int v, cudaStream_t s);
+// Raise the release threshold of the current device's default memory pool (once
+// per device), so that the scratch the kernel-level calls allocate stream-ordered
+// is reused from call to call instead of being unmapped at each synchronisation.
+void keep_pool_memory();
 cudaError_t launch_norm_finalize(const float* partials, int nparts, NormState st, cudaStream_t s);
 // One block per volume: NormState and partials of volume p in the tables.
 struct NormBatch {

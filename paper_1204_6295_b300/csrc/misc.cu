@@ -236,6 +236,22 @@ cudaError_t launch_up2(const float* rc, float* rf, int nx, int ny, int nz, cudaS
   return cudaGetLastError();
 }
 
+void keep_pool_memory() {
+  static bool done[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return;
+  }
+  if (done[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    unsigned long long keep = ~0ull;   // hold freed blocks for the next call instead of unmapping them
+    if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep) == cudaSuccess) done[dev] = true;
+  }
+  cudaGetLastError();
+}
+
 cudaError_t launch_set_int(int* p, int v, cudaStream_t s) {
   k_set_int<<<1, 1, 0, s>>>(p, v);
   return cudaGetLastError();

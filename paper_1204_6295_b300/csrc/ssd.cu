@@ -125,6 +125,7 @@ disc_status disc_k_ssd_loss(const float* Im, const float* zs, const float* r, do
   if (!loss_out) return DISC_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const size_t N = (size_t)nx * ny * nz;
+  keep_pool_memory();
   float* m = nullptr;
   if (cudaMallocAsync(&m, sizeof(float) * N, s) != cudaSuccess) {
     cudaGetLastError();
@@ -156,6 +157,7 @@ disc_status disc_k_ssd_grad(const float* Im, const float* zs, const float* r, fl
   cudaStream_t s = (cudaStream_t)stream;
   const size_t N = (size_t)nx * ny * nz;
   float* work = nullptr;   // m (N) | A B C D (4N) | sums of A B C (3N) | filter scratch (3N)
+  keep_pool_memory();
   if (cudaMallocAsync(&work, sizeof(float) * 11 * N, s) != cudaSuccess) {
     cudaGetLastError();
     return DISC_ERR_OOM;
