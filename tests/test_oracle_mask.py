@@ -73,6 +73,31 @@ def test_jacobi_propagation_distance():
     assert np.all(fa[6:] == 0.0) and np.all(fa[:6] == 2.0)
 
 
+@pytest.mark.parametrize("t_half,seed", [((3, 3, 1), 0), ((1, 2, 2), 1), ((0, 1, 3), 2)])
+def test_fill_front_is_box_dilation(t_half, seed):
+    """A voxel is filled in the first pass after one of its box neighbours is
+    known, so the voxels known after pass p are the p-fold dilation of the
+    unmasked voxels by the box T (scipy's binary dilation, an independent
+    routine): the stamps are the dilation levels, capped by the pass limit."""
+    from scipy import ndimage
+    rng = np.random.default_rng(seed)
+    shape = (9, 13, 17)
+    xi = rng.random(shape) < 0.93                      # mostly masked: deep fronts
+    xi[4, 6, 8] = False
+    known = ~xi
+    tx, ty, tz = t_half
+    box = np.ones((2 * tz + 1, 2 * ty + 1, 2 * tx + 1), bool)
+    level = np.where(known, 0, -1)
+    cur = known.copy()
+    for p in range(1, 7):
+        nxt = ndimage.binary_dilation(cur, structure=box)
+        level[nxt & ~cur] = p
+        cur = nxt
+    a = rng.normal(size=shape)
+    _, _, st = O.fill_coefficients(a, a, xi, rng.normal(0.0, 30.0, shape), 50.0, t_half, 6)
+    np.testing.assert_array_equal(st, level)
+
+
 def test_nothing_known_and_exponent_cap():
     shape = (2, 3, 4)
     xi = np.ones(shape, bool)
