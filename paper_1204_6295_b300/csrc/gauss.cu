@@ -156,12 +156,21 @@ template <int R>
 struct XYLayout {
   static constexpr int IX = kSX + 2 * R;
   static constexpr int IY = kSY + 2 * R;
-  static constexpr int IXP = IX + 1;                   // row stride (odd)
+  // Row strides of the staged plane.  An x-filter task reads its window of
+  // kBX + 2R inputs as 16-byte vectors; the 8 lanes of a quarter warp read 8
+  // consecutive rows, which fall on distinct banks when a row is 4 mod 8 words
+  // long (and every row starts on a 16-byte boundary).
+  static constexpr int NV2 = (kBX + 2 * R) / 2;                  // float4 loads of (ux, uy) pairs
+  static constexpr int NVZ = (kBX + 2 * R + 3) / 4;              // float4 loads of uz
+  static constexpr int IXP = IX + ((2 - IX % 4) + 4) % 4;        // float2 stride: IXP = 2 mod 4
+  static constexpr int IXPZ0 = kSX - kBX + 4 * NVZ;              // floats a task may read in a row
+  static constexpr int IXPZ = IXPZ0 + ((4 - IXPZ0 % 8) + 8) % 8; // float stride: 4 mod 8
+  static_assert((kBX + 2 * R) % 2 == 0 && IXP >= IX && IXPZ >= IX, "staged row strides");
   static constexpr int NXT = IY * (kSX / kBX);         // x-filter tasks (row, x quad)
   static constexpr size_t o_in2 = 0;                   // float2 [IY][IXP]  (ux, uy)
-  static constexpr size_t o_inz = o_in2 + 8 * (size_t)IY * IXP;   // float [IY][IXP]
+  static constexpr size_t o_inz = o_in2 + 8 * (size_t)IY * IXP;   // float [IY][IXPZ]
   static constexpr int XP = kSX + 1;                   // row stride of the x-filtered planes (odd)
-  static constexpr size_t o_x2 = o_inz + 4 * (size_t)IY * IXP;    // float2 [IY][XP]
+  static constexpr size_t o_x2 = o_inz + 4 * (size_t)IY * IXPZ;   // float2 [IY][XP]
   static constexpr size_t o_xz = o_x2 + 8 * (size_t)IY * XP;      // float [IY][XP]
   static constexpr size_t bytes = o_xz + 4 * (size_t)IY * XP;
 };
@@ -210,7 +219,7 @@ __device__ __forceinline__ void gauss_xy_body(const GaussArgs& a, int bx, int by
     if (e < X::IY * X::IX) {
       const int iy = e / X::IX, ix = e - iy * X::IX;
       in2[iy * X::IXP + ix] = make_float2(vx[k], vy[k]);
-      inz[iy * X::IXP + ix] = vz[k];
+      inz[iy * X::IXPZ + ix] = vz[k];
     }
   }
   __syncthreads();
@@ -220,8 +229,24 @@ __device__ __forceinline__ void gauss_xy_body(const GaussArgs& a, int bx, int by
     // consecutive tasks take consecutive rows: the odd row strides then spread a
     // warp's loads and stores over all shared-memory banks
     const int j = t / X::IY, iy = t - j * X::IY;
-    const float2* r2 = in2 + iy * X::IXP + kBX * j;
-    const float* rz = inz + iy * X::IXP + kBX * j;
+    const float4* r2 = reinterpret_cast<const float4*>(in2 + iy * X::IXP + kBX * j);
+    const float4* rz = reinterpret_cast<const float4*>(inz + iy * X::IXPZ + kBX * j);
+    float2 w2[2 * X::NV2];
+    float wz[4 * X::NVZ];
+#pragma unroll
+    for (int g = 0; g < X::NV2; ++g) {
+      const float4 q = r2[g];
+      w2[2 * g] = make_float2(q.x, q.y);
+      w2[2 * g + 1] = make_float2(q.z, q.w);
+    }
+#pragma unroll
+    for (int g = 0; g < X::NVZ; ++g) {
+      const float4 q = rz[g];
+      wz[4 * g] = q.x;
+      wz[4 * g + 1] = q.y;
+      wz[4 * g + 2] = q.z;
+      wz[4 * g + 3] = q.w;
+    }
     float2 acc[kBX];
     float accz[kBX];
 #pragma unroll
@@ -231,8 +256,8 @@ __device__ __forceinline__ void gauss_xy_body(const GaussArgs& a, int bx, int by
     }
 #pragma unroll
     for (int i = 0; i < kBX + 2 * R; ++i) {
-      const float2 v = r2[i];
-      const float vzz = rz[i];
+      const float2 v = w2[i];
+      const float vzz = wz[i];
 #pragma unroll
       for (int b = 0; b < kBX; ++b) {
         const int k = i - b;                  // tap index of input i for output b
