@@ -595,6 +595,8 @@ disc_status disc_set_images(disc_ctx* ctx, const float* ct, const float* cbct, i
   for (int l = 1; l < L; ++l)
     for (int a = 0; a < 3; ++a) dims[l][a] = (dims[l - 1][a] + 1) / 2;
   const bool same = ctx->have_images && ctx->nx == nx && ctx->ny == ny && ctx->nz == nz;
+  // scalars the captured iteration graphs hold by value (buffers are reused as they are)
+  const float old_qs_m = ctx->qs_m, old_hu0 = ctx->mask_hu0, old_am = ctx->mask_am;
   if (!same) {
     free_levels(ctx);
     int max_parts = 1;
@@ -664,14 +666,6 @@ disc_status disc_set_images(disc_ctx* ctx, const float* ct, const float* cbct, i
     ctx->ny = ny;
     ctx->nz = nz;
     ctx->L = L;
-  } else {
-    for (int l = 0; l < L; ++l) {
-      if (ctx->lev[l].graph) cudaGraphExecDestroy(ctx->lev[l].graph);
-      if (ctx->lev[l].loop) cudaGraphExecDestroy(ctx->lev[l].loop);
-      ctx->lev[l].graph = nullptr;
-      ctx->lev[l].loop = nullptr;
-      ctx->lev[l].graph_iters = 0;
-    }
   }
   ctx->have_images = true;
   CK(enter(ctx));
@@ -740,6 +734,17 @@ disc_status disc_set_images(disc_ctx* ctx, const float* ct, const float* cbct, i
     std::memcpy(&hi, &res[8], sizeof(float));
     ctx->mask_am = res[0] > 0 ? (float)(0.5 * ((double)lo + (double)hi)) : 0.0f;
     ctx->mask_hu0 = ctx->p.hu0_factor * (float)std::fabs(dhu);
+  }
+  // the graphs of the previous images stay valid unless a scalar they captured
+  // changed: the fixed-point scale of I_m or the mask thresholds
+  if (same && (ctx->qs_m != old_qs_m || ctx->mask_hu0 != old_hu0 || ctx->mask_am != old_am)) {
+    for (int l = 0; l < L; ++l) {
+      if (ctx->lev[l].graph) cudaGraphExecDestroy(ctx->lev[l].graph);
+      if (ctx->lev[l].loop) cudaGraphExecDestroy(ctx->lev[l].loop);
+      ctx->lev[l].graph = nullptr;
+      ctx->lev[l].loop = nullptr;
+      ctx->lev[l].graph_iters = 0;
+    }
   }
   const Level& c = ctx->lev[L - 1];
   CK(cudaMemsetAsync(c.r, 0, 3 * c.N * sizeof(float), ctx->s));
