@@ -518,6 +518,8 @@ __global__ void __launch_bounds__(kThreads, 3)
     k_box_tma(const BoxArgs a, const __grid_constant__ CUtensorMap map_w, const __grid_constant__ CUtensorMap map_f,
               const __grid_constant__ CUtensorMap map_z, const __grid_constant__ CUtensorMap map_r) {
   extern __shared__ __align__(128) unsigned char smem[];
+  pdl_wait();
+  pdl_release();
   if (a.stop != nullptr && *(volatile const int*)a.stop != 0) return;
   if (!tma_cta_setup<MODE, H>(smem, a.err)) return;
   uint32_t pa = 0, pb = 0;
@@ -627,8 +629,7 @@ cudaError_t launch_tma(const BoxArgs& a, const BoxPlan& p, cudaStream_t s) {
   if (!encode_maps<MODE, H>(a, m)) return cudaErrorInvalidValue;
   cudaError_t e = prepare(k_box_tma<MODE, H>, B::bytes, set);
   if (e != cudaSuccess) return e;
-  k_box_tma<MODE, H><<<p.grid, kThreads, B::bytes, s>>>(a, m[0], m[1], m[2], m[3]);
-  return cudaGetLastError();
+  return launch_pdl(k_box_tma<MODE, H>, p.grid, dim3(kThreads), B::bytes, s, a, m[0], m[1], m[2], m[3]);
 }
 
 template <int MODE, int H>

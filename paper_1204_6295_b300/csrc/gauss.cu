@@ -333,6 +333,8 @@ __device__ __forceinline__ void gauss_xy_body(const GaussArgs& a, int bx, int by
 
 template <int R>
 __global__ void __launch_bounds__(kThreads) k_gauss_xy(GaussArgs a) {
+  pdl_wait();
+  pdl_release();
   gauss_xy_body<R>(a, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
@@ -436,6 +438,8 @@ __device__ __forceinline__ void gauss_z_body(const GaussArgs& a, int bx, int by,
 
 template <int R, bool WARP>
 __global__ void __launch_bounds__(kZThreads, 4) k_gauss_z(GaussArgs a) {
+  pdl_wait();
+  pdl_release();
   gauss_z_body<R, WARP>(a, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
@@ -497,19 +501,15 @@ cudaError_t launch_split(const GaussArgs& a, const GaussPlan& p, cudaStream_t s)
   GaussArgs xy = a;
   xy.r = a.t;
   dim3 gxy((a.nx + kSX - 1) / kSX, (a.ny + kSY - 1) / kSY, a.nz);
-  k_gauss_xy<R><<<gxy, kThreads, XYLayout<R>::bytes, s>>>(xy);
-  e = cudaGetLastError();
+  e = launch_pdl(k_gauss_xy<R>, gxy, dim3(kThreads), XYLayout<R>::bytes, s, xy);
   if (e != cudaSuccess) return e;
   // z: t -> r (and m)
   GaussArgs zz = a;
   zz.u = a.t;
   zz.zlen = p.zlen;
   dim3 gz((a.nx + kZThreads - 1) / kZThreads, a.ny, (a.nz + p.zlen - 1) / p.zlen);
-  if (a.m != nullptr)
-    k_gauss_z<R, true><<<gz, kZThreads, 0, s>>>(zz);
-  else
-    k_gauss_z<R, false><<<gz, kZThreads, 0, s>>>(zz);
-  return cudaGetLastError();
+  if (a.m != nullptr) return launch_pdl(k_gauss_z<R, true>, gz, dim3(kZThreads), 0, s, zz);
+  return launch_pdl(k_gauss_z<R, false>, gz, dim3(kZThreads), 0, s, zz);
 }
 
 cudaError_t launch_split_any(const GaussArgs& a, const GaussPlan& p, cudaStream_t s) {

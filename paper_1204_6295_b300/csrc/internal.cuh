@@ -268,6 +268,31 @@ struct NormState {
 };
 // *p = v (a one-thread kernel, stream-ordered)
 cudaError_t launch_set_int(int* p, int v, cudaStream_t s);
+
+// Programmatic dependent launch of the per-iteration kernels (box pass, the two
+// Gaussian passes, the norm): a kernel launched this way may be scheduled while
+// its predecessor on the stream finishes; it calls pdl_wait() before touching
+// global memory, which returns once every prerequisite grid has completed and
+// its writes are visible, and pdl_release() to let its own successor be
+// scheduled once all of its CTAs run.  Both are no-ops for a normal launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
 // Raise the release threshold of the current device's default memory pool (once
 // per device), so that the scratch the kernel-level calls allocate stream-ordered
 // is reused from call to call instead of being unmapped at each synchronisation.

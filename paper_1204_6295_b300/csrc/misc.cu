@@ -179,6 +179,8 @@ __device__ __forceinline__ void norm_finalize_body(const float* partials, int np
 }
 
 __global__ void k_norm_finalize(const float* partials, int nparts, NormState st) {
+  pdl_wait();
+  pdl_release();
   norm_finalize_body(partials, nparts, st);
 }
 
@@ -258,8 +260,7 @@ cudaError_t launch_set_int(int* p, int v, cudaStream_t s) {
 }
 
 cudaError_t launch_norm_finalize(const float* partials, int nparts, NormState st, cudaStream_t s) {
-  k_norm_finalize<<<1, kRedThreads, 0, s>>>(partials, nparts, st);
-  return cudaGetLastError();
+  return launch_pdl(k_norm_finalize, dim3(1), dim3(kRedThreads), 0, s, partials, nparts, st);
 }
 
 cudaError_t launch_norm_finalize_batch(const NormBatch& nb, int count, cudaStream_t s) {
