@@ -536,6 +536,8 @@ template <int MODE, int H>
 __global__ void __launch_bounds__(kThreads, 3)
     k_box_tma_batch(const __grid_constant__ BoxBatch bt, const CUtensorMap* __restrict__ maps) {
   extern __shared__ __align__(128) unsigned char smem[];
+  pdl_wait();
+  pdl_release();
   if (!tma_cta_setup<MODE, H>(smem, nullptr)) return;
   uint32_t pa = 0, pb = 0;
   const int total = bt.offset[bt.count];
@@ -638,8 +640,7 @@ cudaError_t launch_tma_batch(const BoxBatch* bt, const CUtensorMap* maps, int gr
   static int set[kMaxDevices] = {};
   cudaError_t e = prepare(k_box_tma_batch<MODE, H>, B::bytes, set);
   if (e != cudaSuccess) return e;
-  k_box_tma_batch<MODE, H><<<grid, kThreads, B::bytes, s>>>(*bt, maps);
-  return cudaGetLastError();
+  return launch_pdl(k_box_tma_batch<MODE, H>, dim3(grid), dim3(kThreads), B::bytes, s, *bt, maps);
 }
 
 template <typename K>

@@ -347,6 +347,8 @@ __device__ __forceinline__ int batch_find(const int* offset, int count, int i) {
 
 template <int R>
 __global__ void __launch_bounds__(kThreads) k_gauss_xy_batch(const __grid_constant__ GaussBatch bt) {
+  pdl_wait();
+  pdl_release();
   const int i = blockIdx.x;
   const int p = batch_find(bt.offset, bt.count, i);
   const int j = i - bt.offset[p];
@@ -445,6 +447,8 @@ __global__ void __launch_bounds__(kZThreads, 4) k_gauss_z(GaussArgs a) {
 
 template <int R, bool WARP>
 __global__ void __launch_bounds__(kZThreads, 4) k_gauss_z_batch(const __grid_constant__ GaussBatch bt) {
+  pdl_wait();
+  pdl_release();
   const int i = blockIdx.x;
   const int p = batch_find(bt.offset, bt.count, i);
   const int j = i - bt.offset[p];
@@ -469,16 +473,13 @@ cudaError_t launch_batch_r(const GaussBatch& xy, int xy_total, const GaussBatch&
     if (e != cudaSuccess) return e;
     set[dev] = 1;
   }
-  if (xy_total > 0) k_gauss_xy_batch<R><<<xy_total, kThreads, XYLayout<R>::bytes, s>>>(xy);
-  e = cudaGetLastError();
+  if (xy_total > 0) e = launch_pdl(k_gauss_xy_batch<R>, dim3(xy_total), dim3(kThreads), XYLayout<R>::bytes, s, xy);
   if (e != cudaSuccess) return e;
   if (z_total > 0) {
-    if (warp)
-      k_gauss_z_batch<R, true><<<z_total, kZThreads, 0, s>>>(z);
-    else
-      k_gauss_z_batch<R, false><<<z_total, kZThreads, 0, s>>>(z);
+    if (warp) return launch_pdl(k_gauss_z_batch<R, true>, dim3(z_total), dim3(kZThreads), 0, s, z);
+    return launch_pdl(k_gauss_z_batch<R, false>, dim3(z_total), dim3(kZThreads), 0, s, z);
   }
-  return cudaGetLastError();
+  return cudaSuccess;
 }
 
 template <int R>

@@ -186,6 +186,8 @@ __global__ void k_norm_finalize(const float* partials, int nparts, NormState st)
 
 // One block per volume of a batch.
 __global__ void k_norm_finalize_batch(const __grid_constant__ NormBatch nb) {
+  pdl_wait();
+  pdl_release();
   const int p = blockIdx.x;
   norm_finalize_body(nb.partials[p], nb.nparts[p], nb.st[p]);
 }
@@ -265,8 +267,7 @@ cudaError_t launch_norm_finalize(const float* partials, int nparts, NormState st
 
 cudaError_t launch_norm_finalize_batch(const NormBatch& nb, int count, cudaStream_t s) {
   if (count < 1) return cudaSuccess;
-  k_norm_finalize_batch<<<count, kRedThreads, 0, s>>>(nb);
-  return cudaGetLastError();
+  return launch_pdl(k_norm_finalize_batch, dim3(count), dim3(kRedThreads), 0, s, nb);
 }
 
 cudaError_t launch_partials_sum(const float* partials, int nparts, int comp, double* out,
