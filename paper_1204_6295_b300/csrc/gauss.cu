@@ -148,7 +148,8 @@ __global__ void __launch_bounds__(kThreads) k_gauss(GaussArgs a) {
 // ---------------------------------------------------------------------------
 constexpr int kSX = 32;        // xy tile
 constexpr int kSY = 32;
-constexpr int kZThreads = 128; // z kernel: threads along x
+constexpr int kZThreads = 128; // z kernel: a CTA is kZX columns along x by kZY rows
+constexpr int kZX = 32, kZY = kZThreads / kZX;   // (the rows' warps share I_m rows in L1 for the warp)
 constexpr int kBX = 4;         // x outputs per x-filter task
 constexpr int kBY = 4;         // y outputs per thread in the y filter
 
@@ -362,8 +363,8 @@ __device__ __forceinline__ void gauss_z_body(const GaussArgs& a, int bx, int by,
   constexpr int KZ = 2 * R + 1;
   if (a.stop != nullptr && *(volatile const int*)a.stop != 0) return;
   const int nx = a.nx, ny = a.ny, nz = a.nz;
-  const int x = bx * kZThreads + threadIdx.x, y = by;
-  if (x >= nx) return;
+  const int x = bx * kZX + threadIdx.x % kZX, y = by * kZY + threadIdx.x / kZX;
+  if (x >= nx || y >= ny) return;
   const size_t plane = (size_t)nx * ny;
   const size_t N = plane * nz;
   const int z0 = bz * a.zlen;
@@ -508,7 +509,7 @@ cudaError_t launch_split(const GaussArgs& a, const GaussPlan& p, cudaStream_t s)
   GaussArgs zz = a;
   zz.u = a.t;
   zz.zlen = p.zlen;
-  dim3 gz((a.nx + kZThreads - 1) / kZThreads, a.ny, (a.nz + p.zlen - 1) / p.zlen);
+  dim3 gz((a.nx + kZX - 1) / kZX, (a.ny + kZY - 1) / kZY, (a.nz + p.zlen - 1) / p.zlen);
   if (a.m != nullptr) return launch_pdl(k_gauss_z<R, true>, gz, dim3(kZThreads), 0, s, zz);
   return launch_pdl(k_gauss_z<R, false>, gz, dim3(kZThreads), 0, s, zz);
 }
@@ -535,7 +536,7 @@ cudaError_t gauss_launch_batch(const GaussBatch& xy, int xy_total, const GaussBa
 
 void gauss_grids(int nx, int ny, int nz, const GaussPlan& p, dim3* xy, dim3* z) {
   *xy = dim3((nx + kSX - 1) / kSX, (ny + kSY - 1) / kSY, nz);
-  *z = dim3((nx + kZThreads - 1) / kZThreads, ny, (nz + p.zlen - 1) / p.zlen);
+  *z = dim3((nx + kZX - 1) / kZX, (ny + kZY - 1) / kZY, (nz + p.zlen - 1) / p.zlen);
 }
 
 int gauss_radius(float sigma, int radius) {
@@ -559,7 +560,7 @@ GaussPlan gauss_plan(int nx, int ny, int nz, int R, int num_sms) {
   if (p.queue) {
     p.smem = 0;
     // z kernel: chunks long enough to amortise the 2R halo planes, enough CTAs
-    const long long cols = (long long)((nx + kZThreads - 1) / kZThreads) * ny;
+    const long long cols = (long long)((nx + kZX - 1) / kZX) * ((ny + kZY - 1) / kZY);
     long long chunks = (8LL * num_sms + cols - 1) / cols;
     if (chunks < 1) chunks = 1;
     long long max_chunks = (nz + 15) / 16;   // at least 16 planes per chunk
