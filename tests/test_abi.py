@@ -23,10 +23,45 @@ def test_library_exports_every_header_function():
 
 
 def test_library_targets_sm_103a():
-    out = subprocess.run(["cuobjdump", "--list-elf", disc.LIB_PATH], capture_output=True, text=True)
-    if out.returncode != 0:
-        pytest.skip("cuobjdump unavailable")
-    assert "sm_103a" in out.stdout
+    from paper_1204_6295_b300 import build
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def _header_struct_fields(name):
+    """(type, field, count) of a C struct typedef in include/disc.h, comments removed."""
+    import re
+    text = open(disc.HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    body = re.search(r"typedef struct \{(.*?)\}\s*" + name + ";", text, flags=re.S).group(1)
+    out = []
+    for decl in body.split(";"):
+        decl = " ".join(decl.split())
+        if not decl:
+            continue
+        m = re.fullmatch(r"(\w+) (.+)", decl)
+        ctype = m.group(1)
+        for item in m.group(2).split(","):
+            item = item.strip()
+            a = re.fullmatch(r"(\w+)(?:\[(\w+)\])?", item)
+            count = a.group(2)
+            if count is not None and not count.isdigit():
+                count = str(getattr(disc, count.replace("DISC_", ""), None) or disc.MAX_LEVELS)
+            out.append((ctype, a.group(1), int(count) if count else 1))
+    return out
+
+
+def test_params_struct_matches_header():
+    """The binding's disc_params mirrors the header field by field (names, types,
+    array lengths), so the struct the library reads is the one Python fills."""
+    ctypes_of = {"int32_t": ctypes.c_int32, "float": ctypes.c_float}
+    fields = _header_struct_fields("disc_params")
+    assert [f[1] for f in fields] == [f[0] for f in disc.Params._fields_]
+    for (ctype, name, count), (pname, ptype) in zip(fields, disc.Params._fields_):
+        base = ctypes_of[ctype]
+        expect = base * count if count > 1 else base
+        assert ctypes.sizeof(ptype) == ctypes.sizeof(expect), name
+        elem = ptype._type_ if issubclass(ptype, ctypes.Array) else ptype
+        assert elem == base and (issubclass(ptype, ctypes.Array) == (count > 1)), name
 
 
 def test_params_default_and_status_strings():
