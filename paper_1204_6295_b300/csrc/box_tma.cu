@@ -216,7 +216,7 @@ __device__ __forceinline__ bool box_tma_body(const BoxArgs& a, int bx, int by, i
   auto issue_a = [&](int zi) {               // thread 0 only
     const uint32_t nb = bytes_a<MODE, H>(st, zi);
     if (nb == 0) return;
-    mbar_expect_tx(&bar[0], nb);
+    mbar_expect_tx(&bar[0], zi == st.zi0 ? nb + a.stall_tx : nb);
     const int zo = zi - (2 * H + 1), zc = zi - H;
     if (zi < nz) tma_load_3d(wn, map_w, x0 - B::XW, y0 - B::EXT - H, zi, &bar[0]);
     if (zo >= st.zi0) tma_load_3d(wo, map_w, x0 - B::XW, y0 - B::EXT - H, zo, &bar[0]);
@@ -631,7 +631,12 @@ cudaError_t launch_tma(const BoxArgs& a, const BoxPlan& p, cudaStream_t s) {
   if (!encode_maps<MODE, H>(a, m)) return cudaErrorInvalidValue;
   cudaError_t e = prepare(k_box_tma<MODE, H>, B::bytes, set);
   if (e != cudaSuccess) return e;
-  return launch_pdl(k_box_tma<MODE, H>, p.grid, dim3(kThreads), B::bytes, s, a, m[0], m[1], m[2], m[3]);
+  BoxArgs b = a;
+  // DISC_TEST_TMA_STALL=1: the iteration pass waits for 16 bytes no copy delivers
+  // (exercises the bounded wait and the timeout report; nothing else changes)
+  const char* stall = std::getenv("DISC_TEST_TMA_STALL");
+  b.stall_tx = (MODE == kModeIterate && stall != nullptr && stall[0] == '1') ? 16u : 0u;
+  return launch_pdl(k_box_tma<MODE, H>, p.grid, dim3(kThreads), B::bytes, s, b, m[0], m[1], m[2], m[3]);
 }
 
 template <int MODE, int H>

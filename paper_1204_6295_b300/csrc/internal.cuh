@@ -70,6 +70,9 @@ struct BoxArgs {
   float hu0, a_min, a_max;
   int ratio_only;
   int u_is_dr;          // kModeIterate: write u = dr instead of r + dr (smoothing of dr, Sec. 2.1)
+  // test of the bounded waits (bulk-copy-fed pass only): bytes the first copy group
+  // of a CTA is armed for beyond what its copies deliver, so that its wait gives up
+  uint32_t stall_tx;
 };
 
 struct BoxPlan {

@@ -140,3 +140,36 @@ def test_registration_bitwise(disc):
         else:
             fields.append(run())
     np.testing.assert_array_equal(fields[0], fields[1])
+
+
+def test_bounded_wait_reports_timeout_and_device_stays_usable(disc):
+    """A copy group armed for 16 bytes more than its copies deliver (the
+    DISC_TEST_TMA_STALL hook of the iteration pass) never completes: the wait gives
+    up after about a second, the CTA drains and returns, the context reports
+    DISC_ERR_TIMEOUT and then refuses further work, and a new context on the same
+    device runs normally."""
+    pair = phantom.ellipsoid_pair(64, 48, 16, seed=3)
+    kw = dict(patch=(3, 3, 3), sigma=1.0, levels=1, iters=(1,))
+    old = os.environ.get("DISC_TEST_TMA_STALL")
+    os.environ["DISC_TEST_TMA_STALL"] = "1"
+    try:
+        reg = disc.Registration(**kw)
+        reg.set_images(pair.ct, pair.cbct)          # the static pass is not stalled
+        with pytest.raises(disc.DiscError) as e:
+            reg.iterate(-1)
+        assert e.value.status == 6                  # DISC_ERR_TIMEOUT
+        with pytest.raises(disc.DiscError) as e2:
+            reg.iterate(-1)
+        assert e2.value.status == 3                 # DISC_ERR_STATE: the failure is sticky
+        reg.close()
+    finally:
+        if old is None:
+            del os.environ["DISC_TEST_TMA_STALL"]
+        else:
+            os.environ["DISC_TEST_TMA_STALL"] = old
+    with disc.Registration(**kw) as reg:
+        reg.set_images(pair.ct, pair.cbct)
+        done, _ = reg.iterate(-1)
+        r = reg.get_field()
+    assert done == 1 and np.isfinite(r).all() and np.abs(r).max() > 0
+    disc.k_check_error()
