@@ -623,7 +623,11 @@ disc_status disc_set_images(disc_ctx* ctx, const float* ct, const float* cbct, i
       }
       v.norm_lo = lo;
       v.norm_hi = hi;
-      cudaError_t e = cudaMalloc(&v.Im, v.N * sizeof(float));
+      // DISC_FAULT=alloc: host-side fault injection, the first allocation reports
+      // an out-of-memory error (tests the recovery of a context)
+      const char* fault = std::getenv("DISC_FAULT");
+      cudaError_t e = (fault != nullptr && std::strcmp(fault, "alloc") == 0) ? cudaErrorMemoryAllocation
+                                                                             : cudaMalloc(&v.Im, v.N * sizeof(float));
       if (e == cudaSuccess) e = cudaMalloc(&v.Is, v.N * sizeof(float));
       if (e == cudaSuccess) e = cudaMalloc(&v.zs, v.N * sizeof(float));
       if (e == cudaSuccess) e = cudaMalloc(&v.m, v.N * sizeof(float));
