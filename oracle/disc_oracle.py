@@ -71,7 +71,8 @@ def level_dims(dims, levels):
 
 
 def downsample2(img):
-    """Mean over each 2x2x2 cell; a partial last cell averages its in-bounds voxels."""
+    """Sec. 2.3 multi-scale strategy (reading R13): mean over each 2x2x2 cell; a
+    partial last cell averages its in-bounds voxels."""
     img = np.asarray(img, np.float64)
     nz, ny, nx = img.shape
     cz, cy, cx = (nz + 1) // 2, (ny + 1) // 2, (nx + 1) // 2
@@ -87,7 +88,8 @@ def downsample2(img):
 
 
 def _clamped_linear_coords(n_fine, n_coarse):
-    """Index pairs and weights mapping fine voxel i to coarse position (i - 0.5)/2."""
+    """Reading R13 (cell-centred up-sampling): index pairs and weights mapping fine
+    voxel i to coarse position (i - 0.5)/2, clamped."""
     pos = (np.arange(n_fine, dtype=np.float64) - 0.5) / 2.0
     pos = np.clip(pos, 0.0, n_coarse - 1)
     i0 = np.floor(pos).astype(np.int64)
@@ -127,7 +129,8 @@ def upsample_field2(r_coarse, fine_shape):
 # ---------------------------------------------------------------------------
 
 def warp(I_m, r):
-    """Deformed moving image I_m^(k)(x) = I_m(x + r(x)), trilinear interpolation."""
+    """Deformed moving image I_m^(k)(x) = I_m(x + r(x)) (Sec. 2.1; Sec. 2.3 kernel 5),
+    trilinear interpolation with the sample position clamped to the volume (R6)."""
     I_m = np.asarray(I_m, np.float64)
     r = np.asarray(r, np.float64)
     nz, ny, nx = I_m.shape
@@ -151,7 +154,7 @@ def warp(I_m, r):
 
 
 def warp_region(I_m, r_region, origin):
-    """I_m(x + r(x)) for the voxels x of a sub-box of the grid.
+    """I_m(x + r(x)) (Sec. 2.1, reading R6) for the voxels x of a sub-box of the grid.
 
     ``r_region`` is the field on the sub-box ([3][dz][dy][dx]) whose first
     voxel is ``origin`` = (x0, y0, z0) of the full grid of ``I_m``; used to
@@ -183,7 +186,8 @@ def warp_region(I_m, r_region, origin):
 # ---------------------------------------------------------------------------
 
 def box_sum(X, half):
-    """Sum of X over the box |dx|<=hx, |dy|<=hy, |dz|<=hz clipped to the volume.
+    """Patch sum of Eq. (3) (truncated box, reading R7): the sum of X over the box
+    |dx|<=hx, |dy|<=hy, |dz|<=hz clipped to the volume.
 
     ``half`` = (hx, hy, hz).  Out-of-volume positions contribute nothing.
     """
@@ -208,7 +212,8 @@ def box_sum(X, half):
 
 
 def box_count(shape, half):
-    """Number of in-volume voxels n(x) of the truncated box around each voxel."""
+    """n(x) of Eq. (3) for the truncated box (reading R7): the number of in-volume
+    voxels of the box around each voxel."""
     return box_sum(np.ones(shape), half)
 
 
@@ -260,7 +265,8 @@ def correct(m, I_s, half, var_floor=1e-6):
 # ---------------------------------------------------------------------------
 
 def gradient(f):
-    """Gradient of an image, returned as [3][nz][ny][nx] with components (x, y, z)."""
+    """Image gradient of Sec. 2.3 kernel 3 (reading R10: central differences inside,
+    one-sided at the faces, voxel units), returned as [3][nz][ny][nx], components (x, y, z)."""
     f = np.asarray(f, np.float64)
     g = np.zeros((3,) + f.shape)
     for comp in range(3):
@@ -284,7 +290,8 @@ def gradient(f):
 # ---------------------------------------------------------------------------
 
 def force(m, f, mode=FORCE_THIRION, den_floor=1e-9):
-    """Displacement increment dr at every voxel ([3][nz][ny][nx])."""
+    """Demons force of Eq. (1) (Algorithm A1 step 4; readings R1, R2, R11): the
+    displacement increment dr at every voxel ([3][nz][ny][nx])."""
     m = np.asarray(m, np.float64)
     f = np.asarray(f, np.float64)
     diff = f - m
@@ -307,7 +314,8 @@ def force(m, f, mode=FORCE_THIRION, den_floor=1e-9):
 # ---------------------------------------------------------------------------
 
 def gaussian_taps(sigma, radius=0):
-    """Unnormalised taps w_i = exp(-i^2 / (2 sigma^2)), i = -R..R (R = ceil(3 sigma))."""
+    """Algorithm A1 step 6 (reading R12): unnormalised taps w_i = exp(-i^2 / (2 sigma^2)),
+    i = -R..R (R = ceil(3 sigma))."""
     if radius <= 0:
         radius = int(math.ceil(3.0 * sigma))
     i = np.arange(-radius, radius + 1, dtype=np.float64)
@@ -315,7 +323,8 @@ def gaussian_taps(sigma, radius=0):
 
 
 def gaussian_smooth(v, sigma, radius=0):
-    """Separable Gaussian of a scalar volume, renormalised over in-volume taps."""
+    """Algorithm A1 step 6 (reading R12): separable Gaussian of a scalar volume,
+    renormalised over the in-volume taps of each axis."""
     w = gaussian_taps(sigma, radius)
     R = (len(w) - 1) // 2
     out = np.asarray(v, np.float64)
@@ -351,13 +360,15 @@ def gaussian_smooth_field(r, sigma, radius=0):
 # ---------------------------------------------------------------------------
 
 def relative_norm(dr, r):
-    """l^(k) = sum |dr^(k+1)| / sum |r^(k)|."""
+    """Convergence norm of Sec. 2.3 (reading R5): l^(k) = sum |dr^(k+1)| / sum |r^(k)|."""
     num = np.sqrt((np.asarray(dr, np.float64) ** 2).sum(axis=0)).sum()
     den = np.sqrt((np.asarray(r, np.float64) ** 2).sum(axis=0)).sum()
     return math.inf if den == 0.0 else num / den
 
 
 def should_stop(history, eps, window=10):
+    """Stop rule of Sec. 2.3 (reading R5): after at least `window` iterations, stop
+    once l^(k - window) - l^(k) <= eps."""
     k = len(history) - 1
     if eps <= 0 or k < window:
         return False
@@ -418,7 +429,8 @@ def mask_xi(m, I_s, a, valid, hu0, a_min, a_max):
 
 
 def _shifted(X, d, fill):
-    """Y[i] = X[i + d] where i + d is inside the volume, else `fill`."""
+    """Helper of the box T of Eqs. (8)-(10): Y[i] = X[i + d] where i + d is inside the
+    volume, else `fill`."""
     Y = np.full(X.shape, fill, dtype=X.dtype)
     src, dst = [], []
     for ax, dd in zip((2, 1, 0), d):
@@ -559,6 +571,8 @@ def iteration(I_m, I_s, r, p: Params, mask: MaskState = None):
 
 
 def build_pyramid(img, levels):
+    """Sec. 2.3 multi-scale strategy (reading R13): finest level first, each next
+    level the 2x2x2 mean of the previous."""
     pyr = [np.asarray(img, np.float64)]
     for _ in range(1, levels):
         pyr.append(downsample2(pyr[-1]))
@@ -611,13 +625,16 @@ def register(I_m, I_s, p: Params, return_history=False):
 # ---------------------------------------------------------------------------
 
 def ssd_loss(I_m, I_s, r, half, var_floor=1e-6):
+    """Reading R15 (the differentiable form): L(r) = sum_x (I_m(x + r(x)) - I'_s(x))^2
+    with I'_s the moment-matched CBCT of Eqs. (5)-(6)."""
     m = warp(I_m, r)
     f = correct(m, I_s, half, var_floor)
     return float(((m - f) ** 2).sum())
 
 
 def warp_coord_gradient(I_m, r):
-    """d I_m(p) / d p at p = x + r(x) for trilinear interpolation, [3][...].
+    """d I_m(p) / d p at p = x + r(x) for the trilinear interpolation of Sec. 2.1
+    (reading R6), [3][...].
 
     Zero along an axis where the sample position is clamped to the volume.
     """
@@ -655,7 +672,8 @@ def warp_coord_gradient(I_m, r):
 
 
 def ssd_grad(I_m, I_s, r, half, var_floor=1e-6):
-    """dL/dr by the adjoint of warp -> patch moments -> correction -> SSD.
+    """Reading R15: dL/dr by the adjoint of warp -> patch moments (Eq. 3) ->
+    correction (Eqs. 5-6) -> SSD.
 
     f(x) = z_s(x) sigma_m(x) + mu_m(x) with z_s = (I_s - E(S)) / STD(S)
     (algebraically a I_s + b of Eqs. 5-6).  Back-propagation:
@@ -714,6 +732,7 @@ def ssd_grad(I_m, I_s, r, half, var_floor=1e-6):
 # ---------------------------------------------------------------------------
 
 def _f32(x):
+    """float32 scalar (readings R21, R22 take their integer decisions in float32)."""
     return np.float32(x)
 
 
@@ -747,6 +766,8 @@ def nmi(A, B, bins=64):
 
 
 def _canny_taps(sigma):
+    """Reading R22: Gaussian taps of the Canny smoothing (Eq. 11 names the edges),
+    normalised, float32, radius ceil(3 sigma)."""
     R = int(math.ceil(3.0 * sigma))
     i = np.arange(-R, R + 1, dtype=np.float64)
     w = np.exp(-i * i / (2.0 * sigma * sigma))
@@ -754,7 +775,7 @@ def _canny_taps(sigma):
 
 
 def _smooth_axis(P, w, R, axis):
-    """One separable pass in float32: taps in ascending order, then the
+    """Reading R22: one separable pass in float32: taps in ascending order, then the
     renormalisation over the in-slice taps (product, sum, division in float32)."""
     n = P.shape[axis]
     out = np.zeros(P.shape, np.float32)
@@ -783,6 +804,8 @@ def _smooth_axis(P, w, R, axis):
 
 
 def _diff_axis(S, axis):
+    """Reading R22: central difference along one axis of a slice in float32,
+    one-sided at the ends."""
     n = S.shape[axis]
     g = np.zeros(S.shape, np.float32)
     if n < 2:
