@@ -141,6 +141,7 @@ void free_levels(disc_ctx* c) {
     cudaFree(v.hsum);
     cudaFree(v.sd);
     cudaFree(v.ab);
+    cudaFree(v.isab);
     cudaFree(v.dm);
     cudaFree(v.stamp);
     cudaFree(v.kbits);
@@ -209,8 +210,7 @@ cudaError_t queue_mask_fill(disc_ctx* c, int l, const int* stop) {
   a.is = v.Is;
   a.sd = v.sd;
   a.out = v.dm;
-  a.a_out = v.ab;
-  a.b_out = v.ab + v.N;
+  a.isab = v.isab;
   a.stamp = v.stamp;
   a.count = v.cnt;
   a.hu0 = c->mask_hu0;
@@ -221,10 +221,8 @@ cudaError_t queue_mask_fill(disc_ctx* c, int l, const int* stop) {
   a.inv_qscale = 1.0f / c->qs_m;
   e = box_launch(kModeMaskAB, a, v.pm, c->s);
   FillArgs f{};
-  f.is = v.Is;
+  f.isab = v.isab;
   f.m = v.m;
-  f.a = v.ab;
-  f.b = v.ab + v.N;
   f.d = v.dm;
   f.stamp = v.stamp;
   f.cnt = v.cnt;
@@ -641,6 +639,7 @@ disc_status disc_set_images(disc_ctx* ctx, const float* ct, const float* cbct, i
         if (v.pm.grid.x == 0) e = cudaErrorInvalidConfiguration;
         if (e == cudaSuccess) e = cudaMalloc(&v.sd, v.N * sizeof(float));
         if (e == cudaSuccess) e = cudaMalloc(&v.ab, 2 * v.N * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&v.isab, v.N * sizeof(float4));
         if (e == cudaSuccess) e = cudaMalloc(&v.dm, v.N * sizeof(float));
         if (e == cudaSuccess) e = cudaMalloc(&v.stamp, v.N * sizeof(int));
         if (e == cudaSuccess) e = cudaMalloc(&v.kbits, 2 * sizeof(unsigned) * (size_t)fill_words(v.nx, v.ny, v.nz));
@@ -1089,9 +1088,10 @@ disc_status disc_k_correct_masked(const float* m, const float* Is, const float* 
   a.zs = zs;
   a.is = Is;
   a.sd = sd;
+  float4* isab = nullptr;   // the fill's working set, unpacked into av, bv at the end
+  if (e == cudaSuccess) e = cudaMallocAsync(&isab, sizeof(float4) * N, s);
   a.out = d;
-  a.a_out = av;
-  a.b_out = bv;
+  a.isab = isab;
   a.stamp = stamp;
   a.count = cnt;
   a.hu0 = hu0;
@@ -1099,10 +1099,8 @@ disc_status disc_k_correct_masked(const float* m, const float* Is, const float* 
   a.a_max = a_max;
   if (e == cudaSuccess) st = klaunch(kModeMaskAB, a, s);
   FillArgs f{};
-  f.is = Is;
+  f.isab = isab;
   f.m = m;
-  f.a = av;
-  f.b = bv;
   f.d = d;
   f.stamp = stamp;
   f.cnt = cnt;
@@ -1126,6 +1124,11 @@ disc_status disc_k_correct_masked(const float* m, const float* Is, const float* 
     e = launch_fill_pass(f, s);
   }
   if (e == cudaSuccess && st == DISC_OK && remaining_out) e = launch_fill_remaining(cnt, fill_passes, remaining_out, s);
+  if (e == cudaSuccess && st == DISC_OK) e = launch_unpack_ab(isab, av, bv, (int64_t)N, s);
+  if (isab) {
+    const cudaError_t ef = cudaFreeAsync(isab, s);
+    if (e == cudaSuccess) e = ef;
+  }
   cudaError_t e2 = cudaFreeAsync(work, s);
   if (st != DISC_OK) return st;
   if (e != cudaSuccess || e2 != cudaSuccess) {

@@ -74,13 +74,11 @@ static __device__ __forceinline__ void mask_epilogue(const BoxArgs& a, size_t g,
   const float av = sd > 0.0f ? sg / sd : 0.0f;
   const bool xi = !(sd > 0.0f) || fabsf(vc - is) > a.hu0 || av < a.a_min || av > a.a_max;
   if (!xi) {
-    a.a_out[g] = av;
-    a.b_out[g] = (vc + dc) - av * fmaf(-zsv, sd, is);
+    a.isab[g] = make_float4(is, av, (vc + dc) - av * fmaf(-zsv, sd, is), 0.0f);
     a.out[g] = fmaf(zsv, sg, dc);
     a.stamp[g] = 0;
   } else {
-    a.a_out[g] = 0.0f;
-    a.b_out[g] = 0.0f;
+    a.isab[g] = make_float4(is, 0.0f, 0.0f, 0.0f);
     a.out[g] = -vc;
     a.stamp[g] = -1;
     atomicAdd(a.count, 1);

@@ -36,7 +36,8 @@ struct Level {
   int norm_lo = 0, norm_hi = 0;   // planes entering those sums (all when norm_hi <= norm_lo)
   // mask and fill (mask_mode 1)
   float* sd = nullptr;   // STD(S)
-  float* ab = nullptr;   // a [N] then b [N]
+  float* ab = nullptr;   // a [N] then b [N] (the ratio a of the median a_m)
+  float4* isab = nullptr;   // [N] (I_s, a, b, 0): the mask pass writes it, the fill completes it
   float* dm = nullptr;   // I'_s - m of the masked correction
   int* stamp = nullptr;  // 0 known, p filled by pass p, -1 not filled
   unsigned* kbits = nullptr;   // [2][fill_words] known-voxel bit masks of the fill passes

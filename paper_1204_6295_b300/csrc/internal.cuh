@@ -63,8 +63,9 @@ struct BoxArgs {
   // ratio_only: write only a = STD(M)/STD(S) (-1 where undefined) into a_out.
   const float* is;
   const float* sd;
-  float* a_out;
+  float* a_out;         // ratio_only: a per voxel (planar)
   float* b_out;
+  float4* isab;         // kModeMaskAB: (I_s, a, b, 0) per voxel, the fill's working set
   int* stamp;
   int* count;
   float hu0, a_min, a_max;
@@ -182,10 +183,8 @@ cudaError_t launch_ssd_final(const float* Im, const float* r, const float* m, co
 // Mask and fill of a, b (Eqs. 7-10), mask.cu
 // ----------------------------------------------------------------------------
 struct FillArgs {
-  const float* is;      // I_s
+  float4* isab;         // (I_s, a, b, 0) per voxel: known a, b in, filled a, b out
   const float* m;       // I_m^(k)
-  float* a;             // a, b: known values in, filled values out
-  float* b;
   float* d;             // I'_s - m, written where a voxel is filled
   int* stamp;           // 0: xi = 0; p: filled by pass p; -1: not yet
   const unsigned* kin;  // known before this pass: bit masks, fill_words() words
@@ -205,6 +204,8 @@ struct FillArgs {
 // One fill pass: the dilation of the known mask kin into kout, then the voxels
 // of kout not in kin.  Before pass 1, launch_fill_pack sets kin from the stamps.
 cudaError_t launch_fill_pass(const FillArgs& f, cudaStream_t s);
+// a, b out of the interleaved fill buffer into planar arrays.
+cudaError_t launch_unpack_ab(const float4* isab, float* a, float* b, int64_t n, cudaStream_t s);
 int fill_words(int nx, int ny, int nz);
 int fill_front_blocks(int nx, int ny, int nz);
 cudaError_t launch_fill_pack(const int* stamp, unsigned* k, int nx, int ny, int nz, cudaStream_t s);

@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(kFillThreads) k_fill_pass(FillArgs f) {
     const int z = (int)(g / plane);
     const int rem = (int)(g - (size_t)z * plane);
     const int y = rem / nx, x = rem - y * nx;
-    const float isx = __ldg(f.is + g);
+    const float isx = f.isab[g].x;
     float num_a = 0.0f, num_b = 0.0f, den = 0.0f;
     const int x_lo = max(0, x - f.tx), x_hi = min(nx - 1, x + f.tx);
     const int w0 = x_lo >> 5, w1 = x_hi >> 5, sh = x_lo & 31;
@@ -187,18 +187,17 @@ __global__ void __launch_bounds__(kFillThreads) k_fill_pass(FillArgs f) {
         while (bits) {
           const int j = __ffsll((long long)bits) - 1;
           bits &= bits - 1ull;
-          const size_t gi = row + j;
-          const float e = (__ldg(f.is + gi) - isx) * f.inv_h;
+          const float4 q = f.isab[row + j];              // (I_s, a, b) of a known neighbour
+          const float e = (q.x - isx) * f.inv_h;
           const float wt = expf(-fminf(e * e, 80.0f));    // Eq. (10), exponent capped
-          num_a = fmaf(wt, f.a[gi], num_a);
-          num_b = fmaf(wt, f.b[gi], num_b);
+          num_a = fmaf(wt, q.y, num_a);
+          num_b = fmaf(wt, q.z, num_b);
           den += wt;
         }
       }
     if (den > 0.0f) {
       const float av = num_a / den, bv = num_b / den;     // Eqs. (8), (9)
-      f.a[g] = av;
-      f.b[g] = bv;
+      f.isab[g] = make_float4(isx, av, bv, 0.0f);
       f.d[g] = fmaf(av, isx, bv) - __ldg(f.m + g);        // d = I'_s - m
       f.stamp[g] = f.pass;
       ++nfilled;
@@ -390,6 +389,23 @@ cudaError_t launch_fill_pack(const int* stamp, unsigned* k, int nx, int ny, int 
 
 int fill_front_blocks(int nx, int ny, int nz) {
   return (fill_words(nx, ny, nz) + kFrontWords - 1) / kFrontWords;
+}
+
+__global__ void k_unpack_ab(const float4* __restrict__ isab, float* __restrict__ a, float* __restrict__ b,
+                            int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 q = isab[i];
+    a[i] = q.y;
+    b[i] = q.z;
+  }
+}
+
+cudaError_t launch_unpack_ab(const float4* isab, float* a, float* b, int64_t n, cudaStream_t s) {
+  long long blocks = (n + 255) / 256;
+  if (blocks > 148 * 8) blocks = 148 * 8;
+  if (blocks < 1) blocks = 1;
+  k_unpack_ab<<<(int)blocks, 256, 0, s>>>(isab, a, b, n);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_fill_pass(const FillArgs& f, cudaStream_t s) {
