@@ -404,6 +404,72 @@ def time_batched(disc, torch, dist, steps=2):
                     "after the other; value = all ranks' voxel-iterations / slowest rank's time"}
 
 
+MIXED_HEADNECK_PAIRS = 4
+
+
+def time_mixed_batch(disc, torch, w, pair_dev, dist, steps=1):
+    """The large pair batched with four head-and-neck-sized pairs (256x256x128)
+    under the large pair's parameters, against the same five pairs run one
+    after the other as separate contexts."""
+    from paper_1204_6295_b300 import phantom
+    hn = [(256, 256, 128)] * MIXED_HEADNECK_PAIRS
+    images = [pair_dev] + [(torch.from_numpy(c).cuda(), torch.from_numpy(b).cuda())
+                           for c, b in phantom.batch_pair_images(len(hn), sizes=hn)]
+    dims = [tuple(w["dims"])] + hn
+    units = sum(schedule_units(dict(w, dims=d)) for d in dims)
+    kw = dict(patch=w["patch"], sigma=w["sigma"], levels=w["levels"], iters=w["iters"])
+    s = torch.cuda.current_stream()
+
+    def timed(step):
+        step()                                    # warm-up (graphs, tuning)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(steps):
+            step()
+        e1.record(s)
+        torch.cuda.synchronize()
+        return reduce_max(dist, e0.elapsed_time(e1) / steps / 1e3)
+
+    batch = disc.Batch(len(images), **kw)
+    for i, (ct, cbct) in enumerate(images):
+        batch.set_images(i, ct, cbct)
+
+    def batch_step():
+        batch.restart()
+        batch.iterate(-1)
+
+    t_batch = timed(batch_step)
+    batch.close()
+    regs = []
+    for ct, cbct in images:
+        reg = disc.Registration(**kw)
+        reg.set_images(ct, cbct)
+        nz, ny, nx = ct.shape
+        cz, cy, cx = level_dims((nx, ny, nz), w["levels"])[-1][::-1]
+        regs.append((reg, torch.zeros((3, cz, cy, cx), dtype=torch.float32, device="cuda")))
+
+    def loop_step():
+        for reg, z in regs:
+            reg.set_field(w["levels"] - 1, z)
+            reg.iterate(-1, sync=False)
+
+    t_loop = timed(loop_step)
+    for reg, _ in regs:
+        reg.close()
+    world = dist.get_world_size() if dist else 1
+    return {"value": job_throughput(units, world, t_batch), "unit": UNIT,
+            "plain_loop_value": job_throughput(units, world, t_loop),
+            "speedup_vs_plain_loop": t_loop / t_batch, "ms_per_step": t_batch * 1e3,
+            "plain_loop_ms_per_step": t_loop * 1e3, "voxel_iterations_per_step": units,
+            "pairs": [list(d) for d in dims],
+            "what": "the large pair and four 256x256x128 head-and-neck pairs in one disc_batch "
+                    "(patch, sigma and schedule of the large pair) vs the five pairs' separate "
+                    "contexts one after the other; every rank runs the same five pairs"}
+
+
 def reduce_max(dist, seconds, device="cuda"):
     """Largest value over the ranks of the process group (the step time of the job)."""
     if dist is None:
@@ -477,6 +543,8 @@ def run_ours(args, w, rank, world, local_rank):
 
     batched = None if args.no_batched else time_batched(disc, torch, dist)
     masked = time_masked(disc, torch, w, (ct, cbct), dist)
+    mixed = (time_mixed_batch(disc, torch, w, (ct, cbct), dist)
+             if args.workload == "large-512x512x256" and not args.no_batched else None)
 
     # end to end through the public API with host buffers (pinned)
     ct_h = torch.from_numpy(pair.ct).pin_memory()
@@ -534,6 +602,7 @@ def run_ours(args, w, rank, world, local_rank):
                   "batched": batched,
                   "differentiable": diff_form,
                   "masked": masked,
+                  **({"batched_with_headneck": mixed} if mixed else {}),
                   "effective_hbm_frac_32B_model": value * 1e9 * 32 / (peak * 1e9)},
         "e2e": e2e,
         "gpu_launches": launches * args.steps,

@@ -270,17 +270,21 @@ def _batch_pair_images(args):
     return p.ct, p.cbct
 
 
-def batch_pair_images(n_pairs=16, seed=SEED_BASE + 4, workers=None, indices=None):
+def batch_pair_images(n_pairs=16, seed=SEED_BASE + 4, workers=None, indices=None, sizes=None):
     """(CT, CBCT) of the batched workload's pairs, drawn in parallel processes.
 
-    n_pairs head-and-neck pairs of uneven size (2s, 2s, s), s from 64 to 160;
-    with `indices`, only those pairs (a rank's share), in that order.  The
-    worker processes are started with 'spawn' (safe after CUDA is initialised).
+    n_pairs head-and-neck pairs of uneven size (2s, 2s, s), s from 64 to 160,
+    or of the given (nx, ny, nz) `sizes`; with `indices`, only those pairs (a
+    rank's share), in that order.  The worker processes are started with
+    'spawn' (safe after CUDA is initialised).
     """
     import multiprocessing as mp
     import os
     from concurrent.futures import ProcessPoolExecutor
-    sizes = batch_sizes(n_pairs, seed)
+    if sizes is None:
+        sizes = batch_sizes(n_pairs, seed)
+    elif len(sizes) != n_pairs:
+        raise ValueError("one size per pair")
     if indices is None:
         indices = range(n_pairs)
     jobs = [(i, sizes[i], seed) for i in indices]
