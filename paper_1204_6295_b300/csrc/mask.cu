@@ -60,14 +60,18 @@ __device__ __forceinline__ unsigned dilate_word(const FillArgs& f, long long i, 
   const int w = (int)(i % nwx);
   const long long row = i / nwx;
   const int y = (int)(row % ny), z = (int)(row / ny);
-  unsigned acc = 0u;
+  // union over the box's rows of words w - 1, w, w + 1; the x dilation is
+  // applied once to the union (shifts distribute over OR)
+  unsigned uc = 0u, ul = 0u, uh = 0u;
   for (int zz = max(0, z - f.tz); zz <= min(nz - 1, z + f.tz); ++zz)
     for (int yy = max(0, y - f.ty); yy <= min(ny - 1, y + f.ty); ++yy) {
       const unsigned* r = f.kin + ((long long)zz * ny + yy) * nwx;
-      const unsigned c = r[w], l = w > 0 ? r[w - 1] : 0u, h = w + 1 < nwx ? r[w + 1] : 0u;
-      acc |= c;
-      for (int d = 1; d <= f.tx; ++d) acc |= (c << d) | (l >> (32 - d)) | (c >> d) | (h << (32 - d));
+      uc |= r[w];
+      if (w > 0) ul |= r[w - 1];
+      if (w + 1 < nwx) uh |= r[w + 1];
     }
+  unsigned acc = uc;
+  for (int d = 1; d <= f.tx; ++d) acc |= (uc << d) | (ul >> (32 - d)) | (uc >> d) | (uh << (32 - d));
   return w == nwx - 1 ? (acc & tail) : acc;
 }
 
@@ -160,7 +164,9 @@ __global__ void __launch_bounds__(kFrontWords) k_fill_front_list(FillArgs f) {
 
 // Eqs. (8)-(10) for the listed front voxels, summing the neighbours known before
 // the pass (the set bits of K_p in the voxel's box, rows in z, y order and each
-// row in increasing x).
+// row in increasing x).  A row's entries are all loaded (independent loads in
+// flight) and the unknown ones enter with weight 0, which leaves every sum
+// unchanged: the working set holds finite values everywhere.
 __global__ void __launch_bounds__(kFillThreads) k_fill_pass(FillArgs f) {
   if (pass_idle(f)) return;
   const int n = f.nfront[0];
@@ -176,7 +182,8 @@ __global__ void __launch_bounds__(kFillThreads) k_fill_pass(FillArgs f) {
     float num_a = 0.0f, num_b = 0.0f, den = 0.0f;
     const int x_lo = max(0, x - f.tx), x_hi = min(nx - 1, x + f.tx);
     const int w0 = x_lo >> 5, w1 = x_hi >> 5, sh = x_lo & 31;
-    const unsigned long long span = (1ull << (x_hi - x_lo + 1)) - 1ull;
+    const int xn = x_hi - x_lo + 1;
+    const unsigned long long span = (1ull << xn) - 1ull;
     for (int zz = max(0, z - f.tz); zz <= min(nz - 1, z + f.tz); ++zz)
       for (int yy = max(0, y - f.ty); yy <= min(ny - 1, y + f.ty); ++yy) {
         const size_t rw = ((size_t)zz * ny + yy) * nwx;
