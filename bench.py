@@ -642,6 +642,22 @@ def run_profile_once(w):
     return 0
 
 
+def run_profile_masked(w, iters=2):
+    """`iters` masked iterations (Eqs. 7-10) at the finest level only, from r = 0
+    (for ncu captures of the fill passes): one context with one level."""
+    import torch
+    from paper_1204_6295_b300 import disc
+    pair = make_pair(w)
+    ct = torch.from_numpy(pair.ct).cuda()
+    cbct = torch.from_numpy(pair.cbct).cuda()
+    with disc.Registration(patch=w["patch"], sigma=w["sigma"], levels=1, iters=(iters,), mask_mode=1) as reg:
+        reg.set_images(ct, cbct)
+        done, _ = reg.iterate(-1)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_masked": True, "workload": list(w["dims"]), "iterations": done}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -653,6 +669,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 16-pair batched form")
     ap.add_argument("--profile-once", action="store_true",
                     help="launch each per-iteration kernel once at the finest level and exit")
+    ap.add_argument("--profile-masked", type=int, default=0, metavar="K",
+                    help="run K masked iterations at the finest level and exit")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus > 0 else 1)))
@@ -662,6 +680,8 @@ def main():
     w = WORKLOADS[args.workload]
     if args.profile_once:
         return run_profile_once(w)
+    if args.profile_masked > 0:
+        return run_profile_masked(w, args.profile_masked)
     if args.impl == "reference":
         return run_reference(args, w, rank, world)
     return run_ours(args, w, rank, world, local_rank)
