@@ -13,6 +13,9 @@
 //     plane that leaves the window, and the F box of m at the next centre plane;
 //   group B, issued at the top of step z and awaited after the x sums:
 //     the F box of zs at the centre plane and the r tile of the force plane.
+// The first planes of the window, which only enter the z sums, come as bursts of
+// W boxes staged over the buffers the march has not used yet (one wait per
+// burst, not per plane).
 // Out-of-volume parts of a box arrive as zeros, which is exactly what the
 // truncated sums need, so the march has no per-element bounds tests and no
 // per-thread global loads.  A box starts on a 16-byte boundary in x (x offsets
@@ -87,6 +90,9 @@ struct TmaLayout {
   static constexpr size_t o_red = o_dr + (EXT ? 12 * (size_t)FN : 0);   // norm partials
   static constexpr size_t o_bar = (o_red + 8 * (kThreads / 32) + 7) & ~(size_t)7;   // 2 mbarriers
   static constexpr size_t bytes = o_bar + 16;
+  // W boxes the warm-up burst stages at once, over every buffer below o_red
+  static constexpr int WST = (int)(o_red / al128(WB));
+  static_assert(WST >= 2, "staging area");
 };
 
 // ---- PTX wrappers: mbarrier and bulk tensor copies ---------------------------
@@ -268,11 +274,52 @@ __device__ __forceinline__ bool box_tma_body(const BoxArgs& a, int bx, int by, i
 
   float acc0 = 0.0f, acc1 = 0.0f;
   const float keep = a.u_is_dr ? 0.0f : 1.0f;   // the force stage writes u = keep r + dr
-  if (tid == 0) issue_a(st.zi0);
+
+  // ---- warm-up: planes zi0 .. zw - 1 only enter the z sums (no plane leaves the
+  // window and no centre plane is due), so they arrive as bursts of W boxes in the
+  // buffers the march has not yet used, one copy wait per burst instead of one per
+  // plane, and are summed in the order the march would have summed them
+  const int zw = st.zc_lo + H;              // first step with a centre plane
+  {
+    fence_proxy_async();                    // earlier generic writes of the staging area
+    __syncthreads();
+    const int zb_end = min(zw, nz);
+    for (int zb = st.zi0; zb < zb_end; zb += B::WST) {
+      const int nb = min(B::WST, zb_end - zb);
+      if (tid == 0) {
+        mbar_expect_tx(&bar[0], (uint32_t)nb * B::WB + (zb == st.zi0 ? a.stall_tx : 0u));
+        for (int j = 0; j < nb; ++j)
+          tma_load_3d(smem + j * al128(B::WB), map_w, x0 - B::XW, y0 - B::EXT - H, zb + j, &bar[0]);
+      }
+      int bad = 0;
+      if (tid == 0) bad = !mbar_wait(&bar[0], pa);
+      if (__syncthreads_or(bad)) {
+        if (tid == 0) {
+          atomicOr(err, 1);
+          mbar_wait(&bar[0], pa);          // bounded: let this CTA's copies drain
+        }
+        __syncthreads();
+        return false;
+      }
+      pa ^= 1u;
+      for (int j = 0; j < nb; ++j) {
+        const float* wj = reinterpret_cast<const float*>(smem + j * al128(B::WB));
+#pragma unroll
+        for (int k = 0; k < B::K1; ++k) {
+          if (sidx[k] < 0) continue;
+          const int qn = __float2int_rn(wj[stg[k]] * qs);
+          s1r[k] += qn;
+          s2r[k] += (long long)qn * qn;
+        }
+      }
+      __syncthreads();                       // the staging area is consumed
+    }
+  }
+  if (tid == 0) issue_a(zw);
 
   // slot of the centre plane in the ring of d planes, kept incrementally
-  int zc3 = ((st.zi0 - H) % 3 + 3) % 3;
-  for (int zi = st.zi0; zi <= st.zi1; ++zi, zc3 = (zc3 == 2 ? 0 : zc3 + 1)) {
+  int zc3 = ((zw - H) % 3 + 3) % 3;
+  for (int zi = zw; zi <= st.zi1; ++zi, zc3 = (zc3 == 2 ? 0 : zc3 + 1)) {
     const int zc = zi - H;                   // centre plane of the patch window
     const bool do2 = zc >= st.zc_lo && zc <= st.zc_hi;
     const int zf = zc - 1;                   // plane whose force is computed this step
