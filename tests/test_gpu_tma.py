@@ -7,7 +7,11 @@ must therefore be bitwise equal.  DISC_NO_TMA=1 selects the plain-load form at
 planning time.  The TMA form needs nx a multiple of 4 and extents of at least
 one staging box (48 x 30 voxels for patch 11 in iteration mode); the shapes
 below meet that with ragged tiles in x, y and z.  (The per-kernel oracle
-tests include shapes that take the TMA form as well.)
+tests include shapes that take the TMA form as well.)  The TMA form also takes
+the first planes of each chunk's z window, which only enter the z sums, as
+bursts of bulk copies; the shapes include chunks at the volume's start (fewer
+warm-up planes), a volume shorter than the patch, and warm-ups longer than one
+burst.
 """
 import os
 
@@ -45,6 +49,10 @@ CASES = [
     ((9, 64, 48), 15),      # patch wider than the chunk, exact box width
     ((40, 31, 52), 7),
     ((17, 52, 96), 5),
+    # patch 15 on 40 planes: chunks starting at z >= 8 have 14 warm-up planes,
+    # more than the staging area holds (12 boxes in iteration mode, 8 in the
+    # static pass), so the warm-up burst runs in two rounds
+    ((40, 36, 48), 15),
 ]
 
 
@@ -85,7 +93,7 @@ def test_force_update_bitwise(disc, shape, patch, force_mode):
     np.testing.assert_allclose(outs[0][2], outs[1][2], rtol=1e-6)
 
 
-@pytest.mark.parametrize("shape,patch", CASES[:3])
+@pytest.mark.parametrize("shape,patch", CASES[:3] + CASES[-1:])
 def test_static_norm_bitwise(disc, shape, patch):
     P = (patch,) * 3
     _, cbct, _ = _inputs(shape, patch, 7)
