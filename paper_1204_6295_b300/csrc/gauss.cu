@@ -150,6 +150,7 @@ constexpr int kSX = 32;        // xy tile
 constexpr int kSY = 32;
 constexpr int kZThreads = 128; // z kernel: a CTA is kZX columns along x by kZY rows
 constexpr int kZX = 32, kZY = kZThreads / kZX;   // (the rows' warps share I_m rows in L1 for the warp)
+constexpr int kZCtasPerSM = 4;  // z kernel CTAs resident per SM (its launch bound)
 constexpr int kBX = 4;         // x outputs per x-filter task
 constexpr int kBY = 4;         // y outputs per thread in the y filter
 
@@ -440,14 +441,14 @@ __device__ __forceinline__ void gauss_z_body(const GaussArgs& a, int bx, int by,
 }
 
 template <int R, bool WARP>
-__global__ void __launch_bounds__(kZThreads, 4) k_gauss_z(GaussArgs a) {
+__global__ void __launch_bounds__(kZThreads, kZCtasPerSM) k_gauss_z(GaussArgs a) {
   pdl_wait();
   pdl_release();
   gauss_z_body<R, WARP>(a, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 template <int R, bool WARP>
-__global__ void __launch_bounds__(kZThreads, 4) k_gauss_z_batch(const __grid_constant__ GaussBatch bt) {
+__global__ void __launch_bounds__(kZThreads, kZCtasPerSM) k_gauss_z_batch(const __grid_constant__ GaussBatch bt) {
   pdl_wait();
   pdl_release();
   const int i = blockIdx.x;
@@ -566,6 +567,13 @@ GaussPlan gauss_plan(int nx, int ny, int nz, int R, int num_sms) {
     long long max_chunks = (nz + 15) / 16;   // at least 16 planes per chunk
     if (max_chunks < 1) max_chunks = 1;
     if (chunks > max_chunks) chunks = max_chunks;
+    // small volumes: as many chunks of at least 4 planes as one wave of resident
+    // CTAs holds, when that is more (the march's plane latency, not its 2R halo
+    // planes, bounds them)
+    long long wave = (long long)kZCtasPerSM * num_sms / cols;
+    const long long max_short = (nz + 3) / 4;
+    if (wave > max_short) wave = max_short;
+    if (chunks < wave) chunks = wave;
     p.zlen = (int)((nz + chunks - 1) / chunks);
     p.grid = dim3(1, 1, 1);
     return p;
