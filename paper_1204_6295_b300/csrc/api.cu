@@ -200,6 +200,52 @@ BoxArgs box_args(const disc_ctx* c, const Level& v) {
 // Mask-and-fill correction of level l for the current m (Algorithm A1 steps
 // 1-3 with Eqs. 7-10): d = I'_s - m in v.dm.  stop: the level's stop flag, or
 // NULL to run regardless.
+// Inside a graph capture: the fill passes as a conditional WHILE node whose body
+// (kFillPassesPerBody passes, captured on the side stream) runs again only while
+// the last pass's front was not empty, so passes with nothing left to fill cost
+// no launches (a pass after an empty front returns at entry).  The pass index
+// lives on the device after cnt[passes].
+constexpr int kFillPassesPerBody = 2;
+cudaError_t queue_fill_loop(disc_ctx* c, Level& v, FillArgs f, size_t W) {
+  f.next = v.cnt + c->p.fill_passes + 1;
+  f.kbits = v.kbits;
+  f.kwords = (long long)W;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(c->s, &cs, nullptr, &g, &deps, nullptr, &nd);
+  if (e != cudaSuccess) return e;
+  cudaGraphConditionalHandle h = 0;
+  e = cudaGraphConditionalHandleCreate(&h, g, 0u, 0u);
+  if (e != cudaSuccess) return e;
+  f.cond = h;
+  f.use_cond = 1;
+  e = launch_fill_loop_start(f, c->s);       // pass 1 next; run the loop if anything is masked
+  if (e != cudaSuccess) return e;
+  e = cudaStreamGetCaptureInfo(c->s, &cs, nullptr, &g, &deps, nullptr, &nd);
+  if (e != cudaSuccess) return e;
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &cp);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamBeginCaptureToGraph(c->side, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                    cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t e1 = cudaSuccess;
+  for (int k = 0; k < kFillPassesPerBody && e1 == cudaSuccess; ++k) e1 = launch_fill_pass(f, c->side);
+  cudaGraph_t body = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(c->side, &body);
+  if (e1 != cudaSuccess) return e1;
+  if (e2 != cudaSuccess) return e2;
+  // the capture of c->s continues after the loop node
+  return cudaStreamUpdateCaptureDependencies(c->s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
 cudaError_t queue_mask_fill(disc_ctx* c, int l, const int* stop) {
   Level& v = c->lev[l];
   cudaError_t e = cudaMemsetAsync(v.cnt, 0, (c->p.fill_passes + 1) * sizeof(int), c->s);
@@ -241,6 +287,9 @@ cudaError_t queue_mask_fill(disc_ctx* c, int l, const int* stop) {
   f.tz = (c->p.fill_t[2] - 1) / 2;
   f.inv_h = 1.0f / c->p.fill_h;
   f.stop = stop;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (e == cudaSuccess) e = cudaStreamIsCapturing(c->s, &cs);
+  if (e == cudaSuccess && cs == cudaStreamCaptureStatusActive) return queue_fill_loop(c, v, f, W);
   for (int p = 1; p <= c->p.fill_passes && e == cudaSuccess; ++p) {
     f.pass = p;
     f.kin = v.kbits + ((p - 1) % 2) * W;
@@ -537,6 +586,7 @@ disc_status disc_create(const disc_params* p, int device, void* cuda_stream, dis
   ctx->use_loop = p->stop_eps > 0.0f && !(ul && ul[0] == '1');
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
   cudaError_t e = cudaStreamCreateWithFlags(&ctx->s, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming);
   ctx->user = static_cast<cudaStream_t>(cuda_stream);   // NULL: the legacy default stream
@@ -570,6 +620,7 @@ disc_status disc_destroy(disc_ctx* ctx) {
   if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
   if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
   if (ctx->s) cudaStreamDestroy(ctx->s);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
   cudaGetLastError();
   delete ctx;
   return DISC_OK;
@@ -645,7 +696,7 @@ disc_status disc_set_images(disc_ctx* ctx, const float* ct, const float* cbct, i
         if (e == cudaSuccess) e = cudaMalloc(&v.kbits, 2 * sizeof(unsigned) * (size_t)fill_words(v.nx, v.ny, v.nz));
         if (e == cudaSuccess)
           e = cudaMalloc(&v.flist, sizeof(int) * (v.N + (size_t)fill_front_blocks(v.nx, v.ny, v.nz) + 1));
-        if (e == cudaSuccess) e = cudaMalloc(&v.cnt, (ctx->p.fill_passes + 1) * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&v.cnt, (ctx->p.fill_passes + 2) * sizeof(int));
       }
       if (e != cudaSuccess) {
         free_levels(ctx);

@@ -42,7 +42,7 @@ struct Level {
   int* stamp = nullptr;  // 0 known, p filled by pass p, -1 not filled
   unsigned* kbits = nullptr;   // [2][fill_words] known-voxel bit masks of the fill passes
   int* flist = nullptr;        // [N] a fill pass's front; then [fill_front_blocks + 1] block offsets, length
-  int* cnt = nullptr;    // [fill_passes + 1] masked voxels, voxels filled per pass
+  int* cnt = nullptr;    // [fill_passes + 2] masked voxels, voxels filled per pass; then the pass counter
   BoxPlan pa{};
   BoxPlan pm{};          // kModeMaskAB
   GaussPlan pb{};
@@ -60,6 +60,7 @@ struct disc_ctx {
   int num_sms = disc::kNumSMs;
   cudaStream_t user = nullptr;
   cudaStream_t s = nullptr;
+  cudaStream_t side = nullptr;   // captures the bodies of the fill loops
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   int hx = 0, hy = 0, hz = 0, R = 0;
   float w[2 * DISC_MAX_GAUSS_RADIUS + 1] = {};

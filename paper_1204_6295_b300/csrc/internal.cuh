@@ -200,10 +200,25 @@ struct FillArgs {
   float inv_h;          // 1 / h of Eq. 10
   int pass;             // 1, 2, ...
   const int* stop;
+  // Device-driven passes (the body of a graph loop): when `next` is set, the
+  // pass index is read from *next (the pass the next count kernel runs; the
+  // scan kernel advances it) and kin, kout are picked from the pair `kbits`
+  // ([2][kwords]) by its parity, in place of `pass`, `kin` and `kout`; with
+  // use_cond the scan kernel also sets `cond` to continue while the front it
+  // counted is not empty and passes remain.
+  int* next;
+  unsigned* kbits;
+  long long kwords;
+  cudaGraphConditionalHandle cond;
+  int use_cond;
 };
 // One fill pass: the dilation of the known mask kin into kout, then the voxels
 // of kout not in kin.  Before pass 1, launch_fill_pack sets kin from the stamps.
 cudaError_t launch_fill_pass(const FillArgs& f, cudaStream_t s);
+// Start of device-driven passes: *next = 1, and `cond` (the loop around the
+// passes) set to run them unless the level has stopped, nothing is masked
+// (cnt[0] = 0) or passes = 0.
+cudaError_t launch_fill_loop_start(const FillArgs& f, cudaStream_t s);
 // a, b out of the interleaved fill buffer into planar arrays.
 cudaError_t launch_unpack_ab(const float4* isab, float* a, float* b, int64_t n, cudaStream_t s);
 int fill_words(int nx, int ny, int nz);

@@ -55,7 +55,8 @@ __global__ void k_fill_pack(const int* __restrict__ stamp, unsigned* __restrict_
 }
 
 // Dilation word i of K_{p+1}: K_p dilated by the box T, clipped to the volume.
-__device__ __forceinline__ unsigned dilate_word(const FillArgs& f, long long i, unsigned tail) {
+__device__ __forceinline__ unsigned dilate_word(const FillArgs& f, const unsigned* kin, long long i,
+                                                unsigned tail) {
   const int nwx = f.nwx, ny = f.ny, nz = f.nz;
   const int w = (int)(i % nwx);
   const long long row = i / nwx;
@@ -65,7 +66,7 @@ __device__ __forceinline__ unsigned dilate_word(const FillArgs& f, long long i, 
   unsigned uc = 0u, ul = 0u, uh = 0u;
   for (int zz = max(0, z - f.tz); zz <= min(nz - 1, z + f.tz); ++zz)
     for (int yy = max(0, y - f.ty); yy <= min(ny - 1, y + f.ty); ++yy) {
-      const unsigned* r = f.kin + ((long long)zz * ny + yy) * nwx;
+      const unsigned* r = kin + ((long long)zz * ny + yy) * nwx;
       uc |= r[w];
       if (w > 0) ul |= r[w - 1];
       if (w + 1 < nwx) uh |= r[w + 1];
@@ -81,8 +82,23 @@ __device__ __forceinline__ unsigned dilate_word(const FillArgs& f, long long i, 
 constexpr int kFrontWords = 256;
 constexpr int kScanThreads = 1024;
 
-__device__ __forceinline__ bool pass_idle(const FillArgs& f) {
-  return (f.stop != nullptr && *(volatile const int*)f.stop != 0) || f.cnt[f.pass - 1] == 0;
+// The pass a kernel works on and its masks: from the arguments, or (device-driven)
+// from the pass counter, which the scan kernel has already advanced for the
+// list and fill kernels (behind = 1).
+struct PassSel {
+  int p;
+  const unsigned* kin;
+  unsigned* kout;
+};
+
+__device__ __forceinline__ PassSel pass_sel(const FillArgs& f, int behind) {
+  if (f.next == nullptr) return {f.pass, f.kin, f.kout};
+  const int p = *(volatile const int*)f.next - behind;
+  return {p, f.kbits + ((p - 1) & 1) * f.kwords, f.kbits + (p & 1) * f.kwords};
+}
+
+__device__ __forceinline__ bool pass_idle(const FillArgs& f, int p) {
+  return (f.stop != nullptr && *(volatile const int*)f.stop != 0) || f.cnt[p - 1] == 0;
 }
 
 __device__ __forceinline__ int block_exclusive_scan(int v, int* red, int& total) {
@@ -110,16 +126,17 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* red, int& total)
 }
 
 __global__ void __launch_bounds__(kFrontWords) k_fill_front_count(FillArgs f) {
-  if (pass_idle(f)) return;
+  const PassSel P = pass_sel(f, 0);
+  if (pass_idle(f, P.p)) return;
   __shared__ int red[32];
   const long long words = (long long)f.nwx * f.ny * f.nz;
   const long long i = (long long)blockIdx.x * kFrontWords + threadIdx.x;
   const unsigned tail = (f.nx & 31) ? (1u << (f.nx & 31)) - 1u : 0xffffffffu;
   int c = 0;
   if (i < words) {
-    const unsigned k = dilate_word(f, i, tail);
-    f.kout[i] = k;
-    c = __popc(k & ~f.kin[i]);
+    const unsigned k = dilate_word(f, P.kin, i, tail);
+    P.kout[i] = k;
+    c = __popc(k & ~P.kin[i]);
   }
   int total = 0;
   block_exclusive_scan(c, red, total);
@@ -127,27 +144,43 @@ __global__ void __launch_bounds__(kFrontWords) k_fill_front_count(FillArgs f) {
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_fill_front_scan(FillArgs f, int nblocks) {
-  if (pass_idle(f)) return;
+  const PassSel P = pass_sel(f, 0);
+  const bool idle = pass_idle(f, P.p);       // uniform: *next changes only below
   __shared__ int red[32];
   int carry = 0;
-  for (int base = 0; base < nblocks; base += kScanThreads) {
-    const int j = base + threadIdx.x;
-    const int v = j < nblocks ? f.boff[j] : 0;
-    int total = 0;
-    const int ex = block_exclusive_scan(v, red, total);
-    if (j < nblocks) f.boff[j] = carry + ex;
-    carry += total;
+  if (!idle) {
+    for (int base = 0; base < nblocks; base += kScanThreads) {
+      const int j = base + threadIdx.x;
+      const int v = j < nblocks ? f.boff[j] : 0;
+      int total = 0;
+      const int ex = block_exclusive_scan(v, red, total);
+      if (j < nblocks) f.boff[j] = carry + ex;
+      carry += total;
+    }
   }
-  if (threadIdx.x == 0) f.nfront[0] = carry;
+  __syncthreads();                           // every thread has read *next
+  if (threadIdx.x == 0) {
+    if (!idle) f.nfront[0] = carry;
+    if (f.next != nullptr) *f.next = P.p + 1;
+    // pass p fills exactly its front: pass p + 1 has work only after a non-empty one
+    if (f.use_cond) cudaGraphSetConditional(f.cond, (!idle && carry > 0 && P.p < f.passes) ? 1u : 0u);
+  }
+}
+
+__global__ void k_fill_loop_start(FillArgs f) {
+  *f.next = 1;
+  const bool stopped = f.stop != nullptr && *(volatile const int*)f.stop != 0;
+  if (f.use_cond) cudaGraphSetConditional(f.cond, (!stopped && f.cnt[0] > 0 && f.passes > 0) ? 1u : 0u);
 }
 
 __global__ void __launch_bounds__(kFrontWords) k_fill_front_list(FillArgs f) {
-  if (pass_idle(f)) return;
+  const PassSel P = pass_sel(f, 1);
+  if (pass_idle(f, P.p)) return;
   __shared__ int red[32];
   const long long words = (long long)f.nwx * f.ny * f.nz;
   const long long i = (long long)blockIdx.x * kFrontWords + threadIdx.x;
   unsigned b = 0u;
-  if (i < words) b = f.kout[i] & ~f.kin[i];
+  if (i < words) b = P.kout[i] & ~P.kin[i];
   int total = 0;
   int pos = f.boff[blockIdx.x] + block_exclusive_scan(__popc(b), red, total);
   if (b) {
@@ -168,7 +201,8 @@ __global__ void __launch_bounds__(kFrontWords) k_fill_front_list(FillArgs f) {
 // flight) and the unknown ones enter with weight 0, which leaves every sum
 // unchanged: the working set holds finite values everywhere.
 __global__ void __launch_bounds__(kFillThreads) k_fill_pass(FillArgs f) {
-  if (pass_idle(f)) return;
+  const PassSel P = pass_sel(f, 1);
+  if (pass_idle(f, P.p)) return;
   const int n = f.nfront[0];
   const int nx = f.nx, ny = f.ny, nz = f.nz, nwx = f.nwx;
   const size_t plane = (size_t)nx * ny;
@@ -187,8 +221,8 @@ __global__ void __launch_bounds__(kFillThreads) k_fill_pass(FillArgs f) {
     for (int zz = max(0, z - f.tz); zz <= min(nz - 1, z + f.tz); ++zz)
       for (int yy = max(0, y - f.ty); yy <= min(ny - 1, y + f.ty); ++yy) {
         const size_t rw = ((size_t)zz * ny + yy) * nwx;
-        unsigned long long bits = f.kin[rw + w0];
-        if (w1 != w0) bits |= (unsigned long long)f.kin[rw + w1] << 32;
+        unsigned long long bits = P.kin[rw + w0];
+        if (w1 != w0) bits |= (unsigned long long)P.kin[rw + w1] << 32;
         bits = (bits >> sh) & span;
         const size_t row = (size_t)zz * plane + (size_t)yy * nx + x_lo;
         while (bits) {
@@ -206,12 +240,12 @@ __global__ void __launch_bounds__(kFillThreads) k_fill_pass(FillArgs f) {
       const float av = num_a / den, bv = num_b / den;     // Eqs. (8), (9)
       f.isab[g] = make_float4(isx, av, bv, 0.0f);
       f.d[g] = fmaf(av, isx, bv) - __ldg(f.m + g);        // d = I'_s - m
-      f.stamp[g] = f.pass;
+      f.stamp[g] = P.p;
       ++nfilled;
     }
   }
   for (int off = 16; off > 0; off >>= 1) nfilled += __shfl_down_sync(0xffffffffu, nfilled, off);
-  if ((threadIdx.x & 31) == 0 && nfilled) atomicAdd(&f.cnt[f.pass], nfilled);
+  if ((threadIdx.x & 31) == 0 && nfilled) atomicAdd(&f.cnt[P.p], nfilled);
 }
 
 // One-sided differences at the faces as s * (v[+r] - v[-l]), l, r in {0, 1}.
@@ -425,6 +459,11 @@ cudaError_t launch_fill_pass(const FillArgs& f, cudaStream_t s) {
   if (blocks > 148 * 16) blocks = 148 * 16;
   if (blocks < 1) blocks = 1;
   k_fill_pass<<<(int)blocks, kFillThreads, 0, s>>>(f);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_loop_start(const FillArgs& f, cudaStream_t s) {
+  k_fill_loop_start<<<1, 1, 0, s>>>(f);
   return cudaGetLastError();
 }
 
