@@ -97,8 +97,10 @@ __device__ __forceinline__ PassSel pass_sel(const FillArgs& f, int behind) {
   return {p, f.kbits + ((p - 1) & 1) * f.kwords, f.kbits + (p & 1) * f.kwords};
 }
 
+// A pass has nothing to do when the level has stopped, the previous pass filled
+// nothing, or the cap is passed (a loop body's later passes after the last one).
 __device__ __forceinline__ bool pass_idle(const FillArgs& f, int p) {
-  return (f.stop != nullptr && *(volatile const int*)f.stop != 0) || f.cnt[p - 1] == 0;
+  return p > f.passes || (f.stop != nullptr && *(volatile const int*)f.stop != 0) || f.cnt[p - 1] == 0;
 }
 
 __device__ __forceinline__ int block_exclusive_scan(int v, int* red, int& total) {

@@ -90,3 +90,25 @@ def test_stopped_level_costs_no_kernels(disc):
             assert 10 < done < 3000
     # the unrolled graph still launches every one of the 3000 iterations' kernels
     assert times["loop"] < 0.5 * times["unrolled"]
+
+
+@pytest.mark.parametrize("fill_passes", [32, 3])
+def test_masked_fill_loop_matches_stream(disc, fill_passes):
+    """The masked form's fill passes: inside a captured graph they are the body of
+    their own WHILE node (nested in the level's loop when the stop rule is on),
+    with the pass index on the device; with plain stream launches the host queues
+    every pass.  The fields, iteration counts and norm histories are bitwise the
+    same, with every masked voxel reached (32 passes) or with a pass cap that
+    leaves some unfilled (3)."""
+    pair = phantom.ellipsoid_pair(48, 40, 24, seed=23)
+    kw = dict(patch=(5, 5, 5), sigma=1.0, levels=2, iters=(12, 60), stop_eps=2e-3, mask_mode=1,
+              fill_passes=fill_passes)
+    out = {m: _run(disc, m, pair, (5, -1), **kw) for m in MODES}
+    f0, d0, h0 = out["stream"]
+    assert np.isfinite(f0).all() and np.abs(f0).max() > 0
+    for m in ("loop", "unrolled"):
+        f, d, h = out[m]
+        np.testing.assert_array_equal(f, f0)
+        assert d == d0
+        for a, b in zip(h, h0):
+            np.testing.assert_array_equal(a, b)
