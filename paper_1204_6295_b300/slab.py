@@ -38,6 +38,10 @@ The convergence norm l^(k) = sum |dr| / sum |r| (Sec. 2.3) is a ratio of two
 whole-volume sums: each slab sums its interior only (``norm_planes``), the two
 sums are added over the slabs (the allreduce of a multi-device run) and the
 stop rule is applied to the ratio, ending the level in every slab at once.
+
+With one rank per slab, ``halo_exchange`` and ``allreduce_norm_sums`` are the
+two collectives of an iteration (point-to-point halo planes, a two-scalar
+allreduce) over torch.distributed.
 Scope: the mask off (its median a_m is a whole-volume statistic).
 """
 from __future__ import annotations
@@ -101,6 +105,42 @@ def exchange_sources(plan, s):
         if lo < hi:
             out.append((t, lo, hi))
     return out
+
+
+def halo_exchange(plan, rank, buf, dist, group=None):
+    """One halo exchange of a multi-rank slab split, rank `rank` owning slab
+    `rank` of `plan`: `buf` ([3][b1 - b0][ny][nx] torch tensor, the rank's
+    buffer field) gets every plane it holds but does not own from that plane's
+    owner, and sends the planes of its interior that other buffers hold.
+    Point-to-point messages (one per neighbouring pair and direction, matched by
+    the plan that every rank computes alone); `dist` is torch.distributed with an
+    initialised process group (NCCL for device tensors, gloo for host ones)."""
+    _, _, b0, _ = plan[rank]
+    reqs, recvs = [], []
+    for s in range(len(plan)):
+        if s == rank:
+            continue
+        for t, lo, hi in exchange_sources(plan, s):
+            if t == rank:                          # planes [lo, hi) of my interior, for s
+                reqs.append(dist.isend(buf[:, lo - b0:hi - b0].contiguous(), dst=s, group=group))
+    for t, lo, hi in exchange_sources(plan, rank):
+        if t != rank:                              # planes [lo, hi) of my buffer, from t
+            tmp = buf.new_empty((buf.shape[0], hi - lo) + tuple(buf.shape[2:]))
+            reqs.append(dist.irecv(tmp, src=t, group=group))
+            recvs.append((tmp, lo))
+    for q in reqs:
+        q.wait()
+    for tmp, lo in recvs:
+        buf[:, lo - b0:lo - b0 + tmp.shape[1]] = tmp
+    return buf
+
+
+def allreduce_norm_sums(sums, dist, group=None):
+    """The two sums behind l^(k) (sum |dr|, sum |r| over a rank's interior planes,
+    a float64 tensor of 2) added over the ranks in place: the scalar allreduce of
+    the convergence norm (Sec. 2.3)."""
+    dist.all_reduce(sums, op=dist.ReduceOp.SUM, group=group)
+    return sums
 
 
 class SlabRegistration:
