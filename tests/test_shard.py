@@ -77,7 +77,7 @@ def _rank_main(rank, world, port, out):
 
 def test_two_gloo_ranks_agree_on_disjoint_complete_shares():
     world = 2
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.start_processes(_rank_main, args=(world, _free_port(), out), nprocs=world, start_method="spawn")
     share0, seen0, loads = out[0]

@@ -74,7 +74,7 @@ def _rank_main(rank, world, port, out, exchange):
 @pytest.mark.parametrize("exchange", [True, False])
 def test_three_gloo_ranks_equal_whole_volume_oracle(exchange):
     world = 3
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.start_processes(_rank_main, args=(world, _free_port(), out, exchange), nprocs=world,
                        start_method="spawn")
