@@ -5,7 +5,6 @@ import ctypes
 import subprocess
 
 import numpy as np
-import pytest
 
 from paper_1204_6295_b300 import disc
 

@@ -6,7 +6,7 @@ import pytest
 from oracle import disc_oracle as O
 from paper_1204_6295_b300 import phantom
 
-from gpu_util import ct_like, dev, empty, host
+from gpu_util import ct_like, dev, host
 
 pytestmark = pytest.mark.gpu
 
