@@ -456,3 +456,72 @@ def test_smoothing_order_variant_linearity():
     np.testing.assert_allclose(rb - ra, r - O.gaussian_smooth_field(r, 1.0), atol=1e-12)
     z = np.zeros_like(r)
     np.testing.assert_allclose(O.iteration(I_m, I_s, z, pa)[0], O.iteration(I_m, I_s, z, pb)[0], atol=1e-12)
+
+
+# ------------------------------------------- direct pins of three building blocks
+
+def test_box_sum_against_brute_force():
+    """Eq. (3)'s truncated patch sum against a scalar loop over the clipped box,
+    with an anisotropic half size (hx, hy, hz) so that a swapped axis fails."""
+    X = _rng(41).normal(size=(5, 6, 7))           # [nz][ny][nx]
+    half = (2, 1, 0)                               # (hx, hy, hz)
+    got = O.box_sum(X, half)
+    nz, ny, nx = X.shape
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                s = 0.0
+                for zz in range(max(0, z - half[2]), min(nz, z + half[2] + 1)):
+                    for yy in range(max(0, y - half[1]), min(ny, y + half[1] + 1)):
+                        for xx in range(max(0, x - half[0]), min(nx, x + half[0] + 1)):
+                            s += X[zz, yy, xx]
+                assert got[z, y, x] == pytest.approx(s, abs=1e-12)
+
+
+def test_warp_coord_gradient_is_the_derivative_of_the_warp():
+    """d I_m(x + r) / d r_a equals the oracle's coordinate gradient: inside a
+    trilinear cell the warp is linear along each axis, so a central difference
+    of the warp with a step that stays in the cell is exact (up to rounding); an
+    axis whose sample is clamped has derivative 0."""
+    rng = _rng(43)
+    I_m = rng.normal(size=(6, 7, 8)) * 100.0
+    shape = I_m.shape
+    # fractions in [0.2, 0.8] and sample positions strictly inside the volume
+    base = rng.integers(-1, 2, size=(3,) + shape).astype(np.float64)
+    r = base + rng.uniform(0.2, 0.8, size=(3,) + shape)
+    z, y, x = np.meshgrid(*(np.arange(n) for n in shape), indexing="ij")
+    pos = [x + r[0], y + r[1], z + r[2]]
+    inside = np.ones(shape, bool)
+    for a, n in enumerate((shape[2], shape[1], shape[0])):
+        inside &= (pos[a] > 0.0) & (pos[a] < n - 1)
+    assert inside.sum() > 100
+    g = O.warp_coord_gradient(I_m, r)
+    eps = 1e-3
+    for a in range(3):
+        rp, rm = r.copy(), r.copy()
+        rp[a] += eps
+        rm[a] -= eps
+        fd = (O.warp(I_m, rp) - O.warp(I_m, rm)) / (2.0 * eps)
+        np.testing.assert_allclose(g[a][inside], fd[inside], rtol=1e-6, atol=1e-6)
+    # a sample pushed far outside along x is clamped there: zero x derivative
+    rc = r.copy()
+    rc[0] = 100.0
+    assert np.all(O.warp_coord_gradient(I_m, rc)[0] == 0.0)
+
+
+def test_build_pyramid_shapes_means_and_worked_example():
+    """Sec. 2.3's pyramid (reading R13): each level halves every extent rounding
+    up; for even extents a level's mean equals the finer level's (2x2x2 means of
+    full cells); the 2x2x2 volume 0..7 becomes its mean 3.5."""
+    img = _rng(47).normal(size=(8, 12, 16))
+    pyr = O.build_pyramid(img, 3)
+    assert [p.shape for p in pyr] == [(8, 12, 16), (4, 6, 8), (2, 3, 4)]
+    assert pyr[1].mean() == pytest.approx(img.mean(), abs=1e-12)
+    assert pyr[2].mean() == pytest.approx(img.mean(), abs=1e-12)
+    assert pyr[1][1, 2, 3] == pytest.approx(img[2:4, 4:6, 6:8].mean(), abs=1e-12)
+    small = O.build_pyramid(np.arange(8.0).reshape(2, 2, 2), 2)
+    assert small[1].shape == (1, 1, 1) and small[1][0, 0, 0] == 3.5
+    odd = O.build_pyramid(np.arange(27.0).reshape(3, 3, 3), 2)[1]
+    assert odd.shape == (2, 2, 2)
+    assert odd[1, 1, 1] == 26.0                       # a partial corner cell: its one voxel
+    assert odd[0, 0, 1] == pytest.approx(np.mean([2, 5, 11, 14]), abs=1e-12)
