@@ -7,7 +7,9 @@ allreduce of l^(k)), and refreshes its halo planes from their owners with
 point-to-point messages (`slab.halo_exchange`).  The assembled interiors must
 equal the whole-volume run to FP64 rounding, and the summed norms must give the
 whole volume's l^(k).  Three ranks, so the middle slab exchanges with both
-neighbours.  Without the exchange the interiors must differ.
+neighbours, and four ranks whose halo is deeper than a slab, so a buffer takes
+planes from a slab that is not its neighbour.  Without the exchange the
+interiors must differ.
 """
 import os
 import socket
@@ -21,7 +23,7 @@ from oracle import disc_oracle as O
 from paper_1204_6295_b300 import phantom
 from paper_1204_6295_b300.slab import allreduce_norm_sums, halo_exchange, halo_planes, slab_plan
 
-NZ, NY, NX = 30, 12, 14
+NY, NX = 12, 14
 ITERS = 3
 
 
@@ -33,10 +35,10 @@ def _free_port():
     return port
 
 
-def _inputs():
-    I_m = phantom.random_volume((NZ, NY, NX), 3, -200.0, 200.0).astype(np.float64)
-    I_s = I_m + phantom.random_volume((NZ, NY, NX), 4, -40.0, 40.0)
-    r0 = phantom.smooth_random_field((NZ, NY, NX), 5, amp=1.5).astype(np.float64)
+def _inputs(nz):
+    I_m = phantom.random_volume((nz, NY, NX), 3, -200.0, 200.0).astype(np.float64)
+    I_s = I_m + phantom.random_volume((nz, NY, NX), 4, -40.0, 40.0)
+    r0 = phantom.smooth_random_field((nz, NY, NX), 5, amp=1.5).astype(np.float64)
     p = O.Params(patch=(3, 3, 5), sigma=0.8, levels=1, iters=[ITERS])
     return I_m, I_s, r0, p
 
@@ -45,15 +47,15 @@ def _norm_sum(v):
     return float(np.sqrt((v ** 2).sum(axis=0)).sum())
 
 
-def _rank_main(rank, world, port, out, exchange):
+def _rank_main(rank, world, port, out, nz, exchange):
     import sys
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import torch
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    I_m, I_s, r0, p = _inputs()
-    plan = slab_plan(NZ, world, halo_planes(p.patch, p.sigma, 0, 2.0))
+    I_m, I_s, r0, p = _inputs(nz)
+    plan = slab_plan(nz, world, halo_planes(p.patch, p.sigma, 0, 2.0))
     z0, z1, b0, b1 = plan[rank]
     rb = torch.from_numpy(r0[:, b0:b1].copy())
     sums = []
@@ -71,14 +73,17 @@ def _rank_main(rank, world, port, out, exchange):
     dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("exchange", [True, False])
-def test_three_gloo_ranks_equal_whole_volume_oracle(exchange):
-    world = 3
+@pytest.mark.parametrize("world,nz,exchange", [
+    (3, 30, True),
+    (3, 30, False),
+    (4, 24, True),      # 6-plane slabs under a 10-plane halo: buffers span non-adjacent owners
+])
+def test_gloo_ranks_equal_whole_volume_oracle(world, nz, exchange):
     mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
-    mp.start_processes(_rank_main, args=(world, _free_port(), out, exchange), nprocs=world,
+    mp.start_processes(_rank_main, args=(world, _free_port(), out, nz, exchange), nprocs=world,
                        start_method="spawn")
-    I_m, I_s, r0, p = _inputs()
+    I_m, I_s, r0, p = _inputs(nz)
     whole, ls = r0, []
     for _ in range(ITERS):
         rn, dr, l, _ = O.iteration(I_m, I_s, whole, p)
@@ -86,6 +91,8 @@ def test_three_gloo_ranks_equal_whole_volume_oracle(exchange):
         whole = rn
     assert np.abs(whole[2]).max() < 2.0                    # |r_z| stays below the halo's d = 2
     plan = out[0][2]
+    if world == 4:                                         # slab 0's buffer reaches slab 2
+        assert plan[0][3] > plan[2][0]
     got = np.empty_like(whole)
     for rank, (z0, z1, _, _) in enumerate(plan):
         got[:, z0:z1] = out[rank][0]
