@@ -163,6 +163,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def host_cpu():
+    """The host the oracle is timed on: logical CPUs and the CPU model."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or None
+    return {"nproc": os.cpu_count(), "cpu": model}
+
+
 def cpu_baseline(w, pair, budget_s=15.0):
     """The FP64 oracle timed on this host: iterations on a z-slab of the finest level."""
     import numpy as np
@@ -183,7 +200,7 @@ def cpu_baseline(w, pair, budget_s=15.0):
         el = time.perf_counter() - t0
         if el >= budget_s or its >= 50:
             break
-    return {"value": its * n_vox / el / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": its * n_vox / el / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
             "sample": f"{its} oracle iterations on the first {planes} z-planes ({nx}x{ny}x{planes}) "
                       f"of the finest level, numpy float64, single thread, {el:.1f} s"}
 
@@ -217,7 +234,8 @@ def run_reference(args, w, rank, world):
             "config": {"workload": args.workload, "dims": list(w["dims"]), "patch": list(w["patch"]),
                        "sigma": w["sigma"], "levels": w["levels"], "iters": list(w["iters"]),
                        "sample_planes": planes},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
+                             "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
