@@ -66,3 +66,13 @@ def test_reference_arm_prints_one_contract_line():
     assert d["cpu_baseline"]["host"]["nproc"] >= 1           # the host the oracle ran on
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["config"]["workload"] == "headneck-256x256x128"
+
+
+def test_cpu_baseline_entry():
+    """The bench's `cpu_baseline` entry (run after the GPU forms): the FP64 oracle
+    on a bounded sample, with the host it ran on."""
+    import bench
+    w = bench.WORKLOADS["ellipsoid-64x64x32"]
+    d = bench.cpu_baseline(w, bench.make_pair(w), budget_s=0.5)
+    assert d["kind"] == "oracle" and d["cores"] == 1 and d["value"] > 0
+    assert d["unit"] == bench.UNIT and d["host"]["nproc"] >= 1 and "z-planes" in d["sample"]
