@@ -38,7 +38,8 @@ WORKLOADS = {
     "large-512x512x256": dict(dims=(512, 512, 256), patch=(15, 15, 15), sigma=2.0, levels=4,
                               iters=(200, 200, 200, 200), gen="head_neck"),
 }
-DEFAULT_WORKLOAD = "headneck-256x256x128"
+DEFAULT_WORKLOAD = "large-512x512x256"
+CONTINUITY_WORKLOAD = "headneck-256x256x128"   # timed beside the headline as a second plain form
 METRIC = "Gvoxel-iterations/s and % of HBM roofline, plain vs batched/adjoint form, 1 B300"
 UNIT = "Gvoxel-it/s"
 BOX_BYTES_PER_VOXEL = 32     # moments/force pass: read m (4) + zs (4) + r (12), write u (12)
@@ -180,8 +181,94 @@ def host_cpu():
     return {"nproc": os.cpu_count(), "cpu": model}
 
 
-def cpu_baseline(w, pair, budget_s=15.0):
-    """The FP64 oracle timed on this host: iterations on a z-slab of the finest level."""
+def host_cores():
+    """Logical CPUs this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+ORACLE_BLOCK = (128, 128, 32)   # (x, y, z) interior of one worker's block of the finest level
+
+
+def _oracle_block_job(job):
+    """Worker process: `iters` oracle iterations (from r = 0) on one block of the
+    finest level, its z interior plus a halo of planes on each side (the halo is
+    the reach of one iteration: Gaussian radius, patch half size, one plane of
+    the gradient); returns (interior voxel-iterations, seconds)."""
+    ct, Is, patch, sigma, iters, interior = job
+    import numpy as np
+    from oracle import disc_oracle as O
+    P = O.Params(patch=patch, sigma=sigma, levels=1, iters=[1])
+    r = np.zeros((3,) + ct.shape)
+    t0 = time.perf_counter()
+    for _ in range(iters):
+        r, _, _, _ = O.iteration(ct, Is, r, P)
+    return interior * iters, time.perf_counter() - t0
+
+
+def _noop(_):
+    return 0
+
+
+def oracle_blocks(w, pair, n_jobs):
+    """Jobs for the multi-core oracle timing: blocks of ORACLE_BLOCK voxels (x, y
+    crops of the finest level, z slabs with the one-iteration halo) taken in
+    order over the volume."""
+    import math
+
+    import numpy as np
+    from oracle import disc_oracle as O
+    nx, ny, nz = w["dims"]
+    bx, by, bz = (min(b, n) for b, n in zip(ORACLE_BLOCK, (nx, ny, nz)))
+    R = int(math.ceil(3.0 * w["sigma"]))
+    halo = R + (w["patch"][2] - 1) // 2 + 1
+    Is, _ = O.global_shift(pair.ct, pair.cbct)
+    jobs = []
+    for z0 in range(0, nz - bz + 1, bz):
+        for y0 in range(0, ny - by + 1, by):
+            for x0 in range(0, nx - bx + 1, bx):
+                if len(jobs) == n_jobs:
+                    return jobs, halo
+                za, zb = max(0, z0 - halo), min(nz, z0 + bz + halo)
+                sl = (slice(za, zb), slice(y0, y0 + by), slice(x0, x0 + bx))
+                jobs.append((np.ascontiguousarray(pair.ct[sl], np.float64),
+                             np.ascontiguousarray(Is[sl]), tuple(w["patch"]), w["sigma"], 1, bx * by * bz))
+    return jobs, halo
+
+
+def oracle_all_cores(w, pair, iters=4, pool=None):
+    """The FP64 oracle timed on every host core: one spawned process per core,
+    each running `iters` iterations on its own block of the finest level.
+    Returns (Gvoxel-it/s over the interiors, cores, sample text, seconds)."""
+    import multiprocessing as mp
+    cores = host_cores()
+    jobs, halo = oracle_blocks(w, pair, cores)
+    jobs = [j[:4] + (iters,) + j[5:] for j in jobs]
+    own = pool is None
+    if own:
+        pool = mp.get_context("spawn").Pool(len(jobs))
+        pool.map(_noop, range(len(jobs)))      # process start and imports outside the timing
+    try:
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_block_job, jobs, chunksize=1)
+        el = time.perf_counter() - t0
+    finally:
+        if own:
+            pool.close()
+            pool.join()
+    units = sum(r[0] for r in res)
+    bx, by, bz = (min(b, n) for b, n in zip(ORACLE_BLOCK, w["dims"]))
+    sample = (f"{len(jobs)} processes (one per logical CPU), each {iters} oracle iteration(s) from r = 0 on "
+              f"its own {bx}x{by}x{bz} block of the finest level plus {halo} halo planes per side in z "
+              f"(halo work not counted), numpy float64, {el:.1f} s wall")
+    return units / el / 1e9, len(jobs), sample, el
+
+
+def cpu_baseline(w, pair, budget_s=8.0):
+    """The FP64 oracle timed on this host: every core (one process per core,
+    blocks of the finest level), and one thread on a z-slab of the finest level."""
     import numpy as np
     from oracle import disc_oracle as O
     nx, ny, nz = w["dims"]
@@ -200,42 +287,50 @@ def cpu_baseline(w, pair, budget_s=15.0):
         el = time.perf_counter() - t0
         if el >= budget_s or its >= 50:
             break
-    return {"value": its * n_vox / el / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
-            "sample": f"{its} oracle iterations on the first {planes} z-planes ({nx}x{ny}x{planes}) "
-                      f"of the finest level, numpy float64, single thread, {el:.1f} s"}
+    single = its * n_vox / el / 1e9
+    value, cores, sample, _ = oracle_all_cores(w, pair)
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "host": host_cpu(),
+            "sample": sample,
+            "single_thread": {"value": single, "unit": UNIT, "cores": 1,
+                              "sample": f"{its} oracle iterations on the first {planes} z-planes "
+                                        f"({nx}x{ny}x{planes}) of the finest level, numpy float64, one "
+                                        f"thread, {el:.1f} s"}}
 
 
 def run_reference(args, w, rank, world):
     if rank != 0:
         return 0
-    import numpy as np
-    from oracle import disc_oracle as O
+    import multiprocessing as mp
     pair = make_pair(w)
-    nx, ny, nz = w["dims"]
-    planes = max(1, min(nz, (1 << 20) // (nx * ny)))
-    P = O.Params(patch=w["patch"], sigma=w["sigma"], levels=1, iters=[1])
-    Is, _ = O.global_shift(pair.ct, pair.cbct)
-    ct = pair.ct[:planes].astype(np.float64)
-    Is = Is[:planes]
-    r = np.zeros((3,) + ct.shape)
-    for _ in range(args.warmup):
-        r, _, _, _ = O.iteration(ct, Is, r, P)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        r, _, _, _ = O.iteration(ct, Is, r, P)
-    el = time.perf_counter() - t0
-    value = args.steps * ct.size / el / 1e9
-    sample = (f"each step = one oracle iteration (warp, moments, correction, force, Gaussian) on the first "
-              f"{planes} z-planes ({nx}x{ny}x{planes}) of the finest level, numpy float64, single thread")
+    cores = host_cores()
+    jobs, halo = oracle_blocks(w, pair, cores)
+    pool = mp.get_context("spawn").Pool(len(jobs))
+    pool.map(_noop, range(len(jobs)))
+    try:
+        for _ in range(args.warmup):
+            pool.map(_oracle_block_job, jobs, chunksize=1)
+        t0 = time.perf_counter()
+        units = 0
+        for _ in range(args.steps):
+            units += sum(r[0] for r in pool.map(_oracle_block_job, jobs, chunksize=1))
+        el = time.perf_counter() - t0
+    finally:
+        pool.close()
+        pool.join()
+    value = units / el / 1e9
+    bx, by, bz = (min(b, n) for b, n in zip(ORACLE_BLOCK, w["dims"]))
+    sample = (f"each step = one oracle iteration (warp, moments, correction, force, Gaussian) from r = 0 in "
+              f"each of {len(jobs)} processes (one per logical CPU), each on its own {bx}x{by}x{bz} block of "
+              f"the finest level plus {halo} halo planes per side in z (halo work not counted), numpy float64")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
             "config": {"workload": args.workload, "dims": list(w["dims"]), "patch": list(w["patch"]),
                        "sigma": w["sigma"], "levels": w["levels"], "iters": list(w["iters"]),
-                       "sample_planes": planes},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
-                             "sample": sample},
+                       "sample_block": [bx, by, bz], "sample_halo_planes": halo},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": len(jobs), "kind": "oracle",
+                             "host": host_cpu(), "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -421,6 +516,41 @@ def time_batched(disc, torch, dist, steps=2):
                     "after the other; value = all ranks' voxel-iterations / slowest rank's time"}
 
 
+def time_plain(disc, torch, w, dist, steps=5, warmup=2):
+    """Another plain workload's full schedule (a second line of the plain form)."""
+    pair = make_pair(w)
+    nx, ny, nz = w["dims"]
+    cnx, cny, cnz = level_dims(w["dims"], w["levels"])[-1]
+    ct = torch.from_numpy(pair.ct).cuda()
+    cbct = torch.from_numpy(pair.cbct).cuda()
+    zeros = torch.zeros((3, cnz, cny, cnx), dtype=torch.float32, device="cuda")
+    s = torch.cuda.current_stream()
+    with disc.Registration(patch=w["patch"], sigma=w["sigma"], levels=w["levels"], iters=w["iters"]) as reg:
+        reg.set_images(ct, cbct)
+
+        def step():
+            reg.set_field(w["levels"] - 1, zeros)
+            reg.iterate(-1, sync=False)
+
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(steps):
+            step()
+        e1.record(s)
+        torch.cuda.synchronize()
+    t = reduce_max(dist, e0.elapsed_time(e1) / steps / 1e3)
+    world = dist.get_world_size() if dist else 1
+    return {"value": job_throughput(schedule_units(w), world, t), "unit": UNIT, "ms_per_step": t * 1e3,
+            "steps": steps, "dims": list(w["dims"]), "patch": list(w["patch"]), "sigma": w["sigma"],
+            "levels": w["levels"], "iters_coarse_to_fine": list(w["iters"]),
+            "voxel_iterations_per_step": schedule_units(w)}
+
+
 MIXED_HEADNECK_PAIRS = 4
 
 
@@ -533,6 +663,7 @@ def run_ours(args, w, rank, world, local_rank):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
+    launches0 = reg.launch_count()
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local_rank) as clk:
@@ -544,6 +675,7 @@ def run_ours(args, w, rank, world, local_rank):
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
+    launches = reg.launch_count() - launches0     # kernels disc_iterate launched in the timed steps
     ms = reduce_max(dist, e0.elapsed_time(e1) / args.steps)
     value = job_throughput(units, world, ms / 1e3)
 
@@ -558,6 +690,8 @@ def run_ours(args, w, rank, world, local_rank):
     warp_gbs = WARP_BYTES_PER_VOXEL * kt["N"] / kt["warp_s"] / 1e9
     traffic = recorded_traffic(args.workload)
 
+    continuity = (time_plain(disc, torch, WORKLOADS[CONTINUITY_WORKLOAD], dist)
+                  if args.workload != CONTINUITY_WORKLOAD else None)
     batched = None if args.no_batched else time_batched(disc, torch, dist)
     masked = time_masked(disc, torch, w, (ct, cbct), dist)
     mixed = (time_mixed_batch(disc, torch, w, (ct, cbct), dist)
@@ -592,9 +726,6 @@ def run_ours(args, w, rank, world, local_rank):
         if dist:
             dist.destroy_process_group()
         return 0
-    # per level: one warp, then 4 launches per iteration (box, Gaussian xy, Gaussian z
-    # with the next warp, norm); one up-sampling between levels
-    launches = sum(w["iters"]) * 4 + L + (L - 1)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -616,13 +747,16 @@ def run_ours(args, w, rank, world, local_rank):
                     "warp": {"achieved_gbs": warp_gbs, "frac": warp_gbs / peak, "launch_ms": kt["warp_s"] * 1e3,
                              "algorithmic_bytes_per_voxel": WARP_BYTES_PER_VOXEL}},
         "forms": {"plain": {"value": value, "unit": UNIT},
+                  **({"plain_" + CONTINUITY_WORKLOAD: continuity} if continuity else {}),
                   "batched": batched,
                   "differentiable": diff_form,
                   "masked": masked,
                   **({"batched_with_headneck": mixed} if mixed else {}),
                   "effective_hbm_frac_32B_model": value * 1e9 * 32 / (peak * 1e9)},
         "e2e": e2e,
-        "gpu_launches": launches * args.steps,
+        "gpu_launches": launches,
+        "gpu_launches_source": "disc_get_launch_count over the timed steps: kernel nodes of each "
+                               "replayed level graph plus the up-sampling launches",
         "clocks": clk.summary(),
     }
     if world == 1 and not args.no_cpu_baseline:

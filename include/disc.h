@@ -182,6 +182,17 @@ disc_status disc_set_field(disc_ctx* ctx, int32_t level, const float* r,
 disc_status disc_get_progress(disc_ctx* ctx, int32_t* level, int32_t* iter,
                               int32_t dims[3]);
 
+/* Kernel launches disc_iterate has issued on this context since its creation
+ * (the paper has no counterpart; evidence that the hot path ran as kernels):
+ * each replay of a level's iteration graph adds the graph's kernel nodes, each
+ * up-sampling between levels adds one.  Exact with fixed iteration counts and
+ * the mask off.  With the stop rule, a level's iteration loop runs a number of
+ * times decided on the device: its body's kernels are counted once per
+ * iteration the call allows.  The mask's fill passes (a conditional loop
+ * inside each iteration) are not counted.  -1 after a call that ran without
+ * graphs (DISC_SW_NO_GRAPH), whose launches are not counted.  Host memory. */
+disc_status disc_get_launch_count(disc_ctx* ctx, int64_t* launches);
+
 /* Copy the l^(k) history of `level` (up to `cap` values, one per iteration
  * run there) into host memory; *count receives the number written. */
 disc_status disc_get_norm_history(disc_ctx* ctx, int32_t level, float* out,
@@ -250,6 +261,20 @@ disc_status disc_batch_get_field(disc_batch* b, int32_t pair, float* out, int me
  * DISC_ERR_STATE before the level has run. */
 disc_status disc_batch_get_tuning(disc_batch* b, int32_t level, int32_t* items, int32_t* grid,
                                   int32_t* zmult);
+
+/* Which moment/force kernel `level` runs: *tma = 1 for the bulk-tensor-copy-
+ * fed kernel (every pair's level meets its conditions: nx a multiple of 4,
+ * extents of at least one staging box, 16-byte aligned buffers), 0 for the
+ * per-thread-load kernel.  DISC_ERR_STATE before the level has run. */
+disc_status disc_batch_get_box_path(disc_batch* b, int32_t level, int32_t* tma);
+
+/* Pin the tuning of `level` instead of letting the autotuner time it: z
+ * chunking `zmult` (as disc_batch_get_tuning reports it; non-zero) and the
+ * moment/force launch's grid: 0 for one CTA per work item, g > 0 for
+ * min(g, items) persistent CTAs striding over the work table.  Takes effect
+ * at the level's next iteration (the level's graph is rebuilt); synchronises
+ * the batch's stream.  The fields do not depend on the tuning (bit for bit). */
+disc_status disc_batch_pin_tuning(disc_batch* b, int32_t level, int32_t zmult, int32_t grid);
 
 /* Release the batch and every pair context.  NULL is accepted. */
 disc_status disc_batch_destroy(disc_batch* b);
@@ -365,8 +390,10 @@ disc_status disc_k_ssd_grad(const float* Im, const float* zs, const float* r, fl
  * that would need more than 8192 CTAs (roughly, planes larger than about
  * 2048 x 2048 voxels) are rejected with DISC_ERR_SHAPE before any work is
  * queued.  The first call on each device looks up the array's device address
- * (call it once before any stream capture).  All calls share the array:
- * calls whose work overlaps on the GPU race on it. */
+ * and caches it for the life of the process (call it once before any stream
+ * capture).  The cached address does not survive cudaDeviceReset: a process
+ * that resets a device must not call this entry point on it again.  All calls
+ * share the array: calls whose work overlaps on the GPU race on it. */
 disc_status disc_k_pass_a_static(const float* Im, const float* zs, const float* r,
                                  float* u, float* m_out, float* d_out,
                                  double* norms_out, int32_t nx, int32_t ny, int32_t nz,
@@ -453,6 +480,38 @@ disc_status disc_k_edge_rmse(const uint8_t* e1, const uint8_t* e2, int64_t n, do
  * their next synchronising call.)  The paper has no counterpart: it is the
  * failure report of this implementation's bounded waits. */
 disc_status disc_k_check_error(void* stream);
+
+/* ---------------------------------------------------------------------
+ * Test switches (the paper has no counterpart).  Process-wide bits that
+ * select the alternative paths the test suite compares against the default
+ * ones, and failure hooks that need no GPU fault:
+ *   DISC_SW_NO_TMA          moment passes read through per-thread loads
+ *                           instead of bulk tensor copies (same results);
+ *   DISC_SW_TMA_STALL       the bulk-copy-fed iteration pass arms its first
+ *                           copy group for 16 bytes no copy delivers, so its
+ *                           bounded wait gives up (about 1 s) and the call
+ *                           reports DISC_ERR_TIMEOUT;
+ *   DISC_SW_NO_GRAPH        contexts created afterwards launch each kernel on
+ *                           the stream instead of replaying CUDA graphs;
+ *   DISC_SW_UNROLLED_GRAPH  contexts created afterwards use unrolled graphs
+ *                           even with a stop rule;
+ *   DISC_SW_FAULT_ALLOC     disc_set_images's first device allocation reports
+ *                           out-of-memory (host-side fault injection).
+ * The initial bits come from the environment (DISC_NO_TMA, DISC_TEST_TMA_STALL,
+ * DISC_NO_GRAPH, DISC_UNROLLED_GRAPH set to a non-zero value; DISC_FAULT=alloc),
+ * read once when the library is loaded.  disc_set_test_switches replaces all
+ * bits; *previous (may be NULL) receives the old ones.  DISC_ERR_ARG for an
+ * unknown bit.  Not synchronised with work in flight: change the switches
+ * between calls, not during one. */
+enum {
+  DISC_SW_NO_TMA = 1,
+  DISC_SW_TMA_STALL = 2,
+  DISC_SW_NO_GRAPH = 4,
+  DISC_SW_UNROLLED_GRAPH = 8,
+  DISC_SW_FAULT_ALLOC = 16,
+  DISC_SW_ALL = 31
+};
+disc_status disc_set_test_switches(uint32_t flags, uint32_t* previous);
 
 #ifdef __cplusplus
 }

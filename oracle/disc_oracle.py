@@ -708,51 +708,45 @@ def ssd_grad(I_m, I_s, r, half, var_floor=1e-6):
 # ---------------------------------------------------------------------------
 # Sec. 2.4.3: evaluation metrics between two images (not on the iteration
 # path): normalised mutual information and the RMSE of binary Canny edge
-# images, Eq. (11).  Readings:
+# images, Eq. (11).  Both are written here as their plain definitions in
+# float64; the GPU takes the same decisions in float32, so a test accepts a
+# different decision only where the float64 margin of that decision is within
+# float32 rounding.  Readings:
 #  R21 NMI = 2 I(A;B) / (H(A) + H(B)) (it ranges over [0, 1] as the paper says),
 #      entropies of a joint histogram with `bins` bins per image over each
-#      image's [min, max]; bin(v) = floor((v - min) * (bins / (max - min))),
-#      clamped to bins - 1, the bin index taken in float32 (the GPU's
-#      precision: a floating-point decision of an integer); NMI = 1 when both
-#      images are constant.
+#      image's [min, max]; bin(v) = floor((v - min) * bins / (max - min)),
+#      clamped to bins - 1; NMI = 1 when both images are constant.
 #  R22 Canny edges per transverse slice (2-D): Gaussian smoothing (sigma,
 #      taps |i| <= ceil(3 sigma), renormalised over in-slice taps, x then y),
 #      central-difference gradient (one-sided at the borders), magnitude
 #      M = sqrt(gx^2 + gy^2); non-maximum suppression along the gradient
-#      direction quantised to 0, 45, 90, 135 degrees (tan 22.5 = sqrt(2) - 1),
-#      neighbours outside the slice count as 0, a pixel is kept when M is above
-#      1e-5 max_slice |I| (a constant slice smoothed in float32 has rounding-level
-#      gradients, which relative thresholds would otherwise turn into edges) and
-#      M >= both neighbours; strong where M >= t_high max_slice(M), weak where
-#      M >= t_low * that threshold; edges = 8-connected components of the kept
-#      strong and weak pixels that contain a strong pixel.  Every
-#      floating-point step is taken in float32 with the GPU's operation order
-#      (separate multiply and add, no fused multiply-add), so the edge maps are
-#      the same bit for bit.
+#      direction quantised to 0, 45, 90, 135 degrees (sector boundaries at
+#      tan 22.5 = sqrt(2) - 1 and tan 67.5 = sqrt(2) + 1), neighbours outside
+#      the slice count as 0, a pixel is kept when M is above 1e-5 max_slice |I|
+#      (a constant slice has only rounding-level gradients in finite
+#      precision, which relative thresholds would otherwise turn into edges)
+#      and M >= both neighbours; strong where M >= t_high max_slice(M), weak
+#      where M >= t_low * that threshold; edges = 8-connected components of the
+#      kept strong and weak pixels that contain a strong pixel (hysteresis).
 # ---------------------------------------------------------------------------
 
-def _f32(x):
-    """float32 scalar (readings R21, R22 take their integer decisions in float32)."""
-    return np.float32(x)
+def nmi_bins(X, bins):
+    """Reading R21: histogram bin of every value of X (float64), clamped to bins - 1."""
+    X = np.asarray(X, np.float64).ravel()
+    mn, mx = X.min(), X.max()
+    if mx == mn:
+        return np.zeros(X.shape, np.int64)
+    t = (X - mn) * bins / (mx - mn)
+    return np.minimum(np.floor(t).astype(np.int64), bins - 1)
 
 
 def nmi(A, B, bins=64):
-    """Normalised mutual information of two images (reading R21)."""
-    A = np.asarray(A, np.float32).ravel()
-    B = np.asarray(B, np.float32).ravel()
-
-    def binned(X):
-        mn, mx = X.min(), X.max()
-        if mx == mn:
-            return np.zeros(X.shape, np.int64)
-        s = np.float32(bins) / np.float32(mx - mn)
-        t = np.float32(X - mn) * s                          # float32 throughout
-        return np.minimum(np.floor(t).astype(np.int64), bins - 1)
-
-    ia, ib = binned(A), binned(B)
+    """Normalised mutual information of two images (reading R21), float64."""
+    ia, ib = nmi_bins(A, bins), nmi_bins(B, bins)
+    n = ia.size
     joint = np.zeros((bins, bins))
     np.add.at(joint, (ia, ib), 1.0)
-    p = joint / A.size
+    p = joint / n
     pa, pb = p.sum(1), p.sum(0)
 
     def ent(q):
@@ -766,27 +760,19 @@ def nmi(A, B, bins=64):
 
 
 def _canny_taps(sigma):
-    """Reading R22: Gaussian taps of the Canny smoothing (Eq. 11 names the edges),
-    normalised, float32, radius ceil(3 sigma)."""
+    """Reading R22: Gaussian taps of the Canny smoothing, normalised, radius ceil(3 sigma)."""
     R = int(math.ceil(3.0 * sigma))
     i = np.arange(-R, R + 1, dtype=np.float64)
     w = np.exp(-i * i / (2.0 * sigma * sigma))
-    return (w / w.sum()).astype(np.float32), R
+    return w / w.sum(), R
 
 
 def _smooth_axis(P, w, R, axis):
-    """Reading R22: one separable pass in float32: taps in ascending order, then the
-    renormalisation over the in-slice taps (product, sum, division in float32)."""
+    """Reading R22: one separable smoothing pass along `axis`, renormalised over the
+    taps that fall inside the slice."""
     n = P.shape[axis]
-    out = np.zeros(P.shape, np.float32)
-    nrm = np.zeros(n, np.float32)
-    for c in range(n):
-        s = np.float32(0.0)
-        for k in range(-R, R + 1):
-            if 0 <= c + k < n:
-                s = np.float32(s + w[k + R])
-        nrm[c] = s
-    acc = np.zeros(P.shape, np.float32)
+    acc = np.zeros(P.shape)
+    nrm = np.zeros(n)
     for k in range(-R, R + 1):
         lo, hi = max(0, -k), min(n, n - k)
         if lo >= hi:
@@ -795,64 +781,80 @@ def _smooth_axis(P, w, R, axis):
         dst = [slice(None)] * P.ndim
         src[axis] = slice(lo + k, hi + k)
         dst[axis] = slice(lo, hi)
-        acc[tuple(dst)] = acc[tuple(dst)] + w[k + R] * P[tuple(src)]   # float32 mul, then add
+        acc[tuple(dst)] += w[k + R] * P[tuple(src)]
+        nrm[lo:hi] += w[k + R]
     shape = [1] * P.ndim
     shape[axis] = n
-    nr = nrm.reshape(shape)
-    out[...] = np.where(nr == np.float32(1.0), acc, acc / nr)
-    return out
+    return acc / nrm.reshape(shape)
 
 
 def _diff_axis(S, axis):
-    """Reading R22: central difference along one axis of a slice in float32,
-    one-sided at the ends."""
+    """Reading R22: central difference along one axis, one-sided at the ends."""
     n = S.shape[axis]
-    g = np.zeros(S.shape, np.float32)
+    g = np.zeros(S.shape)
     if n < 2:
         return g
     sl = lambda a, b: tuple(slice(a, b) if ax == axis else slice(None) for ax in range(S.ndim))
-    g[sl(1, n - 1)] = np.float32(0.5) * (S[sl(2, n)] - S[sl(0, n - 2)])
+    g[sl(1, n - 1)] = 0.5 * (S[sl(2, n)] - S[sl(0, n - 2)])
     g[sl(0, 1)] = S[sl(1, 2)] - S[sl(0, 1)]
     g[sl(n - 1, n)] = S[sl(n - 1, n)] - S[sl(n - 2, n - 1)]
     return g
 
 
+CANNY_TAN1 = math.sqrt(2.0) - 1.0     # tan 22.5 degrees
+CANNY_TAN2 = math.sqrt(2.0) + 1.0     # tan 67.5 degrees
+CANNY_SECTORS = ((0, 1), (1, 0), (1, 1), (1, -1))   # (dy, dx) of the first neighbour per sector
+
+
+def canny_slice(P, sigma=1.0, t_low=0.4, t_high=0.2):
+    """The quantities behind the Canny decisions of one slice (reading R22), float64:
+    a dict with the smoothed slice S, gradient gx, gy, magnitude M, the sector of
+    every pixel (0 horizontal gradient, 1 vertical, 2 and 3 the diagonals with
+    gx gy > 0 and <= 0), the neighbour magnitudes n1, n2 of every sector
+    ([4][ny][nx]), the floor, the strong threshold hi and the weak one lo."""
+    P = np.asarray(P, np.float64)
+    w, R = _canny_taps(sigma)
+    S = _smooth_axis(_smooth_axis(P, w, R, 1), w, R, 0)
+    gx = _diff_axis(S, 1)
+    gy = _diff_axis(S, 0)
+    M = np.sqrt(gx * gx + gy * gy)
+    Mp = np.pad(M, 1)                                    # neighbours outside count as 0
+
+    def nb(dy, dx):
+        return Mp[1 + dy:1 + dy + M.shape[0], 1 + dx:1 + dx + M.shape[1]]
+
+    ax, ay = np.abs(gx), np.abs(gy)
+    sector = np.where(ay <= CANNY_TAN1 * ax, 0, np.where(ay >= CANNY_TAN2 * ax, 1, np.where(gx * gy > 0, 2, 3)))
+    n1 = np.stack([nb(dy, dx) for dy, dx in CANNY_SECTORS])
+    n2 = np.stack([nb(-dy, -dx) for dy, dx in CANNY_SECTORS])
+    hi = t_high * M.max()
+    return dict(S=S, gx=gx, gy=gy, M=M, sector=sector, n1=n1, n2=n2, floor=1e-5 * np.abs(P).max(),
+                hi=hi, lo=t_low * hi)
+
+
+def canny_hysteresis(cand, strong):
+    """Reading R22: the 8-connected components of `cand` (2-D bool) that contain a
+    pixel of `strong`."""
+    from scipy import ndimage
+    strong = strong & cand
+    if not strong.any():
+        return np.zeros(cand.shape, bool)
+    lab, _ = ndimage.label(cand, structure=np.ones((3, 3), int))
+    good = np.unique(lab[strong])
+    return np.isin(lab, good[good > 0])
+
+
 def canny(img, sigma=1.0, t_low=0.4, t_high=0.2):
     """Binary Canny edge image, slice by slice (reading R22); bool [nz][ny][nx]."""
-    from scipy import ndimage
-    img = np.asarray(img, np.float32)
-    w, R = _canny_taps(sigma)
+    img = np.asarray(img, np.float64)
     edges = np.zeros(img.shape, bool)
-    t1 = _f32(math.sqrt(2.0) - 1.0)
-    t2 = _f32(math.sqrt(2.0) + 1.0)
     for z in range(img.shape[0]):
-        P = img[z]
-        S = _smooth_axis(_smooth_axis(P, w, R, 1), w, R, 0)
-        gx = _diff_axis(S, 1)
-        gy = _diff_axis(S, 0)
-        M = np.sqrt(gx * gx + gy * gy).astype(np.float32)
-        Mp = np.pad(M, 1)                                    # neighbours outside count as 0
-
-        def nb(dy, dx):
-            return Mp[1 + dy:1 + dy + M.shape[0], 1 + dx:1 + dx + M.shape[1]]
-
-        ax, ay = np.abs(gx), np.abs(gy)
-        horiz = ay <= t1 * ax
-        vert = ay >= t2 * ax
-        diag_pos = (gx * gy) > 0
-        n1 = np.where(horiz, nb(0, 1), np.where(vert, nb(1, 0), np.where(diag_pos, nb(1, 1), nb(1, -1))))
-        n2 = np.where(horiz, nb(0, -1), np.where(vert, nb(-1, 0), np.where(diag_pos, nb(-1, -1), nb(-1, 1))))
-        floor = _f32(1e-5) * np.abs(P).max()
-        keep = (M > floor) & (M >= n1) & (M >= n2)
-        hi = _f32(t_high) * M.max()
-        lo = _f32(t_low) * hi
-        strong = keep & (M >= hi)
-        cand = keep & (M >= lo)
-        if not strong.any():
-            continue
-        lab, _ = ndimage.label(cand, structure=np.ones((3, 3), int))
-        good = np.unique(lab[strong])
-        edges[z] = np.isin(lab, good[good > 0])
+        q = canny_slice(img[z], sigma, t_low, t_high)
+        M, sec = q["M"], q["sector"]
+        n1 = np.take_along_axis(q["n1"], sec[None], 0)[0]
+        n2 = np.take_along_axis(q["n2"], sec[None], 0)[0]
+        keep = (M > q["floor"]) & (M >= n1) & (M >= n2)
+        edges[z] = canny_hysteresis(keep & (M >= q["lo"]), keep & (M >= q["hi"]))
     return edges
 
 

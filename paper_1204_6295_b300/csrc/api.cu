@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "internal.cuh"
 #include "context.cuh"
@@ -385,6 +386,38 @@ cudaError_t queue_iterations(disc_ctx* c, int l, int n, const LoopCond* loop) {
   return cudaSuccess;
 }
 
+// Kernel nodes of a graph, child graphs included; kernels inside a
+// conditional node's body (run a number of times decided on the device) are
+// not counted.
+long long graph_kernel_nodes(cudaGraph_t g) {
+  size_t n = 0;
+  if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (n > 0 && cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  long long k = 0;
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType t = cudaGraphNodeTypeEmpty;
+    if (cudaGraphNodeGetType(nd, &t) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (t == cudaGraphNodeTypeKernel) {
+      ++k;
+    } else if (t == cudaGraphNodeTypeGraph) {
+      cudaGraph_t child = nullptr;
+      if (cudaGraphChildGraphNodeGetGraph(nd, &child) == cudaSuccess) k += graph_kernel_nodes(child);
+      else cudaGetLastError();
+    }
+  }
+  return k;
+}
+
 // The loop graph of level l: a conditional WHILE node whose body is one
 // iteration; the body's norm kernel leaves the loop when the launch's budget
 // of iterations is spent or the stop rule fires (Sec. 2.3), so a stopped level
@@ -412,6 +445,7 @@ cudaError_t build_loop_graph(disc_ctx* c, int l) {
       cudaGraph_t captured = nullptr;
       const cudaError_t e2 = cudaStreamEndCapture(c->s, &captured);
       e = e1 != cudaSuccess ? e1 : e2;
+      if (e == cudaSuccess) v.loop_kernels = graph_kernel_nodes(body);
     }
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&v.loop, g, 0);
@@ -423,7 +457,10 @@ cudaError_t build_loop_graph(disc_ctx* c, int l) {
 cudaError_t run_iterations(disc_ctx* c, int l, int n) {
   if (n <= 0) return cudaSuccess;
   Level& v = c->lev[l];
-  if (!c->use_graphs) return queue_iterations(c, l, n, nullptr);
+  if (!c->use_graphs) {
+    c->launches = -1;                      // stream launches are not counted
+    return queue_iterations(c, l, n, nullptr);
+  }
   if (c->use_loop) {
     if (v.loop == nullptr) {
       const cudaError_t e = build_loop_graph(c, l);
@@ -432,6 +469,9 @@ cudaError_t run_iterations(disc_ctx* c, int l, int n) {
     cudaError_t e = launch_warp(v.Im, v.r, v.m, v.nx, v.ny, v.nz, c->d_stop + l, c->s);
     if (e == cudaSuccess) e = launch_set_int(c->d_budget + l, n, c->s);
     if (e == cudaSuccess) e = cudaGraphLaunch(v.loop, c->s);
+    // the body's kernels for each of the n iterations the budget allows (the
+    // stop rule may end the level earlier)
+    if (e == cudaSuccess && c->launches >= 0) c->launches += 2 + v.loop_kernels * n;
     return e;
   }
   if (v.graph == nullptr || v.graph_iters != n) {
@@ -449,6 +489,7 @@ cudaError_t run_iterations(disc_ctx* c, int l, int n) {
       return e;
     }
     if (e2 != cudaSuccess) return e2;
+    v.graph_kernels = graph_kernel_nodes(gph);
     e = cudaGraphInstantiate(&v.graph, gph, 0);
     cudaGraphDestroy(gph);
     if (e != cudaSuccess) {
@@ -457,7 +498,9 @@ cudaError_t run_iterations(disc_ctx* c, int l, int n) {
     }
     v.graph_iters = n;
   }
-  return cudaGraphLaunch(v.graph, c->s);
+  const cudaError_t e = cudaGraphLaunch(v.graph, c->s);
+  if (e == cudaSuccess && c->launches >= 0) c->launches += v.graph_kernels;
+  return e;
 }
 
 cudaError_t reset_level_counters(disc_ctx* c, int l) {
@@ -578,12 +621,11 @@ disc_status disc_create(const disc_params* p, int device, void* cuda_stream, dis
   ctx->hz = (p->patch[2] - 1) / 2;
   ctx->R = gauss_radius(p->gauss_sigma, p->gauss_radius);
   gauss_taps(p->gauss_sigma, ctx->R, ctx->w);
-  const char* ng = std::getenv("DISC_NO_GRAPH");
-  ctx->use_graphs = !(ng && ng[0] == '1');
+  const uint32_t sw = test_switches();
+  ctx->use_graphs = (sw & DISC_SW_NO_GRAPH) == 0u;
   // the loop graph pays a few microseconds per iteration for its condition; it
   // is used where it saves work, when the stop rule can end a level early
-  const char* ul = std::getenv("DISC_UNROLLED_GRAPH");
-  ctx->use_loop = p->stop_eps > 0.0f && !(ul && ul[0] == '1');
+  ctx->use_loop = p->stop_eps > 0.0f && (sw & DISC_SW_UNROLLED_GRAPH) == 0u;
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
   cudaError_t e = cudaStreamCreateWithFlags(&ctx->s, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
@@ -672,11 +714,10 @@ disc_status disc_set_images(disc_ctx* ctx, const float* ct, const float* cbct, i
       }
       v.norm_lo = lo;
       v.norm_hi = hi;
-      // DISC_FAULT=alloc: host-side fault injection, the first allocation reports
-      // an out-of-memory error (tests the recovery of a context)
-      const char* fault = std::getenv("DISC_FAULT");
-      cudaError_t e = (fault != nullptr && std::strcmp(fault, "alloc") == 0) ? cudaErrorMemoryAllocation
-                                                                             : cudaMalloc(&v.Im, v.N * sizeof(float));
+      // DISC_SW_FAULT_ALLOC: host-side fault injection, the first allocation
+      // reports an out-of-memory error (tests the recovery of a context)
+      cudaError_t e = (test_switches() & DISC_SW_FAULT_ALLOC) ? cudaErrorMemoryAllocation
+                                                             : cudaMalloc(&v.Im, v.N * sizeof(float));
       if (e == cudaSuccess) e = cudaMalloc(&v.Is, v.N * sizeof(float));
       if (e == cudaSuccess) e = cudaMalloc(&v.zs, v.N * sizeof(float));
       if (e == cudaSuccess) e = cudaMalloc(&v.m, v.N * sizeof(float));
@@ -842,6 +883,7 @@ disc_status disc_iterate(disc_ctx* ctx, int32_t max_iters, int32_t* iters_done, 
       // level finished: up-sample the field to the next finer level (Algorithm A1)
       const Level& fine = ctx->lev[l - 1];
       CK(launch_up2(ctx->lev[l].r, fine.r, fine.nx, fine.ny, fine.nz, ctx->s));
+      if (ctx->launches >= 0) ctx->launches += 1;
       CK(reset_level_counters(ctx, l - 1));
       ctx->cur_level = l - 1;
       ctx->cur_iter = 0;
@@ -1000,6 +1042,12 @@ disc_status disc_set_field(disc_ctx* ctx, int32_t level, const float* r, int mem
   ctx->cur_iter = 0;
   if (mem_kind == DISC_MEM_HOST) CK(cudaStreamSynchronize(ctx->s));
   CK(leave(ctx));
+  return DISC_OK;
+}
+
+disc_status disc_get_launch_count(disc_ctx* ctx, int64_t* launches) {
+  if (!ctx || !launches) return DISC_ERR_ARG;
+  *launches = ctx->launches;
   return DISC_OK;
 }
 

@@ -45,6 +45,10 @@ struct disc_batch {
   void* d_maps[DISC_MAX_LEVELS] = {};
   cudaGraphExec_t graph[DISC_MAX_LEVELS] = {};
   int graph_iters[DISC_MAX_LEVELS] = {};
+  // tuning pinned by the caller (disc_batch_pin_tuning): z chunking and grid
+  // (0: one CTA per work item) used instead of the autotuner's choice
+  bool pinned[DISC_MAX_LEVELS] = {};
+  int pin_zmult[DISC_MAX_LEVELS] = {}, pin_grid[DISC_MAX_LEVELS] = {};
   int cur_level = 0, cur_iter = 0;
   disc_status sticky = DISC_OK;
 };
@@ -212,6 +216,16 @@ cudaError_t tune_level(disc_batch* b, int l) {
   if (e != cudaSuccess) {
     cudaEventDestroy(e0);
     return e;
+  }
+  if (b->pinned[l]) {                        // the caller's choice, untimed
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int total = 0;
+    make_box_table(b, l, b->pin_zmult[l], &total);
+    b->zmult[l] = b->pin_zmult[l];
+    b->box_total[l] = total;
+    b->box_grid[l] = b->pin_grid[l] > 0 && b->pin_grid[l] < total ? b->pin_grid[l] : total;
+    return cudaSuccess;
   }
   float best = 1e30f;
   int best_mult = 1, best_grid = 0;
@@ -447,6 +461,26 @@ disc_status disc_batch_get_tuning(disc_batch* b, int32_t level, int32_t* items, 
   if (items) *items = b->box_total[level];
   if (grid) *grid = b->box_grid[level];
   if (zmult) *zmult = b->zmult[level];
+  return DISC_OK;
+}
+
+disc_status disc_batch_get_box_path(disc_batch* b, int32_t level, int32_t* tma) {
+  if (!b || !tma || level < 0 || level >= b->L) return DISC_ERR_ARG;
+  if (!b->ready[level]) return DISC_ERR_STATE;
+  *tma = b->tma[level] ? 1 : 0;
+  return DISC_OK;
+}
+
+disc_status disc_batch_pin_tuning(disc_batch* b, int32_t level, int32_t zmult, int32_t grid) {
+  if (!b || level < 0 || level >= b->L) return DISC_ERR_ARG;
+  if (zmult == 0 || grid < 0) return DISC_ERR_ARG;
+  if (b->sticky != DISC_OK) return DISC_ERR_STATE;
+  DeviceGuard guard(b->device);
+  BCK(cudaStreamSynchronize(b->s));          // the level's graph may be in flight
+  drop_level(b, level);                      // re-planned at the level's next iteration
+  b->pinned[level] = true;
+  b->pin_zmult[level] = zmult;
+  b->pin_grid[level] = grid;
   return DISC_OK;
 }
 

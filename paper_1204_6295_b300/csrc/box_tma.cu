@@ -679,10 +679,9 @@ cudaError_t launch_tma(const BoxArgs& a, const BoxPlan& p, cudaStream_t s) {
   cudaError_t e = prepare(k_box_tma<MODE, H>, B::bytes, set);
   if (e != cudaSuccess) return e;
   BoxArgs b = a;
-  // DISC_TEST_TMA_STALL=1: the iteration pass waits for 16 bytes no copy delivers
+  // DISC_SW_TMA_STALL: the iteration pass waits for 16 bytes no copy delivers
   // (exercises the bounded wait and the timeout report; nothing else changes)
-  const char* stall = std::getenv("DISC_TEST_TMA_STALL");
-  b.stall_tx = (MODE == kModeIterate && stall != nullptr && stall[0] == '1') ? 16u : 0u;
+  b.stall_tx = (MODE == kModeIterate && (test_switches() & DISC_SW_TMA_STALL)) ? 16u : 0u;
   return launch_pdl(k_box_tma<MODE, H>, p.grid, dim3(kThreads), B::bytes, s, b, m[0], m[1], m[2], m[3]);
 }
 
@@ -776,10 +775,7 @@ struct Extent {   // smallest volume extents that hold every TMA box of this ker
   }
 };
 
-bool tma_disabled() {
-  const char* e = std::getenv("DISC_NO_TMA");
-  return e != nullptr && e[0] != '\0' && e[0] != '0';
-}
+bool tma_disabled() { return (test_switches() & DISC_SW_NO_TMA) != 0u; }
 
 }  // namespace
 

@@ -48,7 +48,9 @@ struct Level {
   GaussPlan pb{};
   cudaGraphExec_t graph = nullptr;   // n iterations unrolled (graph_iters = n)
   int graph_iters = 0;
+  long long graph_kernels = 0;       // kernel nodes of `graph`
   cudaGraphExec_t loop = nullptr;    // one iteration inside a conditional WHILE node
+  long long loop_kernels = 0;        // kernel nodes of one iteration of `loop`
 };
 
 
@@ -84,6 +86,7 @@ struct disc_ctx {
   disc_status sticky = DISC_OK;
   bool use_graphs = true;
   bool use_loop = true;      // conditional-node loop graphs (with a stop rule; else unrolled graphs)
+  long long launches = 0;    // kernels disc_iterate has launched (disc_get_launch_count); -1: not kept
 };
 
 

@@ -10,6 +10,10 @@
 
 namespace disc {
 
+// Test switches (disc_set_test_switches): one atomic word, set from the
+// environment once at load and by the ABI call afterwards.
+uint32_t test_switches();
+
 constexpr int kThreads = 256;          // threads per CTA of every z-marching kernel
 constexpr int kNumSMs = 148;           // B300: 2 dies x 74 SMs (queried at run time too)
 
@@ -106,8 +110,8 @@ cudaError_t box_fast_launch(int mode, const BoxArgs& a, const BoxPlan& p, cudaSt
 
 // Bulk-tensor-copy path (box_tma.cu): usable when box_tma_ok (cubic patch, nx a
 // multiple of 4, extents at least one staging box) and, per launch, when the
-// buffers are 16-byte aligned (box_tma_aligned); DISC_NO_TMA=1 in the
-// environment turns it off.
+// buffers are 16-byte aligned (box_tma_aligned); the DISC_SW_NO_TMA test switch
+// turns it off.
 bool box_tma_ok(int mode, int nx, int ny, int nz, int hx, int hy, int hz);
 bool box_tma_aligned(int mode, const BoxArgs& a);
 size_t box_tma_smem(int mode, int h);

@@ -14,8 +14,11 @@
 // process.  Host code cannot pass the array's name to a kernel (on the host it
 // names a host-side stand-in, not device memory), so the first call on each
 // device looks its device address up with cudaGetSymbolAddress while that
-// device is current, and caches it.  That first call should therefore come
-// before any stream capture.  Every call shares the one array: two calls whose
+// device is current, and caches it for the life of the process.  That first
+// call should therefore come before any stream capture.  The cache is never
+// invalidated: after cudaDeviceReset the device's module (and the array) is
+// loaded anew, possibly elsewhere, so a process that resets a device must not
+// call this entry point on it again.  Every call shares the one array: two calls whose
 // work overlaps on the GPU race on it.  Each launch overwrites every partial it
 // later reads, so nothing needs clearing between calls.
 

@@ -1,0 +1,52 @@
+// Test switches of the library (disc_set_test_switches in include/disc.h).
+//
+// The switches select alternative code paths that the test suite compares
+// against the default ones (per-thread loads instead of bulk tensor copies,
+// stream launches instead of graph replay) and host- or device-side failure
+// hooks that need no GPU fault (an allocation that reports out-of-memory, a
+// copy wait that is made to run out).  Their initial value comes from the
+// environment, read once when the library is loaded; afterwards only
+// disc_set_test_switches changes them.  Launch paths read one atomic word.
+
+#include <atomic>
+#include <cstdlib>
+
+#include "internal.cuh"
+
+namespace {
+
+bool env_on(const char* name) {
+  const char* v = std::getenv(name);
+  return v != nullptr && v[0] != '\0' && v[0] != '0';
+}
+
+uint32_t env_switches() {
+  uint32_t f = 0;
+  if (env_on("DISC_NO_TMA")) f |= DISC_SW_NO_TMA;
+  if (env_on("DISC_TEST_TMA_STALL")) f |= DISC_SW_TMA_STALL;
+  if (env_on("DISC_NO_GRAPH")) f |= DISC_SW_NO_GRAPH;
+  if (env_on("DISC_UNROLLED_GRAPH")) f |= DISC_SW_UNROLLED_GRAPH;
+  const char* fault = std::getenv("DISC_FAULT");
+  if (fault != nullptr && fault[0] == 'a' && fault[1] == 'l' && fault[2] == 'l' && fault[3] == 'o' &&
+      fault[4] == 'c' && fault[5] == '\0')
+    f |= DISC_SW_FAULT_ALLOC;
+  return f;
+}
+
+// initialised during the library's static initialisation (dlopen)
+std::atomic<uint32_t> g_switches{env_switches()};
+
+}  // namespace
+
+namespace disc {
+
+uint32_t test_switches() { return g_switches.load(std::memory_order_relaxed); }
+
+}  // namespace disc
+
+extern "C" disc_status disc_set_test_switches(uint32_t flags, uint32_t* previous) {
+  if ((flags & ~(uint32_t)DISC_SW_ALL) != 0u) return DISC_ERR_ARG;
+  const uint32_t old = g_switches.exchange(flags, std::memory_order_relaxed);
+  if (previous) *previous = old;
+  return DISC_OK;
+}

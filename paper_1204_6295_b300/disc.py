@@ -81,6 +81,7 @@ _SIGS = {
     "disc_get_progress": (_st, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "disc_get_norm_history": (_st, [_vp, _i32, _vp, _i32, ctypes.POINTER(_i32)]),
     "disc_get_norm_sums": (_st, [_vp, _i32, _vp, _i32, ctypes.POINTER(_i32)]),
+    "disc_get_launch_count": (_st, [_vp, ctypes.POINTER(_i64)]),
     "disc_destroy": (_st, [_vp]),
     "disc_qscale": (_f32, [_f32, ctypes.POINTER(_i32)]),
     "disc_batch_create": (_st, [ctypes.POINTER(Params), ctypes.c_int, _vp, _i32, ctypes.POINTER(_vp)]),
@@ -90,6 +91,8 @@ _SIGS = {
     "disc_batch_get_field": (_st, [_vp, _i32, _vp, ctypes.c_int]),
     "disc_batch_get_tuning": (_st, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "disc_batch_destroy": (_st, [_vp]),
+    "disc_batch_get_box_path": (_st, [_vp, _i32, ctypes.POINTER(_i32)]),
+    "disc_batch_pin_tuning": (_st, [_vp, _i32, _i32, _i32]),
     "disc_k_max_abs": (_st, [_vp, _i64, _vp, _vp]),
     "disc_k_global_shift": (_st, [_vp, _vp, _vp, _i64, _vp, _vp]),
     "disc_k_downsample2": (_st, [_vp, _vp, _i32, _i32, _i32, _vp]),
@@ -102,6 +105,7 @@ _SIGS = {
                                    ctypes.POINTER(_i32), _f32, _f32, _i32, _vp]),
     "disc_k_gauss": (_st, [_vp, _vp, _i32, _i32, _i32, _f32, _i32, _vp]),
     "disc_k_check_error": (_st, [_vp]),
+    "disc_set_test_switches": (_st, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]),
     "disc_get_mask_constants": (_st, [_vp, ctypes.POINTER(_f32), ctypes.POINTER(_f32)]),
     "disc_k_static_stats": (_st, [_vp, _vp, _vp, _i32, _i32, _i32, ctypes.POINTER(_i32), _f32, _f32, _vp]),
     "disc_k_ratio_median": (_st, [_vp, _vp, _vp, _vp, _vp, _i32, _i32, _i32, ctypes.POINTER(_i32), _f32, _f32,
@@ -137,6 +141,27 @@ def header_functions(path=HEADER):
 def _check(status, where):
     if status != 0:
         raise DiscError(status, where)
+
+
+SW_NO_TMA, SW_TMA_STALL, SW_NO_GRAPH, SW_UNROLLED_GRAPH, SW_FAULT_ALLOC = 1, 2, 4, 8, 16
+
+
+class test_switches:
+    """Context manager: set the library's test switches (disc_set_test_switches)
+    to `flags` inside the block and restore the previous ones after it."""
+    __test__ = False
+
+    def __init__(self, flags):
+        self.flags = int(flags)
+
+    def __enter__(self):
+        old = ctypes.c_uint32(0)
+        _check(_lib.disc_set_test_switches(self.flags, ctypes.byref(old)), "disc_set_test_switches")
+        self.old = old.value
+        return self
+
+    def __exit__(self, *exc):
+        _check(_lib.disc_set_test_switches(self.old, None), "disc_set_test_switches")
 
 
 def _ptr(t):
@@ -324,6 +349,12 @@ class Registration:
                                      ctypes.byref(nmi), ctypes.byref(rmse)), "disc_get_metrics")
         return nmi.value, rmse.value
 
+    def launch_count(self):
+        """Kernel launches disc_iterate has issued on this context (disc_get_launch_count)."""
+        n = _i64(0)
+        _check(_lib.disc_get_launch_count(self._h, ctypes.byref(n)), "disc_get_launch_count")
+        return int(n.value)
+
     def mask_constants(self):
         """(HU0, a_m) fixed at set_images when the mask is on (Eq. 7, Sec. 2.3)."""
         hu0, am = _f32(0.0), _f32(0.0)
@@ -393,6 +424,16 @@ class Batch:
         _check(_lib.disc_batch_get_tuning(self._h, int(level), ctypes.byref(items), ctypes.byref(grid),
                                           ctypes.byref(zmult)), "disc_batch_get_tuning")
         return int(items.value), int(grid.value), int(zmult.value)
+
+    def box_path_tma(self, level):
+        """True when `level`'s moment/force launch is the bulk-tensor-copy-fed kernel."""
+        t = _i32(0)
+        _check(_lib.disc_batch_get_box_path(self._h, int(level), ctypes.byref(t)), "disc_batch_get_box_path")
+        return bool(t.value)
+
+    def pin_tuning(self, level, zmult, grid):
+        """Use z chunking `zmult` and grid `grid` (0: one CTA per item) at `level` instead of the autotuner."""
+        _check(_lib.disc_batch_pin_tuning(self._h, int(level), int(zmult), int(grid)), "disc_batch_pin_tuning")
 
 
 # ---------------------------------------------------------------------------

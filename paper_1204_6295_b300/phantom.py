@@ -28,6 +28,7 @@ Sec. 2.4.1 and Sec. 2.4.2, which are not available):
 from __future__ import annotations
 
 import math
+import os
 from dataclasses import dataclass
 
 import numpy as np
@@ -223,20 +224,28 @@ def head_neck_pair(nx=256, ny=256, nz=128, seed=SEED_BASE + 2, spacing=(1.0, 1.0
     k_j = rng.integers(3, 7, size=n_streaks)
     slab = max(1, (1 << 21) // (nx * ny))
     sp = np.asarray(spacing, dtype=np.float64)
+    starts = list(range(0, nz, slab))
+    # the slabs are independent numpy work (which releases the GIL): threads
+    from concurrent.futures import ThreadPoolExecutor
+    workers = max(1, min(len(starts), os.cpu_count() or 1))
+
     # pass 1: peak physical magnitude of the raw field over the whole grid
-    peak = 0.0
-    for zs in range(0, nz, slab):
+    def slab_peak(zs):
         x, y, z = _grid(nx, ny, min(nz, zs + slab) - zs)
         c = _eval_modes(modes, x, y, z + zs, (nx, ny, nz))
-        peak = max(peak, float(np.sqrt((c[0] * sp[0]) ** 2 + (c[1] * sp[1]) ** 2
-                                       + (c[2] * sp[2]) ** 2).max()))
+        return float(np.sqrt((c[0] * sp[0]) ** 2 + (c[1] * sp[1]) ** 2 + (c[2] * sp[2]) ** 2).max())
+
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        peak = max([0.0] + list(ex.map(slab_peak, starts)))
     # field in mm = raw * sp * (max_mm / peak); in voxels divide by sp again
     scale = max_mm / peak
     ct = np.empty((nz, ny, nx), np.float32)
     cbct = np.empty((nz, ny, nx), np.float32)
     prim = np.empty((nz, ny, nx), np.float32)
     u = np.empty((3, nz, ny, nx), np.float32)
-    for zs in range(0, nz, slab):
+    base = np.empty((nz, ny, nx), np.float64)     # the CBCT before its noise
+
+    def slab_images(zs):
         ze = min(nz, zs + slab)
         x, y, z = _grid(nx, ny, ze - zs)
         z = z + zs
@@ -252,8 +261,15 @@ def head_neck_pair(nx=256, ny=256, nz=128, seed=SEED_BASE + 2, spacing=(1.0, 1.0
         for j in range(n_streaks):
             st += np.cos(k_j[j] * (theta - theta_j[j]))
         st *= streak * np.exp(-rho / (0.35 * rho_max)) / n_streaks
-        cbct[zs:ze] = p + bias + st + noise_rng.normal(0.0, noise, size=p.shape)
+        base[zs:ze] = p + bias + st
         u[0, zs:ze], u[1, zs:ze], u[2, zs:ze] = ux, uy, uz
+
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        list(ex.map(slab_images, starts))
+    # the noise is drawn slab after slab from one generator, in z order
+    for zs in starts:
+        ze = min(nz, zs + slab)
+        cbct[zs:ze] = base[zs:ze] + noise_rng.normal(0.0, noise, size=base[zs:ze].shape)
     return Pair(ct, cbct, u, prim)
 
 

@@ -54,7 +54,8 @@ def test_reference_arm_prints_one_contract_line():
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
-                          "--warmup", "0"], capture_output=True, text=True, cwd=root, timeout=600, check=True)
+                          "--warmup", "0", "--workload", "headneck-256x256x128"], capture_output=True, text=True,
+                         cwd=root, timeout=600, check=True)
     lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1
     d = json.loads(lines[0])
@@ -66,6 +67,15 @@ def test_reference_arm_prints_one_contract_line():
     assert d["cpu_baseline"]["host"]["nproc"] >= 1           # the host the oracle ran on
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["config"]["workload"] == "headneck-256x256x128"
+    assert 1 <= d["cpu_baseline"]["cores"] <= d["cpu_baseline"]["host"]["nproc"]   # one process per core
+    assert "processes" in d["cpu_baseline"]["sample"]
+
+
+def test_default_workload_is_the_largest_single_gpu_configuration():
+    import bench
+    assert bench.DEFAULT_WORKLOAD == "large-512x512x256"
+    sizes = {k: bench.schedule_units(w) for k, w in bench.WORKLOADS.items()}
+    assert max(sizes, key=sizes.get) == bench.DEFAULT_WORKLOAD
 
 
 def test_cpu_baseline_entry():
@@ -74,5 +84,7 @@ def test_cpu_baseline_entry():
     import bench
     w = bench.WORKLOADS["ellipsoid-64x64x32"]
     d = bench.cpu_baseline(w, bench.make_pair(w), budget_s=0.5)
-    assert d["kind"] == "oracle" and d["cores"] == 1 and d["value"] > 0
-    assert d["unit"] == bench.UNIT and d["host"]["nproc"] >= 1 and "z-planes" in d["sample"]
+    assert d["kind"] == "oracle" and d["cores"] >= 1 and d["value"] > 0
+    assert d["unit"] == bench.UNIT and d["host"]["nproc"] >= 1 and "processes" in d["sample"]
+    st = d["single_thread"]
+    assert st["cores"] == 1 and st["value"] > 0 and "z-planes" in st["sample"]

@@ -65,3 +65,77 @@ def test_batched_device_buffers_and_errors(disc, pairs):
         assert e.value.status == 3
         f0, f1 = b.get_field(0), b.get_field(1)
     np.testing.assert_array_equal(f0, f1)
+
+
+# Pairs whose finest level meets the bulk-tensor-copy conditions of the batched
+# moment/force kernel (nx a multiple of 4 and at least 48, ny at least 26 for
+# patch 9), of uneven sizes; their coarse level takes the per-thread-load kernel.
+TMA_DIMS = [(96, 64, 24), (112, 48, 20), (64, 80, 30)]
+TMA_KW = dict(patch=(9, 9, 9), sigma=1.5, levels=2, iters=(4, 6))
+
+
+@pytest.fixture(scope="module")
+def tma_pairs():
+    return [phantom.head_neck_pair(nx, ny, nz, seed=700 + i) for i, (nx, ny, nz) in enumerate(TMA_DIMS)]
+
+
+@pytest.fixture(scope="module")
+def tma_single(disc, tma_pairs):
+    out = []
+    for p in tma_pairs:
+        with disc.Registration(**TMA_KW) as reg:
+            reg.set_images(p.ct, p.cbct)
+            reg.iterate(-1)
+            out.append(reg.get_field())
+    return out
+
+
+# z chunking x grid: one CTA per work item, and persistent grids smaller than the
+# work table, so that a CTA runs several items (of different pairs) in turn and
+# carries its copy barriers' phases from one to the next
+@pytest.mark.parametrize("zmult,grid", [(1, 0), (1, 5), (2, 3), (-(1 << 20), 2), (-32, 0)])
+def test_batched_tma_kernel_equals_single_pair_runs(disc, tma_pairs, tma_single, zmult, grid):
+    with disc.Batch(len(tma_pairs), **TMA_KW) as b:
+        for i, p in enumerate(tma_pairs):
+            b.set_images(i, p.ct, p.cbct)
+        for lev in range(2):
+            b.pin_tuning(lev, zmult, grid)
+        assert b.iterate(-1) == 10
+        assert b.box_path_tma(0)                   # the finest level ran k_box_tma_batch
+        items, g, zm = b.tuning(0)
+        assert zm == zmult and g == (items if grid == 0 else min(grid, items))
+        assert grid == 0 or g < items              # persistent CTAs strode over several items
+        got = [b.get_field(i) for i in range(len(tma_pairs))]
+    for i in range(len(tma_pairs)):
+        np.testing.assert_array_equal(got[i], tma_single[i])
+
+
+def test_batched_tma_kernel_sampled_against_oracle(disc):
+    """One level of two iterations, persistent grid, TMA-fed batch: sampled voxels
+    of every pair against the FP64 oracle on a crop holding everything they
+    depend on (as the full-size parity test does)."""
+    from oracle import disc_oracle as O
+    kw = dict(patch=(9, 9, 9), sigma=1.5, levels=1, iters=(2,))
+    pairs = [phantom.head_neck_pair(nx, ny, nz, seed=710 + i) for i, (nx, ny, nz) in enumerate(TMA_DIMS)]
+    with disc.Batch(len(pairs), **kw) as b:
+        for i, p in enumerate(pairs):
+            b.set_images(i, p.ct, p.cbct)
+        b.pin_tuning(0, 1, 4)
+        b.iterate(-1)
+        assert b.box_path_tma(0)
+        fields = [b.get_field(i) for i in range(len(pairs))]
+    P = O.Params(patch=(9, 9, 9), sigma=1.5, levels=1, iters=[2])
+    halo = 2 * (5 + 4 + 2) + 2
+    for p, r in zip(pairs, fields):
+        nz, ny, nx = p.ct.shape
+        Is, _ = O.global_shift(p.ct, p.cbct)
+        for (z, y, x) in [(0, 0, 0), (nz - 1, ny - 1, nx - 1), (nz // 2, ny // 2, nx // 2), (3, ny - 5, 40)]:
+            z0, z1 = max(0, z - halo), min(nz, z + halo + 1)
+            y0, y1 = max(0, y - halo), min(ny, y + halo + 1)
+            x0, x1 = max(0, x - halo), min(nx, x + halo + 1)
+            sl = (slice(z0, z1), slice(y0, y1), slice(x0, x1))
+            cr = np.zeros((3, z1 - z0, y1 - y0, x1 - x0))
+            for _ in range(2):
+                cr, _, _, _ = O.iteration(p.ct[sl].astype(np.float64), Is[sl], cr, P)
+            ref = cr[:, z - z0, y - y0, x - x0]
+            assert np.abs(r[:, z, y, x] - ref).max() <= 2e-3, ((z, y, x), r[:, z, y, x], ref)

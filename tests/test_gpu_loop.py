@@ -3,11 +3,10 @@ node whose body is one iteration, and the norm kernel leaves the loop when the
 call's iteration budget is spent or the stop rule of Sec. 2.3 fires.
 
 Checked against the two other schedules of the same kernels (the n-iteration
-unrolled graph, DISC_UNROLLED_GRAPH=1, and plain stream launches,
-DISC_NO_GRAPH=1): bitwise the same field, the same iteration counts and norm
+unrolled graph, test switch DISC_SW_UNROLLED_GRAPH, and plain stream launches,
+DISC_SW_NO_GRAPH): bitwise the same field, the same iteration counts and norm
 history, in one call or in chunks; and a stopped level costs no more kernels.
 """
-import os
 import time
 
 import numpy as np
@@ -24,27 +23,11 @@ def disc():
     return d
 
 
-class _Env:
-    def __init__(self, **kv):
-        self.kv = kv
-
-    def __enter__(self):
-        self.old = {k: os.environ.get(k) for k in self.kv}
-        os.environ.update(self.kv)
-
-    def __exit__(self, *exc):
-        for k, v in self.old.items():
-            if v is None:
-                del os.environ[k]
-            else:
-                os.environ[k] = v
-
-
-MODES = {"loop": {}, "unrolled": {"DISC_UNROLLED_GRAPH": "1"}, "stream": {"DISC_NO_GRAPH": "1"}}
+MODES = {"loop": 0, "unrolled": 8, "stream": 4}   # disc_set_test_switches bits
 
 
 def _run(disc, mode, pair, chunks, **kw):
-    with _Env(**MODES[mode]):
+    with disc.test_switches(MODES[mode]):
         reg = disc.Registration(**kw)
     with reg:
         reg.set_images(pair.ct, pair.cbct)

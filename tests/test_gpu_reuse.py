@@ -43,22 +43,18 @@ def test_context_reuse_matches_fresh_contexts(disc, kw):
 
 
 def test_allocation_failure_is_recoverable(disc):
-    """Host-side fault injection (DISC_FAULT=alloc): disc_set_images reports
+    """Host-side fault injection (the DISC_SW_FAULT_ALLOC test switch): disc_set_images reports
     DISC_ERR_OOM when its first device allocation fails; the failure is not sticky,
     so the same context then takes the images and registers them exactly as a
     fresh context does."""
-    import os
     kw = dict(patch=(3, 3, 3), sigma=1.0, levels=2, iters=(3, 2))
     p = phantom.ellipsoid_pair(40, 32, 16, seed=33)
     ct, cbct = np.ascontiguousarray(p.ct, np.float32), np.ascontiguousarray(p.cbct, np.float32)
     with disc.Registration(**kw) as reg:
-        os.environ["DISC_FAULT"] = "alloc"
-        try:
+        with disc.test_switches(disc.SW_FAULT_ALLOC):
             with pytest.raises(disc.DiscError) as e:
                 reg.set_images(ct, cbct)
             assert e.value.status == 4              # DISC_ERR_OOM
-        finally:
-            del os.environ["DISC_FAULT"]
         reg.set_images(ct, cbct)
         reg.iterate(-1)
         got = reg.get_field()

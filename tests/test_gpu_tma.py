@@ -3,7 +3,7 @@
 Both forms run the same arithmetic in the same order; only the way the z march
 reads global memory differs (bulk tensor copies into shared memory, with zeros
 outside the volume, versus per-thread loads with bounds tests).  Their outputs
-must therefore be bitwise equal.  DISC_NO_TMA=1 selects the plain-load form at
+must therefore be bitwise equal.  The DISC_SW_NO_TMA test switch selects the plain-load form at
 planning time.  The TMA form needs nx a multiple of 4 and extents of at least
 one staging box (48 x 30 voxels for patch 11 in iteration mode); the shapes
 below meet that with ragged tiles in x, y and z.  (The per-kernel oracle
@@ -13,7 +13,6 @@ bursts of bulk copies; the shapes include chunks at the volume's start (fewer
 warm-up planes), a volume shorter than the patch, and warm-ups longer than one
 burst.
 """
-import os
 
 import numpy as np
 import pytest
@@ -31,16 +30,9 @@ def disc():
     return d
 
 
-class _NoTma:
-    def __enter__(self):
-        self.old = os.environ.get("DISC_NO_TMA")
-        os.environ["DISC_NO_TMA"] = "1"
-
-    def __exit__(self, *exc):
-        if self.old is None:
-            del os.environ["DISC_NO_TMA"]
-        else:
-            os.environ["DISC_NO_TMA"] = self.old
+def _NoTma():
+    from paper_1204_6295_b300 import disc
+    return disc.test_switches(disc.SW_NO_TMA)
 
 
 CASES = [
@@ -152,15 +144,13 @@ def test_registration_bitwise(disc):
 
 def test_bounded_wait_reports_timeout_and_device_stays_usable(disc):
     """A copy group armed for 16 bytes more than its copies deliver (the
-    DISC_TEST_TMA_STALL hook of the iteration pass) never completes: the wait gives
+    DISC_SW_TMA_STALL test switch of the iteration pass) never completes: the wait gives
     up after about a second, the CTA drains and returns, the context reports
     DISC_ERR_TIMEOUT and then refuses further work, and a new context on the same
     device runs normally."""
     pair = phantom.ellipsoid_pair(64, 48, 16, seed=3)
     kw = dict(patch=(3, 3, 3), sigma=1.0, levels=1, iters=(1,))
-    old = os.environ.get("DISC_TEST_TMA_STALL")
-    os.environ["DISC_TEST_TMA_STALL"] = "1"
-    try:
+    with disc.test_switches(disc.SW_TMA_STALL):
         reg = disc.Registration(**kw)
         reg.set_images(pair.ct, pair.cbct)          # the static pass is not stalled
         with pytest.raises(disc.DiscError) as e:
@@ -170,11 +160,6 @@ def test_bounded_wait_reports_timeout_and_device_stays_usable(disc):
             reg.iterate(-1)
         assert e2.value.status == 3                 # DISC_ERR_STATE: the failure is sticky
         reg.close()
-    finally:
-        if old is None:
-            del os.environ["DISC_TEST_TMA_STALL"]
-        else:
-            os.environ["DISC_TEST_TMA_STALL"] = old
     with disc.Registration(**kw) as reg:
         reg.set_images(pair.ct, pair.cbct)
         done, _ = reg.iterate(-1)

@@ -69,3 +69,37 @@ def test_edge_rmse_closed_form():
     E2[1, 2, 3] = E2[0, 0, 0] = E2[2, 4, 6] = True
     assert O.edge_rmse(E1, E2) == pytest.approx(math.sqrt(3 / E1.size), rel=1e-15)
     assert O.edge_rmse(E2, E2) == 0.0
+
+
+def test_nmi_histogram_matches_numpy_histogram2d():
+    """The joint histogram of reading R21 is numpy's histogram2d over each image's
+    [min, max] with `bins` equal bins (a library special case), so the NMI built
+    from histogram2d's counts is the oracle's."""
+    rng = np.random.default_rng(5)
+    A = rng.normal(0.0, 300.0, size=(5, 20, 30))
+    B = 0.5 * A + rng.normal(0.0, 100.0, size=A.shape)
+    for bins in (2, 7, 64):
+        h, _, _ = np.histogram2d(A.ravel(), B.ravel(), bins=bins,
+                                 range=[[A.min(), A.max()], [B.min(), B.max()]])
+        p = h / A.size
+        pa, pb = p.sum(1), p.sum(0)
+        ent = lambda q: -(q[q > 0] * np.log(q[q > 0])).sum()
+        ha, hb, hab = ent(pa), ent(pb), ent(p.ravel())
+        assert O.nmi(A, B, bins) == pytest.approx(2.0 * (ha + hb - hab) / (ha + hb), abs=1e-13)
+
+
+def test_canny_diagonal_step_is_one_pixel_wide():
+    """A step across the line x + y = c has its gradient along the 45-degree
+    diagonal: non-maximum suppression along that diagonal (reading R22) leaves
+    a line one pixel wide in the direction of the gradient, on the step."""
+    ny, nx = 32, 32
+    y, x = np.mgrid[0:ny, 0:nx]
+    img = np.where(x + y > 31, 100.0, 0.0)[None]
+    E = O.canny(img, sigma=1.0)[0]
+    inner = E[6:-6, 6:-6]
+    yy, xx = np.nonzero(inner)
+    assert yy.size > 0
+    s = (xx + 6) + (yy + 6)
+    assert set(np.unique(s)) <= {31, 32}          # on the step
+    # one pixel wide along the gradient (the diagonal): never both of a pixel and its (+1, +1) neighbour
+    assert not np.any(E[:-1, :-1] & E[1:, 1:])

@@ -3,40 +3,49 @@
 It serves callers that cannot let the library allocate device memory (an
 application that owns all device memory through its own pool or a fixed
 budget, or a host that forbids plug-ins from allocating).  Its only scratch is
-a fixed array inside the library that every call reuses, so this test calls it
-twice in a row through the C ABI and checks both results against the
-allocating entry point disc_k_pass_a, within the per-kernel tolerance used by
-the other parity tests.  The file name makes pytest collect it last.
+a fixed array inside the library that every call reuses.  It runs the same
+kernels with the same launch plan as the allocating entry point
+disc_k_pass_a, so this test calls both through the C ABI, twice in a row on
+inputs of different sizes (the larger grid first, so that the second call
+would read partial sums the first one left behind if it read any it did not
+write), and requires bitwise equal m, d, u and norms.  Each result is also
+checked against the FP64 oracle's force on the GPU's own m and d, within the
+per-kernel tolerance of the other parity tests.  The file name makes pytest
+collect it last.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+from oracle import disc_oracle as O
 from paper_1204_6295_b300 import phantom
 
-from gpu_util import ct_like, dev, empty, host, rel_err
+from gpu_util import ct_like, dev, empty, host
 
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-5
 
+# (nz, ny, nx), patch: the first launch has more CTAs than the second
+CALLS = [((21, 45, 70), (5, 5, 5), 33), ((13, 18, 36), (3, 3, 3), 34)]
 
-def test_static_scratch_pass_a_matches_allocating_entry_point_twice():
+
+def test_static_scratch_pass_a_equals_allocating_entry_point_bitwise_twice():
     import torch
     from paper_1204_6295_b300 import disc
-    shape, patch = (21, 45, 70), (5, 5, 5)
-    Im = ct_like(shape, 31)
-    Is = ct_like(shape, 32, noise=25.0)
-    qs_s = disc.qscale(float(np.abs(Is).max()), patch)
-    qs_m = disc.qscale(float(np.abs(Im).max()), patch)
-    zs = empty(*shape)
-    disc.k_static_norm(dev(Is), zs, patch, qs_s)
-    Im_d = dev(Im)
-    u_ref, m_ref, d_ref = empty(3, *shape), empty(*shape), empty(*shape)
-    n_ref = torch.zeros(2, dtype=torch.float64, device="cuda")
-    for call, seed in enumerate((33, 34)):
-        r = dev(phantom.smooth_random_field(shape, seed, amp=2.0))
+    for call, (shape, patch, seed) in enumerate(CALLS):
+        Im = ct_like(shape, seed)
+        Is = ct_like(shape, seed + 100, noise=25.0)
+        qs_s = disc.qscale(float(np.abs(Is).max()), patch)
+        qs_m = disc.qscale(float(np.abs(Im).max()), patch)
+        zs = empty(*shape)
+        disc.k_static_norm(dev(Is), zs, patch, qs_s)
+        Im_d = dev(Im)
+        r_np = phantom.smooth_random_field(shape, seed, amp=2.0)
+        r = dev(r_np)
+        u_ref, m_ref, d_ref = empty(3, *shape), empty(*shape), empty(*shape)
+        n_ref = torch.zeros(2, dtype=torch.float64, device="cuda")
         disc.k_pass_a(Im_d, zs, r, u_ref, patch, qs_m, m_out=m_ref, d_out=d_ref, norms_out=n_ref)
         u, m, d = empty(3, *shape), empty(*shape), empty(*shape)
         norms = torch.full((2,), -1.0, dtype=torch.float64, device="cuda")
@@ -46,10 +55,20 @@ def test_static_scratch_pass_a_matches_allocating_entry_point_twice():
             norms.data_ptr(), shape[2], shape[1], shape[0], p, qs_m, 1e-6, 0,
             torch.cuda.current_stream().cuda_stream)
         assert status == 0, (call, disc._lib.disc_status_str(status))
-        assert rel_err(host(m), host(m_ref)) <= TOL, call
-        assert rel_err(host(d), host(d_ref)) <= TOL, call
-        assert rel_err(host(u) - host(r), host(u_ref) - host(r)) <= TOL, call
-        np.testing.assert_allclose(host(norms), host(n_ref), rtol=TOL)
+        # the same kernels on the same inputs: bit for bit
+        np.testing.assert_array_equal(host(m), host(m_ref), err_msg=f"m, call {call}")
+        np.testing.assert_array_equal(host(d), host(d_ref), err_msg=f"d, call {call}")
+        np.testing.assert_array_equal(host(u), host(u_ref), err_msg=f"u, call {call}")
+        np.testing.assert_array_equal(host(norms), host(n_ref), err_msg=f"norms, call {call}")
+        # and the force against the oracle's (Eq. 1) on the GPU's own m and I'_s = m + d
+        m_g, f_g = host(m), host(m) + host(d)
+        dr_ref = O.force(m_g, f_g, O.FORCE_THIRION)
+        dr_g = host(u) - r_np.astype(np.float64)
+        scale = max(np.abs(dr_ref).max(), 1e-3)
+        assert np.abs(dr_g - dr_ref).max() <= TOL * scale, call
+        n_g = host(norms)
+        assert n_g[0] == pytest.approx(np.sqrt((dr_ref ** 2).sum(0)).sum(), rel=1e-5, abs=1e-6)
+        assert n_g[1] == pytest.approx(np.sqrt((r_np.astype(np.float64) ** 2).sum(0)).sum(), rel=1e-5)
 
 
 def test_static_scratch_pass_a_rejects_grids_beyond_its_scratch():
