@@ -56,6 +56,48 @@ static __device__ __forceinline__ void patch_moments(long long S1, long long S2,
   sigma = var > var_floor ? sqrt_approx(var) : 0.0f;
 }
 
+// Demons force of Eq. (1) (reading R1: the difference taken as I'_s - I_m^(k))
+// at one voxel, with grad I'_s = grad d + grad m.  Inputs: d0 = d = I'_s - m at
+// the voxel and, per axis, the difference scale s (1/2 for a central
+// difference, 1 for a one-sided one at a face, 0 on an axis of one voxel) with
+// the differences dd, dm of d and m between the two neighbours used.  A term
+// is 0 where its denominator is <= 1e-9 (reading R11); `dbl` adds the second
+// term of the double force.  Every rounding is explicit, so each kernel that
+// computes the force gets the same bits.
+struct Dr {
+  float x, y, z;
+};
+static __device__ __forceinline__ Dr demons_dr(float d0, float sx, float ddx, float dmx, float sy, float ddy,
+                                               float dmy, float sz, float ddz, float dmz, bool dbl) {
+  const float gmx = __fmul_rn(sx, dmx), gmy = __fmul_rn(sy, dmy), gmz = __fmul_rn(sz, dmz);
+  const float gfx = fmaf(sx, ddx, gmx), gfy = fmaf(sy, ddy, gmy), gfz = fmaf(sz, ddz, gmz);
+  const float d2 = __fmul_rn(d0, d0);
+  const float den = fmaf(gfx, gfx, fmaf(gfy, gfy, fmaf(gfz, gfz, d2)));
+  const float sc = den > 1e-9f ? __fdividef(d0, den) : 0.0f;
+  Dr dr{__fmul_rn(sc, gfx), __fmul_rn(sc, gfy), __fmul_rn(sc, gfz)};
+  if (dbl) {
+    const float den2 = fmaf(gmx, gmx, fmaf(gmy, gmy, fmaf(gmz, gmz, d2)));
+    const float s2 = den2 > 1e-9f ? __fdividef(d0, den2) : 0.0f;
+    dr.x = fmaf(s2, gmx, dr.x);
+    dr.y = fmaf(s2, gmy, dr.y);
+    dr.z = fmaf(s2, gmz, dr.z);
+  }
+  return dr;
+}
+
+// |v| of a 3-vector for the convergence norm l^(k) (Sec. 2.3): per-CTA float
+// partial sums of these are added in a fixed order.
+static __device__ __forceinline__ float norm3(float x, float y, float z) {
+  return sqrt_approx(fmaf(x, x, fmaf(y, y, __fmul_rn(z, z))));
+}
+
+// Difference scale of an axis position c of n voxels (reading R10): the
+// neighbours used are c + lo and c + hi (lo, hi in {-step, 0} and {0, step}).
+static __device__ __forceinline__ float diff_scale(int c, int n) {
+  const bool l = c > 0, h = c < n - 1;
+  return (l && h) ? 0.5f : ((l || h) ? 1.0f : 0.0f);
+}
+
 // kModeMaskAB epilogue at voxel g (Eqs. 5-7; readings R17, R18), shared by the
 // box kernels.  vc = m at the voxel, dc = E(M) - m, sg = STD(M), zsv = zs.
 //   a = STD(M) / STD(S), b = E(M) - a E(S) with E(S) = I_s - zs STD(S);

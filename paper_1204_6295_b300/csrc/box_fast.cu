@@ -52,12 +52,6 @@ struct FastLayout {
   static constexpr size_t bytes = ((o_ro + (EXT ? 4 * 3 * (size_t)TN : 0)) + 15) & ~(size_t)15;
 };
 
-__device__ __forceinline__ float diff1(float vm, float v0, float vp, int c, int n) {
-  if (n < 2) return 0.0f;
-  if (c == 0) return vp - v0;
-  if (c == n - 1) return v0 - vm;
-  return 0.5f * (vp - vm);
-}
 
 
 // The CTA body: tile (bx, by) of the 32 x 16 tiling, z chunk bz; part = index
@@ -306,27 +300,14 @@ __device__ __forceinline__ void box_body(const BoxArgs& a, int bx, int by, int b
         const int gx = x0 + ox, gy = y0 + oy;
         const int fi = (oy + 1) * B::FX + (ox + 1);
         const float d0 = dp[fi], m0 = mp[fi];
-        const float gdx = diff1(dp[fi - 1], d0, dp[fi + 1], gx, nx);
-        const float gmx = diff1(mp[fi - 1], m0, mp[fi + 1], gx, nx);
-        const float gdy = diff1(dp[fi - B::FX], d0, dp[fi + B::FX], gy, ny);
-        const float gmy = diff1(mp[fi - B::FX], m0, mp[fi + B::FX], gy, ny);
+        const int xl = gx > 0 ? -1 : 0, xh = gx < nx - 1 ? 1 : 0;
+        const int yl = gy > 0 ? -B::FX : 0, yh = gy < ny - 1 ? B::FX : 0;
         const float dzm = zlo ? dring[sm * B::FN + fi] : d0, dzp = zhi ? dring[sp * B::FN + fi] : d0;
         const float mzm = zlo ? mring[sm * B::FN + fi] : m0, mzp = zhi ? mring[sp * B::FN + fi] : m0;
-        const float gdz = diff1(dzm, d0, dzp, zo, nz);
-        const float gmz = diff1(mzm, m0, mzp, zo, nz);
-        const float gfx = gdx + gmx, gfy = gdy + gmy, gfz = gdz + gmz;
-        const float diff = d0;
-        const float d2 = diff * diff;
-        const float den = fmaf(gfx, gfx, fmaf(gfy, gfy, fmaf(gfz, gfz, d2)));
-        const float s = den > 1e-9f ? __fdividef(diff, den) : 0.0f;
-        float drx = s * gfx, dry = s * gfy, drz = s * gfz;
-        if (a.force_mode == DISC_FORCE_DOUBLE) {
-          const float den2 = fmaf(gmx, gmx, fmaf(gmy, gmy, fmaf(gmz, gmz, d2)));
-          const float s2 = den2 > 1e-9f ? __fdividef(diff, den2) : 0.0f;
-          drx = fmaf(s2, gmx, drx);
-          dry = fmaf(s2, gmy, dry);
-          drz = fmaf(s2, gmz, drz);
-        }
+        const Dr dr = demons_dr(d0, diff_scale(gx, nx), dp[fi + xh] - dp[fi + xl], mp[fi + xh] - mp[fi + xl],
+                                diff_scale(gy, ny), dp[fi + yh] - dp[fi + yl], mp[fi + yh] - mp[fi + yl],
+                                diff_scale(zo, nz), dzp - dzm, mzp - mzm, a.force_mode == DISC_FORCE_DOUBLE);
+        const float drx = dr.x, dry = dr.y, drz = dr.z;
         const size_t g = (size_t)zo * plane + ooff[i];
         float rx, ry, rz;
         if (back == 1) {                       // staged in stage 1
@@ -343,8 +324,8 @@ __device__ __forceinline__ void box_body(const BoxArgs& a, int bx, int by, int b
         a.out[(size_t)N + g] = fmaf(keep, ry, dry);
         a.out[2 * (size_t)N + g] = fmaf(keep, rz, drz);
         const bool nin = a.norm_hi <= a.norm_lo || (zo >= a.norm_lo && zo < a.norm_hi);   // the plane enters the norm sums
-        acc0 += nin ? sqrt_approx(fmaf(drx, drx, fmaf(dry, dry, drz * drz))) : 0.0f;
-        acc1 += nin ? sqrt_approx(fmaf(rx, rx, fmaf(ry, ry, rz * rz))) : 0.0f;
+        acc0 += nin ? norm3(drx, dry, drz) : 0.0f;
+        acc1 += nin ? norm3(rx, ry, rz) : 0.0f;
       }
     }
     }

@@ -101,15 +101,6 @@ __device__ __forceinline__ void patch_moments(long long S1, long long S2, int n,
   sigma = var > var_floor ? sqrtf(var) : 0.0f;
 }
 
-// Central difference inside, one-sided at the faces, for an axis of n voxels:
-// returns value(c+1) - value(c-1) halved, or the one-sided difference.
-__device__ __forceinline__ float diff_axis(float vm, float v0, float vp, int c, int n) {
-  if (n < 2) return 0.0f;
-  if (c == 0) return vp - v0;
-  if (c == n - 1) return v0 - vm;
-  return 0.5f * (vp - vm);
-}
-
 template <int MODE, int TX, int TY>
 __global__ void __launch_bounds__(kThreads) k_box_pass(BoxArgs a) {
   if (a.stop != nullptr && *(volatile const int*)a.stop != 0) return;
@@ -274,40 +265,29 @@ __global__ void __launch_bounds__(kThreads) k_box_pass(BoxArgs a) {
         const size_t g = (size_t)zo * plane + (size_t)gy * nx + gx;
         const float d0 = dp[fi];
         const float m0 = __ldg(src + g);
-        // neighbours (clamped reads; diff_axis picks the one-sided form at faces)
+        // neighbours (clamped reads: one-sided differences at the faces)
         const float mxm = gx > 0 ? __ldg(src + g - 1) : m0;
         const float mxp = gx < nx - 1 ? __ldg(src + g + 1) : m0;
         const float mym = gy > 0 ? __ldg(src + g - nx) : m0;
         const float myp = gy < ny - 1 ? __ldg(src + g + nx) : m0;
         const float mzm = zo > 0 ? __ldg(src + g - plane) : m0;
         const float mzp = zo < nz - 1 ? __ldg(src + g + plane) : m0;
-        const float gmx = diff_axis(mxm, m0, mxp, gx, nx);
-        const float gmy = diff_axis(mym, m0, myp, gy, ny);
-        const float gmz = diff_axis(mzm, m0, mzp, zo, nz);
-        const float gdx = diff_axis(dp[fi - 1], d0, dp[fi + 1], gx, nx);
-        const float gdy = diff_axis(dp[fi - FX], d0, dp[fi + FX], gy, ny);
-        const float gdz = diff_axis(zo > 0 ? dm[fi] : d0, d0, zo < nz - 1 ? dn[fi] : d0, zo, nz);
-        const float gfx = gdx + gmx, gfy = gdy + gmy, gfz = gdz + gmz;
-        const float diff = d0;                         // I'_s - I_m^(k)
-        const float d2 = diff * diff;
-        const float den = fmaf(gfx, gfx, fmaf(gfy, gfy, fmaf(gfz, gfz, d2)));
-        const float s = den > 1e-9f ? diff / den : 0.0f;
-        float drx = s * gfx, dry = s * gfy, drz = s * gfz;
-        if (a.force_mode == DISC_FORCE_DOUBLE) {
-          const float den2 = fmaf(gmx, gmx, fmaf(gmy, gmy, fmaf(gmz, gmz, d2)));
-          const float s2 = den2 > 1e-9f ? diff / den2 : 0.0f;
-          drx = fmaf(s2, gmx, drx);
-          dry = fmaf(s2, gmy, dry);
-          drz = fmaf(s2, gmz, drz);
-        }
+        // neighbours at the faces fall back to the voxel itself (one-sided differences)
+        const float dxm = gx > 0 ? dp[fi - 1] : d0, dxp = gx < nx - 1 ? dp[fi + 1] : d0;
+        const float dym = gy > 0 ? dp[fi - FX] : d0, dyp = gy < ny - 1 ? dp[fi + FX] : d0;
+        const float dzm = zo > 0 ? dm[fi] : d0, dzp = zo < nz - 1 ? dn[fi] : d0;
+        const Dr dr = demons_dr(d0, diff_scale(gx, nx), dxp - dxm, mxp - mxm, diff_scale(gy, ny), dyp - dym,
+                                myp - mym, diff_scale(zo, nz), dzp - dzm, mzp - mzm,
+                                a.force_mode == DISC_FORCE_DOUBLE);
+        const float drx = dr.x, dry = dr.y, drz = dr.z;
         const float rx = __ldg(a.r + g), ry = __ldg(a.r + N + g), rz = __ldg(a.r + 2 * N + g);
         const float keep = a.u_is_dr ? 0.0f : 1.0f;   // u = r + dr, or dr alone
         a.out[g] = fmaf(keep, rx, drx);
         a.out[N + g] = fmaf(keep, ry, dry);
         a.out[2 * N + g] = fmaf(keep, rz, drz);
         const bool nin = a.norm_hi <= a.norm_lo || (zo >= a.norm_lo && zo < a.norm_hi);   // the plane enters the norm sums
-        acc0 += nin ? sqrtf(fmaf(drx, drx, fmaf(dry, dry, drz * drz))) : 0.0f;
-        acc1 += nin ? sqrtf(fmaf(rx, rx, fmaf(ry, ry, rz * rz))) : 0.0f;
+        acc0 += nin ? norm3(drx, dry, drz) : 0.0f;
+        acc1 += nin ? norm3(rx, ry, rz) : 0.0f;
       }
     }
     // the next plane's stage 1 and 2a do not touch the d ring; stage 2b's write

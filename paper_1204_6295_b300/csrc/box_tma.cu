@@ -482,34 +482,17 @@ __device__ __forceinline__ bool box_tma_body(const BoxArgs& a, int bx, int by, i
       for (int i = 0; i < B::KO; ++i) {
         const int fi = fo3[i];
         if (fi < 0) continue;
-        const float d0 = dp[fi];
-        const float gdx = sxo * (dp[fi + rxo] - dp[fi + lxo]);
-        const float gmx = sxo * (mp[fi + rxo] - mp[fi + lxo]);
-        const float gdy = syo[i] * (dp[fi + ryo[i]] - dp[fi + lyo[i]]);
-        const float gmy = syo[i] * (mp[fi + ryo[i]] - mp[fi + lyo[i]]);
-        const float gdz = sz * (dzp[fi] - dzm[fi]);
-        const float gmz = sz * (mzp[fi] - mzm[fi]);
-        const float gfx = gdx + gmx, gfy = gdy + gmy, gfz = gdz + gmz;
-        const float diff = d0;
-        const float d2 = diff * diff;
-        const float den = fmaf(gfx, gfx, fmaf(gfy, gfy, fmaf(gfz, gfz, d2)));
-        const float sc = den > 1e-9f ? __fdividef(diff, den) : 0.0f;
-        float drx = sc * gfx, dry = sc * gfy, drz = sc * gfz;
-        if (a.force_mode == DISC_FORCE_DOUBLE) {
-          const float den2 = fmaf(gmx, gmx, fmaf(gmy, gmy, fmaf(gmz, gmz, d2)));
-          const float s2 = den2 > 1e-9f ? __fdividef(diff, den2) : 0.0f;
-          drx = fmaf(s2, gmx, drx);
-          dry = fmaf(s2, gmy, dry);
-          drz = fmaf(s2, gmz, drz);
-        }
+        const Dr dr = demons_dr(dp[fi], sxo, dp[fi + rxo] - dp[fi + lxo], mp[fi + rxo] - mp[fi + lxo], syo[i],
+                                dp[fi + ryo[i]] - dp[fi + lyo[i]], mp[fi + ryo[i]] - mp[fi + lyo[i]], sz,
+                                dzp[fi] - dzm[fi], mzp[fi] - mzm[fi], a.force_mode == DISC_FORCE_DOUBLE);
         const int o = tid + i * kThreads;
         const float rx = ro[o], ry = ro[B::TN + o], rz = ro[2 * B::TN + o];   // staged by group B
         float* po = out0 + goff3[i];
-        po[0] = fmaf(keep, rx, drx);
-        po[(size_t)N] = fmaf(keep, ry, dry);
-        po[2 * (size_t)N] = fmaf(keep, rz, drz);
-        acc0 += nin ? sqrt_approx(fmaf(drx, drx, fmaf(dry, dry, drz * drz))) : 0.0f;
-        acc1 += nin ? sqrt_approx(fmaf(rx, rx, fmaf(ry, ry, rz * rz))) : 0.0f;
+        po[0] = fmaf(keep, rx, dr.x);
+        po[(size_t)N] = fmaf(keep, ry, dr.y);
+        po[2 * (size_t)N] = fmaf(keep, rz, dr.z);
+        acc0 += nin ? norm3(dr.x, dr.y, dr.z) : 0.0f;
+        acc1 += nin ? norm3(rx, ry, rz) : 0.0f;
       }
     }
     // the next step's stage 1 rewrites the z sums, group B the zs and r slots,

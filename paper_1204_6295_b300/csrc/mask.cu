@@ -273,34 +273,18 @@ __global__ void __launch_bounds__(kForceThreads) k_force_dm(ForceArgs f) {
     diff_coeffs(z, nz, plane, lz, rz, sz);
     const float* dp = f.d + g;
     const float* mp = f.m + g;
-    const float d0 = dp[0];
-    const float gdx = sx * (dp[rx] - dp[lx]);
-    const float gmx = sx * (mp[rx] - mp[lx]);
-    const float gdy = sy * (dp[ry] - dp[ly]);
-    const float gmy = sy * (mp[ry] - mp[ly]);
-    const float gdz = sz * (dp[rz] - dp[lz]);
-    const float gmz = sz * (mp[rz] - mp[lz]);
-    const float gfx = gdx + gmx, gfy = gdy + gmy, gfz = gdz + gmz;   // grad I'_s = grad d + grad m
-    const float diff = d0;
-    const float d2 = diff * diff;
-    const float den = fmaf(gfx, gfx, fmaf(gfy, gfy, fmaf(gfz, gfz, d2)));
-    const float sc = den > 1e-9f ? __fdividef(diff, den) : 0.0f;
-    float drx = sc * gfx, dry = sc * gfy, drz = sc * gfz;
-    if (f.force_mode == DISC_FORCE_DOUBLE) {
-      const float den2 = fmaf(gmx, gmx, fmaf(gmy, gmy, fmaf(gmz, gmz, d2)));
-      const float s2 = den2 > 1e-9f ? __fdividef(diff, den2) : 0.0f;
-      drx = fmaf(s2, gmx, drx);
-      dry = fmaf(s2, gmy, dry);
-      drz = fmaf(s2, gmz, drz);
-    }
+    // grad I'_s = grad d + grad m
+    const Dr dr = demons_dr(dp[0], sx, dp[rx] - dp[lx], mp[rx] - mp[lx], sy, dp[ry] - dp[ly], mp[ry] - mp[ly], sz,
+                            dp[rz] - dp[lz], mp[rz] - mp[lz], f.force_mode == DISC_FORCE_DOUBLE);
+    const float drx = dr.x, dry = dr.y, drz = dr.z;
     const float rxv = __ldg(f.r + g), ryv = __ldg(f.r + (size_t)N + g), rzv = __ldg(f.r + 2 * (size_t)N + g);
     const float keep = f.u_is_dr ? 0.0f : 1.0f;   // u = r + dr, or dr alone
     f.u[g] = fmaf(keep, rxv, drx);
     f.u[(size_t)N + g] = fmaf(keep, ryv, dry);
     f.u[2 * (size_t)N + g] = fmaf(keep, rzv, drz);
     const bool nin = f.norm_hi <= f.norm_lo || (z >= f.norm_lo && z < f.norm_hi);   // the plane enters the norm sums
-    acc0 += nin ? sqrt_approx(fmaf(drx, drx, fmaf(dry, dry, drz * drz))) : 0.0f;
-    acc1 += nin ? sqrt_approx(fmaf(rxv, rxv, fmaf(ryv, ryv, rzv * rzv))) : 0.0f;
+    acc0 += nin ? norm3(drx, dry, drz) : 0.0f;
+    acc1 += nin ? norm3(rxv, ryv, rzv) : 0.0f;
   }
   __shared__ float red[2][kForceThreads / 32];
   for (int off = 16; off > 0; off >>= 1) {

@@ -59,7 +59,7 @@ def test_stopped_level_costs_no_kernels(disc):
     kw = dict(patch=(3, 3, 3), sigma=1.0, levels=1, iters=(3000,), stop_eps=1e-2)
     times = {}
     for mode in ("loop", "unrolled"):
-        with _Env(**MODES[mode]):
+        with disc.test_switches(MODES[mode]):
             reg = disc.Registration(**kw)
         with reg:
             reg.set_images(pair.ct, pair.cbct)

@@ -131,6 +131,13 @@ def test_mask_and_fill(disc, shape, patch, fill_t, passes):
     if passes < 32:
         assert (fst < 0).any()                   # the cap left some voxels unfilled
     assert rel_err(host(a), fa) <= 1e-4
+    # a of Eq. 5 where it is not filled and both patch variances are well away
+    # from the quantisation (> 1 HU^2): 1e-5 relative, voxel by voxel
+    EM, EM2 = O.patch_moments(m64, half)
+    good = (fst == 0) & (np.maximum(EM2 - EM * EM, 0.0) > 1.0) & (np.maximum(ES2 - ES * ES, 0.0) > 1.0)
+    assert good.mean() > 0.5
+    ag = host(a)
+    assert np.all(np.abs(ag[good] - fa[good]) <= 1e-5 * np.abs(fa[good]))
     # b = E(M) - a E(S) cancels: its error scales with the intensities, not with b
     assert np.abs(host(b) - fb).max() <= 1e-4 * np.abs(fa * Is64).max()
     f_ref = fa * Is64 + fb
@@ -174,7 +181,77 @@ def test_registration_mask_with_nothing_masked_equals_plain(disc):
     np.testing.assert_array_equal(fields[0], fields[1])
 
 
-def test_registration_masked_matches_oracle(disc):
+BAND = 1e-4      # relative margin within which float32 and float64 may decide xi differently
+
+
+def _oracle_masked_run(ct, Is, p):
+    """The oracle's masked registration (as O.register), also returning the smallest
+    relative margin of any xi decision (Eq. 7) of the run: | |m - I_s| - HU0 | / HU0
+    and |a - a_min| / a_min, |a - a_max| / a_max where a is defined."""
+    I_m, I_s = ct.astype(np.float64), Is.astype(np.float64)
+    I_s, dhu = O.global_shift(I_m, I_s)
+    a_m = O.ratio_median(I_m, I_s, p.half, p.var_floor)
+    mask = O.MaskState(p.hu0_factor * abs(dhu), p.a_lo * a_m, p.a_hi * a_m)
+    pm, ps = O.build_pyramid(I_m, p.levels), O.build_pyramid(I_s, p.levels)
+    r = np.zeros((3,) + pm[-1].shape)
+    worst, masked, in_band, decisions = 1.0, [], 0, 0
+    for lev in range(p.levels - 1, -1, -1):
+        for _ in range(p.iters[p.levels - 1 - lev]):
+            m = O.warp(pm[lev], r)
+            a, _ = O.intensity_coefficients(m, ps[lev], p.half, p.var_floor)
+            ES, ES2 = O.patch_moments(ps[lev], p.half)
+            valid = np.maximum(ES2 - ES * ES, 0.0) > p.var_floor
+            hm = np.abs(np.abs(m - ps[lev]) - mask.hu0) / mask.hu0
+            am = np.minimum(np.abs(a - mask.a_min) / mask.a_min, np.abs(a - mask.a_max) / mask.a_max)[valid]
+            worst = min(worst, hm.min(), am.min() if am.size else 1.0)
+            in_band += int(np.count_nonzero(hm <= BAND) + np.count_nonzero(am <= BAND))
+            decisions += hm.size
+            masked.append(O.mask_xi(m, ps[lev], a, valid, mask.hu0, mask.a_min, mask.a_max).mean())
+            r, _, _, _ = O.iteration(pm[lev], ps[lev], r, p, mask)
+        if lev > 0:
+            r = O.upsample_field2(r, pm[lev - 1].shape)
+    return r, worst, masked, mask, (in_band, decisions)
+
+
+def test_registration_masked_matches_oracle_at_full_bars(disc):
+    """A masked registration whose every xi decision (at every voxel and
+    iteration of the oracle's run) lies further than BAND from its threshold:
+    float32 and float64 then take the same decisions, and the field must meet
+    the end-to-end bars (1e-2 voxel max, 1e-4 mean) everywhere.  The thresholds'
+    factors are stepped from the paper's (2, 0.5, 1.5) until the oracle's run has
+    no decision inside the band."""
+    shape = (12, 24, 40)
+    ct, Is = _pair(shape, 9)
+    kw = dict(patch=(3, 3, 3), sigma=1.0, levels=2, iters=(5, 4), mask_mode=1)
+    for t in range(16):
+        f = dict(hu0_factor=2.0 * 1.013 ** t, a_lo=0.5 * 0.987 ** t, a_hi=1.5 * 1.011 ** t)
+        p = O.Params(patch=kw["patch"], sigma=kw["sigma"], levels=kw["levels"], iters=list(kw["iters"]),
+                     mask_mode=1, **f)
+        ref, worst, masked, mask, _ = _oracle_masked_run(ct, Is, p)
+        if worst > BAND:
+            break
+    assert worst > BAND, worst
+    assert min(masked) > 0.01                      # the mask and the fill are exercised
+    reg = disc.Registration(**kw, **f)
+    reg.set_images(dev(ct), dev(Is))
+    hu0, a_m = reg.mask_constants()
+    reg.iterate(-1)
+    out = empty(3, *shape)
+    reg.get_field(out)
+    reg.close()
+    disc.k_check_error()
+    assert hu0 == pytest.approx(mask.hu0, rel=1e-5)
+    assert a_m * f["a_lo"] == pytest.approx(mask.a_min, rel=1e-5)
+    diff = np.sqrt(((host(out) - ref) ** 2).sum(0))
+    assert diff.max() <= 1e-2 and diff.mean() <= 1e-4, (diff.max(), diff.mean())
+
+
+def test_registration_masked_with_threshold_ties(disc):
+    """The paper's threshold factors on a larger pair, where some xi decisions of
+    the run lie within BAND of their thresholds: the two precisions may decide
+    those differently.  Checks that such decisions are rare (under 0.01% of the
+    run's decisions lie in the band) and that the field stays within a
+    documented looser bar (mean 1e-3, 99.9th percentile 1e-2 voxel)."""
     shape = (16, 32, 48)
     ct, Is = _pair(shape, 9)
     kw = dict(patch=(3, 3, 3), sigma=1.0, levels=2, iters=(6, 5), mask_mode=1)
@@ -184,14 +261,17 @@ def test_registration_masked_matches_oracle(disc):
     reg.iterate(-1)
     out = empty(3, *shape)
     reg.get_field(out)
+    reg.close()
     disc.k_check_error()
     p = O.Params(patch=(3, 3, 3), sigma=1.0, levels=2, iters=[6, 5], mask_mode=1)
     ref = O.register(ct, Is, p)
+    ref2, worst, _, _, (in_band, decisions) = _oracle_masked_run(ct, Is, p)
+    np.testing.assert_array_equal(ref, ref2)      # the replay is the oracle's registration
+    assert worst <= BAND and 0 < in_band <= 1e-4 * decisions, (worst, in_band, decisions)
     _, dhu = O.global_shift(ct, Is)
     assert hu0 == pytest.approx(2.0 * abs(dhu), rel=1e-5)
     Is_sh = Is.astype(np.float64) + dhu
     assert a_m == pytest.approx(O.ratio_median(ct, Is_sh, (1, 1, 1)), rel=1e-4)
-    diff = np.abs(host(out) - ref)
-    # isolated threshold decisions may differ between float32 and float64 (see above)
+    diff = np.sqrt(((host(out) - ref) ** 2).sum(0))
     assert np.mean(diff) <= 1e-3
     assert np.quantile(diff, 0.999) <= 1e-2
