@@ -82,7 +82,7 @@ def load_peaks():
         return 6400.0, "fallback"
 
 
-ROOFLINE_SOURCES = ("box_tma.cu", "box_dev.cuh", "box_pass.cu")   # the box kernel and its planner
+ROOFLINE_SOURCES = ("box_wide.cu", "box_tma.cu", "box_dev.cuh", "box_pass.cu", "tma_dev.cuh")   # the pass and its planner
 
 
 def source_digest():
@@ -735,7 +735,10 @@ def run_ours(args, w, rank, world, local_rank):
                    "voxel_iterations_per_step": units, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2: finest-level working set "
                          f"{(9 * nx * ny * nz * 4) / 1e6:.0f} MB > 126 MB"},
-        "roofline": {"bound": "hbm", "kernel": "k_box_tma<kModeIterate> (patch moments, correction, force, update; bulk-tensor-copy fed)",
+        "roofline": {"bound": "hbm",
+                     "kernel": "the iteration pass at the finest level (patch moments, correction, force, update): "
+                               "k_box_wide (32 x 32 tiles, balanced z shares, bulk-tensor-copy fed) where the "
+                               "planner picks it, as on the 512x512x256 and 256x256x128 finest levels",
                      "achieved": box_gbs, "peak": peak, "unit": "GB/s", "frac": box_gbs / peak,
                      "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                      "traffic": traffic, "algorithmic_bytes_per_voxel": BOX_BYTES_PER_VOXEL,

@@ -177,6 +177,19 @@ disc_status disc_get_corrected(disc_ctx* ctx, float* out, int mem_kind);
 disc_status disc_set_field(disc_ctx* ctx, int32_t level, const float* r,
                            int mem_kind);
 
+/* Differentiable form on the context's own data (not in the paper): for a
+ * field r on pyramid level `level` ([3][nz][ny][nx] of that level, its voxel
+ * units), the SSD between the warped CT and the moment-matched CBCT of that
+ * level, L(r) = sum_x (I_m(x + r(x)) - I'_s(x))^2 (as disc_k_ssd_loss, with the
+ * context's CBCT normalisation zs and fixed-point scale), into *loss (host
+ * double, may be NULL), and dL/dr into grad (same layout and memory kind as r,
+ * may be NULL; as disc_k_ssd_grad: cubic patches of half size 1..8 only, else
+ * DISC_ERR_SHAPE).  At least one of loss and grad is required.  Does not change
+ * the registration's state (field, level, iteration count); the next
+ * disc_iterate rebuilds the scratch this call uses.  Synchronises when loss is
+ * requested or the buffers are host memory. */
+disc_status disc_ssd(disc_ctx* ctx, int32_t level, const float* r, double* loss, float* grad, int mem_kind);
+
 /* Position in the schedule: current level (0 = finest) and iterations
  * already run at it.  *dims receives that level's (nx, ny, nz) if non-NULL. */
 disc_status disc_get_progress(disc_ctx* ctx, int32_t* level, int32_t* iter,
@@ -384,7 +397,10 @@ disc_status disc_k_ssd_grad(const float* Im, const float* zs, const float* r, fl
  * under a fixed memory budget, and hosts that forbid plug-ins from calling
  * cudaMalloc or the stream-ordered allocator).  Same computation and outputs
  * as disc_k_pass_a, except that m_out is required (it receives m and is the
- * working buffer the moment pass reads).  The only scratch, the per-CTA norm
+ * working buffer the moment pass reads), and that it always runs the 32 x 16
+ * tiling (on volumes large enough for disc_k_pass_a's wide-tile pass, m, d and
+ * u are the same bits but the norms may differ in their last bits: their float
+ * partial sums are grouped by other CTAs).  The only scratch, the per-CTA norm
  * partial sums, lives in a fixed 64 KiB __device__ array inside the library,
  * present on every device that loads it until the process exits; launches
  * that would need more than 8192 CTAs (roughly, planes larger than about
@@ -496,9 +512,14 @@ disc_status disc_k_check_error(void* stream);
  *   DISC_SW_UNROLLED_GRAPH  contexts created afterwards use unrolled graphs
  *                           even with a stop rule;
  *   DISC_SW_FAULT_ALLOC     disc_set_images's first device allocation reports
- *                           out-of-memory (host-side fault injection).
+ *                           out-of-memory (host-side fault injection);
+ *   DISC_SW_WIDE_ANY        iteration passes planned afterwards take the
+ *                           wide-tile kernel wherever it applies, whatever the
+ *                           volume's size (same results; the planner otherwise
+ *                           keeps it for volumes large enough to fill the GPU).
  * The initial bits come from the environment (DISC_NO_TMA, DISC_TEST_TMA_STALL,
- * DISC_NO_GRAPH, DISC_UNROLLED_GRAPH set to a non-zero value; DISC_FAULT=alloc),
+ * DISC_NO_GRAPH, DISC_UNROLLED_GRAPH, DISC_WIDE_ANY set to a non-zero value;
+ * DISC_FAULT=alloc),
  * read once when the library is loaded.  disc_set_test_switches replaces all
  * bits; *previous (may be NULL) receives the old ones.  DISC_ERR_ARG for an
  * unknown bit.  Not synchronised with work in flight: change the switches
@@ -509,7 +530,8 @@ enum {
   DISC_SW_NO_GRAPH = 4,
   DISC_SW_UNROLLED_GRAPH = 8,
   DISC_SW_FAULT_ALLOC = 16,
-  DISC_SW_ALL = 31
+  DISC_SW_WIDE_ANY = 32,
+  DISC_SW_ALL = 63
 };
 disc_status disc_set_test_switches(uint32_t flags, uint32_t* previous);
 

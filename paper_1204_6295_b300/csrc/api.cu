@@ -526,7 +526,7 @@ BoxArgs ctx_box_args(const disc_ctx* c, int l) {
   a.stop = c->d_stop + l;
   a.qscale = c->qs_m;
   a.inv_qscale = 1.0f / c->qs_m;
-  a.zlen = v.pa.zlen;
+  a.zlen = v.pn.zlen;
   return a;
 }
 
@@ -697,7 +697,8 @@ disc_status disc_set_images(disc_ctx* ctx, const float* ct, const float* cbct, i
       v.ny = dims[l][1];
       v.nz = dims[l][2];
       v.N = (size_t)v.nx * v.ny * v.nz;
-      v.pa = box_plan(kModeIterate, v.nx, v.ny, v.nz, ctx->hx, ctx->hy, ctx->hz, ctx->num_sms);
+      v.pa = box_plan_iter(v.nx, v.ny, v.nz, ctx->hx, ctx->hy, ctx->hz, ctx->num_sms, nullptr);
+      v.pn = box_plan(kModeIterate, v.nx, v.ny, v.nz, ctx->hx, ctx->hy, ctx->hz, ctx->num_sms);
       v.pb = gauss_plan(v.nx, v.ny, v.nz, ctx->R, ctx->num_sms);
       BoxPlan ps = box_plan(kModeStatic, v.nx, v.ny, v.nz, ctx->hx, ctx->hy, ctx->hz, ctx->num_sms);
       if (v.pa.grid.x == 0 || v.pb.grid.x == 0 || ps.grid.x == 0) {
@@ -705,7 +706,9 @@ disc_status disc_set_images(disc_ctx* ctx, const float* ct, const float* cbct, i
         return DISC_ERR_SHAPE;   // patch or radius too large for shared memory
       }
       const int np = (int)(v.pa.grid.x * v.pa.grid.y * v.pa.grid.z);
+      const int nn = (int)(v.pn.grid.x * v.pn.grid.y * v.pn.grid.z);
       if (np > max_parts) max_parts = np;
+      if (nn > max_parts) max_parts = nn;
       v.hist_cap = ctx->p.iters[L - 1 - l] > 0 ? ctx->p.iters[L - 1 - l] : 1;
       int lo = ctx->p.norm_planes[0], hi = ctx->p.norm_planes[1];
       for (int k = 0; k < l; ++k) {
@@ -1027,6 +1030,49 @@ disc_status disc_get_level_field(disc_ctx* ctx, int32_t level, float* out, int m
   return DISC_OK;
 }
 
+disc_status disc_ssd(disc_ctx* ctx, int32_t level, const float* r, double* loss, float* grad, int mem_kind) {
+  if (!ctx || !r || (!loss && !grad)) return DISC_ERR_ARG;
+  if (mem_kind != DISC_MEM_HOST && mem_kind != DISC_MEM_DEVICE) return DISC_ERR_ARG;
+  if (ctx->sticky != DISC_OK) return DISC_ERR_STATE;
+  if (!ctx->have_images) return DISC_ERR_STATE;
+  if (level < 0 || level >= ctx->L) return DISC_ERR_ARG;
+  DeviceGuard guard(ctx->device);
+  if (!guard.ok) return DISC_ERR_CUDA;
+  CK(enter(ctx));
+  Level& v = ctx->lev[level];
+  const size_t bytes = 3 * v.N * sizeof(float);
+  // host fields go through the level's u and t buffers, which every iteration
+  // rewrites before reading (its warp rebuilds m as well)
+  const float* rd = r;
+  if (mem_kind == DISC_MEM_HOST) {
+    CK(memcpy_kind(v.u, r, bytes, DISC_MEM_DEVICE, DISC_MEM_HOST, ctx->s));
+    rd = v.u;
+  }
+  float* gd = grad && mem_kind == DISC_MEM_HOST ? v.t : grad;
+  double* dl = nullptr;
+  if (loss) CK(cudaMallocAsync(&dl, sizeof(double), ctx->s));
+  const int32_t patch[3] = {ctx->p.patch[0], ctx->p.patch[1], ctx->p.patch[2]};
+  disc_status st = gd ? disc_k_ssd_grad(v.Im, v.zs, rd, gd, dl, v.nx, v.ny, v.nz, patch, ctx->qs_m,
+                                        ctx->p.var_floor, ctx->s)
+                      : disc_k_ssd_loss(v.Im, v.zs, rd, dl, v.nx, v.ny, v.nz, patch, ctx->qs_m, ctx->p.var_floor,
+                                        ctx->s);
+  if (st == DISC_OK && grad && mem_kind == DISC_MEM_HOST)
+    CK(memcpy_kind(grad, gd, bytes, DISC_MEM_HOST, DISC_MEM_DEVICE, ctx->s));
+  double lv = 0.0;
+  if (st == DISC_OK && loss) CK(cudaMemcpyAsync(&lv, dl, sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+  if (dl) CK(cudaFreeAsync(dl, ctx->s));
+  if (st != DISC_OK) {
+    if (st == DISC_ERR_CUDA && ctx->sticky == DISC_OK) ctx->sticky = DISC_ERR_CUDA;
+    return st;
+  }
+  if (loss || mem_kind == DISC_MEM_HOST) {
+    CK_DEV(ctx);                              // synchronises the stream
+    if (loss) *loss = lv;
+  }
+  CK(leave(ctx));
+  return DISC_OK;
+}
+
 disc_status disc_set_field(disc_ctx* ctx, int32_t level, const float* r, int mem_kind) {
   if (!ctx || !r) return DISC_ERR_ARG;
   if (mem_kind != DISC_MEM_HOST && mem_kind != DISC_MEM_DEVICE) return DISC_ERR_ARG;
@@ -1305,7 +1351,8 @@ disc_status disc_k_edge_rmse(const uint8_t* e1, const uint8_t* e2, int64_t n, do
 
 disc_status disc_k_check_error(void* stream) {
   int flag = 0;
-  if (box_tma_error((cudaStream_t)stream, &flag) != cudaSuccess) {
+  if (box_tma_error((cudaStream_t)stream, &flag) != cudaSuccess ||
+      box_wide_error((cudaStream_t)stream, &flag) != cudaSuccess) {
     cudaGetLastError();
     return DISC_ERR_CUDA;
   }
@@ -1422,7 +1469,7 @@ disc_status disc_k_pass_a(const float* Im, const float* zs, const float* r, floa
   int dev = 0, sms = kNumSMs;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  BoxPlan p = box_plan(kModeIterate, nx, ny, nz, h[0], h[1], h[2], sms);
+  BoxPlan p = box_plan_iter(nx, ny, nz, h[0], h[1], h[2], sms, m_out);   // m_out NULL: pool memory, aligned
   if (p.grid.x == 0) return DISC_ERR_SHAPE;
   cudaStream_t s = (cudaStream_t)stream;
   disc_ctx* ctx = nullptr;
@@ -1479,7 +1526,7 @@ disc_status disc_k_force_update(const float* m, const float* zs, const float* r,
   int dev = 0, sms = kNumSMs;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  BoxPlan p = box_plan(kModeIterate, nx, ny, nz, h[0], h[1], h[2], sms);
+  BoxPlan p = box_plan_iter(nx, ny, nz, h[0], h[1], h[2], sms, m);
   if (p.grid.x == 0) return DISC_ERR_SHAPE;
   cudaStream_t s = (cudaStream_t)stream;
   disc_ctx* ctx = nullptr;

@@ -104,10 +104,10 @@ void make_box_table(disc_batch* b, int l, int zmult, int* total) {
     const disc_ctx* c = b->pair[i];
     const Level& v = c->lev[l];
     BoxArgs a = ctx_box_args(c, l);
-    a.zlen = zmult > 0 ? v.pa.zlen * zmult : (-zmult > v.pa.zlen ? -zmult : v.pa.zlen);
+    a.zlen = zmult > 0 ? v.pn.zlen * zmult : (-zmult > v.pn.zlen ? -zmult : v.pn.zlen);
     if (a.zlen > v.nz) a.zlen = v.nz;
     h.args[i] = a;
-    h.grid[i] = dim3(v.pa.grid.x, v.pa.grid.y, (v.nz + a.zlen - 1) / a.zlen);
+    h.grid[i] = dim3(v.pn.grid.x, v.pn.grid.y, (v.nz + a.zlen - 1) / a.zlen);
     h.offset[i] = off;
     off += (int)(h.grid[i].x * h.grid[i].y * h.grid[i].z);
   }

@@ -388,8 +388,32 @@ BoxPlan box_plan(int mode, int nx, int ny, int nz, int hx, int hy, int hz, int n
   return p;
 }
 
+BoxPlan box_plan_iter(int nx, int ny, int nz, int hx, int hy, int hz, int num_sms, const float* src) {
+  // the wide-tile pass where its one wave gets enough planes per CTA to
+  // amortise the z warm-up of a march; the 32 x 16 tiling otherwise
+  if (((uintptr_t)src & 15u) == 0u && box_wide_ok(nx, ny, nz, hx, hy, hz)) {
+    int tx = 0, ty = 0;
+    box_wide_tile(&tx, &ty);
+    const int occ = box_wide_occupancy(hx);
+    const long long slots = (long long)num_sms * (occ < 1 ? 1 : occ);
+    const long long P = (long long)((nx + tx - 1) / tx) * ((ny + ty - 1) / ty) * nz;
+    if (occ >= 1 && (P >= kWideMinPlanes * slots || (test_switches() & DISC_SW_WIDE_ANY))) {
+      BoxPlan p;
+      p.tx = tx;
+      p.ty = ty;
+      p.fast = p.tma = p.wide = true;
+      p.smem = box_wide_smem(hx);
+      p.zlen = nz;
+      p.grid = dim3((unsigned)slots, 1, 1);
+      return p;
+    }
+  }
+  return box_plan(kModeIterate, nx, ny, nz, hx, hy, hz, num_sms);
+}
+
 cudaError_t box_launch(int mode, const BoxArgs& a, const BoxPlan& p, cudaStream_t s) {
   if (p.grid.x == 0) return cudaErrorInvalidConfiguration;
+  if (p.wide) return mode == kModeIterate ? box_wide_launch(a, p, s) : cudaErrorInvalidValue;
   BoxArgs b = a;
   b.zlen = p.zlen;
   if (p.tma) {

@@ -32,6 +32,7 @@
 
 #include "box_dev.cuh"
 #include "internal.cuh"
+#include "tma_dev.cuh"
 
 namespace disc {
 
@@ -40,9 +41,6 @@ namespace {
 // Error word of launches that were given none (kernel-level entry points).
 __device__ int g_box_err;
 
-constexpr int ceil4(int v) { return (v + 3) & ~3; }
-constexpr size_t al128(size_t v) { return (v + 127) & ~(size_t)127; }
-constexpr long long kWaitCycles = 2000000000LL;   // about 1 s at the B300 SM clock
 
 template <int MODE, int H>
 struct TmaLayout {
@@ -94,63 +92,6 @@ struct TmaLayout {
   static constexpr int WST = (int)(o_red / al128(WB));
   static_assert(WST >= 2, "staging area");
 };
-
-// ---- PTX wrappers: mbarrier and bulk tensor copies ---------------------------
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-// make the initialised barriers visible to the async (TMA) proxy
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Wait for the phase of the given parity to complete; false after kWaitCycles.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > kWaitCycles) return false;
-  return true;
-}
-
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
-                                            uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-      "[%5];" ::"r"(smem_addr(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int x, int y, int z, int c,
-                                            uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
-      "%5}], [%6];" ::"r"(smem_addr(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(c), "r"(smem_addr(bar))
-      : "memory");
-}
 
 // Step bookkeeping shared by every thread (all values are CTA-uniform).
 struct March {
@@ -591,34 +532,9 @@ __global__ void __launch_bounds__(kThreads, 3)
 }
 
 // ---- host side ---------------------------------------------------------------
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static std::once_flag once;
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  std::call_once(once, [] {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    else
-      cudaGetLastError();
-  });
-  return fn;
-}
-
-// Plane-wise float32 volume [nz][ny][nx] (rank 3) or field [3][nz][ny][nx] (rank 4).
 bool encode(CUtensorMap* m, const float* base, int rank, int nx, int ny, int nz, uint32_t bx, uint32_t by,
             uint32_t bc) {
-  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
-  if (!fn) return false;
-  const cuuint64_t dims[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, 3};
-  const cuuint64_t strides[3] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4, (cuuint64_t)nx * ny * nz * 4};
-  const cuuint32_t box[4] = {bx, by, 1, bc};
-  const cuuint32_t es[4] = {1, 1, 1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, const_cast<float*>(base), dims, strides,
-            box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  return tma_encode_volume(m, base, rank, nx, ny, nz, bx, by, bc);
 }
 
 constexpr int kMaxDevices = 64;
@@ -767,7 +683,7 @@ bool box_tma_ok(int mode, int nx, int ny, int nz, int hx, int hy, int hz) {
   if (nx % 4 != 0) return false;             // row stride: a multiple of 16 bytes
   const int ex = dispatch<Extent, int>(mode, hx, 0, 0), ey = dispatch<Extent, int>(mode, hx, 0, 1);
   if (ex == 0 || nx < ex || ny < ey || nz < 1) return false;
-  return encode_fn() != nullptr;
+  return tma_encode_available();
 }
 
 bool box_tma_aligned(int mode, const BoxArgs& a) {
@@ -796,6 +712,42 @@ cudaError_t box_tma_launch_batch(const BoxBatch& bt, const void* maps, int h, in
   if (grid < 1) return cudaSuccess;
   return dispatch<LaunchBatch, cudaError_t>(kModeIterate, h, cudaErrorInvalidValue, &bt,
                                             static_cast<const CUtensorMap*>(maps), grid, s);
+}
+
+// ---- tensor-map encoding shared by the bulk-copy-fed kernels ---------------------
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+}  // namespace
+
+bool tma_encode_available() { return encode_fn() != nullptr; }
+
+// Plane-wise float32 volume [nz][ny][nx] (rank 3) or field [3][nz][ny][nx] (rank 4).
+bool tma_encode_volume(CUtensorMap* m, const float* base, int rank, int nx, int ny, int nz, uint32_t bx,
+                       uint32_t by, uint32_t bc) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, 3};
+  const cuuint64_t strides[3] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4, (cuuint64_t)nx * ny * nz * 4};
+  const cuuint32_t box[4] = {bx, by, 1, bc};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, const_cast<float*>(base), dims, strides,
+            box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 cudaError_t box_tma_error(cudaStream_t s, int* flag) {

@@ -1,0 +1,540 @@
+// Moment, correction, force and update pass on wide tiles (iteration mode,
+// cubic patches, sm_103a): the hot pass of every iteration on the large levels.
+//
+// Same arithmetic as the other cubic-patch kernels (box_fast.cu, box_tma.cu),
+// so the outputs are bit-identical: exact integer sliding sums of q = rint(v 2^e)
+// and q^2 over the truncated patch (Eq. 3), the patch moments (Appendix A.4),
+// the moment-matched CBCT kept as d = I'_s - m (Eqs. 5-6), the demons force of
+// Eq. (1) with grad I'_s = grad d + grad m, and u = r + dr (Algorithm A1 steps
+// 3-5).  What differs is the work per voxel:
+//  - tiles of TX x TY = 32 x 32 columns (two CTAs of 256 threads per SM): the
+//    patch halo of the z sums costs 1.9 summed columns per output voxel at
+//    patch 11^3 (2.4 on 32 x 16 tiles) and the x sums 1.5 (1.9);
+//  - only the patch-halo boxes of m travel by bulk tensor copy (the entering
+//    plane, the leaving plane and the moment region of the centre plane, one
+//    group per z step); zs and r, read once per voxel, are loaded straight into
+//    registers at the top of the step that uses them, so their latency hides
+//    behind the sums;
+//  - the q^2 z sums advance by one 32 x 32 -> 64-bit multiply-add,
+//    q_new^2 - q_old^2 = (q_new - q_old)(q_new + q_old);
+//  - the z-sum and x-sum planes have odd row strides (no bank conflicts on the
+//    column-wise 64-bit reads);
+//  - each CTA marches a balanced share of all (tile, plane) pairs of the volume,
+//    possibly two tiles in turn, so every CTA of the single wave ends together.
+// Every wait on a copy is bounded: after about a second without completion the
+// CTA raises the error word, waits (bounded again) for its own copies and
+// returns.
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "box_dev.cuh"
+#include "internal.cuh"
+#include "tma_dev.cuh"
+
+namespace disc {
+
+namespace {
+
+__device__ int g_wide_err;   // error word of launches that were given none
+
+constexpr int kWideThreads = 256;
+
+template <int H, int TX, int TY>
+struct WideLayout {
+  static constexpr int NT = kWideThreads;
+  static constexpr int FX = TX + 2, FY = TY + 2;               // moment region: tile + gradient halo
+  static constexpr int WX = FX + 2 * H, WY = FY + 2 * H;       // z-summed columns: + patch halo
+  static constexpr int WXP = WX | 1;                           // odd row stride of the z sums
+  static constexpr int XBS = FX | 1;                           // odd row stride of the x sums
+  static constexpr int WN = WX * WY;
+  static constexpr int K1 = (WN + NT - 1) / NT;                // z-summed columns per thread
+  static constexpr int XW = ceil4(1 + H);                      // W box: x from x0 - XW,
+  static constexpr int WXT = ceil4(XW + TX + 1 + H);           //   WXT floats wide, WY rows
+  static constexpr int WOFF = XW - 1 - H;                      // column of W element 0 in the box
+  static constexpr int XF = 4;                                 // F box: x from x0 - 4,
+  static constexpr int FXT = ceil4(XF + TX + 1);               //   FXT floats wide, FY rows
+  static constexpr int FO = XF - 1;                            // column of F element 0 in the box
+  static constexpr int FN = FXT * FY;                          // floats of an F plane
+  static constexpr int NMS = 4;                                // F planes of m in flight
+  static constexpr int TN = TX * TY;
+  static constexpr int KO = TN / NT;                           // tile voxels per thread
+  static_assert(TN % NT == 0 && NT % TX == 0, "tile and CTA shape");
+  static constexpr int NSX0 = (NT / WY) < 1 ? 1 : (NT / WY);   // x tasks: segments per W row
+  static constexpr int SX = (FX + NSX0 - 1) / NSX0;
+  static constexpr int NSX = (FX + SX - 1) / SX;
+  static constexpr int NSY0 = (NT / FX) < 1 ? 1 : (NT / FX);   // y tasks: segments per F column
+  static constexpr int SY = (FY + NSY0 - 1) / NSY0;
+  static constexpr int NSY = (FY + SY - 1) / SY;
+  static constexpr int NP = (2 * H + 1) * (2 * H + 1) * (2 * H + 1);
+  static constexpr uint32_t WB = 4u * WXT * WY;                // bytes of a W box
+  static constexpr uint32_t FB = 4u * FXT * FY;                // bytes of an F box
+  static constexpr int MS = (int)(al128(FB) / 4);              // float stride of the m planes
+  // shared memory map; the bulk-copy destinations first, on 128-byte boundaries
+  static constexpr size_t o_wn = 0;                            // W box, entering plane
+  static constexpr size_t o_wo = o_wn + al128(WB);             // W box, leaving plane
+  static constexpr size_t o_mr = o_wo + al128(WB);             // NMS F planes of m
+  static constexpr size_t o_s2z = o_mr + NMS * al128(FB);      // z sums of q^2 (int64)
+  static constexpr size_t o_xb1 = o_s2z + 8 * (size_t)WY * WXP;   // x sums of q (int64)
+  static constexpr size_t o_xb2 = o_xb1 + 8 * (size_t)WY * XBS;  // x sums of q^2 (int64)
+  static constexpr size_t o_s1z = o_xb2 + 8 * (size_t)WY * XBS;  // z sums of q (int32)
+  static constexpr size_t o_dr = o_s1z + 4 * (size_t)WY * WXP;   // 3 F planes of d
+  static constexpr size_t o_red = o_dr + 12 * (size_t)FN;      // norm partials of the warps
+  static constexpr size_t o_bar = (o_red + 8 * (NT / 32) + 7) & ~(size_t)7;   // the mbarrier
+  static constexpr size_t bytes = o_bar + 8;
+  // W boxes the warm-up burst stages at once, over every buffer below o_red
+  static constexpr int WST = (int)(o_red / al128(WB));
+  static_assert(WST >= 2, "staging area");
+};
+
+// One march of tile (bx, by) over output planes [z0, z1).  pa is the phase
+// parity of the copy barrier, carried over the marches of a CTA (every phase
+// armed in a march is awaited in it); acc0, acc1 gather sum |dr| and sum |r|.
+// Returns false when a copy wait gave up: the CTA must stop.
+template <int H, int TX, int TY>
+__device__ __forceinline__ bool wide_march(const BoxArgs& a, int bx, int by, int z0, int z1,
+                                           const CUtensorMap* map_w, const CUtensorMap* map_f, unsigned char* smem,
+                                           uint32_t& pa, float& acc0, float& acc1) {
+  using B = WideLayout<H, TX, TY>;
+  constexpr int NT = B::NT;
+  int* err = a.err ? a.err : &g_wide_err;
+  float* wn = reinterpret_cast<float*>(smem + B::o_wn);
+  float* wo = reinterpret_cast<float*>(smem + B::o_wo);
+  float* mring = reinterpret_cast<float*>(smem + B::o_mr);
+  long long* s2z = reinterpret_cast<long long*>(smem + B::o_s2z);
+  long long* xb1 = reinterpret_cast<long long*>(smem + B::o_xb1);
+  long long* xb2 = reinterpret_cast<long long*>(smem + B::o_xb2);
+  int* s1z = reinterpret_cast<int*>(smem + B::o_s1z);
+  float* dring = reinterpret_cast<float*>(smem + B::o_dr);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + B::o_bar);
+
+  const int tid = threadIdx.x;
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const int plane = nx * ny;                  // 3 N < 2^31 is checked on the host
+  const int N = plane * nz;
+  const int x0 = bx * TX, y0 = by * TY;
+  // planes whose moments are needed (the force of plane z reads d at z - 1 .. z + 1)
+  const int zc_lo = max(0, z0 - 1), zc_hi = min(nz - 1, z1);
+  const int zi0 = max(0, zc_lo - H);          // first plane summed in z
+  const int zw = zc_lo + H;                   // first step with a centre plane
+  const int zi1 = z1 + H;                     // the force of z1 - 1 comes in the step of centre z1
+  const float qs = a.qscale, inv_qs = a.inv_qscale, vfl = a.var_floor;
+  const bool dbl = a.force_mode == DISC_FORCE_DOUBLE;
+  const float keep = a.u_is_dr ? 0.0f : 1.0f;   // u = keep r + dr
+
+  auto bytes_a = [&](int zi) -> uint32_t {
+    const int zc = zi - H;
+    return (zi < nz ? B::WB : 0u) + (zi - (2 * H + 1) >= zi0 ? B::WB : 0u) +
+           (zc >= zc_lo && zc <= zc_hi ? B::FB : 0u);
+  };
+  auto issue_a = [&](int zi) {                // thread 0 only
+    const uint32_t nb = bytes_a(zi);
+    if (nb == 0) return;
+    mbar_expect_tx(bar, zi == zw ? nb + a.stall_tx : nb);
+    const int zo = zi - (2 * H + 1), zc = zi - H;
+    if (zi < nz) tma_load_3d(wn, map_w, x0 - B::XW, y0 - 1 - H, zi, bar);
+    if (zo >= zi0) tma_load_3d(wo, map_w, x0 - B::XW, y0 - 1 - H, zo, bar);
+    if (zc >= zc_lo && zc <= zc_hi)
+      tma_load_3d(mring + ((unsigned)zc % B::NMS) * B::MS, map_f, x0 - B::XF, y0 - 1, zc, bar);
+  };
+  // a wait for phase pa that gives up stops the CTA (after its copies drain)
+  auto wait_a = [&](bool armed) -> bool {
+    int bad = 0;
+    if (armed && tid == 0) bad = !mbar_wait(bar, pa);
+    if (__syncthreads_or(bad)) {
+      if (tid == 0) {
+        atomicOr(err, 1);
+        mbar_wait(bar, pa);                   // bounded: let this CTA's copies drain
+      }
+      __syncthreads();
+      return false;
+    }
+    if (armed) pa ^= 1u;
+    return true;
+  };
+
+  // ---- per-thread maps, fixed for the march -----------------------------------
+  // W column k of this thread: W box index << 16 | z-sum index (-1: none); running z sums
+  int cmap[B::K1], s1r[B::K1];
+  long long s2r[B::K1];
+  static_assert(B::WXT * B::WY < 65536 && B::WXP * B::WY < 65536, "packed column map");
+#pragma unroll
+  for (int k = 0; k < B::K1; ++k) {
+    const int e = tid + k * NT;
+    const int wy = e / B::WX, wx = e - wy * B::WX;
+    cmap[k] = e < B::WN ? ((wy * B::WXT + wx + B::WOFF) << 16) | (wy * B::WXP + wx) : -1;
+    s1r[k] = 0;
+    s2r[k] = 0;
+  }
+  // y task of this thread: F column fx, rows fy0 .. fy0 + SY - 1
+  const int ty_task = tid < B::NSY * B::FX ? tid : -1;
+  const int sy_ = tid / B::FX, fx_y = tid - sy_ * B::FX;
+  const int fy0 = sy_ * B::SY;
+  const int gx_y = x0 - 1 + fx_y;
+  const bool ycol = ty_task >= 0 && gx_y >= 0 && gx_y < nx;
+  const bool xin_y = gx_y >= H && gx_y < nx - H;
+  const int nxc_y = box_count(gx_y, nx, H);
+  // force stage: tile voxels (ox, oy0 + i NT / TX), i < KO
+  const int ox = tid % TX, oy0 = tid / TX;
+  const int gxo = x0 + ox;
+  const int lxo = gxo > 0 ? -1 : 0, rxo = gxo < nx - 1 ? 1 : 0;
+  const float sxo = diff_scale(gxo, nx);
+  const int fi0 = (oy0 + 1) * B::FXT + ox + 1 + B::FO;
+  const int gy0 = y0 + oy0;
+  constexpr int DY = NT / TX;                 // tile rows between a thread's voxels
+
+  // ---- warm-up: planes zi0 .. zw - 1 only enter the z sums; they arrive as
+  // bursts of W boxes over the buffers the march has not used yet, one copy wait
+  // per burst, and are summed in the order the march would have summed them
+  {
+    fence_proxy_async();                      // earlier generic writes of the staging area
+    __syncthreads();
+    const int zb_end = min(zw, nz);
+    for (int zb = zi0; zb < zb_end; zb += B::WST) {
+      const int nb = min(B::WST, zb_end - zb);
+      if (tid == 0) {
+        mbar_expect_tx(bar, (uint32_t)nb * B::WB);
+        for (int j = 0; j < nb; ++j)
+          tma_load_3d(smem + j * al128(B::WB), map_w, x0 - B::XW, y0 - 1 - H, zb + j, bar);
+      }
+      if (!wait_a(true)) return false;
+      for (int j = 0; j < nb; ++j) {
+        const float* wj = reinterpret_cast<const float*>(smem + j * al128(B::WB));
+#pragma unroll
+        for (int k = 0; k < B::K1; ++k) {
+          if (cmap[k] < 0) continue;
+          const int qn = __float2int_rn(wj[cmap[k] >> 16] * qs);
+          s1r[k] += qn;
+          s2r[k] += (long long)qn * qn;
+        }
+      }
+      __syncthreads();                        // the staging area is consumed
+    }
+  }
+  if (tid == 0) issue_a(zw);
+
+  int zc3 = ((zw - H) % 3 + 3) % 3;           // ring slot of the centre plane's d
+  for (int zi = zw; zi <= zi1; ++zi, zc3 = (zc3 == 2 ? 0 : zc3 + 1)) {
+    const int zc = zi - H;                    // centre plane of the patch window
+    const bool do2 = zc >= zc_lo && zc <= zc_hi;
+    const int zf = zc - 1;                    // plane whose force is computed this step
+    const bool do3 = zf >= z0 && zf < z1;
+    // ---- loads into registers for this step: zs of the y task, r of the force --
+    float zsr[B::SY];
+    if (do2 && ycol) {
+      const float* zp = a.zs + (size_t)zc * plane + gx_y;
+#pragma unroll
+      for (int j = 0; j < B::SY; ++j) {
+        const int gy = y0 - 1 + fy0 + j;
+        zsr[j] = (fy0 + j < B::FY && gy >= 0 && gy < ny) ? __ldg(zp + (size_t)gy * nx) : 0.0f;
+      }
+    }
+    float rxr[B::KO], ryr[B::KO], rzr[B::KO];
+    if (do3 && gxo < nx) {
+      const float* rp = a.r + (size_t)zf * plane + (size_t)gy0 * nx + gxo;
+#pragma unroll
+      for (int i = 0; i < B::KO; ++i) {
+        if (gy0 + i * DY >= ny) continue;
+        const float* q = rp + (size_t)(i * DY) * nx;
+        rxr[i] = __ldg(q);
+        ryr[i] = __ldg(q + (size_t)N);
+        rzr[i] = __ldg(q + 2 * (size_t)N);
+      }
+    }
+    // ---- the step's copies have landed --------------------------------------
+    if (!wait_a(bytes_a(zi) != 0)) return false;
+
+    // ---- stage 1: z sliding sums of the W columns -----------------------------
+    const bool has_new = zi < nz, has_old = zi - (2 * H + 1) >= zi0;
+#pragma unroll
+    for (int k = 0; k < B::K1; ++k) {
+      if (cmap[k] < 0) continue;
+      const int bi = cmap[k] >> 16, si = cmap[k] & 0xffff;
+      const float vn = has_new ? wn[bi] : 0.0f;
+      const float vo = has_old ? wo[bi] : 0.0f;
+      const int qn = __float2int_rn(vn * qs), qo = __float2int_rn(vo * qs);
+      s1r[k] += qn - qo;
+      s2r[k] += (long long)(qn - qo) * (long long)(qn + qo);   // q_n^2 - q_o^2
+      s1z[si] = s1r[k];
+      s2z[si] = s2r[k];
+    }
+    __syncthreads();
+    if (tid == 0 && zi < zi1) issue_a(zi + 1);   // the W boxes are consumed
+    if (!do2 && !do3) continue;                 // uniform
+
+    if (do2) {
+      // ---- stage 2a: x window sums, sliding, one task per (segment, W row) -----
+      if (tid < B::NSX * B::WY) {
+        const int sg = tid / B::WY, wy = tid - sg * B::WY;
+        const int fx0 = sg * B::SX;
+        const int* r1 = s1z + wy * B::WXP + fx0;
+        const long long* r2 = s2z + wy * B::WXP + fx0;
+        long long b1 = tree_sum<2 * H + 1, int>(r1, 1), b2 = tree_sum<2 * H + 1, long long>(r2, 1);
+        long long* o1 = xb1 + wy * B::XBS + fx0;
+        long long* o2 = xb2 + wy * B::XBS + fx0;
+        o1[0] = b1;
+        o2[0] = b2;
+#pragma unroll
+        for (int j = 1; j < B::SX; ++j) {
+          if (fx0 + j < B::FX) {
+            b1 += r1[j + 2 * H] - r1[j - 1];
+            b2 += r2[j + 2 * H] - r2[j - 1];
+            o1[j] = b1;
+            o2[j] = b2;
+          }
+        }
+      }
+      __syncthreads();
+
+      // ---- stage 2b: y window sums, sliding; moments and correction ------------
+      if (ycol) {
+        const bool zin = zc >= H && zc < nz - H;
+        const int nzc = box_count(zc, nz, H);
+        const bool out_plane = zc >= z0 && zc < z1;
+        const float* mr = mring + ((unsigned)zc % B::NMS) * B::MS;
+        float* dcur = dring + zc3 * B::FN;
+        long long b1 = tree_sum<2 * H + 1, long long>(xb1 + fy0 * B::XBS + fx_y, B::XBS);
+        long long b2 = tree_sum<2 * H + 1, long long>(xb2 + fy0 * B::XBS + fx_y, B::XBS);
+#pragma unroll
+        for (int j = 0; j < B::SY; ++j) {
+          const int fy = fy0 + j;
+          if (fy >= B::FY) break;
+          if (j > 0) {
+            b1 += xb1[(fy + 2 * H) * B::XBS + fx_y] - xb1[(fy - 1) * B::XBS + fx_y];
+            b2 += xb2[(fy + 2 * H) * B::XBS + fx_y] - xb2[(fy - 1) * B::XBS + fx_y];
+          }
+          const int gy = y0 - 1 + fy;
+          if (gy < 0 || gy >= ny) continue;
+          int n;
+          float inv_n;
+          if (xin_y && zin && gy >= H && gy < ny - H) {
+            n = B::NP;
+            inv_n = 1.0f / (float)B::NP;
+          } else {
+            n = nxc_y * box_count(gy, ny, H) * nzc;
+            inv_n = 1.0f / (float)n;
+          }
+          const int fi = fy * B::FXT + fx_y + B::FO;
+          const float vc = mr[fi];
+          float dc, sg_;
+          patch_moments(b1, b2, n, inv_n, __float2int_rn(vc * qs), inv_qs, vfl, dc, sg_);
+          const float d = fmaf(zsr[j], sg_, dc);   // I'_s - I_m^(k)
+          dcur[fi] = d;
+          if (a.f_tap && out_plane && fx_y >= 1 && fx_y <= TX && fy >= 1 && fy <= TY)
+            a.f_tap[(size_t)zc * plane + (size_t)gy * nx + gx_y] = d;
+        }
+      }
+    }
+    if (do3) {
+      __syncthreads();
+      // ---- stage 3: demons force (Eq. 1) and update of plane zf = zc - 1 ---------
+      const bool zlo = zf > 0, zhi = zf < nz - 1;
+      const float sz = diff_scale(zf, nz);
+      const int s_m1 = zc3 == 2 ? 0 : zc3 + 1;      // slot of zc - 2
+      const int s_0 = zc3 == 0 ? 2 : zc3 - 1;       // slot of zc - 1 = zf
+      const float* dp = dring + s_0 * B::FN;
+      const float* dzm = dring + (zlo ? s_m1 : s_0) * B::FN;
+      const float* dzp = dring + (zhi ? zc3 : s_0) * B::FN;
+      const float* mp = mring + ((unsigned)zf % B::NMS) * B::MS;
+      const float* mzm = mring + ((unsigned)(zlo ? zf - 1 : zf) % B::NMS) * B::MS;
+      const float* mzp = mring + ((unsigned)(zhi ? zf + 1 : zf) % B::NMS) * B::MS;
+      float* out0 = a.out + (size_t)zf * plane + (size_t)gy0 * nx + gxo;
+      const bool nin = a.norm_hi <= a.norm_lo || (zf >= a.norm_lo && zf < a.norm_hi);
+#pragma unroll
+      for (int i = 0; i < B::KO; ++i) {
+        const int gy = gy0 + i * DY;
+        if (gxo >= nx || gy >= ny) continue;
+        const int fi = fi0 + i * DY * B::FXT;
+        const int lyo = gy > 0 ? -B::FXT : 0, ryo = gy < ny - 1 ? B::FXT : 0;
+        const Dr dr = demons_dr(dp[fi], sxo, dp[fi + rxo] - dp[fi + lxo], mp[fi + rxo] - mp[fi + lxo],
+                                diff_scale(gy, ny), dp[fi + ryo] - dp[fi + lyo], mp[fi + ryo] - mp[fi + lyo], sz,
+                                dzp[fi] - dzm[fi], mzp[fi] - mzm[fi], dbl);
+        float* po = out0 + (size_t)(i * DY) * nx;
+        po[0] = fmaf(keep, rxr[i], dr.x);
+        po[(size_t)N] = fmaf(keep, ryr[i], dr.y);
+        po[2 * (size_t)N] = fmaf(keep, rzr[i], dr.z);
+        acc0 += nin ? norm3(dr.x, dr.y, dr.z) : 0.0f;
+        acc1 += nin ? norm3(rxr[i], ryr[i], rzr[i]) : 0.0f;
+      }
+    }
+    // the next step's stage 1 rewrites the z sums and the next stage 2b a d plane
+    // that stage 3 may still read: the next step's barriers separate them
+  }
+  return true;
+}
+
+// Per-CTA end: the CTA's partial sums of sum |dr| and sum |r| (fixed order).
+__device__ __forceinline__ void write_partials(float acc0, float acc1, float* red, float* partials, size_t part) {
+  for (int off = 16; off > 0; off >>= 1) {
+    acc0 += __shfl_down_sync(0xffffffffu, acc0, off);
+    acc1 += __shfl_down_sync(0xffffffffu, acc1, off);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[wid] = acc0;
+    red[kWideThreads / 32 + wid] = acc1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && partials != nullptr) {
+    float t0 = 0.0f, t1 = 0.0f;
+    for (int w = 0; w < kWideThreads / 32; ++w) {
+      t0 += red[w];
+      t1 += red[kWideThreads / 32 + w];
+    }
+    partials[2 * part] = t0;
+    partials[2 * part + 1] = t1;
+  }
+}
+
+template <int H, int TX, int TY>
+__device__ __forceinline__ bool wide_setup(unsigned char* smem, int* err) {
+  using B = WideLayout<H, TX, TY>;
+  if ((smem_addr(smem) & 127u) != 0u) {
+    if (threadIdx.x == 0) atomicOr(err ? err : &g_wide_err, 2);
+    return false;
+  }
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + B::o_bar);
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_proxy_async();
+  }
+  __syncthreads();
+  return true;
+}
+
+// One volume: CTA c marches the planes [c P / G, (c + 1) P / G) of the
+// sequence of all P = tiles x nz (tile, plane) pairs, tile after tile (at most
+// a few tiles per CTA), G = gridDim.x.
+template <int H, int TX, int TY>
+__global__ void __launch_bounds__(kWideThreads, 2)
+    k_box_wide(const BoxArgs a, const __grid_constant__ CUtensorMap map_w, const __grid_constant__ CUtensorMap map_f,
+               int tiles_x, int tiles_y) {
+  using B = WideLayout<H, TX, TY>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  pdl_wait();
+  pdl_release();
+  if (a.stop != nullptr && *(volatile const int*)a.stop != 0) return;
+  if (!wide_setup<H, TX, TY>(smem, a.err)) return;
+  uint32_t pa = 0;
+  float acc0 = 0.0f, acc1 = 0.0f;
+  const long long P = (long long)tiles_x * tiles_y * a.nz;
+  const long long lo = P * blockIdx.x / gridDim.x, hi = P * (blockIdx.x + 1) / gridDim.x;
+  for (long long gp = lo; gp < hi;) {
+    const int t = (int)(gp / a.nz), z0 = (int)(gp - (long long)t * a.nz);
+    const int z1 = (int)min((long long)a.nz, (long long)z0 + (hi - gp));
+    __syncthreads();                          // the previous march's reads of the buffers are done
+    if (!wide_march<H, TX, TY>(a, t % tiles_x, t / tiles_x, z0, z1, &map_w, &map_f, smem, pa, acc0, acc1))
+      return;
+    gp += z1 - z0;
+  }
+  write_partials(acc0, acc1, reinterpret_cast<float*>(smem + B::o_red), a.partials, blockIdx.x);
+}
+
+// ---- host side ---------------------------------------------------------------
+constexpr int kMaxDevices = 64;
+
+template <int H>
+struct WideHost {
+  static constexpr int TX = 32, TY = 32;
+  using B = WideLayout<H, TX, TY>;
+  static size_t smem() { return B::bytes; }
+  static int extent(int axis) { return axis == 0 ? B::WXT : B::WY; }
+  static int occupancy() {
+    auto k = k_box_wide<H, TX, TY>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B::bytes) != cudaSuccess ||
+        cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kWideThreads, B::bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    return n;
+  }
+  static cudaError_t launch(const BoxArgs& a, const BoxPlan& p, cudaStream_t s) {
+    static int set[kMaxDevices] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    auto k = k_box_wide<H, TX, TY>;
+    if (!set[dev]) {
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B::bytes);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+      if (e != cudaSuccess) return e;
+      set[dev] = 1;
+    }
+    CUtensorMap mw{}, mf{};
+    if (!tma_encode_volume(&mw, a.src, 3, a.nx, a.ny, a.nz, B::WXT, B::WY, 1) ||
+        !tma_encode_volume(&mf, a.src, 3, a.nx, a.ny, a.nz, B::FXT, B::FY, 1))
+      return cudaErrorInvalidValue;
+    BoxArgs b = a;
+    // DISC_SW_TMA_STALL: the first copy group waits for 16 bytes no copy delivers
+    b.stall_tx = (test_switches() & DISC_SW_TMA_STALL) ? 16u : 0u;
+    const int tx = (a.nx + TX - 1) / TX, ty = (a.ny + TY - 1) / TY;
+    return launch_pdl(k, p.grid, dim3(kWideThreads), B::bytes, s, b, mw, mf, tx, ty);
+  }
+};
+
+template <typename R, typename F>
+R wide_dispatch(int h, R fallback, F f) {
+  switch (h) {
+    case 1: return f(WideHost<1>{});
+    case 2: return f(WideHost<2>{});
+    case 3: return f(WideHost<3>{});
+    case 4: return f(WideHost<4>{});
+    case 5: return f(WideHost<5>{});
+    case 6: return f(WideHost<6>{});
+    case 7: return f(WideHost<7>{});
+    default: return fallback;
+  }
+}
+
+}  // namespace
+
+bool box_wide_ok(int nx, int ny, int nz, int hx, int hy, int hz) {
+  if (hx != hy || hy != hz || hx < 1 || hx > 7) return false;
+  if ((test_switches() & DISC_SW_NO_TMA) != 0u || nx % 4 != 0 || nz < 1) return false;
+  const int ex = wide_dispatch<int>(hx, 0, [](auto w) { return decltype(w)::extent(0); });
+  const int ey = wide_dispatch<int>(hx, 0, [](auto w) { return decltype(w)::extent(1); });
+  if (ex == 0 || nx < ex || ny < ey) return false;
+  return tma_encode_available();
+}
+
+size_t box_wide_smem(int h) {
+  return wide_dispatch<size_t>(h, (size_t)0, [](auto w) { return decltype(w)::smem(); });
+}
+
+int box_wide_occupancy(int h) {
+  return wide_dispatch<int>(h, 0, [](auto w) { return decltype(w)::occupancy(); });
+}
+
+void box_wide_tile(int* tx, int* ty) {
+  *tx = WideHost<1>::TX;
+  *ty = WideHost<1>::TY;
+}
+
+cudaError_t box_wide_launch(const BoxArgs& a, const BoxPlan& p, cudaStream_t s) {
+  if (((uintptr_t)a.src & 15u) != 0u) return cudaErrorInvalidValue;
+  return wide_dispatch<cudaError_t>(a.hx, cudaErrorInvalidValue, [&](auto w) { return decltype(w)::launch(a, p, s); });
+}
+
+cudaError_t box_wide_error(cudaStream_t s, int* flag) {
+  int* dev = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&dev), g_wide_err);
+  if (e != cudaSuccess) return e;
+  int v = 0;
+  e = cudaMemcpyAsync(&v, dev, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && v != 0) e = cudaMemsetAsync(dev, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  *flag |= v;
+  return e;
+}
+
+}  // namespace disc

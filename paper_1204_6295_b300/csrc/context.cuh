@@ -43,7 +43,8 @@ struct Level {
   unsigned* kbits = nullptr;   // [2][fill_words] known-voxel bit masks of the fill passes
   int* flist = nullptr;        // [N] a fill pass's front; then [fill_front_blocks + 1] block offsets, length
   int* cnt = nullptr;    // [fill_passes + 2] masked voxels, voxels filled per pass; then the pass counter
-  BoxPlan pa{};
+  BoxPlan pa{};          // iteration pass of this context (possibly the wide-tile one)
+  BoxPlan pn{};          // iteration pass on the 32 x 16 tiling (the batched launches)
   BoxPlan pm{};          // kModeMaskAB
   GaussPlan pb{};
   cudaGraphExec_t graph = nullptr;   // n iterations unrolled (graph_iters = n)

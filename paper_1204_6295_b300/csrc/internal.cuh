@@ -87,6 +87,8 @@ struct BoxPlan {
   int tx, ty;
   bool fast;            // cubic-patch kernel specialised on the half size (box_fast.cu)
   bool tma;             // the same kernel fed by bulk tensor copies (box_tma.cu)
+  bool wide = false;    // iteration mode on wide tiles (box_wide.cu): grid.x CTAs share
+                        // the volume's (tile, plane) pairs evenly
 };
 
 // Work table of a batched launch over many volumes (pairs): volume p owns the
@@ -128,6 +130,19 @@ cudaError_t box_tma_launch_batch(const BoxBatch& bt, const void* maps, int h, in
 
 // Plan a launch (grid, z chunk, dynamic shared memory) for a volume and patch.
 BoxPlan box_plan(int mode, int nx, int ny, int nz, int hx, int hy, int hz, int num_sms);
+// Iteration-mode plan: the wide-tile pass (box_wide.cu) when the patch is cubic,
+// the bulk-copy conditions hold (src 16-byte aligned; NULL = library-owned
+// buffers, which are) and the volume gives each CTA of its wave at least
+// kWideMinPlanes planes; else box_plan's.
+constexpr int kWideMinPlanes = 16;
+BoxPlan box_plan_iter(int nx, int ny, int nz, int hx, int hy, int hz, int num_sms, const float* src);
+bool box_wide_ok(int nx, int ny, int nz, int hx, int hy, int hz);
+size_t box_wide_smem(int h);
+int box_wide_occupancy(int h);
+void box_wide_tile(int* tx, int* ty);
+cudaError_t box_wide_launch(const BoxArgs& a, const BoxPlan& p, cudaStream_t s);
+// Reads (synchronising s) and clears the wide pass's own error word, OR-ing it into *flag.
+cudaError_t box_wide_error(cudaStream_t s, int* flag);
 cudaError_t box_launch(int mode, const BoxArgs& a, const BoxPlan& plan, cudaStream_t s);
 
 // Trilinear warp m = I_m(x + r(x)), warp.cu

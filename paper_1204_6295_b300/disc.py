@@ -82,6 +82,7 @@ _SIGS = {
     "disc_get_norm_history": (_st, [_vp, _i32, _vp, _i32, ctypes.POINTER(_i32)]),
     "disc_get_norm_sums": (_st, [_vp, _i32, _vp, _i32, ctypes.POINTER(_i32)]),
     "disc_get_launch_count": (_st, [_vp, ctypes.POINTER(_i64)]),
+    "disc_ssd": (_st, [_vp, _i32, _vp, ctypes.POINTER(ctypes.c_double), _vp, ctypes.c_int]),
     "disc_destroy": (_st, [_vp]),
     "disc_qscale": (_f32, [_f32, ctypes.POINTER(_i32)]),
     "disc_batch_create": (_st, [ctypes.POINTER(Params), ctypes.c_int, _vp, _i32, ctypes.POINTER(_vp)]),
@@ -143,7 +144,7 @@ def _check(status, where):
         raise DiscError(status, where)
 
 
-SW_NO_TMA, SW_TMA_STALL, SW_NO_GRAPH, SW_UNROLLED_GRAPH, SW_FAULT_ALLOC = 1, 2, 4, 8, 16
+SW_NO_TMA, SW_TMA_STALL, SW_NO_GRAPH, SW_UNROLLED_GRAPH, SW_FAULT_ALLOC, SW_WIDE_ANY = 1, 2, 4, 8, 16, 32
 
 
 class test_switches:
@@ -348,6 +349,17 @@ class Registration:
         _check(_lib.disc_get_metrics(self._h, int(bins), float(sigma), float(t_low), float(t_high),
                                      ctypes.byref(nmi), ctypes.byref(rmse)), "disc_get_metrics")
         return nmi.value, rmse.value
+
+    def ssd(self, level, r, grad=None):
+        """SSD loss of field r on pyramid level `level` (disc_ssd); with `grad` (same
+        kind and shape as r) also dL/dr.  Returns the loss."""
+        loss = ctypes.c_double(0.0)
+        kind = _mem_kind(r)
+        if grad is not None and _mem_kind(grad) != kind:
+            raise ValueError("r and grad must both be host or both be device buffers")
+        _check(_lib.disc_ssd(self._h, int(level), _ptr(r), ctypes.byref(loss),
+                             _ptr(grad) if grad is not None else None, kind), "disc_ssd")
+        return loss.value
 
     def launch_count(self):
         """Kernel launches disc_iterate has issued on this context (disc_get_launch_count)."""

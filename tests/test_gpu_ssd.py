@@ -137,3 +137,46 @@ def test_ssd_full_size_gradient_at_sampled_voxels(disc):
         got = grad[:, z, y, x]
         scale = max(np.abs(ref).max(), 1e-6 * np.abs(grad).max())
         assert np.abs(got - ref).max() <= GRAD_TOL * scale, ((z, y, x), got, ref)
+
+
+@pytest.mark.parametrize("level", [0, 1])
+def test_context_ssd_equals_kernel_level_calls(disc, level):
+    """disc_ssd on a registration context's own pyramid level (its CT, its CBCT
+    normalisation zs and fixed-point scale) equals the kernel-level calls on the
+    same level's images bit for bit, for device and host buffers."""
+    import torch
+    shape, patch = (20, 36, 48), (5, 5, 5)
+    ct = ct_like(shape, 51)
+    cbct = (ct_like(shape, 52, noise=20.0) * 0.8 + 30.0).astype(np.float32)
+    kw = dict(patch=patch, sigma=1.0, levels=2, iters=(2, 2), global_shift=0)
+    with disc.Registration(**kw) as reg:
+        reg.set_images(dev(ct), dev(cbct))
+        ct_l, cb_l = dev(ct), dev(cbct)
+        if level == 1:
+            nz, ny, nx = [(s + 1) // 2 for s in shape]
+            a, b = empty(nz, ny, nx), empty(nz, ny, nx)
+            disc.k_downsample2(ct_l, a)
+            disc.k_downsample2(cb_l, b)
+            ct_l, cb_l = a, b
+        lshape = tuple(ct_l.shape)
+        r = phantom.smooth_random_field(lshape, 53 + level, amp=1.5).astype(np.float32)
+        g_dev = empty(3, *lshape)
+        loss_dev = reg.ssd(level, dev(r), g_dev)
+        g_host = np.empty((3,) + lshape, np.float32)
+        loss_host = reg.ssd(level, r, g_host)
+        loss_only = reg.ssd(level, dev(r))
+        # the registration state is untouched: it still runs its schedule
+        assert reg.iterate(-1)[0] == 4
+    qs_m = disc.qscale(float(np.abs(ct).max()), patch)      # the finest level's scales serve every level
+    qs_s = disc.qscale(float(np.abs(cbct).max()), patch)
+    zs = empty(*lshape)
+    disc.k_static_norm(cb_l, zs, patch, qs_s)
+    g_ref = empty(3, *lshape)
+    l_ref = torch.zeros(1, dtype=torch.float64, device="cuda")
+    l_ref2 = torch.zeros(1, dtype=torch.float64, device="cuda")
+    disc.k_ssd_grad(ct_l, zs, dev(r), g_ref, patch, qs_m, loss_out=l_ref)
+    disc.k_ssd_loss(ct_l, zs, dev(r), l_ref2, patch, qs_m)
+    np.testing.assert_array_equal(host(g_dev), host(g_ref))
+    np.testing.assert_array_equal(g_host, host(g_ref).astype(np.float32))
+    assert loss_dev == float(l_ref.item()) and loss_host == loss_dev
+    assert loss_only == float(l_ref2.item())

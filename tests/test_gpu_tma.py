@@ -35,6 +35,12 @@ def _NoTma():
     return disc.test_switches(disc.SW_NO_TMA)
 
 
+def _Wide():
+    """The wide-tile iteration pass (32 x 32 tiles, balanced z shares) at any size."""
+    from paper_1204_6295_b300 import disc
+    return disc.test_switches(disc.SW_WIDE_ANY)
+
+
 CASES = [
     ((20, 40, 64), 3),      # (nz, ny, nx), patch
     ((33, 47, 100), 11),    # ragged in all three axes
@@ -68,21 +74,23 @@ def test_force_update_bitwise(disc, shape, patch, force_mode):
     disc.k_static_norm(Is, zs, P, qs_s)
     disc.k_warp(Im, rd, m)
     outs = []
-    for plain in (False, True):
+    for form in ("tma", "plain", "wide"):
         u = empty(3, *shape)
         d = empty(*shape)
         norms = empty(2).double()
-        if plain:
-            with _NoTma():
+        ctx = {"plain": _NoTma, "wide": _Wide}.get(form)
+        if ctx:
+            with ctx():
                 disc.k_force_update(m, zs, rd, u, P, qs_m, d_out=d, norms_out=norms, force_mode=force_mode)
         else:
             disc.k_force_update(m, zs, rd, u, P, qs_m, d_out=d, norms_out=norms, force_mode=force_mode)
         outs.append((host(u), host(d), host(norms)))
     disc.k_check_error()
-    np.testing.assert_array_equal(outs[0][0], outs[1][0])
-    np.testing.assert_array_equal(outs[0][1], outs[1][1])
-    # the norm partials are per CTA, and the two forms may chunk z differently
-    np.testing.assert_allclose(outs[0][2], outs[1][2], rtol=1e-6)
+    for o in outs[1:]:
+        np.testing.assert_array_equal(outs[0][0], o[0])
+        np.testing.assert_array_equal(outs[0][1], o[1])
+        # the norm partials are per CTA, and the forms split the volume differently
+        np.testing.assert_allclose(outs[0][2], o[2], rtol=1e-6)
 
 
 @pytest.mark.parametrize("shape,patch", CASES[:3] + CASES[-1:])
@@ -122,11 +130,12 @@ def test_ssd_bitwise(disc, shape, patch):
 
 
 def test_registration_bitwise(disc):
-    """A whole two-level schedule through the context, TMA form vs plain loads."""
+    """A whole two-level schedule through the context: the TMA form, plain loads,
+    and the wide-tile pass at the finest level."""
     shape = (32, 64, 64)
     ct, cbct, _ = _inputs(shape, 9, 11)
     fields = []
-    for plain in (False, True):
+    for form in ("tma", "plain", "wide"):
         def run():
             reg = disc.Registration(patch=(9, 9, 9), sigma=1.0, levels=2, iters=(6, 5))
             reg.set_images(dev(ct), dev(cbct))
@@ -134,12 +143,42 @@ def test_registration_bitwise(disc):
             out = empty(3, *shape)
             reg.get_field(out)
             return host(out)
-        if plain:
-            with _NoTma():
+        ctx = {"plain": _NoTma, "wide": _Wide}.get(form)
+        if ctx:
+            with ctx():
                 fields.append(run())
         else:
             fields.append(run())
     np.testing.assert_array_equal(fields[0], fields[1])
+    np.testing.assert_array_equal(fields[0], fields[2])
+
+
+# Shapes on which the planner itself picks the wide-tile pass (enough (tile,
+# plane) pairs for its wave): ragged in y and z, patch 11 and 15, Thirion and
+# double force, against the plain-load 32 x 16 pass.
+@pytest.mark.parametrize("shape,patch,force_mode", [((150, 250, 256), 11, 0), ((131, 200, 192), 15, 1)])
+def test_planner_wide_pass_bitwise(disc, shape, patch, force_mode):
+    P = (patch,) * 3
+    ct, cbct, r = _inputs(shape, patch, 60 + patch)
+    qs_m = disc.qscale(float(np.abs(ct).max()), P)
+    qs_s = disc.qscale(float(np.abs(cbct).max()), P)
+    Im, Is, rd = dev(ct), dev(cbct), dev(r)
+    zs, m = empty(*shape), empty(*shape)
+    disc.k_static_norm(Is, zs, P, qs_s)
+    disc.k_warp(Im, rd, m)
+    outs = []
+    for plain in (False, True):
+        u, d, norms = empty(3, *shape), empty(*shape), empty(2).double()
+        if plain:
+            with _NoTma():
+                disc.k_force_update(m, zs, rd, u, P, qs_m, d_out=d, norms_out=norms, force_mode=force_mode)
+        else:
+            disc.k_force_update(m, zs, rd, u, P, qs_m, d_out=d, norms_out=norms, force_mode=force_mode)
+        outs.append((host(u), host(d), host(norms)))
+    disc.k_check_error()
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])
+    np.testing.assert_allclose(outs[0][2], outs[1][2], rtol=1e-6)
 
 
 def test_bounded_wait_reports_timeout_and_device_stays_usable(disc):

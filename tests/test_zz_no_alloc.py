@@ -3,9 +3,10 @@
 It serves callers that cannot let the library allocate device memory (an
 application that owns all device memory through its own pool or a fixed
 budget, or a host that forbids plug-ins from allocating).  Its only scratch is
-a fixed array inside the library that every call reuses.  It runs the same
-kernels with the same launch plan as the allocating entry point
-disc_k_pass_a, so this test calls both through the C ABI, twice in a row on
+a fixed array inside the library that every call reuses.  On the volumes of
+this test it runs the same kernels with the same launch plan as the
+allocating entry point disc_k_pass_a, so this test calls both through the C
+ABI, twice in a row on
 inputs of different sizes (the larger grid first, so that the second call
 would read partial sums the first one left behind if it read any it did not
 write), and requires bitwise equal m, d, u and norms.  Each result is also
@@ -72,14 +73,24 @@ def test_static_scratch_pass_a_equals_allocating_entry_point_bitwise_twice():
 
 
 def test_static_scratch_pass_a_rejects_grids_beyond_its_scratch():
+    """Launches larger than the fixed scratch are refused before any work is
+    queued.  The buffers are real device memory of the right sizes, so that a
+    call that did run would only compute on them."""
     import torch
     from paper_1204_6295_b300 import disc
     p = (ctypes.c_int32 * 3)(3, 3, 3)
-    fake = ctypes.c_void_p(256)
-    other = ctypes.c_void_p(512)
-    # a 4096 x 4096 plane needs 128 x 256 tiles: more CTAs than the fixed scratch holds
-    status = disc._lib.disc_k_pass_a_static(fake, fake, fake, other, fake, None, None, 4096, 4096, 1, p,
-                                            1.0, 1e-6, 0, torch.cuda.current_stream().cuda_stream)
+    # a 4096 x 4096 plane needs 128 x 256 tiles of 32 x 16: more CTAs than the fixed scratch holds
+    shape = (1, 4096, 4096)
+    Im, zs, m = empty(*shape), empty(*shape), empty(*shape)
+    r, u = empty(3, *shape), empty(3, *shape)
+    for t in (Im, zs, m, r):
+        t.zero_()
+    status = disc._lib.disc_k_pass_a_static(Im.data_ptr(), zs.data_ptr(), r.data_ptr(), u.data_ptr(),
+                                            m.data_ptr(), None, None, 4096, 4096, 1, p, 1.0, 1e-6, 0,
+                                            torch.cuda.current_stream().cuda_stream)
     assert status == 2
-    assert disc._lib.disc_k_pass_a_static(fake, fake, fake, other, None, None, None, 8, 8, 8, p, 1.0, 1e-6,
-                                          0, None) == 1     # m_out is required
+    small = (8, 8, 8)
+    Im, zs, r, u = empty(*small), empty(*small), empty(3, *small), empty(3, *small)
+    assert disc._lib.disc_k_pass_a_static(Im.data_ptr(), zs.data_ptr(), r.data_ptr(), u.data_ptr(), None, None,
+                                          None, 8, 8, 8, p, 1.0, 1e-6, 0, None) == 1     # m_out is required
+    torch.cuda.synchronize()
