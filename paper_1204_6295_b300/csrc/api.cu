@@ -697,7 +697,7 @@ disc_status disc_set_images(disc_ctx* ctx, const float* ct, const float* cbct, i
       v.ny = dims[l][1];
       v.nz = dims[l][2];
       v.N = (size_t)v.nx * v.ny * v.nz;
-      v.pa = box_plan_iter(v.nx, v.ny, v.nz, ctx->hx, ctx->hy, ctx->hz, ctx->num_sms, nullptr);
+      v.pa = box_plan_iter(v.nx, v.ny, v.nz, ctx->hx, ctx->hy, ctx->hz, ctx->num_sms, nullptr, nullptr, nullptr);
       v.pn = box_plan(kModeIterate, v.nx, v.ny, v.nz, ctx->hx, ctx->hy, ctx->hz, ctx->num_sms);
       v.pb = gauss_plan(v.nx, v.ny, v.nz, ctx->R, ctx->num_sms);
       BoxPlan ps = box_plan(kModeStatic, v.nx, v.ny, v.nz, ctx->hx, ctx->hy, ctx->hz, ctx->num_sms);
@@ -1469,7 +1469,7 @@ disc_status disc_k_pass_a(const float* Im, const float* zs, const float* r, floa
   int dev = 0, sms = kNumSMs;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  BoxPlan p = box_plan_iter(nx, ny, nz, h[0], h[1], h[2], sms, m_out);   // m_out NULL: pool memory, aligned
+  BoxPlan p = box_plan_iter(nx, ny, nz, h[0], h[1], h[2], sms, m_out, r, u);   // m_out NULL: pool memory, aligned
   if (p.grid.x == 0) return DISC_ERR_SHAPE;
   cudaStream_t s = (cudaStream_t)stream;
   disc_ctx* ctx = nullptr;
@@ -1526,7 +1526,7 @@ disc_status disc_k_force_update(const float* m, const float* zs, const float* r,
   int dev = 0, sms = kNumSMs;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  BoxPlan p = box_plan_iter(nx, ny, nz, h[0], h[1], h[2], sms, m);
+  BoxPlan p = box_plan_iter(nx, ny, nz, h[0], h[1], h[2], sms, m, r, u);
   if (p.grid.x == 0) return DISC_ERR_SHAPE;
   cudaStream_t s = (cudaStream_t)stream;
   disc_ctx* ctx = nullptr;

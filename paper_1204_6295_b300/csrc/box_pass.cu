@@ -388,10 +388,12 @@ BoxPlan box_plan(int mode, int nx, int ny, int nz, int hx, int hy, int hz, int n
   return p;
 }
 
-BoxPlan box_plan_iter(int nx, int ny, int nz, int hx, int hy, int hz, int num_sms, const float* src) {
+BoxPlan box_plan_iter(int nx, int ny, int nz, int hx, int hy, int hz, int num_sms, const float* src,
+                      const float* r, const float* u) {
   // the wide-tile pass where its one wave gets enough planes per CTA to
   // amortise the z warm-up of a march; the 32 x 16 tiling otherwise
-  if (((uintptr_t)src & 15u) == 0u && box_wide_ok(nx, ny, nz, hx, hy, hz)) {
+  const bool aligned = (((uintptr_t)src | (uintptr_t)r | (uintptr_t)u) & 15u) == 0u;
+  if (aligned && box_wide_ok(nx, ny, nz, hx, hy, hz)) {
     int tx = 0, ty = 0;
     box_wide_tile(&tx, &ty);
     const int occ = box_wide_occupancy(hx);

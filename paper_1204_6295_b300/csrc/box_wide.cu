@@ -58,8 +58,9 @@ struct WideLayout {
   static constexpr int FN = FXT * FY;                          // floats of an F plane
   static constexpr int NMS = 4;                                // F planes of m in flight
   static constexpr int TN = TX * TY;
-  static constexpr int KO = TN / NT;                           // tile voxels per thread
-  static_assert(TN % NT == 0 && NT % TX == 0, "tile and CTA shape");
+  static constexpr int QX = TX / 4;                            // force stage: x quads per tile row
+  static_assert(TX % 4 == 0 && NT == QX * TY, "force stage: one x quad of the tile per thread");
+  static_assert(FXT % 4 == 0 && (1 + FO) % 4 == 0, "force stage: 16-byte aligned quads in the F planes");
   static constexpr int NSX0 = (NT / WY) < 1 ? 1 : (NT / WY);   // x tasks: segments per W row
   static constexpr int SX = (FX + NSX0 - 1) / NSX0;
   static constexpr int NSX = (FX + SX - 1) / SX;
@@ -78,7 +79,7 @@ struct WideLayout {
   static constexpr size_t o_xb1 = o_s2z + 8 * (size_t)WY * WXP;   // x sums of q (int64)
   static constexpr size_t o_xb2 = o_xb1 + 8 * (size_t)WY * XBS;  // x sums of q^2 (int64)
   static constexpr size_t o_s1z = o_xb2 + 8 * (size_t)WY * XBS;  // z sums of q (int32)
-  static constexpr size_t o_dr = o_s1z + 4 * (size_t)WY * WXP;   // 3 F planes of d
+  static constexpr size_t o_dr = al128(o_s1z + 4 * (size_t)WY * WXP);   // 3 F planes of d
   static constexpr size_t o_red = o_dr + 12 * (size_t)FN;      // norm partials of the warps
   static constexpr size_t o_bar = (o_red + 8 * (NT / 32) + 7) & ~(size_t)7;   // the mbarrier
   static constexpr size_t bytes = o_bar + 8;
@@ -154,17 +155,16 @@ __device__ __forceinline__ bool wide_march(const BoxArgs& a, int bx, int by, int
   };
 
   // ---- per-thread maps, fixed for the march -----------------------------------
-  // W column k of this thread: W box index << 16 | z-sum index (-1: none); running z sums
-  int cmap[B::K1], s1r[B::K1];
-  long long s2r[B::K1];
+  // W column k of this thread: W box index << 16 | z-sum index (-1: none).  The
+  // running z sums live in the z-sum planes themselves (registers only during
+  // the warm-up), which keeps the march's register state small.
+  int cmap[B::K1];
   static_assert(B::WXT * B::WY < 65536 && B::WXP * B::WY < 65536, "packed column map");
 #pragma unroll
   for (int k = 0; k < B::K1; ++k) {
     const int e = tid + k * NT;
     const int wy = e / B::WX, wx = e - wy * B::WX;
     cmap[k] = e < B::WN ? ((wy * B::WXT + wx + B::WOFF) << 16) | (wy * B::WXP + wx) : -1;
-    s1r[k] = 0;
-    s2r[k] = 0;
   }
   // y task of this thread: F column fx, rows fy0 .. fy0 + SY - 1
   const int ty_task = tid < B::NSY * B::FX ? tid : -1;
@@ -174,19 +174,29 @@ __device__ __forceinline__ bool wide_march(const BoxArgs& a, int bx, int by, int
   const bool ycol = ty_task >= 0 && gx_y >= 0 && gx_y < nx;
   const bool xin_y = gx_y >= H && gx_y < nx - H;
   const int nxc_y = box_count(gx_y, nx, H);
-  // force stage: tile voxels (ox, oy0 + i NT / TX), i < KO
-  const int ox = tid % TX, oy0 = tid / TX;
-  const int gxo = x0 + ox;
-  const int lxo = gxo > 0 ? -1 : 0, rxo = gxo < nx - 1 ? 1 : 0;
-  const float sxo = diff_scale(gxo, nx);
-  const int fi0 = (oy0 + 1) * B::FXT + ox + 1 + B::FO;
-  const int gy0 = y0 + oy0;
-  constexpr int DY = NT / TX;                 // tile rows between a thread's voxels
+  // force stage: the x quad gxq .. gxq + 3 of tile row oyq (nx is a multiple of 4:
+  // a quad lies wholly inside or outside the volume, and holds no face of the
+  // volume but at its first or last voxel, as nx >= 8)
+  const int oxq = 4 * (tid % B::QX), oyq = tid / B::QX;
+  const int gxq = x0 + oxq, gyq = y0 + oyq;
+  const bool qin = gxq < nx && gyq < ny;
+  const int fq = (oyq + 1) * B::FXT + oxq + 1 + B::FO;   // F index of the quad's first voxel (16-byte aligned)
+  const bool xlo = gxq > 0, xhi = gxq + 3 < nx - 1;      // neighbours beyond the quad's ends exist
+  const float sx0 = xlo ? 0.5f : 1.0f, sx3 = xhi ? 0.5f : 1.0f;
+  const int yl = gyq > 0 ? -B::FXT : 0, yh = gyq < ny - 1 ? B::FXT : 0;
+  const float syq = diff_scale(gyq, ny);
 
   // ---- warm-up: planes zi0 .. zw - 1 only enter the z sums; they arrive as
   // bursts of W boxes over the buffers the march has not used yet, one copy wait
   // per burst, and are summed in the order the march would have summed them
   {
+    int s1r[B::K1];
+    long long s2r[B::K1];
+#pragma unroll
+    for (int k = 0; k < B::K1; ++k) {
+      s1r[k] = 0;
+      s2r[k] = 0;
+    }
     fence_proxy_async();                      // earlier generic writes of the staging area
     __syncthreads();
     const int zb_end = min(zw, nz);
@@ -210,6 +220,13 @@ __device__ __forceinline__ bool wide_march(const BoxArgs& a, int bx, int by, int
       }
       __syncthreads();                        // the staging area is consumed
     }
+    // the z-sum planes (inside the staging area) take over the running sums
+#pragma unroll
+    for (int k = 0; k < B::K1; ++k) {
+      if (cmap[k] < 0) continue;
+      s1z[cmap[k] & 0xffff] = s1r[k];
+      s2z[cmap[k] & 0xffff] = s2r[k];
+    }
   }
   if (tid == 0) issue_a(zw);
 
@@ -229,17 +246,11 @@ __device__ __forceinline__ bool wide_march(const BoxArgs& a, int bx, int by, int
         zsr[j] = (fy0 + j < B::FY && gy >= 0 && gy < ny) ? __ldg(zp + (size_t)gy * nx) : 0.0f;
       }
     }
-    float rxr[B::KO], ryr[B::KO], rzr[B::KO];
-    if (do3 && gxo < nx) {
-      const float* rp = a.r + (size_t)zf * plane + (size_t)gy0 * nx + gxo;
+    float4 rq[3];                              // r of the force quad, components x, y, z
+    if (do3 && qin) {
+      const float4* rp = reinterpret_cast<const float4*>(a.r + (size_t)zf * plane + (size_t)gyq * nx + gxq);
 #pragma unroll
-      for (int i = 0; i < B::KO; ++i) {
-        if (gy0 + i * DY >= ny) continue;
-        const float* q = rp + (size_t)(i * DY) * nx;
-        rxr[i] = __ldg(q);
-        ryr[i] = __ldg(q + (size_t)N);
-        rzr[i] = __ldg(q + 2 * (size_t)N);
-      }
+      for (int c = 0; c < 3; ++c) rq[c] = __ldg(rp + (size_t)c * (N / 4));
     }
     // ---- the step's copies have landed --------------------------------------
     if (!wait_a(bytes_a(zi) != 0)) return false;
@@ -253,10 +264,8 @@ __device__ __forceinline__ bool wide_march(const BoxArgs& a, int bx, int by, int
       const float vn = has_new ? wn[bi] : 0.0f;
       const float vo = has_old ? wo[bi] : 0.0f;
       const int qn = __float2int_rn(vn * qs), qo = __float2int_rn(vo * qs);
-      s1r[k] += qn - qo;
-      s2r[k] += (long long)(qn - qo) * (long long)(qn + qo);   // q_n^2 - q_o^2
-      s1z[si] = s1r[k];
-      s2z[si] = s2r[k];
+      s1z[si] += qn - qo;
+      s2z[si] += (long long)(qn - qo) * (long long)(qn + qo);   // q_n^2 - q_o^2
     }
     __syncthreads();
     if (tid == 0 && zi < zi1) issue_a(zi + 1);   // the W boxes are consumed
@@ -338,23 +347,48 @@ __device__ __forceinline__ bool wide_march(const BoxArgs& a, int bx, int by, int
       const float* mp = mring + ((unsigned)zf % B::NMS) * B::MS;
       const float* mzm = mring + ((unsigned)(zlo ? zf - 1 : zf) % B::NMS) * B::MS;
       const float* mzp = mring + ((unsigned)(zhi ? zf + 1 : zf) % B::NMS) * B::MS;
-      float* out0 = a.out + (size_t)zf * plane + (size_t)gy0 * nx + gxo;
       const bool nin = a.norm_hi <= a.norm_lo || (zf >= a.norm_lo && zf < a.norm_hi);
+      if (qin) {
+        // the quad's values and its neighbours': 16-byte loads of whole quads
+        const float4 dc = *reinterpret_cast<const float4*>(dp + fq);
+        const float4 mc = *reinterpret_cast<const float4*>(mp + fq);
+        const float dl = dp[fq + (xlo ? -1 : 0)], dr4 = dp[fq + (xhi ? 4 : 3)];
+        const float ml = mp[fq + (xlo ? -1 : 0)], mr4 = mp[fq + (xhi ? 4 : 3)];
+        const float4 dym = *reinterpret_cast<const float4*>(dp + fq + yl);
+        const float4 dyp = *reinterpret_cast<const float4*>(dp + fq + yh);
+        const float4 mym = *reinterpret_cast<const float4*>(mp + fq + yl);
+        const float4 myp = *reinterpret_cast<const float4*>(mp + fq + yh);
+        const float4 dz0 = *reinterpret_cast<const float4*>(dzm + fq);
+        const float4 dz1 = *reinterpret_cast<const float4*>(dzp + fq);
+        const float4 mz0 = *reinterpret_cast<const float4*>(mzm + fq);
+        const float4 mz1 = *reinterpret_cast<const float4*>(mzp + fq);
+        const float dcv[4] = {dc.x, dc.y, dc.z, dc.w}, mcv[4] = {mc.x, mc.y, mc.z, mc.w};
+        const float dymv[4] = {dym.x, dym.y, dym.z, dym.w}, dypv[4] = {dyp.x, dyp.y, dyp.z, dyp.w};
+        const float mymv[4] = {mym.x, mym.y, mym.z, mym.w}, mypv[4] = {myp.x, myp.y, myp.z, myp.w};
+        const float dz0v[4] = {dz0.x, dz0.y, dz0.z, dz0.w}, dz1v[4] = {dz1.x, dz1.y, dz1.z, dz1.w};
+        const float mz0v[4] = {mz0.x, mz0.y, mz0.z, mz0.w}, mz1v[4] = {mz1.x, mz1.y, mz1.z, mz1.w};
+        const float rxv[4] = {rq[0].x, rq[0].y, rq[0].z, rq[0].w};
+        const float ryv[4] = {rq[1].x, rq[1].y, rq[1].z, rq[1].w};
+        const float rzv[4] = {rq[2].x, rq[2].y, rq[2].z, rq[2].w};
+        float ux[4], uy[4], uz[4];
 #pragma unroll
-      for (int i = 0; i < B::KO; ++i) {
-        const int gy = gy0 + i * DY;
-        if (gxo >= nx || gy >= ny) continue;
-        const int fi = fi0 + i * DY * B::FXT;
-        const int lyo = gy > 0 ? -B::FXT : 0, ryo = gy < ny - 1 ? B::FXT : 0;
-        const Dr dr = demons_dr(dp[fi], sxo, dp[fi + rxo] - dp[fi + lxo], mp[fi + rxo] - mp[fi + lxo],
-                                diff_scale(gy, ny), dp[fi + ryo] - dp[fi + lyo], mp[fi + ryo] - mp[fi + lyo], sz,
-                                dzp[fi] - dzm[fi], mzp[fi] - mzm[fi], dbl);
-        float* po = out0 + (size_t)(i * DY) * nx;
-        po[0] = fmaf(keep, rxr[i], dr.x);
-        po[(size_t)N] = fmaf(keep, ryr[i], dr.y);
-        po[2 * (size_t)N] = fmaf(keep, rzr[i], dr.z);
-        acc0 += nin ? norm3(dr.x, dr.y, dr.z) : 0.0f;
-        acc1 += nin ? norm3(rxr[i], ryr[i], rzr[i]) : 0.0f;
+        for (int e = 0; e < 4; ++e) {
+          // x neighbours: inside the quad, or beyond its ends (the voxel itself at a face)
+          const float dxm = e == 0 ? dl : dcv[e - 1], dxp = e == 3 ? dr4 : dcv[e + 1];
+          const float mxm = e == 0 ? ml : mcv[e - 1], mxp = e == 3 ? mr4 : mcv[e + 1];
+          const float sx = e == 0 ? sx0 : (e == 3 ? sx3 : 0.5f);
+          const Dr dr = demons_dr(dcv[e], sx, dxp - dxm, mxp - mxm, syq, dypv[e] - dymv[e], mypv[e] - mymv[e],
+                                  sz, dz1v[e] - dz0v[e], mz1v[e] - mz0v[e], dbl);
+          ux[e] = fmaf(keep, rxv[e], dr.x);
+          uy[e] = fmaf(keep, ryv[e], dr.y);
+          uz[e] = fmaf(keep, rzv[e], dr.z);
+          acc0 += nin ? norm3(dr.x, dr.y, dr.z) : 0.0f;
+          acc1 += nin ? norm3(rxv[e], ryv[e], rzv[e]) : 0.0f;
+        }
+        float4* po = reinterpret_cast<float4*>(a.out + (size_t)zf * plane + (size_t)gyq * nx + gxq);
+        po[0] = make_float4(ux[0], ux[1], ux[2], ux[3]);
+        po[N / 4] = make_float4(uy[0], uy[1], uy[2], uy[3]);
+        po[2 * (size_t)(N / 4)] = make_float4(uz[0], uz[1], uz[2], uz[3]);
       }
     }
     // the next step's stage 1 rewrites the z sums and the next stage 2b a d plane
@@ -520,7 +554,7 @@ void box_wide_tile(int* tx, int* ty) {
 }
 
 cudaError_t box_wide_launch(const BoxArgs& a, const BoxPlan& p, cudaStream_t s) {
-  if (((uintptr_t)a.src & 15u) != 0u) return cudaErrorInvalidValue;
+  if ((((uintptr_t)a.src | (uintptr_t)a.r | (uintptr_t)a.out) & 15u) != 0u) return cudaErrorInvalidValue;
   return wide_dispatch<cudaError_t>(a.hx, cudaErrorInvalidValue, [&](auto w) { return decltype(w)::launch(a, p, s); });
 }
 

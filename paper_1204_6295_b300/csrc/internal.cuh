@@ -131,11 +131,13 @@ cudaError_t box_tma_launch_batch(const BoxBatch& bt, const void* maps, int h, in
 // Plan a launch (grid, z chunk, dynamic shared memory) for a volume and patch.
 BoxPlan box_plan(int mode, int nx, int ny, int nz, int hx, int hy, int hz, int num_sms);
 // Iteration-mode plan: the wide-tile pass (box_wide.cu) when the patch is cubic,
-// the bulk-copy conditions hold (src 16-byte aligned; NULL = library-owned
-// buffers, which are) and the volume gives each CTA of its wave at least
-// kWideMinPlanes planes; else box_plan's.
+// the bulk-copy conditions hold, the warped image src, the field r and the
+// output u are 16-byte aligned (NULL = library-owned buffers, which are) and
+// the volume gives each CTA of its wave at least kWideMinPlanes planes; else
+// box_plan's.
 constexpr int kWideMinPlanes = 16;
-BoxPlan box_plan_iter(int nx, int ny, int nz, int hx, int hy, int hz, int num_sms, const float* src);
+BoxPlan box_plan_iter(int nx, int ny, int nz, int hx, int hy, int hz, int num_sms, const float* src,
+                      const float* r, const float* u);
 bool box_wide_ok(int nx, int ny, int nz, int hx, int hy, int hz);
 size_t box_wide_smem(int h);
 int box_wide_occupancy(int h);
