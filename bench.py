@@ -770,11 +770,81 @@ def run_ours(args, w, rank, world, local_rank):
     return 0
 
 
+def run_slab_split(args, w, rank, world, local_rank):
+    """One volume split into z slabs, one slab per rank (slab.run_slab_rank):
+    per iteration each rank's context advances its slab, the interior norm sums
+    are added over the ranks (NCCL allreduce) and the halo planes of the field
+    are exchanged point to point into each rank's own buffer.  Strong scaling:
+    value = the whole volume's voxel-iterations / the slowest rank's time."""
+    import torch
+    from paper_1204_6295_b300 import disc, slab
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    pair = make_pair(w)                           # every rank draws the same seeded volume
+    nx, ny, nz = w["dims"]
+    L = w["levels"]
+    ct = torch.from_numpy(pair.ct).cuda()
+    cbct = torch.from_numpy(pair.cbct).cuda()
+    shifted = torch.empty_like(cbct)
+    disc.k_global_shift(ct, cbct, shifted)        # Sec. 2.3: over the whole volume
+    mx = torch.empty(2, dtype=torch.float32, device="cuda")
+    disc.k_max_abs(ct, mx[0:1])
+    disc.k_max_abs(shifted, mx[1:2])
+    qmax = [float(v) for v in mx.cpu()]
+    halo = slab.halo_planes(w["patch"], w["sigma"], 0, 8.0, L)
+    plan = slab.slab_plan(nz, world, halo, 1 << (L - 1))
+    z0, z1, b0, b1 = plan[rank]
+    eng = slab.LibdiscSlab(ct[b0:b1].contiguous(), shifted[b0:b1].contiguous(), qmax, (z0 - b0, z1 - b0),
+                           device=local_rank, patch=w["patch"], sigma=w["sigma"], levels=L, iters=w["iters"])
+    del ct, cbct, shifted
+    cz, cy, cx = eng.level_shape(L - 1)
+    zeros = torch.zeros((3, cz, cy, cx), dtype=torch.float32, device="cuda")
+
+    def step():
+        eng.set_level_field(L - 1, zeros)
+        slab.run_slab_rank(eng, plan, rank, nz, L, w["iters"], dist, sums_device="cuda")
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(args.steps):
+        step()
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = reduce_max(dist, e0.elapsed_time(e1) / args.steps)
+    eng.close()
+    if rank == 0:
+        units = schedule_units(w)
+        print(json.dumps({
+            "metric": METRIC, "value": units / (ms / 1e3) / 1e9, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "dims": list(w["dims"]), "patch": list(w["patch"]),
+                       "sigma": w["sigma"], "levels": L, "iters_coarse_to_fine": list(w["iters"]),
+                       "voxel_iterations_per_step": units, "parallelism": f"z-slabs x{world}",
+                       "halo_planes": halo, "split": "slab"},
+            "what": "one volume in z slabs, one per rank: per iteration a context step on each slab, an "
+                    "allreduce of the interior norm sums and a point-to-point halo exchange"}), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_profile_once(w):
     """One launch of each per-iteration kernel at the finest level (for ncu captures).
 
     Launch order: static patch normalisation, warp, box pass (iteration mode),
-    Gaussian xy pass, Gaussian z pass.
+    Gaussian xy pass, Gaussian z pass; then a one-level context's set-up and
+    two iterations (warp, then per iteration the box pass, the Gaussian xy
+    pass, the Gaussian z pass with the fused warp and the norm).
     """
     import torch
     from paper_1204_6295_b300 import disc
@@ -791,6 +861,11 @@ def run_profile_once(w):
     disc.k_static_norm(cbct, zs, patch, qs_s)
     disc.k_pass_a(ct, zs, r, u, patch, qs_m, m_out=m)
     disc.k_gauss(u, r2, w["sigma"])
+    # then two iterations of the finest level as the schedule runs them (box pass,
+    # Gaussian xy, Gaussian z with the fused warp, norm), in a one-level context
+    with disc.Registration(patch=patch, sigma=w["sigma"], levels=1, iters=(2,)) as reg:
+        reg.set_images(ct, cbct)
+        reg.iterate(-1, sync=False)
     torch.cuda.synchronize()
     print(json.dumps({"profile_once": True, "workload": [nx, ny, nz], "patch": list(patch)}))
     return 0
@@ -821,6 +896,9 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 16-pair batched form")
+    ap.add_argument("--split", default="replicas", choices=["replicas", "slab"],
+                    help="replicas: each rank runs the whole workload (weak scaling); slab: one volume "
+                         "split into z slabs over the ranks (strong scaling)")
     ap.add_argument("--profile-once", action="store_true",
                     help="launch each per-iteration kernel once at the finest level and exit")
     ap.add_argument("--profile-masked", type=int, default=0, metavar="K",
@@ -838,6 +916,8 @@ def main():
         return run_profile_masked(w, args.profile_masked)
     if args.impl == "reference":
         return run_reference(args, w, rank, world)
+    if args.split == "slab":
+        return run_slab_split(args, w, rank, world, local_rank)
     return run_ours(args, w, rank, world, local_rank)
 
 

@@ -217,6 +217,19 @@ disc_status disc_get_norm_history(disc_ctx* ctx, int32_t level, float* out,
  * of iterations written.  Host memory. */
 disc_status disc_get_norm_sums(disc_ctx* ctx, int32_t level, double* out, int32_t cap, int32_t* count);
 
+/* The convergence norm and stop rule of Sec. 2.3 for sums gathered outside a
+ * context, e.g. a z-slab split of one volume over several ranks, where each
+ * rank's interior sums (disc_get_norm_sums with norm_planes set) are added over
+ * the ranks.  sums[2k] = sum |dr|, sums[2k + 1] = sum |r| of iterations
+ * k = 0 .. count - 1 of one level (host memory).  l_out (host, may be NULL)
+ * receives l^(k) = sum |dr| / sum |r| for every k (float; +inf while sum |r| = 0);
+ * *stop is 1 when the rule ends the level after its last iteration:
+ * count - 1 >= window, both l^(count - 1 - window) and l^(count - 1) finite, and
+ * their difference <= eps (eps <= 0: never).  The same arithmetic as a
+ * context's own norm kernel.  No device work: callable without a GPU. */
+disc_status disc_norm_stop_rule(const double* sums, int32_t count, int32_t window, float eps,
+                                float* l_out, int32_t* stop);
+
 /* The mask thresholds fixed by disc_set_images (mask_mode 1): HU0 and a_m
  * (a_min = a_lo a_m, a_max = a_hi a_m).  DISC_ERR_STATE before images or
  * with the mask off.  Any pointer may be NULL. */

@@ -277,3 +277,21 @@ cudaError_t launch_partials_sum(const float* partials, int nparts, int comp, dou
 }
 
 }  // namespace disc
+
+// Sec. 2.3 stop rule over sums gathered outside a context (disc_norm_stop_rule):
+// the arithmetic of norm_finalize_body above, on the host.
+extern "C" disc_status disc_norm_stop_rule(const double* sums, int32_t count, int32_t window, float eps,
+                                           float* l_out, int32_t* stop) {
+  if (!sums || count < 1 || window < 1 || !stop) return DISC_ERR_ARG;
+  float lp = 0.0f, l = 0.0f;
+  for (int32_t k = 0; k < count; ++k) {
+    const double sdr = sums[2 * k], sr = sums[2 * k + 1];
+    const float v = sr > 0.0 ? (float)(sdr / sr) : INFINITY;
+    if (l_out) l_out[k] = v;
+    if (k == count - 1 - window) lp = v;
+    if (k == count - 1) l = v;
+  }
+  const int32_t k = count - 1;
+  *stop = (eps > 0.0f && k >= window && std::isfinite(lp) && std::isfinite(l) && lp - l <= eps) ? 1 : 0;
+  return DISC_OK;
+}

@@ -83,6 +83,7 @@ _SIGS = {
     "disc_get_norm_sums": (_st, [_vp, _i32, _vp, _i32, ctypes.POINTER(_i32)]),
     "disc_get_launch_count": (_st, [_vp, ctypes.POINTER(_i64)]),
     "disc_ssd": (_st, [_vp, _i32, _vp, ctypes.POINTER(ctypes.c_double), _vp, ctypes.c_int]),
+    "disc_norm_stop_rule": (_st, [_vp, _i32, _i32, _f32, _vp, ctypes.POINTER(_i32)]),
     "disc_destroy": (_st, [_vp]),
     "disc_qscale": (_f32, [_f32, ctypes.POINTER(_i32)]),
     "disc_batch_create": (_st, [ctypes.POINTER(Params), ctypes.c_int, _vp, _i32, ctypes.POINTER(_vp)]),
@@ -446,6 +447,17 @@ class Batch:
     def pin_tuning(self, level, zmult, grid):
         """Use z chunking `zmult` and grid `grid` (0: one CTA per item) at `level` instead of the autotuner."""
         _check(_lib.disc_batch_pin_tuning(self._h, int(level), int(zmult), int(grid)), "disc_batch_pin_tuning")
+
+
+def norm_stop_rule(sums, window, eps):
+    """Sec. 2.3 on summed norms (disc_norm_stop_rule): `sums` [k][2] float64 (sum |dr|,
+    sum |r| per iteration of a level).  Returns (l history float32, stop after the last)."""
+    s = np.ascontiguousarray(sums, np.float64).reshape(-1, 2)
+    l_out = np.empty(s.shape[0], np.float32)
+    stop = _i32(0)
+    _check(_lib.disc_norm_stop_rule(s.ctypes.data, s.shape[0], int(window), float(eps), l_out.ctypes.data,
+                                    ctypes.byref(stop)), "disc_norm_stop_rule")
+    return l_out, bool(stop.value)
 
 
 # ---------------------------------------------------------------------------

@@ -243,25 +243,23 @@ class SlabRegistration:
             reg.set_field(level, buf)
 
     def _norm_step(self, level):
-        """l^(k) of the iteration just run from the slabs' summed interior sums;
-        True when the stop rule of Sec. 2.3 ends the level."""
+        """The slabs' interior sums of the iteration just run, added (the allreduce of
+        a multi-rank run); True when the stop rule of Sec. 2.3 ends the level
+        (disc_norm_stop_rule on the summed history)."""
         sdr = sr = 0.0
         for reg in self.regs:
             s = reg.norm_sums(level, cap=1)      # each exchange restarts the count: this iteration's sums
             sdr += float(s[0, 0])
             sr += float(s[0, 1])
-        h = self.hist[level]
-        lk = np.float32(sdr / sr) if sr > 0.0 else np.float32(np.inf)
-        k = len(h)
-        h.append(lk)
-        if self.stop_eps > 0.0 and k >= self.stop_window:
-            lp = h[k - self.stop_window]
-            return bool(np.isfinite(lp) and np.isfinite(lk) and lp - lk <= np.float32(self.stop_eps))
-        return False
+        self.hist[level].append((sdr, sr))
+        _, stop = disc.norm_stop_rule(self.hist[level], self.stop_window, self.stop_eps)
+        return stop
 
     def norm_history(self, level):
         """l^(k) of the iterations run at `level` (float32, as a context reports it)."""
-        return np.array(self.hist[level], np.float32)
+        if not self.hist[level]:
+            return np.zeros(0, np.float32)
+        return disc.norm_stop_rule(self.hist[level], self.stop_window, self.stop_eps)[0]
 
     def iterate(self):
         """The whole schedule, coarsest level first; returns the iterations run."""
@@ -294,3 +292,101 @@ class SlabRegistration:
         for f, (z0, z1, b0, _) in zip(self._fields(0), self.plan):
             out[:, z0:z1] = f[:, z0 - b0:z1 - b0]
         return out
+
+
+# ---------------------------------------------------------------------------
+# One slab per rank
+# ---------------------------------------------------------------------------
+
+class LibdiscSlab:
+    """The per-rank engine of run_slab_rank: one registration context on this
+    rank's device, over the buffer planes [b0, b1) of its slab.
+
+    ``ct`` and ``cbct_shifted`` are the rank's buffer planes of the CT and of the
+    globally shifted CBCT (torch CUDA tensors on the rank's device); ``qmax`` the
+    whole volume's largest |I_m| and |I_s| (after the shift), so that every
+    interior voxel is computed from the same integers as in a whole-volume run;
+    ``norm_planes`` the interior planes relative to b0.  The engine only ever
+    reads and writes its own context's buffers.
+    """
+
+    def __init__(self, ct, cbct_shifted, qmax, norm_planes, device=0, **kw):
+        p = disc.make_params(global_shift=False, quant_max=tuple(qmax), norm_planes=tuple(norm_planes), **kw)
+        self.reg = disc.Registration(p, device=device)
+        self.reg.set_images(ct, cbct_shifted)
+        self.device = ct.device
+        self.shape = tuple(ct.shape)
+
+    def close(self):
+        self.reg.close()
+
+    def level_shape(self, level):
+        """(nz, ny, nx) of this slab's buffer at pyramid level `level`."""
+        nz, ny, nx = self.shape
+        for _ in range(level):
+            nz, ny, nx = (nz + 1) // 2, (ny + 1) // 2, (nx + 1) // 2
+        return nz, ny, nx
+
+    def iterate_once(self, level):
+        """One iteration at `level`; the interior sums (sum |dr|, sum |r|) of it."""
+        self.reg.iterate(1, sync=False)
+        s = self.reg.norm_sums(level, cap=1)     # set_level_field restarts the count
+        return float(s[0, 0]), float(s[0, 1])
+
+    def level_field(self, level):
+        import torch
+        nz, ny, nx = self.level_shape(level)
+        f = torch.empty((3, nz, ny, nx), dtype=torch.float32, device=self.device)
+        return self.reg.get_level_field(level, f)
+
+    def set_level_field(self, level, field):
+        self.reg.set_field(level, field.contiguous())
+
+    def upsample(self, level):
+        """This slab's buffer field at `level` up-sampled to level - 1 (Algorithm A1)."""
+        import torch
+        nz, ny, nx = self.level_shape(level - 1)
+        rf = torch.empty((3, nz, ny, nx), dtype=torch.float32, device=self.device)
+        disc.k_upsample_field2(self.level_field(level), rf)
+        return rf
+
+
+def run_slab_rank(engine, plan, rank, nz, levels, iters, dist, stop_eps=0.0, stop_window=10, group=None,
+                  sums_device="cpu"):
+    """Algorithm A1 for slab `rank` of `plan` (slab_plan over the finest level's
+    nz planes), one slab per rank: per iteration the engine's step on the rank's
+    buffer, the allreduce of the interior norm sums (allreduce_norm_sums), the
+    stop rule of Sec. 2.3 on the summed history (disc_norm_stop_rule; every rank
+    decides alike), and the halo exchange (halo_exchange); at a level's end each
+    rank up-samples its own buffer and the finer level starts with an exchange.
+    ``iters`` coarsest first.  Returns the summed norm sums per level (finest
+    first), [k][2] float64 each.  `engine` provides iterate_once(level) ->
+    (sum |dr|, sum |r|), level_field(level), set_level_field(level, field) and
+    upsample(level) (LibdiscSlab on a GPU; the tests drive the FP64 oracle
+    through the same calls on CPU ranks).  ``dist`` None: a single rank (one
+    slab, no collectives)."""
+    import torch
+    hist = [[] for _ in range(levels)]
+    for level in range(levels - 1, -1, -1):
+        lplan = level_plan(plan, nz, level)
+        for _ in range(iters[levels - 1 - level]):
+            sdr, sr = engine.iterate_once(level)
+            if dist is not None:
+                sums = torch.tensor([sdr, sr], dtype=torch.float64, device=sums_device)
+                allreduce_norm_sums(sums, dist, group)
+                sdr, sr = float(sums[0]), float(sums[1])
+            hist[level].append((sdr, sr))
+            _, stop = disc.norm_stop_rule(hist[level], stop_window, stop_eps)
+            if dist is not None:
+                buf = engine.level_field(level)
+                halo_exchange(lplan, rank, buf, dist, group)
+                engine.set_level_field(level, buf)
+            if stop:
+                break
+        if level > 0:
+            fine = engine.upsample(level)
+            if dist is not None:
+                halo_exchange(level_plan(plan, nz, level - 1), rank, fine, dist, group)
+            engine.set_level_field(level - 1, fine)
+    return [np.array(h, np.float64).reshape(-1, 2) for h in hist]
+
