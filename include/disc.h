@@ -548,6 +548,17 @@ enum {
 };
 disc_status disc_set_test_switches(uint32_t flags, uint32_t* previous);
 
+/* Bounds-checked build (the paper has no counterpart; the memory-safety check
+ * of the test suite): a library compiled with -DDISC_BOUNDS_CHECK tests every
+ * global index of the per-iteration kernels (warp, moment/force passes,
+ * Gaussian passes, pyramid up- and down-sampling) against its buffer's extent
+ * before the access; an index out of range is not accessed (loads read 0,
+ * stores are dropped) and is counted on the device, never trapped.  This call
+ * synchronises `stream`, returns the count recorded since the last call in
+ * *count and clears it; *checked_build (may be NULL) receives 1 for such a
+ * build.  In the normal build *count and *checked_build are 0. */
+disc_status disc_bounds_violations(void* stream, int64_t* count, int32_t* checked_build);
+
 #ifdef __cplusplus
 }
 #endif

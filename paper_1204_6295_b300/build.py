@@ -40,12 +40,21 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose=False, force=False, extra_flags=()):
+LIB_BOUNDS = os.path.join(HERE, "libdisc_bc.so")   # the bounds-checked build (-DDISC_BOUNDS_CHECK)
+
+
+def build(verbose=False, force=False, extra_flags=(), bounds_check=False):
+    """Compile libdisc.so, or with bounds_check=True the bounds-checked library
+    libdisc_bc.so (every global index of the per-iteration kernels tested before
+    its access; see disc_bounds_violations in include/disc.h)."""
     srcs = sources()
     deps = srcs + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
-    if not force and not _stale(LIB, deps):
-        return LIB
-    objdir = os.path.join(HERE, "_build")
+    lib = LIB_BOUNDS if bounds_check else LIB
+    if bounds_check:
+        extra_flags = tuple(extra_flags) + ("-DDISC_BOUNDS_CHECK",)
+    if not force and not _stale(lib, deps):
+        return lib
+    objdir = os.path.join(HERE, "_build_bc" if bounds_check else "_build")
     os.makedirs(objdir, exist_ok=True)
     objs, cmds = [], []
     for src in srcs:
@@ -59,14 +68,15 @@ def build(verbose=False, force=False, extra_flags=()):
     with concurrent.futures.ThreadPoolExecutor(max_workers=max(1, os.cpu_count() or 1)) as ex:
         for done in ex.map(lambda c: subprocess.run(c, check=True), cmds):
             pass
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [_nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-lrt", "-ldl", "-lpthread"]
     if verbose:
         print(" ".join(cmd), flush=True)
     subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     build(verbose=True, force="--force" in sys.argv)
+    build(verbose=True, force="--force" in sys.argv, bounds_check=True)

@@ -139,8 +139,8 @@ __device__ __forceinline__ void box_body(const BoxArgs& a, int bx, int by, int b
     float vn[B::K1], vo[B::K1];
 #pragma unroll
     for (int k = 0; k < B::K1; ++k) {
-      vn[k] = (has_new && goff[k] >= 0) ? __ldg(pn + goff[k]) : 0.0f;
-      vo[k] = (has_old && goff[k] >= 0) ? __ldg(po + goff[k]) : 0.0f;
+      vn[k] = (has_new && goff[k] >= 0) ? ldg_in(src, (long long)(pn - src) + goff[k], N) : 0.0f;
+      vo[k] = (has_old && goff[k] >= 0) ? ldg_in(src, (long long)(po - src) + goff[k], N) : 0.0f;
     }
     float fm[B::KF], fz[B::KF];
     if (do2) {
@@ -148,8 +148,8 @@ __device__ __forceinline__ void box_body(const BoxArgs& a, int bx, int by, int b
       const float* pz = a.zs + (size_t)zc * plane;
 #pragma unroll
       for (int k = 0; k < B::KF; ++k) {
-        fm[k] = foff[k] >= 0 ? __ldg(pc + foff[k]) : 0.0f;
-        fz[k] = (MODE != kModeStatic && foff[k] >= 0) ? __ldg(pz + foff[k]) : 0.0f;
+        fm[k] = foff[k] >= 0 ? ldg_in(src, (long long)(pc - src) + foff[k], N) : 0.0f;
+        fz[k] = (MODE != kModeStatic && foff[k] >= 0) ? ldg_in(a.zs, (long long)(pz - a.zs) + foff[k], N) : 0.0f;
       }
     }
     float rv[3][B::KO];
@@ -158,7 +158,8 @@ __device__ __forceinline__ void box_body(const BoxArgs& a, int bx, int by, int b
 #pragma unroll
       for (int k = 0; k < B::KO; ++k)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) rv[c][k] = ooff[k] >= 0 ? __ldg(pr + (size_t)c * N + ooff[k]) : 0.0f;
+        for (int c = 0; c < 3; ++c)
+          rv[c][k] = ooff[k] >= 0 ? ldg_in(a.r, (long long)(pr - a.r) + (long long)c * N + ooff[k], 3LL * N) : 0.0f;
     }
     // z sliding sums
 #pragma unroll
@@ -252,7 +253,7 @@ __device__ __forceinline__ void box_body(const BoxArgs& a, int bx, int by, int b
         patch_moments(b1, b2, n, inv_n, __float2int_rn(vc * qs), inv_qs, vfl, dc, sg_);
         const size_t gz = (size_t)zc * plane + (size_t)gy * nx + gx;
         if (MODE == kModeStatic) {
-          a.out[gz] = sg_ > 0.0f ? -dc / sg_ : 0.0f;   // (I_s - E(S)) / STD(S)
+          st_in(a.out, gz, N, sg_ > 0.0f ? -dc / sg_ : 0.0f);   // (I_s - E(S)) / STD(S)
           if (a.sd_out) a.sd_out[gz] = sg_;
           continue;
         }
@@ -260,11 +261,11 @@ __device__ __forceinline__ void box_body(const BoxArgs& a, int bx, int by, int b
         const float d = fmaf(zsv, sg_, dc);               // I'_s - I_m^(k)
         if (MODE == kModeIterate) {
           dring[(zc % 3) * B::FN + fi] = d;
-          if (a.f_tap && out_plane && fx >= 1 && fx <= B::TX && fy >= 1 && fy <= B::TY) a.f_tap[gz] = d;
+          if (a.f_tap && out_plane && fx >= 1 && fx <= B::TX && fy >= 1 && fy <= B::TY) st_in(a.f_tap, gz, N, d);
         } else if (MODE == kModeMaskAB) {
           mask_epilogue(a, gz, vc, dc, sg_, zsv);
         } else if (MODE == kModeCorrected) {
-          a.out[gz] = vc + d;
+          st_in(a.out, gz, N, vc + d);
         } else if (MODE == kModeSsdLoss) {
           acc0 = fmaf(d, d, acc0);
         } else if (MODE == kModeSsdAdjoint) {
@@ -272,10 +273,10 @@ __device__ __forceinline__ void box_body(const BoxArgs& a, int bx, int by, int b
           const float D = -2.0f * d;
           const float A = -D * inv_n;
           const float Bc = sg_ > 0.0f ? -D * zsv * inv_n / sg_ : 0.0f;
-          a.out[gz] = A;
-          a.out[(size_t)N + gz] = Bc;
-          a.out[2 * (size_t)N + gz] = Bc * (vc + dc);
-          a.out[3 * (size_t)N + gz] = D;
+          st_in(a.out, gz, 4LL * N, A);
+          st_in(a.out, (long long)N + gz, 4LL * N, Bc);
+          st_in(a.out, 2LL * N + gz, 4LL * N, Bc * (vc + dc));
+          st_in(a.out, 3LL * N + gz, 4LL * N, D);
         }
       }
     }
@@ -315,14 +316,14 @@ __device__ __forceinline__ void box_body(const BoxArgs& a, int bx, int by, int b
           ry = ro[B::TN + o];
           rz = ro[2 * B::TN + o];
         } else {                               // last plane of the volume only
-          rx = __ldg(a.r + g);
-          ry = __ldg(a.r + (size_t)N + g);
-          rz = __ldg(a.r + 2 * (size_t)N + g);
+          rx = ldg_in(a.r, g, 3LL * N);
+          ry = ldg_in(a.r, (long long)N + g, 3LL * N);
+          rz = ldg_in(a.r, 2LL * N + g, 3LL * N);
         }
         const float keep = a.u_is_dr ? 0.0f : 1.0f;   // u = r + dr, or dr alone
-        a.out[g] = fmaf(keep, rx, drx);
-        a.out[(size_t)N + g] = fmaf(keep, ry, dry);
-        a.out[2 * (size_t)N + g] = fmaf(keep, rz, drz);
+        st_in(a.out, g, 3LL * N, fmaf(keep, rx, drx));
+        st_in(a.out, (long long)N + g, 3LL * N, fmaf(keep, ry, dry));
+        st_in(a.out, 2LL * N + g, 3LL * N, fmaf(keep, rz, drz));
         const bool nin = a.norm_hi <= a.norm_lo || (zo >= a.norm_lo && zo < a.norm_hi);   // the plane enters the norm sums
         acc0 += nin ? norm3(drx, dry, drz) : 0.0f;
         acc1 += nin ? norm3(rx, ry, rz) : 0.0f;

@@ -376,7 +376,7 @@ __device__ __forceinline__ bool box_tma_body(const BoxArgs& a, int bx, int by, i
         patch_moments(b1, b2, n, inv_n, __float2int_rn(vc * qs), inv_qs, vfl, dc, sg_);
         const size_t gz = (size_t)zc * plane + (size_t)gy * nx + gx;
         if (MODE == kModeStatic) {
-          a.out[gz] = sg_ > 0.0f ? -dc / sg_ : 0.0f;   // (I_s - E(S)) / STD(S)
+          st_in(a.out, gz, N, sg_ > 0.0f ? -dc / sg_ : 0.0f);   // (I_s - E(S)) / STD(S)
           if (a.sd_out) a.sd_out[gz] = sg_;
           continue;
         }
@@ -384,11 +384,11 @@ __device__ __forceinline__ bool box_tma_body(const BoxArgs& a, int bx, int by, i
         const float d = fmaf(zsv, sg_, dc);               // I'_s - I_m^(k)
         if (MODE == kModeIterate) {
           dcur[fi] = d;
-          if (a.f_tap && out_plane && fx >= 1 && fx <= B::TX && fy >= 1 && fy <= B::TY) a.f_tap[gz] = d;
+          if (a.f_tap && out_plane && fx >= 1 && fx <= B::TX && fy >= 1 && fy <= B::TY) st_in(a.f_tap, gz, N, d);
         } else if (MODE == kModeMaskAB) {
           mask_epilogue(a, gz, vc, dc, sg_, zsv);
         } else if (MODE == kModeCorrected) {
-          a.out[gz] = vc + d;
+          st_in(a.out, gz, N, vc + d);
         } else if (MODE == kModeSsdLoss) {
           acc0 = fmaf(d, d, acc0);
         } else if (MODE == kModeSsdAdjoint) {
@@ -396,10 +396,10 @@ __device__ __forceinline__ bool box_tma_body(const BoxArgs& a, int bx, int by, i
           const float D = -2.0f * d;
           const float A = -D * inv_n;
           const float Bc = sg_ > 0.0f ? -D * zsv * inv_n / sg_ : 0.0f;
-          a.out[gz] = A;
-          a.out[(size_t)N + gz] = Bc;
-          a.out[2 * (size_t)N + gz] = Bc * (vc + dc);
-          a.out[3 * (size_t)N + gz] = D;
+          st_in(a.out, gz, 4LL * N, A);
+          st_in(a.out, (long long)N + gz, 4LL * N, Bc);
+          st_in(a.out, 2LL * N + gz, 4LL * N, Bc * (vc + dc));
+          st_in(a.out, 3LL * N + gz, 4LL * N, D);
         }
       }
     }
@@ -417,7 +417,6 @@ __device__ __forceinline__ bool box_tma_body(const BoxArgs& a, int bx, int by, i
       const float* mp = mring + ((unsigned)zo % B::NMS) * B::MS;
       const float* mzm = mring + ((unsigned)(zlo ? zo - 1 : zo) % B::NMS) * B::MS;
       const float* mzp = mring + ((unsigned)(zhi ? zo + 1 : zo) % B::NMS) * B::MS;
-      float* out0 = a.out + (size_t)zo * plane;
       const bool nin = a.norm_hi <= a.norm_lo || (zo >= a.norm_lo && zo < a.norm_hi);   // the plane enters the norm sums
 #pragma unroll
       for (int i = 0; i < B::KO; ++i) {
@@ -428,10 +427,10 @@ __device__ __forceinline__ bool box_tma_body(const BoxArgs& a, int bx, int by, i
                                 dzp[fi] - dzm[fi], mzp[fi] - mzm[fi], a.force_mode == DISC_FORCE_DOUBLE);
         const int o = tid + i * kThreads;
         const float rx = ro[o], ry = ro[B::TN + o], rz = ro[2 * B::TN + o];   // staged by group B
-        float* po = out0 + goff3[i];
-        po[0] = fmaf(keep, rx, dr.x);
-        po[(size_t)N] = fmaf(keep, ry, dr.y);
-        po[2 * (size_t)N] = fmaf(keep, rz, dr.z);
+        const long long go = (long long)zo * plane + goff3[i];
+        st_in(a.out, go, 3LL * N, fmaf(keep, rx, dr.x));
+        st_in(a.out, go + N, 3LL * N, fmaf(keep, ry, dr.y));
+        st_in(a.out, go + 2LL * N, 3LL * N, fmaf(keep, rz, dr.z));
         acc0 += nin ? norm3(dr.x, dr.y, dr.z) : 0.0f;
         acc1 += nin ? norm3(rx, ry, rz) : 0.0f;
       }

@@ -243,14 +243,17 @@ __device__ __forceinline__ bool wide_march(const BoxArgs& a, int bx, int by, int
 #pragma unroll
       for (int j = 0; j < B::SY; ++j) {
         const int gy = y0 - 1 + fy0 + j;
-        zsr[j] = (fy0 + j < B::FY && gy >= 0 && gy < ny) ? __ldg(zp + (size_t)gy * nx) : 0.0f;
+        zsr[j] = (fy0 + j < B::FY && gy >= 0 && gy < ny)
+                     ? ldg_in(a.zs, (long long)(zp - a.zs) + (long long)gy * nx, N)
+                     : 0.0f;
       }
     }
     float4 rq[3];                              // r of the force quad, components x, y, z
     if (do3 && qin) {
-      const float4* rp = reinterpret_cast<const float4*>(a.r + (size_t)zf * plane + (size_t)gyq * nx + gxq);
+      const long long q0 = ((long long)zf * plane + (long long)gyq * nx + gxq) / 4;
+      const float4* r4 = reinterpret_cast<const float4*>(a.r);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) rq[c] = __ldg(rp + (size_t)c * (N / 4));
+      for (int c = 0; c < 3; ++c) rq[c] = ldg_in(r4, q0 + (long long)c * (N / 4), 3LL * (N / 4));
     }
     // ---- the step's copies have landed --------------------------------------
     if (!wait_a(bytes_a(zi) != 0)) return false;
@@ -330,7 +333,7 @@ __device__ __forceinline__ bool wide_march(const BoxArgs& a, int bx, int by, int
           const float d = fmaf(zsr[j], sg_, dc);   // I'_s - I_m^(k)
           dcur[fi] = d;
           if (a.f_tap && out_plane && fx_y >= 1 && fx_y <= TX && fy >= 1 && fy <= TY)
-            a.f_tap[(size_t)zc * plane + (size_t)gy * nx + gx_y] = d;
+            st_in(a.f_tap, (long long)zc * plane + (long long)gy * nx + gx_y, N, d);
         }
       }
     }
@@ -385,10 +388,11 @@ __device__ __forceinline__ bool wide_march(const BoxArgs& a, int bx, int by, int
           acc0 += nin ? norm3(dr.x, dr.y, dr.z) : 0.0f;
           acc1 += nin ? norm3(rxv[e], ryv[e], rzv[e]) : 0.0f;
         }
-        float4* po = reinterpret_cast<float4*>(a.out + (size_t)zf * plane + (size_t)gyq * nx + gxq);
-        po[0] = make_float4(ux[0], ux[1], ux[2], ux[3]);
-        po[N / 4] = make_float4(uy[0], uy[1], uy[2], uy[3]);
-        po[2 * (size_t)(N / 4)] = make_float4(uz[0], uz[1], uz[2], uz[3]);
+        float4* o4 = reinterpret_cast<float4*>(a.out);
+        const long long q0 = ((long long)zf * plane + (long long)gyq * nx + gxq) / 4, nq = 3LL * (N / 4);
+        st_in(o4, q0, nq, make_float4(ux[0], ux[1], ux[2], ux[3]));
+        st_in(o4, q0 + N / 4, nq, make_float4(uy[0], uy[1], uy[2], uy[3]));
+        st_in(o4, q0 + 2LL * (N / 4), nq, make_float4(uz[0], uz[1], uz[2], uz[3]));
       }
     }
     // the next step's stage 1 rewrites the z sums and the next stage 2b a d plane

@@ -14,6 +14,33 @@ namespace disc {
 // environment once at load and by the ABI call afterwards.
 uint32_t test_switches();
 
+// Bounds-checked build (compiled with -DDISC_BOUNDS_CHECK; the memory-safety
+// check that stands in for a sanitizer): the per-iteration kernels test every
+// global index against the extent of its buffer before the access.  An index
+// out of range is not accessed (a load reads 0, a store is dropped) and is
+// counted in a device-wide word that disc_bounds_violations reads; nothing
+// traps.  In the normal build the test compiles to nothing.
+#ifdef DISC_BOUNDS_CHECK
+extern __device__ unsigned long long g_bounds_violations;
+__device__ __forceinline__ bool index_ok(long long i, long long n) {
+  if (i >= 0 && i < n) return true;
+  atomicAdd(&g_bounds_violations, 1ull);
+  return false;
+}
+#define DISC_IN(i, n) ::disc::index_ok((long long)(i), (long long)(n))
+#else
+#define DISC_IN(i, n) true
+#endif
+// p[i] of a buffer of n elements (read-only path), and p[i] = v, under that test.
+template <typename T>
+__device__ __forceinline__ T ldg_in(const T* p, long long i, long long n) {
+  return DISC_IN(i, n) ? __ldg(p + i) : T{};
+}
+template <typename T>
+__device__ __forceinline__ void st_in(T* p, long long i, long long n, T v) {
+  if (DISC_IN(i, n)) p[i] = v;
+}
+
 constexpr int kThreads = 256;          // threads per CTA of every z-marching kernel
 constexpr int kNumSMs = 148;           // B300: 2 dies x 74 SMs (queried at run time too)
 

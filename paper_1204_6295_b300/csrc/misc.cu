@@ -94,11 +94,11 @@ __global__ void k_down2(const float* __restrict__ in, float* __restrict__ out, i
         for (int dx = 0; dx < 2; ++dx) {
           const int X = 2 * x + dx, Y = 2 * y + dy, Z = 2 * z + dz;
           if (X < nx && Y < ny && Z < nz) {
-            s += __ldg(in + vix(X, Y, Z, nx, ny));
+            s += ldg_in(in, (long long)vix(X, Y, Z, nx, ny), (long long)nx * ny * nz);
             ++cnt;
           }
         }
-    out[i] = s / (float)cnt;
+    st_in(out, i, nc, s / (float)cnt);
   }
 }
 
@@ -126,13 +126,15 @@ __global__ void k_up2(const float* __restrict__ rc, float* __restrict__ rf, int 
     up_axis(y, cy, y0, y1, ty);
     up_axis(z, cz, z0, z1, tz);
     for (int c = 0; c < 3; ++c) {
-      const float* v = rc + c * ncv;
-      const float c00 = fmaf(tx, __ldg(v + vix(x1, y0, z0, cx, cy)) - __ldg(v + vix(x0, y0, z0, cx, cy)), __ldg(v + vix(x0, y0, z0, cx, cy)));
-      const float c01 = fmaf(tx, __ldg(v + vix(x1, y1, z0, cx, cy)) - __ldg(v + vix(x0, y1, z0, cx, cy)), __ldg(v + vix(x0, y1, z0, cx, cy)));
-      const float c10 = fmaf(tx, __ldg(v + vix(x1, y0, z1, cx, cy)) - __ldg(v + vix(x0, y0, z1, cx, cy)), __ldg(v + vix(x0, y0, z1, cx, cy)));
-      const float c11 = fmaf(tx, __ldg(v + vix(x1, y1, z1, cx, cy)) - __ldg(v + vix(x0, y1, z1, cx, cy)), __ldg(v + vix(x0, y1, z1, cx, cy)));
+      auto at = [&](int a, int b, int d) {
+        return ldg_in(rc, (long long)c * ncv + (long long)vix(a, b, d, cx, cy), 3LL * ncv);
+      };
+      const float c00 = fmaf(tx, at(x1, y0, z0) - at(x0, y0, z0), at(x0, y0, z0));
+      const float c01 = fmaf(tx, at(x1, y1, z0) - at(x0, y1, z0), at(x0, y1, z0));
+      const float c10 = fmaf(tx, at(x1, y0, z1) - at(x0, y0, z1), at(x0, y0, z1));
+      const float c11 = fmaf(tx, at(x1, y1, z1) - at(x0, y1, z1), at(x0, y1, z1));
       const float c0 = fmaf(ty, c01 - c00, c00), c1 = fmaf(ty, c11 - c10, c10);
-      rf[c * nf + i] = 2.0f * fmaf(tz, c1 - c0, c0);
+      st_in(rf, c * nf + i, 3 * nf, 2.0f * fmaf(tz, c1 - c0, c0));
     }
   }
 }

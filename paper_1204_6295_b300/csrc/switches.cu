@@ -51,3 +51,36 @@ extern "C" disc_status disc_set_test_switches(uint32_t flags, uint32_t* previous
   if (previous) *previous = old;
   return DISC_OK;
 }
+
+// ---- bounds-checked build -----------------------------------------------------
+#ifdef DISC_BOUNDS_CHECK
+namespace disc {
+__device__ unsigned long long g_bounds_violations = 0;
+}
+#endif
+
+extern "C" disc_status disc_bounds_violations(void* stream, int64_t* count, int32_t* checked_build) {
+  if (!count) return DISC_ERR_ARG;
+  *count = 0;
+#ifdef DISC_BOUNDS_CHECK
+  if (checked_build) *checked_build = 1;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long* dev = nullptr;
+  unsigned long long v = 0;
+  cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&dev), disc::g_bounds_violations);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&v, dev, sizeof(v), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && v != 0) e = cudaMemsetAsync(dev, 0, sizeof(v), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return DISC_ERR_CUDA;
+  }
+  *count = (int64_t)v;
+#else
+  (void)stream;
+  if (checked_build) *checked_build = 0;
+#endif
+  return DISC_OK;
+}
+

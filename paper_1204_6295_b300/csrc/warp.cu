@@ -21,7 +21,9 @@ __global__ void __launch_bounds__(kWarpThreads) k_warp(const float* __restrict__
   if (x >= nx) return;
   const size_t N = (size_t)nx * ny * nz;
   const size_t g = ((size_t)z * ny + y) * nx + x;
-  m[g] = warp_at(Im, x, y, z, __ldg(r + g), __ldg(r + N + g), __ldg(r + 2 * N + g), nx, ny, nz);
+  st_in(m, g, N,
+        warp_at(Im, x, y, z, ldg_in(r, g, 3 * N), ldg_in(r, N + g, 3 * N), ldg_in(r, 2 * N + g, 3 * N), nx, ny,
+                nz));
 }
 }  // namespace
 
@@ -39,7 +41,9 @@ __global__ void __launch_bounds__(kWarpBatchThreads) k_warp_batch(const __grid_c
   const size_t N = (size_t)nx * ny * nz;
   const size_t g = ((size_t)z * ny + y) * nx + x;
   const float* r = wb.r[p];
-  wb.m[p][g] = warp_at(wb.Im[p], x, y, z, __ldg(r + g), __ldg(r + N + g), __ldg(r + 2 * N + g), nx, ny, nz);
+  st_in(wb.m[p], g, N,
+        warp_at(wb.Im[p], x, y, z, ldg_in(r, g, 3 * N), ldg_in(r, N + g, 3 * N), ldg_in(r, 2 * N + g, 3 * N), nx,
+                ny, nz));
 }
 
 cudaError_t launch_warp_batch(const WarpBatch& wb, int total_blocks, cudaStream_t s) {

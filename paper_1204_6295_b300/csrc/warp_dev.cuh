@@ -5,6 +5,8 @@
 
 #include <cuda_runtime.h>
 
+#include "internal.cuh"
+
 namespace disc {
 
 // Sample position along one axis: voxel c displaced by rv, clamped to
@@ -37,10 +39,16 @@ static __device__ __forceinline__ float warp_at(const float* __restrict__ Im, in
   axis_setup(z, rz, nz, z0, z1, tz);
   const size_t sy0 = (size_t)y0 * nx, sy1 = (size_t)y1 * nx;
   const size_t sz0 = (size_t)z0 * ny * nx, sz1 = (size_t)z1 * ny * nx;
-  const float c000 = __ldg(Im + sz0 + sy0 + x0), c001 = __ldg(Im + sz0 + sy0 + x1);
-  const float c010 = __ldg(Im + sz0 + sy1 + x0), c011 = __ldg(Im + sz0 + sy1 + x1);
-  const float c100 = __ldg(Im + sz1 + sy0 + x0), c101 = __ldg(Im + sz1 + sy0 + x1);
-  const float c110 = __ldg(Im + sz1 + sy1 + x0), c111 = __ldg(Im + sz1 + sy1 + x1);
+#ifdef DISC_BOUNDS_CHECK
+  const long long n = (long long)nx * ny * nz;
+  auto ld = [&](size_t i) { return DISC_IN(i, n) ? __ldg(Im + i) : 0.0f; };
+#else
+  auto ld = [&](size_t i) { return __ldg(Im + i); };
+#endif
+  const float c000 = ld(sz0 + sy0 + x0), c001 = ld(sz0 + sy0 + x1);
+  const float c010 = ld(sz0 + sy1 + x0), c011 = ld(sz0 + sy1 + x1);
+  const float c100 = ld(sz1 + sy0 + x0), c101 = ld(sz1 + sy0 + x1);
+  const float c110 = ld(sz1 + sy1 + x0), c111 = ld(sz1 + sy1 + x1);
   const float c00 = lerpf(c000, c001, tx), c01 = lerpf(c010, c011, tx);
   const float c10 = lerpf(c100, c101, tx), c11 = lerpf(c110, c111, tx);
   return lerpf(lerpf(c00, c01, ty), lerpf(c10, c11, ty), tz);
@@ -69,7 +77,10 @@ static __device__ __forceinline__ void warp_grad_at(const float* __restrict__ Im
     axis_setup(c[a], rv[a], n[a], i0[a], i1[a], t[a]);
   }
   const size_t sx = 1, sy = (size_t)nx, sz = (size_t)nx * ny;
-  auto at = [&](int a, int b, int cc) { return __ldg(Im + (size_t)cc * sz + (size_t)b * sy + (size_t)a * sx); };
+  auto at = [&](int a, int b, int cc) {
+    const size_t i = (size_t)cc * sz + (size_t)b * sy + (size_t)a * sx;
+    return DISC_IN(i, (long long)nx * ny * nz) ? __ldg(Im + i) : 0.0f;
+  };
   const float c000 = at(i0[0], i0[1], i0[2]), c100 = at(i1[0], i0[1], i0[2]);
   const float c010 = at(i0[0], i1[1], i0[2]), c110 = at(i1[0], i1[1], i0[2]);
   const float c001 = at(i0[0], i0[1], i1[2]), c101 = at(i1[0], i0[1], i1[2]);

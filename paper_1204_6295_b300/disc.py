@@ -14,7 +14,8 @@ import re
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libdisc.so")
+# DISC_LIBRARY=bounds loads the bounds-checked build libdisc_bc.so instead
+LIB_PATH = os.path.join(_HERE, "libdisc_bc.so" if os.environ.get("DISC_LIBRARY") == "bounds" else "libdisc.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "disc.h")
 
 if not os.path.exists(LIB_PATH):
@@ -108,6 +109,7 @@ _SIGS = {
     "disc_k_gauss": (_st, [_vp, _vp, _i32, _i32, _i32, _f32, _i32, _vp]),
     "disc_k_check_error": (_st, [_vp]),
     "disc_set_test_switches": (_st, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]),
+    "disc_bounds_violations": (_st, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i32)]),
     "disc_get_mask_constants": (_st, [_vp, ctypes.POINTER(_f32), ctypes.POINTER(_f32)]),
     "disc_k_static_stats": (_st, [_vp, _vp, _vp, _i32, _i32, _i32, ctypes.POINTER(_i32), _f32, _f32, _vp]),
     "disc_k_ratio_median": (_st, [_vp, _vp, _vp, _vp, _vp, _i32, _i32, _i32, ctypes.POINTER(_i32), _f32, _f32,
@@ -143,6 +145,15 @@ def header_functions(path=HEADER):
 def _check(status, where):
     if status != 0:
         raise DiscError(status, where)
+
+
+def bounds_violations(stream=None):
+    """(out-of-range accesses counted since the last call, whether this is the
+    bounds-checked build): disc_bounds_violations."""
+    n, chk = _i64(0), _i32(0)
+    _check(_lib.disc_bounds_violations(_stream(stream), ctypes.byref(n), ctypes.byref(chk)),
+           "disc_bounds_violations")
+    return int(n.value), bool(chk.value)
 
 
 SW_NO_TMA, SW_TMA_STALL, SW_NO_GRAPH, SW_UNROLLED_GRAPH, SW_FAULT_ALLOC, SW_WIDE_ANY = 1, 2, 4, 8, 16, 32
