@@ -516,16 +516,21 @@ def time_batched(disc, torch, dist, steps=2):
                     "after the other; value = all ranks' voxel-iterations / slowest rank's time"}
 
 
-def time_plain(disc, torch, w, dist, steps=5, warmup=2):
-    """Another plain workload's full schedule (a second line of the plain form)."""
-    pair = make_pair(w)
-    nx, ny, nz = w["dims"]
+def time_plain(disc, torch, w, dist, steps=5, warmup=2, pair_dev=None, switches=0):
+    """A plain workload's full schedule: another workload (a second line of the
+    plain form), or the same one with test switches (an alternative schedule)."""
+    if pair_dev is None:
+        pair = make_pair(w)
+        ct = torch.from_numpy(pair.ct).cuda()
+        cbct = torch.from_numpy(pair.cbct).cuda()
+    else:
+        ct, cbct = pair_dev
     cnx, cny, cnz = level_dims(w["dims"], w["levels"])[-1]
-    ct = torch.from_numpy(pair.ct).cuda()
-    cbct = torch.from_numpy(pair.cbct).cuda()
     zeros = torch.zeros((3, cnz, cny, cnx), dtype=torch.float32, device="cuda")
     s = torch.cuda.current_stream()
-    with disc.Registration(patch=w["patch"], sigma=w["sigma"], levels=w["levels"], iters=w["iters"]) as reg:
+    with disc.test_switches(switches):
+        reg = disc.Registration(patch=w["patch"], sigma=w["sigma"], levels=w["levels"], iters=w["iters"])
+    with reg:
         reg.set_images(ct, cbct)
 
         def step():
@@ -692,6 +697,13 @@ def run_ours(args, w, rank, world, local_rank):
 
     continuity = (time_plain(disc, torch, WORKLOADS[CONTINUITY_WORKLOAD], dist)
                   if args.workload != CONTINUITY_WORKLOAD else None)
+    # the same schedule with the next iteration's warp in a kernel of its own
+    # (after the Gaussian) instead of inside the Gaussian z pass
+    sep = time_plain(disc, torch, w, dist, steps=min(args.steps, 3), warmup=1, pair_dev=(ct, cbct),
+                     switches=disc.SW_SEPARATE_WARP)
+    warp_placement = {"fused_in_gauss_z_ms": ms, "separate_kernel_ms": sep["ms_per_step"],
+                      "what": "whole schedule, the warp of I_m by the new field inside the Gaussian z pass "
+                              "(default) or as a kernel of its own (four voxels per thread) after it"}
     batched = None if args.no_batched else time_batched(disc, torch, dist)
     masked = time_masked(disc, torch, w, (ct, cbct), dist)
     mixed = (time_mixed_batch(disc, torch, w, (ct, cbct), dist)
@@ -751,6 +763,7 @@ def run_ours(args, w, rank, world, local_rank):
                              "algorithmic_bytes_per_voxel": WARP_BYTES_PER_VOXEL}},
         "forms": {"plain": {"value": value, "unit": UNIT},
                   **({"plain_" + CONTINUITY_WORKLOAD: continuity} if continuity else {}),
+                  "warp_placement": warp_placement,
                   "batched": batched,
                   "differentiable": diff_form,
                   "masked": masked,

@@ -526,12 +526,17 @@ disc_status disc_k_check_error(void* stream);
  *                           even with a stop rule;
  *   DISC_SW_FAULT_ALLOC     disc_set_images's first device allocation reports
  *                           out-of-memory (host-side fault injection);
+ *   DISC_SW_SEPARATE_WARP   contexts created afterwards warp I_m for the next
+ *                           iteration in a kernel of its own after the
+ *                           Gaussian, instead of inside the Gaussian z pass
+ *                           (same results);
  *   DISC_SW_WIDE_ANY        iteration passes planned afterwards take the
  *                           wide-tile kernel wherever it applies, whatever the
  *                           volume's size (same results; the planner otherwise
  *                           keeps it for volumes large enough to fill the GPU).
  * The initial bits come from the environment (DISC_NO_TMA, DISC_TEST_TMA_STALL,
- * DISC_NO_GRAPH, DISC_UNROLLED_GRAPH, DISC_WIDE_ANY set to a non-zero value;
+ * DISC_NO_GRAPH, DISC_UNROLLED_GRAPH, DISC_WIDE_ANY, DISC_SEPARATE_WARP set to a
+ * non-zero value;
  * DISC_FAULT=alloc),
  * read once when the library is loaded.  disc_set_test_switches replaces all
  * bits; *previous (may be NULL) receives the old ones.  DISC_ERR_ARG for an
@@ -544,7 +549,8 @@ enum {
   DISC_SW_UNROLLED_GRAPH = 8,
   DISC_SW_FAULT_ALLOC = 16,
   DISC_SW_WIDE_ANY = 32,
-  DISC_SW_ALL = 63
+  DISC_SW_SEPARATE_WARP = 64,
+  DISC_SW_ALL = 127
 };
 disc_status disc_set_test_switches(uint32_t flags, uint32_t* previous);
 

@@ -322,6 +322,7 @@ cudaError_t queue_masked(disc_ctx* c, int l, int n, const GaussArgs& g, const No
     cudaError_t e = queue_mask_fill(c, l, c->d_stop + l);
     if (e == cudaSuccess) e = launch_force_dm(fa, blocks, c->s);
     if (e == cudaSuccess) e = gauss_launch(g, v.pb, c->s);
+    if (e == cudaSuccess && c->separate_warp) e = launch_warp(v.Im, v.r, v.m, v.nx, v.ny, v.nz, c->d_stop + l, c->s);
     if (e == cudaSuccess) e = launch_norm_finalize(c->partials, blocks, st, c->s);
     if (e != cudaSuccess) return e;
   }
@@ -353,7 +354,7 @@ cudaError_t queue_iterations(disc_ctx* c, int l, int n, const LoopCond* loop) {
   g.r = v.r;
   g.t = v.t;
   g.Im = v.Im;
-  g.m = v.m;                // the z pass also warps I_m for the next iteration
+  g.m = c->separate_warp ? nullptr : v.m;   // the z pass also warps I_m for the next iteration
   g.add = c->p.smooth_mode ? v.r : nullptr;   // r <- r + G * dr (Sec. 2.1 order)
   g.stop = c->d_stop + l;
   g.nx = v.nx;
@@ -380,6 +381,10 @@ cudaError_t queue_iterations(disc_ctx* c, int l, int n, const LoopCond* loop) {
     if (e != cudaSuccess) return e;
     e = gauss_launch(g, v.pb, c->s);
     if (e != cudaSuccess) return e;
+    if (c->separate_warp) {
+      e = launch_warp(v.Im, v.r, v.m, v.nx, v.ny, v.nz, c->d_stop + l, c->s);
+      if (e != cudaSuccess) return e;
+    }
     e = launch_norm_finalize(c->partials, nparts, st, c->s);
     if (e != cudaSuccess) return e;
   }
@@ -626,6 +631,7 @@ disc_status disc_create(const disc_params* p, int device, void* cuda_stream, dis
   // the loop graph pays a few microseconds per iteration for its condition; it
   // is used where it saves work, when the stop rule can end a level early
   ctx->use_loop = p->stop_eps > 0.0f && (sw & DISC_SW_UNROLLED_GRAPH) == 0u;
+  ctx->separate_warp = (sw & DISC_SW_SEPARATE_WARP) != 0u;
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
   cudaError_t e = cudaStreamCreateWithFlags(&ctx->s, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);

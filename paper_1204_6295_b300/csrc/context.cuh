@@ -88,6 +88,7 @@ struct disc_ctx {
   bool use_graphs = true;
   bool use_loop = true;      // conditional-node loop graphs (with a stop rule; else unrolled graphs)
   long long launches = 0;    // kernels disc_iterate has launched (disc_get_launch_count); -1: not kept
+  bool separate_warp = false;   // warp of the next iteration in its own kernel, not in the Gaussian z pass
 };
 
 

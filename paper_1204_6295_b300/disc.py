@@ -157,6 +157,7 @@ def bounds_violations(stream=None):
 
 
 SW_NO_TMA, SW_TMA_STALL, SW_NO_GRAPH, SW_UNROLLED_GRAPH, SW_FAULT_ALLOC, SW_WIDE_ANY = 1, 2, 4, 8, 16, 32
+SW_SEPARATE_WARP = 64
 
 
 class test_switches:

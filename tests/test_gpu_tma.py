@@ -41,6 +41,12 @@ def _Wide():
     return disc.test_switches(disc.SW_WIDE_ANY)
 
 
+def _SeparateWarp():
+    """The next iteration's warp in a kernel of its own, after the Gaussian."""
+    from paper_1204_6295_b300 import disc
+    return disc.test_switches(disc.SW_SEPARATE_WARP)
+
+
 CASES = [
     ((20, 40, 64), 3),      # (nz, ny, nx), patch
     ((33, 47, 100), 11),    # ragged in all three axes
@@ -135,7 +141,7 @@ def test_registration_bitwise(disc):
     shape = (32, 64, 64)
     ct, cbct, _ = _inputs(shape, 9, 11)
     fields = []
-    for form in ("tma", "plain", "wide"):
+    for form in ("tma", "plain", "wide", "separate_warp"):
         def run():
             reg = disc.Registration(patch=(9, 9, 9), sigma=1.0, levels=2, iters=(6, 5))
             reg.set_images(dev(ct), dev(cbct))
@@ -143,14 +149,14 @@ def test_registration_bitwise(disc):
             out = empty(3, *shape)
             reg.get_field(out)
             return host(out)
-        ctx = {"plain": _NoTma, "wide": _Wide}.get(form)
+        ctx = {"plain": _NoTma, "wide": _Wide, "separate_warp": _SeparateWarp}.get(form)
         if ctx:
             with ctx():
                 fields.append(run())
         else:
             fields.append(run())
-    np.testing.assert_array_equal(fields[0], fields[1])
-    np.testing.assert_array_equal(fields[0], fields[2])
+    for f in fields[1:]:
+        np.testing.assert_array_equal(fields[0], f)
 
 
 # Shapes on which the planner itself picks the wide-tile pass (enough (tile,
