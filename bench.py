@@ -697,13 +697,18 @@ def run_ours(args, w, rank, world, local_rank):
 
     continuity = (time_plain(disc, torch, WORKLOADS[CONTINUITY_WORKLOAD], dist)
                   if args.workload != CONTINUITY_WORKLOAD else None)
-    # the same schedule with the next iteration's warp in a kernel of its own
-    # (after the Gaussian) instead of inside the Gaussian z pass
+    # the same schedule with the next iteration's warp inside the Gaussian z pass
+    # at every level, and in a kernel of its own at every level (the default
+    # takes the kernel of its own on levels of at least 4 Mi voxels)
+    fused = time_plain(disc, torch, w, dist, steps=min(args.steps, 3), warmup=1, pair_dev=(ct, cbct),
+                       switches=disc.SW_FUSED_WARP)
     sep = time_plain(disc, torch, w, dist, steps=min(args.steps, 3), warmup=1, pair_dev=(ct, cbct),
                      switches=disc.SW_SEPARATE_WARP)
-    warp_placement = {"fused_in_gauss_z_ms": ms, "separate_kernel_ms": sep["ms_per_step"],
-                      "what": "whole schedule, the warp of I_m by the new field inside the Gaussian z pass "
-                              "(default) or as a kernel of its own (four voxels per thread) after it"}
+    warp_placement = {"default_ms": ms, "fused_in_gauss_z_everywhere_ms": fused["ms_per_step"],
+                      "separate_kernel_everywhere_ms": sep["ms_per_step"],
+                      "what": "whole schedule: the warp of I_m by the new field inside the Gaussian z pass, or "
+                              "as a kernel of its own after it (a thread marches a column in z and loads the "
+                              "field two planes ahead of its gathers); the default picks per level"}
     batched = None if args.no_batched else time_batched(disc, torch, dist)
     masked = time_masked(disc, torch, w, (ct, cbct), dist)
     mixed = (time_mixed_batch(disc, torch, w, (ct, cbct), dist)

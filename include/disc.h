@@ -283,23 +283,31 @@ disc_status disc_batch_get_field(disc_batch* b, int32_t pair, float* out, int me
 /* Tuning chosen for `level`: work items of the moment/force launch, its grid
  * (equal to items, or one wave of persistent CTAs), and the z chunking: a
  * positive value k lengthens each pair's single-pair chunk k times, a
- * negative value -c sets chunks of c planes (capped at each pair's depth).
- * DISC_ERR_STATE before the level has run. */
+ * negative value -c sets chunks of c planes (capped at each pair's depth), 0
+ * the wide-tile kernel (items = the (tile, plane) pairs of all pairs, capped
+ * at 2^30).  DISC_ERR_STATE before the level has run. */
 disc_status disc_batch_get_tuning(disc_batch* b, int32_t level, int32_t* items, int32_t* grid,
                                   int32_t* zmult);
 
-/* Which moment/force kernel `level` runs: *tma = 1 for the bulk-tensor-copy-
- * fed kernel (every pair's level meets its conditions: nx a multiple of 4,
- * extents of at least one staging box, 16-byte aligned buffers), 0 for the
- * per-thread-load kernel.  DISC_ERR_STATE before the level has run. */
+/* Which moment/force kernel `level` runs: *tma = 2 for the wide-tile kernel
+ * (32 x 32 tiles, the (tile, plane) pairs of all pairs shared evenly by one
+ * wave of CTAs), 1 for the bulk-tensor-copy-fed kernel on 32 x 16 tiles, 0 for
+ * the per-thread-load kernel on 32 x 16 tiles.  Both bulk-copy kernels need
+ * every pair's level to meet their conditions (nx a multiple of 4, extents of
+ * at least one staging box, 16-byte aligned buffers); the tuner times the wide
+ * kernel against the 32 x 16 tilings and keeps the fastest.  DISC_ERR_STATE
+ * before the level has run. */
 disc_status disc_batch_get_box_path(disc_batch* b, int32_t level, int32_t* tma);
 
-/* Pin the tuning of `level` instead of letting the autotuner time it: z
- * chunking `zmult` (as disc_batch_get_tuning reports it; non-zero) and the
- * moment/force launch's grid: 0 for one CTA per work item, g > 0 for
- * min(g, items) persistent CTAs striding over the work table.  Takes effect
- * at the level's next iteration (the level's graph is rebuilt); synchronises
- * the batch's stream.  The fields do not depend on the tuning (bit for bit). */
+/* Pin the tuning of `level` instead of letting the autotuner time it.  zmult
+ * non-zero: the 32 x 16 tilings with z chunking `zmult` (as
+ * disc_batch_get_tuning reports it) and the moment/force launch's grid: 0 for
+ * one CTA per work item, g > 0 for min(g, items) persistent CTAs striding over
+ * the work table.  zmult 0: the wide-tile kernel with one wave of CTAs (grid
+ * 0) or g CTAs sharing the planes (DISC_ERR_CUDA at the level's first
+ * iteration when a pair's level cannot take it).  Takes effect at the level's
+ * next iteration (the level's graph is rebuilt); synchronises the batch's
+ * stream.  The fields do not depend on the tuning (bit for bit). */
 disc_status disc_batch_pin_tuning(disc_batch* b, int32_t level, int32_t zmult, int32_t grid);
 
 /* Release the batch and every pair context.  NULL is accepted. */
@@ -528,15 +536,17 @@ disc_status disc_k_check_error(void* stream);
  *                           out-of-memory (host-side fault injection);
  *   DISC_SW_SEPARATE_WARP   contexts created afterwards warp I_m for the next
  *                           iteration in a kernel of its own after the
- *                           Gaussian, instead of inside the Gaussian z pass
- *                           (same results);
+ *                           Gaussian at every level (same results);
+ *   DISC_SW_FUSED_WARP      ... inside the Gaussian z pass at every level (by
+ *                           default levels of at least 4 Mi voxels take the
+ *                           separate kernel, smaller ones the fused form);
  *   DISC_SW_WIDE_ANY        iteration passes planned afterwards take the
  *                           wide-tile kernel wherever it applies, whatever the
  *                           volume's size (same results; the planner otherwise
  *                           keeps it for volumes large enough to fill the GPU).
  * The initial bits come from the environment (DISC_NO_TMA, DISC_TEST_TMA_STALL,
- * DISC_NO_GRAPH, DISC_UNROLLED_GRAPH, DISC_WIDE_ANY, DISC_SEPARATE_WARP set to a
- * non-zero value;
+ * DISC_NO_GRAPH, DISC_UNROLLED_GRAPH, DISC_WIDE_ANY, DISC_SEPARATE_WARP,
+ * DISC_FUSED_WARP set to a non-zero value;
  * DISC_FAULT=alloc),
  * read once when the library is loaded.  disc_set_test_switches replaces all
  * bits; *previous (may be NULL) receives the old ones.  DISC_ERR_ARG for an
@@ -550,7 +560,8 @@ enum {
   DISC_SW_FAULT_ALLOC = 16,
   DISC_SW_WIDE_ANY = 32,
   DISC_SW_SEPARATE_WARP = 64,
-  DISC_SW_ALL = 127
+  DISC_SW_FUSED_WARP = 128,
+  DISC_SW_ALL = 255
 };
 disc_status disc_set_test_switches(uint32_t flags, uint32_t* previous);
 

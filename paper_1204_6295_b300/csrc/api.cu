@@ -322,7 +322,7 @@ cudaError_t queue_masked(disc_ctx* c, int l, int n, const GaussArgs& g, const No
     cudaError_t e = queue_mask_fill(c, l, c->d_stop + l);
     if (e == cudaSuccess) e = launch_force_dm(fa, blocks, c->s);
     if (e == cudaSuccess) e = gauss_launch(g, v.pb, c->s);
-    if (e == cudaSuccess && c->separate_warp) e = launch_warp(v.Im, v.r, v.m, v.nx, v.ny, v.nz, c->d_stop + l, c->s);
+    if (e == cudaSuccess && v.sep_warp) e = launch_warp(v.Im, v.r, v.m, v.nx, v.ny, v.nz, c->d_stop + l, c->s);
     if (e == cudaSuccess) e = launch_norm_finalize(c->partials, blocks, st, c->s);
     if (e != cudaSuccess) return e;
   }
@@ -354,7 +354,7 @@ cudaError_t queue_iterations(disc_ctx* c, int l, int n, const LoopCond* loop) {
   g.r = v.r;
   g.t = v.t;
   g.Im = v.Im;
-  g.m = c->separate_warp ? nullptr : v.m;   // the z pass also warps I_m for the next iteration
+  g.m = v.sep_warp ? nullptr : v.m;   // the z pass also warps I_m for the next iteration
   g.add = c->p.smooth_mode ? v.r : nullptr;   // r <- r + G * dr (Sec. 2.1 order)
   g.stop = c->d_stop + l;
   g.nx = v.nx;
@@ -381,7 +381,7 @@ cudaError_t queue_iterations(disc_ctx* c, int l, int n, const LoopCond* loop) {
     if (e != cudaSuccess) return e;
     e = gauss_launch(g, v.pb, c->s);
     if (e != cudaSuccess) return e;
-    if (c->separate_warp) {
+    if (v.sep_warp) {
       e = launch_warp(v.Im, v.r, v.m, v.nx, v.ny, v.nz, c->d_stop + l, c->s);
       if (e != cudaSuccess) return e;
     }
@@ -520,6 +520,27 @@ namespace disc {
 
 cudaError_t ctx_reset_level_counters(disc_ctx* c, int l) { return reset_level_counters(c, l); }
 
+cudaError_t ctx_reserve_partials(disc_ctx* c, int n) {
+  if (n <= c->max_parts) return cudaSuccess;
+  cudaError_t e = cudaStreamSynchronize(c->s);
+  if (e != cudaSuccess) return e;
+  cudaFree(c->partials);
+  c->partials = nullptr;
+  c->max_parts = 0;
+  e = cudaMalloc(&c->partials, sizeof(float) * 2 * (size_t)n);
+  if (e != cudaSuccess) return e;
+  c->max_parts = n;
+  for (int l = 0; l < DISC_MAX_LEVELS; ++l) {   // the context's own graphs hold the old buffer
+    Level& v = c->lev[l];
+    if (v.graph) cudaGraphExecDestroy(v.graph);
+    if (v.loop) cudaGraphExecDestroy(v.loop);
+    v.graph = nullptr;
+    v.loop = nullptr;
+    v.graph_iters = 0;
+  }
+  return cudaSuccess;
+}
+
 BoxArgs ctx_box_args(const disc_ctx* c, int l) {
   const Level& v = c->lev[l];
   BoxArgs a = box_args(c, v);
@@ -631,7 +652,7 @@ disc_status disc_create(const disc_params* p, int device, void* cuda_stream, dis
   // the loop graph pays a few microseconds per iteration for its condition; it
   // is used where it saves work, when the stop rule can end a level early
   ctx->use_loop = p->stop_eps > 0.0f && (sw & DISC_SW_UNROLLED_GRAPH) == 0u;
-  ctx->separate_warp = (sw & DISC_SW_SEPARATE_WARP) != 0u;
+  ctx->separate_warp = (sw & DISC_SW_SEPARATE_WARP) ? 1 : ((sw & DISC_SW_FUSED_WARP) ? 0 : -1);
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
   cudaError_t e = cudaStreamCreateWithFlags(&ctx->s, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
@@ -706,6 +727,7 @@ disc_status disc_set_images(disc_ctx* ctx, const float* ct, const float* cbct, i
       v.pa = box_plan_iter(v.nx, v.ny, v.nz, ctx->hx, ctx->hy, ctx->hz, ctx->num_sms, nullptr, nullptr, nullptr);
       v.pn = box_plan(kModeIterate, v.nx, v.ny, v.nz, ctx->hx, ctx->hy, ctx->hz, ctx->num_sms);
       v.pb = gauss_plan(v.nx, v.ny, v.nz, ctx->R, ctx->num_sms);
+      v.sep_warp = ctx->separate_warp >= 0 ? ctx->separate_warp == 1 : v.N >= kSeparateWarpVoxels;
       BoxPlan ps = box_plan(kModeStatic, v.nx, v.ny, v.nz, ctx->hx, ctx->hy, ctx->hz, ctx->num_sms);
       if (v.pa.grid.x == 0 || v.pb.grid.x == 0 || ps.grid.x == 0) {
         free_levels(ctx);

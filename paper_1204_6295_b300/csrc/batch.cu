@@ -43,6 +43,14 @@ struct disc_batch {
   // all pairs in device memory, 4 per pair
   bool tma[DISC_MAX_LEVELS] = {};
   void* d_maps[DISC_MAX_LEVELS] = {};
+  // the wide-tile box pass (32 x 32 tiles, balanced plane shares over all pairs)
+  // where every pair's level allows it: its table, tensor maps and grid; used[l]
+  // when the tuner (or a pin) chose it
+  bool wide_ok[DISC_MAX_LEVELS] = {};
+  bool wide[DISC_MAX_LEVELS] = {};
+  WideBatch wtab[DISC_MAX_LEVELS];
+  void* d_wmaps[DISC_MAX_LEVELS] = {};
+  int wide_grid[DISC_MAX_LEVELS] = {};
   cudaGraphExec_t graph[DISC_MAX_LEVELS] = {};
   int graph_iters[DISC_MAX_LEVELS] = {};
   // tuning pinned by the caller (disc_batch_pin_tuning): z chunking and grid
@@ -149,6 +157,61 @@ cudaError_t prepare_tma(disc_batch* b, int l) {
   return cudaSuccess;
 }
 
+// Whether every pair's level l can take the wide-tile box pass; if so its work
+// table, tensor maps (device memory) and grid (one wave), and pair partials
+// that hold one float2 per CTA of that grid.
+cudaError_t prepare_wide(disc_batch* b, int l) {
+  b->wide_ok[l] = false;
+  for (int i = 0; i < b->npairs; ++i) {
+    const Level& v = b->pair[i]->lev[l];
+    if (!box_wide_ok(v.nx, v.ny, v.nz, b->H, b->H, b->H)) return cudaSuccess;
+  }
+  int tx = 0, ty = 0;
+  box_wide_tile(&tx, &ty);
+  const int occ = box_wide_occupancy(b->H);
+  if (occ < 1) return cudaSuccess;
+  const int grid = b->num_sms * occ;
+  alignas(128) unsigned char maps[kMaxBatch * 2 * kTmaMapBytes];
+  WideBatch& w = b->wtab[l];
+  std::memset(&w, 0, sizeof(w));
+  w.count = b->npairs;
+  long long off = 0;
+  for (int i = 0; i < b->npairs; ++i) {
+    cudaError_t e = ctx_reserve_partials(b->pair[i], grid);
+    if (e != cudaSuccess) return e;
+    const Level& v = b->pair[i]->lev[l];
+    w.args[i] = ctx_box_args(b->pair[i], l);
+    if (!box_wide_encode(w.args[i], maps + i * 2 * kTmaMapBytes)) return cudaSuccess;
+    w.tiles_x[i] = (v.nx + tx - 1) / tx;
+    w.off[i] = off;
+    off += (long long)w.tiles_x[i] * ((v.ny + ty - 1) / ty) * v.nz;
+  }
+  w.off[b->npairs] = off;
+  if (!b->d_wmaps[l]) {
+    cudaError_t e = cudaMalloc(&b->d_wmaps[l], kMaxBatch * 2 * kTmaMapBytes);
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e = cudaMemcpyAsync(b->d_wmaps[l], maps, b->npairs * 2 * kTmaMapBytes, cudaMemcpyHostToDevice, b->s);
+  if (e != cudaSuccess) return e;
+  // pageable source: cudaMemcpyAsync has staged it when it returns; the stream
+  // orders the copy before the launches
+  b->wide_grid[l] = grid;
+  b->wide_ok[l] = true;
+  return cudaSuccess;
+}
+
+// Norm table of the wide launch: every pair adds one partial per CTA.
+void make_wide_norm_table(disc_batch* b, int l, int grid) {
+  NormBatch& n = b->norm[l];
+  std::memset(&n, 0, sizeof(n));
+  n.count = b->npairs;
+  for (int i = 0; i < b->npairs; ++i) {
+    n.partials[i] = b->pair[i]->partials;
+    n.nparts[i] = grid;
+    n.st[i] = ctx_norm_state(b->pair[i], l);
+  }
+}
+
 void build_tables(disc_batch* b, int l) {
   GaussBatch& xy = b->xy[l];
   GaussBatch& z = b->zt[l];
@@ -197,6 +260,7 @@ size_t box_smem(const disc_batch* b, int l) {
 }
 
 cudaError_t launch_box(disc_batch* b, int l, int total, int grid) {
+  if (b->wide[l]) return box_wide_launch_batch(b->wtab[l], b->d_wmaps[l], b->H, grid, b->s);
   if (b->tma[l]) return box_tma_launch_batch(b->box[l], b->d_maps[l], b->H, grid, b->s);
   return box_fast_launch_batch(b->box[l], b->H, total, grid, box_smem(b, l), b->s);
 }
@@ -216,6 +280,19 @@ cudaError_t tune_level(disc_batch* b, int l) {
   if (e != cudaSuccess) {
     cudaEventDestroy(e0);
     return e;
+  }
+  b->wide[l] = false;
+  if (b->pinned[l] && b->pin_zmult[l] == 0) {   // the caller's choice: the wide-tile pass
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!b->wide_ok[l]) return cudaErrorInvalidValue;
+    const int g = b->pin_grid[l] > 0 && b->pin_grid[l] < b->wide_grid[l] ? b->pin_grid[l] : b->wide_grid[l];
+    b->wide[l] = true;
+    b->zmult[l] = 0;
+    b->box_total[l] = (int)(b->wtab[l].off[b->npairs] < (1LL << 30) ? b->wtab[l].off[b->npairs] : (1LL << 30));
+    b->box_grid[l] = g;
+    make_wide_norm_table(b, l, g);
+    return cudaSuccess;
   }
   if (b->pinned[l]) {                        // the caller's choice, untimed
     cudaEventDestroy(e0);
@@ -252,9 +329,39 @@ cudaError_t tune_level(disc_batch* b, int l) {
       }
     }
   }
+  // the wide-tile pass over all pairs, one wave
+  bool best_wide = false;
+  if (e == cudaSuccess && b->wide_ok[l]) {
+    b->wide[l] = true;
+    const int g = b->wide_grid[l];
+    e = launch_box(b, l, 0, g);               // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(e0, b->s);
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = launch_box(b, l, 0, g);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, b->s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    // the wide launch changes the pass's resource use, which its three timed
+    // launches alone do not show (the Gaussian passes that follow share the
+    // SMs): it has to win by a clear margin
+    if (e == cudaSuccess && ms < 0.9f * best) {
+      best = ms;
+      best_wide = true;
+    }
+    b->wide[l] = false;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (e != cudaSuccess) return e;
+  if (best_wide) {
+    const long long P = b->wtab[l].off[b->npairs];
+    b->wide[l] = true;
+    b->zmult[l] = 0;
+    b->box_total[l] = (int)(P < (1LL << 30) ? P : (1LL << 30));
+    b->box_grid[l] = b->wide_grid[l];
+    make_wide_norm_table(b, l, b->wide_grid[l]);
+    return cudaSuccess;
+  }
   int total = 0;
   make_box_table(b, l, best_mult, &total);
   b->zmult[l] = best_mult;
@@ -351,6 +458,7 @@ disc_status disc_batch_destroy(disc_batch* b) {
   for (int l = 0; l < DISC_MAX_LEVELS; ++l) {
     if (b->graph[l]) cudaGraphExecDestroy(b->graph[l]);
     if (b->d_maps[l]) cudaFree(b->d_maps[l]);
+    if (b->d_wmaps[l]) cudaFree(b->d_wmaps[l]);
   }
   for (int i = 0; i < b->npairs; ++i) disc_destroy(b->pair[i]);
   if (b->ev_in) cudaEventDestroy(b->ev_in);
@@ -411,6 +519,7 @@ disc_status disc_batch_iterate(disc_batch* b, int32_t max_iters, int32_t* iters_
     if (left > 0 && budget > 0) {
       if (!b->ready[l]) {
         BCK(prepare_tma(b, l));
+        BCK(prepare_wide(b, l));
         build_tables(b, l);
         BCK(launch_warp_batch(b->warp[l], b->warp_total[l], b->s));     // m for the tuning launches
         BCK(tune_level(b, l));
@@ -467,13 +576,13 @@ disc_status disc_batch_get_tuning(disc_batch* b, int32_t level, int32_t* items, 
 disc_status disc_batch_get_box_path(disc_batch* b, int32_t level, int32_t* tma) {
   if (!b || !tma || level < 0 || level >= b->L) return DISC_ERR_ARG;
   if (!b->ready[level]) return DISC_ERR_STATE;
-  *tma = b->tma[level] ? 1 : 0;
+  *tma = b->wide[level] ? 2 : (b->tma[level] ? 1 : 0);
   return DISC_OK;
 }
 
 disc_status disc_batch_pin_tuning(disc_batch* b, int32_t level, int32_t zmult, int32_t grid) {
   if (!b || level < 0 || level >= b->L) return DISC_ERR_ARG;
-  if (zmult == 0 || grid < 0) return DISC_ERR_ARG;
+  if (grid < 0) return DISC_ERR_ARG;
   if (b->sticky != DISC_OK) return DISC_ERR_STATE;
   DeviceGuard guard(b->device);
   BCK(cudaStreamSynchronize(b->s));          // the level's graph may be in flight

@@ -133,8 +133,10 @@ __device__ __forceinline__ bool wide_march(const BoxArgs& a, int bx, int by, int
     if (nb == 0) return;
     mbar_expect_tx(bar, zi == zw ? nb + a.stall_tx : nb);
     const int zo = zi - (2 * H + 1), zc = zi - H;
-    if (zi < nz) tma_load_3d(wn, map_w, x0 - B::XW, y0 - 1 - H, zi, bar);
-    if (zo >= zi0) tma_load_3d(wo, map_w, x0 - B::XW, y0 - 1 - H, zo, bar);
+    // the entering plane is read again when it is the centre plane and when it
+    // leaves the window: kept in L2; the leaving plane's lines are done
+    if (zi < nz) tma_load_3d_hint(wn, map_w, x0 - B::XW, y0 - 1 - H, zi, bar, l2_policy_evict_last());
+    if (zo >= zi0) tma_load_3d_hint(wo, map_w, x0 - B::XW, y0 - 1 - H, zo, bar, l2_policy_evict_first());
     if (zc >= zc_lo && zc <= zc_hi)
       tma_load_3d(mring + ((unsigned)zc % B::NMS) * B::MS, map_f, x0 - B::XF, y0 - 1, zc, bar);
   };
@@ -244,7 +246,7 @@ __device__ __forceinline__ bool wide_march(const BoxArgs& a, int bx, int by, int
       for (int j = 0; j < B::SY; ++j) {
         const int gy = y0 - 1 + fy0 + j;
         zsr[j] = (fy0 + j < B::FY && gy >= 0 && gy < ny)
-                     ? ldg_in(a.zs, (long long)(zp - a.zs) + (long long)gy * nx, N)
+                     ? ldcs_in(a.zs, (long long)(zp - a.zs) + (long long)gy * nx, N)
                      : 0.0f;
       }
     }
@@ -253,7 +255,7 @@ __device__ __forceinline__ bool wide_march(const BoxArgs& a, int bx, int by, int
       const long long q0 = ((long long)zf * plane + (long long)gyq * nx + gxq) / 4;
       const float4* r4 = reinterpret_cast<const float4*>(a.r);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) rq[c] = ldg_in(r4, q0 + (long long)c * (N / 4), 3LL * (N / 4));
+      for (int c = 0; c < 3; ++c) rq[c] = ldcs_in(r4, q0 + (long long)c * (N / 4), 3LL * (N / 4));
     }
     // ---- the step's copies have landed --------------------------------------
     if (!wait_a(bytes_a(zi) != 0)) return false;
@@ -390,9 +392,9 @@ __device__ __forceinline__ bool wide_march(const BoxArgs& a, int bx, int by, int
         }
         float4* o4 = reinterpret_cast<float4*>(a.out);
         const long long q0 = ((long long)zf * plane + (long long)gyq * nx + gxq) / 4, nq = 3LL * (N / 4);
-        st_in(o4, q0, nq, make_float4(ux[0], ux[1], ux[2], ux[3]));
-        st_in(o4, q0 + N / 4, nq, make_float4(uy[0], uy[1], uy[2], uy[3]));
-        st_in(o4, q0 + 2LL * (N / 4), nq, make_float4(uz[0], uz[1], uz[2], uz[3]));
+        stcs_in(o4, q0, nq, make_float4(ux[0], ux[1], ux[2], ux[3]));
+        stcs_in(o4, q0 + N / 4, nq, make_float4(uy[0], uy[1], uy[2], uy[3]));
+        stcs_in(o4, q0 + 2LL * (N / 4), nq, make_float4(uz[0], uz[1], uz[2], uz[3]));
       }
     }
     // the next step's stage 1 rewrites the z sums and the next stage 2b a d plane
@@ -468,6 +470,63 @@ __global__ void __launch_bounds__(kWideThreads, 2)
   write_partials(acc0, acc1, reinterpret_cast<float*>(smem + B::o_red), a.partials, blockIdx.x);
 }
 
+// Many volumes in one launch: the (tile, plane) pairs of volume p are the
+// planes [off[p], off[p + 1]) of one sequence over all volumes, which the CTAs
+// share evenly as in k_box_wide; a march never crosses a volume.  The tensor
+// maps of volume p are maps[2p], maps[2p + 1] (W box, F box of its m) in global
+// memory.  Each CTA writes its partial sums into slot blockIdx.x of every
+// volume's partials (zeros for the volumes it has no planes of), so that each
+// volume's norm adds gridDim.x partials.
+template <int H, int TX, int TY>
+__global__ void __launch_bounds__(kWideThreads, 2)
+    k_box_wide_batch(const __grid_constant__ WideBatch wb, const CUtensorMap* __restrict__ maps) {
+  using B = WideLayout<H, TX, TY>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  pdl_wait();
+  pdl_release();
+  if (!wide_setup<H, TX, TY>(smem, nullptr)) return;
+  float* red = reinterpret_cast<float*>(smem + B::o_red);
+  uint32_t pa = 0;
+  const long long P = wb.off[wb.count];
+  const long long lo = P * blockIdx.x / gridDim.x, hi = P * (blockIdx.x + 1) / gridDim.x;
+  // volumes without planes in [lo, hi): zero partials
+  if (threadIdx.x == 0) {
+    for (int p = 0; p < wb.count; ++p)
+      if (wb.args[p].partials != nullptr && (wb.off[p + 1] <= lo || wb.off[p] >= hi)) {
+        wb.args[p].partials[2 * blockIdx.x] = 0.0f;
+        wb.args[p].partials[2 * blockIdx.x + 1] = 0.0f;
+      }
+  }
+  int p = 0;
+  while (p + 1 < wb.count && wb.off[p + 1] <= lo) ++p;
+  for (long long gp = lo; gp < hi && p < wb.count; ++p) {
+    const BoxArgs& a = wb.args[p];
+    const long long pend = min(hi, wb.off[p + 1]);
+    float acc0 = 0.0f, acc1 = 0.0f;
+    const CUtensorMap* mw = maps + 2 * p;
+    if (threadIdx.x == 0) {
+      // the maps reach the tensor-map proxy through global memory
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(mw))
+                   : "memory");
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(mw + 1))
+                   : "memory");
+    }
+    const bool stopped = a.stop != nullptr && *(volatile const int*)a.stop != 0;
+    while (gp < pend) {
+      const long long local = gp - wb.off[p];
+      const int t = (int)(local / a.nz), z0 = (int)(local - (long long)t * a.nz);
+      const int z1 = (int)min((long long)a.nz, (long long)z0 + (pend - gp));
+      __syncthreads();                        // the previous march's reads of the buffers are done
+      if (!stopped && !wide_march<H, TX, TY>(a, t % wb.tiles_x[p], t / wb.tiles_x[p], z0, z1, mw, mw + 1, smem, pa,
+                                               acc0, acc1))
+        return;
+      gp += z1 - z0;
+    }
+    write_partials(acc0, acc1, red, a.partials, blockIdx.x);
+    __syncthreads();                          // red is reused by the next volume's partials
+  }
+}
+
 // ---- host side ---------------------------------------------------------------
 constexpr int kMaxDevices = 64;
 
@@ -517,6 +576,29 @@ struct WideHost {
     const int tx = (a.nx + TX - 1) / TX, ty = (a.ny + TY - 1) / TY;
     return launch_pdl(k, p.grid, dim3(kWideThreads), B::bytes, s, b, mw, mf, tx, ty);
   }
+  static bool encode(const BoxArgs& a, CUtensorMap* m) {
+    m[0] = CUtensorMap{};
+    m[1] = CUtensorMap{};
+    return tma_encode_volume(&m[0], a.src, 3, a.nx, a.ny, a.nz, B::WXT, B::WY, 1) &&
+           tma_encode_volume(&m[1], a.src, 3, a.nx, a.ny, a.nz, B::FXT, B::FY, 1);
+  }
+  static cudaError_t launch_batch(const WideBatch& wb, const CUtensorMap* maps, int grid, cudaStream_t s) {
+    static int set[kMaxDevices] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    auto k = k_box_wide_batch<H, TX, TY>;
+    if (!set[dev]) {
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B::bytes);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+      if (e != cudaSuccess) return e;
+      set[dev] = 1;
+    }
+    return launch_pdl(k, dim3(grid), dim3(kWideThreads), B::bytes, s, wb, maps);
+  }
 };
 
 template <typename R, typename F>
@@ -560,6 +642,18 @@ void box_wide_tile(int* tx, int* ty) {
 cudaError_t box_wide_launch(const BoxArgs& a, const BoxPlan& p, cudaStream_t s) {
   if ((((uintptr_t)a.src | (uintptr_t)a.r | (uintptr_t)a.out) & 15u) != 0u) return cudaErrorInvalidValue;
   return wide_dispatch<cudaError_t>(a.hx, cudaErrorInvalidValue, [&](auto w) { return decltype(w)::launch(a, p, s); });
+}
+
+bool box_wide_encode(const BoxArgs& a, void* maps) {
+  return wide_dispatch<bool>(a.hx, false,
+                             [&](auto w) { return decltype(w)::encode(a, static_cast<CUtensorMap*>(maps)); });
+}
+
+cudaError_t box_wide_launch_batch(const WideBatch& wb, const void* maps, int h, int grid, cudaStream_t s) {
+  if (grid < 1) return cudaSuccess;
+  return wide_dispatch<cudaError_t>(h, cudaErrorInvalidValue, [&](auto w) {
+    return decltype(w)::launch_batch(wb, static_cast<const CUtensorMap*>(maps), grid, s);
+  });
 }
 
 cudaError_t box_wide_error(cudaStream_t s, int* flag) {

@@ -52,7 +52,15 @@ struct Level {
   long long graph_kernels = 0;       // kernel nodes of `graph`
   cudaGraphExec_t loop = nullptr;    // one iteration inside a conditional WHILE node
   long long loop_kernels = 0;        // kernel nodes of one iteration of `loop`
+  bool sep_warp = false;             // this level's warp runs in its own kernel
 };
+
+// Levels this large warp I_m in a kernel of their own (k_warp_z: the field is
+// loaded two planes ahead of the gathers) rather than inside the Gaussian z
+// pass, whose register queue leaves too few warps to hide the gathers: the
+// separate kernel measured 5.6% faster per iteration at 512x512x256 and 4% at
+// 256x256x128, and slower at 128x128x64 and below.
+constexpr size_t kSeparateWarpVoxels = (size_t)4 << 20;
 
 
 }  // namespace disc
@@ -88,13 +96,19 @@ struct disc_ctx {
   bool use_graphs = true;
   bool use_loop = true;      // conditional-node loop graphs (with a stop rule; else unrolled graphs)
   long long launches = 0;    // kernels disc_iterate has launched (disc_get_launch_count); -1: not kept
-  bool separate_warp = false;   // warp of the next iteration in its own kernel, not in the Gaussian z pass
+  // where the next iteration's warp runs: 1 in a kernel of its own after the
+  // Gaussian (levels of at least kSeparateWarpVoxels voxels), 0 inside the
+  // Gaussian z pass; -1 decides per level
+  int separate_warp = -1;
 };
 
 
 namespace disc {
 // Helpers of api.cu used by the batched API.
 cudaError_t ctx_reset_level_counters(disc_ctx* c, int l);
+// Grow the context's per-CTA norm partials to at least n (float2 each); drops
+// its own captured graphs, which hold the old buffer.
+cudaError_t ctx_reserve_partials(disc_ctx* c, int n);
 BoxArgs ctx_box_args(const disc_ctx* c, int l);       // iteration-mode box arguments of level l
 GaussArgs ctx_gauss_args(const disc_ctx* c, int l);   // Gaussian arguments of level l (with warp)
 NormState ctx_norm_state(const disc_ctx* c, int l);

@@ -40,6 +40,16 @@ template <typename T>
 __device__ __forceinline__ void st_in(T* p, long long i, long long n, T v) {
   if (DISC_IN(i, n)) p[i] = v;
 }
+// The same for data read or written once: streaming loads and stores (evicted
+// first from L2, so that they do not push out data the kernel reuses).
+template <typename T>
+__device__ __forceinline__ T ldcs_in(const T* p, long long i, long long n) {
+  return DISC_IN(i, n) ? __ldcs(p + i) : T{};
+}
+template <typename T>
+__device__ __forceinline__ void stcs_in(T* p, long long i, long long n, T v) {
+  if (DISC_IN(i, n)) __stcs(p + i, v);
+}
 
 constexpr int kThreads = 256;          // threads per CTA of every z-marching kernel
 constexpr int kNumSMs = 148;           // B300: 2 dies x 74 SMs (queried at run time too)
@@ -172,6 +182,19 @@ void box_wide_tile(int* tx, int* ty);
 cudaError_t box_wide_launch(const BoxArgs& a, const BoxPlan& p, cudaStream_t s);
 // Reads (synchronising s) and clears the wide pass's own error word, OR-ing it into *flag.
 cudaError_t box_wide_error(cudaStream_t s, int* flag);
+// Batched wide-tile launch over many volumes: volume p owns planes [off[p],
+// off[p + 1]) of the sequence of every volume's (tile, plane) pairs (tiles_x[p]
+// tiles per row, args[p].nz planes per tile column); its two tensor maps are
+// maps[2p], maps[2p + 1] (kTmaMapBytes each, written by box_wide_encode).
+// args[p].partials needs one float2 per CTA of the launch.
+struct WideBatch {
+  int count;
+  long long off[kMaxBatch + 1];
+  int tiles_x[kMaxBatch];
+  BoxArgs args[kMaxBatch];
+};
+bool box_wide_encode(const BoxArgs& a, void* maps /* 2 x kTmaMapBytes, 64-byte aligned */);
+cudaError_t box_wide_launch_batch(const WideBatch& wb, const void* maps, int h, int grid, cudaStream_t s);
 cudaError_t box_launch(int mode, const BoxArgs& a, const BoxPlan& plan, cudaStream_t s);
 
 // Trilinear warp m = I_m(x + r(x)), warp.cu

@@ -28,6 +28,7 @@ uint32_t env_switches() {
   if (env_on("DISC_UNROLLED_GRAPH")) f |= DISC_SW_UNROLLED_GRAPH;
   if (env_on("DISC_WIDE_ANY")) f |= DISC_SW_WIDE_ANY;
   if (env_on("DISC_SEPARATE_WARP")) f |= DISC_SW_SEPARATE_WARP;
+  if (env_on("DISC_FUSED_WARP")) f |= DISC_SW_FUSED_WARP;
   const char* fault = std::getenv("DISC_FAULT");
   if (fault != nullptr && fault[0] == 'a' && fault[1] == 'l' && fault[2] == 'l' && fault[3] == 'o' &&
       fault[4] == 'c' && fault[5] == '\0')

@@ -25,30 +25,52 @@ __global__ void __launch_bounds__(kWarpThreads) k_warp(const float* __restrict__
         warp_at(Im, x, y, z, ldg_in(r, g, 3 * N), ldg_in(r, N + g, 3 * N), ldg_in(r, 2 * N + g, 3 * N), nx, ny,
                 nz));
 }
-// Four x-consecutive voxels per thread (nx a multiple of 4, 16-byte aligned
-// buffers): the field is read and m written as 16-byte vectors, and the 32
-// gathers of a thread are independent, so more of them are in flight.
-constexpr int kWarp4Threads = 128;
-__global__ void __launch_bounds__(kWarp4Threads) k_warp4(const float* __restrict__ Im, const float* __restrict__ r,
-                                                         float* __restrict__ m, int nx, int ny, int nz,
-                                                         const int* stop) {
+// z-marching form: a thread owns one (x, y) column of a chunk of planes and
+// loads the field of plane z + kWarpAhead while it gathers I_m for plane z, so
+// that the field's trip to memory overlaps the gathers instead of preceding
+// them (the two are otherwise dependent round trips per voxel).  CTAs of 32 x 4
+// columns: a warp's field loads and m stores are coalesced rows, and its rows'
+// gathers share cache lines.
+constexpr int kWarpZX = 32, kWarpZY = 4, kWarpAhead = 2, kWarpZChunk = 16;
+__global__ void __launch_bounds__(kWarpZX * kWarpZY) k_warp_z(const float* __restrict__ Im, const float* __restrict__ r,
+                                                               float* __restrict__ m, int nx, int ny, int nz,
+                                                               const int* stop) {
   pdl_wait();
   pdl_release();
   if (stop != nullptr && *(volatile const int*)stop != 0) return;
-  const int x = 4 * (blockIdx.x * kWarp4Threads + threadIdx.x);
-  const int y = blockIdx.y, z = blockIdx.z;
-  if (x >= nx) return;
-  const long long N = (long long)nx * ny * nz;
-  const long long q = (((long long)z * ny + y) * nx + x) / 4;   // float4 index
-  const float4* r4 = reinterpret_cast<const float4*>(r);
-  const float4 rx = ldg_in(r4, q, 3 * (N / 4)), ry = ldg_in(r4, q + N / 4, 3 * (N / 4));
-  const float4 rz = ldg_in(r4, q + 2 * (N / 4), 3 * (N / 4));
-  float4 o;
-  o.x = warp_at(Im, x, y, z, rx.x, ry.x, rz.x, nx, ny, nz);
-  o.y = warp_at(Im, x + 1, y, z, rx.y, ry.y, rz.y, nx, ny, nz);
-  o.z = warp_at(Im, x + 2, y, z, rx.z, ry.z, rz.z, nx, ny, nz);
-  o.w = warp_at(Im, x + 3, y, z, rx.w, ry.w, rz.w, nx, ny, nz);
-  st_in(reinterpret_cast<float4*>(m), q, N / 4, o);
+  const int x = blockIdx.x * kWarpZX + threadIdx.x % kWarpZX;
+  const int y = blockIdx.y * kWarpZY + threadIdx.x / kWarpZX;
+  if (x >= nx || y >= ny) return;
+  const int z0 = blockIdx.z * kWarpZChunk, z1 = min(nz, z0 + kWarpZChunk);
+  const long long plane = (long long)nx * ny, N = plane * nz;
+  const long long col = (long long)y * nx + x;
+  float rq[kWarpAhead + 1][3];
+#pragma unroll
+  for (int k = 0; k < kWarpAhead; ++k) {
+    const int z = z0 + k;
+    if (z < z1) {
+      const long long g = z * plane + col;
+      rq[k][0] = ldcs_in(r, g, 3 * N);
+      rq[k][1] = ldcs_in(r, N + g, 3 * N);
+      rq[k][2] = ldcs_in(r, 2 * N + g, 3 * N);
+    }
+  }
+  for (int zb = z0; zb < z1; zb += kWarpAhead + 1) {
+#pragma unroll
+    for (int j = 0; j <= kWarpAhead; ++j) {   // slots rotate with z: the unrolled loop keeps them static
+      const int z = zb + j;
+      if (z >= z1) break;
+      const int zn = z + kWarpAhead;          // the plane whose field is loaded now
+      const int sn = (j + kWarpAhead) % (kWarpAhead + 1);
+      if (zn < z1) {
+        const long long g = zn * plane + col;
+        rq[sn][0] = ldcs_in(r, g, 3 * N);
+        rq[sn][1] = ldcs_in(r, N + g, 3 * N);
+        rq[sn][2] = ldcs_in(r, 2 * N + g, 3 * N);
+      }
+      st_in(m, z * plane + col, N, warp_at(Im, x, y, z, rq[j][0], rq[j][1], rq[j][2], nx, ny, nz));
+    }
+  }
 }
 }  // namespace
 
@@ -80,9 +102,9 @@ cudaError_t launch_warp_batch(const WarpBatch& wb, int total_blocks, cudaStream_
 cudaError_t launch_warp(const float* Im, const float* r, float* m, int nx, int ny, int nz, const int* stop,
                         cudaStream_t s) {
   if (ny > 65535 || nz > 65535) return cudaErrorInvalidConfiguration;
-  if (nx % 4 == 0 && (((uintptr_t)r | (uintptr_t)m) & 15u) == 0u) {
-    dim3 grid((nx / 4 + kWarp4Threads - 1) / kWarp4Threads, ny, nz);
-    return launch_pdl(k_warp4, grid, dim3(kWarp4Threads), 0, s, Im, r, m, nx, ny, nz, stop);
+  if (nx >= kWarpZX && nz >= kWarpZChunk) {
+    dim3 grid((nx + kWarpZX - 1) / kWarpZX, (ny + kWarpZY - 1) / kWarpZY, (nz + kWarpZChunk - 1) / kWarpZChunk);
+    return launch_pdl(k_warp_z, grid, dim3(kWarpZX * kWarpZY), 0, s, Im, r, m, nx, ny, nz, stop);
   }
   dim3 grid((nx + kWarpThreads - 1) / kWarpThreads, ny, nz);
   k_warp<<<grid, kWarpThreads, 0, s>>>(Im, r, m, nx, ny, nz, stop);

@@ -157,7 +157,7 @@ def bounds_violations(stream=None):
 
 
 SW_NO_TMA, SW_TMA_STALL, SW_NO_GRAPH, SW_UNROLLED_GRAPH, SW_FAULT_ALLOC, SW_WIDE_ANY = 1, 2, 4, 8, 16, 32
-SW_SEPARATE_WARP = 64
+SW_SEPARATE_WARP, SW_FUSED_WARP = 64, 128
 
 
 class test_switches:
@@ -450,11 +450,15 @@ class Batch:
                                           ctypes.byref(zmult)), "disc_batch_get_tuning")
         return int(items.value), int(grid.value), int(zmult.value)
 
-    def box_path_tma(self, level):
-        """True when `level`'s moment/force launch is the bulk-tensor-copy-fed kernel."""
+    def box_path(self, level):
+        """`level`'s moment/force kernel: 2 wide tiles, 1 bulk-copy-fed 32 x 16, 0 per-thread loads."""
         t = _i32(0)
         _check(_lib.disc_batch_get_box_path(self._h, int(level), ctypes.byref(t)), "disc_batch_get_box_path")
-        return bool(t.value)
+        return int(t.value)
+
+    def box_path_tma(self, level):
+        """True when `level`'s moment/force launch is the bulk-tensor-copy-fed 32 x 16 kernel."""
+        return self.box_path(level) == 1
 
     def pin_tuning(self, level, zmult, grid):
         """Use z chunking `zmult` and grid `grid` (0: one CTA per item) at `level` instead of the autotuner."""

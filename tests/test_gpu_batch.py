@@ -38,7 +38,7 @@ def test_batched_fields_equal_single_pair_runs(disc, pairs):
         got = [b.get_field(i) for i in range(len(pairs))]
         for lev in range(2):
             items, grid, zmult = b.tuning(lev)
-            assert 1 <= grid <= items and zmult in (1, 2, 4, -32, -64, -(1 << 20))
+            assert 1 <= grid <= items and zmult in (0, 1, 2, 4, -32, -64, -(1 << 20))
         # restart and run again in two calls: identical
         b.restart()
         assert b.iterate(5) + b.iterate(-1) == 16
@@ -105,6 +105,38 @@ def test_batched_tma_kernel_equals_single_pair_runs(disc, tma_pairs, tma_single,
         items, g, zm = b.tuning(0)
         assert zm == zmult and g == (items if grid == 0 else min(grid, items))
         assert grid == 0 or g < items              # persistent CTAs strode over several items
+        got = [b.get_field(i) for i in range(len(tma_pairs))]
+    for i in range(len(tma_pairs)):
+        np.testing.assert_array_equal(got[i], tma_single[i])
+
+
+@pytest.mark.parametrize("grid", [0, 7, 2])
+def test_batched_wide_kernel_equals_single_pair_runs(disc, tma_pairs, tma_single, grid):
+    """The wide-tile batched kernel at the finest level: one wave sharing every
+    pair's (tile, plane) pairs, or a few CTAs each marching planes of several
+    pairs in turn (their copy barriers' phases carried across pairs)."""
+    with disc.Batch(len(tma_pairs), **TMA_KW) as b:
+        for i, p in enumerate(tma_pairs):
+            b.set_images(i, p.ct, p.cbct)
+        b.pin_tuning(0, 0, grid)
+        b.pin_tuning(1, 1, 0)
+        assert b.iterate(-1) == 10
+        assert b.box_path(0) == 2 and b.box_path(1) in (0, 1)
+        items, g, zm = b.tuning(0)
+        assert zm == 0 and (grid == 0 or g == grid)
+        got = [b.get_field(i) for i in range(len(tma_pairs))]
+    for i in range(len(tma_pairs)):
+        np.testing.assert_array_equal(got[i], tma_single[i])
+
+
+def test_batched_tuner_picks_a_tiling(disc, tma_pairs, tma_single):
+    """Unpinned: the autotuner times the 32 x 16 tilings and the wide one and
+    keeps the fastest; the fields are the single-pair ones whatever it picks."""
+    with disc.Batch(len(tma_pairs), **TMA_KW) as b:
+        for i, p in enumerate(tma_pairs):
+            b.set_images(i, p.ct, p.cbct)
+        b.iterate(-1)
+        assert b.box_path(0) in (1, 2)            # every pair's finest level takes a bulk-copy kernel
         got = [b.get_field(i) for i in range(len(tma_pairs))]
     for i in range(len(tma_pairs)):
         np.testing.assert_array_equal(got[i], tma_single[i])

@@ -42,9 +42,15 @@ def _Wide():
 
 
 def _SeparateWarp():
-    """The next iteration's warp in a kernel of its own, after the Gaussian."""
+    """The next iteration's warp in a kernel of its own, after the Gaussian, at every level."""
     from paper_1204_6295_b300 import disc
     return disc.test_switches(disc.SW_SEPARATE_WARP)
+
+
+def _FusedWarp():
+    """The next iteration's warp inside the Gaussian z pass at every level."""
+    from paper_1204_6295_b300 import disc
+    return disc.test_switches(disc.SW_FUSED_WARP)
 
 
 CASES = [
@@ -141,7 +147,7 @@ def test_registration_bitwise(disc):
     shape = (32, 64, 64)
     ct, cbct, _ = _inputs(shape, 9, 11)
     fields = []
-    for form in ("tma", "plain", "wide", "separate_warp"):
+    for form in ("tma", "plain", "wide", "separate_warp", "fused_warp"):
         def run():
             reg = disc.Registration(patch=(9, 9, 9), sigma=1.0, levels=2, iters=(6, 5))
             reg.set_images(dev(ct), dev(cbct))
@@ -149,7 +155,7 @@ def test_registration_bitwise(disc):
             out = empty(3, *shape)
             reg.get_field(out)
             return host(out)
-        ctx = {"plain": _NoTma, "wide": _Wide, "separate_warp": _SeparateWarp}.get(form)
+        ctx = {"plain": _NoTma, "wide": _Wide, "separate_warp": _SeparateWarp, "fused_warp": _FusedWarp}.get(form)
         if ctx:
             with ctx():
                 fields.append(run())
