@@ -242,6 +242,17 @@ disc_status disc_get_mask_constants(disc_ctx* ctx, float* hu0, float* a_m);
 disc_status disc_get_metrics(disc_ctx* ctx, int32_t bins, float sigma, float t_low, float t_high,
                              double* nmi, double* rmse_edge);
 
+/* The averages of the correction coefficients (Sec. 3.4 shows their maps and
+ * their averages over the iterations): for the current field at the current
+ * level, a = STD(M)/STD(S) and b = E(M) - a E(S) of Eqs. 5-6 (with the mask on,
+ * after the mask and fill of Eqs. 7-10, as the next iteration would use them),
+ * averaged over the voxels where they are defined (STD(S) > 0; with the mask,
+ * the voxels known or filled).  Host outputs (any may be NULL; not all); NaN
+ * means when no voxel qualifies.  Synchronises; the registration's state is
+ * unchanged.  A caller logs the averages per iteration by iterating one step
+ * at a time. */
+disc_status disc_get_correction_means(disc_ctx* ctx, double* mean_a, double* mean_b, int64_t* count);
+
 /* Release every resource of the context.  NULL is accepted. */
 disc_status disc_destroy(disc_ctx* ctx);
 

@@ -377,15 +377,26 @@ cudaError_t queue_iterations(disc_ctx* c, int l, int n, const LoopCond* loop) {
   }
   if (c->p.mask_mode) return queue_masked(c, l, n, g, st);
   for (int k = 0; k < n; ++k) {
-    cudaError_t e = box_launch(kModeIterate, a, v.pa, c->s);
+    cudaError_t e;
+    {
+      NvtxRange r("disc moments, correction, force");
+      e = box_launch(kModeIterate, a, v.pa, c->s);
+    }
     if (e != cudaSuccess) return e;
-    e = gauss_launch(g, v.pb, c->s);
+    {
+      NvtxRange r("disc Gaussian");
+      e = gauss_launch(g, v.pb, c->s);
+    }
     if (e != cudaSuccess) return e;
     if (v.sep_warp) {
+      NvtxRange r("disc warp");
       e = launch_warp(v.Im, v.r, v.m, v.nx, v.ny, v.nz, c->d_stop + l, c->s);
       if (e != cudaSuccess) return e;
     }
-    e = launch_norm_finalize(c->partials, nparts, st, c->s);
+    {
+      NvtxRange r("disc norm");
+      e = launch_norm_finalize(c->partials, nparts, st, c->s);
+    }
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -462,6 +473,9 @@ cudaError_t build_loop_graph(disc_ctx* c, int l) {
 cudaError_t run_iterations(disc_ctx* c, int l, int n) {
   if (n <= 0) return cudaSuccess;
   Level& v = c->lev[l];
+  char name[64];
+  std::snprintf(name, sizeof(name), "disc level %d: %d iterations", l, n);
+  NvtxRange range(name);
   if (!c->use_graphs) {
     c->launches = -1;                      // stream launches are not counted
     return queue_iterations(c, l, n, nullptr);
@@ -697,6 +711,7 @@ disc_status disc_destroy(disc_ctx* ctx) {
 
 disc_status disc_set_images(disc_ctx* ctx, const float* ct, const float* cbct, int32_t nx, int32_t ny,
                             int32_t nz, int mem_kind) {
+  NvtxRange nvtx_range("disc_set_images");
   if (!ctx || !ct || !cbct) return DISC_ERR_ARG;
   if (mem_kind != DISC_MEM_HOST && mem_kind != DISC_MEM_DEVICE) return DISC_ERR_ARG;
   if (ctx->sticky != DISC_OK) return DISC_ERR_STATE;
@@ -882,6 +897,7 @@ disc_status disc_set_images(disc_ctx* ctx, const float* ct, const float* cbct, i
 }
 
 disc_status disc_iterate(disc_ctx* ctx, int32_t max_iters, int32_t* iters_done, float* last_l) {
+  NvtxRange nvtx_range("disc_iterate");
   if (!ctx) return DISC_ERR_ARG;
   if (ctx->sticky != DISC_OK) return DISC_ERR_STATE;
   if (!ctx->have_images) return DISC_ERR_STATE;
@@ -950,6 +966,7 @@ disc_status disc_iterate(disc_ctx* ctx, int32_t max_iters, int32_t* iters_done, 
 }
 
 disc_status disc_get_field(disc_ctx* ctx, float* out, int mem_kind) {
+  NvtxRange nvtx_range("disc_get_field");
   if (!ctx || !out) return DISC_ERR_ARG;
   if (mem_kind != DISC_MEM_HOST && mem_kind != DISC_MEM_DEVICE) return DISC_ERR_ARG;
   if (ctx->sticky != DISC_OK) return DISC_ERR_STATE;
@@ -996,6 +1013,78 @@ cudaError_t corrected_into_u(disc_ctx* ctx) {
 }  // namespace
 
 extern "C" {
+
+disc_status disc_get_correction_means(disc_ctx* ctx, double* mean_a, double* mean_b, int64_t* count) {
+  if (!ctx || (!mean_a && !mean_b && !count)) return DISC_ERR_ARG;
+  if (ctx->sticky != DISC_OK) return DISC_ERR_STATE;
+  if (!ctx->have_images) return DISC_ERR_STATE;
+  DeviceGuard guard(ctx->device);
+  if (!guard.ok) return DISC_ERR_CUDA;
+  NvtxRange nvtx_range("disc_get_correction_means");
+  CK(enter(ctx));
+  Level& v = ctx->lev[ctx->cur_level];
+  CK(launch_warp(v.Im, v.r, v.m, v.nx, v.ny, v.nz, nullptr, ctx->s));
+  double* sums = nullptr;                     // sum a, sum b, count
+  CK(cudaMallocAsync(&sums, 3 * sizeof(double), ctx->s));
+  cudaError_t e = cudaSuccess;
+  float* tmp = nullptr;
+  if (ctx->p.mask_mode) {
+    // the masked correction as an iteration computes it: a, b after the fill
+    e = queue_mask_fill(ctx, ctx->cur_level, nullptr);
+    if (e == cudaSuccess) e = launch_ab_sums(v.isab, v.stamp, (int64_t)v.N, sums, ctx->s);
+  } else {
+    // Eqs. 5-6 where a is defined: STD(S) of the level, then the mask pass with
+    // thresholds that mask nothing but the voxels without STD(S)
+    e = cudaMallocAsync(&tmp, v.N * (sizeof(float4) + 3 * sizeof(float) + sizeof(int)) + 64, ctx->s);
+    float4* isab = reinterpret_cast<float4*>(tmp);
+    float* sd = reinterpret_cast<float*>(isab + v.N);
+    float* zs = sd + v.N;
+    float* d = zs + v.N;
+    int* stamp = reinterpret_cast<int*>(d + v.N);
+    int* cnt = stamp + v.N;
+    if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(int), ctx->s);
+    BoxArgs a = box_args(ctx, v);
+    a.src = v.Is;
+    a.out = zs;
+    a.sd_out = sd;
+    a.qscale = ctx->qs_s;
+    a.inv_qscale = 1.0f / ctx->qs_s;
+    const BoxPlan ps = box_plan(kModeStatic, v.nx, v.ny, v.nz, ctx->hx, ctx->hy, ctx->hz, ctx->num_sms);
+    if (e == cudaSuccess) e = box_launch(kModeStatic, a, ps, ctx->s);
+    BoxArgs b = box_args(ctx, v);
+    b.src = v.m;
+    b.zs = zs;
+    b.is = v.Is;
+    b.sd = sd;
+    b.out = d;
+    b.isab = isab;
+    b.stamp = stamp;
+    b.count = cnt;
+    b.hu0 = INFINITY;
+    b.a_min = 0.0f;
+    b.a_max = INFINITY;
+    b.qscale = ctx->qs_m;
+    b.inv_qscale = 1.0f / ctx->qs_m;
+    const BoxPlan pm = box_plan(kModeMaskAB, v.nx, v.ny, v.nz, ctx->hx, ctx->hy, ctx->hz, ctx->num_sms);
+    if (e == cudaSuccess) e = box_launch(kModeMaskAB, b, pm, ctx->s);
+    if (e == cudaSuccess) e = launch_ab_sums(isab, stamp, (int64_t)v.N, sums, ctx->s);
+  }
+  double h[3] = {0.0, 0.0, 0.0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, ctx->s);
+  if (tmp) {
+    const cudaError_t ef = cudaFreeAsync(tmp, ctx->s);
+    if (e == cudaSuccess) e = ef;
+  }
+  const cudaError_t ef = cudaFreeAsync(sums, ctx->s);
+  if (e == cudaSuccess) e = ef;
+  CK(e);
+  CK_DEV(ctx);                                // synchronises
+  if (mean_a) *mean_a = h[2] > 0.0 ? h[0] / h[2] : NAN;
+  if (mean_b) *mean_b = h[2] > 0.0 ? h[1] / h[2] : NAN;
+  if (count) *count = (int64_t)h[2];
+  CK(leave(ctx));
+  return DISC_OK;
+}
 
 disc_status disc_get_corrected(disc_ctx* ctx, float* out, int mem_kind) {
   if (!ctx || !out) return DISC_ERR_ARG;

@@ -505,6 +505,7 @@ disc_status disc_batch_restart(disc_batch* b) {
 }
 
 disc_status disc_batch_iterate(disc_batch* b, int32_t max_iters, int32_t* iters_done) {
+  NvtxRange nvtx_range("disc_batch_iterate");
   if (!b) return DISC_ERR_ARG;
   if (b->sticky != DISC_OK) return DISC_ERR_STATE;
   if (!all_images(b)) return DISC_ERR_STATE;

@@ -2,9 +2,21 @@
 // single-pair API (api.cu) and the batched API (batch.cu).
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.cuh"
 
 namespace disc {
+
+// NVTX range for the profilers' timelines (header-only NVTX 3: a no-op unless a
+// tool is attached).  The library marks its calls, each level's iterations and,
+// when kernels are launched one by one (no graph replay), each pass.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct DeviceGuard {
   int prev = -1;

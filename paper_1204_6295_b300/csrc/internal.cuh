@@ -290,6 +290,8 @@ cudaError_t launch_fill_pass(const FillArgs& f, cudaStream_t s);
 // passes) set to run them unless the level has stopped, nothing is masked
 // (cnt[0] = 0) or passes = 0.
 cudaError_t launch_fill_loop_start(const FillArgs& f, cudaStream_t s);
+// out[0..2] = sum of a, sum of b and the number of voxels with stamp >= 0.
+cudaError_t launch_ab_sums(const float4* isab, const int* stamp, int64_t n, double* out, cudaStream_t s);
 // a, b out of the interleaved fill buffer into planar arrays.
 cudaError_t launch_unpack_ab(const float4* isab, float* a, float* b, int64_t n, cudaStream_t s);
 int fill_words(int nx, int ny, int nz);

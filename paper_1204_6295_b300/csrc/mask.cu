@@ -427,6 +427,48 @@ __global__ void k_unpack_ab(const float4* __restrict__ isab, float* __restrict__
   }
 }
 
+// Sums of a and b (Eqs. 5-6, after the fill) over the voxels whose stamp is at
+// least 0 (known or filled), and their count, into out[0..2] (one CTA, fixed
+// order): the averages of Sec. 3.4.
+__global__ void k_ab_sums(const float4* __restrict__ isab, const int* __restrict__ stamp, long long n,
+                          double* out) {
+  __shared__ double sh[3][8];
+  double sa = 0.0, sb = 0.0, c = 0.0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+    if (stamp[i] >= 0) {
+      const float4 v = isab[i];
+      sa += (double)v.y;
+      sb += (double)v.z;
+      c += 1.0;
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    sa += __shfl_down_sync(0xffffffffu, sa, off);
+    sb += __shfl_down_sync(0xffffffffu, sb, off);
+    c += __shfl_down_sync(0xffffffffu, c, off);
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    sh[0][w] = sa;
+    sh[1][w] = sb;
+    sh[2][w] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < (int)(blockDim.x / 32); ++k)
+      for (int j = 0; j < 3; ++j) t[j] += sh[j][k];
+    out[0] = t[0];
+    out[1] = t[1];
+    out[2] = t[2];
+  }
+}
+
+cudaError_t launch_ab_sums(const float4* isab, const int* stamp, int64_t n, double* out, cudaStream_t s) {
+  k_ab_sums<<<1, 256, 0, s>>>(isab, stamp, (long long)n, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_unpack_ab(const float4* isab, float* a, float* b, int64_t n, cudaStream_t s) {
   long long blocks = (n + 255) / 256;
   if (blocks > 148 * 8) blocks = 148 * 8;

@@ -84,6 +84,8 @@ _SIGS = {
     "disc_get_norm_sums": (_st, [_vp, _i32, _vp, _i32, ctypes.POINTER(_i32)]),
     "disc_get_launch_count": (_st, [_vp, ctypes.POINTER(_i64)]),
     "disc_ssd": (_st, [_vp, _i32, _vp, ctypes.POINTER(ctypes.c_double), _vp, ctypes.c_int]),
+    "disc_get_correction_means": (_st, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(_i64)]),
     "disc_norm_stop_rule": (_st, [_vp, _i32, _i32, _f32, _vp, ctypes.POINTER(_i32)]),
     "disc_destroy": (_st, [_vp]),
     "disc_qscale": (_f32, [_f32, ctypes.POINTER(_i32)]),
@@ -373,6 +375,13 @@ class Registration:
         _check(_lib.disc_ssd(self._h, int(level), _ptr(r), ctypes.byref(loss),
                              _ptr(grad) if grad is not None else None, kind), "disc_ssd")
         return loss.value
+
+    def correction_means(self):
+        """(mean a, mean b, voxels) of Eqs. 5-6 for the current field and level (disc_get_correction_means)."""
+        ma, mb, n = ctypes.c_double(0.0), ctypes.c_double(0.0), _i64(0)
+        _check(_lib.disc_get_correction_means(self._h, ctypes.byref(ma), ctypes.byref(mb), ctypes.byref(n)),
+               "disc_get_correction_means")
+        return ma.value, mb.value, int(n.value)
 
     def launch_count(self):
         """Kernel launches disc_iterate has issued on this context (disc_get_launch_count)."""
