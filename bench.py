@@ -484,6 +484,8 @@ def time_batched(disc, torch, dist, steps=2):
 
     t_batch = timed(batch_step)
     tuning = [batch.tuning(l) for l in range(bw["levels"])]
+    gauss_tuning = [batch.gauss_tuning(l) for l in range(bw["levels"])]
+    box_paths = [batch.box_path(l) for l in range(bw["levels"])]
     batch.close()
     regs = []
     for ct, cbct in images:
@@ -509,6 +511,8 @@ def time_batched(disc, torch, dist, steps=2):
             "pairs_per_rank": [len(x) for x in share],
             "max_over_mean_rank_load": max(shard.rank_loads(loads, share)) * world / units,
             "tuning_items_grid_zmult_per_level_fine_first": tuning,
+            "box_path_per_level_fine_first": box_paths,
+            "gauss_zlen_separate_warp_per_level_fine_first": gauss_tuning,
             "what": "16 head-and-neck pairs (2s, 2s, s) per rank, s in 64..160, patch 9^3, "
                     "sigma 1.5, 3 levels x 100 iterations, pairs sharded across ranks by the "
                     "longest-processing-time rule (no exchange): disc_batch (one launch per step "
@@ -889,6 +893,23 @@ def run_profile_once(w):
     return 0
 
 
+def run_profile_schedule(w):
+    """One whole schedule of the workload from a zero field (for launch lists):
+    set-up, then every level's iterations as the timed steps run them."""
+    import torch
+    from paper_1204_6295_b300 import disc
+    pair = make_pair(w)
+    ct = torch.from_numpy(pair.ct).cuda()
+    cbct = torch.from_numpy(pair.cbct).cuda()
+    with disc.Registration(patch=w["patch"], sigma=w["sigma"], levels=w["levels"], iters=w["iters"]) as reg:
+        reg.set_images(ct, cbct)
+        reg.iterate(-1, sync=False)
+        torch.cuda.synchronize()
+        launches = reg.launch_count()
+    print(json.dumps({"profile_schedule": True, "workload": list(w["dims"]), "launches": launches}))
+    return 0
+
+
 def run_profile_masked(w, iters=2):
     """`iters` masked iterations (Eqs. 7-10) at the finest level only, from r = 0
     (for ncu captures of the fill passes): one context with one level."""
@@ -919,6 +940,8 @@ def main():
                          "split into z slabs over the ranks (strong scaling)")
     ap.add_argument("--profile-once", action="store_true",
                     help="launch each per-iteration kernel once at the finest level and exit")
+    ap.add_argument("--profile-schedule", action="store_true",
+                    help="run one whole schedule of the workload and exit")
     ap.add_argument("--profile-masked", type=int, default=0, metavar="K",
                     help="run K masked iterations at the finest level and exit")
     args = ap.parse_args()
@@ -930,6 +953,8 @@ def main():
     w = WORKLOADS[args.workload]
     if args.profile_once:
         return run_profile_once(w)
+    if args.profile_schedule:
+        return run_profile_schedule(w)
     if args.profile_masked > 0:
         return run_profile_masked(w, args.profile_masked)
     if args.impl == "reference":

@@ -264,7 +264,12 @@ disc_status disc_destroy(disc_ctx* ctx);
  * pair's tiles, a level's iterations are one CUDA graph, and the tile
  * scheduling of the moment/force launch is tuned per level at first use.
  * All pairs share the parameters and the schedule.  Cubic patches of 3..15
- * voxels, Gaussian radius 1..8 and mask_mode 0 only (DISC_ERR_ARG otherwise).
+ * voxels and Gaussian radius 1..8 only (DISC_ERR_ARG otherwise).
+ * With mask_mode 1 (Eqs. 7-10) the number of fill passes differs per pair and
+ * iteration, so the pairs run their own single-pair schedules concurrently on
+ * their own streams, forked from and joined to the batch's stream in each
+ * disc_batch_iterate call (bit-identical to separate runs as well); the tuning
+ * getters then return DISC_ERR_STATE.
  * ------------------------------------------------------------------- */
 typedef struct disc_batch disc_batch;
 
@@ -309,6 +314,20 @@ disc_status disc_batch_get_tuning(disc_batch* b, int32_t level, int32_t* items, 
  * kernel against the 32 x 16 tilings and keeps the fastest.  DISC_ERR_STATE
  * before the level has run. */
 disc_status disc_batch_get_box_path(disc_batch* b, int32_t level, int32_t* tma);
+
+/* Tuning of `level`'s Gaussian z pass and warp (Algorithm A1 step 6 and the
+ * warp of step 1 for the next iteration): *zlen = the z chunk length of the
+ * z pass (0: each pair's single-pair plan; else chunks of that many planes,
+ * capped at each pair's depth) and *separate_warp = 1 when the warp runs as
+ * the z-marching warp kernel after the z pass, 0 when it runs inside it.  At
+ * the level's first iteration the tuner times the xy and z passes (and the
+ * warp) on scratch copies of r and m for chunks of the pairs' plans, 16, 32
+ * and 64 planes, with either placement, and keeps the default (fused, the
+ * plans) unless a choice is at least 2% faster.  Bitwise neutral: every output
+ * is the same sum in the same order either way.  Either output may be NULL.
+ * DISC_ERR_STATE before the level has run (and always with mask_mode 1). */
+disc_status disc_batch_get_gauss_tuning(disc_batch* b, int32_t level, int32_t* zlen,
+                                        int32_t* separate_warp);
 
 /* Pin the tuning of `level` instead of letting the autotuner time it.  zmult
  * non-zero: the 32 x 16 tilings with z chunking `zmult` (as

@@ -594,6 +594,44 @@ NormState ctx_norm_state(const disc_ctx* c, int l) {
   return NormState{v.hist, v.hsum, c->d_iter + l, c->d_stop + l, v.hist_cap, c->p.stop_window, c->p.stop_eps};
 }
 
+// Queue up to `budget` iterations of the schedule on ctx->s, from the
+// context's current level and iteration (finished levels are up-sampled).
+cudaError_t ctx_advance(disc_ctx* ctx, long long budget, int* touched, int* ntouched, long long* queued) {
+  const int L = ctx->L;
+  int nt = 0;
+  long long q = 0;
+  while (true) {
+    const int l = ctx->cur_level;
+    const int total = ctx->p.iters[L - 1 - l];
+    const int left = total - ctx->cur_iter;
+    if (left > 0 && budget > 0) {
+      const int n = (int)(left < budget ? left : budget);
+      const cudaError_t e = run_iterations(ctx, l, n);
+      if (e != cudaSuccess) return e;
+      if (touched && (nt == 0 || touched[nt - 1] != l)) touched[nt++] = l;
+      ctx->cur_iter += n;
+      budget -= n;
+      q += n;
+    }
+    if (ctx->cur_iter >= total && l > 0) {
+      // level finished: up-sample the field to the next finer level (Algorithm A1)
+      const Level& fine = ctx->lev[l - 1];
+      cudaError_t e = launch_up2(ctx->lev[l].r, fine.r, fine.nx, fine.ny, fine.nz, ctx->s);
+      if (e != cudaSuccess) return e;
+      if (ctx->launches >= 0) ctx->launches += 1;
+      e = reset_level_counters(ctx, l - 1);
+      if (e != cudaSuccess) return e;
+      ctx->cur_level = l - 1;
+      ctx->cur_iter = 0;
+      continue;
+    }
+    break;
+  }
+  if (ntouched) *ntouched = nt;
+  if (queued) *queued = q;
+  return cudaSuccess;
+}
+
 }  // namespace disc
 
 // ============================================================================
@@ -904,7 +942,6 @@ disc_status disc_iterate(disc_ctx* ctx, int32_t max_iters, int32_t* iters_done, 
   DeviceGuard guard(ctx->device);
   if (!guard.ok) return DISC_ERR_CUDA;
   CK(enter(ctx));
-  const int L = ctx->L;
   const int l_start = ctx->cur_level;
   long long budget = max_iters < 0 ? (1LL << 40) : max_iters;
   int touched[DISC_MAX_LEVELS];
@@ -915,29 +952,7 @@ disc_status disc_iterate(disc_ctx* ctx, int32_t max_iters, int32_t* iters_done, 
     CK(cudaMemcpyAsync(before, ctx->d_iter, sizeof(int) * DISC_MAX_LEVELS, cudaMemcpyDeviceToHost, ctx->s));
     CK(cudaStreamSynchronize(ctx->s));
   }
-  while (true) {
-    const int l = ctx->cur_level;
-    const int total = ctx->p.iters[L - 1 - l];
-    const int left = total - ctx->cur_iter;
-    if (left > 0 && budget > 0) {
-      const int n = (int)(left < budget ? left : budget);
-      CK(run_iterations(ctx, l, n));
-      if (ntouched == 0 || touched[ntouched - 1] != l) touched[ntouched++] = l;
-      ctx->cur_iter += n;
-      budget -= n;
-    }
-    if (ctx->cur_iter >= total && l > 0) {
-      // level finished: up-sample the field to the next finer level (Algorithm A1)
-      const Level& fine = ctx->lev[l - 1];
-      CK(launch_up2(ctx->lev[l].r, fine.r, fine.nx, fine.ny, fine.nz, ctx->s));
-      if (ctx->launches >= 0) ctx->launches += 1;
-      CK(reset_level_counters(ctx, l - 1));
-      ctx->cur_level = l - 1;
-      ctx->cur_iter = 0;
-      continue;
-    }
-    break;
-  }
+  CK(ctx_advance(ctx, budget, touched, &ntouched, nullptr));
   if (need_counts) {
     int after[DISC_MAX_LEVELS] = {0};
     CK(cudaMemcpyAsync(after, ctx->d_iter, sizeof(int) * DISC_MAX_LEVELS, cudaMemcpyDeviceToHost, ctx->s));

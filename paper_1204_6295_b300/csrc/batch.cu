@@ -12,7 +12,8 @@
 // bulk-tensor-copy conditions, the moment/force launch is the TMA-fed kernel,
 // with each pair's four tensor maps in device memory.  Per pair the arithmetic
 // is the one of the single-pair path, so each pair's field is bit-identical to
-// a separate run.
+// a separate run.  With the mask of Eqs. 7-10 on, the pairs instead run their
+// own single-pair schedules concurrently on their own streams (run_masked_batch).
 
 #include <cstring>
 #include <new>
@@ -38,6 +39,13 @@ struct disc_batch {
   WarpBatch warp[DISC_MAX_LEVELS];
   int box_total[DISC_MAX_LEVELS] = {}, box_grid[DISC_MAX_LEVELS] = {}, zmult[DISC_MAX_LEVELS] = {};
   int xy_total[DISC_MAX_LEVELS] = {}, z_total[DISC_MAX_LEVELS] = {}, warp_total[DISC_MAX_LEVELS] = {};
+  // the Gaussian z pass and the warp of the next iteration, tuned per level:
+  // z chunk length (0: each pair's single-pair plan) and whether the warp runs
+  // in the z pass or as the z-marching warp kernel after it (table warpz)
+  int gauss_zlen[DISC_MAX_LEVELS] = {};
+  bool sep_warp[DISC_MAX_LEVELS] = {};
+  WarpBatch warpz[DISC_MAX_LEVELS];
+  int warpz_total[DISC_MAX_LEVELS] = {};
   bool ready[DISC_MAX_LEVELS] = {};
   // bulk-tensor-copy box pass at level l (every pair eligible): tensor maps of
   // all pairs in device memory, 4 per pair
@@ -212,6 +220,59 @@ void make_wide_norm_table(disc_batch* b, int l, int grid) {
   }
 }
 
+// Gaussian z-pass table of level l with chunks of `zlen` planes (0: each
+// pair's single-pair plan), writing r and m to the given buffers (per pair;
+// NULL: the pair's own).
+int make_z_table(disc_batch* b, int l, int zlen, GaussBatch& z, float* const* r_to, float* const* m_to) {
+  std::memset(&z, 0, sizeof(z));
+  z.count = b->npairs;
+  int oz = 0;
+  for (int i = 0; i < b->npairs; ++i) {
+    const disc_ctx* c = b->pair[i];
+    const Level& v = c->lev[l];
+    GaussArgs g = ctx_gauss_args(c, l);
+    g.u = g.t;                   // z pass: t -> r (and m)
+    if (zlen > 0) g.zlen = zlen < v.nz ? zlen : v.nz;
+    if (r_to) {
+      g.r = r_to[i];
+      if (g.add) g.add = r_to[i];
+    }
+    if (m_to) g.m = m_to[i];
+    z.args[i] = g;
+    GaussPlan pl = v.pb;
+    pl.zlen = g.zlen;
+    dim3 gxy;
+    gauss_grids(v.nx, v.ny, v.nz, pl, &gxy, &z.grid[i]);
+    z.offset[i] = oz;
+    oz += (int)(z.grid[i].x * z.grid[i].y * z.grid[i].z);
+  }
+  z.offset[b->npairs] = oz;
+  return oz;
+}
+
+// Batched z-marching warp table of level l (m from the given r per pair; NULL:
+// the pair's own buffers).
+int make_warpz_table(disc_batch* b, int l, WarpBatch& w, float* const* r_from, float* const* m_to) {
+  std::memset(&w, 0, sizeof(w));
+  w.count = b->npairs;
+  int ow = 0;
+  for (int i = 0; i < b->npairs; ++i) {
+    const disc_ctx* c = b->pair[i];
+    const Level& v = c->lev[l];
+    w.offset[i] = ow;
+    w.Im[i] = v.Im;
+    w.r[i] = r_from ? r_from[i] : v.r;
+    w.m[i] = m_to ? m_to[i] : v.m;
+    w.nx[i] = v.nx;
+    w.ny[i] = v.ny;
+    w.nz[i] = v.nz;
+    w.stop[i] = c->d_stop + l;
+    ow += warp_z_blocks(v.nx, v.ny, v.nz);
+  }
+  w.offset[b->npairs] = ow;
+  return ow;
+}
+
 void build_tables(disc_batch* b, int l) {
   GaussBatch& xy = b->xy[l];
   GaussBatch& z = b->zt[l];
@@ -253,6 +314,86 @@ void build_tables(disc_batch* b, int l) {
   b->xy_total[l] = oxy;
   b->z_total[l] = oz;
   b->warp_total[l] = ow;
+  b->gauss_zlen[l] = 0;
+  b->sep_warp[l] = false;
+  b->warpz_total[l] = make_warpz_table(b, l, b->warpz[l], nullptr, nullptr);
+}
+
+// Tuner of the Gaussian z pass and the warp placement at level l: the xy pass
+// and the z pass (with the warp fused, or followed by the z-marching warp
+// kernel) for z chunks of each pair's plan, 16, 32 and 64 planes, timed on
+// scratch copies of r and m so that the level's state is untouched (the xy
+// pass writes only t, which every iteration overwrites).  The default (fused,
+// the pairs' plans) is replaced only by a choice at least 2% faster.  The test
+// switches DISC_SW_SEPARATE_WARP / DISC_SW_FUSED_WARP fix the placement.
+cudaError_t tune_gauss(disc_batch* b, int l) {
+  size_t total = 0;
+  for (int i = 0; i < b->npairs; ++i) total += 4 * b->pair[i]->lev[l].N;
+  float* scratch = nullptr;
+  cudaError_t e = cudaMallocAsync(&scratch, total * sizeof(float), b->s);
+  if (e != cudaSuccess) return e;
+  float* r_to[kMaxBatch];
+  float* m_to[kMaxBatch];
+  size_t off = 0;
+  for (int i = 0; i < b->npairs; ++i) {
+    const size_t N = b->pair[i]->lev[l].N;
+    r_to[i] = scratch + off;
+    m_to[i] = scratch + off + 3 * N;
+    off += 4 * N;
+  }
+  e = cudaMemsetAsync(scratch, 0, total * sizeof(float), b->s);
+  const uint32_t sw = test_switches();
+  const int place_lo = (sw & DISC_SW_SEPARATE_WARP) ? 1 : 0;
+  const int place_hi = (sw & DISC_SW_FUSED_WARP) ? 0 : 1;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  GaussBatch* zt_p = new (std::nothrow) GaussBatch;
+  WarpBatch* wt_p = new (std::nothrow) WarpBatch;
+  if (e == cudaSuccess && (!zt_p || !wt_p)) e = cudaErrorMemoryAllocation;
+  GaussBatch& zt = *zt_p;
+  WarpBatch& wt = *wt_p;
+  const int zlens[4] = {0, 16, 32, 64};
+  float best = 1e30f, deflt = 1e30f;
+  int best_zlen = 0, best_sep = place_lo;
+  for (int place = place_lo; place <= place_hi && e == cudaSuccess; ++place) {
+    const int wtot = make_warpz_table(b, l, wt, r_to, m_to);
+    for (int zi = 0; zi < 4 && e == cudaSuccess; ++zi) {
+      const int ztot = make_z_table(b, l, zlens[zi], zt, r_to, m_to);
+      float ms = 0.0f;
+      for (int k = 0; k < 4 && e == cudaSuccess; ++k) {   // one warm-up, three timed
+        if (k == 1) e = cudaEventRecord(e0, b->s);
+        if (e == cudaSuccess)
+          e = gauss_launch_batch(b->xy[l], b->xy_total[l], zt, ztot, b->R, place == 0, b->s);
+        if (e == cudaSuccess && place == 1) e = launch_warp_z_batch(wt, wtot, b->s);
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(e1, b->s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) break;
+      if (place == place_lo && zi == 0) deflt = ms;
+      if (ms < best) {
+        best = ms;
+        best_zlen = zlens[zi];
+        best_sep = place;
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  delete zt_p;
+  delete wt_p;
+  const cudaError_t ef = cudaFreeAsync(scratch, b->s);
+  if (e == cudaSuccess) e = ef;
+  if (e != cudaSuccess) return e;
+  if (!(best < 0.98f * deflt)) {
+    best_zlen = 0;
+    best_sep = place_lo;
+  }
+  b->gauss_zlen[l] = best_zlen;
+  b->sep_warp[l] = best_sep != 0;
+  b->z_total[l] = make_z_table(b, l, best_zlen, b->zt[l], nullptr, nullptr);
+  return cudaSuccess;
 }
 
 size_t box_smem(const disc_batch* b, int l) {
@@ -375,10 +516,35 @@ cudaError_t queue_batch_iterations(disc_batch* b, int l, int n) {
   for (int k = 0; k < n && e == cudaSuccess; ++k) {
     e = launch_box(b, l, b->box_total[l], b->box_grid[l]);
     if (e == cudaSuccess)
-      e = gauss_launch_batch(b->xy[l], b->xy_total[l], b->zt[l], b->z_total[l], b->R, true, b->s);
+      e = gauss_launch_batch(b->xy[l], b->xy_total[l], b->zt[l], b->z_total[l], b->R, !b->sep_warp[l], b->s);
+    if (e == cudaSuccess && b->sep_warp[l]) e = launch_warp_z_batch(b->warpz[l], b->warpz_total[l], b->s);
     if (e == cudaSuccess) e = launch_norm_finalize_batch(b->norm[l], b->npairs, b->s);
   }
   return e;
+}
+
+// The masked batch (Eqs. 7-10 on): the mask-and-fill step has a data-dependent
+// number of fill passes per pair, which a shared work table cannot carry, so
+// each pair runs its own single-pair schedule (captured graphs, the fill loop
+// as a conditional node) on its own stream, and the pairs' streams run
+// concurrently between one fork and one join on the batch stream.
+cudaError_t run_masked_batch(disc_batch* b, long long budget, long long* queued) {
+  cudaError_t e = cudaEventRecord(b->ev_in, b->s);
+  long long q = 0;
+  for (int i = 0; i < b->npairs && e == cudaSuccess; ++i) {
+    disc_ctx* c = b->pair[i];
+    e = cudaStreamWaitEvent(c->s, b->ev_in, 0);
+    long long qi = 0;
+    if (e == cudaSuccess) e = ctx_advance(c, budget, nullptr, nullptr, &qi);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_out, c->s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->s, c->ev_out, 0);
+    q = qi;                                   // the same schedule for every pair
+  }
+  if (e != cudaSuccess) return e;
+  b->cur_level = b->pair[0]->cur_level;
+  b->cur_iter = b->pair[0]->cur_iter;
+  *queued = q;
+  return cudaSuccess;
 }
 
 cudaError_t run_batch_iterations(disc_batch* b, int l, int n) {
@@ -423,7 +589,6 @@ disc_status disc_batch_create(const disc_params* p, int device, void* cuda_strea
       p->patch[0] % 2 == 0)
     return DISC_ERR_ARG;
   if (p->levels < 1 || p->levels > DISC_MAX_LEVELS || !(p->gauss_sigma > 0.0f)) return DISC_ERR_ARG;
-  if (p->mask_mode != 0) return DISC_ERR_ARG;   // the batched tables carry the unmasked pass only
   const int R = gauss_radius(p->gauss_sigma, p->gauss_radius);
   if (R < 1 || R > 8) return DISC_ERR_ARG;
   disc_batch* b = new (std::nothrow) disc_batch();
@@ -513,6 +678,13 @@ disc_status disc_batch_iterate(disc_batch* b, int32_t max_iters, int32_t* iters_
   BCK(benter(b));
   long long budget = max_iters < 0 ? (1LL << 40) : max_iters;
   int done = 0;
+  if (b->p.mask_mode) {
+    long long q = 0;
+    BCK(run_masked_batch(b, budget, &q));
+    if (iters_done) *iters_done = (int32_t)q;
+    BCK(bleave(b));
+    return DISC_OK;
+  }
   while (true) {
     const int l = b->cur_level;
     const int total = b->p.iters[b->L - 1 - l];
@@ -524,6 +696,7 @@ disc_status disc_batch_iterate(disc_batch* b, int32_t max_iters, int32_t* iters_
         build_tables(b, l);
         BCK(launch_warp_batch(b->warp[l], b->warp_total[l], b->s));     // m for the tuning launches
         BCK(tune_level(b, l));
+        BCK(tune_gauss(b, l));
         b->ready[l] = true;
       }
       const int n = (int)(left < budget ? left : budget);
@@ -578,6 +751,14 @@ disc_status disc_batch_get_box_path(disc_batch* b, int32_t level, int32_t* tma) 
   if (!b || !tma || level < 0 || level >= b->L) return DISC_ERR_ARG;
   if (!b->ready[level]) return DISC_ERR_STATE;
   *tma = b->wide[level] ? 2 : (b->tma[level] ? 1 : 0);
+  return DISC_OK;
+}
+
+disc_status disc_batch_get_gauss_tuning(disc_batch* b, int32_t level, int32_t* zlen, int32_t* separate_warp) {
+  if (!b || level < 0 || level >= b->L) return DISC_ERR_ARG;
+  if (!b->ready[level]) return DISC_ERR_STATE;
+  if (zlen) *zlen = b->gauss_zlen[level];
+  if (separate_warp) *separate_warp = b->sep_warp[level] ? 1 : 0;
   return DISC_OK;
 }
 

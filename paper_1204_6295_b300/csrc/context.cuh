@@ -124,4 +124,10 @@ cudaError_t ctx_reserve_partials(disc_ctx* c, int n);
 BoxArgs ctx_box_args(const disc_ctx* c, int l);       // iteration-mode box arguments of level l
 GaussArgs ctx_gauss_args(const disc_ctx* c, int l);   // Gaussian arguments of level l (with warp)
 NormState ctx_norm_state(const disc_ctx* c, int l);
+// Queue up to `budget` iterations of the schedule on c->s from the current
+// level and iteration, up-sampling each level finished on the way (Algorithm
+// A1).  touched/ntouched: the levels that ran iterations (may be NULL);
+// queued: the number of iterations queued (may be NULL).  No stream
+// ordering with the caller's stream: the caller provides it.
+cudaError_t ctx_advance(disc_ctx* c, long long budget, int* touched, int* ntouched, long long* queued);
 }  // namespace disc

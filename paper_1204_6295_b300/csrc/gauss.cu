@@ -211,10 +211,9 @@ __device__ __forceinline__ void gauss_xy_body(const GaussArgs& a, int bx, int by
     const int gx = x0 - R + ix, gy = y0 - R + iy;
     const bool ok = e < X::IY * X::IX && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
     const size_t g = ok ? (size_t)gy * nx + gx : 0;
-    const long long gu = (long long)(ux - a.u) + (long long)g;
-    vx[k] = ok ? ldg_in(a.u, gu, 3LL * N) : 0.0f;
-    vy[k] = ok ? ldg_in(a.u, (long long)N + gu, 3LL * N) : 0.0f;
-    vz[k] = ok ? ldg_in(a.u, 2LL * N + gu, 3LL * N) : 0.0f;
+    vx[k] = ok ? ldg_at(ux + g, a.u, 3LL * N) : 0.0f;
+    vy[k] = ok ? ldg_at(ux + N + g, a.u, 3LL * N) : 0.0f;
+    vz[k] = ok ? ldg_at(ux + 2 * N + g, a.u, 3LL * N) : 0.0f;
   }
 #pragma unroll
   for (int k = 0; k < NL; ++k) {
@@ -325,10 +324,10 @@ __device__ __forceinline__ void gauss_xy_body(const GaussArgs& a, int bx, int by
             accz[b] = accz[b] / n;
           }
         }
-        const long long g = (long long)(t - a.r) + (long long)gy * nx + gx;
-        st_in(a.r, g, 3LL * N, acc[b].x);
-        st_in(a.r, (long long)N + g, 3LL * N, acc[b].y);
-        st_in(a.r, 2LL * N + g, 3LL * N, accz[b]);
+        const size_t g = (size_t)gy * nx + gx;
+        st_at(t + g, a.r, 3LL * N, acc[b].x);
+        st_at(t + N + g, a.r, 3LL * N, acc[b].y);
+        st_at(t + 2 * N + g, a.r, 3LL * N, accz[b]);
       }
     }
   }
@@ -397,10 +396,9 @@ __device__ __forceinline__ void gauss_z_body(const GaussArgs& a, int bx, int by,
     for (int j = 0; j < KZ; ++j) {
       const int zi = zb + j;
       const bool ok = zi >= zs && zi <= ze && zi < nz;
-      const long long tq = (long long)(tb - a.u) + (long long)j * plane;
-      v2[j] = ok ? make_float2(ldg_in(a.u, tq, 3LL * N), ldg_in(a.u, (long long)N + tq, 3LL * N))
-                 : make_float2(0.0f, 0.0f);
-      vz[j] = ok ? ldg_in(a.u, 2LL * N + tq, 3LL * N) : 0.0f;
+      const float* tp = tb + (size_t)j * plane;
+      v2[j] = ok ? make_float2(ldg_at(tp, a.u, 3LL * N), ldg_at(tp + N, a.u, 3LL * N)) : make_float2(0.0f, 0.0f);
+      vz[j] = ok ? ldg_at(tp + 2 * N, a.u, 3LL * N) : 0.0f;
     }
 #pragma unroll
     for (int j = 0; j < KZ; ++j) {
@@ -424,17 +422,19 @@ __device__ __forceinline__ void gauss_z_body(const GaussArgs& a, int bx, int by,
           o2.y = o2.y / nrm;
           oz = oz / nrm;
         }
-        const long long ro = (long long)(rb - a.r) + (long long)j * plane;   // this output's index
+        float* rp = rb + (size_t)j * plane;
         if (a.add) {                          // r = r_prev + G * dr (in place: same element)
-          o2.x += DISC_IN(ro, 3LL * N) ? a.add[ro] : 0.0f;
-          o2.y += DISC_IN((long long)N + ro, 3LL * N) ? a.add[N + ro] : 0.0f;
-          oz += DISC_IN(2LL * N + ro, 3LL * N) ? a.add[2 * N + ro] : 0.0f;
+          const float* ap = a.add + (rp - a.r);
+          o2.x += DISC_IN(ap - a.add, 3LL * N) ? ap[0] : 0.0f;
+          o2.y += DISC_IN(ap + N - a.add, 3LL * N) ? ap[N] : 0.0f;
+          oz += DISC_IN(ap + 2 * N - a.add, 3LL * N) ? ap[2 * N] : 0.0f;
         }
-        st_in(a.r, ro, 3LL * N, o2.x);
-        st_in(a.r, (long long)N + ro, 3LL * N, o2.y);
-        st_in(a.r, 2LL * N + ro, 3LL * N, oz);
+        st_at(rp, a.r, 3LL * N, o2.x);
+        st_at(rp + N, a.r, 3LL * N, o2.y);
+        st_at(rp + 2 * N, a.r, 3LL * N, oz);
         if (WARP)
-          st_in(a.m, (long long)zo * plane + col, (long long)N, warp_at(a.Im, x, y, zo, o2.x, o2.y, oz, nx, ny, nz));
+          st_at(a.m + (size_t)zo * plane + col, a.m, (long long)N,
+                warp_at(a.Im, x, y, zo, o2.x, o2.y, oz, nx, ny, nz));
       }
       q2[so] = make_float2(0.0f, 0.0f);
       qz[so] = 0.0f;

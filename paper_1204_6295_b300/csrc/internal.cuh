@@ -40,6 +40,16 @@ template <typename T>
 __device__ __forceinline__ void st_in(T* p, long long i, long long n, T v) {
   if (DISC_IN(i, n)) p[i] = v;
 }
+// The same with the element given by its address p inside the buffer that
+// starts at base (the index is formed only by the checked build).
+template <typename T>
+__device__ __forceinline__ T ldg_at(const T* p, const T* base, long long n) {
+  return DISC_IN(p - base, n) ? __ldg(p) : T{};
+}
+template <typename T>
+__device__ __forceinline__ void st_at(T* p, const T* base, long long n, T v) {
+  if (DISC_IN(p - base, n)) *p = v;
+}
 // The same for data read or written once: streaming loads and stores (evicted
 // first from L2, so that they do not push out data the kernel reuses).
 template <typename T>
@@ -410,6 +420,10 @@ struct WarpBatch {
 };
 cudaError_t launch_warp_batch(const WarpBatch& wb, int total_blocks, cudaStream_t s);
 constexpr int kWarpBatchThreads = 128;
+// The z-marching warp over a work table whose offsets count warp_z_blocks of
+// each pair's volume (warp.cu).
+int warp_z_blocks(int nx, int ny, int nz);
+cudaError_t launch_warp_z_batch(const WarpBatch& wb, int total_blocks, cudaStream_t s);
 // Deterministic fixed-order sum of per-CTA float partials (stride 2, component c) into *out.
 cudaError_t launch_partials_sum(const float* partials, int nparts, int comp, double* out,
                                 cudaStream_t s);

@@ -32,16 +32,14 @@ __global__ void __launch_bounds__(kWarpThreads) k_warp(const float* __restrict__
 // columns: a warp's field loads and m stores are coalesced rows, and its rows'
 // gathers share cache lines.
 constexpr int kWarpZX = 32, kWarpZY = 4, kWarpAhead = 2, kWarpZChunk = 16;
-__global__ void __launch_bounds__(kWarpZX * kWarpZY) k_warp_z(const float* __restrict__ Im, const float* __restrict__ r,
-                                                               float* __restrict__ m, int nx, int ny, int nz,
-                                                               const int* stop) {
-  pdl_wait();
-  pdl_release();
-  if (stop != nullptr && *(volatile const int*)stop != 0) return;
-  const int x = blockIdx.x * kWarpZX + threadIdx.x % kWarpZX;
-  const int y = blockIdx.y * kWarpZY + threadIdx.x / kWarpZX;
+// Column (x, y) of CTA (bx, by), planes [bz kWarpZChunk, (bz + 1) kWarpZChunk).
+__device__ __forceinline__ void warp_z_body(const float* __restrict__ Im, const float* __restrict__ r,
+                                            float* __restrict__ m, int nx, int ny, int nz, int bx, int by,
+                                            int bz) {
+  const int x = bx * kWarpZX + threadIdx.x % kWarpZX;
+  const int y = by * kWarpZY + threadIdx.x / kWarpZX;
   if (x >= nx || y >= ny) return;
-  const int z0 = blockIdx.z * kWarpZChunk, z1 = min(nz, z0 + kWarpZChunk);
+  const int z0 = bz * kWarpZChunk, z1 = min(nz, z0 + kWarpZChunk);
   const long long plane = (long long)nx * ny, N = plane * nz;
   const long long col = (long long)y * nx + x;
   float rq[kWarpAhead + 1][3];
@@ -72,6 +70,30 @@ __global__ void __launch_bounds__(kWarpZX * kWarpZY) k_warp_z(const float* __res
     }
   }
 }
+
+__global__ void __launch_bounds__(kWarpZX * kWarpZY) k_warp_z(const float* __restrict__ Im, const float* __restrict__ r,
+                                                               float* __restrict__ m, int nx, int ny, int nz,
+                                                               const int* stop) {
+  pdl_wait();
+  pdl_release();
+  if (stop != nullptr && *(volatile const int*)stop != 0) return;
+  warp_z_body(Im, r, m, nx, ny, nz, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Batched z-marching warp: CTA i runs block i - offset[p] of pair p's grid
+// (warp_z_blocks of its volume, x fastest).
+__global__ void __launch_bounds__(kWarpZX * kWarpZY) k_warp_z_batch(const __grid_constant__ WarpBatch wb) {
+  pdl_wait();
+  pdl_release();
+  const int i = blockIdx.x;
+  int p = 0;
+  while (p + 1 < wb.count && wb.offset[p + 1] <= i) ++p;
+  if (wb.stop[p] != nullptr && *(volatile const int*)wb.stop[p] != 0) return;
+  const int nx = wb.nx[p], ny = wb.ny[p];
+  const int gx = (nx + kWarpZX - 1) / kWarpZX, gy = (ny + kWarpZY - 1) / kWarpZY;
+  const int j = i - wb.offset[p];
+  warp_z_body(wb.Im[p], wb.r[p], wb.m[p], nx, ny, wb.nz[p], j % gx, (j / gx) % gy, j / (gx * gy));
+}
 }  // namespace
 
 __global__ void __launch_bounds__(kWarpBatchThreads) k_warp_batch(const __grid_constant__ WarpBatch wb) {
@@ -97,6 +119,15 @@ cudaError_t launch_warp_batch(const WarpBatch& wb, int total_blocks, cudaStream_
   if (total_blocks < 1) return cudaSuccess;
   k_warp_batch<<<total_blocks, kWarpBatchThreads, 0, s>>>(wb);
   return cudaGetLastError();
+}
+
+int warp_z_blocks(int nx, int ny, int nz) {
+  return ((nx + kWarpZX - 1) / kWarpZX) * ((ny + kWarpZY - 1) / kWarpZY) * ((nz + kWarpZChunk - 1) / kWarpZChunk);
+}
+
+cudaError_t launch_warp_z_batch(const WarpBatch& wb, int total_blocks, cudaStream_t s) {
+  if (total_blocks < 1) return cudaSuccess;
+  return launch_pdl(k_warp_z_batch, dim3(total_blocks), dim3(kWarpZX * kWarpZY), 0, s, wb);
 }
 
 cudaError_t launch_warp(const float* Im, const float* r, float* m, int nx, int ny, int nz, const int* stop,

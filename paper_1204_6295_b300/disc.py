@@ -98,6 +98,7 @@ _SIGS = {
     "disc_batch_destroy": (_st, [_vp]),
     "disc_batch_get_box_path": (_st, [_vp, _i32, ctypes.POINTER(_i32)]),
     "disc_batch_pin_tuning": (_st, [_vp, _i32, _i32, _i32]),
+    "disc_batch_get_gauss_tuning": (_st, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "disc_k_max_abs": (_st, [_vp, _i64, _vp, _vp]),
     "disc_k_global_shift": (_st, [_vp, _vp, _vp, _i64, _vp, _vp]),
     "disc_k_downsample2": (_st, [_vp, _vp, _i32, _i32, _i32, _vp]),
@@ -468,6 +469,13 @@ class Batch:
     def box_path_tma(self, level):
         """True when `level`'s moment/force launch is the bulk-tensor-copy-fed 32 x 16 kernel."""
         return self.box_path(level) == 1
+
+    def gauss_tuning(self, level):
+        """(z chunk of the Gaussian z pass, 0 = pair plans; 1 if the warp runs after it) at `level`."""
+        zlen, sep = _i32(0), _i32(0)
+        _check(_lib.disc_batch_get_gauss_tuning(self._h, int(level), ctypes.byref(zlen), ctypes.byref(sep)),
+               "disc_batch_get_gauss_tuning")
+        return int(zlen.value), int(sep.value)
 
     def pin_tuning(self, level, zmult, grid):
         """Use z chunking `zmult` and grid `grid` (0: one CTA per item) at `level` instead of the autotuner."""

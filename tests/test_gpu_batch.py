@@ -142,6 +142,26 @@ def test_batched_tuner_picks_a_tiling(disc, tma_pairs, tma_single):
         np.testing.assert_array_equal(got[i], tma_single[i])
 
 
+@pytest.mark.parametrize("switch,separate", [("SW_SEPARATE_WARP", 1), ("SW_FUSED_WARP", 0), (None, None)])
+def test_batched_warp_placement_and_z_chunks(disc, tma_pairs, tma_single, switch, separate):
+    """The Gaussian z pass and warp tuner: the warp inside the z pass or as the
+    z-marching warp kernel after it (forced by the test switches, or chosen by
+    the tuner), z chunks of any length; the fields stay the single-pair ones."""
+    sw = getattr(disc, switch) if switch else 0
+    with disc.test_switches(sw):
+        with disc.Batch(len(tma_pairs), **TMA_KW) as b:
+            for i, p in enumerate(tma_pairs):
+                b.set_images(i, p.ct, p.cbct)
+            assert b.iterate(-1) == 10
+            for lev in range(2):
+                zlen, sep = b.gauss_tuning(lev)
+                assert zlen in (0, 16, 32, 64)
+                assert separate is None or sep == separate
+            got = [b.get_field(i) for i in range(len(tma_pairs))]
+    for i in range(len(tma_pairs)):
+        np.testing.assert_array_equal(got[i], tma_single[i])
+
+
 def test_batched_tma_kernel_sampled_against_oracle(disc):
     """One level of two iterations, persistent grid, TMA-fed batch: sampled voxels
     of every pair against the FP64 oracle on a crop holding everything they
@@ -171,3 +191,34 @@ def test_batched_tma_kernel_sampled_against_oracle(disc):
                 cr, _, _, _ = O.iteration(p.ct[sl].astype(np.float64), Is[sl], cr, P)
             ref = cr[:, z - z0, y - y0, x - x0]
             assert np.abs(r[:, z, y, x] - ref).max() <= 2e-3, ((z, y, x), r[:, z, y, x], ref)
+
+
+MASK_KW = dict(patch=(5, 5, 5), sigma=1.0, levels=2, iters=(5, 4), mask_mode=1)
+
+
+def test_batched_masked_pairs_equal_single_pair_runs(disc, pairs):
+    """The mask of Eqs. 7-10 in a batch: the pairs run their own schedules on
+    their own streams, concurrently; each field must be its single-pair run's,
+    also when the schedule is advanced in two calls."""
+    sub = [pairs[0], pairs[2], pairs[4]]
+    refs = []
+    for p in sub:
+        with disc.Registration(**MASK_KW) as reg:
+            reg.set_images(p.ct, p.cbct)
+            reg.iterate(-1)
+            refs.append(reg.get_field())
+    with disc.Batch(len(sub), **MASK_KW) as b:
+        for i, p in enumerate(sub):
+            b.set_images(i, p.ct, p.cbct)
+        assert b.iterate(3) == 3
+        assert b.iterate(-1) == 6
+        got = [b.get_field(i) for i in range(len(sub))]
+        with pytest.raises(disc.DiscError) as e:
+            b.tuning(0)                            # no shared work table in this form
+        assert e.value.status == 3
+        b.restart()
+        assert b.iterate(-1) == 9
+        again = [b.get_field(i) for i in range(len(sub))]
+    for i in range(len(sub)):
+        np.testing.assert_array_equal(got[i], refs[i])
+        np.testing.assert_array_equal(again[i], refs[i])
