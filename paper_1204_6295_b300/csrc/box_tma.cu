@@ -418,6 +418,7 @@ __device__ __forceinline__ bool box_tma_body(const BoxArgs& a, int bx, int by, i
       const float* mzm = mring + ((unsigned)(zlo ? zo - 1 : zo) % B::NMS) * B::MS;
       const float* mzp = mring + ((unsigned)(zhi ? zo + 1 : zo) % B::NMS) * B::MS;
       const bool nin = a.norm_hi <= a.norm_lo || (zo >= a.norm_lo && zo < a.norm_hi);   // the plane enters the norm sums
+      float* out0 = a.out + (size_t)zo * plane;
 #pragma unroll
       for (int i = 0; i < B::KO; ++i) {
         const int fi = fo3[i];
@@ -427,10 +428,10 @@ __device__ __forceinline__ bool box_tma_body(const BoxArgs& a, int bx, int by, i
                                 dzp[fi] - dzm[fi], mzp[fi] - mzm[fi], a.force_mode == DISC_FORCE_DOUBLE);
         const int o = tid + i * kThreads;
         const float rx = ro[o], ry = ro[B::TN + o], rz = ro[2 * B::TN + o];   // staged by group B
-        const long long go = (long long)zo * plane + goff3[i];
-        st_in(a.out, go, 3LL * N, fmaf(keep, rx, dr.x));
-        st_in(a.out, go + N, 3LL * N, fmaf(keep, ry, dr.y));
-        st_in(a.out, go + 2LL * N, 3LL * N, fmaf(keep, rz, dr.z));
+        float* po = out0 + goff3[i];
+        st_at(po, a.out, 3LL * N, fmaf(keep, rx, dr.x));
+        st_at(po + N, a.out, 3LL * N, fmaf(keep, ry, dr.y));
+        st_at(po + 2 * (size_t)N, a.out, 3LL * N, fmaf(keep, rz, dr.z));
         acc0 += nin ? norm3(dr.x, dr.y, dr.z) : 0.0f;
         acc1 += nin ? norm3(rx, ry, rz) : 0.0f;
       }
