@@ -93,6 +93,8 @@ def source_digest():
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())
+    with open(os.path.join(ROOT, "paper_1204_6295_b300", "build.py"), "rb") as f:   # the compile flags
+        h.update(f.read())
     return h.hexdigest()[:16]
 
 
