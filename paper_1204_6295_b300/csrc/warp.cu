@@ -33,6 +33,7 @@ __global__ void __launch_bounds__(kWarpThreads) k_warp(const float* __restrict__
 // gathers share cache lines.
 constexpr int kWarpZX = 32, kWarpZY = 4, kWarpAhead = 2, kWarpZChunk = 16;
 // Column (x, y) of CTA (bx, by), planes [bz kWarpZChunk, (bz + 1) kWarpZChunk).
+// The field and image indices fit 32 bits (3 N < 2^31, checked by the launch).
 __device__ __forceinline__ void warp_z_body(const float* __restrict__ Im, const float* __restrict__ r,
                                             float* __restrict__ m, int nx, int ny, int nz, int bx, int by,
                                             int bz) {
@@ -40,17 +41,17 @@ __device__ __forceinline__ void warp_z_body(const float* __restrict__ Im, const 
   const int y = by * kWarpZY + threadIdx.x / kWarpZX;
   if (x >= nx || y >= ny) return;
   const int z0 = bz * kWarpZChunk, z1 = min(nz, z0 + kWarpZChunk);
-  const long long plane = (long long)nx * ny, N = plane * nz;
-  const long long col = (long long)y * nx + x;
+  const int plane = nx * ny, N = plane * nz;
+  const int col = y * nx + x;
   float rq[kWarpAhead + 1][3];
 #pragma unroll
   for (int k = 0; k < kWarpAhead; ++k) {
     const int z = z0 + k;
     if (z < z1) {
-      const long long g = z * plane + col;
-      rq[k][0] = ldcs_in(r, g, 3 * N);
-      rq[k][1] = ldcs_in(r, N + g, 3 * N);
-      rq[k][2] = ldcs_in(r, 2 * N + g, 3 * N);
+      const int g = z * plane + col;
+      rq[k][0] = ldcs_in(r, g, 3LL * N);
+      rq[k][1] = ldcs_in(r, N + g, 3LL * N);
+      rq[k][2] = ldcs_in(r, 2 * N + g, 3LL * N);
     }
   }
   for (int zb = z0; zb < z1; zb += kWarpAhead + 1) {
@@ -61,12 +62,12 @@ __device__ __forceinline__ void warp_z_body(const float* __restrict__ Im, const 
       const int zn = z + kWarpAhead;          // the plane whose field is loaded now
       const int sn = (j + kWarpAhead) % (kWarpAhead + 1);
       if (zn < z1) {
-        const long long g = zn * plane + col;
-        rq[sn][0] = ldcs_in(r, g, 3 * N);
-        rq[sn][1] = ldcs_in(r, N + g, 3 * N);
-        rq[sn][2] = ldcs_in(r, 2 * N + g, 3 * N);
+        const int g = zn * plane + col;
+        rq[sn][0] = ldcs_in(r, g, 3LL * N);
+        rq[sn][1] = ldcs_in(r, N + g, 3LL * N);
+        rq[sn][2] = ldcs_in(r, 2 * N + g, 3LL * N);
       }
-      st_in(m, z * plane + col, N, warp_at(Im, x, y, z, rq[j][0], rq[j][1], rq[j][2], nx, ny, nz));
+      st_in(m, z * plane + col, (long long)N, warp_at32(Im, x, y, z, rq[j][0], rq[j][1], rq[j][2], nx, ny, nz));
     }
   }
 }
@@ -133,7 +134,7 @@ cudaError_t launch_warp_z_batch(const WarpBatch& wb, int total_blocks, cudaStrea
 cudaError_t launch_warp(const float* Im, const float* r, float* m, int nx, int ny, int nz, const int* stop,
                         cudaStream_t s) {
   if (ny > 65535 || nz > 65535) return cudaErrorInvalidConfiguration;
-  if (nx >= kWarpZX && nz >= kWarpZChunk) {
+  if (nx >= kWarpZX && nz >= kWarpZChunk && 3.0 * nx * ny * nz < 2147483647.0) {
     dim3 grid((nx + kWarpZX - 1) / kWarpZX, (ny + kWarpZY - 1) / kWarpZY, (nz + kWarpZChunk - 1) / kWarpZChunk);
     return launch_pdl(k_warp_z, grid, dim3(kWarpZX * kWarpZY), 0, s, Im, r, m, nx, ny, nz, stop);
   }

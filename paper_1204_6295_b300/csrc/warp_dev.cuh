@@ -30,6 +30,34 @@ static __device__ __forceinline__ void axis_setup(int c, float rv, int n, int& i
 
 static __device__ __forceinline__ float lerpf(float a, float b, float t) { return fmaf(t, b - a, a); }
 
+// warp_at for volumes of fewer than 2^31 voxels: the eight sample indices in
+// 32-bit arithmetic (one wide address computation per gather).  Same samples,
+// same interpolation, same bits.
+static __device__ __forceinline__ float warp_at32(const float* __restrict__ Im, int x, int y, int z, float rx,
+                                                  float ry, float rz, int nx, int ny, int nz) {
+  int x0, x1, y0, y1, z0, z1;
+  float tx, ty, tz;
+  axis_setup(x, rx, nx, x0, x1, tx);
+  axis_setup(y, ry, ny, y0, y1, ty);
+  axis_setup(z, rz, nz, z0, z1, tz);
+  const int plane = nx * ny;
+  const int b00 = z0 * plane + y0 * nx, b01 = z0 * plane + y1 * nx;
+  const int b10 = z1 * plane + y0 * nx, b11 = z1 * plane + y1 * nx;
+#ifdef DISC_BOUNDS_CHECK
+  const long long n = (long long)plane * nz;
+  auto ld = [&](int i) { return DISC_IN(i, n) ? __ldg(Im + i) : 0.0f; };
+#else
+  auto ld = [&](int i) { return __ldg(Im + i); };
+#endif
+  const float c000 = ld(b00 + x0), c001 = ld(b00 + x1);
+  const float c010 = ld(b01 + x0), c011 = ld(b01 + x1);
+  const float c100 = ld(b10 + x0), c101 = ld(b10 + x1);
+  const float c110 = ld(b11 + x0), c111 = ld(b11 + x1);
+  const float c00 = lerpf(c000, c001, tx), c01 = lerpf(c010, c011, tx);
+  const float c10 = lerpf(c100, c101, tx), c11 = lerpf(c110, c111, tx);
+  return lerpf(lerpf(c00, c01, ty), lerpf(c10, c11, ty), tz);
+}
+
 static __device__ __forceinline__ float warp_at(const float* __restrict__ Im, int x, int y, int z, float rx,
                                          float ry, float rz, int nx, int ny, int nz) {
   int x0, x1, y0, y1, z0, z1;

@@ -132,7 +132,8 @@ def test_pass_a_constant_patches_give_zero_force(disc):
     assert np.all(host(u)[:, interior] == 0.0)
 
 
-@pytest.mark.parametrize("shape", [(13, 37, 70), (1, 1, 1), (4, 3, 129), (6, 1, 1)])
+# the per-voxel kernel, and the z-marching one (nx >= 32, nz >= 16: ragged chunks and tiles)
+@pytest.mark.parametrize("shape", [(13, 37, 70), (1, 1, 1), (4, 3, 129), (6, 1, 1), (20, 37, 70), (33, 64, 96)])
 def test_warp_matches_oracle(disc, shape):
     Im = ct_like(shape, 12)
     r = phantom.random_field(shape, 13, amp=4.0)        # samples leave the volume too
