@@ -388,11 +388,12 @@ BoxPlan box_plan(int mode, int nx, int ny, int nz, int hx, int hy, int hz, int n
   return p;
 }
 
-BoxPlan box_plan_iter(int nx, int ny, int nz, int hx, int hy, int hz, int num_sms, const float* src,
-                      const float* r, const float* u) {
-  // the wide-tile pass where its one wave gets enough planes per CTA to
-  // amortise the z warm-up of a march; the 32 x 16 tiling otherwise
-  const bool aligned = (((uintptr_t)src | (uintptr_t)r | (uintptr_t)u) & 15u) == 0u;
+namespace {
+// The wide-tile plan where its one wave gets enough planes per CTA to amortise
+// the z warm-up of a march (grid.x = 0: not eligible).
+BoxPlan wide_plan(int nx, int ny, int nz, int hx, int hy, int hz, int num_sms, bool aligned) {
+  BoxPlan none{};
+  none.grid = dim3(0, 0, 0);
   if (aligned && box_wide_ok(nx, ny, nz, hx, hy, hz)) {
     int tx = 0, ty = 0;
     box_wide_tile(&tx, &ty);
@@ -410,12 +411,27 @@ BoxPlan box_plan_iter(int nx, int ny, int nz, int hx, int hy, int hz, int num_sm
       return p;
     }
   }
-  return box_plan(kModeIterate, nx, ny, nz, hx, hy, hz, num_sms);
+  return none;
+}
+}  // namespace
+
+BoxPlan box_plan_iter(int nx, int ny, int nz, int hx, int hy, int hz, int num_sms, const float* src,
+                      const float* r, const float* u) {
+  const bool aligned = (((uintptr_t)src | (uintptr_t)r | (uintptr_t)u) & 15u) == 0u;
+  const BoxPlan w = wide_plan(nx, ny, nz, hx, hy, hz, num_sms, aligned);
+  return w.grid.x != 0 ? w : box_plan(kModeIterate, nx, ny, nz, hx, hy, hz, num_sms);
+}
+
+BoxPlan box_plan_adjoint(int nx, int ny, int nz, int hx, int hy, int hz, int num_sms, const float* src,
+                         const float* out) {
+  const bool aligned = (((uintptr_t)src | (uintptr_t)out) & 15u) == 0u;
+  const BoxPlan w = wide_plan(nx, ny, nz, hx, hy, hz, num_sms, aligned);
+  return w.grid.x != 0 ? w : box_plan(kModeSsdAdjoint, nx, ny, nz, hx, hy, hz, num_sms);
 }
 
 cudaError_t box_launch(int mode, const BoxArgs& a, const BoxPlan& p, cudaStream_t s) {
   if (p.grid.x == 0) return cudaErrorInvalidConfiguration;
-  if (p.wide) return mode == kModeIterate ? box_wide_launch(a, p, s) : cudaErrorInvalidValue;
+  if (p.wide) return box_wide_launch(mode, a, p, s);
   BoxArgs b = a;
   b.zlen = p.zlen;
   if (p.tma) {

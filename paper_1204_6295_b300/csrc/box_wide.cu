@@ -92,7 +92,7 @@ struct WideLayout {
 // parity of the copy barrier, carried over the marches of a CTA (every phase
 // armed in a march is awaited in it); acc0, acc1 gather sum |dr| and sum |r|.
 // Returns false when a copy wait gave up: the CTA must stop.
-template <int H, int TX, int TY>
+template <int H, int TX, int TY, int MODE = kModeIterate>
 __device__ __forceinline__ bool wide_march(const BoxArgs& a, int bx, int by, int z0, int z1,
                                            const CUtensorMap* map_w, const CUtensorMap* map_f, unsigned char* smem,
                                            uint32_t& pa, float& acc0, float& acc1) {
@@ -114,11 +114,17 @@ __device__ __forceinline__ bool wide_march(const BoxArgs& a, int bx, int by, int
   const int plane = nx * ny;                  // 3 N < 2^31 is checked on the host
   const int N = plane * nz;
   const int x0 = bx * TX, y0 = by * TY;
-  // planes whose moments are needed (the force of plane z reads d at z - 1 .. z + 1)
-  const int zc_lo = max(0, z0 - 1), zc_hi = min(nz - 1, z1);
+  // the adjoint mode of the SSD form writes its coefficients at the centre plane
+  // itself; the iteration mode's force of plane z reads d at z - 1 .. z + 1
+  constexpr bool ADJ = MODE == kModeSsdAdjoint;
+  static_assert(MODE == kModeIterate || ADJ, "wide pass modes");
+  // planes whose moments are needed
+  const int zc_lo = ADJ ? z0 : max(0, z0 - 1), zc_hi = ADJ ? z1 - 1 : min(nz - 1, z1);
   const int zi0 = max(0, zc_lo - H);          // first plane summed in z
   const int zw = zc_lo + H;                   // first step with a centre plane
-  const int zi1 = z1 + H;                     // the force of z1 - 1 comes in the step of centre z1
+  // the last step: the adjoint's last centre plane z1 - 1; the force of plane
+  // z1 - 1 comes in the step of centre z1 (past the volume at its end)
+  const int zi1 = ADJ ? z1 - 1 + H : z1 + H;
   const float qs = a.qscale, inv_qs = a.inv_qscale, vfl = a.var_floor;
   const bool dbl = a.force_mode == DISC_FORCE_DOUBLE;
   const float keep = a.u_is_dr ? 0.0f : 1.0f;   // u = keep r + dr
@@ -237,7 +243,7 @@ __device__ __forceinline__ bool wide_march(const BoxArgs& a, int bx, int by, int
     const int zc = zi - H;                    // centre plane of the patch window
     const bool do2 = zc >= zc_lo && zc <= zc_hi;
     const int zf = zc - 1;                    // plane whose force is computed this step
-    const bool do3 = zf >= z0 && zf < z1;
+    const bool do3 = !ADJ && zf >= z0 && zf < z1;
     // ---- loads into registers for this step: zs of the y task, r of the force --
     float zsr[B::SY];
     if (do2 && ycol) {
@@ -333,9 +339,24 @@ __device__ __forceinline__ bool wide_march(const BoxArgs& a, int bx, int by, int
           float dc, sg_;
           patch_moments(b1, b2, n, inv_n, __float2int_rn(vc * qs), inv_qs, vfl, dc, sg_);
           const float d = fmaf(zsr[j], sg_, dc);   // I'_s - I_m^(k)
-          dcur[fi] = d;
-          if (a.f_tap && out_plane && fx_y >= 1 && fx_y <= TX && fy >= 1 && fy <= TY)
-            st_in(a.f_tap, (long long)zc * plane + (long long)gy * nx + gx_y, N, d);
+          if constexpr (ADJ) {
+            // the SSD loss and the adjoint coefficients at the tile's own voxels
+            if (out_plane && fx_y >= 1 && fx_y <= TX && fy >= 1 && fy <= TY) {
+              acc0 = fmaf(d, d, acc0);
+              const float D = -2.0f * d;
+              const float A = -D * inv_n;
+              const float Bc = sg_ > 0.0f ? -D * zsr[j] * inv_n / sg_ : 0.0f;
+              const long long gz = (long long)zc * plane + (long long)gy * nx + gx_y;
+              st_in(a.out, gz, 4LL * N, A);
+              st_in(a.out, (long long)N + gz, 4LL * N, Bc);
+              st_in(a.out, 2LL * N + gz, 4LL * N, Bc * (vc + dc));
+              st_in(a.out, 3LL * N + gz, 4LL * N, D);
+            }
+          } else {
+            dcur[fi] = d;
+            if (a.f_tap && out_plane && fx_y >= 1 && fx_y <= TX && fy >= 1 && fy <= TY)
+              st_in(a.f_tap, (long long)zc * plane + (long long)gy * nx + gx_y, N, d);
+          }
         }
       }
     }
@@ -445,7 +466,7 @@ __device__ __forceinline__ bool wide_setup(unsigned char* smem, int* err) {
 // One volume: CTA c marches the planes [c P / G, (c + 1) P / G) of the
 // sequence of all P = tiles x nz (tile, plane) pairs, tile after tile (at most
 // a few tiles per CTA), G = gridDim.x.
-template <int H, int TX, int TY>
+template <int H, int TX, int TY, int MODE>
 __global__ void __launch_bounds__(kWideThreads, 2)
     k_box_wide(const BoxArgs a, const __grid_constant__ CUtensorMap map_w, const __grid_constant__ CUtensorMap map_f,
                int tiles_x, int tiles_y) {
@@ -463,7 +484,7 @@ __global__ void __launch_bounds__(kWideThreads, 2)
     const int t = (int)(gp / a.nz), z0 = (int)(gp - (long long)t * a.nz);
     const int z1 = (int)min((long long)a.nz, (long long)z0 + (hi - gp));
     __syncthreads();                          // the previous march's reads of the buffers are done
-    if (!wide_march<H, TX, TY>(a, t % tiles_x, t / tiles_x, z0, z1, &map_w, &map_f, smem, pa, acc0, acc1))
+    if (!wide_march<H, TX, TY, MODE>(a, t % tiles_x, t / tiles_x, z0, z1, &map_w, &map_f, smem, pa, acc0, acc1))
       return;
     gp += z1 - z0;
   }
@@ -537,7 +558,7 @@ struct WideHost {
   static size_t smem() { return B::bytes; }
   static int extent(int axis) { return axis == 0 ? B::WXT : B::WY; }
   static int occupancy() {
-    auto k = k_box_wide<H, TX, TY>;
+    auto k = k_box_wide<H, TX, TY, kModeIterate>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B::bytes) != cudaSuccess ||
         cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess) {
@@ -551,13 +572,14 @@ struct WideHost {
     }
     return n;
   }
+  template <int MODE>
   static cudaError_t launch(const BoxArgs& a, const BoxPlan& p, cudaStream_t s) {
     static int set[kMaxDevices] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    auto k = k_box_wide<H, TX, TY>;
+    auto k = k_box_wide<H, TX, TY, MODE>;
     if (!set[dev]) {
       e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B::bytes);
       if (e == cudaSuccess)
@@ -639,9 +661,15 @@ void box_wide_tile(int* tx, int* ty) {
   *ty = WideHost<1>::TY;
 }
 
-cudaError_t box_wide_launch(const BoxArgs& a, const BoxPlan& p, cudaStream_t s) {
+cudaError_t box_wide_launch(int mode, const BoxArgs& a, const BoxPlan& p, cudaStream_t s) {
   if ((((uintptr_t)a.src | (uintptr_t)a.r | (uintptr_t)a.out) & 15u) != 0u) return cudaErrorInvalidValue;
-  return wide_dispatch<cudaError_t>(a.hx, cudaErrorInvalidValue, [&](auto w) { return decltype(w)::launch(a, p, s); });
+  if (mode == kModeSsdAdjoint)
+    return wide_dispatch<cudaError_t>(a.hx, cudaErrorInvalidValue, [&](auto w) {
+      return decltype(w)::template launch<kModeSsdAdjoint>(a, p, s);
+    });
+  if (mode != kModeIterate) return cudaErrorInvalidValue;
+  return wide_dispatch<cudaError_t>(a.hx, cudaErrorInvalidValue,
+                                    [&](auto w) { return decltype(w)::template launch<kModeIterate>(a, p, s); });
 }
 
 bool box_wide_encode(const BoxArgs& a, void* maps) {

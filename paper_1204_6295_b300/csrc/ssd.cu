@@ -151,9 +151,8 @@ disc_status disc_k_ssd_grad(const float* Im, const float* zs, const float* r, fl
   // need one half size for all three axes
   if (h[0] != h[1] || h[1] != h[2] || h[0] < 1 || h[0] > 8) return DISC_ERR_SHAPE;
   const int sms = device_sms();
-  const BoxPlan p = box_plan(kModeSsdAdjoint, nx, ny, nz, h[0], h[1], h[2], sms);
   GaussPlan gp = gauss_plan(nx, ny, nz, h[0], sms);
-  if (p.grid.x == 0 || gp.grid.x == 0 || !gp.queue) return DISC_ERR_SHAPE;
+  if (gp.grid.x == 0 || !gp.queue) return DISC_ERR_SHAPE;
   cudaStream_t s = (cudaStream_t)stream;
   const size_t N = (size_t)nx * ny * nz;
   float* work = nullptr;   // m (N) | A B C D (4N) | sums of A B C (3N) | filter scratch (3N)
@@ -166,6 +165,13 @@ disc_status disc_k_ssd_grad(const float* Im, const float* zs, const float* r, fl
   float* abcd = work + N;
   float* sums = work + 5 * N;
   float* tmp = work + 8 * N;
+  // the wide-tile adjoint pass on large volumes (one wave of CTAs), the 32 x 16
+  // tiling otherwise
+  const BoxPlan p = box_plan_adjoint(nx, ny, nz, h[0], h[1], h[2], sms, m, abcd);
+  if (p.grid.x == 0) {
+    cudaFreeAsync(work, s);
+    return DISC_ERR_SHAPE;
+  }
   const int nparts = (int)(p.grid.x * p.grid.y * p.grid.z);
   float* parts = nullptr;   // the loss from the adjoint pass's own d (one pass for both)
   cudaError_t e = loss_out ? cudaMallocAsync(&parts, sizeof(float) * 2 * nparts, s) : cudaSuccess;

@@ -193,6 +193,31 @@ def test_planner_wide_pass_bitwise(disc, shape, patch, force_mode):
     np.testing.assert_allclose(outs[0][2], outs[1][2], rtol=1e-6)
 
 
+# The SSD adjoint pass on wide tiles: where the planner picks it (large volumes)
+# and forced on a small ragged one, against the plain-load 32 x 16 pass; the
+# gradient bit for bit, the loss to the partial sums' rounding.
+@pytest.mark.parametrize("shape,patch,wide_any", [((150, 250, 256), 11, False), ((131, 200, 192), 15, False),
+                                                  ((33, 70, 96), 5, True)])
+def test_wide_adjoint_pass_bitwise(disc, shape, patch, wide_any):
+    P = (patch,) * 3
+    ct, cbct, r = _inputs(shape, patch, 80 + patch)
+    qs_m = disc.qscale(float(np.abs(ct).max()), P)
+    qs_s = disc.qscale(float(np.abs(cbct).max()), P)
+    Im, Is, rd = dev(ct), dev(cbct), dev(r)
+    zs = empty(*shape)
+    disc.k_static_norm(Is, zs, P, qs_s)
+    res = []
+    for plain in (False, True):
+        g = empty(3, *shape)
+        loss = empty(1).double()
+        with (_NoTma() if plain else disc.test_switches(disc.SW_WIDE_ANY if wide_any else 0)):
+            disc.k_ssd_grad(Im, zs, rd, g, P, qs_m, loss_out=loss)
+        res.append((host(g), host(loss)))
+    disc.k_check_error()
+    np.testing.assert_array_equal(res[0][0], res[1][0])
+    np.testing.assert_allclose(res[0][1], res[1][1], rtol=1e-6)
+
+
 def test_bounded_wait_reports_timeout_and_device_stays_usable(disc):
     """A copy group armed for 16 bytes more than its copies deliver (the
     DISC_SW_TMA_STALL test switch of the iteration pass) never completes: the wait gives
