@@ -1,5 +1,7 @@
-// Moment, correction, force and update pass on wide tiles (iteration mode,
-// cubic patches, sm_103a): the hot pass of every iteration on the large levels.
+// Moment, correction, force and update pass on wide tiles (cubic patches,
+// sm_103a): the hot pass of every iteration on the large levels.  The same
+// kernel in its adjoint mode computes the SSD form's coefficients (the patch
+// moments, the loss and A, B, C, D at the tile's own voxels; no force stage).
 //
 // Same arithmetic as the other cubic-patch kernels (box_fast.cu, box_tma.cu),
 // so the outputs are bit-identical: exact integer sliding sums of q = rint(v 2^e)
