@@ -811,7 +811,9 @@ disc_status disc_set_images(disc_ctx* ctx, const float* ct, const float* cbct, i
       if (e == cudaSuccess) e = cudaMalloc(&v.hist, v.hist_cap * sizeof(float));
       if (e == cudaSuccess) e = cudaMalloc(&v.hsum, 2 * (size_t)v.hist_cap * sizeof(double));
       if (e == cudaSuccess && ctx->p.mask_mode) {
-        v.pm = box_plan(kModeMaskAB, v.nx, v.ny, v.nz, ctx->hx, ctx->hy, ctx->hz, ctx->num_sms);
+        // the wide-tile mask pass on large levels (library buffers: aligned)
+        v.pm = box_plan_wide_mode(kModeMaskAB, v.nx, v.ny, v.nz, ctx->hx, ctx->hy, ctx->hz, ctx->num_sms,
+                                  nullptr, nullptr);
         if (v.pm.grid.x == 0) e = cudaErrorInvalidConfiguration;
         if (e == cudaSuccess) e = cudaMalloc(&v.sd, v.N * sizeof(float));
         if (e == cudaSuccess) e = cudaMalloc(&v.ab, 2 * v.N * sizeof(float));
@@ -1080,7 +1082,8 @@ disc_status disc_get_correction_means(disc_ctx* ctx, double* mean_a, double* mea
     b.a_max = INFINITY;
     b.qscale = ctx->qs_m;
     b.inv_qscale = 1.0f / ctx->qs_m;
-    const BoxPlan pm = box_plan(kModeMaskAB, v.nx, v.ny, v.nz, ctx->hx, ctx->hy, ctx->hz, ctx->num_sms);
+    const BoxPlan pm = box_plan_wide_mode(kModeMaskAB, v.nx, v.ny, v.nz, ctx->hx, ctx->hy, ctx->hz,
+                                          ctx->num_sms, nullptr, nullptr);
     if (e == cudaSuccess) e = box_launch(kModeMaskAB, b, pm, ctx->s);
     if (e == cudaSuccess) e = launch_ab_sums(isab, stamp, (int64_t)v.N, sums, ctx->s);
   }

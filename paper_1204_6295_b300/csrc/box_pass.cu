@@ -422,11 +422,11 @@ BoxPlan box_plan_iter(int nx, int ny, int nz, int hx, int hy, int hz, int num_sm
   return w.grid.x != 0 ? w : box_plan(kModeIterate, nx, ny, nz, hx, hy, hz, num_sms);
 }
 
-BoxPlan box_plan_adjoint(int nx, int ny, int nz, int hx, int hy, int hz, int num_sms, const float* src,
-                         const float* out) {
+BoxPlan box_plan_wide_mode(int mode, int nx, int ny, int nz, int hx, int hy, int hz, int num_sms,
+                           const float* src, const float* out) {
   const bool aligned = (((uintptr_t)src | (uintptr_t)out) & 15u) == 0u;
   const BoxPlan w = wide_plan(nx, ny, nz, hx, hy, hz, num_sms, aligned);
-  return w.grid.x != 0 ? w : box_plan(kModeSsdAdjoint, nx, ny, nz, hx, hy, hz, num_sms);
+  return w.grid.x != 0 ? w : box_plan(mode, nx, ny, nz, hx, hy, hz, num_sms);
 }
 
 cudaError_t box_launch(int mode, const BoxArgs& a, const BoxPlan& p, cudaStream_t s) {

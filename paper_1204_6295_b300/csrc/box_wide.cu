@@ -1,7 +1,8 @@
 // Moment, correction, force and update pass on wide tiles (cubic patches,
 // sm_103a): the hot pass of every iteration on the large levels.  The same
 // kernel in its adjoint mode computes the SSD form's coefficients (the patch
-// moments, the loss and A, B, C, D at the tile's own voxels; no force stage).
+// moments, the loss and A, B, C, D at the tile's own voxels; no force stage),
+// and in its mask mode the a, b and xi of Eqs. 5-7 of the masked correction.
 //
 // Same arithmetic as the other cubic-patch kernels (box_fast.cu, box_tma.cu),
 // so the outputs are bit-identical: exact integer sliding sums of q = rint(v 2^e)
@@ -116,9 +117,9 @@ __device__ __forceinline__ bool wide_march(const BoxArgs& a, int bx, int by, int
   const int plane = nx * ny;                  // 3 N < 2^31 is checked on the host
   const int N = plane * nz;
   const int x0 = bx * TX, y0 = by * TY;
-  // the adjoint mode of the SSD form writes its coefficients at the centre plane
+  // the SSD adjoint and the mask modes write their outputs at the centre plane
   // itself; the iteration mode's force of plane z reads d at z - 1 .. z + 1
-  constexpr bool ADJ = MODE == kModeSsdAdjoint;
+  constexpr bool ADJ = MODE == kModeSsdAdjoint || MODE == kModeMaskAB;
   static_assert(MODE == kModeIterate || ADJ, "wide pass modes");
   // planes whose moments are needed
   const int zc_lo = ADJ ? z0 : max(0, z0 - 1), zc_hi = ADJ ? z1 - 1 : min(nz - 1, z1);
@@ -341,7 +342,11 @@ __device__ __forceinline__ bool wide_march(const BoxArgs& a, int bx, int by, int
           float dc, sg_;
           patch_moments(b1, b2, n, inv_n, __float2int_rn(vc * qs), inv_qs, vfl, dc, sg_);
           const float d = fmaf(zsr[j], sg_, dc);   // I'_s - I_m^(k)
-          if constexpr (ADJ) {
+          if constexpr (MODE == kModeMaskAB) {
+            // a, b, xi of Eqs. 5-7 at the tile's own voxels (or the ratio alone)
+            if (out_plane && fx_y >= 1 && fx_y <= TX && fy >= 1 && fy <= TY)
+              mask_epilogue(a, (size_t)zc * plane + (size_t)gy * nx + gx_y, vc, dc, sg_, zsr[j]);
+          } else if constexpr (MODE == kModeSsdAdjoint) {
             // the SSD loss and the adjoint coefficients at the tile's own voxels
             if (out_plane && fx_y >= 1 && fx_y <= TX && fy >= 1 && fy <= TY) {
               acc0 = fmaf(d, d, acc0);
@@ -668,6 +673,10 @@ cudaError_t box_wide_launch(int mode, const BoxArgs& a, const BoxPlan& p, cudaSt
   if (mode == kModeSsdAdjoint)
     return wide_dispatch<cudaError_t>(a.hx, cudaErrorInvalidValue, [&](auto w) {
       return decltype(w)::template launch<kModeSsdAdjoint>(a, p, s);
+    });
+  if (mode == kModeMaskAB)
+    return wide_dispatch<cudaError_t>(a.hx, cudaErrorInvalidValue, [&](auto w) {
+      return decltype(w)::template launch<kModeMaskAB>(a, p, s);
     });
   if (mode != kModeIterate) return cudaErrorInvalidValue;
   return wide_dispatch<cudaError_t>(a.hx, cudaErrorInvalidValue,

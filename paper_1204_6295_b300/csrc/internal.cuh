@@ -185,15 +185,16 @@ BoxPlan box_plan(int mode, int nx, int ny, int nz, int hx, int hy, int hz, int n
 constexpr int kWideMinPlanes = 16;
 BoxPlan box_plan_iter(int nx, int ny, int nz, int hx, int hy, int hz, int num_sms, const float* src,
                       const float* r, const float* u);
-// The same choice for the SSD adjoint pass (kModeSsdAdjoint): src the warped
-// image, out its coefficient buffer (4 N floats).
-BoxPlan box_plan_adjoint(int nx, int ny, int nz, int hx, int hy, int hz, int num_sms, const float* src,
-                         const float* out);
+// The same choice for the SSD adjoint pass (kModeSsdAdjoint) and the mask pass
+// (kModeMaskAB): src the warped image, out the pass's first output buffer (the
+// library's buffers are aligned; NULL is accepted).
+BoxPlan box_plan_wide_mode(int mode, int nx, int ny, int nz, int hx, int hy, int hz, int num_sms,
+                           const float* src, const float* out);
 bool box_wide_ok(int nx, int ny, int nz, int hx, int hy, int hz);
 size_t box_wide_smem(int h);
 int box_wide_occupancy(int h);
 void box_wide_tile(int* tx, int* ty);
-// mode: kModeIterate or kModeSsdAdjoint
+// mode: kModeIterate, kModeSsdAdjoint or kModeMaskAB
 cudaError_t box_wide_launch(int mode, const BoxArgs& a, const BoxPlan& p, cudaStream_t s);
 // Reads (synchronising s) and clears the wide pass's own error word, OR-ing it into *flag.
 cudaError_t box_wide_error(cudaStream_t s, int* flag);

@@ -167,7 +167,7 @@ disc_status disc_k_ssd_grad(const float* Im, const float* zs, const float* r, fl
   float* tmp = work + 8 * N;
   // the wide-tile adjoint pass on large volumes (one wave of CTAs), the 32 x 16
   // tiling otherwise
-  const BoxPlan p = box_plan_adjoint(nx, ny, nz, h[0], h[1], h[2], sms, m, abcd);
+  const BoxPlan p = box_plan_wide_mode(kModeSsdAdjoint, nx, ny, nz, h[0], h[1], h[2], sms, m, abcd);
   if (p.grid.x == 0) {
     cudaFreeAsync(work, s);
     return DISC_ERR_SHAPE;

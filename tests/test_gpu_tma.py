@@ -218,6 +218,25 @@ def test_wide_adjoint_pass_bitwise(disc, shape, patch, wide_any):
     np.testing.assert_allclose(res[0][1], res[1][1], rtol=1e-6)
 
 
+def test_wide_mask_pass_bitwise(disc):
+    """The mask pass of Eqs. 5-7 on wide tiles (and the ratio pass of a_m at set-up)
+    inside a masked two-level registration, against the plain-load 32 x 16 pass:
+    the same mask constants and the same field, bit for bit."""
+    pair = phantom.ellipsoid_pair(96, 64, 40, seed=81)
+    kw = dict(patch=(7, 7, 7), sigma=1.0, levels=2, iters=(3, 3), mask_mode=1)
+    out = []
+    for ctx in (lambda: disc.test_switches(disc.SW_WIDE_ANY), _NoTma):
+        with ctx():
+            with disc.Registration(**kw) as reg:
+                reg.set_images(pair.ct, pair.cbct)
+                consts = reg.mask_constants()
+                reg.iterate(-1)
+                out.append((consts, reg.get_field()))
+    disc.k_check_error()
+    assert out[0][0] == out[1][0]
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+
+
 def test_bounded_wait_reports_timeout_and_device_stays_usable(disc):
     """A copy group armed for 16 bytes more than its copies deliver (the
     DISC_SW_TMA_STALL test switch of the iteration pass) never completes: the wait gives
