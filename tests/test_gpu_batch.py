@@ -222,3 +222,25 @@ def test_batched_masked_pairs_equal_single_pair_runs(disc, pairs):
     for i in range(len(sub)):
         np.testing.assert_array_equal(got[i], refs[i])
         np.testing.assert_array_equal(again[i], refs[i])
+
+
+def test_batched_sec21_order_and_warp_placements(disc, tma_pairs):
+    """smooth_mode 1 (r <- r + G * dr, Sec. 2.1) in a batch: the z pass adds into r
+    in place, also when the tuner times it on scratch copies; each field equals
+    its single-pair run whatever the warp placement."""
+    kw = dict(TMA_KW, smooth_mode=1)
+    refs = []
+    for p in tma_pairs:
+        with disc.Registration(**kw) as reg:
+            reg.set_images(p.ct, p.cbct)
+            reg.iterate(-1)
+            refs.append(reg.get_field())
+    for sw in (disc.SW_SEPARATE_WARP, disc.SW_FUSED_WARP):
+        with disc.test_switches(sw):
+            with disc.Batch(len(tma_pairs), **kw) as b:
+                for i, p in enumerate(tma_pairs):
+                    b.set_images(i, p.ct, p.cbct)
+                b.iterate(-1)
+                got = [b.get_field(i) for i in range(len(tma_pairs))]
+        for i in range(len(tma_pairs)):
+            np.testing.assert_array_equal(got[i], refs[i])

@@ -110,3 +110,11 @@ def test_correction_means_masked_match_oracle(disc):
         assert n == int(known.sum())
         assert ma == pytest.approx(fa[known].mean(), rel=1e-5)
         assert abs(mb - fb[known].mean()) <= 1e-5 * scale
+
+
+def test_correction_means_errors(disc):
+    reg = disc.Registration(patch=PATCH, sigma=1.0, levels=1, iters=(1,))
+    with pytest.raises(disc.DiscError) as e:
+        reg.correction_means()                   # no images yet
+    assert e.value.status == 3
+    reg.close()

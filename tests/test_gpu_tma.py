@@ -212,6 +212,9 @@ def test_wide_adjoint_pass_bitwise(disc, shape, patch, wide_any):
         loss = empty(1).double()
         with (_NoTma() if plain else disc.test_switches(disc.SW_WIDE_ANY if wide_any else 0)):
             disc.k_ssd_grad(Im, zs, rd, g, P, qs_m, loss_out=loss)
+            g2 = empty(3, *shape)
+            disc.k_ssd_grad(Im, zs, rd, g2, P, qs_m)        # no loss: no partials
+        np.testing.assert_array_equal(host(g), host(g2))
         res.append((host(g), host(loss)))
     disc.k_check_error()
     np.testing.assert_array_equal(res[0][0], res[1][0])
