@@ -244,3 +244,25 @@ def test_batched_sec21_order_and_warp_placements(disc, tma_pairs):
                 got = [b.get_field(i) for i in range(len(tma_pairs))]
         for i in range(len(tma_pairs)):
             np.testing.assert_array_equal(got[i], refs[i])
+
+
+def test_batched_patch15_sigma2_equals_single_pair_runs(disc):
+    """The large workload's parameters (patch 15^3, sigma 2: R = 6) in a batch of
+    uneven pairs, the shape of the bench's mixed batch: each field is its
+    single-pair run's, whatever the tuner picks."""
+    kw = dict(patch=(15, 15, 15), sigma=2.0, levels=2, iters=(3, 3))
+    pairs = [phantom.head_neck_pair(nx, ny, nz, seed=720 + i)
+             for i, (nx, ny, nz) in enumerate([(96, 64, 40), (64, 80, 32), (128, 96, 48)])]
+    refs = []
+    for p in pairs:
+        with disc.Registration(**kw) as reg:
+            reg.set_images(p.ct, p.cbct)
+            reg.iterate(-1)
+            refs.append(reg.get_field())
+    with disc.Batch(len(pairs), **kw) as b:
+        for i, p in enumerate(pairs):
+            b.set_images(i, p.ct, p.cbct)
+        assert b.iterate(-1) == 6
+        got = [b.get_field(i) for i in range(len(pairs))]
+    for i in range(len(pairs)):
+        np.testing.assert_array_equal(got[i], refs[i])
