@@ -532,7 +532,11 @@ cudaError_t reset_level_counters(disc_ctx* c, int l) {
 
 namespace disc {
 
-cudaError_t ctx_reset_level_counters(disc_ctx* c, int l) { return reset_level_counters(c, l); }
+cudaError_t ctx_reset_level_counters(disc_ctx* c, int l, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(c->d_iter + l, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  return cudaMemsetAsync(c->d_stop + l, 0, sizeof(int), s);
+}
 
 cudaError_t ctx_reserve_partials(disc_ctx* c, int n) {
   if (n <= c->max_parts) return cudaSuccess;

@@ -659,7 +659,7 @@ disc_status disc_batch_restart(disc_batch* b) {
   for (int i = 0; i < b->npairs; ++i) {
     disc_ctx* c = b->pair[i];
     BCK(cudaMemsetAsync(c->lev[lc].r, 0, 3 * c->lev[lc].N * sizeof(float), b->s));
-    for (int l = 0; l < b->L; ++l) BCK(ctx_reset_level_counters(c, l));
+    for (int l = 0; l < b->L; ++l) BCK(ctx_reset_level_counters(c, l, b->s));
     c->cur_level = lc;
     c->cur_iter = 0;
   }
@@ -711,7 +711,7 @@ disc_status disc_batch_iterate(disc_batch* b, int32_t max_iters, int32_t* iters_
         disc_ctx* c = b->pair[i];
         const Level& fine = c->lev[l - 1];
         BCK(launch_up2(c->lev[l].r, fine.r, fine.nx, fine.ny, fine.nz, b->s));
-        BCK(ctx_reset_level_counters(c, l - 1));
+        BCK(ctx_reset_level_counters(c, l - 1, b->s));
         c->cur_level = l - 1;
         c->cur_iter = 0;
       }

@@ -117,7 +117,9 @@ struct disc_ctx {
 
 namespace disc {
 // Helpers of api.cu used by the batched API.
-cudaError_t ctx_reset_level_counters(disc_ctx* c, int l);
+// Zero level l's iteration counter and stop flag, in stream order on s (the
+// batch's stream, where the batched kernels that use them run).
+cudaError_t ctx_reset_level_counters(disc_ctx* c, int l, cudaStream_t s);
 // Grow the context's per-CTA norm partials to at least n (float2 each); drops
 // its own captured graphs, which hold the old buffer.
 cudaError_t ctx_reserve_partials(disc_ctx* c, int n);
