@@ -703,18 +703,16 @@ def run_ours(args, w, rank, world, local_rank):
 
     continuity = (time_plain(disc, torch, WORKLOADS[CONTINUITY_WORKLOAD], dist)
                   if args.workload != CONTINUITY_WORKLOAD else None)
-    # the same schedule with the next iteration's warp inside the Gaussian z pass
-    # at every level, and in a kernel of its own at every level (the default
-    # takes the kernel of its own on levels of at least 4 Mi voxels)
-    fused = time_plain(disc, torch, w, dist, steps=min(args.steps, 3), warmup=1, pair_dev=(ct, cbct),
-                       switches=disc.SW_FUSED_WARP)
+    # the same schedule with the next iteration's warp in a kernel of its own
+    # at every level (the default runs it inside the Gaussian's xy pass)
     sep = time_plain(disc, torch, w, dist, steps=min(args.steps, 3), warmup=1, pair_dev=(ct, cbct),
                      switches=disc.SW_SEPARATE_WARP)
-    warp_placement = {"default_ms": ms, "fused_in_gauss_z_everywhere_ms": fused["ms_per_step"],
+    warp_placement = {"default_fused_in_gauss_xy_ms": ms,
                       "separate_kernel_everywhere_ms": sep["ms_per_step"],
-                      "what": "whole schedule: the warp of I_m by the new field inside the Gaussian z pass, or "
-                              "as a kernel of its own after it (a thread marches a column in z and loads the "
-                              "field two planes ahead of its gathers); the default picks per level"}
+                      "what": "whole schedule: the warp of I_m by the new field inside the Gaussian's last "
+                              "pass (the xy pass, r in registers), or as a kernel of its own after the "
+                              "Gaussian (a thread marches a column in z and loads the field two planes ahead "
+                              "of its gathers)"}
     batched = None if args.no_batched else time_batched(disc, torch, dist)
     masked = time_masked(disc, torch, w, (ct, cbct), dist)
     mixed = (time_mixed_batch(disc, torch, w, (ct, cbct), dist)
@@ -866,9 +864,9 @@ def run_profile_once(w):
     """One launch of each per-iteration kernel at the finest level (for ncu captures).
 
     Launch order: static patch normalisation, warp, box pass (iteration mode),
-    Gaussian xy pass, Gaussian z pass; then a one-level context's set-up and
-    two iterations (warp, then per iteration the box pass, the Gaussian xy
-    pass, the Gaussian z pass with the fused warp and the norm).
+    Gaussian z pass, Gaussian xy pass; then a one-level context's set-up and
+    two iterations (warp, then per iteration the box pass, the Gaussian z
+    pass, the Gaussian xy pass with the fused warp and the norm).
     """
     import torch
     from paper_1204_6295_b300 import disc

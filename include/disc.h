@@ -315,13 +315,14 @@ disc_status disc_batch_get_tuning(disc_batch* b, int32_t level, int32_t* items, 
  * before the level has run. */
 disc_status disc_batch_get_box_path(disc_batch* b, int32_t level, int32_t* tma);
 
-/* Tuning of `level`'s Gaussian z pass and warp (Algorithm A1 step 6 and the
- * warp of step 1 for the next iteration): *zlen = the z chunk length of the
- * z pass (0: each pair's single-pair plan; else chunks of that many planes,
- * capped at each pair's depth) and *separate_warp = 1 when the warp runs as
- * the z-marching warp kernel after the z pass, 0 when it runs inside it.  At
- * the level's first iteration the tuner times the xy and z passes (and the
- * warp) on scratch copies of r and m for chunks of the pairs' plans, 16, 32
+/* Tuning of `level`'s Gaussian and warp (Algorithm A1 step 6 and the warp of
+ * step 1 for the next iteration): *zlen = the z chunk length of the Gaussian's
+ * z pass, its first (0: each pair's single-pair plan; else chunks of that many
+ * planes, capped at each pair's depth) and *separate_warp = 1 when the warp
+ * runs as the z-marching warp kernel after the Gaussian, 0 when it runs inside
+ * its last pass, the xy pass.  At the level's first iteration the tuner times
+ * the z and xy passes (and the warp) on scratch copies of r and m for chunks
+ * of the pairs' plans, 16, 32
  * and 64 planes, with either placement, and keeps the default (fused, the
  * plans) unless a choice is at least 2% faster.  Bitwise neutral: every output
  * is the same sum in the same order either way.  Either output may be NULL.
@@ -567,9 +568,9 @@ disc_status disc_k_check_error(void* stream);
  *   DISC_SW_SEPARATE_WARP   contexts created afterwards warp I_m for the next
  *                           iteration in a kernel of its own after the
  *                           Gaussian at every level (same results);
- *   DISC_SW_FUSED_WARP      ... inside the Gaussian z pass at every level (by
- *                           default levels of at least 4 Mi voxels take the
- *                           separate kernel, smaller ones the fused form);
+ *   DISC_SW_FUSED_WARP      ... inside the Gaussian's xy pass at every level
+ *                           (the default; in a batch it also keeps the
+ *                           tuner from choosing the separate kernel);
  *   DISC_SW_WIDE_ANY        iteration passes planned afterwards take the
  *                           wide-tile kernel wherever it applies, whatever the
  *                           volume's size (same results; the planner otherwise

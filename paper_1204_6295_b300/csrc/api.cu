@@ -354,7 +354,7 @@ cudaError_t queue_iterations(disc_ctx* c, int l, int n, const LoopCond* loop) {
   g.r = v.r;
   g.t = v.t;
   g.Im = v.Im;
-  g.m = v.sep_warp ? nullptr : v.m;   // the z pass also warps I_m for the next iteration
+  g.m = v.sep_warp ? nullptr : v.m;   // the xy pass also warps I_m for the next iteration
   g.add = c->p.smooth_mode ? v.r : nullptr;   // r <- r + G * dr (Sec. 2.1 order)
   g.stop = c->d_stop + l;
   g.nx = v.nx;
@@ -370,7 +370,7 @@ cudaError_t queue_iterations(disc_ctx* c, int l, int n, const LoopCond* loop) {
   }
   const int nparts = (int)(v.pa.grid.x * v.pa.grid.y * v.pa.grid.z);
   // m for the field the first iteration starts from; later iterations get it
-  // from the fused warp of the Gaussian z pass
+  // from the fused warp of the Gaussian xy pass
   if (!loop) {
     cudaError_t e0 = launch_warp(v.Im, v.r, v.m, v.nx, v.ny, v.nz, c->d_stop + l, c->s);
     if (e0 != cudaSuccess) return e0;
@@ -708,7 +708,7 @@ disc_status disc_create(const disc_params* p, int device, void* cuda_stream, dis
   // the loop graph pays a few microseconds per iteration for its condition; it
   // is used where it saves work, when the stop rule can end a level early
   ctx->use_loop = p->stop_eps > 0.0f && (sw & DISC_SW_UNROLLED_GRAPH) == 0u;
-  ctx->separate_warp = (sw & DISC_SW_SEPARATE_WARP) ? 1 : ((sw & DISC_SW_FUSED_WARP) ? 0 : -1);
+  ctx->separate_warp = (sw & DISC_SW_SEPARATE_WARP) ? 1 : 0;
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
   cudaError_t e = cudaStreamCreateWithFlags(&ctx->s, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
@@ -784,7 +784,7 @@ disc_status disc_set_images(disc_ctx* ctx, const float* ct, const float* cbct, i
       v.pa = box_plan_iter(v.nx, v.ny, v.nz, ctx->hx, ctx->hy, ctx->hz, ctx->num_sms, nullptr, nullptr, nullptr);
       v.pn = box_plan(kModeIterate, v.nx, v.ny, v.nz, ctx->hx, ctx->hy, ctx->hz, ctx->num_sms);
       v.pb = gauss_plan(v.nx, v.ny, v.nz, ctx->R, ctx->num_sms);
-      v.sep_warp = ctx->separate_warp >= 0 ? ctx->separate_warp == 1 : v.N >= kSeparateWarpVoxels;
+      v.sep_warp = ctx->separate_warp == 1;
       BoxPlan ps = box_plan(kModeStatic, v.nx, v.ny, v.nz, ctx->hx, ctx->hy, ctx->hz, ctx->num_sms);
       if (v.pa.grid.x == 0 || v.pb.grid.x == 0 || ps.grid.x == 0) {
         free_levels(ctx);

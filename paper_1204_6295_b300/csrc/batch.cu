@@ -3,7 +3,7 @@
 // Each pair keeps its own registration context (buffers, pyramid, CBCT patch
 // statistics, field), but an iteration of all pairs is four launches in total
 // instead of four per pair: the moment/force pass, the Gaussian xy pass, the
-// Gaussian z pass (with the next warp) and the norm, each over a work table
+// Gaussian (with the next warp) and the norm, each over a work table
 // that concatenates the CTA grids of every pair.  A level's iterations are
 // captured once as a CUDA graph and replayed.  The moment/force launch is
 // tuned per level at its first use: the z-chunk length of every pair's tiles
@@ -41,7 +41,7 @@ struct disc_batch {
   int xy_total[DISC_MAX_LEVELS] = {}, z_total[DISC_MAX_LEVELS] = {}, warp_total[DISC_MAX_LEVELS] = {};
   // the Gaussian z pass and the warp of the next iteration, tuned per level:
   // z chunk length (0: each pair's single-pair plan) and whether the warp runs
-  // in the z pass or as the z-marching warp kernel after it (table warpz)
+  // in the xy pass or as the z-marching warp kernel after it (table warpz)
   int gauss_zlen[DISC_MAX_LEVELS] = {};
   bool sep_warp[DISC_MAX_LEVELS] = {};
   WarpBatch warpz[DISC_MAX_LEVELS];
@@ -220,10 +220,9 @@ void make_wide_norm_table(disc_batch* b, int l, int grid) {
   }
 }
 
-// Gaussian z-pass table of level l with chunks of `zlen` planes (0: each
-// pair's single-pair plan), writing r and m to the given buffers (per pair;
-// NULL: the pair's own).
-int make_z_table(disc_batch* b, int l, int zlen, GaussBatch& z, float* const* r_to, float* const* m_to) {
+// Gaussian z-pass table of level l (u -> t) with chunks of `zlen` planes (0:
+// each pair's single-pair plan).
+int make_z_table(disc_batch* b, int l, int zlen, GaussBatch& z) {
   std::memset(&z, 0, sizeof(z));
   z.count = b->npairs;
   int oz = 0;
@@ -231,13 +230,10 @@ int make_z_table(disc_batch* b, int l, int zlen, GaussBatch& z, float* const* r_
     const disc_ctx* c = b->pair[i];
     const Level& v = c->lev[l];
     GaussArgs g = ctx_gauss_args(c, l);
-    g.u = g.t;                   // z pass: t -> r (and m)
+    g.r = g.t;
+    g.add = nullptr;
+    g.m = nullptr;
     if (zlen > 0) g.zlen = zlen < v.nz ? zlen : v.nz;
-    if (r_to) {
-      g.r = r_to[i];
-      if (g.add) g.add = r_to[i];
-    }
-    if (m_to) g.m = m_to[i];
     z.args[i] = g;
     GaussPlan pl = v.pb;
     pl.zlen = g.zlen;
@@ -248,6 +244,33 @@ int make_z_table(disc_batch* b, int l, int zlen, GaussBatch& z, float* const* r_
   }
   z.offset[b->npairs] = oz;
   return oz;
+}
+
+// Gaussian xy-pass table of level l (t -> r = add + G u; m = I_m(x + r) when
+// `fused`), writing r and m to the given buffers (per pair; NULL: the pair's
+// own).
+int make_xy_table(disc_batch* b, int l, bool fused, GaussBatch& xy, float* const* r_to, float* const* m_to) {
+  std::memset(&xy, 0, sizeof(xy));
+  xy.count = b->npairs;
+  int oxy = 0;
+  for (int i = 0; i < b->npairs; ++i) {
+    const disc_ctx* c = b->pair[i];
+    const Level& v = c->lev[l];
+    GaussArgs g = ctx_gauss_args(c, l);
+    g.u = g.t;
+    if (r_to) {
+      g.r = r_to[i];
+      if (g.add) g.add = r_to[i];
+    }
+    g.m = fused ? (m_to ? m_to[i] : v.m) : nullptr;
+    xy.args[i] = g;
+    dim3 gz;
+    gauss_grids(v.nx, v.ny, v.nz, v.pb, &xy.grid[i], &gz);
+    xy.offset[i] = oxy;
+    oxy += (int)(xy.grid[i].x * xy.grid[i].y * xy.grid[i].z);
+  }
+  xy.offset[b->npairs] = oxy;
+  return oxy;
 }
 
 // Batched z-marching warp table of level l (m from the given r per pair; NULL:
@@ -274,30 +297,13 @@ int make_warpz_table(disc_batch* b, int l, WarpBatch& w, float* const* r_from, f
 }
 
 void build_tables(disc_batch* b, int l) {
-  GaussBatch& xy = b->xy[l];
-  GaussBatch& z = b->zt[l];
   WarpBatch& w = b->warp[l];
-  std::memset(&xy, 0, sizeof(xy));
-  std::memset(&z, 0, sizeof(z));
   std::memset(&w, 0, sizeof(w));
-  xy.count = z.count = w.count = b->npairs;
-  int oxy = 0, oz = 0, ow = 0;
+  w.count = b->npairs;
+  int ow = 0;
   for (int i = 0; i < b->npairs; ++i) {
     const disc_ctx* c = b->pair[i];
     const Level& v = c->lev[l];
-    const GaussArgs g = ctx_gauss_args(c, l);
-    dim3 gxy, gz;
-    gauss_grids(v.nx, v.ny, v.nz, v.pb, &gxy, &gz);
-    xy.args[i] = g;
-    xy.args[i].r = g.t;          // xy pass: u -> t
-    z.args[i] = g;
-    z.args[i].u = g.t;           // z pass: t -> r (and m)
-    xy.grid[i] = gxy;
-    z.grid[i] = gz;
-    xy.offset[i] = oxy;
-    z.offset[i] = oz;
-    oxy += (int)(gxy.x * gxy.y * gxy.z);
-    oz += (int)(gz.x * gz.y * gz.z);
     w.offset[i] = ow;
     w.Im[i] = v.Im;
     w.r[i] = v.r;
@@ -308,24 +314,22 @@ void build_tables(disc_batch* b, int l) {
     w.stop[i] = c->d_stop + l;
     ow += ((v.nx + kWarpBatchThreads - 1) / kWarpBatchThreads) * v.ny * v.nz;
   }
-  xy.offset[b->npairs] = oxy;
-  z.offset[b->npairs] = oz;
   w.offset[b->npairs] = ow;
-  b->xy_total[l] = oxy;
-  b->z_total[l] = oz;
   b->warp_total[l] = ow;
   b->gauss_zlen[l] = 0;
-  b->sep_warp[l] = false;
+  b->sep_warp[l] = (test_switches() & DISC_SW_SEPARATE_WARP) != 0;
+  b->z_total[l] = make_z_table(b, l, 0, b->zt[l]);
+  b->xy_total[l] = make_xy_table(b, l, !b->sep_warp[l], b->xy[l], nullptr, nullptr);
   b->warpz_total[l] = make_warpz_table(b, l, b->warpz[l], nullptr, nullptr);
 }
 
-// Tuner of the Gaussian z pass and the warp placement at level l: the xy pass
-// and the z pass (with the warp fused, or followed by the z-marching warp
-// kernel) for z chunks of each pair's plan, 16, 32 and 64 planes, timed on
-// scratch copies of r and m so that the level's state is untouched (the xy
-// pass writes only t, which every iteration overwrites).  The default (fused,
-// the pairs' plans) is replaced only by a choice at least 2% faster.  The test
-// switches DISC_SW_SEPARATE_WARP / DISC_SW_FUSED_WARP fix the placement.
+// Tuner of the Gaussian z pass and the warp placement at level l: the z pass
+// for z chunks of each pair's plan, 16, 32 and 64 planes, then the xy pass with
+// the warp fused, or followed by the z-marching warp kernel, timed on scratch
+// copies of r and m so that the level's state is untouched (the z pass writes
+// only t, which every iteration overwrites).  The default (fused, the pairs'
+// plans) is replaced only by a choice at least 2% faster.  The test switches
+// DISC_SW_SEPARATE_WARP / DISC_SW_FUSED_WARP fix the placement.
 cudaError_t tune_gauss(disc_batch* b, int l) {
   size_t total = 0;
   for (int i = 0; i < b->npairs; ++i) total += 4 * b->pair[i]->lev[l].N;
@@ -349,22 +353,25 @@ cudaError_t tune_gauss(disc_batch* b, int l) {
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   GaussBatch* zt_p = new (std::nothrow) GaussBatch;
+  GaussBatch* xt_p = new (std::nothrow) GaussBatch;
   WarpBatch* wt_p = new (std::nothrow) WarpBatch;
-  if (e == cudaSuccess && (!zt_p || !wt_p)) e = cudaErrorMemoryAllocation;
+  if (e == cudaSuccess && (!zt_p || !xt_p || !wt_p)) e = cudaErrorMemoryAllocation;
   GaussBatch& zt = *zt_p;
+  GaussBatch& xt = *xt_p;
   WarpBatch& wt = *wt_p;
   const int zlens[4] = {0, 16, 32, 64};
   float best = 1e30f, deflt = 1e30f;
   int best_zlen = 0, best_sep = place_lo;
   for (int place = place_lo; place <= place_hi && e == cudaSuccess; ++place) {
     const int wtot = make_warpz_table(b, l, wt, r_to, m_to);
+    const int xtot = make_xy_table(b, l, place == 0, xt, r_to, m_to);
     for (int zi = 0; zi < 4 && e == cudaSuccess; ++zi) {
-      const int ztot = make_z_table(b, l, zlens[zi], zt, r_to, m_to);
+      const int ztot = make_z_table(b, l, zlens[zi], zt);
       float ms = 0.0f;
       for (int k = 0; k < 4 && e == cudaSuccess; ++k) {   // one warm-up, three timed
         if (k == 1) e = cudaEventRecord(e0, b->s);
         if (e == cudaSuccess)
-          e = gauss_launch_batch(b->xy[l], b->xy_total[l], zt, ztot, b->R, place == 0, b->s);
+          e = gauss_launch_batch(xt, xtot, zt, ztot, b->R, place == 0, b->s);
         if (e == cudaSuccess && place == 1) e = launch_warp_z_batch(wt, wtot, b->s);
       }
       if (e == cudaSuccess) e = cudaEventRecord(e1, b->s);
@@ -382,6 +389,7 @@ cudaError_t tune_gauss(disc_batch* b, int l) {
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   delete zt_p;
+  delete xt_p;
   delete wt_p;
   const cudaError_t ef = cudaFreeAsync(scratch, b->s);
   if (e == cudaSuccess) e = ef;
@@ -392,7 +400,8 @@ cudaError_t tune_gauss(disc_batch* b, int l) {
   }
   b->gauss_zlen[l] = best_zlen;
   b->sep_warp[l] = best_sep != 0;
-  b->z_total[l] = make_z_table(b, l, best_zlen, b->zt[l], nullptr, nullptr);
+  b->z_total[l] = make_z_table(b, l, best_zlen, b->zt[l]);
+  b->xy_total[l] = make_xy_table(b, l, !b->sep_warp[l], b->xy[l], nullptr, nullptr);
   return cudaSuccess;
 }
 

@@ -67,13 +67,6 @@ struct Level {
   bool sep_warp = false;             // this level's warp runs in its own kernel
 };
 
-// Levels this large warp I_m in a kernel of their own (k_warp_z: the field is
-// loaded two planes ahead of the gathers) rather than inside the Gaussian z
-// pass, whose register queue leaves too few warps to hide the gathers: the
-// separate kernel measured 5.6% faster per iteration at 512x512x256 and 4% at
-// 256x256x128, and slower at 128x128x64 and below.
-constexpr size_t kSeparateWarpVoxels = (size_t)4 << 20;
-
 
 }  // namespace disc
 
@@ -109,9 +102,9 @@ struct disc_ctx {
   bool use_loop = true;      // conditional-node loop graphs (with a stop rule; else unrolled graphs)
   long long launches = 0;    // kernels disc_iterate has launched (disc_get_launch_count); -1: not kept
   // where the next iteration's warp runs: 1 in a kernel of its own after the
-  // Gaussian (levels of at least kSeparateWarpVoxels voxels), 0 inside the
-  // Gaussian z pass; -1 decides per level
-  int separate_warp = -1;
+  // Gaussian, 0 (the default) inside the Gaussian's last pass, the xy pass,
+  // which holds r in registers and gathers I_m tile by tile
+  int separate_warp = 0;
 };
 
 

@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(kThreads) k_gauss(GaussArgs a) {
 constexpr int kSX = 32;        // xy tile
 constexpr int kSY = 32;
 constexpr int kZThreads = 128; // z kernel: a CTA is kZX columns along x by kZY rows
-constexpr int kZX = 32, kZY = kZThreads / kZX;   // (the rows' warps share I_m rows in L1 for the warp)
+constexpr int kZX = 32, kZY = kZThreads / kZX;
 constexpr int kZCtasPerSM = 4;  // z kernel CTAs resident per SM (its launch bound)
 constexpr int kBX = 4;         // x outputs per x-filter task
 constexpr int kBY = 4;         // y outputs per thread in the y filter
@@ -177,7 +177,11 @@ struct XYLayout {
   static constexpr size_t bytes = o_xz + 4 * (size_t)IY * XP;
 };
 
-template <int R>
+// The xy pass is the last of the two passes: it writes r (r = add + G u when
+// a.add is set, in place) and, with WARP, m = I_m(x + r(x)) for the next
+// iteration while r is in registers (WARP 1: 32-bit sample indices, for volumes
+// of fewer than 2^31 voxels; WARP 2: 64-bit).
+template <int R, int WARP = 0>
 __device__ __forceinline__ void gauss_xy_body(const GaussArgs& a, int bx, int by, int bz) {
   using X = XYLayout<R>;
   if (a.stop != nullptr && *(volatile const int*)a.stop != 0) return;
@@ -325,19 +329,31 @@ __device__ __forceinline__ void gauss_xy_body(const GaussArgs& a, int bx, int by
           }
         }
         const size_t g = (size_t)gy * nx + gx;
+        if (a.add) {                          // r = r_prev + G * dr (in place: same element)
+          const float* ap = a.add + (t - a.r) + g;
+          acc[b].x += DISC_IN(ap - a.add, 3LL * N) ? ap[0] : 0.0f;
+          acc[b].y += DISC_IN(ap + N - a.add, 3LL * N) ? ap[N] : 0.0f;
+          accz[b] += DISC_IN(ap + 2 * N - a.add, 3LL * N) ? ap[2 * N] : 0.0f;
+        }
         st_at(t + g, a.r, 3LL * N, acc[b].x);
         st_at(t + N + g, a.r, 3LL * N, acc[b].y);
         st_at(t + 2 * N + g, a.r, 3LL * N, accz[b]);
+        if (WARP == 1)
+          st_at(a.m + (size_t)z * plane + g, a.m, (long long)N,
+                warp_at32(a.Im, gx, gy, z, acc[b].x, acc[b].y, accz[b], nx, ny, a.nz));
+        else if (WARP == 2)
+          st_at(a.m + (size_t)z * plane + g, a.m, (long long)N,
+                warp_at(a.Im, gx, gy, z, acc[b].x, acc[b].y, accz[b], nx, ny, a.nz));
       }
     }
   }
 }
 
-template <int R>
+template <int R, int WARP>
 __global__ void __launch_bounds__(kThreads) k_gauss_xy(GaussArgs a) {
   pdl_wait();
   pdl_release();
-  gauss_xy_body<R>(a, blockIdx.x, blockIdx.y, blockIdx.z);
+  gauss_xy_body<R, WARP>(a, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // Work item i of a batched launch -> (volume p, CTA coordinates in p's grid).
@@ -347,7 +363,7 @@ __device__ __forceinline__ int batch_find(const int* offset, int count, int i) {
   return p;
 }
 
-template <int R>
+template <int R, int WARP>
 __global__ void __launch_bounds__(kThreads) k_gauss_xy_batch(const __grid_constant__ GaussBatch bt) {
   pdl_wait();
   pdl_release();
@@ -355,11 +371,11 @@ __global__ void __launch_bounds__(kThreads) k_gauss_xy_batch(const __grid_consta
   const int p = batch_find(bt.offset, bt.count, i);
   const int j = i - bt.offset[p];
   const dim3 g = bt.grid[p];
-  gauss_xy_body<R>(bt.args[p], j % g.x, (j / g.x) % g.y, j / (g.x * g.y));
+  gauss_xy_body<R, WARP>(bt.args[p], j % g.x, (j / g.x) % g.y, j / (g.x * g.y));
 }
 
-// z pass with a register queue; WARP also evaluates m = I_m(x + r(x)).
-template <int R, bool WARP>
+// z pass with a register queue (the first of the two passes: u -> t).
+template <int R>
 __device__ __forceinline__ void gauss_z_body(const GaussArgs& a, int bx, int by, int bz) {
   constexpr int KZ = 2 * R + 1;
   if (a.stop != nullptr && *(volatile const int*)a.stop != 0) return;
@@ -374,7 +390,7 @@ __device__ __forceinline__ void gauss_z_body(const GaussArgs& a, int bx, int by,
 #pragma unroll
   for (int k = 0; k < KZ; ++k) w[k] = a.w[k];
   const size_t col = (size_t)y * nx + x;
-  const float* t = a.u + col;       // t = G_y G_x u, [3][N]
+  const float* t = a.u + col;       // the input column, [3][N]
   float2 q2[KZ];                    // pending outputs, (x, y) components
   float qz[KZ];
 #pragma unroll
@@ -423,18 +439,9 @@ __device__ __forceinline__ void gauss_z_body(const GaussArgs& a, int bx, int by,
           oz = oz / nrm;
         }
         float* rp = rb + (size_t)j * plane;
-        if (a.add) {                          // r = r_prev + G * dr (in place: same element)
-          const float* ap = a.add + (rp - a.r);
-          o2.x += DISC_IN(ap - a.add, 3LL * N) ? ap[0] : 0.0f;
-          o2.y += DISC_IN(ap + N - a.add, 3LL * N) ? ap[N] : 0.0f;
-          oz += DISC_IN(ap + 2 * N - a.add, 3LL * N) ? ap[2 * N] : 0.0f;
-        }
         st_at(rp, a.r, 3LL * N, o2.x);
         st_at(rp + N, a.r, 3LL * N, o2.y);
         st_at(rp + 2 * N, a.r, 3LL * N, oz);
-        if (WARP)
-          st_at(a.m + (size_t)zo * plane + col, a.m, (long long)N,
-                warp_at(a.Im, x, y, zo, o2.x, o2.y, oz, nx, ny, nz));
       }
       q2[so] = make_float2(0.0f, 0.0f);
       qz[so] = 0.0f;
@@ -442,14 +449,14 @@ __device__ __forceinline__ void gauss_z_body(const GaussArgs& a, int bx, int by,
   }
 }
 
-template <int R, bool WARP>
+template <int R>
 __global__ void __launch_bounds__(kZThreads, kZCtasPerSM) k_gauss_z(GaussArgs a) {
   pdl_wait();
   pdl_release();
-  gauss_z_body<R, WARP>(a, blockIdx.x, blockIdx.y, blockIdx.z);
+  gauss_z_body<R>(a, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
-template <int R, bool WARP>
+template <int R>
 __global__ void __launch_bounds__(kZThreads, kZCtasPerSM) k_gauss_z_batch(const __grid_constant__ GaussBatch bt) {
   pdl_wait();
   pdl_release();
@@ -457,9 +464,21 @@ __global__ void __launch_bounds__(kZThreads, kZCtasPerSM) k_gauss_z_batch(const 
   const int p = batch_find(bt.offset, bt.count, i);
   const int j = i - bt.offset[p];
   const dim3 g = bt.grid[p];
-  gauss_z_body<R, WARP>(bt.args[p], j % g.x, (j / g.x) % g.y, j / (g.x * g.y));
+  gauss_z_body<R>(bt.args[p], j % g.x, (j / g.x) % g.y, j / (g.x * g.y));
 }
 
+// Index width of the fused warp: 32-bit gathers while every index of I_m fits.
+inline int warp_kind(long long voxels) { return voxels < (1LL << 31) ? 1 : 2; }
+
+template <class K>
+cudaError_t set_xy_attrs(K k, size_t bytes) {
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              (int)cudaSharedmemCarveoutMaxShared);
+}
+
+// Batched z pass (u -> t) then batched xy pass (t -> r, with add and warp).
 template <int R>
 cudaError_t launch_batch_r(const GaussBatch& xy, int xy_total, const GaussBatch& z, int z_total, bool warp,
                            cudaStream_t s) {
@@ -469,23 +488,28 @@ cudaError_t launch_batch_r(const GaussBatch& xy, int xy_total, const GaussBatch&
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (!set[dev]) {
-    e = cudaFuncSetAttribute(k_gauss_xy_batch<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)XYLayout<R>::bytes);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_gauss_xy_batch<R>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             (int)cudaSharedmemCarveoutMaxShared);
-    if (e != cudaSuccess) return e;
+    if ((e = set_xy_attrs(k_gauss_xy_batch<R, 0>, XYLayout<R>::bytes)) != cudaSuccess) return e;
+    if ((e = set_xy_attrs(k_gauss_xy_batch<R, 1>, XYLayout<R>::bytes)) != cudaSuccess) return e;
+    if ((e = set_xy_attrs(k_gauss_xy_batch<R, 2>, XYLayout<R>::bytes)) != cudaSuccess) return e;
     set[dev] = 1;
   }
-  if (xy_total > 0) e = launch_pdl(k_gauss_xy_batch<R>, dim3(xy_total), dim3(kThreads), XYLayout<R>::bytes, s, xy);
-  if (e != cudaSuccess) return e;
-  if (z_total > 0) {
-    if (warp) return launch_pdl(k_gauss_z_batch<R, true>, dim3(z_total), dim3(kZThreads), 0, s, z);
-    return launch_pdl(k_gauss_z_batch<R, false>, dim3(z_total), dim3(kZThreads), 0, s, z);
+  if (z_total > 0) e = launch_pdl(k_gauss_z_batch<R>, dim3(z_total), dim3(kZThreads), 0, s, z);
+  if (e != cudaSuccess || xy_total <= 0) return e;
+  if (!warp) return launch_pdl(k_gauss_xy_batch<R, 0>, dim3(xy_total), dim3(kThreads), XYLayout<R>::bytes, s, xy);
+  long long voxels = 0;
+  for (int p = 0; p < xy.count; ++p) {
+    const long long n = (long long)xy.args[p].nx * xy.args[p].ny * xy.args[p].nz;
+    if (n > voxels) voxels = n;
   }
-  return cudaSuccess;
+  if (warp_kind(voxels) == 1)
+    return launch_pdl(k_gauss_xy_batch<R, 1>, dim3(xy_total), dim3(kThreads), XYLayout<R>::bytes, s, xy);
+  return launch_pdl(k_gauss_xy_batch<R, 2>, dim3(xy_total), dim3(kThreads), XYLayout<R>::bytes, s, xy);
 }
 
+// z pass (u -> t) then xy pass (t -> r = add + G u, and m = I_m(x + r) when a.m
+// is set).  The xy pass runs last so that the add and the warp see r in
+// registers: it already stages its planes through shared memory, and its tile
+// of 32 x 32 voxels keeps the warp's gathers of one plane close together.
 template <int R>
 cudaError_t launch_split(const GaussArgs& a, const GaussPlan& p, cudaStream_t s) {
   static int set[64] = {};
@@ -494,27 +518,28 @@ cudaError_t launch_split(const GaussArgs& a, const GaussPlan& p, cudaStream_t s)
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (!set[dev]) {
-    e = cudaFuncSetAttribute(k_gauss_xy<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)XYLayout<R>::bytes);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_gauss_xy<R>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             (int)cudaSharedmemCarveoutMaxShared);
-    if (e != cudaSuccess) return e;
+    if ((e = set_xy_attrs(k_gauss_xy<R, 0>, XYLayout<R>::bytes)) != cudaSuccess) return e;
+    if ((e = set_xy_attrs(k_gauss_xy<R, 1>, XYLayout<R>::bytes)) != cudaSuccess) return e;
+    if ((e = set_xy_attrs(k_gauss_xy<R, 2>, XYLayout<R>::bytes)) != cudaSuccess) return e;
     set[dev] = 1;
   }
-  // xy: u -> t
-  GaussArgs xy = a;
-  xy.r = a.t;
-  dim3 gxy((a.nx + kSX - 1) / kSX, (a.ny + kSY - 1) / kSY, a.nz);
-  e = launch_pdl(k_gauss_xy<R>, gxy, dim3(kThreads), XYLayout<R>::bytes, s, xy);
-  if (e != cudaSuccess) return e;
-  // z: t -> r (and m)
+  // z: u -> t
   GaussArgs zz = a;
-  zz.u = a.t;
+  zz.r = a.t;
+  zz.add = nullptr;
+  zz.m = nullptr;
   zz.zlen = p.zlen;
   dim3 gz((a.nx + kZX - 1) / kZX, (a.ny + kZY - 1) / kZY, (a.nz + p.zlen - 1) / p.zlen);
-  if (a.m != nullptr) return launch_pdl(k_gauss_z<R, true>, gz, dim3(kZThreads), 0, s, zz);
-  return launch_pdl(k_gauss_z<R, false>, gz, dim3(kZThreads), 0, s, zz);
+  e = launch_pdl(k_gauss_z<R>, gz, dim3(kZThreads), 0, s, zz);
+  if (e != cudaSuccess) return e;
+  // xy: t -> r (and m)
+  GaussArgs xy = a;
+  xy.u = a.t;
+  dim3 gxy((a.nx + kSX - 1) / kSX, (a.ny + kSY - 1) / kSY, a.nz);
+  if (a.m == nullptr) return launch_pdl(k_gauss_xy<R, 0>, gxy, dim3(kThreads), XYLayout<R>::bytes, s, xy);
+  if (warp_kind((long long)a.nx * a.ny * a.nz) == 1)
+    return launch_pdl(k_gauss_xy<R, 1>, gxy, dim3(kThreads), XYLayout<R>::bytes, s, xy);
+  return launch_pdl(k_gauss_xy<R, 2>, gxy, dim3(kThreads), XYLayout<R>::bytes, s, xy);
 }
 
 cudaError_t launch_split_any(const GaussArgs& a, const GaussPlan& p, cudaStream_t s) {

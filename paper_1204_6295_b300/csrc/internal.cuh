@@ -223,7 +223,7 @@ cudaError_t launch_warp(const float* Im, const float* r, float* m, int nx, int n
 struct GaussArgs {
   const float* u;       // [3][N] input field
   float* r;             // [3][N] smoothed field
-  float* t;             // [3][N] scratch: the xy-filtered field (split kernels)
+  float* t;             // [3][N] scratch: the z-filtered field (split kernels)
   const float* Im;      // moving image, for the fused warp (may be NULL)
   float* m;             // if non-NULL: m = I_m(x + r(x)) is written too
   const int* stop;
@@ -231,7 +231,7 @@ struct GaussArgs {
   int R;
   int zlen;
   int box_sum;          // 1: plain truncated sums (no renormalisation at the borders)
-  const float* add;     // optional [3][N]: the z pass writes r = add + G * u (add may be r itself)
+  const float* add;     // optional [3][N]: the last pass writes r = add + G * u (add may be r itself)
   float w[2 * DISC_MAX_GAUSS_RADIUS + 1];   // normalised taps (sum 1), or all 1 for box sums
 };
 struct GaussPlan {
@@ -246,9 +246,10 @@ struct GaussBatch {
   dim3 grid[kMaxBatch];
   GaussArgs args[kMaxBatch];
 };
-// Batched Gaussian passes over many volumes (gauss.cu): the xy pass (u -> t) and
-// the z pass (t -> r, and m if args.m) with one launch each.  Work items follow
-// each volume's own grids (xy: tiles x planes; z: column blocks x rows x chunks).
+// Batched Gaussian passes over many volumes (gauss.cu): the z pass (u -> t) and
+// the xy pass (t -> r = add + G u, and m when warp) with one launch each.  Work
+// items follow each volume's own grids (xy: tiles x planes; z: column blocks x
+// rows x chunks).
 cudaError_t gauss_launch_batch(const GaussBatch& xy, int xy_total, const GaussBatch& z, int z_total,
                                int R, bool warp, cudaStream_t s);
 void gauss_grids(int nx, int ny, int nz, const GaussPlan& p, dim3* xy, dim3* z);

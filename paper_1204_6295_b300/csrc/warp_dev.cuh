@@ -1,5 +1,5 @@
 // Trilinear sampling of the moving image, shared by the warp kernel and the
-// fused Gaussian z pass: m(x) = I_m(x + r(x)) with the sample position clamped
+// fused Gaussian xy pass: m(x) = I_m(x + r(x)) with the sample position clamped
 // to the volume (Sec. 2.1; Sec. 2.3 kernel 5).
 #pragma once
 

@@ -471,7 +471,7 @@ class Batch:
         return self.box_path(level) == 1
 
     def gauss_tuning(self, level):
-        """(z chunk of the Gaussian z pass, 0 = pair plans; 1 if the warp runs after it) at `level`."""
+        """(z chunk of the Gaussian z pass, 0 = pair plans; 1 if the warp runs after the Gaussian) at `level`."""
         zlen, sep = _i32(0), _i32(0)
         _check(_lib.disc_batch_get_gauss_tuning(self._h, int(level), ctypes.byref(zlen), ctypes.byref(sep)),
                "disc_batch_get_gauss_tuning")

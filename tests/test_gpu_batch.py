@@ -144,8 +144,8 @@ def test_batched_tuner_picks_a_tiling(disc, tma_pairs, tma_single):
 
 @pytest.mark.parametrize("switch,separate", [("SW_SEPARATE_WARP", 1), ("SW_FUSED_WARP", 0), (None, None)])
 def test_batched_warp_placement_and_z_chunks(disc, tma_pairs, tma_single, switch, separate):
-    """The Gaussian z pass and warp tuner: the warp inside the z pass or as the
-    z-marching warp kernel after it (forced by the test switches, or chosen by
+    """The Gaussian z pass and warp tuner: the warp inside the xy pass or as the
+    z-marching warp kernel after the Gaussian (forced by the test switches, or chosen by
     the tuner), z chunks of any length; the fields stay the single-pair ones."""
     sw = getattr(disc, switch) if switch else 0
     with disc.test_switches(sw):
@@ -225,7 +225,7 @@ def test_batched_masked_pairs_equal_single_pair_runs(disc, pairs):
 
 
 def test_batched_sec21_order_and_warp_placements(disc, tma_pairs):
-    """smooth_mode 1 (r <- r + G * dr, Sec. 2.1) in a batch: the z pass adds into r
+    """smooth_mode 1 (r <- r + G * dr, Sec. 2.1) in a batch: the xy pass adds into r
     in place, also when the tuner times it on scratch copies; each field equals
     its single-pair run whatever the warp placement."""
     kw = dict(TMA_KW, smooth_mode=1)

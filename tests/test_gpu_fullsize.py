@@ -2,7 +2,7 @@
 
 1. Full volumes, in the launch configuration the benchmark times. The registration
    context runs two iterations on the whole volume (the wide-tile iteration pass,
-   the unfused Gaussian z pass and the z-marching warp: the finest level's kernels).
+   the Gaussian z pass and the xy pass with the fused warp: the finest level's kernels).
    Sampled voxels are checked against the FP64 oracle run on a crop that contains
    everything those voxels depend on after two iterations: the Gaussian radius, the
    patch half size, the gradient stencil and the warp displacement, twice. Where they

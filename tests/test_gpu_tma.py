@@ -48,7 +48,7 @@ def _SeparateWarp():
 
 
 def _FusedWarp():
-    """The next iteration's warp inside the Gaussian z pass at every level."""
+    """The next iteration's warp inside the Gaussian xy pass at every level."""
     from paper_1204_6295_b300 import disc
     return disc.test_switches(disc.SW_FUSED_WARP)
 
