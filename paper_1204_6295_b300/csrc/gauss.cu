@@ -136,13 +136,14 @@ __global__ void __launch_bounds__(kThreads) k_gauss(GaussArgs a) {
 
 // ---------------------------------------------------------------------------
 // Split form for radius R = 1..8 (compile time), two streaming kernels:
-//  k_gauss_xy: one CTA per 32 x 16 tile of one plane filters u along x and
-//    then y in shared memory and writes the plane of t = G_y * G_x * u;
-//  k_gauss_z: one thread per (x, y) column and z chunk filters t along z with
+//  k_gauss_z: one thread per (x, y) column and z chunk filters u along z with
 //    a queue of 2R+1 pending output planes in registers (slots made static by
-//    unrolling the plane loop by 2R+1), writes r, and optionally evaluates the
-//    warped moving image m = I_m(x + r(x)) for the next iteration while r is
-//    still in registers (Algorithm A1: "update the moving image").
+//    unrolling the plane loop by 2R+1) and writes t = G_z * u;
+//  k_gauss_xy: one CTA per 32 x 32 tile of one plane filters t along x and
+//    then y in shared memory, writes r (or adds to it), and optionally
+//    evaluates the warped moving image m = I_m(x + r(x)) for the next
+//    iteration while r is still in registers (Algorithm A1: "update the
+//    moving image").
 // The x and y field components are processed as float2 pairs (packed FFMA2),
 // the z component as a scalar.
 // ---------------------------------------------------------------------------

@@ -142,8 +142,12 @@ def test_warp_matches_oracle(disc, shape):
     assert rel_err(host(m), O.warp(Im, r)) <= TOL
 
 
-@pytest.mark.parametrize("shape", [(13, 37, 70), (1, 1, 1), (1, 5, 40), (40, 1, 1), (7, 16, 32), (30, 3, 65)])
-@pytest.mark.parametrize("sigma,radius", [(1.0, 0), (1.5, 0), (2.0, 0), (0.8, 1)])
+# nx a multiple of 4 stages the xy pass's planes as float4 vectors, other nx
+# element by element; radii 1..8 cover every offset of the first tap in a vector
+@pytest.mark.parametrize("shape", [(13, 37, 70), (1, 1, 1), (1, 5, 40), (40, 1, 1), (7, 16, 32), (30, 3, 65),
+                                   (9, 45, 132), (6, 11, 12)])
+@pytest.mark.parametrize("sigma,radius", [(1.0, 0), (1.5, 0), (2.0, 0), (0.8, 1), (1.0, 2), (1.2, 4), (2.0, 7),
+                                          (2.5, 0)])
 def test_gauss_matches_oracle(disc, shape, sigma, radius):
     u = phantom.random_field(shape, 6, amp=3.0)
     r = empty(3, *shape)
