@@ -41,7 +41,7 @@ struct Level {
   float* m = nullptr;    // warped CT I_m(x + r(x))
   float* r = nullptr;    // field [3][N]
   float* u = nullptr;    // r + dr [3][N]
-  float* t = nullptr;    // xy-filtered field [3][N] (Gaussian scratch)
+  float* t = nullptr;    // z-filtered field [3][N] (Gaussian scratch)
   float* hist = nullptr; // l^(k) history
   double* hsum = nullptr;   // [hist_cap][2] sum |dr|, sum |r| behind each l^(k)
   int hist_cap = 0;

@@ -5,10 +5,12 @@
 // w_i proportional to exp(-i^2 / 2 sigma^2), |i| <= R, and on each axis the
 // weights are renormalised over the taps that fall inside the volume.
 //
-// A CTA owns a TX x TY column tile and marches over a chunk of z planes.  Each
-// plane of u (3 components, tile plus R halo) is staged in shared memory,
-// filtered along x and then y, and the xy-filtered plane is kept in a ring of
-// 2R+1 planes from which the z filter emits the output plane R behind.
+// Radii 1..8 take the split form below (a z pass, then an xy pass).  The
+// generic kernel, for any other case: a CTA owns a TX x TY column tile and
+// marches over a chunk of z planes.  Each plane of u (3 components, tile plus R
+// halo) is staged in shared memory, filtered along x and then y, and the
+// xy-filtered plane is kept in a ring of 2R+1 planes from which the z filter
+// emits the output plane R behind.
 
 #include <cmath>
 
