@@ -60,7 +60,6 @@ struct WideLayout {
   static constexpr int FO = XF - 1;                            // column of F element 0 in the box
   static constexpr int FN = FXT * FY;                          // floats of an F plane
   static constexpr int NMS = 4;                                // F planes of m in flight
-  static constexpr int TN = TX * TY;
   static constexpr int QX = TX / 4;                            // force stage: x quads per tile row
   static_assert(TX % 4 == 0 && NT == QX * TY, "force stage: one x quad of the tile per thread");
   static_assert(FXT % 4 == 0 && (1 + FO) % 4 == 0, "force stage: 16-byte aligned quads in the F planes");
