@@ -182,8 +182,9 @@ struct XYLayout {
 
 // The xy pass is the last of the two passes: it writes r (r = add + G u when
 // a.add is set, in place) and, with WARP, m = I_m(x + r(x)) for the next
-// iteration while r is in registers (WARP 1: 32-bit sample indices, for volumes
-// of fewer than 2^31 voxels; WARP 2: 64-bit).
+// iteration while r is in registers (WARP 1).  The warp's sample indices are
+// 32-bit: contexts hold fewer than 2^31 / 3 voxels per level (disc_set_images),
+// and the launches refuse a larger volume.
 template <int R, int WARP = 0>
 __device__ __forceinline__ void gauss_xy_body(const GaussArgs& a, int bx, int by, int bz) {
   using X = XYLayout<R>;
@@ -341,12 +342,9 @@ __device__ __forceinline__ void gauss_xy_body(const GaussArgs& a, int bx, int by
         st_at(t + g, a.r, 3LL * N, acc[b].x);
         st_at(t + N + g, a.r, 3LL * N, acc[b].y);
         st_at(t + 2 * N + g, a.r, 3LL * N, accz[b]);
-        if (WARP == 1)
+        if (WARP != 0)
           st_at(a.m + (size_t)z * plane + g, a.m, (long long)N,
                 warp_at32(a.Im, gx, gy, z, acc[b].x, acc[b].y, accz[b], nx, ny, a.nz));
-        else if (WARP == 2)
-          st_at(a.m + (size_t)z * plane + g, a.m, (long long)N,
-                warp_at(a.Im, gx, gy, z, acc[b].x, acc[b].y, accz[b], nx, ny, a.nz));
       }
     }
   }
@@ -470,8 +468,8 @@ __global__ void __launch_bounds__(kZThreads, kZCtasPerSM) k_gauss_z_batch(const 
   gauss_z_body<R>(bt.args[p], j % g.x, (j / g.x) % g.y, j / (g.x * g.y));
 }
 
-// Index width of the fused warp: 32-bit gathers while every index of I_m fits.
-inline int warp_kind(long long voxels) { return voxels < (1LL << 31) ? 1 : 2; }
+// The fused warp's 32-bit sample indices need every index of I_m to fit.
+inline bool warp_fits(long long voxels) { return voxels < (1LL << 31); }
 
 template <class K>
 cudaError_t set_xy_attrs(K k, size_t bytes) {
@@ -493,20 +491,15 @@ cudaError_t launch_batch_r(const GaussBatch& xy, int xy_total, const GaussBatch&
   if (!set[dev]) {
     if ((e = set_xy_attrs(k_gauss_xy_batch<R, 0>, XYLayout<R>::bytes)) != cudaSuccess) return e;
     if ((e = set_xy_attrs(k_gauss_xy_batch<R, 1>, XYLayout<R>::bytes)) != cudaSuccess) return e;
-    if ((e = set_xy_attrs(k_gauss_xy_batch<R, 2>, XYLayout<R>::bytes)) != cudaSuccess) return e;
     set[dev] = 1;
   }
+  if (warp)
+    for (int p = 0; p < xy.count; ++p)
+      if (!warp_fits((long long)xy.args[p].nx * xy.args[p].ny * xy.args[p].nz)) return cudaErrorInvalidValue;
   if (z_total > 0) e = launch_pdl(k_gauss_z_batch<R>, dim3(z_total), dim3(kZThreads), 0, s, z);
   if (e != cudaSuccess || xy_total <= 0) return e;
   if (!warp) return launch_pdl(k_gauss_xy_batch<R, 0>, dim3(xy_total), dim3(kThreads), XYLayout<R>::bytes, s, xy);
-  long long voxels = 0;
-  for (int p = 0; p < xy.count; ++p) {
-    const long long n = (long long)xy.args[p].nx * xy.args[p].ny * xy.args[p].nz;
-    if (n > voxels) voxels = n;
-  }
-  if (warp_kind(voxels) == 1)
-    return launch_pdl(k_gauss_xy_batch<R, 1>, dim3(xy_total), dim3(kThreads), XYLayout<R>::bytes, s, xy);
-  return launch_pdl(k_gauss_xy_batch<R, 2>, dim3(xy_total), dim3(kThreads), XYLayout<R>::bytes, s, xy);
+  return launch_pdl(k_gauss_xy_batch<R, 1>, dim3(xy_total), dim3(kThreads), XYLayout<R>::bytes, s, xy);
 }
 
 // z pass (u -> t) then xy pass (t -> r = add + G u, and m = I_m(x + r) when a.m
@@ -523,9 +516,9 @@ cudaError_t launch_split(const GaussArgs& a, const GaussPlan& p, cudaStream_t s)
   if (!set[dev]) {
     if ((e = set_xy_attrs(k_gauss_xy<R, 0>, XYLayout<R>::bytes)) != cudaSuccess) return e;
     if ((e = set_xy_attrs(k_gauss_xy<R, 1>, XYLayout<R>::bytes)) != cudaSuccess) return e;
-    if ((e = set_xy_attrs(k_gauss_xy<R, 2>, XYLayout<R>::bytes)) != cudaSuccess) return e;
     set[dev] = 1;
   }
+  if (a.m != nullptr && !warp_fits((long long)a.nx * a.ny * a.nz)) return cudaErrorInvalidValue;
   // z: u -> t
   GaussArgs zz = a;
   zz.r = a.t;
@@ -540,9 +533,7 @@ cudaError_t launch_split(const GaussArgs& a, const GaussPlan& p, cudaStream_t s)
   xy.u = a.t;
   dim3 gxy((a.nx + kSX - 1) / kSX, (a.ny + kSY - 1) / kSY, a.nz);
   if (a.m == nullptr) return launch_pdl(k_gauss_xy<R, 0>, gxy, dim3(kThreads), XYLayout<R>::bytes, s, xy);
-  if (warp_kind((long long)a.nx * a.ny * a.nz) == 1)
-    return launch_pdl(k_gauss_xy<R, 1>, gxy, dim3(kThreads), XYLayout<R>::bytes, s, xy);
-  return launch_pdl(k_gauss_xy<R, 2>, gxy, dim3(kThreads), XYLayout<R>::bytes, s, xy);
+  return launch_pdl(k_gauss_xy<R, 1>, gxy, dim3(kThreads), XYLayout<R>::bytes, s, xy);
 }
 
 cudaError_t launch_split_any(const GaussArgs& a, const GaussPlan& p, cudaStream_t s) {
