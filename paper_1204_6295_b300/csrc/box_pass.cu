@@ -391,7 +391,8 @@ BoxPlan box_plan(int mode, int nx, int ny, int nz, int hx, int hy, int hz, int n
 namespace {
 // The wide-tile plan where its one wave gets enough planes per CTA to amortise
 // the z warm-up of a march (grid.x = 0: not eligible).
-BoxPlan wide_plan(int nx, int ny, int nz, int hx, int hy, int hz, int num_sms, bool aligned) {
+BoxPlan wide_plan(int nx, int ny, int nz, int hx, int hy, int hz, int num_sms, bool aligned,
+                  int min_planes = kWideMinPlanes) {
   BoxPlan none{};
   none.grid = dim3(0, 0, 0);
   if (aligned && box_wide_ok(nx, ny, nz, hx, hy, hz)) {
@@ -400,7 +401,7 @@ BoxPlan wide_plan(int nx, int ny, int nz, int hx, int hy, int hz, int num_sms, b
     const int occ = box_wide_occupancy(hx);
     const long long slots = (long long)num_sms * (occ < 1 ? 1 : occ);
     const long long P = (long long)((nx + tx - 1) / tx) * ((ny + ty - 1) / ty) * nz;
-    if (occ >= 1 && (P >= kWideMinPlanes * slots || (test_switches() & DISC_SW_WIDE_ANY))) {
+    if (occ >= 1 && (P >= (long long)min_planes * slots || (test_switches() & DISC_SW_WIDE_ANY))) {
       BoxPlan p;
       p.tx = tx;
       p.ty = ty;
@@ -425,7 +426,8 @@ BoxPlan box_plan_iter(int nx, int ny, int nz, int hx, int hy, int hz, int num_sm
 BoxPlan box_plan_wide_mode(int mode, int nx, int ny, int nz, int hx, int hy, int hz, int num_sms,
                            const float* src, const float* out) {
   const bool aligned = (((uintptr_t)src | (uintptr_t)out) & 15u) == 0u;
-  const BoxPlan w = wide_plan(nx, ny, nz, hx, hy, hz, num_sms, aligned);
+  const BoxPlan w = wide_plan(nx, ny, nz, hx, hy, hz, num_sms, aligned,
+                              mode == kModeMaskAB ? kWideMinPlanesMask : kWideMinPlanes);
   return w.grid.x != 0 ? w : box_plan(mode, nx, ny, nz, hx, hy, hz, num_sms);
 }
 

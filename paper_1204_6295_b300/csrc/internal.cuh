@@ -183,11 +183,17 @@ BoxPlan box_plan(int mode, int nx, int ny, int nz, int hx, int hy, int hz, int n
 // the volume gives each CTA of its wave at least kWideMinPlanes planes; else
 // box_plan's.
 constexpr int kWideMinPlanes = 16;
+// The mask mode's wide pass writes more per voxel (a, b, d, stamp) and won only
+// where each CTA marches many planes: 4.1184 against 4.2238 s per masked
+// 512x512x256 schedule, but 326.7 against 321.9 ms per 256x256x128 one (about
+// 28 planes per CTA at its finest level).
+constexpr int kWideMinPlanesMask = 64;
 BoxPlan box_plan_iter(int nx, int ny, int nz, int hx, int hy, int hz, int num_sms, const float* src,
                       const float* r, const float* u);
 // The same choice for the SSD adjoint pass (kModeSsdAdjoint) and the mask pass
-// (kModeMaskAB): src the warped image, out the pass's first output buffer (the
-// library's buffers are aligned; NULL is accepted).
+// (kModeMaskAB, at least kWideMinPlanesMask planes per CTA): src the warped
+// image, out the pass's first output buffer (the library's buffers are aligned;
+// NULL is accepted).
 BoxPlan box_plan_wide_mode(int mode, int nx, int ny, int nz, int hx, int hy, int hz, int num_sms,
                            const float* src, const float* out);
 bool box_wide_ok(int nx, int ny, int nz, int hx, int hy, int hz);
