@@ -910,6 +910,30 @@ def run_profile_schedule(w):
     return 0
 
 
+def run_profile_batched():
+    """The batched workload's 16 pairs (for launch lists): one schedule that also
+    tunes each level, then a second one, as the timed steps run it, inside the
+    NVTX range "profiled batch schedule" (ncu --nvtx --nvtx-include selects it)."""
+    import torch
+    from paper_1204_6295_b300 import disc, phantom
+    bw = BATCH_WORKLOAD
+    sizes = phantom.batch_sizes(BATCH_PAIRS_PER_RANK)
+    images = phantom.batch_pair_images(BATCH_PAIRS_PER_RANK)
+    units = sum(schedule_units(dict(bw, dims=d)) for d in sizes)
+    with disc.Batch(len(images), **bw) as batch:
+        for i, (ct, cbct) in enumerate(images):
+            batch.set_images(i, ct, cbct)
+        batch.iterate(-1)                         # tunes every level
+        batch.restart()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("profiled batch schedule")
+        batch.iterate(-1)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+    print(json.dumps({"profile_batched": True, "pairs": [list(d) for d in sizes], "voxel_iterations": units}))
+    return 0
+
+
 def run_profile_masked(w, iters=2):
     """`iters` masked iterations (Eqs. 7-10) at the finest level only, from r = 0
     (for ncu captures of the fill passes): one context with one level."""
@@ -944,6 +968,9 @@ def main():
                     help="run one whole schedule of the workload and exit")
     ap.add_argument("--profile-masked", type=int, default=0, metavar="K",
                     help="run K masked iterations at the finest level and exit")
+    ap.add_argument("--profile-batched", action="store_true",
+                    help="run the 16-pair batched workload's schedule twice (the second in an NVTX range) "
+                         "and exit")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus > 0 else 1)))
@@ -957,6 +984,8 @@ def main():
         return run_profile_schedule(w)
     if args.profile_masked > 0:
         return run_profile_masked(w, args.profile_masked)
+    if args.profile_batched:
+        return run_profile_batched()
     if args.impl == "reference":
         return run_reference(args, w, rank, world)
     if args.split == "slab":
